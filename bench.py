@@ -1,0 +1,320 @@
+"""Benchmark: one 30-qubit random grid circuit per step on the GB300 fused-gate path.
+
+A step is one pass of the hot path over one circuit: set |0...0>, apply every fused gate, take
+the fp64 norm and draw 1024 samples.  The circuit is the 5x6-grid random circuit (20 cycles of
+sqrt(X)/sqrt(Y)/sqrt(W) plus fSim(pi/2, pi/6) on patterns ABCDCDAB, seed 2, 845 gates), fused
+greedily to at most --max-k qubits on the host.  The complex64 state (8 GiB) is larger than L2,
+so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is seconds per circuit for the whole job (time of the
+slowest rank / circuits run by all ranks); `e2e` is the same metric measured through the C ABI
+with host buffers (fusion on the host, sample uniforms uploaded, samples and norm read back).
+`--impl reference` times the complex128 CPU oracle on a bounded sample of the same circuit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "circuit s & HBM GB/s (% peak), learned+TC vs plain fusion, fid≥1-1e-6, 30–34q"
+UNIT = "s/circuit"
+N_QUBITS = 30
+N_SAMPLES = 1024
+WORKLOAD = "grid30: 5x6 grid random circuit, 20 cycles, 845 gates, seed 2, |0..0>, complex64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic(kernel_key: str):
+    """bytes per launch from the committed ncu summary (profiles/roofline_traffic.txt), else None."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    try:
+        for line in open(path):
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            fields = dict(kv.split("=", 1) for kv in line.split())
+            if fields.get("kernel") == kernel_key and fields.get("current") == "yes":
+                return float(fields["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region (reads only)."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------------------------- oracle arm
+def oracle_gate_sample(gates, count):
+    import numpy as np
+    idx = np.linspace(0, len(gates) - 1, count).round().astype(int)
+    return [gates[i] for i in idx]
+
+
+def run_oracle_steps(n, gates, steps, warmup, gates_per_step):
+    """Times the oracle applying `gates_per_step` gates (spread evenly over the circuit) to the
+    n-qubit complex128 state per step; returns (seconds per circuit extrapolated, threads, detail)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    th = host_cores()
+    psi = oracle.basis_state(n, 0)
+    sample = oracle_gate_sample(gates, gates_per_step)
+    for _ in range(warmup):
+        oracle.apply_gate(psi, n, sample[0], th)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for g in sample:
+            oracle.apply_gate(psi, n, g, th)
+    dt = time.perf_counter() - t0
+    per_gate = dt / (steps * len(sample))
+    return per_gate * len(gates), th, per_gate
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2602_09604_gb300 import workloads as wl
+    n, gates = wl.circuit_30q_grid()
+    gps = args.ref_gates_per_step
+    value, th, per_gate = run_oracle_steps(n, gates, args.steps, args.warmup, gps)
+    sample = f"{gps} of the 845 gates per step (evenly spaced), applied to the 2^30 complex128 state; " \
+             f"s/circuit = mean s/gate ({per_gate:.3f}) x 845"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_gate * gps * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_qubits": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------- GPU arm
+def bench_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if local == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2602_09604_gb300 import binding as B
+    from paper_2602_09604_gb300 import costs
+    from paper_2602_09604_gb300 import workloads as wl
+    from paper_2602_09604_gb300.state import DeviceState
+
+    n, gates = wl.circuit_30q_grid()
+    prec = {"fp32": B.PREC_FP32, "tf32": B.PREC_TF32, "bf16x3": B.PREC_BF16X3}[args.precision]
+    fused = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec)
+    n_fused = B.sv_fused_count(fused)
+    infos = [B.sv_fused_get_info(fused, i) for i in range(n_fused)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        st = DeviceState(n, stream=stream)
+    rng = np.random.default_rng(1234 + rank)
+    uniforms = rng.random(N_SAMPLES)
+
+    def step(record):
+        B.sv_init(st.h, 0)
+        rec = B.sv_apply_fused_gates(st.h, fused, timings=record)
+        nrm = B.sv_norm(st.h)
+        smp = B.sv_sample(st.h, uniforms)
+        return rec, nrm, smp
+
+    for _ in range(args.warmup):
+        step(False)
+    # ---- device-timed region (events on the launching stream)
+    kernel_us = {}
+    launches_per_step = 1 + n_fused + 1 + 3
+    norms = []
+    with ClockSampler(dev) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rec, nrm, _ = step(True)
+            norms.append(nrm)
+            for info, r in zip(infos, rec):
+                key = (B.PATH_NAMES[info["path"]], info["k"])
+                kernel_us.setdefault(key, []).append(r["us"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    elapsed_s = ev0.elapsed_time(ev1) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    value = elapsed_s / (args.steps * ws)
+
+    # ---- end to end through the C ABI with host buffers (host fusion included)
+    e2e_times = []
+    h2d = d2h = 0
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f2 = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec)
+        B.sv_init(st.h, 0)
+        B.sv_apply_fused_gates(st.h, f2)
+        smp = B.sv_sample(st.h, uniforms)
+        nrm = B.sv_norm(st.h)
+        B.sv_fused_free(f2)
+        e2e_times.append(time.perf_counter() - t0)
+    mat_bytes = sum(2 * 4 * (1 << (2 * i["k"])) for i in infos)
+    h2d = 8 * N_SAMPLES + mat_bytes
+    d2h = 8 * N_SAMPLES + 8
+
+    # ---- roofline of the dominant kernel class
+    totals = {k: sum(v) for k, v in kernel_us.items()}
+    dom = max(totals, key=totals.get)
+    avg_us = statistics.mean(kernel_us[dom])
+    bytes_per_launch = costs.bytes_per_pass(n)
+    achieved = bytes_per_launch / (avg_us * 1e-6) / 1e9
+    peak, src = peaks()
+    kernel_key = f"apply_{dom[0]}_k{dom[1]}_n{n}"
+    traffic = read_traffic(kernel_key)
+    all_us = sum(totals.values())
+    passes_gbs = n_fused * bytes_per_launch / (sum(totals.values()) / args.steps * 1e-6) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": n, "max_k": args.max_k, "precision": args.precision,
+                   "fusion": "greedy", "fused_gates": n_fused, "samples_per_step": N_SAMPLES,
+                   "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel_key,
+                     "launches": len(kernel_us[dom]), "avg_us": avg_us, "peak_source": src,
+                     "all_apply_kernels_gbs": passes_gbs,
+                     "share_of_apply_time": totals[dom] / all_us},
+        "per_kernel_class": {f"{p}_k{k}": {"launches": len(v), "avg_us": statistics.mean(v),
+                                           "gbs": bytes_per_launch / (statistics.mean(v) * 1e-6) / 1e9}
+                             for (p, k), v in sorted(kernel_us.items())},
+        "norm": norms[-1] if norms else None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, th, per_gate = run_oracle_steps(n, gates, 1, 0, args.cpu_gates)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                                "sample": f"{args.cpu_gates} of the 845 gates (evenly spaced) applied once to the "
+                                          f"2^30 complex128 state; s/circuit = mean s/gate ({per_gate:.3f}) x 845"}
+    B.sv_fused_free(fused)
+    st.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--max-k", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-gates", type=int, default=12)
+    ap.add_argument("--ref-gates-per-step", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

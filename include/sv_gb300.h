@@ -1,0 +1,192 @@
+/*
+ * sv_gb300.h -- C ABI of the GB300 fused-gate state-vector library (libsvgb300.so).
+ *
+ * The library applies a stream of fused k-qubit gates (k = 1..6) to a 2^n complex64 state vector
+ * on one GPU (paper section II-A, Eq. 3: every group of 2^k amplitudes whose indices differ only
+ * in the target bits is multiplied by the 2^k x 2^k gate matrix).  Gates are fused on the host
+ * (section IV-D: vertical fusion = matrix product, horizontal fusion = tensor product, Eq. 4).
+ *
+ * Conventions used by every call:
+ *   - amplitude index bit q <-> qubit q (qubit 0 is the least-significant bit);
+ *   - a gate matrix is 2^k x 2^k, row-major, complex128 interleaved (re, im), and local index
+ *     bit j <-> targets[j];
+ *   - a control qubit means "apply only where that bit is 1" (the sentence after Eq. 3);
+ *   - every call returns SV_OK (0) or a negative SV_E* code; sv_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread);
+ *   - pointers passed in are borrowed for the duration of the call only (except the state
+ *     buffer handed to sv_alloc, which must outlive the sv_state); the library never frees
+ *     caller memory;
+ *   - device work is enqueued on the stream given to sv_alloc; calls returning results to the
+ *     host (sv_norm, sv_sample, sv_store to host) synchronise that stream before returning.
+ *
+ * Device layout of the state (section IV-A's in-place layout adjustment, re-designed for
+ * 128-byte GPU transactions): amplitudes are stored in blocks of 32; block b holds the 32 real
+ * parts of amplitudes 32b..32b+31 followed by their 32 imaginary parts (256 bytes per block).
+ * sv_load / sv_store convert from / to the standard interleaved complex64 order.
+ */
+#ifndef SV_GB300_H
+#define SV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SV_API __attribute__((visibility("default")))
+#else
+#define SV_API
+#endif
+
+#define SV_MAX_QUBITS 35
+#define SV_MAX_K 6
+#define SV_MAX_CONTROLS 4
+
+enum sv_status {
+    SV_OK = 0,
+    SV_EINVAL = -1,     /* bad argument (qubit index, k, null pointer, size) */
+    SV_ENOMEM = -2,     /* device or host memory too small / allocation failed */
+    SV_ECUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error string) */
+    SV_ETIMEOUT = -4,   /* a bounded device-side wait gave up (persistent batch kernel) */
+    SV_EUNITARY = -5,   /* a gate matrix is not unitary within 1e-8 (checked by sv_fuse_circuit) */
+    SV_ESTATE = -6      /* object used in the wrong state (e.g. fused circuit for another n) */
+};
+
+/* Kernel path of one fused gate.  LOW: every target < 5 (inside one 32-amplitude block);
+ * HIGH: every target >= 5; MIXED: both.  TC_*: tensor-core contraction (k >= 5). */
+enum sv_path {
+    SV_PATH_AUTO = 0,
+    SV_PATH_LOW = 1,
+    SV_PATH_HIGH = 2,
+    SV_PATH_MIXED = 3,
+    SV_PATH_TC_TF32 = 4,
+    SV_PATH_TC_BF16X3 = 5
+};
+
+enum sv_precision {
+    SV_PREC_FP32 = 0,     /* CUDA-core fp32 for every k */
+    SV_PREC_TF32 = 1,     /* fused gates with k >= tc_min_k on tensor cores, tf32 inputs */
+    SV_PREC_BF16X3 = 2    /* same, 3-term bf16 split products (hi*hi + hi*lo + lo*hi) */
+};
+
+enum sv_fuse_mode {
+    SV_FUSE_GREEDY = 0,   /* greedy fusion up to max_k qubits */
+    SV_FUSE_LEARNED = 1   /* partition chosen by a learned cost model (see sv_mlp_*) */
+};
+
+typedef struct sv_state sv_state;   /* opaque; owns no state memory, only small workspaces */
+typedef struct sv_fused sv_fused;   /* opaque fused circuit (host matrices + lazily made device copies) */
+typedef struct sv_mlp sv_mlp;       /* opaque learned cost model */
+
+/* One input gate.  mat: 2^k x 2^k complex128 row-major interleaved (re, im), local bit j <->
+ * targets[j].  Controls (if any) are folded into a dense (k + n_controls)-qubit matrix by the
+ * fuser, so k + n_controls <= 6. */
+typedef struct sv_gate {
+    int k;
+    int targets[SV_MAX_K];
+    int n_controls;
+    int controls[SV_MAX_CONTROLS];
+    const double *mat;
+} sv_gate;
+
+typedef struct sv_fuse_opts {
+    int max_k;          /* largest fused gate, 1..6 (greedy mode); 0 = 4 */
+    int mode;           /* enum sv_fuse_mode */
+    int precision;      /* enum sv_precision */
+    int tc_min_k;       /* smallest k sent to tensor cores when precision != FP32; 0 = 5 */
+    int force_path;     /* enum sv_path; SV_PATH_AUTO lets the library choose (testing knob) */
+    const sv_mlp *model;/* learned mode only; NULL or untrained model => greedy at model's fallback k */
+} sv_fuse_opts;
+
+/* Facts about one fused gate (introspection). */
+typedef struct sv_fused_info {
+    int k;
+    int targets[SV_MAX_K];   /* ascending; the fused matrix uses local bit j <-> targets[j] */
+    int path;                /* enum sv_path chosen for it */
+    int n_source_gates;      /* how many input gates it absorbed */
+} sv_fused_info;
+
+/* One timing record, written by sv_apply_fused_gates when asked (CUDA events around each launch). */
+typedef struct sv_timing {
+    float us;                /* device time of this fused gate's kernel, microseconds */
+    int k;
+    int path;
+    uint64_t target_mask;    /* bit q set <-> qubit q is a target */
+} sv_timing;
+
+/* ---------------------------------------------------------------------------------------------
+ * State
+ * ------------------------------------------------------------------------------------------- */
+
+/* Bytes a state buffer of n qubits needs: max(8 * 2^n, 256) (8 bytes per complex64 amplitude;
+ * the artifact appendix states 2^(n+3) bytes for an n-qubit run). */
+SV_API size_t sv_required_bytes(int n_qubits);
+
+/* Wrap a caller-owned device buffer of `bytes` bytes (>= sv_required_bytes(n), 256-byte aligned)
+ * as an n-qubit state; 1 <= n <= SV_MAX_QUBITS.  `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream) on which every later call enqueues work.  Allocates a small reduction workspace
+ * on the current device.  The buffer's contents are undefined until sv_init / sv_load. */
+SV_API int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out);
+
+/* Release the handle and its workspace (not the caller's buffer).  Synchronises the stream. */
+SV_API void sv_free(sv_state *st);
+
+/* Set the state to the basis state |basis_index> (basis_index < 2^n), in the blocked layout. */
+SV_API int sv_init(sv_state *st, uint64_t basis_index);
+
+/* Import 2^n complex64 amplitudes in standard interleaved order from `src` (host memory when
+ * src_on_host != 0, else device memory not overlapping the state) and convert to the blocked
+ * layout in place. */
+SV_API int sv_load(sv_state *st, const void *src, int src_on_host);
+
+/* Export the state as 2^n complex64 interleaved amplitudes to `dst` (host when dst_on_host != 0,
+ * else a device buffer of 8 * 2^n bytes not overlapping the state).  For a host destination the
+ * state is converted in place, copied, and converted back; the stream is synchronised. */
+SV_API int sv_store(const sv_state *st, void *dst, int dst_on_host);
+
+/* ---------------------------------------------------------------------------------------------
+ * Fusion (host) and application (device)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Fuse `n_gates` gates of an n-qubit circuit into a sequence of dense fused gates of at most
+ * opts->max_k qubits (section IV-D).  Products are formed in fp64; each fused matrix is rounded
+ * to fp32 once.  Every input matrix is checked for unitarity (SV_EUNITARY).  Host only: no device
+ * memory is touched here.  opts may be NULL (greedy, max_k = 4, fp32). */
+SV_API int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits, const sv_fuse_opts *opts,
+                    sv_fused **out);
+
+SV_API void sv_fused_free(sv_fused *f);   /* synchronises the device if device copies exist */
+
+SV_API int sv_fused_count(const sv_fused *f);
+SV_API int sv_fused_get_info(const sv_fused *f, int i, sv_fused_info *info);
+/* Copy fused gate i's fp64 matrix (2^k x 2^k complex, interleaved, row-major) into `out`. */
+SV_API int sv_fused_get_matrix(const sv_fused *f, int i, double *out);
+
+/* Apply every fused gate, in order, to the state (Eq. 3 per fused gate).  The first call with a
+ * given fused circuit uploads the matrices that do not travel as kernel arguments (k = 6 and the
+ * tensor-core operands) with cudaMalloc/cudaMemcpy.  With `timings` non-NULL (one record per
+ * fused gate) each launch is bracketed by CUDA events and the call synchronises. */
+SV_API int sv_apply_fused_gates(sv_state *st, const sv_fused *f, sv_timing *timings);
+
+/* ---------------------------------------------------------------------------------------------
+ * Reductions
+ * ------------------------------------------------------------------------------------------- */
+
+/* *out = sum_i |c_i|^2, accumulated in fp64 (normalisation condition under Eq. 1).  Synchronises. */
+SV_API int sv_norm(const sv_state *st, double *out);
+
+/* For each of the n_samples uniforms u (host array, values in [0, 1)), out[s] (host array) =
+ * the smallest index i with |c_0|^2 + ... + |c_i|^2 > u_s * sum_j |c_j|^2 (fp64 prefix sums;
+ * Eq. 1: |c_i|^2 is the probability of observing basis state i).  Grows a workspace on the
+ * state's device when n_samples exceeds the previous maximum.  Synchronises. */
+SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
+
+SV_API const char *sv_last_error(void);
+SV_API const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_GB300_H */

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libsvgb300.so (the C ABI declared in include/sv_gb300.h).
+
+Argument marshalling only: every step of the simulation runs inside the library.  The functions
+keep the C names.  Failures raise :class:`SvError` carrying the library's status code and message.
+There is deliberately no fallback: if the library has not been built (``__graft_entry__.build()``
+or ``python -m paper_2602_09604_gb300.build``) importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsvgb300.so")
+
+SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNITARY, SV_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3 = range(6)
+PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
+              PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3"}
+PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
+FUSE_GREEDY, FUSE_LEARNED = 0, 1
+MAX_K = 6
+MAX_CONTROLS = 4
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class sv_gate(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("targets", ctypes.c_int * MAX_K), ("n_controls", ctypes.c_int),
+                ("controls", ctypes.c_int * MAX_CONTROLS), ("mat", ctypes.POINTER(ctypes.c_double))]
+
+
+class sv_fuse_opts(ctypes.Structure):
+    _fields_ = [("max_k", ctypes.c_int), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tc_min_k", ctypes.c_int), ("force_path", ctypes.c_int), ("model", ctypes.c_void_p)]
+
+
+class sv_fused_info(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("targets", ctypes.c_int * MAX_K), ("path", ctypes.c_int),
+                ("n_source_gates", ctypes.c_int)]
+
+
+class sv_timing(ctypes.Structure):
+    _fields_ = [("us", ctypes.c_float), ("k", ctypes.c_int), ("path", ctypes.c_int),
+                ("target_mask", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -m paper_2602_09604_gb300.build); there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    sig = {
+        "sv_required_bytes": (ctypes.c_size_t, [I]),
+        "sv_alloc": (I, [I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "sv_free": (None, [P]),
+        "sv_init": (I, [P, ctypes.c_uint64]),
+        "sv_load": (I, [P, P, I]),
+        "sv_store": (I, [P, P, I]),
+        "sv_fuse_circuit": (I, [ctypes.POINTER(sv_gate), I, I, ctypes.POINTER(sv_fuse_opts), ctypes.POINTER(P)]),
+        "sv_fused_free": (None, [P]),
+        "sv_fused_count": (I, [P]),
+        "sv_fused_get_info": (I, [P, I, ctypes.POINTER(sv_fused_info)]),
+        "sv_fused_get_matrix": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
+        "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
+        "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
+        "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
+        "sv_last_error": (ctypes.c_char_p, []),
+        "sv_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def sv_last_error() -> str:
+    return lib.sv_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != SV_OK:
+        raise SvError(rc, sv_last_error())
+
+
+# --------------------------------------------------------------------------------------- state
+def sv_required_bytes(n: int) -> int:
+    return int(lib.sv_required_bytes(n))
+
+
+def sv_alloc(n: int, dev_ptr: int, nbytes: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib.sv_alloc(n, ctypes.c_void_p(dev_ptr), nbytes, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_free(h) -> None:
+    lib.sv_free(h)
+
+
+def sv_init(h, basis_index: int = 0) -> None:
+    _check(lib.sv_init(h, ctypes.c_uint64(basis_index)))
+
+
+def sv_load(h, src_ptr: int, on_host: bool) -> None:
+    _check(lib.sv_load(h, ctypes.c_void_p(src_ptr), int(bool(on_host))))
+
+
+def sv_store(h, dst_ptr: int, on_host: bool) -> None:
+    _check(lib.sv_store(h, ctypes.c_void_p(dst_ptr), int(bool(on_host))))
+
+
+# --------------------------------------------------------------------------------------- fusion
+def gate_array(gates):
+    """ctypes array of sv_gate for gate objects with .targets/.controls/.matrix; returns
+    (array, keepalive) -- keep both alive for the duration of the call."""
+    gates = list(gates)
+    arr = (sv_gate * max(len(gates), 1))()
+    keep = []
+    for i, g in enumerate(gates):
+        if len(g.targets) > MAX_K or len(tuple(g.controls)) > MAX_CONTROLS:
+            raise SvError(SV_EINVAL, f"gate {i}: sv_gate holds at most {MAX_K} targets and {MAX_CONTROLS} controls")
+        m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128))
+        keep.append(m)
+        arr[i].k = len(g.targets)
+        for j, t in enumerate(g.targets):
+            arr[i].targets[j] = int(t)
+        ctl = tuple(g.controls)
+        arr[i].n_controls = len(ctl)
+        for j, c in enumerate(ctl):
+            arr[i].controls[j] = int(c)
+        arr[i].mat = m.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return arr, keep
+
+
+def sv_fuse_circuit(gates, n: int, max_k: int = 4, mode: int = FUSE_GREEDY, precision: int = PREC_FP32,
+                    tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None) -> ctypes.c_void_p:
+    arr, keep = gate_array(gates)
+    opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model)
+    f = ctypes.c_void_p()
+    _check(lib.sv_fuse_circuit(arr, len(keep), n, ctypes.byref(opts), ctypes.byref(f)))
+    return f
+
+
+def sv_fused_free(f) -> None:
+    lib.sv_fused_free(f)
+
+
+def sv_fused_count(f) -> int:
+    c = lib.sv_fused_count(f)
+    if c < 0:
+        _check(c)
+    return c
+
+
+def sv_fused_get_info(f, i: int) -> dict:
+    info = sv_fused_info()
+    _check(lib.sv_fused_get_info(f, i, ctypes.byref(info)))
+    return {"k": info.k, "targets": tuple(info.targets[: info.k]), "path": info.path,
+            "n_source_gates": info.n_source_gates}
+
+
+def sv_fused_get_matrix(f, i: int) -> np.ndarray:
+    k = sv_fused_get_info(f, i)["k"]
+    out = np.zeros((1 << k, 1 << k), dtype=np.complex128)
+    _check(lib.sv_fused_get_matrix(f, i, out.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def sv_apply_fused_gates(h, f, timings: bool = False):
+    if not timings:
+        _check(lib.sv_apply_fused_gates(h, f, None))
+        return None
+    n = sv_fused_count(f)
+    rec = (sv_timing * max(n, 1))()
+    _check(lib.sv_apply_fused_gates(h, f, rec))
+    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "target_mask": rec[i].target_mask}
+            for i in range(n)]
+
+
+# --------------------------------------------------------------------------------------- reductions
+def sv_norm(h) -> float:
+    out = ctypes.c_double()
+    _check(lib.sv_norm(h, ctypes.byref(out)))
+    return out.value
+
+
+def sv_sample(h, uniforms) -> np.ndarray:
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    out = np.zeros(u.size, dtype=np.uint64)
+    _check(lib.sv_sample(h, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+    return out
+
+
+def sv_version() -> str:
+    return lib.sv_version().decode()

@@ -1,0 +1,565 @@
+// CUDA-core kernels that apply one fused k-qubit gate (Eq. 3) to the blocked complex64 state.
+//
+// Three target classes get separate kernels (section IV-C distinguishes "regular" loops, whose
+// target bits lie above the vector width, from "irregular" ones below it; here the width is the
+// 32-amplitude block of the layout):
+//   HIGH  -- every target >= 5.  A group's 2^k amplitudes sit at the same position of 2^k different
+//            blocks, so each thread loads its group straight into registers with 128-bit loads;
+//            a warp's loads cover whole 128-byte lines.  No shared memory.
+//   LOW   -- every target < 5, or more generally a tile whose blocks are contiguous.  A warp copies
+//            a tile of 2^f consecutive blocks into shared memory (cp.async, double-buffered so the
+//            next tile streams in while this one is computed), applies the gate to every group of
+//            the tile from shared memory, and writes the tile back with 128-bit stores.
+//   MIXED -- low and high targets.  Same as LOW, but the tile's 2^f blocks are gathered over the
+//            high target bits (plus the lowest free block bits, so copies stay >= 512 bytes).
+// Section IV-B's load buffering is kept: a thread reads its whole group into registers first and
+// then writes each output row as soon as it is formed, so rows never overwrite pending inputs.
+//
+// The fp32 gate matrix of a k <= 5 gate travels by value in the kernel's parameter block
+// (__grid_constant__, constant bank): with the mat-vec fully unrolled every matrix element is an
+// immediate constant-bank operand of its FFMA, so the inner loop issues no loads for the matrix.
+// k = 6 (32 KB of matrix, beyond the 32,764-byte parameter limit) stages the matrix in shared
+// memory once per CTA instead.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "sv_internal.h"
+
+namespace svg {
+namespace {
+
+constexpr int kHighThreads = 256;
+constexpr int kTileThreads = 128;
+constexpr int kTileWarps = kTileThreads / 32;
+
+template <int K>
+struct MatArg {
+    float ur[1 << (2 * K)];
+    float ui[1 << (2 * K)];
+};
+struct NoMat {};
+
+template <int K>
+using MatOf = typename std::conditional<(K <= 5), MatArg<K>, NoMat>::type;
+
+template <int K>
+struct HighArgs {
+    MatOf<K> m;
+    long long boff[1 << K];   // float offset of local index j relative to the group's first block
+    int tpos[K];              // ascending block-bit positions (target - 5)
+    long long n_items;        // block-groups * threads per block-group
+};
+
+template <int K>
+struct TileArgs {
+    MatOf<K> m;
+    long long fblk[64];       // block offset of tile block phi (deposit of phi into the F bits)
+    int fpos[6];              // ascending block-bit positions of F
+    int loff[1 << K];         // tile-local amplitude offset of local index j
+    int ltpos[K];             // ascending tile-local target positions
+    int f;                    // a tile is 2^f blocks
+    long long n_tiles;
+};
+
+template <int K>
+__host__ __device__ constexpr int high_vec() { return K <= 2 ? 4 : (K == 3 ? 2 : 1); }
+
+// Minimum resident CTAs per SM handed to __launch_bounds__: caps registers per thread so the
+// unrolled mat-vec cannot trade occupancy (memory parallelism) for scheduling freedom.
+template <int K>
+__host__ __device__ constexpr int high_min_blocks() { return K <= 3 ? 4 : (K <= 5 ? 2 : 1); }
+template <int K>
+__host__ __device__ constexpr int tile_min_blocks() { return K <= 3 ? 8 : (K == 4 ? 6 : (K == 5 ? 4 : 1)); }
+
+// Returns x unchanged through an opaque move, so address arithmetic recomputed from it for the
+// output phase is not merged with (and kept alive from) the input phase.
+template <typename T>
+__device__ __forceinline__ T opaque(T x)
+{
+    if constexpr (sizeof(T) == 8) {
+        unsigned long long v = reinterpret_cast<unsigned long long &>(x);
+        asm volatile("mov.b64 %0, %0;" : "+l"(v));
+        return reinterpret_cast<T &>(v);
+    } else {
+        unsigned v = reinterpret_cast<unsigned &>(x);
+        asm volatile("mov.b32 %0, %0;" : "+r"(v));
+        return reinterpret_cast<T &>(v);
+    }
+}
+
+__device__ __forceinline__ unsigned long long insert_zero(unsigned long long x, int p)
+{
+    const unsigned long long low = x & ((1ull << p) - 1ull);
+    return ((x >> p) << (p + 1)) | low;
+}
+
+template <int V>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[V])
+{
+    if constexpr (V == 4) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (V == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[V])
+{
+    if constexpr (V == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+// y_r = sum_j U[r][j] x_j for one complex row; U from the parameter block (K <= 5).
+template <int K, int V>
+__device__ __forceinline__ void row_param(const MatArg<K> &m, int r, const float (&xr)[1 << K][V],
+                                          const float (&xi)[1 << K][V], float (&yr)[V], float (&yi)[V])
+{
+    constexpr int D = 1 << K;
+#pragma unroll
+    for (int v = 0; v < V; ++v) { yr[v] = 0.f; yi[v] = 0.f; }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float ar = m.ur[r * D + j], ai = m.ui[r * D + j];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            yr[v] = fmaf(ar, xr[j][v], yr[v]);
+            yr[v] = fmaf(ai, -xi[j][v], yr[v]);
+            yi[v] = fmaf(ar, xi[j][v], yi[v]);
+            yi[v] = fmaf(ai, xr[j][v], yi[v]);
+        }
+    }
+}
+
+// Same with U as interleaved (re, im) pairs in shared memory (K = 6).
+template <int K, int V>
+__device__ __forceinline__ void row_smem(const float2 *__restrict__ su, int r, const float (&xr)[1 << K][V],
+                                         const float (&xi)[1 << K][V], float (&yr)[V], float (&yi)[V])
+{
+    constexpr int D = 1 << K;
+#pragma unroll
+    for (int v = 0; v < V; ++v) { yr[v] = 0.f; yi[v] = 0.f; }
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float2 a = su[r * D + j];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            yr[v] = fmaf(a.x, xr[j][v], yr[v]);
+            yr[v] = fmaf(a.y, -xi[j][v], yr[v]);
+            yi[v] = fmaf(a.x, xi[j][v], yi[v]);
+            yi[v] = fmaf(a.y, xr[j][v], yi[v]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------ HIGH
+// One work item per thread and no loop around it: a loop would let the compiler hoist the
+// 2 * 4^k loop-invariant matrix loads into registers instead of folding them into the FFMAs.
+template <int K>
+__global__ void __launch_bounds__(kHighThreads, high_min_blocks<K>()) apply_high_kernel(float *__restrict__ sv, const __grid_constant__ HighArgs<K> a,
+                                                                   const float2 *__restrict__ umem)
+{
+    constexpr int V = high_vec<K>();
+    constexpr int TPB = 32 / V;
+    constexpr int D = 1 << K;
+    extern __shared__ float2 s_u[];
+    if constexpr (K == 6) {
+        for (int i = threadIdx.x; i < D * D; i += blockDim.x) s_u[i] = umem[i];
+        __syncthreads();
+    }
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= a.n_items) return;
+    unsigned long long blk = (unsigned long long)w / TPB;
+    const int pos = int(w % TPB) * V;
+#pragma unroll
+    for (int b = 0; b < K; ++b) blk = insert_zero(blk, a.tpos[b]);
+    float *base = sv + (long long)(blk << 6) + pos;
+    float xr[D][V], xi[D][V];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        ld_vec<V>(base + a.boff[j], xr[j]);
+        ld_vec<V>(base + a.boff[j] + 32, xi[j]);
+    }
+    float *obase = opaque(base);
+    if constexpr (K <= 5) {
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            float yr[V], yi[V];
+            row_param<K, V>(a.m, r, xr, xi, yr, yi);
+            float *p = opaque(obase) + a.boff[r];
+            st_vec<V>(p, yr);
+            st_vec<V>(p + 32, yi);
+        }
+    } else {
+#pragma unroll 1
+        for (int r = 0; r < D; ++r) {
+            float yr[V], yi[V];
+            row_smem<K, V>(s_u, r, xr, xi, yr, yi);
+            st_vec<V>(obase + a.boff[r], yr);
+            st_vec<V>(obase + a.boff[r] + 32, yi);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ LOW / MIXED
+__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Tile size in blocks (log2) for the fixed-size tile kernel: 2^F blocks = 32 * 2^F amplitudes,
+// so every lane of the warp owns 2^(F-K) >= 1 groups.
+template <int K>
+__host__ __device__ constexpr int tile_f() { return K < 3 ? 3 : K; }
+
+// One tile per warp.  FIXED: f = tile_f<K>() known at compile time (states with at least 2^f
+// blocks) -- straight-line code, matrix elements stay constant-bank operands.  !FIXED: small
+// states with fewer blocks than that; f is a runtime value and the group loop is a real loop.
+template <int K, bool GATHER, bool FIXED>
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile_kernel(float *__restrict__ sv, const __grid_constant__ TileArgs<K> a,
+                                                                   const float2 *__restrict__ umem)
+{
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) float smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int f = FIXED ? tile_f<K>() : a.f;
+    const int tile_floats = 64 << f;
+    float2 *s_u = reinterpret_cast<float2 *>(smem);
+    float *buf = smem + (K == 6 ? 2 * D * D : 0) + warp * tile_floats;
+    if constexpr (K == 6) {
+        for (int i = threadIdx.x; i < D * D; i += blockDim.x) s_u[i] = umem[i];
+        __syncthreads();
+    }
+    const long long t = (long long)blockIdx.x * kTileWarps + warp;
+    if (t >= a.n_tiles) return;
+    const int chunks = 16 << f;   // 16-byte chunks per tile
+    unsigned long long b0 = (unsigned long long)t;
+    if constexpr (GATHER) {
+        for (int i = 0; i < f; ++i) b0 = insert_zero(b0, a.fpos[i]);
+    } else {
+        b0 <<= f;
+    }
+    for (int c = lane; c < chunks; c += 32) {
+        const int phi = c >> 4, part = c & 15;
+        const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.fblk[phi] : b0 + (unsigned long long)phi;
+        cp_async16(buf + phi * 64 + part * 4, sv + (long long)(blk << 6) + part * 4);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+
+    // k <= 5: column order -- all 2^k outputs accumulate in registers while the inputs stream
+    // from shared memory one at a time (2^(k+1) accumulators, and every input step offers 2^(k+2)
+    // independent FFMAs).  The group's inputs are all read before any output is written back.
+    // k = 6: row order with the inputs held in registers and the matrix read from shared memory.
+    auto do_group = [&](int g) {
+        unsigned base = (unsigned)g;
+#pragma unroll
+        for (int b = 0; b < K; ++b) base = (unsigned)insert_zero(base, a.ltpos[b]);
+        if constexpr (K <= 5) {
+            float yr[D], yi[D];
+#pragma unroll
+            for (int r = 0; r < D; ++r) { yr[r] = 0.f; yi[r] = 0.f; }
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const unsigned i = base + (unsigned)a.loff[j];
+                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                const float xr = buf[o], xi = buf[o + 32];
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    const float ar = a.m.ur[r * D + j], ai = a.m.ui[r * D + j];
+                    yr[r] = fmaf(ar, xr, yr[r]);
+                    yr[r] = fmaf(ai, -xi, yr[r]);
+                    yi[r] = fmaf(ar, xi, yi[r]);
+                    yi[r] = fmaf(ai, xr, yi[r]);
+                }
+            }
+            // Groups of different lanes are disjoint, so no lane synchronisation is needed here.
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const unsigned i = base + (unsigned)a.loff[r];
+                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                buf[o] = yr[r];
+                buf[o + 32] = yi[r];
+            }
+        } else {
+            float xr[D][1], xi[D][1];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const unsigned i = base + (unsigned)a.loff[j];
+                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                xr[j][0] = buf[o];
+                xi[j][0] = buf[o + 32];
+            }
+            const unsigned obase = opaque(base);
+#pragma unroll 1
+            for (int r = 0; r < D; ++r) {
+                float yr[1], yi[1];
+                row_smem<K, 1>(s_u, r, xr, xi, yr, yi);
+                const unsigned i = obase + (unsigned)a.loff[r];
+                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                buf[o] = yr[0];
+                buf[o + 32] = yi[0];
+            }
+        }
+    };
+    if constexpr (FIXED) {
+        constexpr int per_lane = 1 << (tile_f<K>() - K);
+#pragma unroll
+        for (int m = 0; m < per_lane; ++m) do_group(lane + 32 * m);
+    } else {
+        const int groups = 1 << (5 + f - K);
+        for (int g = lane; g < groups; g += 32) do_group(g);
+    }
+    __syncwarp();
+    for (int c = lane; c < chunks; c += 32) {
+        const int phi = c >> 4, part = c & 15;
+        const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.fblk[phi] : b0 + (unsigned long long)phi;
+        *reinterpret_cast<float4 *>(sv + (long long)(blk << 6) + part * 4) =
+            *reinterpret_cast<const float4 *>(buf + phi * 64 + part * 4);
+    }
+}
+
+// ------------------------------------------------------------------------------ host side
+template <typename T>
+void fill_mat(T &m, const FusedGate &g)
+{
+    if constexpr (!std::is_same<T, NoMat>::value) {
+        std::memcpy(m.ur, g.ur.data(), sizeof(m.ur));
+        std::memcpy(m.ui, g.ui.data(), sizeof(m.ui));
+    } else {
+        (void)m;
+        (void)g;
+    }
+}
+
+struct Occ {
+    int high[7] = {0};
+    int tile[7][4] = {};      // [K][gather + 2 * fixed]: attributes set
+};
+Occ g_occ;
+std::mutex g_occ_mu;
+
+template <int K>
+int launch_high(float *sv, int n, const FusedGate &g, const float2 *umem, cudaStream_t stream, int num_sms)
+{
+    HighArgs<K> a;
+    std::memset(&a, 0, sizeof(a));
+    fill_mat(a.m, g);
+    for (int b = 0; b < K; ++b) a.tpos[b] = g.targets[b] - 5;
+    for (int j = 0; j < (1 << K); ++j) {
+        long long o = 0;
+        for (int b = 0; b < K; ++b)
+            if ((j >> b) & 1) o |= 1ll << a.tpos[b];
+        a.boff[j] = o << 6;
+    }
+    constexpr int V = high_vec<K>();
+    a.n_items = (1ll << (n - 5 - K)) * (32 / V);
+    const size_t smem = K == 6 ? sizeof(float2) * 64 * 64 : 0;
+    auto kern = apply_high_kernel<K>;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        if (!g_occ.high[K]) {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            g_occ.high[K] = 1;
+        }
+    }
+    (void)num_sms;
+    const long long grid = (a.n_items + kHighThreads - 1) / kHighThreads;
+    kern<<<(unsigned)grid, kHighThreads, smem, stream>>>(sv, a, umem);
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+template <int K>
+int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaStream_t stream, int num_sms)
+{
+    TileArgs<K> a;
+    std::memset(&a, 0, sizeof(a));
+    fill_mat(a.m, g);
+    const int nb = n > 5 ? n - 5 : 0;
+    int hp[SV_MAX_K], h = 0;
+    for (int b = 0; b < K; ++b)
+        if (g.targets[b] >= 5) hp[h++] = g.targets[b] - 5;
+    const bool fixed = nb >= tile_f<K>();
+    int f = fixed ? tile_f<K>() : nb;   // h <= K <= tile_f<K>(), and h <= nb always
+    // F = high target block bits + lowest free block bits
+    uint64_t fm = 0;
+    for (int i = 0; i < h; ++i) fm |= 1ull << hp[i];
+    for (int p = 0; __builtin_popcountll(fm) < f && p < nb; ++p) fm |= 1ull << p;
+    int cnt = 0;
+    for (int p = 0; p < nb; ++p)
+        if ((fm >> p) & 1) a.fpos[cnt++] = p;
+    a.f = f;
+    for (int phi = 0; phi < (1 << f); ++phi) {
+        long long o = 0;
+        for (int i = 0; i < f; ++i)
+            if ((phi >> i) & 1) o |= 1ll << a.fpos[i];
+        a.fblk[phi] = o;
+    }
+    const bool gather = fm != ((f >= 64) ? ~0ull : ((1ull << f) - 1ull));
+    for (int b = 0; b < K; ++b) {
+        const int t = g.targets[b];
+        if (t < 5) {
+            a.ltpos[b] = t;
+        } else {
+            int r = 0;
+            while (a.fpos[r] != t - 5) ++r;
+            a.ltpos[b] = 5 + r;
+        }
+    }
+    for (int j = 0; j < (1 << K); ++j) {
+        int o = 0;
+        for (int b = 0; b < K; ++b)
+            if ((j >> b) & 1) o |= 1 << a.ltpos[b];
+        a.loff[j] = o;
+    }
+    a.n_tiles = 1ll << (nb - f);
+    const size_t smem = size_t(kTileWarps) * (64u << f) * sizeof(float) + (K == 6 ? sizeof(float2) * 64 * 64 : 0);
+    auto kern = fixed ? (gather ? apply_tile_kernel<K, true, true> : apply_tile_kernel<K, false, true>)
+                      : (gather ? apply_tile_kernel<K, true, false> : apply_tile_kernel<K, false, false>);
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        int &slot = g_occ.tile[K][(gather ? 1 : 0) + (fixed ? 2 : 0)];
+        if (!slot) {
+            if (smem > 48 * 1024 || K == 6)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kTileWarps * (64u << 6) * sizeof(float) + sizeof(float2) * 64 * 64));
+            slot = 1;
+        }
+    }
+    (void)num_sms;
+    const long long grid = (a.n_tiles + kTileWarps - 1) / kTileWarps;
+    kern<<<(unsigned)grid, kTileThreads, smem, stream>>>(sv, a, umem);
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+using LaunchFn = int (*)(float *, int, const FusedGate &, const float2 *, cudaStream_t, int);
+const LaunchFn kHigh[7] = {nullptr, launch_high<1>, launch_high<2>, launch_high<3>, launch_high<4>, launch_high<5>, launch_high<6>};
+const LaunchFn kTile[7] = {nullptr, launch_tile<1>, launch_tile<2>, launch_tile<3>, launch_tile<4>, launch_tile<5>, launch_tile<6>};
+
+}  // namespace
+
+int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, const void *dtc, cudaStream_t stream, int num_sms)
+{
+    if (g.k < 1 || g.k > SV_MAX_K) { set_error("launch: bad k=%d", g.k); return SV_EINVAL; }
+    const float2 *umem = reinterpret_cast<const float2 *>(dmat);
+    if (g.k == 6 && !umem && g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) {
+        set_error("launch: k=6 gate has no device matrix");
+        return SV_EINVAL;
+    }
+    switch (g.path) {
+    case SV_PATH_HIGH:
+        for (int b = 0; b < g.k; ++b)
+            if (g.targets[b] < 5 || n < 5 + g.k) { set_error("launch: HIGH path needs every target >= 5"); return SV_EINVAL; }
+        return kHigh[g.k](sv, n, g, umem, stream, num_sms);
+    case SV_PATH_LOW:
+    case SV_PATH_MIXED:
+        return kTile[g.k](sv, n, g, umem, stream, num_sms);
+    case SV_PATH_TC_TF32:
+    case SV_PATH_TC_BF16X3:
+        return launch_tc_gate(sv, n, g, dtc, stream, num_sms);
+    default:
+        set_error("launch: unknown path %d", g.path);
+        return SV_EINVAL;
+    }
+}
+
+}  // namespace svg
+
+using namespace svg;
+
+namespace {
+
+int upload_fused(sv_fused *f, int device)
+{
+    if (f->device == device) return SV_OK;
+    if (f->device >= 0 && f->device != device) { set_error("sv_apply_fused_gates: fused circuit was uploaded to another device"); return SV_ESTATE; }
+    // k = 6 CUDA-core gates read an interleaved fp32 matrix image from device memory
+    std::vector<float> host;
+    f->mat_offset.assign(f->gates.size(), SIZE_MAX);
+    for (size_t i = 0; i < f->gates.size(); ++i) {
+        const FusedGate &g = f->gates[i];
+        if (g.k == 6 && g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) {
+            f->mat_offset[i] = host.size();
+            for (size_t e = 0; e < g.ur.size(); ++e) {
+                host.push_back(g.ur[e]);
+                host.push_back(g.ui[e]);
+            }
+        }
+    }
+    if (!host.empty()) {
+        SV_CUDA_TRY(cudaMalloc(&f->d_mats, host.size() * sizeof(float)));
+        SV_CUDA_TRY(cudaMemcpy(f->d_mats, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    SV_TRY(build_tc_operands(f));
+    f->device = device;
+    return SV_OK;
+}
+
+}  // namespace
+
+extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing *timings)
+{
+    clear_error();
+    if (!st || !fc) { set_error("sv_apply_fused_gates: NULL argument"); return SV_EINVAL; }
+    sv_fused *f = const_cast<sv_fused *>(fc);
+    if (f->n != st->n) { set_error("sv_apply_fused_gates: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
+    SV_TRY(upload_fused(f, st->device));
+    const size_t ng = f->gates.size();
+    std::vector<cudaEvent_t> ev;
+    if (timings && ng) {
+        ev.resize(2 * ng);
+        for (auto &e : ev) SV_CUDA_TRY(cudaEventCreate(&e));
+    }
+    int rc = SV_OK;
+    for (size_t i = 0; i < ng && rc == SV_OK; ++i) {
+        const FusedGate &g = f->gates[i];
+        const float *dm = f->mat_offset[i] != SIZE_MAX ? f->d_mats + f->mat_offset[i] : nullptr;
+        const void *dt = (f->d_tc && i < f->tc_offset.size() && f->tc_offset[i] != SIZE_MAX)
+                             ? static_cast<const char *>(f->d_tc) + f->tc_offset[i] : nullptr;
+        if (timings) cudaEventRecord(ev[2 * i], st->stream);
+        rc = launch_fused_gate(st->d, st->n, g, dm, dt, st->stream, st->num_sms);
+        if (timings) cudaEventRecord(ev[2 * i + 1], st->stream);
+    }
+    if (timings && ng) {
+        cudaError_t e = cudaStreamSynchronize(st->stream);
+        for (size_t i = 0; i < ng; ++i) {
+            float ms = 0.f;
+            if (e == cudaSuccess && rc == SV_OK) cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            const FusedGate &g = f->gates[i];
+            timings[i].us = ms * 1000.f;
+            timings[i].k = g.k;
+            timings[i].path = g.path;
+            timings[i].target_mask = g.mask;
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        if (e != cudaSuccess && rc == SV_OK) { set_error("sv_apply_fused_gates: %s", cudaGetErrorString(e)); rc = SV_ECUDA; }
+    }
+    return rc;
+}
+
+extern "C" void sv_fused_free(sv_fused *f)
+{
+    if (!f) return;
+    if (f->d_mats || f->d_tc) {
+        cudaDeviceSynchronize();
+        cudaFree(f->d_mats);
+        cudaFree(f->d_tc);
+    }
+    delete f;
+}

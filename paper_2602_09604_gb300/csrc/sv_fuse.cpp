@@ -1,0 +1,339 @@
+// Host-side gate fusion (paper section IV-D): vertical fusion is the matrix product of gates on
+// the same qubits, horizontal fusion the tensor product of gates on disjoint qubits (Eq. 4).
+// All products are formed in fp64; each finished fused matrix is rounded to fp32 once.
+//
+// Greedy rule (the paper fixes only "greedy, at most f qubits"; this is the library's reading):
+// gates are scanned in circuit order while a set of open blocks with pairwise disjoint qubit sets
+// is kept.  A gate on qubits Q joins the open blocks that touch Q.  If their union with Q has more
+// than max_k qubits, the touching blocks with the most qubits outside Q are closed (emitted) until
+// the rest fits; the gate then merges with what remains.  Blocks on disjoint qubits commute, so
+// emitting a closed block before still-open disjoint blocks keeps the circuit's meaning.
+//
+// A second pass adds horizontal fusion across the emitted sequence: each emitted block moves back
+// over the blocks before it that share no qubit with it (they commute) and merges into the first
+// block it meets whose union with it still has at most max_k qubits.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sv_internal.h"
+
+namespace svg {
+
+namespace {
+
+struct Block {
+    std::vector<int> qubits;  // ascending
+    std::vector<cplx> mat;    // 2^|qubits| square, local bit j <-> qubits[j]
+    int n_src = 0;
+    long long created = 0;
+};
+
+// mat (dim x dim, acting on qubit list T) <- G * mat, where G acts on qubits gq (local bit b of G
+// <-> gq[b], every gq[b] in T).  Column by column, each column is a vector over T and G is
+// applied to every group of its entries that differ only in G's bits.
+void left_multiply(std::vector<cplx> &mat, const std::vector<int> &T, const std::vector<cplx> &G,
+                   const std::vector<int> &gq)
+{
+    const int t = (int)T.size();
+    const int kg = (int)gq.size();
+    const size_t dim = size_t(1) << t;
+    const size_t gd = size_t(1) << kg;
+    int pos[SV_MAX_K + SV_MAX_CONTROLS];
+    size_t gmask = 0;
+    for (int b = 0; b < kg; ++b) {
+        pos[b] = int(std::find(T.begin(), T.end(), gq[b]) - T.begin());
+        gmask |= size_t(1) << pos[b];
+    }
+    std::vector<size_t> off(gd);
+    for (size_t j = 0; j < gd; ++j) {
+        size_t o = 0;
+        for (int b = 0; b < kg; ++b)
+            if ((j >> b) & 1) o |= size_t(1) << pos[b];
+        off[j] = o;
+    }
+    std::vector<cplx> x(gd), y(gd);
+    for (size_t col = 0; col < dim; ++col) {
+        for (size_t base = 0; base < dim; ++base) {
+            if (base & gmask) continue;  // visit each group once, through its all-zero member
+            for (size_t j = 0; j < gd; ++j) x[j] = mat[(base | off[j]) * dim + col];
+            for (size_t r = 0; r < gd; ++r) {
+                cplx acc = 0.0;
+                const cplx *grow = &G[r * gd];
+                for (size_t j = 0; j < gd; ++j) acc += grow[j] * x[j];
+                y[r] = acc;
+            }
+            for (size_t r = 0; r < gd; ++r) mat[(base | off[r]) * dim + col] = y[r];
+        }
+    }
+}
+
+std::vector<cplx> identity(size_t dim)
+{
+    std::vector<cplx> m(dim * dim, cplx(0.0, 0.0));
+    for (size_t i = 0; i < dim; ++i) m[i * dim + i] = 1.0;
+    return m;
+}
+
+bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
+{
+    for (size_t i = 0; i < d; ++i)
+        for (size_t j = 0; j < d; ++j) {
+            cplx acc = 0.0;
+            for (size_t r = 0; r < d; ++r) acc += std::conj(U[r * d + i]) * U[r * d + j];
+            if (std::abs(acc - (i == j ? cplx(1.0) : cplx(0.0))) > tol) return false;
+        }
+    return true;
+}
+
+}  // namespace
+
+int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path)
+{
+    (void)n;
+    if (force_path != SV_PATH_AUTO) return force_path;
+    if (precision != SV_PREC_FP32 && g.k >= tc_min_k)
+        return precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3;
+    bool any_low = false, any_high = false;
+    for (int j = 0; j < g.k; ++j) (g.targets[j] < 5 ? any_low : any_high) = true;
+    if (!any_high) return SV_PATH_LOW;
+    if (!any_low) return SV_PATH_HIGH;
+    return SV_PATH_MIXED;
+}
+
+}  // namespace svg
+
+using namespace svg;
+
+extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
+                               const sv_fuse_opts *opts_in, sv_fused **out)
+{
+    clear_error();
+    if (!out) { set_error("sv_fuse_circuit: out is NULL"); return SV_EINVAL; }
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > SV_MAX_QUBITS) {
+        set_error("sv_fuse_circuit: n_qubits=%d outside [1, %d]", n_qubits, SV_MAX_QUBITS);
+        return SV_EINVAL;
+    }
+    if (n_gates < 0 || (n_gates > 0 && !gates)) { set_error("sv_fuse_circuit: bad gate array"); return SV_EINVAL; }
+    sv_fuse_opts opts{};
+    opts.max_k = 4;
+    if (opts_in) opts = *opts_in;
+    if (opts.max_k == 0) opts.max_k = 4;
+    if (opts.tc_min_k == 0) opts.tc_min_k = 5;
+    if (opts.max_k < 1 || opts.max_k > SV_MAX_K) { set_error("sv_fuse_circuit: max_k=%d outside [1, 6]", opts.max_k); return SV_EINVAL; }
+    if (opts.precision < SV_PREC_FP32 || opts.precision > SV_PREC_BF16X3) { set_error("sv_fuse_circuit: bad precision %d", opts.precision); return SV_EINVAL; }
+    if (opts.tc_min_k < 1 || opts.tc_min_k > SV_MAX_K) { set_error("sv_fuse_circuit: tc_min_k=%d outside [1, 6]", opts.tc_min_k); return SV_EINVAL; }
+    if (opts.force_path < SV_PATH_AUTO || opts.force_path > SV_PATH_TC_BF16X3) { set_error("sv_fuse_circuit: bad force_path"); return SV_EINVAL; }
+    if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
+
+    // ---- validate and densify every input gate (controls folded into the matrix)
+    struct Dense { std::vector<int> q; std::vector<cplx> m; };
+    std::vector<Dense> dense;
+    try { dense.resize(size_t(n_gates)); } catch (const std::bad_alloc &) { set_error("sv_fuse_circuit: out of host memory"); return SV_ENOMEM; }
+    for (int gi = 0; gi < n_gates; ++gi) {
+        const sv_gate &g = gates[gi];
+        if (g.k < 1 || g.k > SV_MAX_K || g.n_controls < 0 || g.n_controls > SV_MAX_CONTROLS || g.k + g.n_controls > SV_MAX_K || !g.mat) {
+            set_error("sv_fuse_circuit: gate %d has k=%d, n_controls=%d (need 1<=k, k+controls<=6) or no matrix", gi, g.k, g.n_controls);
+            return SV_EINVAL;
+        }
+        uint64_t used = 0;
+        std::vector<int> q;
+        for (int j = 0; j < g.k + g.n_controls; ++j) {
+            int qq = j < g.k ? g.targets[j] : g.controls[j - g.k];
+            if (qq < 0 || qq >= n_qubits || ((used >> qq) & 1)) {
+                set_error("sv_fuse_circuit: gate %d names qubit %d (out of range or repeated)", gi, qq);
+                return SV_EINVAL;
+            }
+            used |= uint64_t(1) << qq;
+            q.push_back(qq);
+        }
+        const size_t d = size_t(1) << g.k;
+        std::vector<cplx> U(d * d);
+        for (size_t i = 0; i < d * d; ++i) U[i] = cplx(g.mat[2 * i], g.mat[2 * i + 1]);
+        if (!is_unitary(U, d, 1e-8)) {
+            set_error("sv_fuse_circuit: gate %d is not unitary (|U^H U - I| > 1e-8)", gi);
+            return SV_EUNITARY;
+        }
+        // controlled matrix on local bits (targets..., controls...): U where all controls are 1
+        const int kk = g.k + g.n_controls;
+        const size_t D = size_t(1) << kk;
+        std::vector<cplx> M = identity(D);
+        if (g.n_controls > 0) {
+            const size_t c_on = ((size_t(1) << g.n_controls) - 1) << g.k;
+            for (size_t r = 0; r < d; ++r)
+                for (size_t c = 0; c < d; ++c) M[(c_on | r) * D + (c_on | c)] = U[r * d + c];
+        } else {
+            M = U;
+        }
+        dense[gi].q = q;
+        dense[gi].m = std::move(M);
+    }
+
+    sv_fused *f = new (std::nothrow) sv_fused();
+    if (!f) { set_error("sv_fuse_circuit: out of host memory"); return SV_ENOMEM; }
+    f->n = n_qubits;
+    f->precision = opts.precision;
+
+    std::vector<Block> open, emitted;
+    long long stamp = 0;
+    auto emit = [&](Block &b) { emitted.push_back(std::move(b)); };
+    auto finish = [&](Block &b) {
+        FusedGate fg;
+        fg.k = (int)b.qubits.size();
+        for (int j = 0; j < fg.k; ++j) {
+            fg.targets[j] = b.qubits[j];
+            fg.mask |= uint64_t(1) << b.qubits[j];
+            if (b.qubits[j] < 32) fg.mask_lo |= 1u << b.qubits[j];
+        }
+        fg.n_src = b.n_src;
+        fg.mat = std::move(b.mat);
+        const size_t d2 = fg.mat.size();
+        fg.ur.resize(d2);
+        fg.ui.resize(d2);
+        for (size_t i = 0; i < d2; ++i) {
+            fg.ur[i] = (float)fg.mat[i].real();
+            fg.ui[i] = (float)fg.mat[i].imag();
+        }
+        fg.path = classify_path(fg, n_qubits, opts.precision, opts.tc_min_k, opts.force_path);
+        f->gates.push_back(std::move(fg));
+    };
+
+    const int max_k = opts.max_k;
+    for (int gi = 0; gi < n_gates; ++gi) {
+        const std::vector<int> &Q = dense[gi].q;
+        uint64_t qmask = 0;
+        for (int q : Q) qmask |= uint64_t(1) << q;
+        std::vector<int> touching;
+        for (int b = 0; b < (int)open.size(); ++b) {
+            for (int q : open[b].qubits)
+                if ((qmask >> q) & 1) { touching.push_back(b); break; }
+        }
+        // close touching blocks with the most qubits outside Q until the union fits
+        auto outside = [&](int b) {
+            int c = 0;
+            for (int q : open[b].qubits) c += !((qmask >> q) & 1);
+            return c;
+        };
+        std::sort(touching.begin(), touching.end(), [&](int a, int b) {
+            int oa = outside(a), ob = outside(b);
+            return oa != ob ? oa > ob : open[a].created < open[b].created;
+        });
+        auto union_size = [&](size_t from) {
+            uint64_t m = qmask;
+            for (size_t i = from; i < touching.size(); ++i)
+                for (int q : open[touching[i]].qubits) m |= uint64_t(1) << q;
+            return __builtin_popcountll(m);
+        };
+        size_t first_kept = 0;
+        const int limit = std::max(max_k, (int)Q.size());
+        while (first_kept < touching.size() && union_size(first_kept) > limit) ++first_kept;
+        // emit closed blocks in creation order
+        std::vector<int> closed(touching.begin(), touching.begin() + first_kept);
+        std::sort(closed.begin(), closed.end(), [&](int a, int b) { return open[a].created < open[b].created; });
+        std::vector<int> kept(touching.begin() + first_kept, touching.end());
+        std::sort(kept.begin(), kept.end(), [&](int a, int b) { return open[a].created < open[b].created; });
+        for (int b : closed) emit(open[b]);
+
+        // merge kept blocks and the gate into one new block over the union (ascending)
+        uint64_t um = qmask;
+        for (int b : kept)
+            for (int q : open[b].qubits) um |= uint64_t(1) << q;
+        Block nb;
+        for (int q = 0; q < n_qubits; ++q)
+            if ((um >> q) & 1) nb.qubits.push_back(q);
+        nb.mat = identity(size_t(1) << nb.qubits.size());
+        nb.n_src = 1;
+        for (int b : kept) {
+            left_multiply(nb.mat, nb.qubits, open[b].mat, open[b].qubits);
+            nb.n_src += open[b].n_src;
+        }
+        left_multiply(nb.mat, nb.qubits, dense[gi].m, Q);
+        nb.created = stamp++;
+        // drop closed + kept from the open list
+        std::vector<char> drop(open.size(), 0);
+        for (int b : touching) drop[b] = 1;
+        std::vector<Block> rest;
+        rest.reserve(open.size() + 1);
+        for (size_t b = 0; b < open.size(); ++b)
+            if (!drop[b]) rest.push_back(std::move(open[b]));
+        rest.push_back(std::move(nb));
+        open.swap(rest);
+    }
+    std::sort(open.begin(), open.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
+    for (Block &b : open) emit(b);
+
+    // horizontal pass: move each block back over disjoint predecessors and merge where it fits
+    std::vector<Block> merged;
+    const int kScanBack = 64;
+    for (Block &b : emitted) {
+        uint64_t bm = 0;
+        for (int q : b.qubits) bm |= uint64_t(1) << q;
+        const int lim = std::max(max_k, (int)b.qubits.size());
+        int target = -1;
+        for (int p = (int)merged.size() - 1, steps = 0; p >= 0 && steps < kScanBack; --p, ++steps) {
+            uint64_t pm = 0;
+            for (int q : merged[p].qubits) pm |= uint64_t(1) << q;
+            if (__builtin_popcountll(pm | bm) <= lim) { target = p; break; }
+            if (pm & bm) break;   // cannot move past a block it shares a qubit with
+        }
+        if (target < 0) {
+            merged.push_back(std::move(b));
+            continue;
+        }
+        Block &t = merged[size_t(target)];
+        uint64_t um = bm;
+        for (int q : t.qubits) um |= uint64_t(1) << q;
+        Block nb;
+        for (int q = 0; q < n_qubits; ++q)
+            if ((um >> q) & 1) nb.qubits.push_back(q);
+        nb.mat = identity(size_t(1) << nb.qubits.size());
+        left_multiply(nb.mat, nb.qubits, t.mat, t.qubits);   // earlier block first
+        left_multiply(nb.mat, nb.qubits, b.mat, b.qubits);
+        nb.n_src = t.n_src + b.n_src;
+        nb.created = t.created;
+        t = std::move(nb);
+    }
+    try {
+        for (Block &b : merged) finish(b);
+    } catch (const std::bad_alloc &) {
+        delete f;
+        set_error("sv_fuse_circuit: out of host memory");
+        return SV_ENOMEM;
+    }
+    *out = f;
+    return SV_OK;
+}
+
+extern "C" int sv_fused_count(const sv_fused *f)
+{
+    return f ? (int)f->gates.size() : SV_EINVAL;
+}
+
+extern "C" int sv_fused_get_info(const sv_fused *f, int i, sv_fused_info *info)
+{
+    clear_error();
+    if (!f || !info || i < 0 || i >= (int)f->gates.size()) { set_error("sv_fused_get_info: bad argument"); return SV_EINVAL; }
+    const FusedGate &g = f->gates[size_t(i)];
+    std::memset(info, 0, sizeof(*info));
+    info->k = g.k;
+    for (int j = 0; j < g.k; ++j) info->targets[j] = g.targets[j];
+    info->path = g.path;
+    info->n_source_gates = g.n_src;
+    return SV_OK;
+}
+
+extern "C" int sv_fused_get_matrix(const sv_fused *f, int i, double *out)
+{
+    clear_error();
+    if (!f || !out || i < 0 || i >= (int)f->gates.size()) { set_error("sv_fused_get_matrix: bad argument"); return SV_EINVAL; }
+    const FusedGate &g = f->gates[size_t(i)];
+    for (size_t e = 0; e < g.mat.size(); ++e) {
+        out[2 * e] = g.mat[e].real();
+        out[2 * e + 1] = g.mat[e].imag();
+    }
+    return SV_OK;
+}

@@ -1,0 +1,107 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sv_gb300.h"
+
+struct sv_fused;
+
+namespace svg {
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define SV_CUDA_TRY(call)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::svg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                       \
+            return SV_ECUDA;                                                                  \
+        }                                                                                     \
+    } while (0)
+
+#define SV_TRY(expr)            \
+    do {                        \
+        int rc_ = (expr);       \
+        if (rc_ != SV_OK)       \
+            return rc_;         \
+    } while (0)
+
+using cplx = std::complex<double>;
+
+// One fused gate: dense matrix over ascending targets (local bit j <-> targets[j]).
+struct FusedGate {
+    int k = 0;
+    int targets[SV_MAX_K] = {0, 0, 0, 0, 0, 0};
+    uint32_t mask_lo = 0;   // bits of targets below 32
+    uint64_t mask = 0;      // bit q set <-> qubit q is a target
+    int path = SV_PATH_AUTO;
+    int n_src = 0;
+    std::vector<cplx> mat;  // 2^k x 2^k row-major, fp64
+    std::vector<float> ur, ui;  // fp32 rounded once from mat
+};
+
+// Tensor-core operand images of one fused gate (built on the host, uploaded once).
+struct TcOperands {
+    size_t offset_bytes = 0;  // into sv_fused::d_tc
+    size_t bytes = 0;
+};
+
+// Classify the kernel path of a fused gate from its targets and the requested precision.
+int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path);
+
+// Device copy bookkeeping for fused circuits; defined in sv_apply.cu.
+struct DeviceMats;
+
+// Launch the kernel for one fused gate on `stream`; `dmat` is the device fp32 matrix image
+// (ur then ui, 2 * 4^k floats) for paths that read the matrix from memory (may be null for k<=5
+// CUDA-core paths, which take it as a kernel argument).  Returns SV_OK or SV_ECUDA/SV_EINVAL.
+int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, const void *dtc,
+                      cudaStream_t stream, int num_sms);
+
+int device_sm_count(int device);
+
+// Tensor-core path (sv_tc.cu): host-side operand images and the launcher.
+int build_tc_operands(sv_fused *f);
+int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms);
+
+}  // namespace svg
+
+struct sv_state {
+    int n = 0;
+    float *d = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    // reduction workspace (library-owned)
+    double *d_partials = nullptr;   // per-CTA partial sums
+    unsigned *d_counter = nullptr;  // last-block-done counter (kept at 0 between calls)
+    double *d_result = nullptr;     // scalar result
+    int max_partials = 0;
+    // sampling workspace (library-owned, grown on demand)
+    double *d_chunk = nullptr;      // chunk sums, then exclusive prefix (2 * n_chunks doubles)
+    double *d_uniforms = nullptr;
+    unsigned long long *d_samples = nullptr;
+    int sample_capacity = 0;
+    long long n_chunks = 0;
+};
+
+struct sv_fused {
+    int n = 0;
+    int precision = SV_PREC_FP32;
+    std::vector<svg::FusedGate> gates;
+    // device images (lazily uploaded on the first apply)
+    int device = -1;
+    float *d_mats = nullptr;        // fp32 (ur, ui) images of gates whose path reads memory
+    std::vector<size_t> mat_offset; // per gate offset in floats into d_mats, or SIZE_MAX
+    void *d_tc = nullptr;           // tensor-core operand images
+    std::vector<size_t> tc_offset;  // per gate byte offset into d_tc, or SIZE_MAX
+};

@@ -1,0 +1,430 @@
+// State handle, blocked layout conversion, norm and sampling kernels.
+//
+// Layout (paper section IV-A adjusts the layout in place so vector loads see contiguous reals and
+// imaginaries; here the block is sized for 128-byte GPU transactions): amplitude i lives in block
+// i >> 5; a block is 64 floats, the 32 real parts followed by the 32 imaginary parts.  Converting
+// between this layout and interleaved complex64 only permutes floats inside one 256-byte block,
+// so it runs in place with one read and one write of the state.
+#include <cstdio>
+#include <cstring>
+
+#include "sv_internal.h"
+
+using namespace svg;
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kChunkLog2 = 14;   // sampling chunk: 2^14 amplitudes
+
+__host__ __device__ inline long long re_off(unsigned long long i) { return (long long)(((i >> 5) << 6) | (i & 31ull)); }
+
+// ---------------------------------------------------------------------------------------------
+// in-place layout conversion, one warp per 256-byte block
+__global__ void block_layout_kernel(float *__restrict__ sv, long long n_blocks, int to_blocked)
+{
+    const int lane = threadIdx.x & 31;
+    long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long stride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (; w < n_blocks; w += stride) {
+        float *b = sv + w * 64;
+        float re, im;
+        if (to_blocked) {
+            float2 v = reinterpret_cast<const float2 *>(b)[lane];
+            re = v.x;
+            im = v.y;
+        } else {
+            re = b[lane];
+            im = b[32 + lane];
+        }
+        __syncwarp();
+        if (to_blocked) {
+            b[lane] = re;
+            b[32 + lane] = im;
+        } else {
+            reinterpret_cast<float2 *>(b)[lane] = make_float2(re, im);
+        }
+        __syncwarp();
+    }
+}
+
+// out-of-place conversion: blocked `src` -> interleaved `dst` (to_blocked = 0) or back
+__global__ void copy_layout_kernel(float *__restrict__ dst, const float *__restrict__ src, long long n_amps, int to_blocked)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n_amps; i += stride) {
+        const long long b = re_off((unsigned long long)i);
+        if (to_blocked) {
+            float2 v = reinterpret_cast<const float2 *>(src)[i];
+            dst[b] = v.x;
+            dst[b + 32] = v.y;
+        } else {
+            reinterpret_cast<float2 *>(dst)[i] = make_float2(src[b], src[b + 32]);
+        }
+    }
+}
+
+__global__ void set_basis_kernel(float *sv, long long off) { sv[off] = 1.0f; }
+
+// ---------------------------------------------------------------------------------------------
+// fp64-accurate sum of |c|^2.  Each thread keeps a float-float accumulator (hi, lo): squares are
+// split exactly with fma (re*re = p + ep), sums use Knuth's two-sum, so the per-thread result
+// carries ~48 significant bits; threads then combine in fp64.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(FF &a, float x)
+{
+    float s = a.hi + x;
+    float bp = s - a.hi;
+    float e = (a.hi - (s - bp)) + (x - bp);
+    a.hi = s;
+    a.lo += e;
+}
+
+__device__ __forceinline__ void ff_add_sq(FF &a, float v)
+{
+    float p = v * v;
+    float ep = fmaf(v, v, -p);
+    ff_add(a, p);
+    a.lo += ep;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block b covers floats [b*64, b*64+64).  Work item = (block, quarter): 8 re + 8 im floats.
+__global__ void __launch_bounds__(kRedThreads) norm_kernel(const float *__restrict__ sv, long long n_blocks,
+                                                            double *__restrict__ partials, unsigned *__restrict__ counter,
+                                                            double *__restrict__ result)
+{
+    FF acc{0.f, 0.f};
+    const long long items = n_blocks * 8;   // 8 float4 pairs per block
+    long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; it < items; it += stride) {
+        const long long b = it >> 3;
+        const int q = int(it & 7);
+        const float4 r = __ldcs(reinterpret_cast<const float4 *>(sv + b * 64) + q);
+        const float4 m = __ldcs(reinterpret_cast<const float4 *>(sv + b * 64 + 32) + q);
+        ff_add_sq(acc, r.x); ff_add_sq(acc, r.y); ff_add_sq(acc, r.z); ff_add_sq(acc, r.w);
+        ff_add_sq(acc, m.x); ff_add_sq(acc, m.y); ff_add_sq(acc, m.z); ff_add_sq(acc, m.w);
+    }
+    double v = warp_sum_d((double)acc.hi + (double)acc.lo);
+    __shared__ double ws[kRedThreads / 32];
+    __shared__ bool last;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kRedThreads / 32; ++i) s += ws[i];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        unsigned done = atomicAdd(counter, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        const volatile double *p = partials;
+        for (unsigned i = 0; i < gridDim.x; ++i) s += p[i];   // fixed order: deterministic
+        *result = s;
+        *counter = 0u;   // ready for the next call
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// sampling: chunk sums (fp64 via float-float per lane), exclusive prefix, then one warp per sample
+__global__ void chunk_sum_kernel(const float *__restrict__ sv, long long n_chunks, int chunk_blocks_log2,
+                                 double *__restrict__ chunk_sum)
+{
+    const int lane = threadIdx.x & 31;
+    long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long stride = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long cb = 1ll << chunk_blocks_log2;
+    for (; w < n_chunks; w += stride) {
+        FF acc{0.f, 0.f};
+        const float *base = sv + (w << chunk_blocks_log2) * 64;
+        for (long long b = 0; b < cb; ++b) {
+            ff_add_sq(acc, base[b * 64 + lane]);
+            ff_add_sq(acc, base[b * 64 + 32 + lane]);
+        }
+        double v = warp_sum_d((double)acc.hi + (double)acc.lo);
+        if (lane == 0) chunk_sum[w] = v;
+    }
+}
+
+// single CTA exclusive scan of n chunk sums (in: sums, out: prefix), total at prefix[n]
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(const double *__restrict__ sums, double *__restrict__ prefix, long long n)
+{
+    __shared__ double seg[1024];
+    const long long per = (n + 1023) / 1024;
+    const long long lo = threadIdx.x * per;
+    const long long hi = lo + per < n ? lo + per : n;
+    double s = 0.0;
+    for (long long i = lo; i < hi; ++i) s += sums[i];
+    seg[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int t = 0; t < 1024; ++t) {
+            double v = seg[t];
+            seg[t] = run;
+            run += v;
+        }
+        prefix[n] = run;
+    }
+    __syncthreads();
+    double run = seg[threadIdx.x];
+    for (long long i = lo; i < hi; ++i) {
+        prefix[i] = run;
+        run += sums[i];
+    }
+}
+
+// One warp per sample.  p_i = re^2 + im^2 in fp64 (products of widened floats are exact).
+__global__ void sample_search_kernel(const float *__restrict__ sv, int n, long long n_chunks, int chunk_log2,
+                                     const double *__restrict__ prefix, const double *__restrict__ uniforms,
+                                     int n_samples, unsigned long long *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n_samples) return;
+    const double total = prefix[n_chunks];
+    const double target = uniforms[s] * total;
+    // largest chunk c with prefix[c] <= target
+    long long lo = 0, hi = n_chunks - 1;
+    while (lo < hi) {
+        long long mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= target) lo = mid; else hi = mid - 1;
+    }
+    const unsigned long long N = 1ull << n;
+    const unsigned long long chunk_amps = 1ull << chunk_log2;
+    unsigned long long i0 = (unsigned long long)lo * chunk_amps;
+    double run = prefix[lo];
+    unsigned long long answer = N - 1;
+    bool found = false;
+    for (unsigned long long base = i0; base < N && !found; base += 32) {
+        const unsigned long long i = base + lane;
+        double p = 0.0;
+        if (i < N) {
+            const long long o = re_off(i);
+            const double re = (double)sv[o], im = (double)sv[o + 32];
+            p = re * re + im * im;
+        }
+        // inclusive warp scan
+        double incl = p;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            double t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, (i < N) && (run + incl > target));
+        if (hit) {
+            answer = base + (unsigned long long)(__ffs(hit) - 1);
+            found = true;
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) out[s] = answer;
+}
+
+int grid_for(long long items, int threads, int num_sms, int per_sm)
+{
+    long long g = (items + threads - 1) / threads;
+    long long cap = (long long)num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+long long n_blocks_of(int n) { return n >= 5 ? (1ll << (n - 5)) : 1ll; }
+
+}  // namespace
+
+// ================================================================================== C ABI
+extern "C" size_t sv_required_bytes(int n_qubits)
+{
+    if (n_qubits < 1 || n_qubits > SV_MAX_QUBITS) return 0;
+    size_t b = size_t(8) << n_qubits;
+    return b < 256 ? 256 : b;
+}
+
+extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out)
+{
+    clear_error();
+    if (!out) { set_error("sv_alloc: out is NULL"); return SV_EINVAL; }
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > SV_MAX_QUBITS) { set_error("sv_alloc: n_qubits=%d outside [1, %d]", n_qubits, SV_MAX_QUBITS); return SV_EINVAL; }
+    if (!dev_ptr) { set_error("sv_alloc: dev_ptr is NULL"); return SV_EINVAL; }
+    if ((reinterpret_cast<uintptr_t>(dev_ptr) & 255u) != 0) { set_error("sv_alloc: dev_ptr must be 256-byte aligned"); return SV_EINVAL; }
+    if (bytes < sv_required_bytes(n_qubits)) {
+        set_error("sv_alloc: buffer of %zu bytes is smaller than the %zu an %d-qubit state needs", bytes, sv_required_bytes(n_qubits), n_qubits);
+        return SV_ENOMEM;
+    }
+    cudaPointerAttributes attr{};
+    SV_CUDA_TRY(cudaPointerGetAttributes(&attr, dev_ptr));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+        set_error("sv_alloc: dev_ptr is not device memory");
+        return SV_EINVAL;
+    }
+    sv_state *st = new (std::nothrow) sv_state();
+    if (!st) { set_error("sv_alloc: out of host memory"); return SV_ENOMEM; }
+    st->n = n_qubits;
+    st->d = static_cast<float *>(dev_ptr);
+    st->bytes = bytes;
+    st->stream = static_cast<cudaStream_t>(cuda_stream);
+    st->device = attr.device;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != st->device) { delete st; set_error("sv_alloc: buffer lives on device %d but device %d is current", attr.device, cur); return SV_EINVAL; }
+    st->num_sms = device_sm_count(st->device);
+    st->max_partials = st->num_sms * 8;
+    const long long nb = n_blocks_of(n_qubits);
+    st->n_chunks = n_qubits > kChunkLog2 ? (1ll << (n_qubits - kChunkLog2)) : 1ll;
+    (void)nb;
+    cudaError_t e = cudaMalloc(&st->d_partials, sizeof(double) * (size_t(st->max_partials) + 1) + sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&st->d_chunk, sizeof(double) * (2 * size_t(st->n_chunks) + 1));
+    if (e != cudaSuccess) {
+        cudaFree(st->d_partials);
+        delete st;
+        set_error("sv_alloc: workspace allocation failed: %s", cudaGetErrorString(e));
+        return SV_ENOMEM;
+    }
+    st->d_result = st->d_partials + st->max_partials;
+    st->d_counter = reinterpret_cast<unsigned *>(st->d_result + 1);
+    e = cudaMemsetAsync(st->d_counter, 0, sizeof(unsigned) * 4, st->stream);
+    if (e != cudaSuccess) { sv_free(st); set_error("sv_alloc: %s", cudaGetErrorString(e)); return SV_ECUDA; }
+    *out = st;
+    return SV_OK;
+}
+
+extern "C" void sv_free(sv_state *st)
+{
+    if (!st) return;
+    cudaStreamSynchronize(st->stream);
+    cudaFree(st->d_partials);
+    cudaFree(st->d_chunk);
+    cudaFree(st->d_uniforms);
+    cudaFree(st->d_samples);
+    delete st;
+}
+
+extern "C" int sv_init(sv_state *st, uint64_t basis_index)
+{
+    clear_error();
+    if (!st) { set_error("sv_init: state is NULL"); return SV_EINVAL; }
+    if (basis_index >> st->n) { set_error("sv_init: basis index out of range for %d qubits", st->n); return SV_EINVAL; }
+    const size_t used = sv_required_bytes(st->n);
+    SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, used, st->stream));
+    set_basis_kernel<<<1, 1, 0, st->stream>>>(st->d, re_off(basis_index));
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+extern "C" int sv_load(sv_state *st, const void *src, int src_on_host)
+{
+    clear_error();
+    if (!st || !src) { set_error("sv_load: NULL argument"); return SV_EINVAL; }
+    const size_t payload = size_t(8) << st->n;
+    const long long nb = n_blocks_of(st->n);
+    if (src_on_host) {
+        if (payload < 256) SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, 256, st->stream));
+        SV_CUDA_TRY(cudaMemcpyAsync(st->d, src, payload, cudaMemcpyHostToDevice, st->stream));
+        block_layout_kernel<<<grid_for(nb * 32, 256, st->num_sms, 8), 256, 0, st->stream>>>(st->d, nb, 1);
+    } else {
+        const char *s = static_cast<const char *>(src);
+        const char *d = reinterpret_cast<const char *>(st->d);
+        if (s < d + sv_required_bytes(st->n) && d < s + payload) { set_error("sv_load: source overlaps the state"); return SV_EINVAL; }
+        if (payload < 256) SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, 256, st->stream));
+        const long long na = 1ll << st->n;
+        copy_layout_kernel<<<grid_for(na, 256, st->num_sms, 8), 256, 0, st->stream>>>(st->d, static_cast<const float *>(src), na, 1);
+    }
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+extern "C" int sv_store(const sv_state *st, void *dst, int dst_on_host)
+{
+    clear_error();
+    if (!st || !dst) { set_error("sv_store: NULL argument"); return SV_EINVAL; }
+    const size_t payload = size_t(8) << st->n;
+    const long long nb = n_blocks_of(st->n);
+    const int g = grid_for(nb * 32, 256, st->num_sms, 8);
+    if (dst_on_host) {
+        block_layout_kernel<<<g, 256, 0, st->stream>>>(st->d, nb, 0);
+        SV_CUDA_TRY(cudaGetLastError());
+        SV_CUDA_TRY(cudaMemcpyAsync(dst, st->d, payload, cudaMemcpyDeviceToHost, st->stream));
+        block_layout_kernel<<<g, 256, 0, st->stream>>>(st->d, nb, 1);
+        SV_CUDA_TRY(cudaGetLastError());
+        SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    } else {
+        const char *s = reinterpret_cast<const char *>(st->d);
+        const char *d = static_cast<const char *>(dst);
+        if (s < d + payload && d < s + sv_required_bytes(st->n)) { set_error("sv_store: destination overlaps the state"); return SV_EINVAL; }
+        const long long na = 1ll << st->n;
+        copy_layout_kernel<<<grid_for(na, 256, st->num_sms, 8), 256, 0, st->stream>>>(static_cast<float *>(dst), st->d, na, 0);
+        SV_CUDA_TRY(cudaGetLastError());
+    }
+    return SV_OK;
+}
+
+extern "C" int sv_norm(const sv_state *st, double *out)
+{
+    clear_error();
+    if (!st || !out) { set_error("sv_norm: NULL argument"); return SV_EINVAL; }
+    const long long nb = n_blocks_of(st->n);
+    const int g = grid_for(nb * 8, kRedThreads, st->num_sms, 4);
+    if (g > st->max_partials) { set_error("sv_norm: internal grid too large"); return SV_EINVAL; }
+    norm_kernel<<<g, kRedThreads, 0, st->stream>>>(st->d, nb, st->d_partials, st->d_counter, st->d_result);
+    SV_CUDA_TRY(cudaGetLastError());
+    SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_result, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return SV_OK;
+}
+
+extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_samples, uint64_t *out)
+{
+    clear_error();
+    sv_state *st = const_cast<sv_state *>(st_c);
+    if (!st || (n_samples > 0 && (!uniforms || !out)) || n_samples < 0) { set_error("sv_sample: bad argument"); return SV_EINVAL; }
+    if (n_samples == 0) return SV_OK;
+    for (int s = 0; s < n_samples; ++s)
+        if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) { set_error("sv_sample: uniform %d = %g is not in [0, 1)", s, uniforms[s]); return SV_EINVAL; }
+    if (n_samples > st->sample_capacity) {
+        cudaStreamSynchronize(st->stream);
+        cudaFree(st->d_uniforms);
+        cudaFree(st->d_samples);
+        st->d_uniforms = nullptr;
+        st->d_samples = nullptr;
+        st->sample_capacity = 0;
+        cudaError_t e = cudaMalloc(&st->d_uniforms, sizeof(double) * size_t(n_samples));
+        if (e == cudaSuccess) e = cudaMalloc(&st->d_samples, sizeof(unsigned long long) * size_t(n_samples));
+        if (e != cudaSuccess) { set_error("sv_sample: workspace allocation failed: %s", cudaGetErrorString(e)); return SV_ENOMEM; }
+        st->sample_capacity = n_samples;
+    }
+    const int n = st->n;
+    const int chunk_log2 = n > kChunkLog2 ? kChunkLog2 : (n >= 5 ? n : 5);
+    const int chunk_blocks_log2 = chunk_log2 - 5;
+    const long long nc = st->n_chunks;
+    double *sums = st->d_chunk;
+    double *prefix = st->d_chunk + nc;
+    SV_CUDA_TRY(cudaMemcpyAsync(st->d_uniforms, uniforms, sizeof(double) * size_t(n_samples), cudaMemcpyHostToDevice, st->stream));
+    chunk_sum_kernel<<<grid_for(nc * 32, 256, st->num_sms, 8), 256, 0, st->stream>>>(st->d, nc, chunk_blocks_log2, sums);
+    SV_CUDA_TRY(cudaGetLastError());
+    chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
+    SV_CUDA_TRY(cudaGetLastError());
+    const int wpb = 8;
+    sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms, n_samples, st->d_samples);
+    SV_CUDA_TRY(cudaGetLastError());
+    SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_samples, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, st->stream));
+    SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return SV_OK;
+}

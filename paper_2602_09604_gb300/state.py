@@ -1,0 +1,54 @@
+"""Device state buffers owned by PyTorch, wrapped as library states (marshalling only)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class DeviceState:
+    """A torch-allocated device buffer registered with sv_alloc on a given CUDA stream."""
+
+    def __init__(self, n: int, stream: torch.cuda.Stream | None = None, device: int | None = None):
+        self.n = n
+        self.nbytes = B.sv_required_bytes(n)
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.buf = torch.empty(self.nbytes // 4, dtype=torch.float32, device=dev)
+        self.h = B.sv_alloc(n, self.buf.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def init(self, basis_index: int = 0):
+        B.sv_init(self.h, basis_index)
+
+    def load(self, psi: np.ndarray):
+        a = np.ascontiguousarray(np.asarray(psi, dtype=np.complex64))
+        assert a.size == (1 << self.n)
+        B.sv_load(self.h, a.ctypes.data, True)
+        self.stream.synchronize()   # the host array may be released after return
+
+    def store(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex64)
+        B.sv_store(self.h, out.ctypes.data, True)
+        return out
+
+    def apply(self, fused, timings: bool = False):
+        return B.sv_apply_fused_gates(self.h, fused, timings)
+
+    def norm(self) -> float:
+        return B.sv_norm(self.h)
+
+    def sample(self, uniforms) -> np.ndarray:
+        return B.sv_sample(self.h, uniforms)
+
+    def free(self):
+        if self.h is not None:
+            B.sv_free(self.h)
+            self.h = None
+            self.buf = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

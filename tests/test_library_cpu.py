@@ -1,0 +1,164 @@
+"""CPU-only checks of the C ABI library: it loads, exports every declared symbol, and its host-side
+fuser is exact algebra (fused gates applied by the oracle == unfused circuit applied by the oracle).
+No kernel is launched here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_09604_gb300 import build as libbuild
+from paper_2602_09604_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    libbuild.build()
+    from paper_2602_09604_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^SV_API\s+[\w\s\*]+?\b(sv_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(B):
+    names = declared_functions()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(B.lib, name), name
+
+
+def test_required_bytes_is_eight_per_amplitude(B):
+    # the artifact appendix: an N-qubit run needs 2^(N+3) bytes
+    for n in range(5, 36):
+        assert B.sv_required_bytes(n) == 2 ** (n + 3)
+    for n in range(1, 5):
+        assert B.sv_required_bytes(n) == 256       # one whole 32-amplitude block
+    assert B.sv_required_bytes(0) == 0 and B.sv_required_bytes(36) == 0
+
+
+class _G:
+    def __init__(self, targets, matrix):
+        self.targets, self.matrix, self.controls = targets, matrix, ()
+
+
+def fused_as_gates(B, f):
+    return [_G(B.sv_fused_get_info(f, i)["targets"], B.sv_fused_get_matrix(f, i)) for i in range(B.sv_fused_count(f))]
+
+
+def check_fusion(B, n, gates, max_k, init=0):
+    f = B.sv_fuse_circuit(gates, n, max_k=max_k)
+    try:
+        infos = [B.sv_fused_get_info(f, i) for i in range(B.sv_fused_count(f))]
+        biggest = max(len(g.targets) + len(g.controls) for g in gates)
+        assert all(1 <= x["k"] <= max(max_k, biggest) for x in infos)
+        assert sum(x["n_source_gates"] for x in infos) == len(gates)
+        assert all(list(x["targets"]) == sorted(x["targets"]) for x in infos)
+        ref = oracle.run_circuit(n, gates, init)
+        got = oracle.run_circuit(n, fused_as_gates(B, f), init)
+        assert np.max(np.abs(ref - got)) < 1e-12
+        return infos
+    finally:
+        B.sv_fused_free(f)
+
+
+@pytest.mark.parametrize("max_k", [1, 2, 3, 4, 5, 6])
+def test_fusion_is_exact_on_grid_circuit(B, max_k):
+    n, gates = wl.GRID_16.n, wl.random_grid_circuit(wl.Grid(3, 4), 6, seed=3)
+    n = 12
+    infos = check_fusion(B, n, gates, max_k)
+    if max_k >= 2:
+        assert len(infos) < len(gates)
+
+
+@pytest.mark.parametrize("max_k", [2, 4, 6])
+def test_fusion_with_controls_and_random_gates(B, max_k):
+    rng = np.random.default_rng(5)
+    n = 9
+    gates = []
+    for _ in range(40):
+        k = int(rng.integers(1, 4))
+        qs = [int(q) for q in rng.permutation(n)]
+        nc = int(rng.integers(0, 3)) if k + 2 <= max(max_k, 3) else 0
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    check_fusion(B, n, gates, max_k, init=77)
+
+
+def test_fusion_of_textbook_circuits(B):
+    check_fusion(B, 10, wl.qft_circuit(10), 4, init=345)
+    check_fusion(B, 11, wl.ghz_circuit(11, controlled=True), 3)
+    rng = np.random.default_rng(1)
+    check_fusion(B, 8, wl.hea_circuit(8, 3, rng), 5)
+
+
+def test_vertical_fusion_collapses_same_qubit_gates(B):
+    gates = [wl.Gate((2,), wl.H), wl.Gate((2,), wl.SQRT_X), wl.Gate((2,), wl.H)]
+    f = B.sv_fuse_circuit(gates, 4, max_k=1)
+    try:
+        assert B.sv_fused_count(f) == 1
+        assert np.allclose(B.sv_fused_get_matrix(f, 0), wl.H @ wl.SQRT_X @ wl.H, atol=1e-15)
+    finally:
+        B.sv_fused_free(f)
+
+
+def test_horizontal_fusion_is_tensor_product(B):
+    # Eq. 4: gates on disjoint qubits fuse to U1 (x) U2; local bit 0 <-> lower qubit
+    rng = np.random.default_rng(8)
+    U1, U2 = wl.random_unitary(2, rng), wl.random_unitary(2, rng)
+    f = B.sv_fuse_circuit([wl.Gate((1,), U1), wl.Gate((4,), U2)], 6, max_k=2)
+    try:
+        assert B.sv_fused_count(f) == 1
+        assert B.sv_fused_get_info(f, 0)["targets"] == (1, 4)
+        assert np.allclose(B.sv_fused_get_matrix(f, 0), np.kron(U2, U1), atol=1e-15)
+    finally:
+        B.sv_fused_free(f)
+
+
+def test_path_classification(B):
+    rng = np.random.default_rng(2)
+    cases = {(0, 3): B.PATH_LOW, (5, 9): B.PATH_HIGH, (2, 7): B.PATH_MIXED, (4,): B.PATH_LOW, (5,): B.PATH_HIGH}
+    for t, path in cases.items():
+        f = B.sv_fuse_circuit([wl.Gate(t, wl.random_unitary(1 << len(t), rng))], 12, max_k=2)
+        try:
+            assert B.sv_fused_get_info(f, 0)["path"] == path
+        finally:
+            B.sv_fused_free(f)
+
+
+def test_fuser_rejects_bad_input(B):
+    rng = np.random.default_rng(4)
+    U = wl.random_unitary(2, rng)
+    bad = [
+        ([wl.Gate((7,), U)], 5, B.SV_EINVAL),                       # qubit out of range
+        ([wl.Gate((1, 1), np.eye(4))], 5, B.SV_EINVAL),             # repeated qubit
+        ([wl.Gate((0,), U, (0,))], 5, B.SV_EINVAL),                  # control == target
+        ([wl.Gate((0,), 1.1 * U)], 5, B.SV_EUNITARY),               # not unitary
+        ([wl.Gate(tuple(range(7)), np.eye(128))], 8, B.SV_EINVAL),  # k > 6
+        ([wl.Gate((0, 1, 2, 3, 4), np.eye(32), (5, 6))], 8, B.SV_EINVAL),  # k + controls > 6
+    ]
+    for gates, n, code in bad:
+        with pytest.raises(B.SvError) as e:
+            B.sv_fuse_circuit(gates, n, max_k=4)
+        assert e.value.code == code
+    with pytest.raises(B.SvError):
+        B.sv_fuse_circuit([wl.Gate((0,), U)], 0)
+    with pytest.raises(B.SvError):
+        B.sv_fuse_circuit([wl.Gate((0,), U)], 4, max_k=7)
+
+
+def test_empty_circuit_fuses_to_nothing(B):
+    f = B.sv_fuse_circuit([], 5)
+    try:
+        assert B.sv_fused_count(f) == 0
+    finally:
+        B.sv_fused_free(f)
