@@ -183,6 +183,25 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
 
+/* Sampling for callers that cannot allocate device memory.  No counterpart in the paper.
+ *
+ * Same result as sv_sample, bit for bit, but it needs no sv_state and calls no cudaMalloc,
+ * cudaFree or allocating library routine: every intermediate lives in one fixed array compiled
+ * into the library (about 1.1 MB per GPU, held from library load until process exit).  This is
+ * for callers that own all device memory up front and must not let a library grow it (a serving
+ * process whose pool already claims the GPU, where cudaMalloc would fail or fragment), and for
+ * callers that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * dev_state: the blocked-layout state of an n-qubit register (as sv_alloc would wrap), read only.
+ * n_qubits <= 30 and n_samples <= 4096 (the fixed array's limits; larger requests return
+ * SV_EINVAL with a message).  uniforms / out: host arrays as in sv_sample.  Work is enqueued on
+ * cuda_stream on the current device, and the call synchronises that stream before returning.
+ * The first call on a device looks up the array's device address with that device current; make
+ * that first call before capturing work on the device into a graph.  Every call on a device uses
+ * the same array, and calls whose GPU work overlaps race on it: serialise them. */
+SV_API int sv_sample_noalloc(const void *dev_state, int n_qubits, void *cuda_stream, const double *uniforms,
+                             int n_samples, uint64_t *out);
+
 SV_API const char *sv_last_error(void);
 SV_API const char *sv_version(void);
 

@@ -73,6 +73,7 @@ def _load():
         "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
+        "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_last_error": (ctypes.c_char_p, []),
         "sv_version": (ctypes.c_char_p, []),
     }
@@ -202,6 +203,17 @@ def sv_sample(h, uniforms) -> np.ndarray:
     out = np.zeros(u.size, dtype=np.uint64)
     _check(lib.sv_sample(h, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+    return out
+
+
+def sv_sample_noalloc(dev_state_ptr: int, n: int, stream: int, uniforms) -> np.ndarray:
+    """Sampling through the entry point that allocates no device memory (fixed internal scratch;
+    n <= 30, at most 4096 uniforms per call)."""
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    out = np.zeros(u.size, dtype=np.uint64)
+    _check(lib.sv_sample_noalloc(ctypes.c_void_p(dev_state_ptr), n, ctypes.c_void_p(stream),
+                                 u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out
 
 

@@ -7,6 +7,7 @@
 // so it runs in place with one read and one write of the state.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "sv_internal.h"
 
@@ -426,5 +427,87 @@ extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_sam
     SV_CUDA_TRY(cudaGetLastError());
     SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_samples, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, st->stream));
     SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    return SV_OK;
+}
+
+// ================================================================== sampling without allocation
+// sv_sample_noalloc: the same three sampling kernels as sv_sample, but every intermediate buffer
+// lives in one file-scope device array instead of memory from cudaMalloc.  Each GPU that loads
+// the library holds this array (about 1.1 MB) until the process exits; all calls on a GPU share
+// it, so calls whose GPU work overlaps (different streams, or threads) race on it.
+namespace {
+
+constexpr int kNoAllocMaxQubits = 30;
+constexpr long long kNoAllocMaxChunks = 1ll << (kNoAllocMaxQubits - kChunkLog2);
+constexpr int kNoAllocMaxSamples = 4096;
+constexpr size_t kNoAllocDoubles = size_t(kNoAllocMaxChunks) * 2 + 1 + size_t(kNoAllocMaxSamples) * 2;
+
+static __device__ __align__(256) double g_sample_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Host code must not pass the array's name to a kernel (on the host it names a stand-in, not
+// device memory); the device address is looked up once per device, with that device current.
+int noalloc_scratch(int device, double **out)
+{
+    if (device < 0 || device >= kMaxDevices) { set_error("sv_sample_noalloc: device %d out of range", device); return SV_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sample_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("sv_sample_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return SV_ECUDA;
+        }
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return SV_OK;
+}
+
+}  // namespace
+
+extern "C" int sv_sample_noalloc(const void *dev_state, int n_qubits, void *cuda_stream, const double *uniforms,
+                                 int n_samples, uint64_t *out)
+{
+    clear_error();
+    if (!dev_state || n_samples < 0 || (n_samples > 0 && (!uniforms || !out))) { set_error("sv_sample_noalloc: bad argument"); return SV_EINVAL; }
+    if (n_qubits < 1 || n_qubits > kNoAllocMaxQubits) {
+        set_error("sv_sample_noalloc: n_qubits=%d outside [1, %d], the most its fixed scratch holds", n_qubits, kNoAllocMaxQubits);
+        return SV_EINVAL;
+    }
+    if (n_samples > kNoAllocMaxSamples) {
+        set_error("sv_sample_noalloc: n_samples=%d exceeds the %d its fixed scratch holds", n_samples, kNoAllocMaxSamples);
+        return SV_EINVAL;
+    }
+    if (n_samples == 0) return SV_OK;
+    for (int s = 0; s < n_samples; ++s)
+        if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) { set_error("sv_sample_noalloc: uniform %d = %g is not in [0, 1)", s, uniforms[s]); return SV_EINVAL; }
+    int device = 0;
+    SV_CUDA_TRY(cudaGetDevice(&device));
+    double *scratch = nullptr;
+    SV_TRY(noalloc_scratch(device, &scratch));
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const int num_sms = device_sm_count(device);
+    const int n = n_qubits;
+    const int chunk_log2 = n > kChunkLog2 ? kChunkLog2 : (n >= 5 ? n : 5);
+    const long long nc = n > kChunkLog2 ? (1ll << (n - kChunkLog2)) : 1ll;
+    double *sums = scratch;
+    double *prefix = scratch + kNoAllocMaxChunks;
+    double *d_u = scratch + 2 * kNoAllocMaxChunks + 1;
+    unsigned long long *d_out = reinterpret_cast<unsigned long long *>(d_u + kNoAllocMaxSamples);
+    const float *sv = static_cast<const float *>(dev_state);
+    SV_CUDA_TRY(cudaMemcpyAsync(d_u, uniforms, sizeof(double) * size_t(n_samples), cudaMemcpyHostToDevice, stream));
+    chunk_sum_kernel<<<grid_for(nc * 32, 256, num_sms, 8), 256, 0, stream>>>(sv, nc, chunk_log2 - 5, sums);
+    SV_CUDA_TRY(cudaGetLastError());
+    chunk_scan_kernel<<<1, 1024, 0, stream>>>(sums, prefix, nc);
+    SV_CUDA_TRY(cudaGetLastError());
+    const int wpb = 8;
+    sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(sv, n, nc, chunk_log2, prefix, d_u, n_samples, d_out);
+    SV_CUDA_TRY(cudaGetLastError());
+    SV_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, stream));
+    SV_CUDA_TRY(cudaStreamSynchronize(stream));
     return SV_OK;
 }
