@@ -55,7 +55,7 @@ enum sv_status {
 };
 
 /* Kernel path of one fused gate.  LOW: every target < 5 (inside one 32-amplitude block);
- * HIGH: every target >= 5; MIXED: both.  TC_*: tensor-core contraction (k >= 5). */
+ * HIGH: every target >= 5; MIXED: both.  TC_*: tensor-core contraction (fused gates of 4-6 qubits). */
 enum sv_path {
     SV_PATH_AUTO = 0,
     SV_PATH_LOW = 1,
@@ -73,7 +73,8 @@ enum sv_precision {
 
 enum sv_fuse_mode {
     SV_FUSE_GREEDY = 0,   /* greedy fusion up to max_k qubits */
-    SV_FUSE_LEARNED = 1   /* partition chosen by a learned cost model (see sv_mlp_*) */
+    SV_FUSE_LEARNED = 1,  /* partition chosen by a learned cost model (see sv_mlp_*) */
+    SV_FUSE_NONE = 2      /* no fusion: every input gate becomes its own dense gate (timing, baselines) */
 };
 
 typedef struct sv_state sv_state;   /* opaque; owns no state memory, only small workspaces */
@@ -182,6 +183,10 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * Eq. 1: |c_i|^2 is the probability of observing basis state i).  Grows a workspace on the
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
+
+/* SV_OK if no kernel on the current device has given up a bounded wait since the last call, else
+ * SV_ETIMEOUT (the error is cleared by the call).  Synchronises the device. */
+SV_API int sv_device_status(void);
 
 /* Sampling for callers that cannot allocate device memory.  No counterpart in the paper.
  *

@@ -20,7 +20,7 @@ PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3 = range
 PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
               PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3"}
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
-FUSE_GREEDY, FUSE_LEARNED = 0, 1
+FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE = 0, 1, 2
 MAX_K = 6
 MAX_CONTROLS = 4
 
@@ -74,6 +74,7 @@ def _load():
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
+        "sv_device_status": (I, []),
         "sv_last_error": (ctypes.c_char_p, []),
         "sv_version": (ctypes.c_char_p, []),
     }
@@ -215,6 +216,10 @@ def sv_sample_noalloc(dev_state_ptr: int, n: int, stream: int, uniforms) -> np.n
                                  u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out
+
+
+def sv_device_status() -> None:
+    _check(lib.sv_device_status())
 
 
 def sv_version() -> str:

@@ -33,10 +33,11 @@ constexpr int kHighThreads = 256;
 constexpr int kTileThreads = 128;
 constexpr int kTileWarps = kTileThreads / 32;
 
+// fp32 matrix image passed by value: (re, im) pairs, ordered the way the kernel walks them so
+// consecutive FFMAs read neighbouring constant-bank words (HIGH: row-major; tile: column-major).
 template <int K>
 struct MatArg {
-    float ur[1 << (2 * K)];
-    float ui[1 << (2 * K)];
+    float u[2 << (2 * K)];
 };
 struct NoMat {};
 
@@ -59,7 +60,11 @@ struct TileArgs {
     int loff[1 << K];         // tile-local amplitude offset of local index j
     int ltpos[K];             // ascending tile-local target positions
     int f;                    // a tile is 2^f blocks
+    int lsh;                  // 5 - (number of targets below 5)
+    int lmask;                // 2^(number of targets below 5) - 1
     long long n_tiles;
+    unsigned char swz[64];    // in-block position XOR of tile block phi (see apply_tile_kernel)
+    unsigned char gswz[32];   // the same XOR, indexed by (group >> lsh) & lmask
 };
 
 template <int K>
@@ -130,7 +135,7 @@ __device__ __forceinline__ void row_param(const MatArg<K> &m, int r, const float
     for (int v = 0; v < V; ++v) { yr[v] = 0.f; yi[v] = 0.f; }
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const float ar = m.ur[r * D + j], ai = m.ui[r * D + j];
+        const float ar = m.u[2 * (r * D + j)], ai = m.u[2 * (r * D + j) + 1];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             yr[v] = fmaf(ar, xr[j][v], yr[v]);
@@ -225,9 +230,26 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int K>
 __host__ __device__ constexpr int tile_f() { return K < 3 ? 3 : K; }
 
+// XOR permutation of the four floats of one 16-byte chunk (s & 1 swaps neighbours, s & 2 swaps
+// pairs); it is its own inverse.
+__device__ __forceinline__ float4 xor_perm4(float4 v, unsigned s)
+{
+    if (s & 1u) { float t = v.x; v.x = v.y; v.y = t; t = v.z; v.z = v.w; v.w = t; }
+    if (s & 2u) { float t = v.x; v.x = v.z; v.z = t; t = v.y; v.y = v.w; v.w = t; }
+    return v;
+}
+
 // One tile per warp.  FIXED: f = tile_f<K>() known at compile time (states with at least 2^f
 // blocks) -- straight-line code, matrix elements stay constant-bank operands.  !FIXED: small
 // states with fewer blocks than that; f is a runtime value and the group loop is a real loop.
+//
+// Bank conflicts: the L targets below 5 leave only 2^(5-L) distinct in-block positions per input
+// index, so lanes whose groups sit in different blocks would hit the same banks 2^L times.  Each
+// tile block phi is therefore stored with its in-block positions XOR-ed by swz[phi], which puts
+// distinct values on the low target bits of the 2^L blocks one warp instruction touches.  Groups
+// keep their members in blocks with the same swizzle (members differ only in target bits), so a
+// lane applies one XOR, gswz, to all of its addresses.  The copies move 16-byte chunks through
+// registers: the XOR's bits 2-4 pick the chunk, bits 0-1 permute inside it.
 template <int K, bool GATHER, bool FIXED>
 __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile_kernel(float *__restrict__ sv, const __grid_constant__ TileArgs<K> a,
                                                                    const float2 *__restrict__ umem)
@@ -246,20 +268,42 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
     }
     const long long t = (long long)blockIdx.x * kTileWarps + warp;
     if (t >= a.n_tiles) return;
-    const int chunks = 16 << f;   // 16-byte chunks per tile
     unsigned long long b0 = (unsigned long long)t;
     if constexpr (GATHER) {
         for (int i = 0; i < f; ++i) b0 = insert_zero(b0, a.fpos[i]);
     } else {
         b0 <<= f;
     }
-    for (int c = lane; c < chunks; c += 32) {
-        const int phi = c >> 4, part = c & 15;
+    // chunk c of the tile: block phi = c >> 4, half (re / im) = (c >> 3) & 1, chunk q = c & 7
+    auto gaddr = [&](int c) -> float * {
+        const int phi = c >> 4;
         const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.fblk[phi] : b0 + (unsigned long long)phi;
-        cp_async16(buf + phi * 64 + part * 4, sv + (long long)(blk << 6) + part * 4);
+        return sv + (long long)(blk << 6) + (c & 15) * 4;
+    };
+    auto saddr = [&](int c, unsigned &sw) -> float * {
+        const int phi = c >> 4;
+        sw = a.swz[phi];
+        return buf + phi * 64 + (c & 8) * 4 + (((c & 7) ^ (int)(sw >> 2)) << 2);
+    };
+    if constexpr (FIXED) {
+        constexpr int CPL = (16 << tile_f<K>()) / 32;   // chunks per lane
+        float4 v[CPL];
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) v[i] = *reinterpret_cast<const float4 *>(gaddr(lane + 32 * i));
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            unsigned sw;
+            float *d = saddr(lane + 32 * i, sw);
+            *reinterpret_cast<float4 *>(d) = xor_perm4(v[i], sw);
+        }
+    } else {
+        for (int c = lane; c < (16 << f); c += 32) {
+            const float4 v = *reinterpret_cast<const float4 *>(gaddr(c));
+            unsigned sw;
+            float *d = saddr(c, sw);
+            *reinterpret_cast<float4 *>(d) = xor_perm4(v, sw);
+        }
     }
-    cp_async_commit();
-    cp_async_wait_all();
     __syncwarp();
 
     // k <= 5: column order -- all 2^k outputs accumulate in registers while the inputs stream
@@ -270,6 +314,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
         unsigned base = (unsigned)g;
 #pragma unroll
         for (int b = 0; b < K; ++b) base = (unsigned)insert_zero(base, a.ltpos[b]);
+        const unsigned sg = a.gswz[(g >> a.lsh) & a.lmask];
         if constexpr (K <= 5) {
             float yr[D], yi[D];
 #pragma unroll
@@ -277,11 +322,11 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const unsigned i = base + (unsigned)a.loff[j];
-                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 const float xr = buf[o], xi = buf[o + 32];
 #pragma unroll
                 for (int r = 0; r < D; ++r) {
-                    const float ar = a.m.ur[r * D + j], ai = a.m.ui[r * D + j];
+                    const float ar = a.m.u[2 * (j * D + r)], ai = a.m.u[2 * (j * D + r) + 1];
                     yr[r] = fmaf(ar, xr, yr[r]);
                     yr[r] = fmaf(ai, -xi, yr[r]);
                     yi[r] = fmaf(ar, xi, yi[r]);
@@ -292,7 +337,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
 #pragma unroll
             for (int r = 0; r < D; ++r) {
                 const unsigned i = base + (unsigned)a.loff[r];
-                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 buf[o] = yr[r];
                 buf[o + 32] = yi[r];
             }
@@ -301,7 +346,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const unsigned i = base + (unsigned)a.loff[j];
-                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 xr[j][0] = buf[o];
                 xi[j][0] = buf[o + 32];
             }
@@ -311,7 +356,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
                 float yr[1], yi[1];
                 row_smem<K, 1>(s_u, r, xr, xi, yr, yi);
                 const unsigned i = obase + (unsigned)a.loff[r];
-                const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 buf[o] = yr[0];
                 buf[o + 32] = yi[0];
             }
@@ -326,24 +371,29 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
         for (int g = lane; g < groups; g += 32) do_group(g);
     }
     __syncwarp();
-    for (int c = lane; c < chunks; c += 32) {
-        const int phi = c >> 4, part = c & 15;
-        const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.fblk[phi] : b0 + (unsigned long long)phi;
-        *reinterpret_cast<float4 *>(sv + (long long)(blk << 6) + part * 4) =
-            *reinterpret_cast<const float4 *>(buf + phi * 64 + part * 4);
+    for (int c = lane; c < (16 << f); c += 32) {
+        unsigned sw;
+        const float *s_ = saddr(c, sw);
+        *reinterpret_cast<float4 *>(gaddr(c)) = xor_perm4(*reinterpret_cast<const float4 *>(s_), sw);
     }
 }
 
 // ------------------------------------------------------------------------------ host side
 template <typename T>
-void fill_mat(T &m, const FusedGate &g)
+void fill_mat(T &m, const FusedGate &g, bool column_major)
 {
     if constexpr (!std::is_same<T, NoMat>::value) {
-        std::memcpy(m.ur, g.ur.data(), sizeof(m.ur));
-        std::memcpy(m.ui, g.ui.data(), sizeof(m.ui));
+        const int D = 1 << g.k;
+        for (int r = 0; r < D; ++r)
+            for (int j = 0; j < D; ++j) {
+                const int e = column_major ? j * D + r : r * D + j;
+                m.u[2 * e] = g.ur[size_t(r) * D + j];
+                m.u[2 * e + 1] = g.ui[size_t(r) * D + j];
+            }
     } else {
         (void)m;
         (void)g;
+        (void)column_major;
     }
 }
 
@@ -359,7 +409,7 @@ int launch_high(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
 {
     HighArgs<K> a;
     std::memset(&a, 0, sizeof(a));
-    fill_mat(a.m, g);
+    fill_mat(a.m, g, false);
     for (int b = 0; b < K; ++b) a.tpos[b] = g.targets[b] - 5;
     for (int j = 0; j < (1 << K); ++j) {
         long long o = 0;
@@ -390,7 +440,7 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
 {
     TileArgs<K> a;
     std::memset(&a, 0, sizeof(a));
-    fill_mat(a.m, g);
+    fill_mat(a.m, g, true);
     const int nb = n > 5 ? n - 5 : 0;
     int hp[SV_MAX_K], h = 0;
     for (int b = 0; b < K; ++b)
@@ -428,6 +478,32 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
             if ((j >> b) & 1) o |= 1 << a.ltpos[b];
         a.loff[j] = o;
     }
+    // swizzle: deposit the lowest L non-target tile-block bits onto the L low target positions
+    int lowt[5], L = 0;
+    for (int b = 0; b < K; ++b)
+        if (g.targets[b] < 5) lowt[L++] = g.targets[b];
+    int nont[6], nn = 0;
+    for (int r = 0; r < f; ++r) {
+        bool is_t = false;
+        for (int b = 0; b < K; ++b)
+            if (a.ltpos[b] == 5 + r) is_t = true;
+        if (!is_t) nont[nn++] = r;
+    }
+    auto deposit_low = [&](int v) {
+        int o = 0;
+        for (int i = 0; i < L; ++i)
+            if ((v >> i) & 1) o |= 1 << lowt[i];
+        return o;
+    };
+    for (int phi = 0; phi < (1 << f); ++phi) {
+        int c = 0;
+        for (int i = 0; i < nn; ++i)
+            if ((phi >> nont[i]) & 1) c |= 1 << i;
+        a.swz[phi] = (unsigned char)deposit_low(c & ((1 << L) - 1));
+    }
+    for (int v = 0; v < (1 << L); ++v) a.gswz[v] = (unsigned char)deposit_low(v);
+    a.lsh = 5 - L;
+    a.lmask = (1 << L) - 1;
     a.n_tiles = 1ll << (nb - f);
     const size_t smem = size_t(kTileWarps) * (64u << f) * sizeof(float) + (K == 6 ? sizeof(float2) * 64 * 64 : 0);
     auto kern = fixed ? (gather ? apply_tile_kernel<K, true, true> : apply_tile_kernel<K, false, true>)
@@ -549,8 +625,26 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
         }
         for (auto &x : ev) cudaEventDestroy(x);
         if (e != cudaSuccess && rc == SV_OK) { set_error("sv_apply_fused_gates: %s", cudaGetErrorString(e)); rc = SV_ECUDA; }
+        int code = 0;
+        if (rc == SV_OK && read_device_errors(&code) == SV_OK && code) {
+            set_error("sv_apply_fused_gates: a kernel gave up a bounded wait (device code 0x%x)", code);
+            rc = SV_ETIMEOUT;
+        }
     }
     return rc;
+}
+
+extern "C" int sv_device_status(void)
+{
+    clear_error();
+    SV_CUDA_TRY(cudaDeviceSynchronize());
+    int code = 0;
+    SV_TRY(read_device_errors(&code));
+    if (code) {
+        set_error("a kernel gave up a bounded wait (device code 0x%x)", code);
+        return SV_ETIMEOUT;
+    }
+    return SV_OK;
 }
 
 extern "C" void sv_fused_free(sv_fused *f)

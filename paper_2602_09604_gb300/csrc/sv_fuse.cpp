@@ -95,7 +95,7 @@ int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int fo
 {
     (void)n;
     if (force_path != SV_PATH_AUTO) return force_path;
-    if (precision != SV_PREC_FP32 && g.k >= tc_min_k)
+    if (precision != SV_PREC_FP32 && g.k >= tc_min_k && g.k >= 4)
         return precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3;
     bool any_low = false, any_high = false;
     for (int j = 0; j < g.k; ++j) (g.targets[j] < 5 ? any_low : any_high) = true;
@@ -128,7 +128,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     if (opts.precision < SV_PREC_FP32 || opts.precision > SV_PREC_BF16X3) { set_error("sv_fuse_circuit: bad precision %d", opts.precision); return SV_EINVAL; }
     if (opts.tc_min_k < 1 || opts.tc_min_k > SV_MAX_K) { set_error("sv_fuse_circuit: tc_min_k=%d outside [1, 6]", opts.tc_min_k); return SV_EINVAL; }
     if (opts.force_path < SV_PATH_AUTO || opts.force_path > SV_PATH_TC_BF16X3) { set_error("sv_fuse_circuit: bad force_path"); return SV_EINVAL; }
-    if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
+    if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
 
     // ---- validate and densify every input gate (controls folded into the matrix)
     struct Dense { std::vector<int> q; std::vector<cplx> m; };
@@ -202,7 +202,27 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         f->gates.push_back(std::move(fg));
     };
 
-    const int max_k = opts.max_k;
+    const int max_k = opts.mode == SV_FUSE_NONE ? 0 : opts.max_k;
+    if (opts.mode == SV_FUSE_NONE) {
+        // one block per input gate, matrix re-expressed over its ascending qubit list
+        try {
+            for (int gi = 0; gi < n_gates; ++gi) {
+                Block b;
+                b.qubits = dense[gi].q;
+                std::sort(b.qubits.begin(), b.qubits.end());
+                b.mat = identity(size_t(1) << b.qubits.size());
+                left_multiply(b.mat, b.qubits, dense[gi].m, dense[gi].q);
+                b.n_src = 1;
+                finish(b);
+            }
+        } catch (const std::bad_alloc &) {
+            delete f;
+            set_error("sv_fuse_circuit: out of host memory");
+            return SV_ENOMEM;
+        }
+        *out = f;
+        return SV_OK;
+    }
     for (int gi = 0; gi < n_gates; ++gi) {
         const std::vector<int> &Q = dense[gi].q;
         uint64_t qmask = 0;

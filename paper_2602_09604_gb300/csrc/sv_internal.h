@@ -71,6 +71,9 @@ int device_sm_count(int device);
 // Tensor-core path (sv_tc.cu): host-side operand images and the launcher.
 int build_tc_operands(sv_fused *f);
 int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms);
+// Reads and clears the current device's error word written by kernels whose bounded waits timed
+// out (0 = none).  Synchronous.
+int read_device_errors(int *code);
 
 }  // namespace svg
 

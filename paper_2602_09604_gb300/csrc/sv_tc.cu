@@ -1,23 +1,563 @@
-// Tensor-core contraction path for large fused gates (placeholder until the tcgen05 kernel lands).
+// Tensor-core path: a fused k-qubit gate (k = 4..6) as a real GEMM on the 5th-generation tensor
+// cores (tcgen05, accumulators in tensor memory).
+//
+// Eq. 3 for all groups at once is the complex product Y = U X with X = [x_g] (2^k x 2^(n-k)).
+// Written over the reals with the groups as rows:
+//     Y^T[g, (c', r)] = sum_(c, j) X^T[g, (c, j)] * B[(c, j), (c', r)]
+// where (c, j) indexes (real/imaginary part, amplitude j of the group) and
+//     B[(0,j),(0,r)] = Re U[r][j]   B[(1,j),(0,r)] = -Im U[r][j]
+//     B[(0,j),(1,r)] = Im U[r][j]   B[(1,j),(1,r)] =  Re U[r][j].
+// One MMA tile is M = 128 groups, N = K = 2^(k+1).  Precision modes:
+//   TF32   -- inputs rounded to tf32 (cvt.rna), one product, fp32 accumulation;
+//   BF16X3 -- each operand split into bf16 hi + lo (lo = the rounded remainder), three products
+//             hi*hi + hi*lo + lo*hi accumulated in fp32; the dropped lo*lo term and the split
+//             remainders are ~2^-16 relative.
+//
+// Kernel structure (persistent, one CTA of 4 warps per SM slot):
+//   * B (the gate's real block matrix, pre-split and pre-laid-out on the host in the tcgen05
+//     K-major no-swizzle core-matrix layout) is copied once per CTA into shared memory with a
+//     bulk asynchronous copy (TMA engine) completing on an mbarrier;
+//   * thread m owns group row m of a tile: it loads its group's 2^k amplitudes (the next tile's
+//     loads are issued before the current tile's epilogue so they overlap), converts them and
+//     writes its A row into one of two shared-memory stages;
+//   * thread 0 issues the tcgen05.mma chain for the tile into one of two TMEM accumulators and
+//     commits it to an mbarrier;
+//   * after the mbarrier completes every thread reads its TMEM lane (tcgen05.ld.32x32b) and
+//     stores the group's 2^k outputs back in place.
+// Every mbarrier wait is bounded: on time-out the kernel records an error code in a device word,
+// frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
 #include "sv_internal.h"
 
 namespace svg {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcM = 128;
+constexpr long long kWaitIters = 4000000;   // ~0.3 s with the backoff below
+
+enum : int { kModeTF32 = 0, kModeBF16X3 = 1 };
+
+struct TcArgs {
+    long long foff[64];        // float offset (blocked layout) of local amplitude j, relative to the group base
+    int tpos[SV_MAX_K];        // ascending target qubits (zero-bit insertion positions)
+    long long n_groups;        // 2^(n-k)
+    long long n_tiles;         // ceil(n_groups / 128)
+    const void *bimg;          // device B image(s)
+    unsigned bbytes;           // bytes of the B image(s)
+    int *err;                  // device error word (bounded-wait time-outs)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on time-out.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (long long i = 0; i < kWaitIters; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading-dimension byte
+// offset >> 4 in bits 16-29, stride-dimension byte offset >> 4 in bits 32-45, the fixed
+// descriptor version 1 in bits 46-47, no base offset, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum)
+{
+    if constexpr (MODE == kModeTF32) {
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                     : "memory");
+    } else {
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t f32_to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// pack (x0 low, x1 high) to bf16x2 with round-to-nearest-even
+__device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ unsigned long long ins0(unsigned long long x, int p)
+{
+    const unsigned long long low = x & ((1ull << p) - 1ull);
+    return ((x >> p) << (p + 1)) | low;
+}
+
+template <int K, int MODE>
+struct TcShape {
+    static constexpr int D = 1 << K;             // amplitudes per group
+    static constexpr int KD = 2 * D;             // GEMM K = N
+    static constexpr int ESZ = MODE == kModeTF32 ? 4 : 2;
+    static constexpr int NIMG = MODE == kModeTF32 ? 1 : 2;            // operand images (hi, lo)
+    static constexpr int ROW_BYTES = KD * ESZ;                         // one A / B row
+    static constexpr int EPC = 16 / ESZ;                               // elements per 16-byte core row
+    static constexpr int A_IMG = kTcM * ROW_BYTES;                     // one A image
+    static constexpr int A_STAGE = NIMG * A_IMG;
+    static constexpr int B_IMG = KD * ROW_BYTES;                       // N = KD rows
+    static constexpr int B_BYTES = NIMG * B_IMG;
+    static constexpr int LBO_A = (kTcM / 8) * 128;                     // next 16-byte K chunk
+    static constexpr int LBO_B = (KD / 8) * 128;
+    static constexpr int SMEM = B_BYTES + 2 * A_STAGE + 256;
+    static constexpr int TMEM_COLS = 2 * KD < 32 ? 32 : 2 * KD;        // two accumulators
+    static constexpr int KSTEP = MODE == kModeTF32 ? 8 : 16;           // K per instruction
+};
+
+// byte offset of element (row, kk) in a K-major no-swizzle operand image with `rows` rows
+template <int ESZ>
+__device__ __host__ __forceinline__ uint32_t core_off(int row, int kk, int rows)
+{
+    constexpr int EPC = 16 / ESZ;
+    const int kc = kk / EPC, e = kk % EPC;
+    return (uint32_t)((kc * (rows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + e * ESZ);
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    using S = TcShape<K, MODE>;
+    constexpr int D = S::D;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sB = smem;
+    unsigned char *sA = smem + S::B_BYTES;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 2 * S::A_STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t bar_b = smem_u32(&bars[0]);
+    const uint32_t bar_mma[2] = {smem_u32(&bars[1]), smem_u32(&bars[2])};
+
+    if (tid == 0) {
+        mbar_init(bar_b, 1);
+        mbar_init(bar_mma[0], 1);
+        mbar_init(bar_mma[1], 1);
+        *status = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)S::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (tid == 0) {   // B image: one bulk copy per 32 KB piece, all completing on bar_b
+        mbar_arrive_expect_tx(bar_b, a.bbytes);
+        for (unsigned off = 0; off < a.bbytes; off += 32768u) {
+            const unsigned sz = a.bbytes - off < 32768u ? a.bbytes - off : 32768u;
+            bulk_g2s(smem_u32(sB + off), static_cast<const unsigned char *>(a.bimg) + off, sz, bar_b);
+        }
+    }
+
+    const uint32_t idesc = (1u << 4) | ((MODE == kModeTF32 ? 2u : 1u) << 7) | ((MODE == kModeTF32 ? 2u : 1u) << 10) |
+                           ((uint32_t)(S::KD >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+    float x[2 * D];   // this thread's group: x[j] = re, x[D + j] = im
+    auto load_group = [&](long long tile, long long &fbase, bool &valid) {
+        const long long g = tile * kTcM + tid;
+        valid = g < a.n_groups;
+        fbase = 0;
+        if (valid) {
+            unsigned long long b = (unsigned long long)g;
+#pragma unroll
+            for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
+            fbase = (long long)(((b >> 5) << 6) | (b & 31ull));
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                x[j] = sv[fbase + a.foff[j]];
+                x[D + j] = sv[fbase + a.foff[j] + 32];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2 * D; ++j) x[j] = 0.f;
+        }
+    };
+    // write this thread's A row (row = tid) into stage `st`
+    auto write_a = [&](int st) {
+        unsigned char *base = sA + st * S::A_STAGE;
+        if constexpr (MODE == kModeTF32) {
+#pragma unroll
+            for (int c = 0; c < S::KD / 4; ++c) {
+                uint4 v;
+                v.x = f32_to_tf32(x[4 * c + 0]);
+                v.y = f32_to_tf32(x[4 * c + 1]);
+                v.z = f32_to_tf32(x[4 * c + 2]);
+                v.w = f32_to_tf32(x[4 * c + 3]);
+                *reinterpret_cast<uint4 *>(base + core_off<4>(tid, 4 * c, kTcM)) = v;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < S::KD / 8; ++c) {
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float x0 = x[8 * c + 2 * p], x1 = x[8 * c + 2 * p + 1];
+                    hi[p] = pack_bf16x2(x0, x1);
+                    const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xffff0000u);
+                    lo[p] = pack_bf16x2(x0 - h0, x1 - h1);
+                }
+                const uint32_t o = core_off<2>(tid, 8 * c, kTcM);
+                *reinterpret_cast<uint4 *>(base + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(base + S::A_IMG + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    };
+    auto issue_mma = [&](int st) {   // thread 0 only
+        const uint32_t a0 = smem_u32(sA + st * S::A_STAGE);
+        const uint32_t b0 = smem_u32(sB);
+        const uint32_t d = tmem + (uint32_t)(st * S::KD);
+        constexpr int NSTEP = S::KD / S::KSTEP;
+        constexpr int CH = S::KSTEP / S::EPC;   // 16-byte chunks per instruction (2)
+        if constexpr (MODE == kModeTF32) {
+#pragma unroll
+            for (int s = 0; s < NSTEP; ++s)
+                mma<MODE>(d, sdesc(a0 + s * CH * S::LBO_A, S::LBO_A, 128), sdesc(b0 + s * CH * S::LBO_B, S::LBO_B, 128), idesc,
+                          s > 0);
+        } else {
+            const uint32_t a_img[3] = {a0, a0, a0 + S::A_IMG};          // hi, hi, lo
+            const uint32_t b_img[3] = {b0, b0 + S::B_IMG, b0};          // hi, lo, hi
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int s = 0; s < NSTEP; ++s)
+                    mma<MODE>(d, sdesc(a_img[p] + s * CH * S::LBO_A, S::LBO_A, 128),
+                              sdesc(b_img[p] + s * CH * S::LBO_B, S::LBO_B, 128), idesc, (p > 0 || s > 0));
+        }
+        mma_commit(bar_mma[st]);
+    };
+    auto epilogue = [&](int st, long long fbase, bool valid) {
+        const uint32_t t0 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(st * S::KD);
+#pragma unroll
+        for (int cb = 0; cb < S::KD / 32; ++cb) {
+            float v[32];
+            tmem_ld32(t0 + cb * 32, v);
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int col = cb * 32 + i;           // column (c', r): c' = col / D, r = col % D
+                    const int r = col % D;
+                    sv[fbase + a.foff[r] + (col >= D ? 32 : 0)] = v[i];
+                }
+            }
+        }
+    };
+
+    long long tile = blockIdx.x;
+    uint32_t phase[2] = {0u, 0u};
+    int st = 0;
+    bool ok = true;
+    long long fb_cur = 0;
+    bool v_cur = false;
+    if (tile < a.n_tiles) {
+        load_group(tile, fb_cur, v_cur);
+        write_a(0);
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            if (!mbar_wait_bounded(bar_b, 0)) { *status = 1; }
+            else issue_mma(0);
+        }
+        __syncthreads();
+        ok = (*status == 0);
+    }
+    while (ok && tile < a.n_tiles) {
+        const long long nt = tile + gridDim.x;
+        long long fb_next = 0;
+        bool v_next = false;
+        if (nt < a.n_tiles) load_group(nt, fb_next, v_next);   // in flight during the wait + epilogue
+        if (tid == 0 && !mbar_wait_bounded(bar_mma[st], phase[st])) *status = 2;
+        __syncthreads();
+        if (*status != 0) { ok = false; break; }
+        phase[st] ^= 1u;
+        tc_fence_after();
+        epilogue(st, fb_cur, v_cur);
+        if (nt < a.n_tiles) write_a(st ^ 1);
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (nt < a.n_tiles && tid == 0) {
+            tc_fence_after();
+            issue_mma(st ^ 1);
+        }
+        tile = nt;
+        st ^= 1;
+        fb_cur = fb_next;
+        v_cur = v_next;
+    }
+    if (!ok && tid == 0) atomicOr(a.err, *status == 1 ? 0x10 : 0x20);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------- host
+uint16_t bf16_rn(double v)
+{
+    // round an fp64 value to bf16 (nearest, ties to even) through fp32: exact enough for |v| <= 1
+    // matrix entries (double rounding only matters within 2^-29 of a tie).
+    float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+double bf16_to_d(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+uint32_t tf32_rna(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    return u;
+}
+
+template <int ESZ>
+uint32_t host_core_off(int row, int kk, int rows)
+{
+    constexpr int EPC = 16 / ESZ;
+    const int kc = kk / EPC, e = kk % EPC;
+    return (uint32_t)((kc * (rows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + e * ESZ);
+}
+
+// B image(s) of one gate in the tcgen05 K-major no-swizzle layout: rows = output columns (c', r),
+// K = input columns (c, j).
+std::vector<unsigned char> make_b_image(const FusedGate &g, int mode)
+{
+    const int D = 1 << g.k, KD = 2 * D;
+    auto B = [&](int kk, int nn) -> double {
+        const int c = kk / D, j = kk % D, cp = nn / D, r = nn % D;
+        const cplx u = g.mat[size_t(r) * D + j];
+        if (c == 0 && cp == 0) return u.real();
+        if (c == 1 && cp == 0) return -u.imag();
+        if (c == 0 && cp == 1) return u.imag();
+        return u.real();
+    };
+    if (mode == kModeTF32) {
+        std::vector<unsigned char> img(size_t(KD) * KD * 4, 0);
+        for (int nn = 0; nn < KD; ++nn)
+            for (int kk = 0; kk < KD; ++kk) {
+                const uint32_t v = tf32_rna(B(kk, nn));
+                std::memcpy(&img[host_core_off<4>(nn, kk, KD)], &v, 4);
+            }
+        return img;
+    }
+    const size_t one = size_t(KD) * KD * 2;
+    std::vector<unsigned char> img(2 * one, 0);
+    for (int nn = 0; nn < KD; ++nn)
+        for (int kk = 0; kk < KD; ++kk) {
+            const double v = B(kk, nn);
+            const uint16_t hi = bf16_rn(v);
+            const uint16_t lo = bf16_rn(v - bf16_to_d(hi));
+            const uint32_t o = host_core_off<2>(nn, kk, KD);
+            std::memcpy(&img[o], &hi, 2);
+            std::memcpy(&img[one + o], &lo, 2);
+        }
+    return img;
+}
+
+int *g_err_word[64] = {};
+std::mutex g_tc_mu;
+
+int device_err_word(int **out)
+{
+    int dev = 0;
+    SV_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (dev < 0 || dev >= 64) { set_error("tc: device id out of range"); return SV_EINVAL; }
+    if (!g_err_word[dev]) {
+        SV_CUDA_TRY(cudaMalloc(&g_err_word[dev], sizeof(int)));
+        SV_CUDA_TRY(cudaMemset(g_err_word[dev], 0, sizeof(int)));
+    }
+    *out = g_err_word[dev];
+    return SV_OK;
+}
+
+template <int K, int MODE>
+int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)
+{
+    using S = TcShape<K, MODE>;
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int b = 0; b < K; ++b) a.tpos[b] = g.targets[b];
+    for (int j = 0; j < (1 << K); ++j) {
+        unsigned long long o = 0;
+        for (int b = 0; b < K; ++b)
+            if ((j >> b) & 1) o |= 1ull << g.targets[b];
+        a.foff[j] = (long long)(((o >> 5) << 6) | (o & 31ull));
+    }
+    a.n_groups = 1ll << (n - K);
+    a.n_tiles = (a.n_groups + kTcM - 1) / kTcM;
+    a.bimg = dtc;
+    a.bbytes = (unsigned)S::B_BYTES;
+    SV_TRY(device_err_word(&a.err));
+    auto kern = apply_tc_kernel<K, MODE>;
+    static bool attr_set[2] = {false, false};
+    {
+        std::lock_guard<std::mutex> lk(g_tc_mu);
+        if (!attr_set[MODE]) {
+            SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+            attr_set[MODE] = true;
+        }
+    }
+    // CTAs per SM bounded by shared memory and by tensor memory (512 columns per SM)
+    const int by_smem = std::max(1, (227 * 1024) / (S::SMEM + 1024));
+    const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
+    const int per_sm = std::min(by_smem, by_tmem);
+    const long long grid = std::min<long long>(a.n_tiles, (long long)num_sms * per_sm);
+    kern<<<(unsigned)grid, kTcThreads, S::SMEM, stream>>>(sv, a);
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+}  // namespace
 
 int build_tc_operands(sv_fused *f)
 {
     f->tc_offset.assign(f->gates.size(), SIZE_MAX);
-    for (const FusedGate &g : f->gates)
-        if (g.path == SV_PATH_TC_TF32 || g.path == SV_PATH_TC_BF16X3) {
-            set_error("tensor-core path is not available in this build");
+    std::vector<unsigned char> host;
+    for (size_t i = 0; i < f->gates.size(); ++i) {
+        const FusedGate &g = f->gates[i];
+        if (g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) continue;
+        if (g.k < 4 || g.k > 6) {
+            set_error("tensor-core path handles fused gates of 4 to 6 qubits (gate %zu has %d)", i, g.k);
             return SV_EINVAL;
         }
+        const std::vector<unsigned char> img = make_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3);
+        const size_t off = (host.size() + 127) & ~size_t(127);
+        host.resize(off + img.size(), 0);
+        std::memcpy(&host[off], img.data(), img.size());
+        f->tc_offset[i] = off;
+    }
+    if (!host.empty()) {
+        SV_CUDA_TRY(cudaMalloc(&f->d_tc, host.size()));
+        SV_CUDA_TRY(cudaMemcpy(f->d_tc, host.data(), host.size(), cudaMemcpyHostToDevice));
+    }
     return SV_OK;
 }
 
-int launch_tc_gate(float *, int, const FusedGate &, const void *, cudaStream_t, int)
+int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)
 {
-    set_error("tensor-core path is not available in this build");
-    return SV_EINVAL;
+    if (!dtc) { set_error("tensor-core gate has no device operand image"); return SV_EINVAL; }
+    const bool tf = g.path == SV_PATH_TC_TF32;
+    switch (g.k) {
+    case 4: return tf ? launch_tc_t<4, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<4, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
+    case 5: return tf ? launch_tc_t<5, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<5, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
+    case 6: return tf ? launch_tc_t<6, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<6, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
+    default: set_error("tensor-core path handles k = 4..6, got %d", g.k); return SV_EINVAL;
+    }
+}
+
+int read_device_errors(int *code)
+{
+    *code = 0;
+    int dev = 0;
+    SV_CUDA_TRY(cudaGetDevice(&dev));
+    int *w = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_tc_mu);
+        if (dev >= 0 && dev < 64) w = g_err_word[dev];
+    }
+    if (!w) return SV_OK;
+    SV_CUDA_TRY(cudaMemcpy(code, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*code) SV_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
+    return SV_OK;
 }
 
 }  // namespace svg

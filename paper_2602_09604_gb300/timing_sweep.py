@@ -1,0 +1,71 @@
+"""Self-recorded fused-gate timings (the training data of the learned cost model).
+
+The simulator times its own kernels: single random fused gates of chosen size k, target set and
+kernel path are applied to an n-qubit state through ``sv_apply_fused_gates`` with CUDA-event
+timing records, and the median over repeats is kept.  Gates are built without fusion
+(``FUSE_NONE``) so each record is exactly one kernel launch.
+"""
+from __future__ import annotations
+
+import statistics
+from collections import defaultdict
+
+import numpy as np
+
+from . import binding as B
+from . import workloads as wl
+
+
+def path_ok(path: int, targets) -> bool:
+    if path == B.PATH_HIGH:
+        return all(t >= 5 for t in targets)
+    return True
+
+
+def random_targets(n: int, k: int, rng: np.random.Generator, cls: str):
+    """k distinct targets of class 'low' (all < 5), 'high' (all >= 5), 'mixed' or 'any'."""
+    if cls == "low" and k <= 5:
+        return tuple(sorted(int(t) for t in rng.choice(5, size=k, replace=False)))
+    if cls == "high" and n - 5 >= k:
+        return tuple(sorted(int(t) for t in 5 + rng.choice(n - 5, size=k, replace=False)))
+    if cls == "mixed" and k >= 2 and n - 5 >= 1:
+        nl = int(rng.integers(1, min(k - 1, 5) + 1))
+        nh = k - nl
+        if nh <= n - 5:
+            lo = rng.choice(5, size=nl, replace=False)
+            hi = 5 + rng.choice(n - 5, size=nh, replace=False)
+            return tuple(sorted(int(t) for t in np.concatenate([lo, hi])))
+    return tuple(sorted(int(t) for t in rng.choice(n, size=k, replace=False)))
+
+
+def time_specs(specs, repeats: int = 5, seed: int = 0, precision: int = B.PREC_FP32, warm: int = 1):
+    """specs: iterable of (n, targets, path).  Returns a list of dicts with the median microseconds."""
+    from .state import DeviceState
+    rng = np.random.default_rng(seed)
+    by_n = defaultdict(list)
+    for i, (n, targets, path) in enumerate(specs):
+        by_n[n].append((i, tuple(targets), path))
+    out = [None] * sum(len(v) for v in by_n.values())
+    for n, items in sorted(by_n.items()):
+        st = DeviceState(n)
+        st.init(0)
+        by_path = defaultdict(list)
+        for i, targets, path in items:
+            by_path[path].append((i, targets))
+        for path, lst in by_path.items():
+            gates = []
+            for _, targets in lst:
+                g = wl.random_gate(n, len(targets), rng, targets=targets)
+                gates += [g] * (repeats + warm)
+            f = B.sv_fuse_circuit(gates, n, mode=B.FUSE_NONE, precision=precision, force_path=path,
+                                  max_k=6)
+            try:
+                rec = st.apply(f, timings=True)
+            finally:
+                B.sv_fused_free(f)
+            for s, (i, targets) in enumerate(lst):
+                r = rec[s * (repeats + warm) + warm:(s + 1) * (repeats + warm)]
+                out[i] = {"n": n, "k": len(targets), "targets": targets, "path": r[0]["path"],
+                          "us": statistics.median(x["us"] for x in r)}
+        st.free()
+    return out

@@ -162,3 +162,18 @@ def test_empty_circuit_fuses_to_nothing(B):
         assert B.sv_fused_count(f) == 0
     finally:
         B.sv_fused_free(f)
+
+
+def test_no_fusion_mode_keeps_every_gate(B):
+    rng = np.random.default_rng(6)
+    n = 7
+    gates = [wl.Gate((3, 1), wl.random_unitary(4, rng)), wl.Gate((3, 1), wl.random_unitary(4, rng)),
+             wl.Gate((0,), wl.X, (5,))]
+    f = B.sv_fuse_circuit(gates, n, mode=B.FUSE_NONE)
+    try:
+        assert B.sv_fused_count(f) == 3
+        assert [B.sv_fused_get_info(f, i)["targets"] for i in range(3)] == [(1, 3), (1, 3), (0, 5)]
+        got = oracle.run_circuit(n, fused_as_gates(B, f), 9)
+        assert np.max(np.abs(got - oracle.run_circuit(n, gates, 9))) < 1e-13
+    finally:
+        B.sv_fused_free(f)
