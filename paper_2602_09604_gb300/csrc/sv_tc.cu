@@ -169,49 +169,85 @@ struct TcShape {
     static constexpr int KD = 2 * D;             // GEMM K = N
     static constexpr int ESZ = MODE == kModeTF32 ? 4 : 2;
     static constexpr int NIMG = MODE == kModeTF32 ? 1 : 2;            // operand images (hi, lo)
-    static constexpr int ROW_BYTES = KD * ESZ;                         // one A / B row
+    static constexpr int ROW_BYTES = KD * ESZ;                         // one B row
     static constexpr int EPC = 16 / ESZ;                               // elements per 16-byte core row
-    static constexpr int A_IMG = kTcM * ROW_BYTES;                     // one A image
-    static constexpr int A_STAGE = NIMG * A_IMG;
     static constexpr int B_IMG = KD * ROW_BYTES;                       // N = KD rows
     static constexpr int B_BYTES = NIMG * B_IMG;
-    static constexpr int LBO_A = (kTcM / 8) * 128;                     // next 16-byte K chunk
-    static constexpr int LBO_B = (KD / 8) * 128;
-    static constexpr int SMEM = B_BYTES + 2 * A_STAGE + 256;
-    static constexpr int TMEM_COLS = 2 * KD < 32 ? 32 : 2 * KD;        // two accumulators
+    static constexpr int LBO_B = (KD / 8) * 128;                       // next 16-byte K chunk
+    static constexpr int SMEM = B_BYTES + 256;
+    static constexpr int A_COLS = KD * ESZ / 4;                        // TMEM columns of one A image
+    static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
+    static constexpr int TMEM_COLS = 2 * WG_COLS < 32 ? 32 : 2 * WG_COLS;   // two warpgroups
     static constexpr int KSTEP = MODE == kModeTF32 ? 8 : 16;           // K per instruction
+    static constexpr int MIN_BLOCKS = K == 6 ? 1 : (K == 5 ? 2 : 3);   // CTAs per SM the registers allow
 };
 
-// byte offset of element (row, kk) in a K-major no-swizzle operand image with `rows` rows
-template <int ESZ>
-__device__ __host__ __forceinline__ uint32_t core_off(int row, int kk, int rows)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
 {
-    constexpr int EPC = 16 / ESZ;
-    const int kc = kk / EPC, e = kk % EPC;
-    return (uint32_t)((kc * (rows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + e * ESZ);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t idesc, uint32_t accum)
+{
+    if constexpr (MODE == kModeTF32) {
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+                     "r"(tmem_a), "l"(bd), "r"(idesc), "r"(accum)
+                     : "memory");
+    } else {
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+                     "r"(tmem_a), "l"(bd), "r"(idesc), "r"(accum)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void wg_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
+
+// Two warpgroups per CTA, each an independent pipeline over every other tile of the CTA, sharing
+// the B operand in shared memory.  Per warpgroup: the group rows of the next tile are loaded into
+// registers before the current tile's epilogue (so 2 x 128 threads x 2^(k+1) floats are in flight
+// per CTA), the A row goes straight into the warpgroup's tensor-memory A region (tcgen05.st), the
+// MMA reads A from tensor memory and B from shared memory, and the accumulator comes back with
+// tcgen05.ld.
 template <int K, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
     using S = TcShape<K, MODE>;
     constexpr int D = S::D;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sB = smem;
-    unsigned char *sA = smem + S::B_BYTES;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 2 * S::A_STAGE);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
-    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);
+    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
     const int tid = threadIdx.x;
+    const int wg = tid >> 7;
+    const int row = tid & 127;
     const int warp = tid >> 5;
     const uint32_t bar_b = smem_u32(&bars[0]);
-    const uint32_t bar_mma[2] = {smem_u32(&bars[1]), smem_u32(&bars[2])};
+    const uint32_t bar_mma = smem_u32(&bars[1 + wg]);
 
     if (tid == 0) {
         mbar_init(bar_b, 1);
-        mbar_init(bar_mma[0], 1);
-        mbar_init(bar_mma[1], 1);
-        *status = 0;
+        mbar_init(smem_u32(&bars[1]), 1);
+        mbar_init(smem_u32(&bars[2]), 1);
+        status[0] = 0;
+        status[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -225,8 +261,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restri
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t t_wg = tmem + (uint32_t)(wg * S::WG_COLS);        // this warpgroup's columns
+    const uint32_t t_lane = ((uint32_t)((warp & 3) * 32)) << 16;     // this warp's lane quarter
+    const uint32_t tA = t_wg;                                         // A image(s)
+    const uint32_t tD = t_wg + (uint32_t)(S::NIMG * S::A_COLS);      // accumulator
 
-    if (tid == 0) {   // B image: one bulk copy per 32 KB piece, all completing on bar_b
+    if (tid == 0) {   // B image: bulk copies of up to 32 KB, all completing on bar_b
         mbar_arrive_expect_tx(bar_b, a.bbytes);
         for (unsigned off = 0; off < a.bbytes; off += 32768u) {
             const unsigned sz = a.bbytes - off < 32768u ? a.bbytes - off : 32768u;
@@ -239,7 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restri
 
     float x[2 * D];   // this thread's group: x[j] = re, x[D + j] = im
     auto load_group = [&](long long tile, long long &fbase, bool &valid) {
-        const long long g = tile * kTcM + tid;
+        const long long g = tile * kTcM + row;
         valid = g < a.n_groups;
         fbase = 0;
         if (valid) {
@@ -257,65 +297,74 @@ __global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restri
             for (int j = 0; j < 2 * D; ++j) x[j] = 0.f;
         }
     };
-    // write this thread's A row (row = tid) into stage `st`
-    auto write_a = [&](int st) {
-        unsigned char *base = sA + st * S::A_STAGE;
+    // this thread's A row into its TMEM lane of the warpgroup's A region
+    auto write_a = [&]() {
         if constexpr (MODE == kModeTF32) {
 #pragma unroll
-            for (int c = 0; c < S::KD / 4; ++c) {
-                uint4 v;
-                v.x = f32_to_tf32(x[4 * c + 0]);
-                v.y = f32_to_tf32(x[4 * c + 1]);
-                v.z = f32_to_tf32(x[4 * c + 2]);
-                v.w = f32_to_tf32(x[4 * c + 3]);
-                *reinterpret_cast<uint4 *>(base + core_off<4>(tid, 4 * c, kTcM)) = v;
+            for (int cb = 0; cb < S::KD / 32; ++cb) {
+                uint32_t r[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) r[i] = f32_to_tf32(x[cb * 32 + i]);
+                tmem_st32(tA + t_lane + cb * 32, r);
             }
         } else {
+            // a 32-bit column holds two bf16 elements: element 2c in the low half of column c.
+            // hi and lo are packed and stored one after the other to keep 32 registers live.
+            constexpr int NC = S::KD / 2 < 32 ? S::KD / 2 : 32;   // columns per chunk
 #pragma unroll
-            for (int c = 0; c < S::KD / 8; ++c) {
-                uint32_t hi[4], lo[4];
+            for (int cb = 0; cb < S::KD / (2 * NC); ++cb) {
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const float x0 = x[8 * c + 2 * p], x1 = x[8 * c + 2 * p + 1];
-                    hi[p] = pack_bf16x2(x0, x1);
-                    const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xffff0000u);
-                    lo[p] = pack_bf16x2(x0 - h0, x1 - h1);
+                for (int part = 0; part < 2; ++part) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        if (c < NC) {
+                            const float x0 = x[cb * 2 * NC + 2 * c], x1 = x[cb * 2 * NC + 2 * c + 1];
+                            const uint32_t hi = pack_bf16x2(x0, x1);
+                            if (part == 0) {
+                                r[c] = hi;
+                            } else {
+                                const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+                                r[c] = pack_bf16x2(x0 - h0, x1 - h1);
+                            }
+                        } else {
+                            r[c] = 0u;
+                        }
+                    }
+                    const uint32_t dst = tA + t_lane + (uint32_t)(part * S::A_COLS + cb * NC);
+                    if constexpr (NC == 32) tmem_st32(dst, r);
+                    else tmem_st16(dst, r);
                 }
-                const uint32_t o = core_off<2>(tid, 8 * c, kTcM);
-                *reinterpret_cast<uint4 *>(base + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4 *>(base + S::A_IMG + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     };
-    auto issue_mma = [&](int st) {   // thread 0 only
-        const uint32_t a0 = smem_u32(sA + st * S::A_STAGE);
+    auto issue_mma = [&]() {   // one thread per warpgroup
         const uint32_t b0 = smem_u32(sB);
-        const uint32_t d = tmem + (uint32_t)(st * S::KD);
         constexpr int NSTEP = S::KD / S::KSTEP;
-        constexpr int CH = S::KSTEP / S::EPC;   // 16-byte chunks per instruction (2)
+        constexpr int ACOL = S::KSTEP * S::ESZ / 4;     // TMEM columns per instruction (8)
+        constexpr int CH = S::KSTEP / S::EPC;           // 16-byte chunks of B per instruction (2)
         if constexpr (MODE == kModeTF32) {
 #pragma unroll
             for (int s = 0; s < NSTEP; ++s)
-                mma<MODE>(d, sdesc(a0 + s * CH * S::LBO_A, S::LBO_A, 128), sdesc(b0 + s * CH * S::LBO_B, S::LBO_B, 128), idesc,
-                          s > 0);
+                mma_ta<MODE>(tD, tA + s * ACOL, sdesc(b0 + s * CH * S::LBO_B, S::LBO_B, 128), idesc, s > 0);
         } else {
-            const uint32_t a_img[3] = {a0, a0, a0 + S::A_IMG};          // hi, hi, lo
-            const uint32_t b_img[3] = {b0, b0 + S::B_IMG, b0};          // hi, lo, hi
+            const uint32_t a_img[3] = {tA, tA, tA + (uint32_t)S::A_COLS};   // hi, hi, lo
+            const uint32_t b_img[3] = {b0, b0 + (uint32_t)S::B_IMG, b0};     // hi, lo, hi
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
                 for (int s = 0; s < NSTEP; ++s)
-                    mma<MODE>(d, sdesc(a_img[p] + s * CH * S::LBO_A, S::LBO_A, 128),
-                              sdesc(b_img[p] + s * CH * S::LBO_B, S::LBO_B, 128), idesc, (p > 0 || s > 0));
+                    mma_ta<MODE>(tD, a_img[p] + s * ACOL, sdesc(b_img[p] + s * CH * S::LBO_B, S::LBO_B, 128), idesc,
+                                 (p > 0 || s > 0));
         }
-        mma_commit(bar_mma[st]);
+        mma_commit(bar_mma);
     };
-    auto epilogue = [&](int st, long long fbase, bool valid) {
-        const uint32_t t0 = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(st * S::KD);
+    auto epilogue = [&](long long fbase, bool valid) {
 #pragma unroll
         for (int cb = 0; cb < S::KD / 32; ++cb) {
             float v[32];
-            tmem_ld32(t0 + cb * 32, v);
+            tmem_ld32(tD + t_lane + cb * 32, v);
             if (valid) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
@@ -327,51 +376,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) apply_tc_kernel(float *__restri
         }
     };
 
-    long long tile = blockIdx.x;
-    uint32_t phase[2] = {0u, 0u};
-    int st = 0;
+    // tiles of this warpgroup: blockIdx.x + (2 i + wg) * gridDim.x
+    const long long tstride = 2ll * gridDim.x;
+    long long tile = blockIdx.x + (long long)wg * gridDim.x;
+    uint32_t phase = 0u;
     bool ok = true;
     long long fb_cur = 0;
     bool v_cur = false;
+    const bool lead = row == 0;
     if (tile < a.n_tiles) {
         load_group(tile, fb_cur, v_cur);
-        write_a(0);
-        fence_proxy_async();
+        write_a();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        wg_sync(wg);
+        if (lead) {
             tc_fence_after();
-            if (!mbar_wait_bounded(bar_b, 0)) { *status = 1; }
-            else issue_mma(0);
+            if (!mbar_wait_bounded(bar_b, 0)) status[wg] = 1;
+            else issue_mma();
         }
-        __syncthreads();
-        ok = (*status == 0);
+        wg_sync(wg);
+        ok = status[wg] == 0;
     }
     while (ok && tile < a.n_tiles) {
-        const long long nt = tile + gridDim.x;
+        const long long nt = tile + tstride;
         long long fb_next = 0;
         bool v_next = false;
         if (nt < a.n_tiles) load_group(nt, fb_next, v_next);   // in flight during the wait + epilogue
-        if (tid == 0 && !mbar_wait_bounded(bar_mma[st], phase[st])) *status = 2;
-        __syncthreads();
-        if (*status != 0) { ok = false; break; }
-        phase[st] ^= 1u;
+        if (lead && !mbar_wait_bounded(bar_mma, phase)) status[wg] = 2;
+        wg_sync(wg);
+        if (status[wg] != 0) { ok = false; break; }
+        phase ^= 1u;
         tc_fence_after();
-        epilogue(st, fb_cur, v_cur);
-        if (nt < a.n_tiles) write_a(st ^ 1);
-        fence_proxy_async();
+        epilogue(fb_cur, v_cur);                                 // reads D; MMA(nt) writes D after the sync
+        if (nt < a.n_tiles) write_a();                            // A region is free: MMA(tile) completed
         tc_fence_before();
-        __syncthreads();
-        if (nt < a.n_tiles && tid == 0) {
+        wg_sync(wg);
+        if (nt < a.n_tiles && lead) {
             tc_fence_after();
-            issue_mma(st ^ 1);
+            issue_mma();
         }
         tile = nt;
-        st ^= 1;
         fb_cur = fb_next;
         v_cur = v_next;
     }
-    if (!ok && tid == 0) atomicOr(a.err, *status == 1 ? 0x10 : 0x20);
+    if (!ok && lead) atomicOr(a.err, status[wg] == 1 ? 0x10 : 0x20);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -496,12 +544,11 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
             attr_set[MODE] = true;
         }
     }
-    // CTAs per SM bounded by shared memory and by tensor memory (512 columns per SM)
-    const int by_smem = std::max(1, (227 * 1024) / (S::SMEM + 1024));
+    // CTAs per SM bounded by registers (MIN_BLOCKS) and by tensor memory (512 columns per SM)
     const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
-    const int per_sm = std::min(by_smem, by_tmem);
-    const long long grid = std::min<long long>(a.n_tiles, (long long)num_sms * per_sm);
-    kern<<<(unsigned)grid, kTcThreads, S::SMEM, stream>>>(sv, a);
+    const int per_sm = std::min(S::MIN_BLOCKS, by_tmem);
+    const long long grid = std::min<long long>((a.n_tiles + 1) / 2, (long long)num_sms * per_sm);
+    kern<<<(unsigned)grid, 2 * kTcThreads, S::SMEM, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
