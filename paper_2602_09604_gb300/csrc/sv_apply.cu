@@ -55,16 +55,7 @@ struct HighArgs {
 template <int K>
 struct TileArgs {
     MatOf<K> m;
-    long long fblk[64];       // block offset of tile block phi (deposit of phi into the F bits)
-    int fpos[6];              // ascending block-bit positions of F
-    int loff[1 << K];         // tile-local amplitude offset of local index j
-    int ltpos[K];             // ascending tile-local target positions
-    int f;                    // a tile is 2^f blocks
-    int lsh;                  // 5 - (number of targets below 5)
-    int lmask;                // 2^(number of targets below 5) - 1
-    long long n_tiles;
-    unsigned char swz[64];    // in-block position XOR of tile block phi (see apply_tile_kernel)
-    unsigned char gswz[32];   // the same XOR, indexed by (group >> lsh) & lmask
+    TileMap t;
 };
 
 template <int K>
@@ -258,7 +249,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int f = FIXED ? tile_f<K>() : a.f;
+    const int f = FIXED ? tile_f<K>() : a.t.f;
     const int tile_floats = 64 << f;
     float2 *s_u = reinterpret_cast<float2 *>(smem);
     float *buf = smem + (K == 6 ? 2 * D * D : 0) + warp * tile_floats;
@@ -267,22 +258,22 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
         __syncthreads();
     }
     const long long t = (long long)blockIdx.x * kTileWarps + warp;
-    if (t >= a.n_tiles) return;
+    if (t >= a.t.n_tiles) return;
     unsigned long long b0 = (unsigned long long)t;
     if constexpr (GATHER) {
-        for (int i = 0; i < f; ++i) b0 = insert_zero(b0, a.fpos[i]);
+        for (int i = 0; i < f; ++i) b0 = insert_zero(b0, a.t.fpos[i]);
     } else {
         b0 <<= f;
     }
     // chunk c of the tile: block phi = c >> 4, half (re / im) = (c >> 3) & 1, chunk q = c & 7
     auto gaddr = [&](int c) -> float * {
         const int phi = c >> 4;
-        const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.fblk[phi] : b0 + (unsigned long long)phi;
+        const unsigned long long blk = GATHER ? b0 + (unsigned long long)a.t.fblk[phi] : b0 + (unsigned long long)phi;
         return sv + (long long)(blk << 6) + (c & 15) * 4;
     };
     auto saddr = [&](int c, unsigned &sw) -> float * {
         const int phi = c >> 4;
-        sw = a.swz[phi];
+        sw = a.t.swz[phi];
         return buf + phi * 64 + (c & 8) * 4 + (((c & 7) ^ (int)(sw >> 2)) << 2);
     };
     if constexpr (FIXED) {
@@ -313,15 +304,15 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
     auto do_group = [&](int g) {
         unsigned base = (unsigned)g;
 #pragma unroll
-        for (int b = 0; b < K; ++b) base = (unsigned)insert_zero(base, a.ltpos[b]);
-        const unsigned sg = a.gswz[(g >> a.lsh) & a.lmask];
+        for (int b = 0; b < K; ++b) base = (unsigned)insert_zero(base, a.t.ltpos[b]);
+        const unsigned sg = a.t.gswz[(g >> a.t.lsh) & a.t.lmask];
         if constexpr (K <= 5) {
             float yr[D], yi[D];
 #pragma unroll
             for (int r = 0; r < D; ++r) { yr[r] = 0.f; yi[r] = 0.f; }
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned i = base + (unsigned)a.loff[j];
+                const unsigned i = base + (unsigned)a.t.loff[j];
                 const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 const float xr = buf[o], xi = buf[o + 32];
 #pragma unroll
@@ -336,7 +327,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
             // Groups of different lanes are disjoint, so no lane synchronisation is needed here.
 #pragma unroll
             for (int r = 0; r < D; ++r) {
-                const unsigned i = base + (unsigned)a.loff[r];
+                const unsigned i = base + (unsigned)a.t.loff[r];
                 const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 buf[o] = yr[r];
                 buf[o + 32] = yi[r];
@@ -345,7 +336,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
             float xr[D][1], xi[D][1];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned i = base + (unsigned)a.loff[j];
+                const unsigned i = base + (unsigned)a.t.loff[j];
                 const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 xr[j][0] = buf[o];
                 xi[j][0] = buf[o + 32];
@@ -355,7 +346,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
             for (int r = 0; r < D; ++r) {
                 float yr[1], yi[1];
                 row_smem<K, 1>(s_u, r, xr, xi, yr, yi);
-                const unsigned i = obase + (unsigned)a.loff[r];
+                const unsigned i = obase + (unsigned)a.t.loff[r];
                 const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
                 buf[o] = yr[0];
                 buf[o + 32] = yi[0];
@@ -442,69 +433,10 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
     std::memset(&a, 0, sizeof(a));
     fill_mat(a.m, g, true);
     const int nb = n > 5 ? n - 5 : 0;
-    int hp[SV_MAX_K], h = 0;
-    for (int b = 0; b < K; ++b)
-        if (g.targets[b] >= 5) hp[h++] = g.targets[b] - 5;
     const bool fixed = nb >= tile_f<K>();
-    int f = fixed ? tile_f<K>() : nb;   // h <= K <= tile_f<K>(), and h <= nb always
-    // F = high target block bits + lowest free block bits
-    uint64_t fm = 0;
-    for (int i = 0; i < h; ++i) fm |= 1ull << hp[i];
-    for (int p = 0; __builtin_popcountll(fm) < f && p < nb; ++p) fm |= 1ull << p;
-    int cnt = 0;
-    for (int p = 0; p < nb; ++p)
-        if ((fm >> p) & 1) a.fpos[cnt++] = p;
-    a.f = f;
-    for (int phi = 0; phi < (1 << f); ++phi) {
-        long long o = 0;
-        for (int i = 0; i < f; ++i)
-            if ((phi >> i) & 1) o |= 1ll << a.fpos[i];
-        a.fblk[phi] = o;
-    }
-    const bool gather = fm != ((f >= 64) ? ~0ull : ((1ull << f) - 1ull));
-    for (int b = 0; b < K; ++b) {
-        const int t = g.targets[b];
-        if (t < 5) {
-            a.ltpos[b] = t;
-        } else {
-            int r = 0;
-            while (a.fpos[r] != t - 5) ++r;
-            a.ltpos[b] = 5 + r;
-        }
-    }
-    for (int j = 0; j < (1 << K); ++j) {
-        int o = 0;
-        for (int b = 0; b < K; ++b)
-            if ((j >> b) & 1) o |= 1 << a.ltpos[b];
-        a.loff[j] = o;
-    }
-    // swizzle: deposit the lowest L non-target tile-block bits onto the L low target positions
-    int lowt[5], L = 0;
-    for (int b = 0; b < K; ++b)
-        if (g.targets[b] < 5) lowt[L++] = g.targets[b];
-    int nont[6], nn = 0;
-    for (int r = 0; r < f; ++r) {
-        bool is_t = false;
-        for (int b = 0; b < K; ++b)
-            if (a.ltpos[b] == 5 + r) is_t = true;
-        if (!is_t) nont[nn++] = r;
-    }
-    auto deposit_low = [&](int v) {
-        int o = 0;
-        for (int i = 0; i < L; ++i)
-            if ((v >> i) & 1) o |= 1 << lowt[i];
-        return o;
-    };
-    for (int phi = 0; phi < (1 << f); ++phi) {
-        int c = 0;
-        for (int i = 0; i < nn; ++i)
-            if ((phi >> nont[i]) & 1) c |= 1 << i;
-        a.swz[phi] = (unsigned char)deposit_low(c & ((1 << L) - 1));
-    }
-    for (int v = 0; v < (1 << L); ++v) a.gswz[v] = (unsigned char)deposit_low(v);
-    a.lsh = 5 - L;
-    a.lmask = (1 << L) - 1;
-    a.n_tiles = 1ll << (nb - f);
+    const int f = fixed ? tile_f<K>() : nb;   // (targets >= 5) <= K <= tile_f<K>(), and <= nb always
+    make_tile_map(g, n, f, &a.t);
+    const bool gather = a.t.gather != 0;
     const size_t smem = size_t(kTileWarps) * (64u << f) * sizeof(float) + (K == 6 ? sizeof(float2) * 64 * 64 : 0);
     auto kern = fixed ? (gather ? apply_tile_kernel<K, true, true> : apply_tile_kernel<K, false, true>)
                       : (gather ? apply_tile_kernel<K, true, false> : apply_tile_kernel<K, false, false>);
@@ -518,7 +450,7 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
         }
     }
     (void)num_sms;
-    const long long grid = (a.n_tiles + kTileWarps - 1) / kTileWarps;
+    const long long grid = (a.t.n_tiles + kTileWarps - 1) / kTileWarps;
     kern<<<(unsigned)grid, kTileThreads, smem, stream>>>(sv, a, umem);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
@@ -529,6 +461,71 @@ const LaunchFn kHigh[7] = {nullptr, launch_high<1>, launch_high<2>, launch_high<
 const LaunchFn kTile[7] = {nullptr, launch_tile<1>, launch_tile<2>, launch_tile<3>, launch_tile<4>, launch_tile<5>, launch_tile<6>};
 
 }  // namespace
+
+void make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
+{
+    std::memset(m, 0, sizeof(*m));
+    const int K = g.k;
+    const int nb = n > 5 ? n - 5 : 0;
+    uint64_t fm = 0;   // F = high target block bits + lowest free block bits
+    for (int b = 0; b < K; ++b)
+        if (g.targets[b] >= 5) fm |= 1ull << (g.targets[b] - 5);
+    for (int p = 0; __builtin_popcountll(fm) < f && p < nb; ++p) fm |= 1ull << p;
+    int cnt = 0;
+    for (int p = 0; p < nb; ++p)
+        if ((fm >> p) & 1) m->fpos[cnt++] = p;
+    m->f = f;
+    for (int phi = 0; phi < (1 << f); ++phi) {
+        long long o = 0;
+        for (int i = 0; i < f; ++i)
+            if ((phi >> i) & 1) o |= 1ll << m->fpos[i];
+        m->fblk[phi] = o;
+    }
+    m->gather = fm != ((1ull << f) - 1ull);
+    for (int b = 0; b < K; ++b) {
+        const int t = g.targets[b];
+        if (t < 5) {
+            m->ltpos[b] = t;
+        } else {
+            int r = 0;
+            while (m->fpos[r] != t - 5) ++r;
+            m->ltpos[b] = 5 + r;
+        }
+    }
+    for (int j = 0; j < (1 << K); ++j) {
+        int o = 0;
+        for (int b = 0; b < K; ++b)
+            if ((j >> b) & 1) o |= 1 << m->ltpos[b];
+        m->loff[j] = o;
+    }
+    // swizzle: deposit the lowest L non-target tile-block bits onto the L low target positions
+    int lowt[5], L = 0;
+    for (int b = 0; b < K; ++b)
+        if (g.targets[b] < 5) lowt[L++] = g.targets[b];
+    int nont[6], nn = 0;
+    for (int r = 0; r < f; ++r) {
+        bool is_t = false;
+        for (int b = 0; b < K; ++b)
+            if (m->ltpos[b] == 5 + r) is_t = true;
+        if (!is_t) nont[nn++] = r;
+    }
+    auto deposit_low = [&](int v) {
+        int o = 0;
+        for (int i = 0; i < L; ++i)
+            if ((v >> i) & 1) o |= 1 << lowt[i];
+        return o;
+    };
+    for (int phi = 0; phi < (1 << f); ++phi) {
+        int c = 0;
+        for (int i = 0; i < nn; ++i)
+            if ((phi >> nont[i]) & 1) c |= 1 << i;
+        m->swz[phi] = (unsigned char)deposit_low(c & ((1 << L) - 1));
+    }
+    for (int v = 0; v < (1 << L); ++v) m->gswz[v] = (unsigned char)deposit_low(v);
+    m->lsh = 5 - L;
+    m->lmask = (1 << L) - 1;
+    m->n_tiles = 1ll << (nb - f);
+}
 
 int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, const void *dtc, cudaStream_t stream, int num_sms)
 {

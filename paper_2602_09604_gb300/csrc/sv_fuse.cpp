@@ -93,9 +93,9 @@ bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
 
 int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path)
 {
-    (void)n;
     if (force_path != SV_PATH_AUTO) return force_path;
-    if (precision != SV_PREC_FP32 && g.k >= tc_min_k && g.k >= 4)
+    // tensor cores for 4..6-qubit gates of states with at least 2^k blocks of 32 amplitudes
+    if (precision != SV_PREC_FP32 && g.k >= tc_min_k && g.k >= 4 && n >= g.k + 5)
         return precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3;
     bool any_low = false, any_high = false;
     for (int j = 0; j < g.k; ++j) (g.targets[j] < 5 ? any_low : any_high) = true;

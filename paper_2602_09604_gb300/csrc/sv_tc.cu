@@ -45,10 +45,11 @@ constexpr long long kWaitIters = 4000000;   // ~0.3 s with the backoff below
 enum : int { kModeTF32 = 0, kModeBF16X3 = 1 };
 
 struct TcArgs {
-    long long foff[64];        // float offset (blocked layout) of local amplitude j, relative to the group base
-    int tpos[SV_MAX_K];        // ascending target qubits (zero-bit insertion positions)
+    TileMap t;                 // per-warp tile geometry (f = k: 32 groups per warp tile), staged variant
+    long long foff[64];        // direct variant: float offset of local amplitude j from the group base
+    int tpos[SV_MAX_K];        // direct variant: ascending target qubits
     long long n_groups;        // 2^(n-k)
-    long long n_tiles;         // ceil(n_groups / 128)
+    long long n_mma_tiles;     // MMA tiles of 128 groups
     const void *bimg;          // device B image(s)
     unsigned bbytes;           // bytes of the B image(s)
     int *err;                  // device error word (bounded-wait time-outs)
@@ -126,21 +127,19 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x)
@@ -155,6 +154,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1)
 {
     __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
     return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ unsigned opaque_u32(unsigned v)
+{
+    asm volatile("mov.b32 %0, %0;" : "+r"(v));
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long ins0(unsigned long long x, int p)
@@ -174,7 +179,9 @@ struct TcShape {
     static constexpr int B_IMG = KD * ROW_BYTES;                       // N = KD rows
     static constexpr int B_BYTES = NIMG * B_IMG;
     static constexpr int LBO_B = (KD / 8) * 128;                       // next 16-byte K chunk
-    static constexpr int SMEM = B_BYTES + 256;
+    static constexpr int WTILE_FLOATS = 64 << K;                       // one warp tile: 2^k blocks
+    static constexpr int SMEM = B_BYTES + 8 * WTILE_FLOATS * 4 + 256;
+    static constexpr int CPL = (16 << K) / 32;                         // 16-byte chunks per lane
     static constexpr int A_COLS = KD * ESZ / 4;                        // TMEM columns of one A image
     static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
     static constexpr int TMEM_COLS = 2 * WG_COLS < 32 ? 32 : 2 * WG_COLS;   // two warpgroups
@@ -219,26 +226,48 @@ __device__ __forceinline__ void mma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_
 
 __device__ __forceinline__ void wg_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
 
-// Two warpgroups per CTA, each an independent pipeline over every other tile of the CTA, sharing
-// the B operand in shared memory.  Per warpgroup: the group rows of the next tile are loaded into
-// registers before the current tile's epilogue (so 2 x 128 threads x 2^(k+1) floats are in flight
-// per CTA), the A row goes straight into the warpgroup's tensor-memory A region (tcgen05.st), the
-// MMA reads A from tensor memory and B from shared memory, and the accumulator comes back with
-// tcgen05.ld.
-template <int K, int MODE>
+__device__ __forceinline__ float4 xor_perm4(float4 v, unsigned sw)
+{
+    if (sw & 1u) { float t = v.x; v.x = v.y; v.y = t; t = v.z; v.z = v.w; v.w = t; }
+    if (sw & 2u) { float t = v.x; v.x = v.z; v.z = t; t = v.y; v.y = v.w; v.w = t; }
+    return v;
+}
+
+// Two warpgroups per CTA, each an independent pipeline over every other MMA tile of the CTA,
+// sharing the B operand in shared memory.
+//
+// DIRECT variant (no target below qubit 5): row m of MMA tile t is group 128 t + m; a warp's 32
+// groups are the 32 positions of one block, so each lane loads its group straight into registers
+// (the next tile's loads are issued before the current tile's epilogue) and stores its outputs
+// straight back -- every warp access is a whole 128-byte line.
+//
+// STAGED variant (some target below qubit 5): an MMA tile is four warp tiles; a warp tile is the
+// 2^k blocks holding 32 groups (the tile geometry of the CUDA-core tile kernel with f = k), so
+// global memory is still read and written in whole 128-byte lines.
+// Per warp and tile:
+//   1. the next warp tile's 16-byte chunks are loaded into registers before the current tile's
+//      epilogue (2 x 128 threads x 2^(k+1) floats in flight per CTA);
+//   2. the epilogue reads the accumulator (tcgen05.ld) into the group's places of the warp's
+//      shared-memory tile, which then goes back to global memory with 16-byte stores;
+//   3. the prefetched chunks are stored XOR-swizzled into the warp's tile (bank-conflict-free
+//      group reads), and each lane streams its A row, 32 tensor-memory columns at a time, into
+//      the warpgroup's A region (tcgen05.st);
+//   4. one thread per warpgroup issues the MMAs (A from tensor memory, B from shared memory).
+template <int K, int MODE, bool STAGED>
 __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
     using S = TcShape<K, MODE>;
     constexpr int D = S::D;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sB = smem;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
-    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
     const int tid = threadIdx.x;
     const int wg = tid >> 7;
-    const int row = tid & 127;
     const int warp = tid >> 5;
+    const int lane = tid & 31;
+    float *wbuf = reinterpret_cast<float *>(smem + S::B_BYTES) + warp * S::WTILE_FLOATS;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 8 * S::WTILE_FLOATS * 4);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
+    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
     const uint32_t bar_b = smem_u32(&bars[0]);
     const uint32_t bar_mma = smem_u32(&bars[1 + wg]);
 
@@ -277,49 +306,115 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) 
     const uint32_t idesc = (1u << 4) | ((MODE == kModeTF32 ? 2u : 1u) << 7) | ((MODE == kModeTF32 ? 2u : 1u) << 10) |
                            ((uint32_t)(S::KD >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 
-    float x[2 * D];   // this thread's group: x[j] = re, x[D + j] = im
-    auto load_group = [&](long long tile, long long &fbase, bool &valid) {
-        const long long g = tile * kTcM + row;
-        valid = g < a.n_groups;
-        fbase = 0;
-        if (valid) {
-            unsigned long long b = (unsigned long long)g;
+    // this lane's group inside the warp tile (fixed for every tile)
+    unsigned gbase = (unsigned)lane;
 #pragma unroll
-            for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
-            fbase = (long long)(((b >> 5) << 6) | (b & 31ull));
+    for (int b = 0; b < K; ++b) gbase = (unsigned)ins0(gbase, a.t.ltpos[b]);
+    const unsigned gsw = a.t.gswz[(lane >> a.t.lsh) & a.t.lmask];
+    // shared-memory float offset of the group's real part j (gb: gbase through an opaque move,
+    // so the offsets are recomputed per use rather than held in registers across the tile loop)
+    auto spos = [&](unsigned gb, int j) -> unsigned {
+        const unsigned i = gb + (unsigned)a.t.loff[j];
+        return ((i >> 5) << 6) | ((i & 31u) ^ gsw);
+    };
+    auto tile_block0 = [&](long long wt) -> unsigned long long {
+        unsigned long long b0 = (unsigned long long)wt;
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                x[j] = sv[fbase + a.foff[j]];
-                x[D + j] = sv[fbase + a.foff[j] + 32];
+        for (int i = 0; i < K; ++i) b0 = ins0(b0, a.t.fpos[i]);
+        return b0;
+    };
+    auto gchunk = [&](unsigned long long b0, int c) -> float * {
+        return sv + (long long)((b0 + (unsigned long long)a.t.fblk[c >> 4]) << 6) + (c & 15) * 4;
+    };
+    auto schunk = [&](int c, unsigned &sw) -> float * {
+        sw = a.t.swz[c >> 4];
+        return wbuf + (c >> 4) * 64 + (c & 8) * 4 + (((c & 7) ^ (int)(sw >> 2)) << 2);
+    };
+
+    // ---- direct variant: the lane's group in registers
+    float xd[STAGED ? 1 : 2 * D];
+    long long fb_next = 0, fb_cur = 0;
+    bool v_next = false, v_cur = false;
+    auto load_direct = [&](long long tile) {
+        if constexpr (!STAGED) {
+            const long long g = tile * kTcM + (tid & 127);
+            v_next = g < a.n_groups;
+            fb_next = 0;
+            if (v_next) {
+                unsigned long long b = (unsigned long long)g;
+#pragma unroll
+                for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
+                fb_next = (long long)(((b >> 5) << 6) | (b & 31ull));
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    xd[j] = sv[fb_next + a.foff[j]];
+                    xd[D + j] = sv[fb_next + a.foff[j] + 32];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 2 * D; ++j) xd[j] = 0.f;
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 2 * D; ++j) x[j] = 0.f;
         }
     };
-    // this thread's A row into its TMEM lane of the warpgroup's A region
-    auto write_a = [&]() {
+    float4 pre[STAGED ? S::CPL : 1];
+    auto prefetch = [&](long long wt) {
+        if constexpr (!STAGED) {
+            (void)wt;
+        } else if (wt < a.t.n_tiles) {
+            const unsigned long long b0 = tile_block0(wt);
+            const int ln = (int)opaque_u32((unsigned)lane);
+#pragma unroll
+            for (int i = 0; i < S::CPL; ++i) pre[i] = *reinterpret_cast<const float4 *>(gchunk(b0, ln + 32 * i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < S::CPL; ++i) pre[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto fetch = [&](long long tile) {   // next MMA tile's inputs, either variant
+        if constexpr (STAGED) prefetch(4 * tile + (warp & 3));
+        else load_direct(tile);
+    };
+    // prefetched chunks -> swizzled warp tile -> this lane's A row in tensor memory
+    auto stage_and_write_a = [&]() {
+        if constexpr (STAGED) {
+            const int ln = (int)opaque_u32((unsigned)lane);
+#pragma unroll
+            for (int i = 0; i < S::CPL; ++i) {
+                unsigned sw;
+                float *d = schunk(ln + 32 * i, sw);
+                *reinterpret_cast<float4 *>(d) = xor_perm4(pre[i], sw);
+            }
+            __syncwarp();
+        }
+        const unsigned gb = opaque_u32(gbase);
+        // A row element kk = (c, j): kk < D real part of amplitude kk, else imaginary part of kk - D
+        auto elem = [&](int kk) -> float {
+            if constexpr (STAGED) return wbuf[spos(gb, kk % D) + (kk >= D ? 32 : 0)];
+            else return xd[kk];
+        };
         if constexpr (MODE == kModeTF32) {
 #pragma unroll
             for (int cb = 0; cb < S::KD / 32; ++cb) {
                 uint32_t r[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) r[i] = f32_to_tf32(x[cb * 32 + i]);
+                for (int i = 0; i < 32; ++i) r[i] = f32_to_tf32(elem(cb * 32 + i));
                 tmem_st32(tA + t_lane + cb * 32, r);
             }
         } else {
-            // a 32-bit column holds two bf16 elements: element 2c in the low half of column c.
-            // hi and lo are packed and stored one after the other to keep 32 registers live.
-            constexpr int NC = S::KD / 2 < 32 ? S::KD / 2 : 32;   // columns per chunk
+            // a 32-bit column holds two bf16 elements: element 2c in the low half of column c
+            constexpr int NC = 16;   // columns per chunk (32 elements): keeps the live set small
 #pragma unroll
             for (int cb = 0; cb < S::KD / (2 * NC); ++cb) {
+                float xs[2 * NC];
+#pragma unroll
+                for (int e = 0; e < 2 * NC; ++e) xs[e] = elem(cb * 2 * NC + e);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                     uint32_t r[32];
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
                         if (c < NC) {
-                            const float x0 = x[cb * 2 * NC + 2 * c], x1 = x[cb * 2 * NC + 2 * c + 1];
+                            const float x0 = xs[2 * c], x1 = xs[2 * c + 1];
                             const uint32_t hi = pack_bf16x2(x0, x1);
                             if (part == 0) {
                                 r[c] = hi;
@@ -331,9 +426,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) 
                             r[c] = 0u;
                         }
                     }
-                    const uint32_t dst = tA + t_lane + (uint32_t)(part * S::A_COLS + cb * NC);
-                    if constexpr (NC == 32) tmem_st32(dst, r);
-                    else tmem_st16(dst, r);
+                    tmem_st16(tA + t_lane + (uint32_t)(part * S::A_COLS + cb * NC), r);
                 }
             }
         }
@@ -346,47 +439,73 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) 
         constexpr int CH = S::KSTEP / S::EPC;           // 16-byte chunks of B per instruction (2)
         if constexpr (MODE == kModeTF32) {
 #pragma unroll
-            for (int s = 0; s < NSTEP; ++s)
-                mma_ta<MODE>(tD, tA + s * ACOL, sdesc(b0 + s * CH * S::LBO_B, S::LBO_B, 128), idesc, s > 0);
+            for (int st = 0; st < NSTEP; ++st)
+                mma_ta<MODE>(tD, tA + st * ACOL, sdesc(b0 + st * CH * S::LBO_B, S::LBO_B, 128), idesc, st > 0);
         } else {
             const uint32_t a_img[3] = {tA, tA, tA + (uint32_t)S::A_COLS};   // hi, hi, lo
             const uint32_t b_img[3] = {b0, b0 + (uint32_t)S::B_IMG, b0};     // hi, lo, hi
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
-                for (int s = 0; s < NSTEP; ++s)
-                    mma_ta<MODE>(tD, a_img[p] + s * ACOL, sdesc(b_img[p] + s * CH * S::LBO_B, S::LBO_B, 128), idesc,
-                                 (p > 0 || s > 0));
+                for (int st = 0; st < NSTEP; ++st)
+                    mma_ta<MODE>(tD, a_img[p] + st * ACOL, sdesc(b_img[p] + st * CH * S::LBO_B, S::LBO_B, 128), idesc,
+                                 (p > 0 || st > 0));
         }
         mma_commit(bar_mma);
     };
-    auto epilogue = [&](long long fbase, bool valid) {
+    // accumulator -> the group's places in the warp tile -> global memory (16-byte stores)
+    auto epilogue_direct = [&]() {
 #pragma unroll
-        for (int cb = 0; cb < S::KD / 32; ++cb) {
-            float v[32];
-            tmem_ld32(tD + t_lane + cb * 32, v);
-            if (valid) {
+        for (int cb = 0; cb < S::KD / 16; ++cb) {
+            float v[16];
+            tmem_ld16(tD + t_lane + cb * 16, v);
+            if (v_cur) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int col = cb * 32 + i;           // column (c', r): c' = col / D, r = col % D
-                    const int r = col % D;
-                    sv[fbase + a.foff[r] + (col >= D ? 32 : 0)] = v[i];
+                for (int i = 0; i < 16; ++i) {
+                    const int col = cb * 16 + i;           // column (c', r): c' = col / D, r = col % D
+                    sv[fb_cur + a.foff[col % D] + (col >= D ? 32 : 0)] = v[i];
                 }
             }
         }
     };
+    auto epilogue = [&](long long wt) {
+#pragma unroll
+        for (int cb = 0; cb < S::KD / 16; ++cb) {
+            float v[16];
+            tmem_ld16(tD + t_lane + cb * 16, v);
+            const unsigned gb = opaque_u32(gbase);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = cb * 16 + i;           // column (c', r): c' = col / D, r = col % D
+                wbuf[spos(gb, col % D) + (col >= D ? 32 : 0)] = v[i];
+            }
+        }
+        __syncwarp();
+        if (wt < a.t.n_tiles) {
+            const unsigned long long b0 = tile_block0(wt);
+            const int ln = (int)opaque_u32((unsigned)lane);
+#pragma unroll
+            for (int i = 0; i < S::CPL; ++i) {
+                const int c = ln + 32 * i;
+                unsigned sw;
+                const float *src = schunk(c, sw);
+                *reinterpret_cast<float4 *>(gchunk(b0, c)) = xor_perm4(*reinterpret_cast<const float4 *>(src), sw);
+            }
+        }
+        __syncwarp();
+    };
 
-    // tiles of this warpgroup: blockIdx.x + (2 i + wg) * gridDim.x
+    // MMA tiles of this warpgroup: blockIdx.x + (2 i + wg) * gridDim.x; warp tile = 4 * tile + (warp & 3)
     const long long tstride = 2ll * gridDim.x;
     long long tile = blockIdx.x + (long long)wg * gridDim.x;
     uint32_t phase = 0u;
     bool ok = true;
-    long long fb_cur = 0;
-    bool v_cur = false;
-    const bool lead = row == 0;
-    if (tile < a.n_tiles) {
-        load_group(tile, fb_cur, v_cur);
-        write_a();
+    const bool lead = (tid & 127) == 0;
+    if (tile < a.n_mma_tiles) {
+        fetch(tile);
+        fb_cur = fb_next;
+        v_cur = v_next;
+        stage_and_write_a();
         tc_fence_before();
         wg_sync(wg);
         if (lead) {
@@ -397,27 +516,26 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) 
         wg_sync(wg);
         ok = status[wg] == 0;
     }
-    while (ok && tile < a.n_tiles) {
+    while (ok && tile < a.n_mma_tiles) {
         const long long nt = tile + tstride;
-        long long fb_next = 0;
-        bool v_next = false;
-        if (nt < a.n_tiles) load_group(nt, fb_next, v_next);   // in flight during the wait + epilogue
+        if (nt < a.n_mma_tiles) fetch(nt);                    // in flight during the wait + epilogue
         if (lead && !mbar_wait_bounded(bar_mma, phase)) status[wg] = 2;
         wg_sync(wg);
         if (status[wg] != 0) { ok = false; break; }
         phase ^= 1u;
         tc_fence_after();
-        epilogue(fb_cur, v_cur);                                 // reads D; MMA(nt) writes D after the sync
-        if (nt < a.n_tiles) write_a();                            // A region is free: MMA(tile) completed
+        if constexpr (STAGED) epilogue(4 * tile + (warp & 3));   // reads D; MMA(nt) writes D after the sync
+        else epilogue_direct();
+        fb_cur = fb_next;
+        v_cur = v_next;
+        if (nt < a.n_mma_tiles) stage_and_write_a();          // A region is free: MMA(tile) completed
         tc_fence_before();
         wg_sync(wg);
-        if (nt < a.n_tiles && lead) {
+        if (nt < a.n_mma_tiles && lead) {
             tc_fence_after();
             issue_mma();
         }
         tile = nt;
-        fb_cur = fb_next;
-        v_cur = v_next;
     }
     if (!ok && lead) atomicOr(a.err, status[wg] == 1 ? 0x10 : 0x20);
     tc_fence_before();
@@ -521,8 +639,11 @@ template <int K, int MODE>
 int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)
 {
     using S = TcShape<K, MODE>;
+    if (n < K + 5) { set_error("tensor-core path needs n >= k + 5 (n=%d, k=%d)", n, K); return SV_EINVAL; }
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
+    const bool staged = g.targets[0] < 5;   // targets ascending: some target inside the 32-amplitude block
+    make_tile_map(g, n, K, &a.t);
     for (int b = 0; b < K; ++b) a.tpos[b] = g.targets[b];
     for (int j = 0; j < (1 << K); ++j) {
         unsigned long long o = 0;
@@ -531,23 +652,24 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
         a.foff[j] = (long long)(((o >> 5) << 6) | (o & 31ull));
     }
     a.n_groups = 1ll << (n - K);
-    a.n_tiles = (a.n_groups + kTcM - 1) / kTcM;
+    a.n_mma_tiles = staged ? (a.t.n_tiles + 3) / 4 : (a.n_groups + kTcM - 1) / kTcM;
     a.bimg = dtc;
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
-    auto kern = apply_tc_kernel<K, MODE>;
+    auto kern = staged ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
     static bool attr_set[2] = {false, false};
     {
         std::lock_guard<std::mutex> lk(g_tc_mu);
-        if (!attr_set[MODE]) {
+        if (!attr_set[staged]) {
             SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
-            attr_set[MODE] = true;
+            attr_set[staged] = true;
         }
     }
-    // CTAs per SM bounded by registers (MIN_BLOCKS) and by tensor memory (512 columns per SM)
+    // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
     const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
-    const int per_sm = std::min(S::MIN_BLOCKS, by_tmem);
-    const long long grid = std::min<long long>((a.n_tiles + 1) / 2, (long long)num_sms * per_sm);
+    const int by_smem = std::max(1, (227 * 1024) / (S::SMEM + 1024));
+    const int per_sm = std::min(S::MIN_BLOCKS, std::min(by_tmem, by_smem));
+    const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
     kern<<<(unsigned)grid, 2 * kTcThreads, S::SMEM, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
