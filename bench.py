@@ -3,8 +3,10 @@
 A step is one pass of the hot path over one circuit: set |0...0>, apply every fused gate, take
 the fp64 norm and draw 1024 samples.  The circuit is the 5x6-grid random circuit (20 cycles of
 sqrt(X)/sqrt(Y)/sqrt(W) plus fSim(pi/2, pi/6) on patterns ABCDCDAB, seed 2, 845 gates), fused
-greedily to at most --max-k qubits on the host.  The complex64 state (8 GiB) is larger than L2,
-so no flush is needed between steps.
+on the host to at most --max-k qubits; fused gates of --tc-min-k or more qubits run on the tensor
+cores in --precision mode.  The complex64 state (8 GiB) is larger than L2, so no flush is needed
+between steps.  The same line reports the plain path for comparison: fp32 CUDA-core kernels with
+fixed greedy fusion at every max size 2..6.
 
 Prints one JSON line (rank 0).  `value` is seconds per circuit for the whole job (time of the
 slowest rank / circuits run by all ranks); `e2e` is the same metric measured through the C ABI
@@ -187,7 +189,7 @@ def bench_ours(args):
 
     n, gates = wl.circuit_30q_grid()
     prec = {"fp32": B.PREC_FP32, "tf32": B.PREC_TF32, "bf16x3": B.PREC_BF16X3}[args.precision]
-    fused = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec)
+    fused = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k)
     n_fused = B.sv_fused_count(fused)
     infos = [B.sv_fused_get_info(fused, i) for i in range(n_fused)]
     stream = torch.cuda.Stream()
@@ -238,7 +240,7 @@ def bench_ours(args):
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f2 = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec)
+        f2 = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k)
         B.sv_init(st.h, 0)
         B.sv_apply_fused_gates(st.h, f2)
         smp = B.sv_sample(st.h, uniforms)
@@ -246,6 +248,24 @@ def bench_ours(args):
         B.sv_fused_free(f2)
         e2e_times.append(time.perf_counter() - t0)
     mat_bytes = sum(2 * 4 * (1 << (2 * i["k"])) for i in infos)
+
+    # ---- the plain path: fp32 CUDA cores, fixed greedy fusion, every max size (device-timed)
+    plain = {}
+    if not args.no_plain_sweep:
+        for mk in range(2, 7):
+            fp = B.sv_fuse_circuit(gates, n, max_k=mk, precision=B.PREC_FP32)
+            B.sv_init(st.h, 0)
+            B.sv_apply_fused_gates(st.h, fp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                B.sv_init(st.h, 0)
+                B.sv_apply_fused_gates(st.h, fp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plain[str(mk)] = {"s_per_circuit": e0.elapsed_time(e1) / 2e3, "fused_gates": B.sv_fused_count(fp)}
+            B.sv_fused_free(fp)
     h2d = 8 * N_SAMPLES + mat_bytes
     d2h = 8 * N_SAMPLES + 8
 
@@ -266,7 +286,7 @@ def bench_ours(args):
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_qubits": n, "max_k": args.max_k, "precision": args.precision,
-                   "fusion": "greedy", "fused_gates": n_fused, "samples_per_step": N_SAMPLES,
+                   "tc_min_k": args.tc_min_k, "fusion": "greedy", "fused_gates": n_fused, "samples_per_step": N_SAMPLES,
                    "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -279,6 +299,9 @@ def bench_ours(args):
         "per_kernel_class": {f"{p}_k{k}": {"launches": len(v), "avg_us": statistics.mean(v),
                                            "gbs": bytes_per_launch / (statistics.mean(v) * 1e-6) / 1e9}
                              for (p, k), v in sorted(kernel_us.items())},
+        "plain_fusion_fp32": plain,
+        "plain_best_s": min((v["s_per_circuit"] for v in plain.values()), default=None),
+        "speedup_vs_best_plain": (min(v["s_per_circuit"] for v in plain.values()) / value) if plain else None,
         "norm": norms[-1] if norms else None,
         "clocks": clk.summary(),
     }
@@ -301,8 +324,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--max-k", type=int, default=4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--max-k", type=int, default=6)
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--tc-min-k", type=int, default=4)
+    ap.add_argument("--no-plain-sweep", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-gates", type=int, default=12)
     ap.add_argument("--ref-gates-per-step", type=int, default=3)

@@ -69,3 +69,29 @@ def time_specs(specs, repeats: int = 5, seed: int = 0, precision: int = B.PREC_F
                           "us": statistics.median(x["us"] for x in r)}
         st.free()
     return out
+
+
+def main(argv=None):
+    """Time single fused gates: python -m paper_2602_09604_gb300.timing_sweep --n 26 --targets 0,1,2,4,10,24 ..."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, required=True)
+    ap.add_argument("--targets", required=True, help="comma-separated target qubits")
+    ap.add_argument("--path", default="auto", choices=list(B.PATH_NAMES.values()))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--repeats", type=int, default=3)
+    ap.add_argument("--warm", type=int, default=1)
+    args = ap.parse_args(argv)
+    path = {v: k for k, v in B.PATH_NAMES.items()}[args.path]
+    prec = {"fp32": B.PREC_FP32, "tf32": B.PREC_TF32, "bf16x3": B.PREC_BF16X3}[args.precision]
+    targets = tuple(int(t) for t in args.targets.split(","))
+    rec = time_specs([(args.n, targets, path)], repeats=args.repeats, precision=prec, warm=args.warm)[0]
+    rec["gbs"] = 16 * (1 << args.n) / (rec["us"] * 1e-6) / 1e9
+    rec["path"] = B.PATH_NAMES[rec["path"]]
+    B.sv_device_status()
+    print(json.dumps(rec))
+
+
+if __name__ == "__main__":
+    main()
