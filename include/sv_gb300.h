@@ -98,7 +98,8 @@ typedef struct sv_fuse_opts {
     int precision;      /* enum sv_precision */
     int tc_min_k;       /* smallest k sent to tensor cores when precision != FP32; 0 = 5 */
     int force_path;     /* enum sv_path; SV_PATH_AUTO lets the library choose (testing knob) */
-    const sv_mlp *model;/* learned mode only; NULL or untrained model => greedy at model's fallback k */
+    const sv_mlp *model;/* learned mode: trained cost model; NULL, untrained or a validation error
+                           above 25% => greedy fusion at max_k (model's fallback k when present) */
 } sv_fuse_opts;
 
 /* Facts about one fused gate (introspection). */
@@ -170,6 +171,63 @@ SV_API int sv_fused_get_matrix(const sv_fused *f, int i, double *out);
  * tensor-core operands) with cudaMalloc/cudaMemcpy.  With `timings` non-NULL (one record per
  * fused gate) each launch is bracketed by CUDA events and the call synchronises. */
 SV_API int sv_apply_fused_gates(sv_state *st, const sv_fused *f, sv_timing *timings);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned fusion cost model (no counterpart in the paper's code: the paper tunes its fusion size
+ * per machine with a synthetic benchmark, section VI-C; here the simulator learns a cost model
+ * from timings of its own kernels).  A 16 -> 64 -> 64 -> 64 -> 1 fp32 MLP with ReLU predicts
+ * y = ln(t / 1 us) - n ln 2 (standardised), the log device time per amplitude of one fused gate.
+ * Forward, backward and Adam run as CUDA kernels on the device current at creation, on the given
+ * stream.  sv_fuse_circuit in SV_FUSE_LEARNED mode uses it to choose the fusion partition, the
+ * largest fused size and each fused gate's kernel path.
+ * ------------------------------------------------------------------------------------------- */
+
+typedef struct sv_mlp_train_opts {
+    int epochs;         /* passes over the training rows */
+    int batch;          /* rows per Adam step, 1..1024 */
+    float lr;           /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8) */
+    uint64_t seed;      /* shuffling and the train / validation split */
+    float val_frac;     /* fraction held out to measure the prediction error, [0, 0.9) */
+    int fallback_k;     /* greedy max size used when the model is not trusted */
+} sv_mlp_train_opts;
+
+typedef struct sv_mlp_stats {
+    float train_loss;   /* mean squared error (standardised) over the last epoch */
+    float val_mape;     /* mean |predicted - measured| / measured time on the held-out rows */
+    long long n_train, n_val, steps;
+    int trained;
+    float y_mean, y_std;
+    int fallback_k;
+} sv_mlp_stats;
+
+/* Number of parameters (9473).  Flat order: W1 (64x16 row-major), b1, W2 (64x64), b2, W3, b3,
+ * W4 (1x64), b4. */
+SV_API int sv_mlp_num_params(void);
+/* New model with He-normal weights drawn from `seed` (SplitMix64 + Box-Muller), zero biases. */
+SV_API int sv_mlp_create(uint64_t seed, void *cuda_stream, sv_mlp **out);
+SV_API void sv_mlp_free(sv_mlp *m);
+SV_API int sv_mlp_get_params(const sv_mlp *m, float *out);     /* host buffer of sv_mlp_num_params() */
+SV_API int sv_mlp_set_params(sv_mlp *m, const float *in);
+/* Feature vector (16 floats) of a fused gate with k targets (any order), kernel path (enum sv_path)
+ * and n qubits: [k/6, sorted targets / n (6, padded with -1), one-hot path LOW..TC_BF16X3 (5),
+ * n/34, (#targets < 5)/5, max target / n, (smallest target < 5)]. */
+SV_API int sv_mlp_features(int k, const int *targets, int path, int n_qubits, float *out);
+/* Loss and gradient of the mean squared error for B rows (X: B x 16, t: B standardised targets,
+ * both host), at the current parameters; grads: host buffer of sv_mlp_num_params().  B <= 1024. */
+SV_API int sv_mlp_gradients(sv_mlp *m, const float *X, const float *t, int B, float *loss, float *grads);
+/* One Adam update with the gradient left by the last sv_mlp_gradients call. */
+SV_API int sv_mlp_adam_step(sv_mlp *m, float lr);
+/* Train on N rows of features X (N x 16, host) and measured times us (N, microseconds, host).
+ * opts may be NULL (200 epochs, batch 256, lr 1e-3, seed 1, 10% validation, fallback k 4). */
+SV_API int sv_mlp_train(sv_mlp *m, const float *X, const float *us, long long N, const sv_mlp_train_opts *opts,
+                        sv_mlp_stats *stats);
+/* Predicted microseconds for `rows` feature rows (host in, host out).  Needs a trained model. */
+SV_API int sv_mlp_predict(sv_mlp *m, const float *X, int rows, double *out_us);
+SV_API int sv_mlp_get_stats(const sv_mlp *m, sv_mlp_stats *stats);
+/* Binary file: 8-byte magic, parameter count, trained flag, fallback k, y mean, y deviation,
+ * validation error, parameters (little-endian fp32). */
+SV_API int sv_mlp_save(const sv_mlp *m, const char *path);
+SV_API int sv_mlp_load(const char *path, void *cuda_stream, sv_mlp **out);
 
 /* ---------------------------------------------------------------------------------------------
  * Reductions

@@ -46,6 +46,17 @@ class sv_fused_info(ctypes.Structure):
                 ("n_source_gates", ctypes.c_int)]
 
 
+class sv_mlp_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("val_frac", ctypes.c_float), ("fallback_k", ctypes.c_int)]
+
+
+class sv_mlp_stats(ctypes.Structure):
+    _fields_ = [("train_loss", ctypes.c_float), ("val_mape", ctypes.c_float), ("n_train", ctypes.c_longlong),
+                ("n_val", ctypes.c_longlong), ("steps", ctypes.c_longlong), ("trained", ctypes.c_int),
+                ("y_mean", ctypes.c_float), ("y_std", ctypes.c_float), ("fallback_k", ctypes.c_int)]
+
+
 class sv_timing(ctypes.Structure):
     _fields_ = [("us", ctypes.c_float), ("k", ctypes.c_int), ("path", ctypes.c_int),
                 ("target_mask", ctypes.c_uint64)]
@@ -75,6 +86,21 @@ def _load():
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_device_status": (I, []),
+        "sv_mlp_num_params": (I, []),
+        "sv_mlp_create": (I, [ctypes.c_uint64, P, ctypes.POINTER(P)]),
+        "sv_mlp_free": (None, [P]),
+        "sv_mlp_get_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+        "sv_mlp_set_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
+        "sv_mlp_features": (I, [I, ctypes.POINTER(ctypes.c_int), I, I, ctypes.POINTER(ctypes.c_float)]),
+        "sv_mlp_gradients": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), I,
+                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "sv_mlp_adam_step": (I, [P, ctypes.c_float]),
+        "sv_mlp_train": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_longlong,
+                             ctypes.POINTER(sv_mlp_train_opts), ctypes.POINTER(sv_mlp_stats)]),
+        "sv_mlp_predict": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(ctypes.c_double)]),
+        "sv_mlp_get_stats": (I, [P, ctypes.POINTER(sv_mlp_stats)]),
+        "sv_mlp_save": (I, [P, ctypes.c_char_p]),
+        "sv_mlp_load": (I, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
         "sv_last_error": (ctypes.c_char_p, []),
         "sv_version": (ctypes.c_char_p, []),
     }
@@ -224,3 +250,90 @@ def sv_device_status() -> None:
 
 def sv_version() -> str:
     return lib.sv_version().decode()
+
+
+# --------------------------------------------------------------------------------------- cost model
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def sv_mlp_num_params() -> int:
+    return int(lib.sv_mlp_num_params())
+
+
+def sv_mlp_create(seed: int = 1, stream: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib.sv_mlp_create(ctypes.c_uint64(seed), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_mlp_free(m) -> None:
+    lib.sv_mlp_free(m)
+
+
+def sv_mlp_get_params(m) -> np.ndarray:
+    out = np.zeros(sv_mlp_num_params(), dtype=np.float32)
+    _check(lib.sv_mlp_get_params(m, _fptr(out)))
+    return out
+
+
+def sv_mlp_set_params(m, params) -> None:
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    assert p.size == sv_mlp_num_params()
+    _check(lib.sv_mlp_set_params(m, _fptr(p)))
+
+
+def sv_mlp_features(k: int, targets, path: int, n: int) -> np.ndarray:
+    t = (ctypes.c_int * MAX_K)(*[int(x) for x in targets])
+    out = np.zeros(16, dtype=np.float32)
+    _check(lib.sv_mlp_features(k, t, path, n, _fptr(out)))
+    return out
+
+
+def sv_mlp_gradients(m, X, t):
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+    loss = ctypes.c_float()
+    g = np.zeros(sv_mlp_num_params(), dtype=np.float32)
+    _check(lib.sv_mlp_gradients(m, _fptr(X), _fptr(t), t.size, ctypes.byref(loss), _fptr(g)))
+    return loss.value, g
+
+
+def sv_mlp_adam_step(m, lr: float) -> None:
+    _check(lib.sv_mlp_adam_step(m, ctypes.c_float(lr)))
+
+
+def _stats_dict(st):
+    return {f: getattr(st, f) for f, _ in sv_mlp_stats._fields_}
+
+
+def sv_mlp_train(m, X, us, epochs=200, batch=256, lr=1e-3, seed=1, val_frac=0.1, fallback_k=4) -> dict:
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    us = np.ascontiguousarray(np.asarray(us, dtype=np.float32))
+    o = sv_mlp_train_opts(epochs, batch, lr, seed, val_frac, fallback_k)
+    st = sv_mlp_stats()
+    _check(lib.sv_mlp_train(m, _fptr(X), _fptr(us), us.size, ctypes.byref(o), ctypes.byref(st)))
+    return _stats_dict(st)
+
+
+def sv_mlp_predict(m, X) -> np.ndarray:
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    out = np.zeros(X.shape[0], dtype=np.float64)
+    _check(lib.sv_mlp_predict(m, _fptr(X), X.shape[0], out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def sv_mlp_get_stats(m) -> dict:
+    st = sv_mlp_stats()
+    _check(lib.sv_mlp_get_stats(m, ctypes.byref(st)))
+    return _stats_dict(st)
+
+
+def sv_mlp_save(m, path: str) -> None:
+    _check(lib.sv_mlp_save(m, path.encode()))
+
+
+def sv_mlp_load(path: str, stream: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib.sv_mlp_load(path.encode(), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h

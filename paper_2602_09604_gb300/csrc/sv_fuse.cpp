@@ -78,6 +78,148 @@ std::vector<cplx> identity(size_t dim)
     return m;
 }
 
+// M_S (acting on qubit list S) re-expressed on the ascending superset T: M_T = M_S (x) I on T \ S.
+std::vector<cplx> expand(const std::vector<cplx> &M, const std::vector<int> &S, const std::vector<int> &T)
+{
+    const int t = (int)T.size(), sz = (int)S.size();
+    if (sz == t) return M;
+    const size_t dT = size_t(1) << t, dS = size_t(1) << sz, dR = size_t(1) << (t - sz);
+    std::vector<size_t> depS(dS), depR(dR);
+    int posS[16], posR[16], nr = 0;
+    for (int i = 0; i < sz; ++i) posS[i] = int(std::find(T.begin(), T.end(), S[i]) - T.begin());
+    for (int i = 0; i < t; ++i)
+        if (std::find(S.begin(), S.end(), T[i]) == S.end()) posR[nr++] = i;
+    for (size_t v = 0; v < dS; ++v) {
+        size_t o = 0;
+        for (int b = 0; b < sz; ++b)
+            if ((v >> b) & 1) o |= size_t(1) << posS[b];
+        depS[v] = o;
+    }
+    for (size_t v = 0; v < dR; ++v) {
+        size_t o = 0;
+        for (int b = 0; b < nr; ++b)
+            if ((v >> b) & 1) o |= size_t(1) << posR[b];
+        depR[v] = o;
+    }
+    std::vector<cplx> out(dT * dT, cplx(0.0, 0.0));
+    for (size_t e = 0; e < dR; ++e)
+        for (size_t r = 0; r < dS; ++r)
+            for (size_t c = 0; c < dS; ++c) out[(depS[r] | depR[e]) * dT + (depS[c] | depR[e])] = M[r * dS + c];
+    return out;
+}
+
+struct Dense {
+    std::vector<int> q;        // qubits: targets then controls (local bit order of m)
+    std::vector<cplx> m;       // dense matrix with the controls folded in
+};
+
+constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above this validation error
+
+// Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
+std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k)
+{
+    std::vector<Block> open, emitted;
+    long long stamp = 0;
+    for (size_t gi = 0; gi < dense.size(); ++gi) {
+        const std::vector<int> &Q = dense[gi].q;
+        uint64_t qmask = 0;
+        for (int q : Q) qmask |= uint64_t(1) << q;
+        std::vector<int> touching;
+        for (int b = 0; b < (int)open.size(); ++b) {
+            for (int q : open[b].qubits)
+                if ((qmask >> q) & 1) { touching.push_back(b); break; }
+        }
+        // close touching blocks with the most qubits outside Q until the union fits
+        auto outside = [&](int b) {
+            int c = 0;
+            for (int q : open[b].qubits) c += !((qmask >> q) & 1);
+            return c;
+        };
+        std::sort(touching.begin(), touching.end(), [&](int a, int b) {
+            int oa = outside(a), ob = outside(b);
+            return oa != ob ? oa > ob : open[a].created < open[b].created;
+        });
+        auto union_size = [&](size_t from) {
+            uint64_t m = qmask;
+            for (size_t i = from; i < touching.size(); ++i)
+                for (int q : open[touching[i]].qubits) m |= uint64_t(1) << q;
+            return __builtin_popcountll(m);
+        };
+        size_t first_kept = 0;
+        const int limit = std::max(max_k, (int)Q.size());
+        while (first_kept < touching.size() && union_size(first_kept) > limit) ++first_kept;
+        // emit closed blocks in creation order
+        std::vector<int> closed(touching.begin(), touching.begin() + first_kept);
+        std::sort(closed.begin(), closed.end(), [&](int a, int b) { return open[a].created < open[b].created; });
+        std::vector<int> kept(touching.begin() + first_kept, touching.end());
+        std::sort(kept.begin(), kept.end(), [&](int a, int b) { return open[a].created < open[b].created; });
+        for (int b : closed) emitted.push_back(std::move(open[b]));
+
+        // merge kept blocks (disjoint, so they commute) and the gate into one block over the union
+        uint64_t um = qmask;
+        for (int b : kept)
+            for (int q : open[b].qubits) um |= uint64_t(1) << q;
+        Block nb;
+        for (int q = 0; q < n_qubits; ++q)
+            if ((um >> q) & 1) nb.qubits.push_back(q);
+        nb.n_src = 1;
+        if (kept.empty()) {
+            nb.mat = identity(size_t(1) << nb.qubits.size());
+        } else {
+            nb.mat = expand(open[kept[0]].mat, open[kept[0]].qubits, nb.qubits);
+            nb.n_src += open[kept[0]].n_src;
+            for (size_t i = 1; i < kept.size(); ++i) {
+                left_multiply(nb.mat, nb.qubits, open[kept[i]].mat, open[kept[i]].qubits);
+                nb.n_src += open[kept[i]].n_src;
+            }
+        }
+        left_multiply(nb.mat, nb.qubits, dense[gi].m, Q);
+        nb.created = stamp++;
+        std::vector<char> drop(open.size(), 0);
+        for (int b : touching) drop[b] = 1;
+        std::vector<Block> rest;
+        rest.reserve(open.size() + 1);
+        for (size_t b = 0; b < open.size(); ++b)
+            if (!drop[b]) rest.push_back(std::move(open[b]));
+        rest.push_back(std::move(nb));
+        open.swap(rest);
+    }
+    std::sort(open.begin(), open.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
+    for (Block &b : open) emitted.push_back(std::move(b));
+
+    // horizontal pass: move each block back over disjoint predecessors and merge where it fits
+    std::vector<Block> merged;
+    const int kScanBack = 64;
+    for (Block &b : emitted) {
+        uint64_t bm = 0;
+        for (int q : b.qubits) bm |= uint64_t(1) << q;
+        const int lim = std::max(max_k, (int)b.qubits.size());
+        int target = -1;
+        for (int p = (int)merged.size() - 1, steps = 0; p >= 0 && steps < kScanBack; --p, ++steps) {
+            uint64_t pm = 0;
+            for (int q : merged[p].qubits) pm |= uint64_t(1) << q;
+            if (__builtin_popcountll(pm | bm) <= lim) { target = p; break; }
+            if (pm & bm) break;   // cannot move past a block it shares a qubit with
+        }
+        if (target < 0) {
+            merged.push_back(std::move(b));
+            continue;
+        }
+        Block &t = merged[size_t(target)];
+        uint64_t um = bm;
+        for (int q : t.qubits) um |= uint64_t(1) << q;
+        std::vector<int> U;
+        for (int q = 0; q < n_qubits; ++q)
+            if ((um >> q) & 1) U.push_back(q);
+        std::vector<cplx> M = expand(t.mat, t.qubits, U);   // earlier block first
+        left_multiply(M, U, b.mat, b.qubits);
+        t.mat = std::move(M);
+        t.qubits = std::move(U);
+        t.n_src += b.n_src;
+    }
+    return merged;
+}
+
 bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
 {
     for (size_t i = 0; i < d; ++i)
@@ -131,7 +273,6 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
 
     // ---- validate and densify every input gate (controls folded into the matrix)
-    struct Dense { std::vector<int> q; std::vector<cplx> m; };
     std::vector<Dense> dense;
     try { dense.resize(size_t(n_gates)); } catch (const std::bad_alloc &) { set_error("sv_fuse_circuit: out of host memory"); return SV_ENOMEM; }
     for (int gi = 0; gi < n_gates; ++gi) {
@@ -178,10 +319,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     f->n = n_qubits;
     f->precision = opts.precision;
 
-    std::vector<Block> open, emitted;
-    long long stamp = 0;
-    auto emit = [&](Block &b) { emitted.push_back(std::move(b)); };
-    auto finish = [&](Block &b) {
+    auto finish = [&](Block &b, int path) {
         FusedGate fg;
         fg.k = (int)b.qubits.size();
         for (int j = 0; j < fg.k; ++j) {
@@ -198,14 +336,13 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             fg.ur[i] = (float)fg.mat[i].real();
             fg.ui[i] = (float)fg.mat[i].imag();
         }
-        fg.path = classify_path(fg, n_qubits, opts.precision, opts.tc_min_k, opts.force_path);
+        fg.path = path >= 0 ? path : classify_path(fg, n_qubits, opts.precision, opts.tc_min_k, opts.force_path);
         f->gates.push_back(std::move(fg));
     };
 
-    const int max_k = opts.mode == SV_FUSE_NONE ? 0 : opts.max_k;
-    if (opts.mode == SV_FUSE_NONE) {
-        // one block per input gate, matrix re-expressed over its ascending qubit list
-        try {
+    try {
+        if (opts.mode == SV_FUSE_NONE) {
+            // one block per input gate, matrix re-expressed over its ascending qubit list
             for (int gi = 0; gi < n_gates; ++gi) {
                 Block b;
                 b.qubits = dense[gi].q;
@@ -213,112 +350,57 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 b.mat = identity(size_t(1) << b.qubits.size());
                 left_multiply(b.mat, b.qubits, dense[gi].m, dense[gi].q);
                 b.n_src = 1;
-                finish(b);
+                finish(b, -1);
             }
-        } catch (const std::bad_alloc &) {
-            delete f;
-            set_error("sv_fuse_circuit: out of host memory");
-            return SV_ENOMEM;
+        } else if (opts.mode == SV_FUSE_GREEDY || !mlp_usable(opts.model, kMaxTrustedError)) {
+            const int k = opts.mode == SV_FUSE_GREEDY ? opts.max_k : (opts.model ? mlp_fallback_k(opts.model) : opts.max_k);
+            std::vector<Block> blocks = greedy_partition(dense, n_qubits, k);
+            for (Block &b : blocks) finish(b, -1);
+        } else {
+            // learned: every greedy partition up to max_k, every allowed kernel path per fused
+            // gate, scored by the cost model in one batched forward pass; keep the cheapest
+            std::vector<std::vector<Block>> cand;
+            for (int k = 2; k <= std::max(2, opts.max_k); ++k) cand.push_back(greedy_partition(dense, n_qubits, k));
+            std::vector<float> X;
+            std::vector<int> row_path;
+            std::vector<std::vector<std::pair<int, int>>> rows_of;   // per candidate, per block: [first row, count)
+            for (auto &c : cand) {
+                rows_of.emplace_back();
+                for (Block &b : c) {
+                    FusedGate g;
+                    g.k = (int)b.qubits.size();
+                    for (int j = 0; j < g.k; ++j) g.targets[j] = b.qubits[j];
+                    std::vector<int> paths = {classify_path(g, n_qubits, SV_PREC_FP32, 7, SV_PATH_AUTO)};
+                    if (opts.precision != SV_PREC_FP32 && g.k >= 4 && n_qubits >= g.k + 5)
+                        paths.push_back(opts.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3);
+                    rows_of.back().push_back({(int)row_path.size(), (int)paths.size()});
+                    for (int p : paths) {
+                        float feat[16];
+                        mlp_features(g.k, g.targets, p, n_qubits, feat);
+                        X.insert(X.end(), feat, feat + 16);
+                        row_path.push_back(p);
+                    }
+                }
+            }
+            std::vector<double> us(row_path.size());
+            const int rc = mlp_predict_us(const_cast<sv_mlp *>(opts.model), X.data(), (int)row_path.size(), us.data());
+            if (rc != SV_OK) { delete f; return rc; }
+            size_t best = 0;
+            double best_t = 0.0;
+            std::vector<std::vector<int>> chosen(cand.size());
+            for (size_t c = 0; c < cand.size(); ++c) {
+                double tot = 0.0;
+                for (auto &rr : rows_of[c]) {
+                    int bp = rr.first;
+                    for (int r = rr.first; r < rr.first + rr.second; ++r)
+                        if (us[size_t(r)] < us[size_t(bp)]) bp = r;
+                    tot += us[size_t(bp)];
+                    chosen[c].push_back(row_path[size_t(bp)]);
+                }
+                if (c == 0 || tot < best_t) { best = c; best_t = tot; }
+            }
+            for (size_t i = 0; i < cand[best].size(); ++i) finish(cand[best][i], chosen[best][i]);
         }
-        *out = f;
-        return SV_OK;
-    }
-    for (int gi = 0; gi < n_gates; ++gi) {
-        const std::vector<int> &Q = dense[gi].q;
-        uint64_t qmask = 0;
-        for (int q : Q) qmask |= uint64_t(1) << q;
-        std::vector<int> touching;
-        for (int b = 0; b < (int)open.size(); ++b) {
-            for (int q : open[b].qubits)
-                if ((qmask >> q) & 1) { touching.push_back(b); break; }
-        }
-        // close touching blocks with the most qubits outside Q until the union fits
-        auto outside = [&](int b) {
-            int c = 0;
-            for (int q : open[b].qubits) c += !((qmask >> q) & 1);
-            return c;
-        };
-        std::sort(touching.begin(), touching.end(), [&](int a, int b) {
-            int oa = outside(a), ob = outside(b);
-            return oa != ob ? oa > ob : open[a].created < open[b].created;
-        });
-        auto union_size = [&](size_t from) {
-            uint64_t m = qmask;
-            for (size_t i = from; i < touching.size(); ++i)
-                for (int q : open[touching[i]].qubits) m |= uint64_t(1) << q;
-            return __builtin_popcountll(m);
-        };
-        size_t first_kept = 0;
-        const int limit = std::max(max_k, (int)Q.size());
-        while (first_kept < touching.size() && union_size(first_kept) > limit) ++first_kept;
-        // emit closed blocks in creation order
-        std::vector<int> closed(touching.begin(), touching.begin() + first_kept);
-        std::sort(closed.begin(), closed.end(), [&](int a, int b) { return open[a].created < open[b].created; });
-        std::vector<int> kept(touching.begin() + first_kept, touching.end());
-        std::sort(kept.begin(), kept.end(), [&](int a, int b) { return open[a].created < open[b].created; });
-        for (int b : closed) emit(open[b]);
-
-        // merge kept blocks and the gate into one new block over the union (ascending)
-        uint64_t um = qmask;
-        for (int b : kept)
-            for (int q : open[b].qubits) um |= uint64_t(1) << q;
-        Block nb;
-        for (int q = 0; q < n_qubits; ++q)
-            if ((um >> q) & 1) nb.qubits.push_back(q);
-        nb.mat = identity(size_t(1) << nb.qubits.size());
-        nb.n_src = 1;
-        for (int b : kept) {
-            left_multiply(nb.mat, nb.qubits, open[b].mat, open[b].qubits);
-            nb.n_src += open[b].n_src;
-        }
-        left_multiply(nb.mat, nb.qubits, dense[gi].m, Q);
-        nb.created = stamp++;
-        // drop closed + kept from the open list
-        std::vector<char> drop(open.size(), 0);
-        for (int b : touching) drop[b] = 1;
-        std::vector<Block> rest;
-        rest.reserve(open.size() + 1);
-        for (size_t b = 0; b < open.size(); ++b)
-            if (!drop[b]) rest.push_back(std::move(open[b]));
-        rest.push_back(std::move(nb));
-        open.swap(rest);
-    }
-    std::sort(open.begin(), open.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
-    for (Block &b : open) emit(b);
-
-    // horizontal pass: move each block back over disjoint predecessors and merge where it fits
-    std::vector<Block> merged;
-    const int kScanBack = 64;
-    for (Block &b : emitted) {
-        uint64_t bm = 0;
-        for (int q : b.qubits) bm |= uint64_t(1) << q;
-        const int lim = std::max(max_k, (int)b.qubits.size());
-        int target = -1;
-        for (int p = (int)merged.size() - 1, steps = 0; p >= 0 && steps < kScanBack; --p, ++steps) {
-            uint64_t pm = 0;
-            for (int q : merged[p].qubits) pm |= uint64_t(1) << q;
-            if (__builtin_popcountll(pm | bm) <= lim) { target = p; break; }
-            if (pm & bm) break;   // cannot move past a block it shares a qubit with
-        }
-        if (target < 0) {
-            merged.push_back(std::move(b));
-            continue;
-        }
-        Block &t = merged[size_t(target)];
-        uint64_t um = bm;
-        for (int q : t.qubits) um |= uint64_t(1) << q;
-        Block nb;
-        for (int q = 0; q < n_qubits; ++q)
-            if ((um >> q) & 1) nb.qubits.push_back(q);
-        nb.mat = identity(size_t(1) << nb.qubits.size());
-        left_multiply(nb.mat, nb.qubits, t.mat, t.qubits);   // earlier block first
-        left_multiply(nb.mat, nb.qubits, b.mat, b.qubits);
-        nb.n_src = t.n_src + b.n_src;
-        nb.created = t.created;
-        t = std::move(nb);
-    }
-    try {
-        for (Block &b : merged) finish(b);
     } catch (const std::bad_alloc &) {
         delete f;
         set_error("sv_fuse_circuit: out of host memory");

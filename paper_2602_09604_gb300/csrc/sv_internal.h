@@ -11,6 +11,7 @@
 #include "../../include/sv_gb300.h"
 
 struct sv_fused;
+struct sv_mlp;
 
 namespace svg {
 
@@ -91,6 +92,12 @@ int device_sm_count(int device);
 // Tensor-core path (sv_tc.cu): host-side operand images and the launcher.
 int build_tc_operands(sv_fused *f);
 int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms);
+// Cost model (sv_mlp.cu): feature vector, batched prediction in microseconds, trust test.
+void mlp_features(int k, const int *targets_sorted, int path, int n, float *f);
+int mlp_predict_us(sv_mlp *m, const float *X, int rows, double *out_us);
+bool mlp_usable(const sv_mlp *m, double max_mape);
+int mlp_fallback_k(const sv_mlp *m);
+
 // Reads and clears the current device's error word written by kernels whose bounded waits timed
 // out (0 = none).  Synchronous.
 int read_device_errors(int *code);

