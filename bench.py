@@ -189,7 +189,17 @@ def bench_ours(args):
 
     n, gates = wl.circuit_30q_grid()
     prec = {"fp32": B.PREC_FP32, "tf32": B.PREC_TF32, "bf16x3": B.PREC_BF16X3}[args.precision]
-    fused = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k)
+    model = None
+    fusion = args.fusion
+    model_path = os.path.join(ROOT, "paper_2602_09604_gb300", "cost_model_gb300.bin")
+    if fusion == "learned":
+        if os.path.exists(model_path):
+            model = B.sv_mlp_load(model_path)
+        else:
+            fusion = "greedy"
+    mode = B.FUSE_LEARNED if fusion == "learned" else B.FUSE_GREEDY
+    fuse_kw = dict(max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k, mode=mode, model=model)
+    fused = B.sv_fuse_circuit(gates, n, **fuse_kw)
     n_fused = B.sv_fused_count(fused)
     infos = [B.sv_fused_get_info(fused, i) for i in range(n_fused)]
     stream = torch.cuda.Stream()
@@ -240,7 +250,7 @@ def bench_ours(args):
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f2 = B.sv_fuse_circuit(gates, n, max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k)
+        f2 = B.sv_fuse_circuit(gates, n, **fuse_kw)
         B.sv_init(st.h, 0)
         B.sv_apply_fused_gates(st.h, f2)
         smp = B.sv_sample(st.h, uniforms)
@@ -286,7 +296,8 @@ def bench_ours(args):
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_qubits": n, "max_k": args.max_k, "precision": args.precision,
-                   "tc_min_k": args.tc_min_k, "fusion": "greedy", "fused_gates": n_fused, "samples_per_step": N_SAMPLES,
+                   "tc_min_k": args.tc_min_k, "fusion": fusion, "fused_gates": n_fused,
+                   "fused_k_histogram": {str(k): sum(1 for i in infos if i["k"] == k) for k in range(1, 7)}, "samples_per_step": N_SAMPLES,
                    "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -311,6 +322,9 @@ def bench_ours(args):
                                 "sample": f"{args.cpu_gates} of the 845 gates (evenly spaced) applied once to the "
                                           f"2^30 complex128 state; s/circuit = mean s/gate ({per_gate:.3f}) x 845"}
     B.sv_fused_free(fused)
+    if model is not None:
+        line["cost_model"] = {k: v for k, v in B.sv_mlp_get_stats(model).items() if k in ("val_mape", "steps")}
+        B.sv_mlp_free(model)
     st.free()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -327,6 +341,7 @@ def main():
     ap.add_argument("--max-k", type=int, default=6)
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--tc-min-k", type=int, default=4)
+    ap.add_argument("--fusion", default="learned", choices=["learned", "greedy"])
     ap.add_argument("--no-plain-sweep", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-gates", type=int, default=12)

@@ -453,6 +453,10 @@ extern "C" int sv_mlp_train(sv_mlp *m, const float *X, const float *us, long lon
         stats->n_train = n_tr;
         stats->n_val = n_val;
         stats->steps = m->step;
+        stats->trained = m->trained;
+        stats->y_mean = m->y_mean;
+        stats->y_std = m->y_std;
+        stats->fallback_k = m->fallback_k;
     }
     return SV_OK;
 }
