@@ -81,6 +81,7 @@ typedef struct sv_state sv_state;   /* opaque; owns no state memory, only small 
 typedef struct sv_fused sv_fused;   /* opaque fused circuit (host matrices + lazily made device copies) */
 typedef struct sv_mlp sv_mlp;       /* opaque learned cost model */
 
+
 /* One input gate.  mat: 2^k x 2^k complex128 row-major interleaved (re, im), local bit j <->
  * targets[j].  Controls (if any) are folded into a dense (k + n_controls)-qubit matrix by the
  * fuser, so k + n_controls <= 6. */
@@ -241,6 +242,40 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * Eq. 1: |c_i|^2 is the probability of observing basis state i).  Grows a workspace on the
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched circuits (no counterpart in the paper's code, which runs one circuit at a time): many
+ * independent circuits of uneven size, each already fused (k <= 5, n <= 30), run from |0...0> in
+ * ONE persistent kernel launch.  CTAs take whole circuits from a device work queue, largest
+ * first; circuits of at most smem_max_n qubits are simulated in shared memory and stored once,
+ * larger ones in their global buffer.  The launch is captured once in a CUDA graph and replayed.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct sv_batch sv_batch;
+
+typedef struct sv_batch_opts {
+    int threads;        /* threads per CTA, multiple of 32 in [32, 1024] (default 256) */
+    int smem_max_n;     /* largest circuit kept in shared memory, 0..14 (default 13) */
+    int ctas;           /* persistent CTAs (default 2 x SM count) */
+    int use_graph;      /* nonzero: capture once, replay (default 1) */
+} sv_batch_opts;
+
+/* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
+ * aligned, in the given order.  0 if a size is outside 1..30. */
+SV_API size_t sv_batch_arena_bytes(const int *n_qubits, int count);
+/* Describe a batch over `circuits` (borrowed: they must outlive the batch) with states in the
+ * caller's device `arena` (>= sv_batch_arena_bytes, 256-byte aligned).  Uploads the fused
+ * matrices (cudaMalloc); work is enqueued on `cuda_stream`. */
+SV_API int sv_batch_create(const sv_fused *const *circuits, int count, void *arena, size_t arena_bytes, void *cuda_stream,
+                           sv_batch **out);
+SV_API void sv_batch_free(sv_batch *b);
+SV_API int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *opts);
+SV_API int sv_batch_get_opts(const sv_batch *b, sv_batch_opts *opts);
+/* Run every circuit from |0...0> into its state buffer: one persistent launch (asynchronous). */
+SV_API int sv_batch_run(sv_batch *b);
+/* The same work as one launch per fused gate, circuit after circuit (comparison baseline). */
+SV_API int sv_batch_run_loop(sv_batch *b);
+/* Byte offset of circuit i's state inside the arena. */
+SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes);
 
 /* SV_OK if no kernel on the current device has given up a bounded wait since the last call, else
  * SV_ETIMEOUT (the error is cleared by the call).  Synchronises the device. */

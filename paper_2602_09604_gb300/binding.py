@@ -57,6 +57,11 @@ class sv_mlp_stats(ctypes.Structure):
                 ("y_mean", ctypes.c_float), ("y_std", ctypes.c_float), ("fallback_k", ctypes.c_int)]
 
 
+class sv_batch_opts(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("smem_max_n", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
 class sv_timing(ctypes.Structure):
     _fields_ = [("us", ctypes.c_float), ("k", ctypes.c_int), ("path", ctypes.c_int),
                 ("target_mask", ctypes.c_uint64)]
@@ -86,6 +91,14 @@ def _load():
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_device_status": (I, []),
+        "sv_batch_arena_bytes": (ctypes.c_size_t, [ctypes.POINTER(ctypes.c_int), I]),
+        "sv_batch_create": (I, [ctypes.POINTER(P), I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "sv_batch_free": (None, [P]),
+        "sv_batch_set_opts": (I, [P, ctypes.POINTER(sv_batch_opts)]),
+        "sv_batch_get_opts": (I, [P, ctypes.POINTER(sv_batch_opts)]),
+        "sv_batch_run": (I, [P]),
+        "sv_batch_run_loop": (I, [P]),
+        "sv_batch_state_offset": (I, [P, I, ctypes.POINTER(ctypes.c_size_t)]),
         "sv_mlp_num_params": (I, []),
         "sv_mlp_create": (I, [ctypes.c_uint64, P, ctypes.POINTER(P)]),
         "sv_mlp_free": (None, [P]),
@@ -337,3 +350,46 @@ def sv_mlp_load(path: str, stream: int = 0):
     h = ctypes.c_void_p()
     _check(lib.sv_mlp_load(path.encode(), ctypes.c_void_p(stream), ctypes.byref(h)))
     return h
+
+
+# --------------------------------------------------------------------------------------- batched circuits
+def sv_batch_arena_bytes(ns) -> int:
+    a = (ctypes.c_int * len(ns))(*[int(x) for x in ns])
+    return int(lib.sv_batch_arena_bytes(a, len(ns)))
+
+
+def sv_batch_create(fused_list, arena_ptr: int, arena_bytes: int, stream: int = 0):
+    arr = (ctypes.c_void_p * len(fused_list))(*[f.value for f in fused_list])
+    h = ctypes.c_void_p()
+    _check(lib.sv_batch_create(arr, len(fused_list), ctypes.c_void_p(arena_ptr), arena_bytes,
+                               ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_batch_free(b) -> None:
+    lib.sv_batch_free(b)
+
+
+def sv_batch_set_opts(b, threads: int, smem_max_n: int, ctas: int, use_graph: bool = True) -> None:
+    o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)))
+    _check(lib.sv_batch_set_opts(b, ctypes.byref(o)))
+
+
+def sv_batch_get_opts(b) -> dict:
+    o = sv_batch_opts()
+    _check(lib.sv_batch_get_opts(b, ctypes.byref(o)))
+    return {f: getattr(o, f) for f, _ in sv_batch_opts._fields_}
+
+
+def sv_batch_run(b) -> None:
+    _check(lib.sv_batch_run(b))
+
+
+def sv_batch_run_loop(b) -> None:
+    _check(lib.sv_batch_run_loop(b))
+
+
+def sv_batch_state_offset(b, i: int) -> int:
+    o = ctypes.c_size_t()
+    _check(lib.sv_batch_state_offset(b, i, ctypes.byref(o)))
+    return int(o.value)
