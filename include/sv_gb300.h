@@ -245,7 +245,7 @@ SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, 
 
 /* ---------------------------------------------------------------------------------------------
  * Batched circuits (no counterpart in the paper's code, which runs one circuit at a time): many
- * independent circuits of uneven size, each already fused (k <= 5, n <= 30), run from |0...0> in
+ * independent circuits of uneven size, each already fused (k <= 4, n <= 24), run from |0...0> in
  * ONE persistent kernel launch.  CTAs take whole circuits from a device work queue, largest
  * first; circuits of at most smem_max_n qubits are simulated in shared memory and stored once,
  * larger ones in their global buffer.  The launch is captured once in a CUDA graph and replayed.
@@ -260,7 +260,7 @@ typedef struct sv_batch_opts {
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
- * aligned, in the given order.  0 if a size is outside 1..30. */
+ * aligned, in the given order.  0 if a size is outside 1..24. */
 SV_API size_t sv_batch_arena_bytes(const int *n_qubits, int count);
 /* Describe a batch over `circuits` (borrowed: they must outlive the batch) with states in the
  * caller's device `arena` (>= sv_batch_arena_bytes, 256-byte aligned).  Uploads the fused

@@ -1,6 +1,6 @@
 """Batched uneven circuits in one persistent launch, with a project-written autotuner.
 
-The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..5), CTA
+The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..4), CTA
 size, the largest circuit kept in shared memory, and the persistent grid -- by coordinate descent
 from a default, each candidate replayed from its captured CUDA graph and timed with CUDA events
 (median of repeats).  The winner is cached in a JSON file keyed by GPU name and a digest of the
@@ -84,7 +84,7 @@ def digest(circuits) -> str:
     return h.hexdigest()[:16]
 
 
-def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4, 5)):
+def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)):
     """Returns (best settings dict, trial log)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     key = f"{torch.cuda.get_device_name(0)}|{digest(circuits)}"

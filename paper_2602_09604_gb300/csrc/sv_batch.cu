@@ -22,7 +22,8 @@ using namespace svg;
 
 namespace {
 
-constexpr int kBatchMaxK = 5;
+constexpr int kBatchMaxK = 4;
+constexpr int kBatchMaxN = 24;   // states up to 2^25 floats: 32-bit offsets
 
 struct BGate {
     int k;
@@ -46,42 +47,61 @@ __device__ __forceinline__ unsigned long long bins0(unsigned long long x, int p)
 
 __device__ __forceinline__ long long boff(unsigned long long i) { return (long long)(((i >> 5) << 6) | (i & 31ull)); }
 
-// Apply one fused gate of K qubits to the state S (shared or global) of n qubits with all threads
-// of the CTA; U (float2, row-major 2^K x 2^K) is in shared memory.
+// Apply one fused gate of K qubits to the state S (shared or global) of n <= 24 qubits with all
+// threads of the CTA; U (float2, row-major 2^K x 2^K) is in shared memory.  Offsets are 32-bit
+// and recomputed for the stores, so a thread holds only its group's 2^(K+1) values.
 template <int K>
 __device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__restrict__ U)
 {
     constexpr int D = 1 << K;
-    const unsigned long long groups = 1ull << (n - K);
-    for (unsigned long long grp = threadIdx.x; grp < groups; grp += blockDim.x) {
-        unsigned long long base = grp;
+    unsigned bit[K];
 #pragma unroll
-        for (int b = 0; b < K; ++b) base = bins0(base, g.targets[b]);
+    for (int b = 0; b < K; ++b) bit[b] = 1u << g.targets[b];
+    const unsigned groups = 1u << (n - K);
+    for (unsigned grp = threadIdx.x; grp < groups; grp += blockDim.x) {
+        // the matrix pointer goes through an opaque move each iteration: otherwise the 4^K
+        // loop-invariant matrix loads are hoisted out of this loop into registers
+        const float2 *Ui;
+        {
+            unsigned long long v = reinterpret_cast<unsigned long long>(U);
+            asm volatile("mov.b64 %0, %0;" : "+l"(v));
+            Ui = reinterpret_cast<const float2 *>(v);
+        }
+        unsigned base = grp;
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const unsigned low = base & (bit[b] - 1u);
+            base = ((base - low) << 1) | low;
+        }
         float xr[D], xi[D];
-        long long off[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            unsigned long long i = base;
+            unsigned i = base;
 #pragma unroll
             for (int b = 0; b < K; ++b)
-                if ((j >> b) & 1) i |= 1ull << g.targets[b];
-            off[j] = boff(i);
-            xr[j] = S[off[j]];
-            xi[j] = S[off[j] + 32];
+                if ((j >> b) & 1) i |= bit[b];
+            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+            xr[j] = S[o];
+            xi[j] = S[o + 32];
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             float yr = 0.f, yi = 0.f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const float2 u = U[r * D + j];
+                const float2 u = Ui[r * D + j];
                 yr = fmaf(u.x, xr[j], yr);
                 yr = fmaf(u.y, -xi[j], yr);
                 yi = fmaf(u.x, xi[j], yi);
                 yi = fmaf(u.y, xr[j], yi);
             }
-            S[off[r]] = yr;
-            S[off[r] + 32] = yi;
+            unsigned i = base;
+#pragma unroll
+            for (int b = 0; b < K; ++b)
+                if ((r >> b) & 1) i |= bit[b];
+            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+            S[o] = yr;
+            S[o + 32] = yi;
         }
     }
 }
@@ -92,15 +112,14 @@ __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U)
     case 1: apply_in_cta<1>(S, n, g, U); break;
     case 2: apply_in_cta<2>(S, n, g, U); break;
     case 3: apply_in_cta<3>(S, n, g, U); break;
-    case 4: apply_in_cta<4>(S, n, g, U); break;
-    default: apply_in_cta<5>(S, n, g, U); break;
+    default: apply_in_cta<4>(S, n, g, U); break;
     }
 }
 
 // blocked-layout float count of an n-qubit state (at least one 64-float block)
 __device__ __host__ __forceinline__ long long state_floats(int n) { return n >= 5 ? (2ll << n) : 64ll; }
 
-__global__ void batch_kernel(float *__restrict__ arena, const BCirc *__restrict__ circ, int n_circ,
+__global__ void __launch_bounds__(512, 1) batch_kernel(float *__restrict__ arena, const BCirc *__restrict__ circ, int n_circ,
                              const BGate *__restrict__ gates, const float2 *__restrict__ mats,
                              unsigned *__restrict__ queue, int smem_max_n)
 {
@@ -193,7 +212,7 @@ extern "C" size_t sv_batch_arena_bytes(const int *n_qubits, int count)
     if (!n_qubits || count < 0) return 0;
     size_t t = 0;
     for (int i = 0; i < count; ++i) {
-        if (n_qubits[i] < 1 || n_qubits[i] > 30) return 0;
+        if (n_qubits[i] < 1 || n_qubits[i] > kBatchMaxN) return 0;
         t += (state_bytes(n_qubits[i]) + 255) & ~size_t(255);
     }
     return t;
@@ -213,7 +232,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
             if (g.k > kBatchMaxK) { set_error("sv_batch_create: circuit %d has a %d-qubit fused gate (batch kernel takes k <= %d)", i, g.k, kBatchMaxK); return SV_EINVAL; }
     }
     const size_t need = sv_batch_arena_bytes(ns.data(), count);
-    if (need == 0) { set_error("sv_batch_create: circuits must have 1..30 qubits"); return SV_EINVAL; }
+    if (need == 0) { set_error("sv_batch_create: circuits must have 1..%d qubits", kBatchMaxN); return SV_EINVAL; }
     if (arena_bytes < need) { set_error("sv_batch_create: arena of %zu bytes is smaller than the %zu needed", arena_bytes, need); return SV_ENOMEM; }
     if ((reinterpret_cast<uintptr_t>(arena) & 255u) != 0) { set_error("sv_batch_create: arena must be 256-byte aligned"); return SV_EINVAL; }
     sv_batch *b = new (std::nothrow) sv_batch();
