@@ -1,0 +1,113 @@
+"""33- and 34-qubit runs (64 GiB and 128 GiB complex64 states): the learned partition against fixed
+greedy fusion at every max size, with correctness from properties that hold at any size.
+
+* 33 qubits: 6x6 grid minus sites (5,3), (5,4), (5,5), 24 cycles.  The circuit followed by its
+  inverse must return |0...0> (unitarity).
+* 34 qubits: QFT of a seeded basis state; sampled amplitudes against the closed form
+  2^(-n/2) exp(2 pi i x y / 2^n), and the norm.
+With SV_REPORT_DIR set, the timings go to <SV_REPORT_DIR>/large_runs.json.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms
+from paper_2602_09604_gb300 import build as libbuild
+from paper_2602_09604_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2602_09604_gb300",
+                     "cost_model_gb300.bin")
+REPORT = {}
+
+
+@pytest.fixture(scope="module")
+def env():
+    libbuild.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2602_09604_gb300 import binding
+    from paper_2602_09604_gb300.state import DeviceState
+    m = binding.sv_mlp_load(MODEL)
+    yield binding, DeviceState, m
+    binding.sv_mlp_free(m)
+    out = os.environ.get("SV_REPORT_DIR")
+    if out and REPORT:
+        with open(os.path.join(out, "large_runs.json"), "w") as fh:
+            json.dump(REPORT, fh, indent=1)
+
+
+def variants(B, m):
+    v = [("learned_bf16x3", dict(max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)),
+         ("plain_fp32_k4", dict(max_k=4))]
+    v += [(f"greedy_k{k}_bf16x3", dict(max_k=k, precision=B.PREC_BF16X3, tc_min_k=4)) for k in range(2, 7)]
+    return v
+
+
+def time_variants(B, st, n, gates, m, init=0):
+    import time
+    res = {}
+    for label, kw in variants(B, m):
+        t0 = time.perf_counter()
+        f = B.sv_fuse_circuit(gates, n, **kw)
+        fuse_s = time.perf_counter() - t0
+        st.init(init)
+        rec = st.apply(f, timings=True)
+        res[label] = {"device_s": sum(r["us"] for r in rec) / 1e6, "fused_gates": len(rec), "fuse_host_s": fuse_s}
+        B.sv_fused_free(f)
+    return res
+
+
+def test_33q_grid_learned_vs_fixed(env):
+    B, DS, m = env
+    n, gates = wl.GRID_33.n, wl.random_grid_circuit(wl.GRID_33, 24, seed=4)
+    assert n == 33
+    st = DS(n)
+    res = time_variants(B, st, n, gates, m)
+    # correctness: learned forward then learned inverse returns |0...0>
+    kw = dict(max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)
+    f = B.sv_fuse_circuit(gates, n, **kw)
+    fi = B.sv_fuse_circuit(wl.inverse(gates), n, **kw)
+    st.init(0)
+    st.apply(f)
+    norm_fwd = st.norm()
+    st.apply(fi)
+    amp0 = complex(st.buf[0].item(), st.buf[32].item())
+    B.sv_fused_free(f)
+    B.sv_fused_free(fi)
+    st.free()
+    REPORT["grid33"] = {"gates": len(gates), "variants": res, "norm_after_circuit": norm_fwd,
+                        "p0_after_inverse": abs(amp0) ** 2}
+    assert abs(norm_fwd - 1) < 1e-4
+    assert abs(amp0) ** 2 >= 1 - 1e-4
+    best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
+    assert res["learned_bf16x3"]["device_s"] <= 1.1 * best_fixed
+    assert res["learned_bf16x3"]["device_s"] < res["plain_fp32_k4"]["device_s"]
+
+
+def test_34q_qft_learned_vs_fixed(env):
+    import torch
+    B, DS, m = env
+    n = 34
+    gates = wl.qft_circuit(n)
+    x = wl.qft_basis_index(n, seed=34)
+    st = DS(n)
+    res = time_variants(B, st, n, gates, m, init=x)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)
+    st.init(x)
+    st.apply(f)
+    B.sv_fused_free(f)
+    nrm = st.norm()
+    idx = np.random.default_rng(34).integers(0, 1 << n, size=1 << 16).astype(np.uint64)
+    o = torch.from_numpy(((idx >> np.uint64(5)) << np.uint64(6) | (idx & np.uint64(31))).astype(np.int64)).cuda()
+    got = st.buf[o].double().cpu().numpy() + 1j * st.buf[o + 32].double().cpu().numpy()
+    ref = closed_forms.qft_amplitudes(n, x, idx)
+    rel = float(np.max(np.abs(got - ref)) * 2.0 ** (n / 2))
+    st.free()
+    REPORT["qft34"] = {"gates": len(gates), "variants": res, "norm": nrm, "max_rel_amp_error": rel}
+    assert abs(nrm - 1) < 1e-4
+    assert rel < 1e-3
+    best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
+    assert res["learned_bf16x3"]["device_s"] <= 1.1 * best_fixed
