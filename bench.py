@@ -238,10 +238,8 @@ def bench_ours(args):
         if ws > 1:
             dist.barrier()
     elapsed_s = ev0.elapsed_time(ev1) / 1e3
-    if ws > 1:
-        t = torch.tensor([elapsed_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_s = float(t.item())
+    from paper_2602_09604_gb300.dist import max_over_ranks
+    elapsed_s = max_over_ranks(elapsed_s, device="cuda")   # the slowest rank defines the job time
     value = elapsed_s / (args.steps * ws)
 
     # ---- end to end through the C ABI with host buffers (host fusion included)
