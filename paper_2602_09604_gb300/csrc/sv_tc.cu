@@ -186,7 +186,10 @@ struct TcShape {
     static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
     static constexpr int TMEM_COLS = 2 * WG_COLS < 32 ? 32 : 2 * WG_COLS;   // two warpgroups
     static constexpr int KSTEP = MODE == kModeTF32 ? 8 : 16;           // K per instruction
-    static constexpr int MIN_BLOCKS = K == 6 ? 1 : (K == 5 ? 2 : 3);   // CTAs per SM the registers allow
+    // CTAs per SM the registers allow: the direct variant gains from more concurrent warpgroup
+    // pipelines; the staged one needs more registers (its shared-memory traffic) and spills if capped
+    static constexpr int MIN_BLOCKS_DIRECT = K == 6 ? 1 : (K == 5 ? 2 : 3);
+    static constexpr int MIN_BLOCKS_STAGED = K == 6 ? 1 : (K == 5 ? 1 : 2);
 };
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
@@ -254,7 +257,7 @@ __device__ __forceinline__ float4 xor_perm4(float4 v, unsigned sw)
 //      the warpgroup's A region (tcgen05.st);
 //   4. one thread per warpgroup issues the MMAs (A from tensor memory, B from shared memory).
 template <int K, int MODE, bool STAGED>
-__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN_BLOCKS_STAGED : TcShape<K, MODE>::MIN_BLOCKS_DIRECT) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
     using S = TcShape<K, MODE>;
     constexpr int D = S::D;
@@ -484,12 +487,26 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS) 
         if (wt < a.t.n_tiles) {
             const unsigned long long b0 = tile_block0(wt);
             const int ln = (int)opaque_u32((unsigned)lane);
+            // ordered batches of four shared loads then four global stores (volatile asm keeps
+            // the order), so at most 16 registers of copy data are live
 #pragma unroll
-            for (int i = 0; i < S::CPL; ++i) {
-                const int c = ln + 32 * i;
-                unsigned sw;
-                const float *src = schunk(c, sw);
-                *reinterpret_cast<float4 *>(gchunk(b0, c)) = xor_perm4(*reinterpret_cast<const float4 *>(src), sw);
+            for (int i0 = 0; i0 < S::CPL; i0 += 4) {
+                float4 v[4];
+                unsigned sw[4];
+#pragma unroll
+                for (int q = 0; q < 4 && i0 + q < S::CPL; ++q) {
+                    const float *src = schunk(ln + 32 * (i0 + q), sw[q]);
+                    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                 : "=f"(v[q].x), "=f"(v[q].y), "=f"(v[q].z), "=f"(v[q].w)
+                                 : "r"(smem_u32(src)));
+                }
+#pragma unroll
+                for (int q = 0; q < 4 && i0 + q < S::CPL; ++q) {
+                    const float4 w = xor_perm4(v[q], sw[q]);
+                    asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(gchunk(b0, ln + 32 * (i0 + q))), "f"(w.x),
+                                 "f"(w.y), "f"(w.z), "f"(w.w)
+                                 : "memory");
+                }
             }
         }
         __syncwarp();
@@ -668,7 +685,7 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
     const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
     const int by_smem = std::max(1, (227 * 1024) / (S::SMEM + 1024));
-    const int per_sm = std::min(S::MIN_BLOCKS, std::min(by_tmem, by_smem));
+    const int per_sm = std::min(staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT, std::min(by_tmem, by_smem));
     const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
     kern<<<(unsigned)grid, 2 * kTcThreads, S::SMEM, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
