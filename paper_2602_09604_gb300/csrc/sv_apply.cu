@@ -435,7 +435,7 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
     const int nb = n > 5 ? n - 5 : 0;
     const bool fixed = nb >= tile_f<K>();
     const int f = fixed ? tile_f<K>() : nb;   // (targets >= 5) <= K <= tile_f<K>(), and <= nb always
-    make_tile_map(g, n, f, &a.t);
+    SV_TRY(make_tile_map(g, n, f, &a.t));
     const bool gather = a.t.gather != 0;
     const size_t smem = size_t(kTileWarps) * (64u << f) * sizeof(float) + (K == 6 ? sizeof(float2) * 64 * 64 : 0);
     auto kern = fixed ? (gather ? apply_tile_kernel<K, true, true> : apply_tile_kernel<K, false, true>)
@@ -462,11 +462,17 @@ const LaunchFn kTile[7] = {nullptr, launch_tile<1>, launch_tile<2>, launch_tile<
 
 }  // namespace
 
-void make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
+int make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
 {
     std::memset(m, 0, sizeof(*m));
     const int K = g.k;
     const int nb = n > 5 ? n - 5 : 0;
+    int high = 0;
+    for (int b = 0; b < K; ++b) high += g.targets[b] >= 5;
+    if (f < 0 || f > kMaxTileF || f > nb || f < high || K < 1 || K > SV_MAX_K) {
+        set_error("tile map: tile of 2^%d blocks does not fit (n=%d, k=%d, %d high targets)", f, n, K, high);
+        return SV_EINVAL;
+    }
     uint64_t fm = 0;   // F = high target block bits + lowest free block bits
     for (int b = 0; b < K; ++b)
         if (g.targets[b] >= 5) fm |= 1ull << (g.targets[b] - 5);
@@ -502,7 +508,7 @@ void make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
     int lowt[5], L = 0;
     for (int b = 0; b < K; ++b)
         if (g.targets[b] < 5) lowt[L++] = g.targets[b];
-    int nont[6], nn = 0;
+    int nont[kMaxTileF], nn = 0;
     for (int r = 0; r < f; ++r) {
         bool is_t = false;
         for (int b = 0; b < K; ++b)
@@ -525,6 +531,7 @@ void make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
     m->lsh = 5 - L;
     m->lmask = (1 << L) - 1;
     m->n_tiles = 1ll << (nb - f);
+    return SV_OK;
 }
 
 int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, const void *dtc, cudaStream_t stream, int num_sms)

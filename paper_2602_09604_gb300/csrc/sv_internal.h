@@ -53,9 +53,11 @@ struct FusedGate {
 // tensor-core kernel).  A tile is 2^f blocks of 32 amplitudes: the blocks obtained by varying the
 // block bits in F = {target block bits} + {lowest non-target block bits}.  Inside a tile the
 // amplitude index has 5 + f bits (in-block position, then the F bits in ascending order).
+constexpr int kMaxTileF = 8;   // tiles of up to 2^8 blocks (64 KB)
+
 struct TileMap {
-    long long fblk[64];       // block offset of tile block phi (deposit of phi into the F bits)
-    int fpos[6];              // ascending block-bit positions of F
+    long long fblk[1 << kMaxTileF];   // block offset of tile block phi (deposit of phi into the F bits)
+    int fpos[kMaxTileF];              // ascending block-bit positions of F
     int loff[64];             // tile-local amplitude offset of local index j
     int ltpos[6];             // ascending tile-local target positions
     int f;                    // a tile is 2^f blocks
@@ -63,11 +65,12 @@ struct TileMap {
     int lmask;                // 2^(number of targets below 5) - 1
     int gather;               // F is not {0 .. f-1}
     long long n_tiles;        // 2^(n - 5 - f)
-    unsigned char swz[64];    // in-block position XOR of tile block phi (bank-conflict swizzle)
+    unsigned char swz[1 << kMaxTileF];   // in-block position XOR of tile block phi (bank-conflict swizzle)
     unsigned char gswz[32];   // the same XOR, indexed by (group >> lsh) & lmask
 };
-// Requires max(0, n - 5) >= f >= (number of targets >= 5).
-void make_tile_map(const FusedGate &g, int n, int f, TileMap *m);
+// Requires kMaxTileF >= f, max(0, n - 5) >= f >= (number of targets >= 5); returns SV_EINVAL
+// (and fills nothing usable) otherwise.
+int make_tile_map(const FusedGate &g, int n, int f, TileMap *m);
 
 // Tensor-core operand images of one fused gate (built on the host, uploaded once).
 struct TcOperands {

@@ -657,10 +657,10 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
 {
     using S = TcShape<K, MODE>;
     if (n < K + 5) { set_error("tensor-core path needs n >= k + 5 (n=%d, k=%d)", n, K); return SV_EINVAL; }
+    const bool staged = g.targets[0] < 5;   // targets ascending: some target inside the 32-amplitude block
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
-    const bool staged = g.targets[0] < 5;   // targets ascending: some target inside the 32-amplitude block
-    make_tile_map(g, n, K, &a.t);
+    SV_TRY(make_tile_map(g, n, K, &a.t));
     for (int b = 0; b < K; ++b) a.tpos[b] = g.targets[b];
     for (int j = 0; j < (1 << K); ++j) {
         unsigned long long o = 0;
