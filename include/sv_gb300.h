@@ -246,17 +246,24 @@ SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, 
 /* ---------------------------------------------------------------------------------------------
  * Batched circuits (no counterpart in the paper's code, which runs one circuit at a time): many
  * independent circuits of uneven size, each already fused (k <= 4, n <= 24), run from |0...0> in
- * ONE persistent kernel launch.  CTAs take whole circuits from a device work queue, largest
- * first; circuits of at most smem_max_n qubits are simulated in shared memory and stored once,
- * larger ones in their global buffer.  The launch is captured once in a CUDA graph and replayed.
+ * ONE persistent kernel launch.  CTAs take work items from a device queue in an order the host
+ * fixes: circuits of at most smem_max_n qubits are simulated whole in one CTA's shared memory and
+ * stored once; circuits of at least split_min_n qubits are cut into tiles of 2^tile_log2 groups
+ * per fused gate that any CTA may take (a tile waits, bounded, for the previous gate's tiles of
+ * its circuit); the rest run whole in one CTA on their global buffer.  If a wait gives up, the
+ * launch ends early and sv_device_status reports SV_ETIMEOUT.  The launch is captured once in a
+ * CUDA graph (per option set) and replayed.
  * ------------------------------------------------------------------------------------------- */
 typedef struct sv_batch sv_batch;
 
 typedef struct sv_batch_opts {
-    int threads;        /* threads per CTA, multiple of 32 in [32, 1024] (default 256) */
-    int smem_max_n;     /* largest circuit kept in shared memory, 0..14 (default 13) */
+    int threads;        /* threads per CTA, multiple of 32 in [32, 512] (default 256) */
+    int smem_max_n;     /* largest circuit kept in shared memory, 0..14 (default 12) */
     int ctas;           /* persistent CTAs (default 2 x SM count) */
     int use_graph;      /* nonzero: capture once, replay (default 1) */
+    int split_min_n;    /* circuits of at least this many qubits are split into tiles of each
+                           step that all CTAs share; 0 = never (default 15) */
+    int tile_log2;      /* groups per tile of a split circuit's step: 2^tile_log2, 5..16 (default 12) */
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
@@ -268,6 +275,8 @@ SV_API size_t sv_batch_arena_bytes(const int *n_qubits, int count);
 SV_API int sv_batch_create(const sv_fused *const *circuits, int count, void *arena, size_t arena_bytes, void *cuda_stream,
                            sv_batch **out);
 SV_API void sv_batch_free(sv_batch *b);
+/* Options take effect at the next sv_batch_run (which rebuilds the work list, synchronously, when
+ * smem_max_n, split_min_n or tile_log2 changed).  SV_EINVAL for a value out of range. */
 SV_API int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *opts);
 SV_API int sv_batch_get_opts(const sv_batch *b, sv_batch_opts *opts);
 /* Run every circuit from |0...0> into its state buffer: one persistent launch (asynchronous). */
@@ -276,6 +285,12 @@ SV_API int sv_batch_run(sv_batch *b);
 SV_API int sv_batch_run_loop(sv_batch *b);
 /* Byte offset of circuit i's state inside the arena. */
 SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes);
+/* Test hook for the bounded waits.  on != 0: from the next sv_batch_run the first split circuit's
+ * initialisation step counts one tile more than exists, so the tiles of its first gate wait on a
+ * counter that never fills; each gives up after about a second, the launch ends early without a
+ * fault, the states are left incomplete and sv_device_status returns SV_ETIMEOUT.  on = 0 undoes
+ * it.  No effect when no circuit is split. */
+SV_API int sv_batch_inject_stall(sv_batch *b, int on);
 
 /* SV_OK if no kernel on the current device has given up a bounded wait since the last call, else
  * SV_ETIMEOUT (the error is cleared by the call).  Synchronises the device. */

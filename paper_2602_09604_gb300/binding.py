@@ -59,7 +59,7 @@ class sv_mlp_stats(ctypes.Structure):
 
 class sv_batch_opts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("smem_max_n", ctypes.c_int), ("ctas", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("split_min_n", ctypes.c_int), ("tile_log2", ctypes.c_int)]
 
 
 class sv_timing(ctypes.Structure):
@@ -99,6 +99,7 @@ def _load():
         "sv_batch_run": (I, [P]),
         "sv_batch_run_loop": (I, [P]),
         "sv_batch_state_offset": (I, [P, I, ctypes.POINTER(ctypes.c_size_t)]),
+        "sv_batch_inject_stall": (I, [P, I]),
         "sv_mlp_num_params": (I, []),
         "sv_mlp_create": (I, [ctypes.c_uint64, P, ctypes.POINTER(P)]),
         "sv_mlp_free": (None, [P]),
@@ -370,8 +371,9 @@ def sv_batch_free(b) -> None:
     lib.sv_batch_free(b)
 
 
-def sv_batch_set_opts(b, threads: int, smem_max_n: int, ctas: int, use_graph: bool = True) -> None:
-    o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)))
+def sv_batch_set_opts(b, threads: int, smem_max_n: int, ctas: int, use_graph: bool = True,
+                      split_min_n: int = 15, tile_log2: int = 12) -> None:
+    o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)), split_min_n, tile_log2)
     _check(lib.sv_batch_set_opts(b, ctypes.byref(o)))
 
 
@@ -387,6 +389,10 @@ def sv_batch_run(b) -> None:
 
 def sv_batch_run_loop(b) -> None:
     _check(lib.sv_batch_run_loop(b))
+
+
+def sv_batch_inject_stall(b, on: bool) -> None:
+    _check(lib.sv_batch_inject_stall(b, int(bool(on))))
 
 
 def sv_batch_state_offset(b, i: int) -> int:

@@ -1,13 +1,17 @@
 // Batched simulation of many independent, uneven circuits in one persistent kernel launch.
 //
 // The paper simulates one circuit at a time (threads share the groups of one gate, section IV);
-// with many small circuits that leaves a GPU idle between launches.  Here every CTA takes whole
-// circuits from a device work queue (largest first) and runs all of a circuit's fused gates
-// itself, so one launch covers the batch:
-//   * circuits of at most `smem_max_n` qubits live in shared memory: the CTA writes |0...0> there,
-//     applies every fused gate with a __syncthreads between gates, and stores the state once;
-//   * larger circuits are initialised and updated in their global state buffer (L2-resident for
-//     the sizes this serves) by the same CTA, gate after gate.
+// with many small circuits that leaves a GPU idle between launches.  Here one launch covers the
+// batch: persistent CTAs take work items from a device queue, a list the host orders once:
+//   * a whole small circuit (at most `smem_max_n` qubits): the CTA writes |0...0> into shared
+//     memory, applies every fused gate with a __syncthreads between gates, stores the state once;
+//   * a whole mid-size circuit, by one CTA in the circuit's global buffer;
+//   * a tile of one step of a large circuit (at least `split_min_n` qubits): step 0 writes
+//     |0...0>, step s applies fused gate s-1 to 2^tile_log2 groups, in the global buffer.  A tile
+//     of step s waits (bounded spin) until every tile of step s-1 of its circuit has finished.
+//     Items are dequeued in list order and a dequeued item is held by a running CTA, so the tiles
+//     waited on were taken earlier and finish (by induction on list position): no deadlock.  The
+//     list interleaves the large circuits step by step, so a wait overlaps other circuits' work.
 // States use the library's blocked layout (32 reals then 32 imaginaries per 256-byte block).
 // The launch can be captured once in a CUDA graph and replayed.
 #include <algorithm>
@@ -36,7 +40,21 @@ struct BCirc {
     int n;
     int gate_begin;
     int gate_count;
-    int pad;
+    int done_off;            // large circuits: first completion counter (one per step)
+};
+
+// Work item kinds.  A circuit runs as one of them:
+//   kWhole  - circuit c entirely in one CTA's shared memory;
+//   kSingle - circuit c by one CTA in its global buffer, gate after gate;
+//   kTile   - tile `tile` of step `step` of circuit c, in its global buffer (step 0 writes |0...0>,
+//             step s >= 1 applies fused gate s-1 to 2^tile_log2 groups).
+enum : int { kWhole = 0, kSingle = 1, kTile = 2 };
+
+struct BItem {
+    int kind;
+    int c;
+    int step;
+    int tile;
 };
 
 __device__ __forceinline__ unsigned long long bins0(unsigned long long x, int p)
@@ -50,15 +68,15 @@ __device__ __forceinline__ long long boff(unsigned long long i) { return (long l
 // Apply one fused gate of K qubits to the state S (shared or global) of n <= 24 qubits with all
 // threads of the CTA; U (float2, row-major 2^K x 2^K) is in shared memory.  Offsets are 32-bit
 // and recomputed for the stores, so a thread holds only its group's 2^(K+1) values.
-template <int K>
-__device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__restrict__ U)
+template <int K, bool L2ONLY>
+__device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
 {
     constexpr int D = 1 << K;
     unsigned bit[K];
 #pragma unroll
     for (int b = 0; b < K; ++b) bit[b] = 1u << g.targets[b];
-    const unsigned groups = 1u << (n - K);
-    for (unsigned grp = threadIdx.x; grp < groups; grp += blockDim.x) {
+    (void)n;
+    for (unsigned grp = g_begin + threadIdx.x; grp < g_end; grp += blockDim.x) {
         // the matrix pointer goes through an opaque move each iteration: otherwise the 4^K
         // loop-invariant matrix loads are hoisted out of this loop into registers
         const float2 *Ui;
@@ -81,8 +99,13 @@ __device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__re
             for (int b = 0; b < K; ++b)
                 if ((j >> b) & 1) i |= bit[b];
             const unsigned o = ((i >> 5) << 6) | (i & 31u);
-            xr[j] = S[o];
-            xi[j] = S[o + 32];
+            if constexpr (L2ONLY) {   // other CTAs wrote these: read through L2, not a stale L1 line
+                xr[j] = __ldcg(S + o);
+                xi[j] = __ldcg(S + o + 32);
+            } else {
+                xr[j] = S[o];
+                xi[j] = S[o + 32];
+            }
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
@@ -106,54 +129,126 @@ __device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__re
     }
 }
 
-__device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U)
+template <bool L2ONLY>
+__device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U, unsigned g_begin, unsigned g_end)
 {
     switch (g.k) {
-    case 1: apply_in_cta<1>(S, n, g, U); break;
-    case 2: apply_in_cta<2>(S, n, g, U); break;
-    case 3: apply_in_cta<3>(S, n, g, U); break;
-    default: apply_in_cta<4>(S, n, g, U); break;
+    case 1: apply_in_cta<1, L2ONLY>(S, n, g, U, g_begin, g_end); break;
+    case 2: apply_in_cta<2, L2ONLY>(S, n, g, U, g_begin, g_end); break;
+    case 3: apply_in_cta<3, L2ONLY>(S, n, g, U, g_begin, g_end); break;
+    default: apply_in_cta<4, L2ONLY>(S, n, g, U, g_begin, g_end); break;
     }
 }
 
 // blocked-layout float count of an n-qubit state (at least one 64-float block)
 __device__ __host__ __forceinline__ long long state_floats(int n) { return n >= 5 ? (2ll << n) : 64ll; }
 
-__global__ void __launch_bounds__(512, 1) batch_kernel(float *__restrict__ arena, const BCirc *__restrict__ circ, int n_circ,
-                             const BGate *__restrict__ gates, const float2 *__restrict__ mats,
-                             unsigned *__restrict__ queue, int smem_max_n)
+constexpr long long kSpinLimit = 1ll << 22;   // bounded wait on a step counter (about a second)
+constexpr int kBatchErrCode = 0xBA7C;          // written to the device error word when a wait gives up
+
+struct BatchArgs {
+    float *arena;
+    const BCirc *circ;
+    const BItem *items;
+    int n_items;
+    const BGate *gates;
+    const float2 *mats;
+    int *sync;         // [0] queue head, [1] abort flag, [2 + i] completion counter i
+    const int *need;   // tiles of each counted step
+    int *err;          // library-wide device error word
+    int tile_log2;
+};
+
+__device__ __forceinline__ void stage_matrix(float2 *sU, const float2 *mats, const BGate &g)
+{
+    const int dd = 1 << (2 * g.k);
+    for (int i = threadIdx.x; i < dd; i += blockDim.x) sU[i] = mats[g.mat_off + i];
+}
+
+__device__ __forceinline__ void zero_floats(float *S, long long f0, long long f1)
+{
+    for (long long i = f0 / 4 + threadIdx.x; i < f1 / 4; i += blockDim.x)
+        reinterpret_cast<float4 *>(S)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float smem[];
     float2 *sU = reinterpret_cast<float2 *>(smem);                  // (1 << 2*kBatchMaxK) complex
     float *sS = smem + 2 * (1 << (2 * kBatchMaxK));                   // state of a shared-memory circuit
     __shared__ int cur;
+    __shared__ int ok;
     for (;;) {
-        if (threadIdx.x == 0) cur = (int)atomicAdd(queue, 1u);
+        if (threadIdx.x == 0) cur = (int)atomicAdd(reinterpret_cast<unsigned *>(A.sync), 1u);
         __syncthreads();
-        const int c = cur;
+        const int it = cur;
         __syncthreads();
-        if (c >= n_circ) break;
-        const BCirc C = circ[c];
-        const bool in_smem = C.n <= smem_max_n;
-        float *S = in_smem ? sS : arena + C.state_off;
+        if (it >= A.n_items) break;
+        const BItem W = A.items[it];
+        const BCirc C = A.circ[W.c];
+        float *G = A.arena + C.state_off;
         const long long nf = state_floats(C.n);
-        // |0...0>
-        for (long long i = threadIdx.x; i < nf / 4; i += blockDim.x)
-            reinterpret_cast<float4 *>(S)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        if (threadIdx.x == 0) S[0] = 1.f;
-        for (int gi = 0; gi < C.gate_count; ++gi) {
-            const BGate g = gates[C.gate_begin + gi];
-            const int dd = 1 << (2 * g.k);
-            for (int i = threadIdx.x; i < dd; i += blockDim.x) sU[i] = mats[g.mat_off + i];
-            __syncthreads();   // matrix staged; previous gate's writes visible
-            apply_gate_cta(S, C.n, g, sU);
+        if (W.kind != kTile) {
+            // whole circuit in one CTA: shared memory or the global buffer
+            float *S = W.kind == kWhole ? sS : G;
+            zero_floats(S, 0, nf);
             __syncthreads();
+            if (threadIdx.x == 0) S[0] = 1.f;
+            for (int gi = 0; gi < C.gate_count; ++gi) {
+                const BGate g = A.gates[C.gate_begin + gi];
+                stage_matrix(sU, A.mats, g);
+                __syncthreads();   // matrix staged; previous gate's writes visible
+                apply_gate_cta<false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                __syncthreads();
+            }
+            if (W.kind == kWhole) {
+                float4 *dst = reinterpret_cast<float4 *>(G);
+                for (long long i = threadIdx.x; i < nf / 4; i += blockDim.x) dst[i] = reinterpret_cast<const float4 *>(S)[i];
+                __syncthreads();
+            }
+            continue;
         }
-        if (in_smem) {
-            float4 *dst = reinterpret_cast<float4 *>(arena + C.state_off);
-            for (long long i = threadIdx.x; i < nf / 4; i += blockDim.x) dst[i] = reinterpret_cast<const float4 *>(S)[i];
+        // one tile of one step of a large circuit
+        int *done = A.sync + 2 + C.done_off;
+        if (threadIdx.x == 0) {
+            ok = 1;
+            if (W.step > 0) {
+                const volatile int *d = done + W.step - 1;
+                const int want = A.need[C.done_off + W.step - 1];
+                long long spin = 0;
+                while (*d < want) {
+                    if (*(volatile int *)(A.sync + 1) || ++spin > kSpinLimit) {
+                        ok = 0;
+                        atomicExch(A.sync + 1, 1);
+                        atomicCAS(A.err, 0, kBatchErrCode);
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                __threadfence();   // acquire: the previous step's writes before this step's reads
+            }
+        }
+        __syncthreads();
+        if (!ok) break;
+        if (W.step == 0) {
+            const long long span = 2ll << (A.tile_log2 + 3);   // floats zeroed per tile
+            const long long f0 = (long long)W.tile * span;
+            zero_floats(G, f0, f0 + span < nf ? f0 + span : nf);
             __syncthreads();
+            if (W.tile == 0 && threadIdx.x == 0) G[0] = 1.f;
+        } else {
+            const BGate g = A.gates[C.gate_begin + W.step - 1];
+            stage_matrix(sU, A.mats, g);
+            __syncthreads();
+            const unsigned groups = 1u << (C.n - g.k);
+            const unsigned g0 = (unsigned)W.tile << A.tile_log2;
+            const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
+            apply_gate_cta<true>(G, C.n, g, sU, g0, g1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();   // release: this tile's writes before the count
+            atomicAdd(done + W.step, 1);
         }
     }
 }
@@ -171,37 +266,127 @@ struct sv_batch {
     std::vector<int> n;              // per circuit (caller order)
     std::vector<long long> off;      // per circuit, floats (caller order)
     std::vector<const sv_fused *> fused;
+    std::vector<BCirc> hc;           // per circuit, largest first (device order)
+    std::vector<BGate> hg;
     BCirc *d_circ = nullptr;
     BGate *d_gates = nullptr;
     float2 *d_mats = nullptr;
-    unsigned *d_queue = nullptr;
-    int n_gates = 0;
+    // work list for the options it was built for
+    BItem *d_items = nullptr;
+    int *d_need = nullptr;
+    int *d_sync = nullptr;
+    int *d_err = nullptr;            // library's device error word (not owned)
+    int n_items = 0;
+    int n_counters = 0;
+    int list_cfg[3] = {-1, -1, -1};  // smem_max_n, split_min_n, tile_log2
+    bool stall = false;              // test hook: first split step counts one tile too many
+    bool list_stall = false;
     sv_batch_opts opts{};
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[3] = {0, 0, 0};
+    int graph_cfg[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
 
 size_t state_bytes(int n) { return sizeof(float) * (size_t)state_floats(n); }
 
+size_t smem_bytes(const sv_batch_opts &o)
+{
+    return sizeof(float) * 2 * (1 << (2 * kBatchMaxK)) + (o.smem_max_n > 0 ? state_bytes(o.smem_max_n) : 0);
+}
+
+// Work list: single-CTA circuits in global memory first (largest first: the rigid chains start
+// early), then the tiles of the split circuits step by step across circuits, then the circuits
+// held in shared memory (short; they fill the tail).
+int build_work_list(sv_batch *b)
+{
+    const int cfg[3] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2};
+    if (b->d_items && std::memcmp(cfg, b->list_cfg, sizeof(cfg)) == 0 && b->list_stall == b->stall) return SV_OK;
+    std::vector<BItem> items;
+    std::vector<int> need;
+    std::vector<BCirc> hc = b->hc;
+    std::vector<int> split;
+    for (int c = 0; c < (int)hc.size(); ++c) {
+        const int n = hc[(size_t)c].n;
+        hc[(size_t)c].done_off = 0;
+        if (n <= b->opts.smem_max_n) continue;
+        if (b->opts.split_min_n > 0 && n >= b->opts.split_min_n) {
+            hc[(size_t)c].done_off = (int)need.size();
+            const long long span = 2ll << (b->opts.tile_log2 + 3);
+            need.push_back((int)((state_floats(n) + span - 1) / span));
+            for (int gi = 0; gi < hc[(size_t)c].gate_count; ++gi) {
+                const BGate &g = b->hg[(size_t)(hc[(size_t)c].gate_begin + gi)];
+                const long long groups = 1ll << (n - g.k);
+                need.push_back((int)((groups + (1ll << b->opts.tile_log2) - 1) >> b->opts.tile_log2));
+            }
+            split.push_back(c);
+        } else {
+            items.push_back(BItem{kSingle, c, 0, 0});
+        }
+    }
+    for (int s = 0;; ++s) {
+        bool any = false;
+        for (int c : split) {
+            if (s > hc[(size_t)c].gate_count) continue;
+            any = true;
+            const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
+            for (int i = 0; i < t; ++i) items.push_back(BItem{kTile, c, s, i});
+        }
+        if (!any) break;
+    }
+    for (int c = 0; c < (int)hc.size(); ++c)
+        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0});
+    if (b->stall && !need.empty()) need[0] += 1;   // nothing completes the extra tile: its waiters give up
+    cudaFree(b->d_items);
+    cudaFree(b->d_need);
+    cudaFree(b->d_sync);
+    b->d_items = nullptr;
+    b->d_need = nullptr;
+    b->d_sync = nullptr;
+    b->n_items = (int)items.size();
+    b->n_counters = (int)need.size();
+    cudaError_t e = cudaMalloc(&b->d_items, sizeof(BItem) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_need, sizeof(int) * std::max<size_t>(need.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, sizeof(int) * (2 + need.size()));
+    if (e == cudaSuccess && !items.empty()) e = cudaMemcpy(b->d_items, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !need.empty()) e = cudaMemcpy(b->d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_circ, hc.data(), sizeof(BCirc) * hc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        b->list_cfg[0] = -1;
+        set_error("sv_batch: work list upload: %s", cudaGetErrorString(e));
+        return SV_ECUDA;
+    }
+    std::memcpy(b->list_cfg, cfg, sizeof(cfg));
+    b->list_stall = b->stall;
+    return SV_OK;
+}
+
 int launch_batch(sv_batch *b)
 {
-    const int smem_n = b->opts.smem_max_n;
-    const size_t smem = sizeof(float) * 2 * (1 << (2 * kBatchMaxK)) + (smem_n > 0 ? state_bytes(smem_n) : 0);
-    SV_CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
-    batch_kernel<<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem, b->stream>>>(b->arena, b->d_circ, b->count, b->d_gates,
-                                                                                       b->d_mats, b->d_queue, smem_n);
+    BatchArgs a;
+    a.arena = b->arena;
+    a.circ = b->d_circ;
+    a.items = b->d_items;
+    a.n_items = b->n_items;
+    a.gates = b->d_gates;
+    a.mats = b->d_mats;
+    a.sync = b->d_sync;
+    a.need = b->d_need;
+    a.err = b->d_err;
+    a.tile_log2 = b->opts.tile_log2;
+    SV_CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, sizeof(int) * (2 + (size_t)b->n_counters), b->stream));
+    batch_kernel<<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
 
-int check_opts(const sv_batch_opts &o, int num_sms)
+int check_opts(const sv_batch_opts &o)
 {
-    (void)num_sms;
-    if (o.threads < 32 || o.threads > 1024 || (o.threads & 31)) { set_error("sv_batch: threads must be a multiple of 32 in [32, 1024]"); return SV_EINVAL; }
+    if (o.threads < 32 || o.threads > 512 || (o.threads & 31)) { set_error("sv_batch: threads must be a multiple of 32 in [32, 512]"); return SV_EINVAL; }
     if (o.smem_max_n < 0 || o.smem_max_n > 14) { set_error("sv_batch: smem_max_n must be in [0, 14]"); return SV_EINVAL; }
     if (o.ctas < 1) { set_error("sv_batch: ctas must be >= 1"); return SV_EINVAL; }
+    if (o.split_min_n < 0 || o.split_min_n > kBatchMaxN) { set_error("sv_batch: split_min_n must be in [0, %d]", kBatchMaxN); return SV_EINVAL; }
+    if (o.tile_log2 < 5 || o.tile_log2 > 16) { set_error("sv_batch: tile_log2 must be in [5, 16]"); return SV_EINVAL; }
     return SV_OK;
 }
 
@@ -249,7 +434,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
         b->off.push_back((long long)(o / sizeof(float)));
         o += (state_bytes(ns[(size_t)i]) + 255) & ~size_t(255);
     }
-    // work queue order: largest circuits first (the long poles start early)
+    // device circuit order: largest first
     std::vector<int> order((size_t)count);
     for (int i = 0; i < count; ++i) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ns[(size_t)x] > ns[(size_t)y]; });
@@ -272,12 +457,9 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
         c.gate_count = (int)hg.size() - c.gate_begin;
         hc.push_back(c);
     }
-    b->n_gates = (int)hg.size();
     cudaError_t e = cudaMalloc(&b->d_circ, sizeof(BCirc) * hc.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_gates, sizeof(BGate) * std::max<size_t>(hg.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_mats, sizeof(float2) * std::max<size_t>(hm.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_circ, hc.data(), sizeof(BCirc) * hc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hg.empty()) e = cudaMemcpy(b->d_gates, hg.data(), sizeof(BGate) * hg.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hm.empty()) e = cudaMemcpy(b->d_mats, hm.data(), sizeof(float2) * hm.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -285,11 +467,20 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
         sv_batch_free(b);
         return SV_ECUDA;
     }
+    b->hc = std::move(hc);
+    b->hg = std::move(hg);
+    // the error word is allocated here, outside any later stream capture
+    if (device_err_word(&b->d_err) != SV_OK) {
+        sv_batch_free(b);
+        return SV_ECUDA;
+    }
     const int sms = device_sm_count(b->device);
     b->opts.threads = 256;
-    b->opts.smem_max_n = 13;
+    b->opts.smem_max_n = 12;
     b->opts.ctas = sms * 2;
     b->opts.use_graph = 1;
+    b->opts.split_min_n = 15;
+    b->opts.tile_log2 = 12;
     *out = b;
     return SV_OK;
 }
@@ -302,7 +493,9 @@ extern "C" void sv_batch_free(sv_batch *b)
     cudaFree(b->d_circ);
     cudaFree(b->d_gates);
     cudaFree(b->d_mats);
-    cudaFree(b->d_queue);
+    cudaFree(b->d_items);
+    cudaFree(b->d_need);
+    cudaFree(b->d_sync);
     delete b;
 }
 
@@ -310,9 +503,8 @@ extern "C" int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *o)
 {
     clear_error();
     if (!b || !o) { set_error("sv_batch_set_opts: NULL argument"); return SV_EINVAL; }
-    SV_TRY(check_opts(*o, device_sm_count(b->device)));
-    const size_t smem = sizeof(float) * 2 * (1 << (2 * kBatchMaxK)) + (o->smem_max_n > 0 ? state_bytes(o->smem_max_n) : 0);
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SV_TRY(check_opts(*o));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
     b->opts = *o;
     return SV_OK;
 }
@@ -329,19 +521,27 @@ extern "C" int sv_batch_run(sv_batch *b)
 {
     clear_error();
     if (!b) { set_error("sv_batch_run: NULL batch"); return SV_EINVAL; }
-    SV_TRY(check_opts(b->opts, 0));
-    {
-        const size_t smem = sizeof(float) * 2 * (1 << (2 * kBatchMaxK)) + (b->opts.smem_max_n > 0 ? state_bytes(b->opts.smem_max_n) : 0);
-        SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SV_TRY(check_opts(b->opts));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
+    const bool relist = !b->d_items || b->list_cfg[0] != b->opts.smem_max_n || b->list_cfg[1] != b->opts.split_min_n ||
+                        b->list_cfg[2] != b->opts.tile_log2 || b->list_stall != b->stall;
+    if (relist) {
+        // the captured graph holds the old list's pointers
+        SV_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        SV_TRY(build_work_list(b));
     }
     if (!b->opts.use_graph) return launch_batch(b);
-    const int cfg[3] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas};
+    const int cfg[5] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2};
     if (b->graph && std::memcmp(cfg, b->graph_cfg, sizeof(cfg)) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
     if (!b->graph) {
-        // capture the queue reset and the persistent launch once; replays reuse them
+        // capture the counter reset and the persistent launch once; replays reuse them
         cudaStream_t cs = nullptr;
         SV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaStream_t saved = b->stream;
@@ -382,6 +582,14 @@ extern "C" int sv_batch_run_loop(sv_batch *b)
         for (const FusedGate &g : b->fused[(size_t)i]->gates)
             SV_TRY(launch_fused_gate(p, n, g, nullptr, nullptr, b->stream, sms));
     }
+    return SV_OK;
+}
+
+extern "C" int sv_batch_inject_stall(sv_batch *b, int on)
+{
+    clear_error();
+    if (!b) { set_error("sv_batch_inject_stall: NULL batch"); return SV_EINVAL; }
+    b->stall = on != 0;
     return SV_OK;
 }
 

@@ -101,6 +101,9 @@ int mlp_predict_us(sv_mlp *m, const float *X, int rows, double *out_us);
 bool mlp_usable(const sv_mlp *m, double max_mape);
 int mlp_fallback_k(const sv_mlp *m);
 
+// The current device's error word (allocated on first use); kernels that give up a bounded wait
+// write a nonzero code there.
+int device_err_word(int **out);
 // Reads and clears the current device's error word written by kernels whose bounded waits timed
 // out (0 = none).  Synchronous.
 int read_device_errors(int *code);

@@ -638,6 +638,8 @@ std::vector<unsigned char> make_b_image(const FusedGate &g, int mode)
 int *g_err_word[64] = {};
 std::mutex g_tc_mu;
 
+}  // namespace
+
 int device_err_word(int **out)
 {
     int dev = 0;
@@ -651,6 +653,8 @@ int device_err_word(int **out)
     *out = g_err_word[dev];
     return SV_OK;
 }
+
+namespace {
 
 template <int K, int MODE>
 int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)

@@ -1,6 +1,8 @@
 """Batched uneven circuits in one persistent (graph-captured) launch: every circuit's state equals
-the circuit run alone (and the oracle for the smaller ones), in every shared-memory tier; graph
-replays are deterministic; the per-circuit launch loop gives the same states."""
+the oracle in every item kind (shared-memory circuits, single-CTA global circuits, circuits split
+into tiles that all CTAs share, with tiles from 32 to 4096 groups and from 1 to many CTAs); graph
+replays are deterministic; the per-circuit launch loop gives the same states; a wait that cannot
+be satisfied gives up and is reported without a fault."""
 import numpy as np
 import pytest
 
@@ -26,17 +28,21 @@ def test_batch_matches_oracle_every_tier(env):
     rng = np.random.default_rng(9)
     circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [5, 16, 9, 3, 14, 12, 7, 15, 10, 13, 1, 11]]
     refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
+    # (threads, smem_max_n, ctas, split_min_n, tile_log2)
+    configs = [(128, 0, 7, 0, 12), (512, 12, 7, 0, 12), (256, 14, 7, 0, 12),
+               (256, 9, 7, 6, 5), (128, 0, 1, 1, 7), (512, 12, 300, 13, 12), (256, 10, 19, 11, 8)]
     for max_k in (2, 3, 4):
         b = batch.Batch(circuits, max_k)
-        for smem_n in (0, 12, 14):
-            for threads in (128, 512):
-                b.set(threads, smem_n, 7)
-                b.arena.fill_(float("nan"))
-                b.run()
-                for i, ref in enumerate(refs):
-                    got = b.state(i)
-                    assert oracle.fidelity(ref, got) >= 1 - 1e-6, (max_k, smem_n, i)
-                    assert oracle.l2_error(ref, got) <= 1e-4
+        for threads, smem_n, ctas, split_n, tl in configs:
+            b.set(threads, smem_n, ctas, True, split_n, tl)
+            b.arena.fill_(float("nan"))
+            b.run()
+            B.sv_device_status()
+            for i, ref in enumerate(refs):
+                got = b.state(i)
+                cfg = (max_k, threads, smem_n, ctas, split_n, tl, i)
+                assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
+                assert oracle.l2_error(ref, got) <= 1e-4, cfg
         b.free()
 
 
@@ -62,6 +68,54 @@ def test_graph_replay_is_deterministic_and_loop_agrees(env):
     b.free()
 
 
+def test_split_tiles_without_graph_and_reuse(env):
+    """Many split circuits interleaved step by step, launched directly (no graph), twice."""
+    B, batch = env
+    circuits = wl.hea_batch(count=30, n_lo=12, n_hi=18, layers=3, seed=11)
+    b = batch.Batch(circuits, 3)
+    b.set(256, 0, 152, False, 12, 10)
+    b.run()
+    first = b.arena.clone()
+    b.set(512, 0, 40, False, 0, 10)       # same circuits, no split: one CTA per circuit
+    b.arena.fill_(float("nan"))
+    b.run()
+    B.sv_device_status()
+    for i in range(len(circuits)):
+        off = B.sv_batch_state_offset(b.h, i) // 4
+        nf = max(2 << circuits[i][0], 64)
+        d = (first[off:off + nf] - b.arena[off:off + nf]).abs().max().item()
+        assert d <= 1e-5, (i, d)
+    for i in (0, 7, 29):
+        n, g = circuits[i]
+        assert oracle.fidelity(oracle.run_circuit(n, g, 0), b.state(i)) >= 1 - 1e-6
+    b.free()
+
+
+def test_stalled_wait_gives_up_and_is_reported(env):
+    """A step counter that can never fill: every wait on it gives up after its bound, the launch
+    ends without a fault, sv_device_status reports SV_ETIMEOUT, and the batch runs correctly next."""
+    B, batch = env
+    import torch
+    rng = np.random.default_rng(2)
+    circuits = [(16, wl.hea_circuit(16, 2, rng)), (10, wl.hea_circuit(10, 2, rng))]
+    b = batch.Batch(circuits, 3)
+    b.set(256, 12, 8, True, 15, 10)
+    B.sv_batch_inject_stall(b.h, True)
+    b.run()
+    torch.cuda.synchronize()
+    with pytest.raises(B.SvError) as e:
+        B.sv_device_status()
+    assert e.value.code == B.SV_ETIMEOUT
+    B.sv_device_status()                  # the error word was cleared by the read
+    B.sv_batch_inject_stall(b.h, False)
+    b.arena.fill_(float("nan"))
+    b.run()
+    B.sv_device_status()
+    for i, (n, g) in enumerate(circuits):
+        assert oracle.fidelity(oracle.run_circuit(n, g, 0), b.state(i)) >= 1 - 1e-6
+    b.free()
+
+
 def test_batch_rejects_bad_input(env):
     B, batch = env
     import torch
@@ -74,6 +128,14 @@ def test_batch_rejects_bad_input(env):
     with pytest.raises(B.SvError) as e:
         B.sv_batch_create([f2], buf.data_ptr(), 64)                   # arena too small
     assert e.value.code == B.SV_ENOMEM
+    h = B.sv_batch_create([f2], buf.data_ptr(), buf.numel() * 4)
+    for bad in (dict(threads=1024), dict(split_min_n=25), dict(tile_log2=4), dict(tile_log2=17), dict(smem_max_n=15)):
+        kw = dict(threads=256, smem_max_n=12, ctas=8, use_graph=True, split_min_n=15, tile_log2=12)
+        kw.update(bad)
+        with pytest.raises(B.SvError) as e:
+            B.sv_batch_set_opts(h, **kw)
+        assert e.value.code == B.SV_EINVAL, bad
+    B.sv_batch_free(h)
     B.sv_fused_free(f6)
     B.sv_fused_free(f2)
 
