@@ -180,7 +180,10 @@ struct TcShape {
     static constexpr int B_BYTES = NIMG * B_IMG;
     static constexpr int LBO_B = (KD / 8) * 128;                       // next 16-byte K chunk
     static constexpr int WTILE_FLOATS = 64 << K;                       // one warp tile: 2^k blocks
-    static constexpr int SMEM = B_BYTES + 8 * WTILE_FLOATS * 4 + 256;
+    // shared memory: B image(s), the eight warp tiles (staged variant only), barriers and status
+    static constexpr int WBUF_BYTES_STAGED = 8 * WTILE_FLOATS * 4;
+    static constexpr int SMEM_STAGED = B_BYTES + WBUF_BYTES_STAGED + 256;
+    static constexpr int SMEM_DIRECT = B_BYTES + 256;   // the rest of the SM's 256 KB stays L1 cache
     static constexpr int CPL = (16 << K) / 32;                         // 16-byte chunks per lane
     static constexpr int A_COLS = KD * ESZ / 4;                        // TMEM columns of one A image
     static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
@@ -239,12 +242,14 @@ __device__ __forceinline__ float4 xor_perm4(float4 v, unsigned sw)
 // Two warpgroups per CTA, each an independent pipeline over every other MMA tile of the CTA,
 // sharing the B operand in shared memory.
 //
-// DIRECT variant (no target below qubit 5): row m of MMA tile t is group 128 t + m; a warp's 32
-// groups are the 32 positions of one block, so each lane loads its group straight into registers
-// (the next tile's loads are issued before the current tile's epilogue) and stores its outputs
-// straight back -- every warp access is a whole 128-byte line.
+// DIRECT variant (at most two targets below qubit 5): row m of MMA tile t is group 128 t + m and
+// each lane loads its group straight into registers (the next tile's loads are issued before the
+// current tile's epilogue) and stores its outputs straight back.  With no low target a warp's 32
+// groups are the 32 positions of one block, so every warp access is a whole 128-byte line; with
+// one or two, an access spans two or four lines whose other parts the neighbouring amplitudes'
+// accesses take (from L1 for loads; merged in L2 for stores).
 //
-// STAGED variant (some target below qubit 5): an MMA tile is four warp tiles; a warp tile is the
+// STAGED variant (three or more targets below qubit 5): an MMA tile is four warp tiles; a warp tile is the
 // 2^k blocks holding 32 groups (the tile geometry of the CUDA-core tile kernel with f = k), so
 // global memory is still read and written in whole 128-byte lines.
 // Per warp and tile:
@@ -267,8 +272,8 @@ __global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN
     const int wg = tid >> 7;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    float *wbuf = reinterpret_cast<float *>(smem + S::B_BYTES) + warp * S::WTILE_FLOATS;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 8 * S::WTILE_FLOATS * 4);
+    float *wbuf = reinterpret_cast<float *>(smem + S::B_BYTES) + warp * S::WTILE_FLOATS;   // staged only
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + (STAGED ? S::WBUF_BYTES_STAGED : 0));
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
     volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
     const uint32_t bar_b = smem_u32(&bars[0]);
@@ -661,7 +666,13 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
 {
     using S = TcShape<K, MODE>;
     if (n < K + 5) { set_error("tensor-core path needs n >= k + 5 (n=%d, k=%d)", n, K); return SV_EINVAL; }
-    const bool staged = g.targets[0] < 5;   // targets ascending: some target inside the 32-amplitude block
+    // Targets below qubit 5 lie inside a 32-amplitude block.  With at most two of them the direct
+    // variant still wins: a warp's accesses for one amplitude span at most four lines and the
+    // complementary parts come from L1 (measured at n = 30: k = 6 5.3-5.8 vs 4.3-4.4 TB/s staged,
+    // k = 5 6.6 vs 5.0-5.2).  From three on, staging through shared memory wins.
+    int nlow = 0;
+    for (int b = 0; b < K; ++b) nlow += g.targets[b] < 5;
+    const bool staged = nlow >= 3;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
     SV_TRY(make_tile_map(g, n, K, &a.t));
@@ -678,20 +689,21 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
     auto kern = staged ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
+    const int smem = staged ? S::SMEM_STAGED : S::SMEM_DIRECT;
     static bool attr_set[2] = {false, false};
     {
         std::lock_guard<std::mutex> lk(g_tc_mu);
         if (!attr_set[staged]) {
-            SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+            SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             attr_set[staged] = true;
         }
     }
     // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
     const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
-    const int by_smem = std::max(1, (227 * 1024) / (S::SMEM + 1024));
+    const int by_smem = std::max(1, (227 * 1024) / (smem + 1024));
     const int per_sm = std::min(staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT, std::min(by_tmem, by_smem));
     const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
-    kern<<<(unsigned)grid, 2 * kTcThreads, S::SMEM, stream>>>(sv, a);
+    kern<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
