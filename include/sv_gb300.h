@@ -243,6 +243,18 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
 
+/* Expectation values of Pauli strings (Section IV: the ExpectationValue routine runs the
+ * ApplyGate group loop and reduces instead of storing).  String p is
+ *     P_p = tensor product over qubits q of sigma_q,
+ *     sigma_q = X if bit q is set in x_masks[p] only, Z if in z_masks[p] only, Y if in both, else I,
+ * and out[p] (host array of count doubles) = <psi|P_p|psi>, real because P_p is Hermitian; the
+ * state is not normalised first (divide by sv_norm for a state that is not unit-norm).  Each
+ * amplitude's term is formed in fp32 and accumulated in float-float per thread, fp64 across
+ * threads, in a fixed order (deterministic).  Strings sharing an x mask share read passes, up to 8
+ * strings per pass over the 8 * 2^n bytes.  SV_EINVAL if a mask has a bit >= n.  Grows a small
+ * workspace on the state's device when count exceeds the previous maximum.  Synchronises. */
+SV_API int sv_expval_pauli(const sv_state *st, const uint64_t *x_masks, const uint64_t *z_masks, int count, double *out);
+
 /* ---------------------------------------------------------------------------------------------
  * Batched circuits (no counterpart in the paper's code, which runs one circuit at a time): many
  * independent circuits of uneven size, each already fused (k <= 4, n <= 24), run from |0...0> in

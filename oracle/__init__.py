@@ -10,6 +10,9 @@ Every function here follows the plain definition of the state-vector method (pap
 * ``norm`` -- sum of |c_i|^2 (condition under Eq. 1) in fp64.
 * ``sample`` -- inverse-CDF lookup of given uniforms in the |c_i|^2 distribution (Eq. 1: |c_i|^2
   is the probability of observing basis state i).
+* ``expval_pauli`` -- <psi|P|psi> for a Pauli string P (the ExpectationValue routine of
+  section IV, read as an expectation value): each single-qubit Pauli factor applied to a copy of
+  psi with ``apply_gate`` (Eq. 3), then the fp64 inner product with psi.
 * ``fidelity`` / ``l2_error`` -- the acceptance metrics, fp64.
 
 Conventions: amplitude index bit q <-> qubit q (qubit 0 is the least-significant bit); a gate's
@@ -131,6 +134,30 @@ def sample(psi: np.ndarray, uniforms: np.ndarray) -> np.ndarray:
                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
     assert rc == 0
     return out
+
+
+PAULI = {
+    "I": np.eye(2, dtype=np.complex128),
+    "X": np.array([[0, 1], [1, 0]], dtype=np.complex128),
+    "Y": np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+    "Z": np.array([[1, 0], [0, -1]], dtype=np.complex128),
+}
+
+
+class _OneQubit:
+    def __init__(self, q, m):
+        self.targets = (int(q),)
+        self.controls = ()
+        self.matrix = m
+
+
+def expval_pauli(psi: np.ndarray, n: int, terms, threads: int = 1) -> complex:
+    """<psi|P|psi> for P = the tensor product of the single-qubit Paulis in ``terms``
+    ({qubit: 'X' | 'Y' | 'Z' | 'I'}; identity on every other qubit), complex128, not normalised."""
+    phi = np.array(psi, dtype=np.complex128, copy=True)
+    for q, s in dict(terms).items():
+        apply_gate(phi, n, _OneQubit(q, PAULI[str(s).upper()]), threads)
+    return complex(np.vdot(np.asarray(psi, dtype=np.complex128), phi))
 
 
 def fidelity(psi_ref: np.ndarray, psi: np.ndarray) -> float:

@@ -91,6 +91,8 @@ def _load():
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_device_status": (I, []),
+        "sv_expval_pauli": (I, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), I,
+                                ctypes.POINTER(ctypes.c_double)]),
         "sv_batch_arena_bytes": (ctypes.c_size_t, [ctypes.POINTER(ctypes.c_int), I]),
         "sv_batch_create": (I, [ctypes.POINTER(P), I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
         "sv_batch_free": (None, [P]),
@@ -237,6 +239,33 @@ def sv_norm(h) -> float:
     out = ctypes.c_double()
     _check(lib.sv_norm(h, ctypes.byref(out)))
     return out.value
+
+
+def pauli_masks(terms) -> tuple[int, int]:
+    """(x_mask, z_mask) of a Pauli string given as {qubit: 'X' | 'Y' | 'Z' | 'I'}."""
+    x = z = 0
+    for q, s in dict(terms).items():
+        s = str(s).upper()
+        if s not in ("I", "X", "Y", "Z"):
+            raise ValueError(f"unknown Pauli {s!r} on qubit {q}")
+        if s in ("X", "Y"):
+            x |= 1 << int(q)
+        if s in ("Z", "Y"):
+            z |= 1 << int(q)
+    return x, z
+
+
+def sv_expval_pauli(h, x_masks, z_masks) -> np.ndarray:
+    """<psi|P|psi> for each Pauli string (x_masks[i], z_masks[i]); see pauli_masks."""
+    xs = np.ascontiguousarray(np.asarray(x_masks, dtype=np.uint64).reshape(-1))
+    zs = np.ascontiguousarray(np.asarray(z_masks, dtype=np.uint64).reshape(-1))
+    if xs.size != zs.size:
+        raise SvError(SV_EINVAL, "x_masks and z_masks differ in length")
+    out = np.zeros(xs.size, dtype=np.float64)
+    _check(lib.sv_expval_pauli(h, xs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                               zs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), xs.size,
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 def sv_sample(h, uniforms) -> np.ndarray:

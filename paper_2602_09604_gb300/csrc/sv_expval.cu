@@ -1,0 +1,254 @@
+// Expectation values of Pauli strings, <psi|P|psi>, as a read-only reduction over the state.
+//
+// Section IV runs ExpectationValue with the same group loop as ApplyGate but reduces the result
+// instead of storing it back.  For a Pauli string the "matrix-vector product" of a group is a
+// signed, phased permutation, so the reduction needs no matrix at all.  Write the string as two
+// bit masks over the qubits: x (X or Y on that qubit) and z (Z or Y).  With Y = i X Z,
+//     P |j> = i^popc(x & z) (-1)^popc(j & z) |j ^ x>,
+//     <psi|P|psi> = i^popc(x & z) * S,   S = sum_j (-1)^popc(j & z) conj(c_(j^x)) c_j.
+// P is Hermitian, so the value is real: Re S, -Im S, -Re S or Im S for popc(x & z) = 0, 1, 2, 3
+// (mod 4); each string accumulates only the component it needs.
+//
+// Strings with the same x read the same pairs of amplitudes, so up to kEvMaxStrings of them are
+// evaluated in one pass: each amplitude is read once, its term conj(c_(j^x)) c_j is formed once in
+// fp32, and every string adds it with its own sign into a float-float accumulator (two-sum); the
+// per-thread results are combined in fp64, per CTA and then in a fixed order by the last CTA.
+//
+// Work unit = one block (x has no bit >= 5) or one pair of blocks b, b ^ (x >> 5) (otherwise);
+// a warp reads each block's 32 real and 32 imaginary parts with coalesced loads, and the partner
+// amplitude j ^ x inside the paired block comes from lane (lane ^ (x & 31)) through a shuffle.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace svg {
+namespace {
+
+constexpr int kEvThreads = 256;
+constexpr int kEvMaxStrings = 8;
+
+struct EvArgs {
+    long long n_units;        // blocks, or block pairs
+    unsigned long long xb;    // x >> 5
+    int xl;                   // x & 31
+    int pair_bit;             // bit of the block index inserted as 0 to enumerate pairs; -1: no pairing
+    unsigned long long zb[kEvMaxStrings];
+    unsigned zl[kEvMaxStrings];
+    int comp[kEvMaxStrings];  // 0: accumulate the real part of the term, 1: the imaginary part
+    int m;                    // strings in this pass (<= the kernel's M; the rest are padding)
+};
+
+struct FF2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add(FF2 &a, float x)
+{
+    const float s = a.hi + x;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (x - bp);
+    a.hi = s;
+    a.lo += e;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ins_zero(unsigned long long v, int p)
+{
+    const unsigned long long low = v & ((1ull << p) - 1ull);
+    return ((v >> p) << (p + 1)) | low;
+}
+
+// the terms of the amplitudes of block `blk` (this lane's position) with partner values (pr, pi)
+template <int M>
+__device__ __forceinline__ void add_terms(FF2 (&acc)[M], const EvArgs &a, unsigned long long blk, unsigned lane, float ur, float ui,
+                                          float pr, float pi)
+{
+    // conj(partner) * own
+    const float tr = fmaf(pr, ur, pi * ui);
+    const float ti = fmaf(pr, ui, -(pi * ur));
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        const int par = (__popcll(blk & a.zb[p]) + __popc(lane & a.zl[p])) & 1;
+        const float t = a.comp[p] ? ti : tr;
+        ff_add(acc[p], par ? -t : t);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restrict__ sv, const __grid_constant__ EvArgs a,
+                                                           double *__restrict__ partials, unsigned *__restrict__ counter,
+                                                           double *__restrict__ result)
+{
+    FF2 acc[M];
+#pragma unroll
+    for (int p = 0; p < M; ++p) acc[p] = FF2{0.f, 0.f};
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned plane = lane ^ (unsigned)a.xl;
+    const long long wstride = (long long)gridDim.x * (kEvThreads / 32);
+    for (long long u = (long long)blockIdx.x * (kEvThreads / 32) + (threadIdx.x >> 5); u < a.n_units; u += wstride) {
+        if (a.pair_bit < 0) {
+            const unsigned long long b = (unsigned long long)u;
+            const float ur = __ldcs(sv + b * 64 + lane);
+            const float ui = __ldcs(sv + b * 64 + 32 + lane);
+            const float pr = __shfl_sync(0xffffffffu, ur, plane);
+            const float pi = __shfl_sync(0xffffffffu, ui, plane);
+            add_terms<M>(acc, a, b, lane, ur, ui, pr, pi);
+        } else {
+            const unsigned long long b = ins_zero((unsigned long long)u, a.pair_bit);
+            const unsigned long long b2 = b ^ a.xb;
+            const float ur = __ldcs(sv + b * 64 + lane);
+            const float ui = __ldcs(sv + b * 64 + 32 + lane);
+            const float vr = __ldcs(sv + b2 * 64 + lane);
+            const float vi = __ldcs(sv + b2 * 64 + 32 + lane);
+            const float vpr = __shfl_sync(0xffffffffu, vr, plane);
+            const float vpi = __shfl_sync(0xffffffffu, vi, plane);
+            const float upr = __shfl_sync(0xffffffffu, ur, plane);
+            const float upi = __shfl_sync(0xffffffffu, ui, plane);
+            add_terms<M>(acc, a, b, lane, ur, ui, vpr, vpi);    // j in block b, partner in b2
+            add_terms<M>(acc, a, b2, lane, vr, vi, upr, upi);   // j in block b2, partner in b
+        }
+    }
+    __shared__ double ws[kEvThreads / 32][M];
+    __shared__ bool last;
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+        const double v = warp_sum((double)acc[p].hi + (double)acc[p].lo);
+        if (lane == 0) ws[threadIdx.x >> 5][p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        double s = 0.0;
+        for (int w = 0; w < kEvThreads / 32; ++w) s += ws[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * M + threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(counter, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && (int)threadIdx.x < a.m) {
+        __threadfence();
+        const volatile double *pp = partials;
+        double s = 0.0;
+        for (unsigned i = 0; i < gridDim.x; ++i) s += pp[(size_t)i * M + threadIdx.x];   // fixed order
+        result[threadIdx.x] = s;
+    }
+    if (last && threadIdx.x == 0) *counter = 0u;   // ready for the next launch
+}
+
+template <int M>
+int launch_ev(const float *sv, const EvArgs &a, double *partials, unsigned *counter, double *result, int grid, cudaStream_t s)
+{
+    expval_kernel<M><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
+int highest_bit(unsigned long long v)
+{
+    int h = -1;
+    while (v) {
+        ++h;
+        v >>= 1;
+    }
+    return h;
+}
+
+}  // namespace
+}  // namespace svg
+
+using namespace svg;
+
+extern "C" int sv_expval_pauli(const sv_state *st_c, const uint64_t *x_masks, const uint64_t *z_masks, int count, double *out)
+{
+    clear_error();
+    sv_state *st = const_cast<sv_state *>(st_c);
+    if (!st || count < 0 || (count > 0 && (!x_masks || !z_masks || !out))) { set_error("sv_expval_pauli: bad argument"); return SV_EINVAL; }
+    if (count == 0) return SV_OK;
+    const int n = st->n;
+    const uint64_t valid = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+    for (int i = 0; i < count; ++i)
+        if ((x_masks[i] | z_masks[i]) & ~valid) {
+            set_error("sv_expval_pauli: string %d acts on a qubit >= n = %d", i, n);
+            return SV_EINVAL;
+        }
+    // workspace: per-CTA partials for one launch, a counter, and one result per string
+    const int max_grid = st->num_sms * 8;
+    if (count > st->ev_capacity) {
+        cudaStreamSynchronize(st->stream);
+        cudaFree(st->d_ev);
+        st->d_ev = nullptr;
+        st->ev_capacity = 0;
+        const size_t doubles = (size_t)max_grid * kEvMaxStrings + (size_t)count + 1;
+        cudaError_t e = cudaMalloc(&st->d_ev, sizeof(double) * doubles);
+        if (e == cudaSuccess) e = cudaMemsetAsync(st->d_ev, 0, sizeof(double) * doubles, st->stream);
+        if (e != cudaSuccess) { set_error("sv_expval_pauli: workspace allocation failed: %s", cudaGetErrorString(e)); return SV_ENOMEM; }
+        st->ev_capacity = count;
+    }
+    double *partials = st->d_ev;
+    double *results = partials + (size_t)max_grid * kEvMaxStrings;
+    unsigned *counter = reinterpret_cast<unsigned *>(results + st->ev_capacity);
+
+    // strings grouped by x mask (first-appearance order), at most kEvMaxStrings per pass
+    std::vector<int> order((size_t)count);
+    for (int i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return x_masks[p] < x_masks[q]; });
+    const long long nb = n >= 5 ? (1ll << (n - 5)) : 1ll;
+    std::vector<int> slot_of((size_t)count);
+    int pos = 0;
+    while (pos < count) {
+        const uint64_t x = x_masks[order[(size_t)pos]];
+        int m = 0;
+        while (pos + m < count && m < kEvMaxStrings && x_masks[order[(size_t)(pos + m)]] == x) ++m;
+        EvArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.xb = x >> 5;
+        a.xl = (int)(x & 31u);
+        a.pair_bit = a.xb ? highest_bit(a.xb) : -1;
+        a.n_units = a.xb ? nb / 2 : nb;
+        a.m = m;
+        for (int p = 0; p < m; ++p) {
+            const int s = order[(size_t)(pos + p)];
+            a.zb[p] = z_masks[s] >> 5;
+            a.zl[p] = (unsigned)(z_masks[s] & 31u);
+            a.comp[p] = __builtin_popcountll(x & z_masks[s]) & 1;
+            slot_of[(size_t)s] = pos + p;
+        }
+        long long g = (a.n_units * 32 + kEvThreads - 1) / kEvThreads;
+        if (g > max_grid) g = max_grid;
+        if (g < 1) g = 1;
+        const float *sv = st->d;
+        double *res = results + pos;
+        int rc;
+        if (m == 1) rc = launch_ev<1>(sv, a, partials, counter, res, (int)g, st->stream);
+        else if (m == 2) rc = launch_ev<2>(sv, a, partials, counter, res, (int)g, st->stream);
+        else if (m <= 4) rc = launch_ev<4>(sv, a, partials, counter, res, (int)g, st->stream);
+        else rc = launch_ev<8>(sv, a, partials, counter, res, (int)g, st->stream);
+        if (rc != SV_OK) return rc;
+        pos += m;
+    }
+    std::vector<double> host((size_t)count + kEvMaxStrings);
+    SV_CUDA_TRY(cudaMemcpyAsync(host.data(), results, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, st->stream));
+    SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    for (int i = 0; i < count; ++i) {
+        const double s = host[(size_t)slot_of[(size_t)i]];
+        // <psi|P|psi> = i^popc(x & z) * S; the accumulated component is Re S (even) or Im S (odd)
+        switch (__builtin_popcountll(x_masks[i] & z_masks[i]) & 3) {
+        case 0: out[i] = s; break;
+        case 1: out[i] = -s; break;
+        case 2: out[i] = -s; break;
+        default: out[i] = s; break;
+        }
+    }
+    return SV_OK;
+}

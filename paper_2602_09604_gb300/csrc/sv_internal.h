@@ -128,6 +128,9 @@ struct sv_state {
     unsigned long long *d_samples = nullptr;
     int sample_capacity = 0;
     long long n_chunks = 0;
+    // expectation-value workspace (library-owned, grown on demand): per-CTA partials, results, counter
+    double *d_ev = nullptr;
+    int ev_capacity = 0;
 };
 
 struct sv_fused {

@@ -315,6 +315,7 @@ extern "C" void sv_free(sv_state *st)
     cudaFree(st->d_chunk);
     cudaFree(st->d_uniforms);
     cudaFree(st->d_samples);
+    cudaFree(st->d_ev);
     delete st;
 }
 

@@ -41,6 +41,11 @@ class DeviceState:
     def sample(self, uniforms) -> np.ndarray:
         return B.sv_sample(self.h, uniforms)
 
+    def expval(self, strings) -> np.ndarray:
+        """<psi|P|psi> for Pauli strings given as {qubit: 'X' | 'Y' | 'Z'} dicts."""
+        masks = [B.pauli_masks(t) for t in strings]
+        return B.sv_expval_pauli(self.h, [m[0] for m in masks], [m[1] for m in masks])
+
     def free(self):
         if self.h is not None:
             B.sv_free(self.h)
