@@ -277,6 +277,31 @@ def bench_ours(args):
     h2d = 8 * N_SAMPLES + mat_bytes
     d2h = 8 * N_SAMPLES + 8
 
+    # ---- Pauli expectation values on the circuit's state (read-only passes of 8 * 2^n bytes)
+    expval = {}
+    if not args.no_expval:
+        B.sv_init(st.h, 0)
+        B.sv_apply_fused_gates(st.h, fused)
+        xr = (1 << 3) | (1 << 8) | (1 << 17) | (1 << 29)
+        groups = {"z_string_x0": ([0], [(1 << 2) | (1 << 20)]),
+                  "xy_string": ([xr], [(1 << 5) | (1 << 3)]),
+                  "z_strings_x0": ([0] * 8, [(1 << q) | (1 << (q + 6)) for q in range(8)]),
+                  "xy_strings_shared_x": ([xr] * 8, [(1 << q) | (xr if q % 2 else 0) for q in range(8)])}
+        for name, (xs, zs) in groups.items():
+            B.sv_expval_pauli(st.h, xs, zs)
+            ts = []
+            for _ in range(5):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.sv_expval_pauli(st.h, xs, zs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3)
+            us = statistics.median(ts)
+            expval[name] = {"strings": len(xs), "passes": 1, "us": us,
+                            "gbs": (8 << n) / (us * 1e-6) / 1e9}
+
     # ---- roofline of the dominant kernel class
     totals = {k: sum(v) for k, v in kernel_us.items()}
     dom = max(totals, key=totals.get)
@@ -312,6 +337,7 @@ def bench_ours(args):
         "plain_best_s": min((v["s_per_circuit"] for v in plain.values()), default=None),
         "speedup_vs_best_plain": (min(v["s_per_circuit"] for v in plain.values()) / value) if plain else None,
         "norm": norms[-1] if norms else None,
+        "expval_pauli": expval or None,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -345,6 +371,7 @@ def main():
     ap.add_argument("--cpu-gates", type=int, default=12)
     ap.add_argument("--ref-gates-per-step", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-expval", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -14,9 +14,16 @@
 // fp32, and every string adds it with its own sign into a float-float accumulator (two-sum); the
 // per-thread results are combined in fp64, per CTA and then in a fixed order by the last CTA.
 //
-// Work unit = one block (x has no bit >= 5) or one pair of blocks b, b ^ (x >> 5) (otherwise);
-// a warp reads each block's 32 real and 32 imaginary parts with coalesced loads, and the partner
-// amplitude j ^ x inside the paired block comes from lane (lane ^ (x & 31)) through a shuffle.
+// Work unit = one block (x has no bit >= 5) or one pair of blocks b, b ^ (x >> 5) with bit
+// `pair_bit` of b clear (otherwise); a warp reads each block's 32 real and 32 imaginary parts with
+// coalesced loads, and the partner amplitude j ^ x inside the paired block comes from lane
+// (lane ^ (x & 31)) through a shuffle.  A warp takes 32 consecutive units and handles them in
+// batches of 8 (eight blocks or pairs of loads in flight per warp).  Signs are bit lookups: for
+// unit u of a range starting at u0 (a multiple of 32), parity(b & zb) = parity(u0 & zu) ^ bit
+// (u - u0) of a 32-bit parity table of zu's low five bits, where zu is zb with the pair bit
+// deleted (b is u with a zero inserted there); these bits are the same in every lane.  The lane
+// part parity(lane & zl) is fixed per thread and applied once at the end.  Each string sums a
+// batch's signed terms in fp32, then adds the batch sum to its float-float accumulator.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -34,8 +41,10 @@ struct EvArgs {
     unsigned long long xb;    // x >> 5
     int xl;                   // x & 31
     int pair_bit;             // bit of the block index inserted as 0 to enumerate pairs; -1: no pairing
-    unsigned long long zb[kEvMaxStrings];
-    unsigned zl[kEvMaxStrings];
+    unsigned long long zu[kEvMaxStrings];   // z >> 5 with the pair bit deleted (unit-index parity mask)
+    unsigned ztab[kEvMaxStrings];           // bit i = parity(i & zu & 31), i < 32
+    unsigned zl[kEvMaxStrings];             // z & 31
+    unsigned pairpar[kEvMaxStrings];        // parity((x >> 5) & (z >> 5)): sign change to the paired block
     int comp[kEvMaxStrings];  // 0: accumulate the real part of the term, 1: the imaginary part
     int m;                    // strings in this pass (<= the kernel's M; the rest are padding)
 };
@@ -66,23 +75,10 @@ __device__ __forceinline__ unsigned long long ins_zero(unsigned long long v, int
     return ((v >> p) << (p + 1)) | low;
 }
 
-// the terms of the amplitudes of block `blk` (this lane's position) with partner values (pr, pi)
-template <int M>
-__device__ __forceinline__ void add_terms(FF2 (&acc)[M], const EvArgs &a, unsigned long long blk, unsigned lane, float ur, float ui,
-                                          float pr, float pi)
-{
-    // conj(partner) * own
-    const float tr = fmaf(pr, ur, pi * ui);
-    const float ti = fmaf(pr, ui, -(pi * ur));
-#pragma unroll
-    for (int p = 0; p < M; ++p) {
-        const int par = (__popcll(blk & a.zb[p]) + __popc(lane & a.zl[p])) & 1;
-        const float t = a.comp[p] ? ti : tr;
-        ff_add(acc[p], par ? -t : t);
-    }
-}
+constexpr int kEvBatch = 8;     // units per batch
+constexpr int kEvRange = 32;    // units per warp range (one parity table)
 
-template <int M>
+template <int M, bool PAIRED>
 __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restrict__ sv, const __grid_constant__ EvArgs a,
                                                            double *__restrict__ partials, unsigned *__restrict__ counter,
                                                            double *__restrict__ result)
@@ -92,30 +88,80 @@ __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restr
     for (int p = 0; p < M; ++p) acc[p] = FF2{0.f, 0.f};
     const unsigned lane = threadIdx.x & 31u;
     const unsigned plane = lane ^ (unsigned)a.xl;
+    const long long n_ranges = (a.n_units + kEvRange - 1) / kEvRange;
     const long long wstride = (long long)gridDim.x * (kEvThreads / 32);
-    for (long long u = (long long)blockIdx.x * (kEvThreads / 32) + (threadIdx.x >> 5); u < a.n_units; u += wstride) {
-        if (a.pair_bit < 0) {
-            const unsigned long long b = (unsigned long long)u;
-            const float ur = __ldcs(sv + b * 64 + lane);
-            const float ui = __ldcs(sv + b * 64 + 32 + lane);
-            const float pr = __shfl_sync(0xffffffffu, ur, plane);
-            const float pi = __shfl_sync(0xffffffffu, ui, plane);
-            add_terms<M>(acc, a, b, lane, ur, ui, pr, pi);
-        } else {
-            const unsigned long long b = ins_zero((unsigned long long)u, a.pair_bit);
-            const unsigned long long b2 = b ^ a.xb;
-            const float ur = __ldcs(sv + b * 64 + lane);
-            const float ui = __ldcs(sv + b * 64 + 32 + lane);
-            const float vr = __ldcs(sv + b2 * 64 + lane);
-            const float vi = __ldcs(sv + b2 * 64 + 32 + lane);
-            const float vpr = __shfl_sync(0xffffffffu, vr, plane);
-            const float vpi = __shfl_sync(0xffffffffu, vi, plane);
-            const float upr = __shfl_sync(0xffffffffu, ur, plane);
-            const float upi = __shfl_sync(0xffffffffu, ui, plane);
-            add_terms<M>(acc, a, b, lane, ur, ui, vpr, vpi);    // j in block b, partner in b2
-            add_terms<M>(acc, a, b2, lane, vr, vi, upr, upi);   // j in block b2, partner in b
+    for (long long r = (long long)blockIdx.x * (kEvThreads / 32) + (threadIdx.x >> 5); r < n_ranges; r += wstride) {
+        const long long u0 = r * kEvRange;
+        unsigned sgn0[M];   // block-parity sign bit of the range base, per string (warp-uniform)
+#pragma unroll
+        for (int p = 0; p < M; ++p) sgn0[p] = (unsigned)(__popcll((unsigned long long)u0 & a.zu[p]) & 1) << 31;
+#pragma unroll 1
+        for (int bt = 0; bt < kEvRange / kEvBatch; ++bt) {
+            float ur[kEvBatch], ui[kEvBatch], vr[kEvBatch], vi[kEvBatch];
+#pragma unroll
+            for (int i = 0; i < kEvBatch; ++i) {
+                const long long u = u0 + bt * kEvBatch + i;
+                ur[i] = ui[i] = vr[i] = vi[i] = 0.f;
+                if (u < a.n_units) {
+                    const unsigned long long b = PAIRED ? ins_zero((unsigned long long)u, a.pair_bit) : (unsigned long long)u;
+                    ur[i] = __ldcs(sv + b * 64 + lane);
+                    ui[i] = __ldcs(sv + b * 64 + 32 + lane);
+                    if constexpr (PAIRED) {
+                        const unsigned long long b2 = b ^ a.xb;
+                        vr[i] = __ldcs(sv + b2 * 64 + lane);
+                        vi[i] = __ldcs(sv + b2 * 64 + 32 + lane);
+                    }
+                }
+            }
+            float tr[kEvBatch], ti[kEvBatch], sr[kEvBatch], si[kEvBatch];
+#pragma unroll
+            for (int i = 0; i < kEvBatch; ++i) {
+                if constexpr (PAIRED) {
+                    const float vpr = __shfl_sync(0xffffffffu, vr[i], plane), vpi = __shfl_sync(0xffffffffu, vi[i], plane);
+                    const float upr = __shfl_sync(0xffffffffu, ur[i], plane), upi = __shfl_sync(0xffffffffu, ui[i], plane);
+                    // j in block b (partner in b2) and j' in block b2 (partner in b)
+                    tr[i] = fmaf(vpr, ur[i], vpi * ui[i]);
+                    ti[i] = fmaf(vpr, ui[i], -(vpi * ur[i]));
+                    sr[i] = fmaf(upr, vr[i], upi * vi[i]);
+                    si[i] = fmaf(upr, vi[i], -(upi * vr[i]));
+                } else {
+                    const float pr = __shfl_sync(0xffffffffu, ur[i], plane), pi = __shfl_sync(0xffffffffu, ui[i], plane);
+                    tr[i] = fmaf(pr, ur[i], pi * ui[i]);
+                    ti[i] = fmaf(pr, ui[i], -(pi * ur[i]));
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < M; ++p) {
+                // block-parity sign bits of the batch's units: warp-uniform; the lane's own parity
+                // (lane & zl) is applied once at the end
+                const unsigned tab = a.ztab[p] >> (bt * kEvBatch);
+                float sum = 0.f;
+                if (a.comp[p] == 0) {
+#pragma unroll
+                    for (int i = 0; i < kEvBatch; ++i) {
+                        const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
+                        sum += __uint_as_float(__float_as_uint(tr[i]) ^ sg);
+                        if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(sr[i]) ^ sg ^ (a.pairpar[p] << 31));
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kEvBatch; ++i) {
+                        const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
+                        sum += __uint_as_float(__float_as_uint(ti[i]) ^ sg);
+                        if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(si[i]) ^ sg ^ (a.pairpar[p] << 31));
+                    }
+                }
+                ff_add(acc[p], sum);
+            }
         }
     }
+    // the lane's parity(lane & zl) sign, common to every term this thread added
+#pragma unroll
+    for (int p = 0; p < M; ++p)
+        if (__popc(lane & a.zl[p]) & 1) {
+            acc[p].hi = -acc[p].hi;
+            acc[p].lo = -acc[p].lo;
+        }
     __shared__ double ws[kEvThreads / 32][M];
     __shared__ bool last;
 #pragma unroll
@@ -149,7 +195,8 @@ __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restr
 template <int M>
 int launch_ev(const float *sv, const EvArgs &a, double *partials, unsigned *counter, double *result, int grid, cudaStream_t s)
 {
-    expval_kernel<M><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
+    if (a.pair_bit >= 0) expval_kernel<M, true><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
+    else expval_kernel<M, false><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -219,12 +266,23 @@ extern "C" int sv_expval_pauli(const sv_state *st_c, const uint64_t *x_masks, co
         a.m = m;
         for (int p = 0; p < m; ++p) {
             const int s = order[(size_t)(pos + p)];
-            a.zb[p] = z_masks[s] >> 5;
+            const unsigned long long zb = z_masks[s] >> 5;
+            unsigned long long zu = zb;
+            if (a.pair_bit >= 0) {   // delete the pair bit: b = u with a zero inserted there
+                const unsigned long long low = zb & ((1ull << a.pair_bit) - 1ull);
+                zu = ((zb >> (a.pair_bit + 1)) << a.pair_bit) | low;
+            }
+            a.zu[p] = zu;
+            unsigned tab = 0;
+            for (unsigned i = 0; i < 32; ++i) tab |= (unsigned)(__builtin_popcountll(i & zu & 31ull) & 1) << i;
+            a.ztab[p] = tab;
             a.zl[p] = (unsigned)(z_masks[s] & 31u);
+            a.pairpar[p] = (unsigned)(__builtin_popcountll(a.xb & zb) & 1);
             a.comp[p] = __builtin_popcountll(x & z_masks[s]) & 1;
             slot_of[(size_t)s] = pos + p;
         }
-        long long g = (a.n_units * 32 + kEvThreads - 1) / kEvThreads;
+        const long long ranges = (a.n_units + kEvRange - 1) / kEvRange;
+        long long g = (ranges * 32 + kEvThreads - 1) / kEvThreads;
         if (g > max_grid) g = max_grid;
         if (g < 1) g = 1;
         const float *sv = st->d;
