@@ -42,7 +42,7 @@ extern "C" {
 
 #define SV_MAX_QUBITS 35
 #define SV_MAX_K 6
-#define SV_MAX_CONTROLS 4
+#define SV_MAX_CONTROLS 33
 
 enum sv_status {
     SV_OK = 0,
@@ -62,7 +62,9 @@ enum sv_path {
     SV_PATH_HIGH = 2,
     SV_PATH_MIXED = 3,
     SV_PATH_TC_TF32 = 4,
-    SV_PATH_TC_BF16X3 = 5
+    SV_PATH_TC_BF16X3 = 5,
+    SV_PATH_CONTROLLED = 6   /* a gate kept with its controls: only amplitudes whose control bits
+                                are all 1 are read and written (Section IV, ApplyControlledGate) */
 };
 
 enum sv_precision {
@@ -83,8 +85,12 @@ typedef struct sv_mlp sv_mlp;       /* opaque learned cost model */
 
 
 /* One input gate.  mat: 2^k x 2^k complex128 row-major interleaved (re, im), local bit j <->
- * targets[j].  Controls (if any) are folded into a dense (k + n_controls)-qubit matrix by the
- * fuser, so k + n_controls <= 6. */
+ * targets[j]; the gate acts only where every control qubit is 1.  The fuser folds the controls
+ * into a dense (k + n_controls)-qubit matrix when k + n_controls <= the fusion size (max_k; 6 in
+ * SV_FUSE_NONE mode), so the gate can fuse with its neighbours.  Otherwise, for k <= 3, it keeps
+ * the gate controlled (SV_PATH_CONTROLLED: one pass over the 2^(n - n_controls) amplitudes whose
+ * control bits are 1; a fusion barrier for every qubit it names); a larger k is folded if
+ * k + n_controls <= 6 and rejected (SV_EINVAL) if not. */
 typedef struct sv_gate {
     int k;
     int targets[SV_MAX_K];
@@ -109,6 +115,7 @@ typedef struct sv_fused_info {
     int targets[SV_MAX_K];   /* ascending; the fused matrix uses local bit j <-> targets[j] */
     int path;                /* enum sv_path chosen for it */
     int n_source_gates;      /* how many input gates it absorbed */
+    uint64_t control_mask;   /* SV_PATH_CONTROLLED: bit q set <-> qubit q is a control; else 0 */
 } sv_fused_info;
 
 /* One timing record, written by sv_apply_fused_gates when asked (CUDA events around each launch). */

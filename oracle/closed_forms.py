@@ -7,8 +7,12 @@
   basis vector): amplitude of |y> is 2^(-n/2) exp(+2 pi i x y / 2^n).  The product x*y is taken
   modulo 2^n in exact integer arithmetic before the phase is formed, so the value is accurate to
   fp64 rounding at any n.
+* Grover search (section V: the oracle flips the marked state's phase, the diffusion amplifies
+  it): the amplitudes after r rounds, from the standard two-dimensional rotation argument.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -42,3 +46,13 @@ def qft_amplitudes(n: int, x: int, ys) -> np.ndarray:
 
 def qft_state(n: int, x: int) -> np.ndarray:
     return qft_amplitudes(n, x, np.arange(1 << n, dtype=np.uint64))
+
+
+def grover_amplitudes(n: int, rounds: int) -> tuple:
+    """(marked amplitude, every other amplitude) after `rounds` Grover rounds from H|0...0> whose
+    diffusion is H(I - 2|0><0|)H = I - 2|s><s| (the textbook operator times -1): with
+    sin t = 2^(-n/2), the textbook iterate rotates by 2t in span{|m>, |m_perp>}, and the extra
+    sign gives (-1)^r sin((2r+1)t) on |m> and (-1)^r cos((2r+1)t)/sqrt(2^n - 1) elsewhere."""
+    t = math.asin(2.0 ** (-n / 2))
+    sgn = -1.0 if rounds % 2 else 1.0
+    return sgn * math.sin((2 * rounds + 1) * t), sgn * math.cos((2 * rounds + 1) * t) / math.sqrt(2.0 ** n - 1)

@@ -16,13 +16,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsvgb300.so")
 
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNITARY, SV_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3 = range(6)
+PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3, PATH_CONTROLLED = range(7)
 PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
-              PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3"}
+              PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3", PATH_CONTROLLED: "controlled"}
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
 FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE = 0, 1, 2
 MAX_K = 6
-MAX_CONTROLS = 4
+MAX_CONTROLS = 33
 
 
 class SvError(RuntimeError):
@@ -43,7 +43,7 @@ class sv_fuse_opts(ctypes.Structure):
 
 class sv_fused_info(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("targets", ctypes.c_int * MAX_K), ("path", ctypes.c_int),
-                ("n_source_gates", ctypes.c_int)]
+                ("n_source_gates", ctypes.c_int), ("control_mask", ctypes.c_uint64)]
 
 
 class sv_mlp_train_opts(ctypes.Structure):
@@ -212,8 +212,10 @@ def sv_fused_count(f) -> int:
 def sv_fused_get_info(f, i: int) -> dict:
     info = sv_fused_info()
     _check(lib.sv_fused_get_info(f, i, ctypes.byref(info)))
+    cm = int(info.control_mask)
     return {"k": info.k, "targets": tuple(info.targets[: info.k]), "path": info.path,
-            "n_source_gates": info.n_source_gates}
+            "n_source_gates": info.n_source_gates,
+            "controls": tuple(q for q in range(64) if (cm >> q) & 1)}
 
 
 def sv_fused_get_matrix(f, i: int) -> np.ndarray:

@@ -58,6 +58,18 @@ struct TileArgs {
     TileMap t;
 };
 
+// Controlled gate kept whole (Section IV, ApplyControlledGate): only the groups whose control
+// bits are all 1 exist, so the group index enumerates the free bits (neither target nor control).
+template <int K>
+struct CtrlArgs {
+    MatArg<K> m;
+    long long foff[1 << K];                 // float offset of local index j from the group base
+    int pos[SV_MAX_K + SV_MAX_CONTROLS];    // ascending target and control qubits
+    int npos;
+    unsigned long long cmask;               // control bits, set in every group base
+    long long n_groups;                     // 2^(n - k - n_controls)
+};
+
 template <int K>
 __host__ __device__ constexpr int high_vec() { return K <= 2 ? 4 : (K == 3 ? 2 : 1); }
 
@@ -395,6 +407,64 @@ struct Occ {
 Occ g_occ;
 std::mutex g_occ_mu;
 
+// One group per thread: the base index has a zero inserted at every target and control position
+// (ascending) and the control bits then set; the 2^K amplitudes are gathered, multiplied by U
+// (constant-bank operands) and written back in place.
+template <int K>
+__global__ void __launch_bounds__(kHighThreads) apply_ctrl_kernel(float *__restrict__ sv, const __grid_constant__ CtrlArgs<K> a)
+{
+    constexpr int D = 1 << K;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n_groups) return;
+    unsigned long long b = (unsigned long long)g;
+    for (int i = 0; i < a.npos; ++i) b = insert_zero(b, a.pos[i]);
+    b |= a.cmask;
+    float *base = sv + (long long)(((b >> 5) << 6) | (b & 31ull));
+    float xr[D][1], xi[D][1];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        xr[j][0] = base[a.foff[j]];
+        xi[j][0] = base[a.foff[j] + 32];
+    }
+    float *obase = opaque(base);
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        float yr[1], yi[1];
+        row_param<K, 1>(a.m, r, xr, xi, yr, yi);
+        obase[a.foff[r]] = yr[0];
+        obase[a.foff[r] + 32] = yi[0];
+    }
+}
+
+template <int K>
+int launch_ctrl(float *sv, int n, const FusedGate &g, const float2 *, cudaStream_t stream, int)
+{
+    CtrlArgs<K> a;
+    std::memset(&a, 0, sizeof(a));
+    fill_mat(a.m, g, false);
+    for (int j = 0; j < (1 << K); ++j) {
+        unsigned long long o = 0;
+        for (int t = 0; t < K; ++t)
+            if ((j >> t) & 1) o |= 1ull << g.targets[t];
+        a.foff[j] = (long long)(((o >> 5) << 6) | (o & 31ull));
+    }
+    const unsigned long long all = g.mask | g.cmask;
+    int np = 0;
+    for (int q = 0; q < n; ++q)
+        if ((all >> q) & 1) a.pos[np++] = q;
+    if (np != K + __builtin_popcountll(g.cmask) || (g.mask & g.cmask) || (all >> n)) {
+        set_error("launch: controlled gate names a qubit twice or outside the state");
+        return SV_EINVAL;
+    }
+    a.npos = np;
+    a.cmask = g.cmask;
+    a.n_groups = 1ll << (n - np);
+    const long long grid = (a.n_groups + kHighThreads - 1) / kHighThreads;
+    apply_ctrl_kernel<K><<<(unsigned)grid, kHighThreads, 0, stream>>>(sv, a);
+    SV_CUDA_TRY(cudaGetLastError());
+    return SV_OK;
+}
+
 template <int K>
 int launch_high(float *sv, int n, const FusedGate &g, const float2 *umem, cudaStream_t stream, int num_sms)
 {
@@ -459,6 +529,7 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
 using LaunchFn = int (*)(float *, int, const FusedGate &, const float2 *, cudaStream_t, int);
 const LaunchFn kHigh[7] = {nullptr, launch_high<1>, launch_high<2>, launch_high<3>, launch_high<4>, launch_high<5>, launch_high<6>};
 const LaunchFn kTile[7] = {nullptr, launch_tile<1>, launch_tile<2>, launch_tile<3>, launch_tile<4>, launch_tile<5>, launch_tile<6>};
+const LaunchFn kCtrl[4] = {nullptr, launch_ctrl<1>, launch_ctrl<2>, launch_ctrl<3>};
 
 }  // namespace
 
@@ -553,6 +624,9 @@ int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, c
     case SV_PATH_TC_TF32:
     case SV_PATH_TC_BF16X3:
         return launch_tc_gate(sv, n, g, dtc, stream, num_sms);
+    case SV_PATH_CONTROLLED:
+        if (g.k > 3 || !g.cmask) { set_error("launch: a controlled gate has 1..3 targets and a control"); return SV_EINVAL; }
+        return kCtrl[g.k](sv, n, g, umem, stream, num_sms);
     default:
         set_error("launch: unknown path %d", g.path);
         return SV_EINVAL;

@@ -413,8 +413,10 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     for (int i = 0; i < count; ++i) {
         if (!circuits[i]) { set_error("sv_batch_create: circuit %d is NULL", i); return SV_EINVAL; }
         ns[(size_t)i] = circuits[i]->n;
-        for (const FusedGate &g : circuits[i]->gates)
+        for (const FusedGate &g : circuits[i]->gates) {
             if (g.k > kBatchMaxK) { set_error("sv_batch_create: circuit %d has a %d-qubit fused gate (batch kernel takes k <= %d)", i, g.k, kBatchMaxK); return SV_EINVAL; }
+            if (g.cmask) { set_error("sv_batch_create: circuit %d keeps a controlled gate (fuse with max_k >= its qubit count)", i); return SV_EINVAL; }
+        }
     }
     const size_t need = sv_batch_arena_bytes(ns.data(), count);
     if (need == 0) { set_error("sv_batch_create: circuits must have 1..%d qubits", kBatchMaxN); return SV_EINVAL; }

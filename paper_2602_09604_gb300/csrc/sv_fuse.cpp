@@ -30,6 +30,7 @@ struct Block {
     std::vector<cplx> mat;    // 2^|qubits| square, local bit j <-> qubits[j]
     int n_src = 0;
     long long created = 0;
+    uint64_t cmask = 0;       // a controlled gate kept whole (qubits = its targets); else 0
 };
 
 // mat (dim x dim, acting on qubit list T) <- G * mat, where G acts on qubits gq (local bit b of G
@@ -109,11 +110,26 @@ std::vector<cplx> expand(const std::vector<cplx> &M, const std::vector<int> &S, 
 }
 
 struct Dense {
-    std::vector<int> q;        // qubits: targets then controls (local bit order of m)
-    std::vector<cplx> m;       // dense matrix with the controls folded in
+    std::vector<int> q;        // qubits: targets then folded controls (local bit order of m)
+    std::vector<cplx> m;       // dense matrix with those controls folded in
+    uint64_t cmask = 0;        // controls kept as controls (the gate is not fused); else 0
 };
 
+// A controlled gate as its own block over its ascending targets.
+Block controlled_block(const Dense &d)
+{
+    Block b;
+    b.qubits = d.q;
+    std::sort(b.qubits.begin(), b.qubits.end());
+    b.mat = identity(size_t(1) << b.qubits.size());
+    left_multiply(b.mat, b.qubits, d.m, d.q);
+    b.n_src = 1;
+    b.cmask = d.cmask;
+    return b;
+}
+
 constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above this validation error
+constexpr int kMaxControlledK = 3;          // targets of a gate kept controlled
 
 // Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
 std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k)
@@ -124,6 +140,25 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         const std::vector<int> &Q = dense[gi].q;
         uint64_t qmask = 0;
         for (int q : Q) qmask |= uint64_t(1) << q;
+        if (dense[gi].cmask) {
+            // a controlled gate is a barrier on every qubit it names: close the blocks it touches
+            // (creation order), emit it, keep the others open (disjoint, so they commute with it)
+            const uint64_t sm = qmask | dense[gi].cmask;
+            std::vector<Block> rest;
+            std::vector<Block> closed;
+            for (Block &b : open) {
+                bool t = false;
+                for (int q : b.qubits) t = t || ((sm >> q) & 1);
+                (t ? closed : rest).push_back(std::move(b));
+            }
+            std::sort(closed.begin(), closed.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
+            for (Block &b : closed) emitted.push_back(std::move(b));
+            Block cb = controlled_block(dense[gi]);
+            cb.created = stamp++;
+            emitted.push_back(std::move(cb));
+            open.swap(rest);
+            continue;
+        }
         std::vector<int> touching;
         for (int b = 0; b < (int)open.size(); ++b) {
             for (int q : open[b].qubits)
@@ -191,14 +226,18 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
     std::vector<Block> merged;
     const int kScanBack = 64;
     for (Block &b : emitted) {
+        if (b.cmask) {   // controlled gates neither merge nor move
+            merged.push_back(std::move(b));
+            continue;
+        }
         uint64_t bm = 0;
         for (int q : b.qubits) bm |= uint64_t(1) << q;
         const int lim = std::max(max_k, (int)b.qubits.size());
         int target = -1;
         for (int p = (int)merged.size() - 1, steps = 0; p >= 0 && steps < kScanBack; --p, ++steps) {
-            uint64_t pm = 0;
+            uint64_t pm = merged[p].cmask;
             for (int q : merged[p].qubits) pm |= uint64_t(1) << q;
-            if (__builtin_popcountll(pm | bm) <= lim) { target = p; break; }
+            if (!merged[p].cmask && __builtin_popcountll(pm | bm) <= lim) { target = p; break; }
             if (pm & bm) break;   // cannot move past a block it shares a qubit with
         }
         if (target < 0) {
@@ -235,6 +274,7 @@ bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
 
 int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path)
 {
+    if (g.cmask) return SV_PATH_CONTROLLED;
     if (force_path != SV_PATH_AUTO) return force_path;
     // tensor cores for 4..6-qubit gates of states with at least 2^k blocks of 32 amplitudes
     if (precision != SV_PREC_FP32 && g.k >= tc_min_k && g.k >= 4 && n >= g.k + 5)
@@ -272,13 +312,22 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     if (opts.force_path < SV_PATH_AUTO || opts.force_path > SV_PATH_TC_BF16X3) { set_error("sv_fuse_circuit: bad force_path"); return SV_EINVAL; }
     if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
 
-    // ---- validate and densify every input gate (controls folded into the matrix)
+    // ---- validate and densify every input gate (controls folded into the matrix where they fit
+    // the fusion size; otherwise small gates stay controlled)
     std::vector<Dense> dense;
     try { dense.resize(size_t(n_gates)); } catch (const std::bad_alloc &) { set_error("sv_fuse_circuit: out of host memory"); return SV_ENOMEM; }
+    const int fold_limit = opts.mode == SV_FUSE_NONE ? SV_MAX_K : opts.max_k;
     for (int gi = 0; gi < n_gates; ++gi) {
         const sv_gate &g = gates[gi];
-        if (g.k < 1 || g.k > SV_MAX_K || g.n_controls < 0 || g.n_controls > SV_MAX_CONTROLS || g.k + g.n_controls > SV_MAX_K || !g.mat) {
-            set_error("sv_fuse_circuit: gate %d has k=%d, n_controls=%d (need 1<=k, k+controls<=6) or no matrix", gi, g.k, g.n_controls);
+        if (g.k < 1 || g.k > SV_MAX_K || g.n_controls < 0 || g.n_controls > SV_MAX_CONTROLS || !g.mat) {
+            set_error("sv_fuse_circuit: gate %d has k=%d, n_controls=%d (need 1 <= k <= 6, 0 <= controls <= %d) or no matrix", gi, g.k,
+                      g.n_controls, SV_MAX_CONTROLS);
+            return SV_EINVAL;
+        }
+        const bool keep_controlled = g.n_controls > 0 && g.k + g.n_controls > fold_limit && g.k <= kMaxControlledK;
+        if (!keep_controlled && g.k + g.n_controls > SV_MAX_K) {
+            set_error("sv_fuse_circuit: gate %d has k=%d and %d controls: a controlled gate keeps at most %d targets, "
+                      "a folded one at most 6 qubits", gi, g.k, g.n_controls, kMaxControlledK);
             return SV_EINVAL;
         }
         uint64_t used = 0;
@@ -298,6 +347,13 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         if (!is_unitary(U, d, 1e-8)) {
             set_error("sv_fuse_circuit: gate %d is not unitary (|U^H U - I| > 1e-8)", gi);
             return SV_EUNITARY;
+        }
+        if (keep_controlled) {
+            q.resize(size_t(g.k));
+            for (int j = 0; j < g.n_controls; ++j) dense[gi].cmask |= uint64_t(1) << g.controls[j];
+            dense[gi].q = q;
+            dense[gi].m = std::move(U);
+            continue;
         }
         // controlled matrix on local bits (targets..., controls...): U where all controls are 1
         const int kk = g.k + g.n_controls;
@@ -328,6 +384,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             if (b.qubits[j] < 32) fg.mask_lo |= 1u << b.qubits[j];
         }
         fg.n_src = b.n_src;
+        fg.cmask = b.cmask;
         fg.mat = std::move(b.mat);
         const size_t d2 = fg.mat.size();
         fg.ur.resize(d2);
@@ -344,6 +401,11 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         if (opts.mode == SV_FUSE_NONE) {
             // one block per input gate, matrix re-expressed over its ascending qubit list
             for (int gi = 0; gi < n_gates; ++gi) {
+                if (dense[gi].cmask) {
+                    Block cb = controlled_block(dense[gi]);
+                    finish(cb, -1);
+                    continue;
+                }
                 Block b;
                 b.qubits = dense[gi].q;
                 std::sort(b.qubits.begin(), b.qubits.end());
@@ -367,6 +429,10 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             for (auto &c : cand) {
                 rows_of.emplace_back();
                 for (Block &b : c) {
+                    if (b.cmask) {   // the same in every candidate: not scored
+                        rows_of.back().push_back({(int)row_path.size(), 0});
+                        continue;
+                    }
                     FusedGate g;
                     g.k = (int)b.qubits.size();
                     for (int j = 0; j < g.k; ++j) g.targets[j] = b.qubits[j];
@@ -391,6 +457,10 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             for (size_t c = 0; c < cand.size(); ++c) {
                 double tot = 0.0;
                 for (auto &rr : rows_of[c]) {
+                    if (rr.second == 0) {
+                        chosen[c].push_back(SV_PATH_CONTROLLED);
+                        continue;
+                    }
                     int bp = rr.first;
                     for (int r = rr.first; r < rr.first + rr.second; ++r)
                         if (us[size_t(r)] < us[size_t(bp)]) bp = r;
@@ -425,6 +495,7 @@ extern "C" int sv_fused_get_info(const sv_fused *f, int i, sv_fused_info *info)
     for (int j = 0; j < g.k; ++j) info->targets[j] = g.targets[j];
     info->path = g.path;
     info->n_source_gates = g.n_src;
+    info->control_mask = g.cmask;
     return SV_OK;
 }
 

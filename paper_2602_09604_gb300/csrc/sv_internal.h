@@ -45,6 +45,7 @@ struct FusedGate {
     uint64_t mask = 0;      // bit q set <-> qubit q is a target
     int path = SV_PATH_AUTO;
     int n_src = 0;
+    uint64_t cmask = 0;     // SV_PATH_CONTROLLED: control qubits (all must be 1); else 0
     std::vector<cplx> mat;  // 2^k x 2^k row-major, fp64
     std::vector<float> ur, ui;  // fp32 rounded once from mat
 };

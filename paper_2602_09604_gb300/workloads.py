@@ -21,6 +21,14 @@ exact layout; the readings below are this library's):
 * GHZ (section V): H on qubit 0, then CNOT(control q, target q+1) for q = 0 .. n-2.
 * hardware-efficient ansatz: per layer RZ(phi) then RY(theta) on every qubit (angles uniform on
   [0, 2 pi)), then a CZ ladder CZ(q, q+1) for q = 0 .. n-2.
+* Grover (section V): H on every qubit, then per round an oracle (X on the qubits where the
+  marked index has a 0, a Z on qubit n-1 controlled by qubits 0 .. n-2, the same X layer) and a
+  diffusion (H, X on every qubit, the same multi-controlled Z, X, H).  The diffusion is
+  H (I - 2|0><0|) H = I - 2|s><s|, the textbook operator times -1 (the oracle's closed form
+  follows from that).
+* Quantum volume (section V): `depth` layers (default n); each draws a random permutation of the
+  qubits and, on every pair (p[2i], p[2i+1]), applies Haar-random single-qubit unitaries and
+  CNOTs: (A1, A2), CNOT, (B1, B2), CNOT, (C1, C2), CNOT, (D1, D2), CNOT controlled by the first.
 """
 from __future__ import annotations
 
@@ -205,6 +213,34 @@ def hea_batch(count: int = 256, n_lo: int = 10, n_hi: int = 20, layers: int = 8,
 
 
 # ----------------------------------------------------------------------------- random unitaries
+def grover_circuit(n: int, marked: int, rounds: int) -> list:
+    assert n >= 2 and 0 <= marked < (1 << n)
+    mcz = Gate((n - 1,), Z, tuple(range(n - 1)), "mcz")
+    gates = [Gate((q,), H, (), "h") for q in range(n)]
+    for _ in range(rounds):
+        flips = [Gate((q,), X, (), "x") for q in range(n) if not (marked >> q) & 1]
+        gates += flips + [mcz] + flips
+        gates += [Gate((q,), H, (), "h") for q in range(n)] + [Gate((q,), X, (), "x") for q in range(n)]
+        gates += [mcz]
+        gates += [Gate((q,), X, (), "x") for q in range(n)] + [Gate((q,), H, (), "h") for q in range(n)]
+    return gates
+
+
+def qv_circuit(n: int, depth: int | None = None, seed: int = 0) -> list:
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(n if depth is None else depth):
+        perm = [int(q) for q in rng.permutation(n)]
+        for i in range(n // 2):
+            a, b = perm[2 * i], perm[2 * i + 1]
+            for layer in range(4):
+                gates.append(Gate((a,), random_unitary(2, rng), (), "u"))
+                gates.append(Gate((b,), random_unitary(2, rng), (), "u"))
+                if layer < 3:
+                    gates.append(Gate((b,), X, (a,), "cx"))
+    return gates
+
+
 def random_unitary(dim: int, rng: np.random.Generator) -> np.ndarray:
     """Haar-random unitary: QR of a complex Gaussian matrix with the phases of R's diagonal removed."""
     z = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))) / math.sqrt(2.0)

@@ -48,12 +48,16 @@ def test_required_bytes_is_eight_per_amplitude(B):
 
 
 class _G:
-    def __init__(self, targets, matrix):
-        self.targets, self.matrix, self.controls = targets, matrix, ()
+    def __init__(self, targets, matrix, controls=()):
+        self.targets, self.matrix, self.controls = targets, matrix, tuple(controls)
 
 
 def fused_as_gates(B, f):
-    return [_G(B.sv_fused_get_info(f, i)["targets"], B.sv_fused_get_matrix(f, i)) for i in range(B.sv_fused_count(f))]
+    out = []
+    for i in range(B.sv_fused_count(f)):
+        info = B.sv_fused_get_info(f, i)
+        out.append(_G(info["targets"], B.sv_fused_get_matrix(f, i), info["controls"]))
+    return out
 
 
 def check_fusion(B, n, gates, max_k, init=0):
@@ -92,6 +96,51 @@ def test_fusion_with_controls_and_random_gates(B, max_k):
         nc = int(rng.integers(0, 3)) if k + 2 <= max(max_k, 3) else 0
         gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
     check_fusion(B, n, gates, max_k, init=77)
+
+
+@pytest.mark.parametrize("max_k", [1, 2, 4, 6])
+def test_fusion_with_many_controls(B, max_k):
+    # gates with up to 7 controls: folded where k + controls fits max_k, kept controlled (a fusion
+    # barrier on every qubit they name) otherwise; the result is exact either way
+    rng = np.random.default_rng(11 + max_k)
+    n = 10
+    gates = []
+    for _ in range(60):
+        k = int(rng.integers(1, 4))
+        nc = int(rng.integers(0, 8)) if rng.random() < 0.6 else 0
+        qs = [int(q) for q in rng.permutation(n)]
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    infos = check_fusion(B, n, gates, max_k, init=333)
+    kept = [g for g in gates if g.controls and len(g.targets) + len(g.controls) > max_k]
+    ctrl = [x for x in infos if x["path"] == B.PATH_CONTROLLED]
+    assert len(ctrl) == len(kept)
+    assert all(x["n_source_gates"] == 1 and x["controls"] for x in ctrl)
+    assert all(not x["controls"] for x in infos if x["path"] != B.PATH_CONTROLLED)
+
+
+def test_controlled_gate_limits(B):
+    rng = np.random.default_rng(4)
+    n = 9
+    big = wl.Gate((0, 1, 2, 3), wl.random_unitary(16, rng), (5, 6, 7))     # 4 targets + 3 controls
+    with pytest.raises(B.SvError) as e:
+        B.sv_fuse_circuit([big], n, max_k=4)
+    assert e.value.code == B.SV_EINVAL
+    fold = wl.Gate((0, 1, 2, 3), wl.random_unitary(16, rng), (5, 6))     # folds into 6 qubits
+    f = B.sv_fuse_circuit([fold], n, max_k=4)
+    try:
+        info = B.sv_fused_get_info(f, 0)
+        assert info["k"] == 6 and info["path"] != B.PATH_CONTROLLED
+    finally:
+        B.sv_fused_free(f)
+
+
+@pytest.mark.parametrize("max_k", [2, 4, 6])
+def test_grover_and_qv_fuse_exactly(B, max_k):
+    n = 9
+    infos = check_fusion(B, n, wl.grover_circuit(n, 300, 3), max_k, init=0)
+    mcz = [x for x in infos if x["path"] == B.PATH_CONTROLLED]
+    assert len(mcz) == 6 and all(x["targets"] == (8,) and x["controls"] == tuple(range(8)) for x in mcz)
+    check_fusion(B, 8, wl.qv_circuit(8, seed=1), max_k, init=5)
 
 
 def test_fusion_of_textbook_circuits(B):
