@@ -302,6 +302,39 @@ def bench_ours(args):
             expval[name] = {"strings": len(xs), "passes": 1, "us": us,
                             "gbs": (8 << n) / (us * 1e-6) / 1e9}
 
+    # ---- NEXT rows on the same state buffer: controlled-gate kernel, Grover and quantum volume
+    next_rows = {}
+    if not args.no_next_rows:
+        rng2 = np.random.default_rng(77)
+        ctrl = {}
+        for k, c in ((1, 1), (1, 3), (2, 2), (3, 3)):
+            qs = [int(q) for q in rng2.permutation(n)]
+            g = wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng2), tuple(qs[k:k + c]))
+            fc = B.sv_fuse_circuit([g] * 4, n, max_k=1)          # k + c > 1: kept controlled
+            recs = B.sv_apply_fused_gates(st.h, fc, timings=True)
+            B.sv_fused_free(fc)
+            us = statistics.median(r["us"] for r in recs[1:])
+            ctrl[f"k{k}_c{c}"] = {"us": us, "gbs": 16 * (1 << (n - c)) / (us * 1e-6) / 1e9,
+                                  "bytes": 16 * (1 << (n - c))}
+        next_rows["controlled_gate"] = ctrl
+        circ = {"grover30_r3": wl.grover_circuit(n, 0x2C0FFEE1, 3), "qv30": wl.qv_circuit(n, seed=1)}
+        for name, gl in circ.items():
+            fcirc = B.sv_fuse_circuit(gl, n, **fuse_kw)
+            cinfo = [B.sv_fused_get_info(fcirc, i) for i in range(B.sv_fused_count(fcirc))]
+            B.sv_init(st.h, 0)
+            B.sv_apply_fused_gates(st.h, fcirc)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.sv_init(st.h, 0)
+            B.sv_apply_fused_gates(st.h, fcirc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            next_rows[name] = {"gates": len(gl), "fused_gates": len(cinfo),
+                               "controlled": sum(1 for i in cinfo if i["path"] == B.PATH_CONTROLLED),
+                               "s_per_circuit": e0.elapsed_time(e1) / 1e3}
+            B.sv_fused_free(fcirc)
+
     # ---- roofline of the dominant kernel class
     totals = {k: sum(v) for k, v in kernel_us.items()}
     dom = max(totals, key=totals.get)
@@ -338,6 +371,7 @@ def bench_ours(args):
         "speedup_vs_best_plain": (min(v["s_per_circuit"] for v in plain.values()) / value) if plain else None,
         "norm": norms[-1] if norms else None,
         "expval_pauli": expval or None,
+        "next_rows": next_rows or None,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -372,6 +406,7 @@ def main():
     ap.add_argument("--ref-gates-per-step", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expval", action="store_true")
+    ap.add_argument("--no-next-rows", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
