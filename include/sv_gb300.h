@@ -283,6 +283,8 @@ typedef struct sv_batch_opts {
     int split_min_n;    /* circuits of at least this many qubits are split into tiles of each
                            step that all CTAs share; 0 = never (default 15) */
     int tile_log2;      /* groups per tile of a split circuit's step: 2^tile_log2, 5..16 (default 12) */
+    int wave_mb;        /* split circuits run in waves of at most this many MB of state, one wave
+                           after another, so a wave's states stay in L2; 0 = one wave (default 0) */
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
@@ -295,7 +297,7 @@ SV_API int sv_batch_create(const sv_fused *const *circuits, int count, void *are
                            sv_batch **out);
 SV_API void sv_batch_free(sv_batch *b);
 /* Options take effect at the next sv_batch_run (which rebuilds the work list, synchronously, when
- * smem_max_n, split_min_n or tile_log2 changed).  SV_EINVAL for a value out of range. */
+ * smem_max_n, split_min_n, tile_log2 or wave_mb changed).  SV_EINVAL for a value out of range. */
 SV_API int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *opts);
 SV_API int sv_batch_get_opts(const sv_batch *b, sv_batch_opts *opts);
 /* Run every circuit from |0...0> into its state buffer: one persistent launch (asynchronous). */

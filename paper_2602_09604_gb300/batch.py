@@ -2,7 +2,8 @@
 
 The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..4), CTA
 size, the largest circuit kept in shared memory, the smallest circuit split into shared tiles, the
-tile size, and the persistent grid -- by coordinate descent
+tile size, the wave size (MB of split-circuit state per wave), and the persistent grid -- by
+coordinate descent
 from a default, each candidate replayed from its captured CUDA graph and timed with CUDA events
 (median of repeats).  The winner is cached in a JSON file keyed by GPU name and a digest of the
 batch's circuit sizes and gate counts.
@@ -39,8 +40,8 @@ class Batch:
         self.fused = [B.sv_fuse_circuit(g, n, max_k=max_k) for n, g in circuits]
         self.h = B.sv_batch_create(self.fused, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
-    def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12):
-        B.sv_batch_set_opts(self.h, threads, smem_max_n, ctas, use_graph, split_min_n, tile_log2)
+    def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0):
+        B.sv_batch_set_opts(self.h, threads, smem_max_n, ctas, use_graph, split_min_n, tile_log2, wave_mb)
 
     def run(self):
         B.sv_batch_run(self.h)
@@ -88,7 +89,7 @@ def digest(circuits) -> str:
 def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)):
     """Returns (best settings dict, trial log)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    key = f"v2|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
+    key = f"v3|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
     if use_cache and os.path.exists(cache):
         try:
             got = json.load(open(cache)).get(key)
@@ -97,12 +98,13 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)
         except Exception:
             pass
     log = []
-    best = {"max_k": 4, "threads": 256, "smem_max_n": 12, "ctas": 2 * sms, "split_min_n": 15, "tile_log2": 12}
+    best = {"max_k": 4, "threads": 256, "smem_max_n": 12, "ctas": 2 * sms, "split_min_n": 15, "tile_log2": 12,
+            "wave_mb": 0}
 
     def measure(cfg, batch=None):
         own = batch is None
         b = batch or Batch(circuits, cfg["max_k"])
-        b.set(cfg["threads"], cfg["smem_max_n"], cfg["ctas"], True, cfg["split_min_n"], cfg["tile_log2"])
+        b.set(cfg["threads"], cfg["smem_max_n"], cfg["ctas"], True, cfg["split_min_n"], cfg["tile_log2"], cfg["wave_mb"])
         ms = b.time(b.run, repeats)
         if own:
             b.free()
@@ -120,6 +122,7 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)
     b = Batch(circuits, best["max_k"])
     for field, values in (("threads", (128, 256, 512)), ("smem_max_n", (0, 11, 12, 13, 14)),
                           ("split_min_n", (0, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
+                          ("wave_mb", (0, 24, 48, 96)),
                           ("ctas", (sms, 2 * sms, 3 * sms, 4 * sms))):
         for v in values:
             if v == best[field]:
@@ -147,9 +150,9 @@ def report(count=256, seed=5):
     circuits = wl.hea_batch(count=count, seed=seed)
     best, log = autotune(circuits, use_cache=False)
     b = Batch(circuits, best["max_k"])
-    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, best["split_min_n"], best["tile_log2"])
+    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, best["split_min_n"], best["tile_log2"], best["wave_mb"])
     t_batch = b.time(b.run)
-    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, 0, best["tile_log2"])
+    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, 0, best["tile_log2"], best["wave_mb"])
     t_nosplit = b.time(b.run)
     t_loop = b.time(b.run_loop, repeats=3)
     traffic = sum(16 * (1 << n) * len([0 for _ in range(B.sv_fused_count(f))]) for n, f in zip(b.ns, b.fused))

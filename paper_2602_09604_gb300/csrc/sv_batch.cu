@@ -11,7 +11,8 @@
 //     of step s waits (bounded spin) until every tile of step s-1 of its circuit has finished.
 //     Items are dequeued in list order and a dequeued item is held by a running CTA, so the tiles
 //     waited on were taken earlier and finish (by induction on list position): no deadlock.  The
-//     list interleaves the large circuits step by step, so a wait overlaps other circuits' work.
+//     list interleaves the large circuits step by step, so a wait overlaps other circuits' work,
+//     optionally in waves of at most `wave_mb` MB of state so that a wave stays in L2.
 // States use the library's blocked layout (32 reals then 32 imaginaries per 256-byte block).
 // The launch can be captured once in a CUDA graph and replayed.
 #include <algorithm>
@@ -278,12 +279,12 @@ struct sv_batch {
     int *d_err = nullptr;            // library's device error word (not owned)
     int n_items = 0;
     int n_counters = 0;
-    int list_cfg[3] = {-1, -1, -1};  // smem_max_n, split_min_n, tile_log2
+    int list_cfg[4] = {-1, -1, -1, -1};   // smem_max_n, split_min_n, tile_log2, wave_mb
     bool stall = false;              // test hook: first split step counts one tile too many
     bool list_stall = false;
     sv_batch_opts opts{};
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[5] = {0, 0, 0, 0, 0};
+    int graph_cfg[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -300,7 +301,7 @@ size_t smem_bytes(const sv_batch_opts &o)
 // held in shared memory (short; they fill the tail).
 int build_work_list(sv_batch *b)
 {
-    const int cfg[3] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2};
+    const int cfg[4] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb};
     if (b->d_items && std::memcmp(cfg, b->list_cfg, sizeof(cfg)) == 0 && b->list_stall == b->stall) return SV_OK;
     std::vector<BItem> items;
     std::vector<int> need;
@@ -324,16 +325,33 @@ int build_work_list(sv_batch *b)
             items.push_back(BItem{kSingle, c, 0, 0});
         }
     }
-    for (int s = 0;; ++s) {
-        bool any = false;
+    // split circuits in waves of at most wave_mb MB of state (0: one wave), so a wave's states can
+    // stay in L2 while its steps run; inside a wave the circuits' steps interleave level by level
+    std::vector<std::vector<int>> waves;
+    {
+        const size_t cap = (size_t)b->opts.wave_mb << 20;
+        size_t acc = 0;
         for (int c : split) {
-            if (s > hc[(size_t)c].gate_count) continue;
-            any = true;
-            const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
-            for (int i = 0; i < t; ++i) items.push_back(BItem{kTile, c, s, i});
+            const size_t bytes = sizeof(float) * (size_t)state_floats(hc[(size_t)c].n);
+            if (waves.empty() || (cap > 0 && acc + bytes > cap && acc > 0)) {
+                waves.emplace_back();
+                acc = 0;
+            }
+            waves.back().push_back(c);
+            acc += bytes;
         }
-        if (!any) break;
     }
+    for (const std::vector<int> &wave : waves)
+        for (int s = 0;; ++s) {
+            bool any = false;
+            for (int c : wave) {
+                if (s > hc[(size_t)c].gate_count) continue;
+                any = true;
+                const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
+                for (int i = 0; i < t; ++i) items.push_back(BItem{kTile, c, s, i});
+            }
+            if (!any) break;
+        }
     for (int c = 0; c < (int)hc.size(); ++c)
         if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0});
     if (b->stall && !need.empty()) need[0] += 1;   // nothing completes the extra tile: its waiters give up
@@ -387,6 +405,7 @@ int check_opts(const sv_batch_opts &o)
     if (o.ctas < 1) { set_error("sv_batch: ctas must be >= 1"); return SV_EINVAL; }
     if (o.split_min_n < 0 || o.split_min_n > kBatchMaxN) { set_error("sv_batch: split_min_n must be in [0, %d]", kBatchMaxN); return SV_EINVAL; }
     if (o.tile_log2 < 5 || o.tile_log2 > 16) { set_error("sv_batch: tile_log2 must be in [5, 16]"); return SV_EINVAL; }
+    if (o.wave_mb < 0 || o.wave_mb > (1 << 20)) { set_error("sv_batch: wave_mb must be in [0, 2^20]"); return SV_EINVAL; }
     return SV_OK;
 }
 
@@ -483,6 +502,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     b->opts.use_graph = 1;
     b->opts.split_min_n = 15;
     b->opts.tile_log2 = 12;
+    b->opts.wave_mb = 0;
     *out = b;
     return SV_OK;
 }
@@ -526,7 +546,7 @@ extern "C" int sv_batch_run(sv_batch *b)
     SV_TRY(check_opts(b->opts));
     SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
     const bool relist = !b->d_items || b->list_cfg[0] != b->opts.smem_max_n || b->list_cfg[1] != b->opts.split_min_n ||
-                        b->list_cfg[2] != b->opts.tile_log2 || b->list_stall != b->stall;
+                        b->list_cfg[2] != b->opts.tile_log2 || b->list_cfg[3] != b->opts.wave_mb || b->list_stall != b->stall;
     if (relist) {
         // the captured graph holds the old list's pointers
         SV_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -537,7 +557,7 @@ extern "C" int sv_batch_run(sv_batch *b)
         SV_TRY(build_work_list(b));
     }
     if (!b->opts.use_graph) return launch_batch(b);
-    const int cfg[5] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2};
+    const int cfg[6] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb};
     if (b->graph && std::memcmp(cfg, b->graph_cfg, sizeof(cfg)) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;

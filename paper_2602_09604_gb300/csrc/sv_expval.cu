@@ -12,7 +12,8 @@
 // Strings with the same x read the same pairs of amplitudes, so up to kEvMaxStrings of them are
 // evaluated in one pass: each amplitude is read once, its term conj(c_(j^x)) c_j is formed once in
 // fp32, and every string adds it with its own sign into a float-float accumulator (two-sum); the
-// per-thread results are combined in fp64, per CTA and then in a fixed order by the last CTA.
+// per-thread results are combined in fp64, per CTA and then by the last CTA in a fixed order
+// (strided per-thread sums, then a fixed-shape tree), so results are deterministic.
 //
 // Work unit = one block (x has no bit >= 5) or one pair of blocks b, b ^ (x >> 5) with bit
 // `pair_bit` of b clear (otherwise); a warp reads each block's 32 real and 32 imaginary parts with
@@ -182,14 +183,30 @@ __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restr
         last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && (int)threadIdx.x < a.m) {
-        __threadfence();
+    if (!last) return;
+    // last CTA: every thread sums a fixed strided subset of the partials, then a fixed-shape tree
+    __threadfence();
+    __shared__ double red[kEvThreads][M];
+    {
         const volatile double *pp = partials;
-        double s = 0.0;
-        for (unsigned i = 0; i < gridDim.x; ++i) s += pp[(size_t)i * M + threadIdx.x];   // fixed order
-        result[threadIdx.x] = s;
+        double s[M];
+#pragma unroll
+        for (int p = 0; p < M; ++p) s[p] = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += kEvThreads)
+#pragma unroll
+            for (int p = 0; p < M; ++p) s[p] += pp[(size_t)i * M + p];
+#pragma unroll
+        for (int p = 0; p < M; ++p) red[threadIdx.x][p] = s[p];
     }
-    if (last && threadIdx.x == 0) *counter = 0u;   // ready for the next launch
+    __syncthreads();
+    for (int w = kEvThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int p = 0; p < M; ++p) red[threadIdx.x][p] += red[threadIdx.x + w][p];
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < a.m) result[threadIdx.x] = red[0][threadIdx.x];
+    if (threadIdx.x == 0) *counter = 0u;   // ready for the next launch
 }
 
 template <int M>

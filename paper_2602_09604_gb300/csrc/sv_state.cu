@@ -131,12 +131,23 @@ __global__ void __launch_bounds__(kRedThreads) norm_kernel(const float *__restri
         last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double s = 0.0;
+    if (!last) return;
+    // last CTA: strided per-thread sums of the partials, then a fixed-shape tree (deterministic)
+    __threadfence();
+    __shared__ double red[kRedThreads];
+    {
         const volatile double *p = partials;
-        for (unsigned i = 0; i < gridDim.x; ++i) s += p[i];   // fixed order: deterministic
-        *result = s;
+        double s = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += kRedThreads) s += p[i];
+        red[threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *result = red[0];
         *counter = 0u;   // ready for the next call
     }
 }

@@ -28,19 +28,20 @@ def test_batch_matches_oracle_every_tier(env):
     rng = np.random.default_rng(9)
     circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [5, 16, 9, 3, 14, 12, 7, 15, 10, 13, 1, 11]]
     refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
-    # (threads, smem_max_n, ctas, split_min_n, tile_log2)
-    configs = [(128, 0, 7, 0, 12), (512, 12, 7, 0, 12), (256, 14, 7, 0, 12),
-               (256, 9, 7, 6, 5), (128, 0, 1, 1, 7), (512, 12, 300, 13, 12), (256, 10, 19, 11, 8)]
+    # (threads, smem_max_n, ctas, split_min_n, tile_log2, wave_mb)
+    configs = [(128, 0, 7, 0, 12, 0), (512, 12, 7, 0, 12, 0), (256, 14, 7, 0, 12, 0),
+               (256, 9, 7, 6, 5, 0), (128, 0, 1, 1, 7, 1), (512, 12, 300, 13, 12, 0), (256, 10, 19, 11, 8, 1),
+               (256, 0, 40, 8, 6, 1)]
     for max_k in (2, 3, 4):
         b = batch.Batch(circuits, max_k)
-        for threads, smem_n, ctas, split_n, tl in configs:
-            b.set(threads, smem_n, ctas, True, split_n, tl)
+        for threads, smem_n, ctas, split_n, tl, wave in configs:
+            b.set(threads, smem_n, ctas, True, split_n, tl, wave)
             b.arena.fill_(float("nan"))
             b.run()
             B.sv_device_status()
             for i, ref in enumerate(refs):
                 got = b.state(i)
-                cfg = (max_k, threads, smem_n, ctas, split_n, tl, i)
+                cfg = (max_k, threads, smem_n, ctas, split_n, tl, wave, i)
                 assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
                 assert oracle.l2_error(ref, got) <= 1e-4, cfg
         b.free()
@@ -129,8 +130,9 @@ def test_batch_rejects_bad_input(env):
         B.sv_batch_create([f2], buf.data_ptr(), 64)                   # arena too small
     assert e.value.code == B.SV_ENOMEM
     h = B.sv_batch_create([f2], buf.data_ptr(), buf.numel() * 4)
-    for bad in (dict(threads=1024), dict(split_min_n=25), dict(tile_log2=4), dict(tile_log2=17), dict(smem_max_n=15)):
-        kw = dict(threads=256, smem_max_n=12, ctas=8, use_graph=True, split_min_n=15, tile_log2=12)
+    for bad in (dict(threads=1024), dict(split_min_n=25), dict(tile_log2=4), dict(tile_log2=17), dict(smem_max_n=15),
+                dict(wave_mb=-1)):
+        kw = dict(threads=256, smem_max_n=12, ctas=8, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0)
         kw.update(bad)
         with pytest.raises(B.SvError) as e:
             B.sv_batch_set_opts(h, **kw)
