@@ -41,6 +41,12 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;
 constexpr long long kWaitIters = 4000000;   // ~0.3 s with the backoff below
+// k = 6 gates with no target below qubit 5 use the shared-memory-A direct kernel (two accumulators
+// per warpgroup, so the products overlap the previous tile's stores): measured at n = 30 it beats
+// the tensor-memory-A direct variant there (5.80 vs 5.53 TB/s) but not with one or two low targets
+// (5.09 vs 5.32: its 192 KB of shared memory leaves little L1 for their partial-line accesses) nor
+// for k = 5 (6.17-6.26 vs 6.53-6.56: four warpgroups per SM already overlap the products).
+constexpr bool kDirectSmemA = true;
 
 enum : int { kModeTF32 = 0, kModeBF16X3 = 1 };
 
@@ -189,6 +195,13 @@ struct TcShape {
     static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
     static constexpr int TMEM_COLS = 2 * WG_COLS < 32 ? 32 : 2 * WG_COLS;   // two warpgroups
     static constexpr int KSTEP = MODE == kModeTF32 ? 8 : 16;           // K per instruction
+    // direct kernel with A in shared memory: per warpgroup the A image(s) for M = 128 rows in the
+    // K-major no-swizzle core-matrix layout, two accumulators in tensor memory
+    static constexpr int A_IMG_SMEM = kTcM * KD * ESZ;
+    static constexpr int A_SMEM = NIMG * A_IMG_SMEM;
+    static constexpr int LBO_A = (kTcM / 8) * 128;                     // next 16-byte K chunk of A
+    static constexpr int SMEM_DIRECT2 = B_BYTES + 2 * A_SMEM + 256;
+    static constexpr int TMEM_COLS_D2 = 4 * KD < 32 ? 32 : 4 * KD;     // 2 warpgroups x 2 accumulators
     // CTAs per SM the registers allow: the direct variant gains from more concurrent warpgroup
     // pipelines; the staged one needs more registers (its shared-memory traffic) and spills if capped
     static constexpr int MIN_BLOCKS_DIRECT = K == 6 ? 1 : (K == 5 ? 2 : 3);
@@ -568,6 +581,210 @@ __global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN
     }
 }
 
+// Direct kernel, shared-memory A form (used for k = 6 with no target below qubit 5).  Like the direct
+// variant above, lane m of a warpgroup owns group 128 t + m of its tile t and moves its amplitudes
+// straight between registers and global memory, but the tile's A operand is written to shared
+// memory (16-byte stores in the K-major core-matrix layout) instead of tensor memory.  That frees
+// tensor memory for two accumulators per warpgroup, so the products of tile t run while the
+// warpgroup stores the results of tile t - 1:
+//   load(t+1) -> epilogue(t-1) from the other accumulator -> wait MMA(t) -> build A(t+1)
+//   -> MMA(t+1) into the accumulator epilogue(t-1) just emptied.
+template <int K, int MODE>
+__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
+    apply_tc_direct_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    using S = TcShape<K, MODE>;
+    constexpr int D = S::D;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int wg = tid >> 7;
+    const int warp = tid >> 5;
+    const int m = tid & 127;   // this thread's row in the warpgroup's tiles
+    unsigned char *sB = smem;
+    unsigned char *sA = smem + S::B_BYTES + wg * S::A_SMEM;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 2 * S::A_SMEM);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 5);
+    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
+    const uint32_t bar_b = smem_u32(&bars[0]);
+    const uint32_t bar_d0 = smem_u32(&bars[1 + 2 * wg]), bar_d1 = smem_u32(&bars[2 + 2 * wg]);
+
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        status[0] = 0;
+        status[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)S::TMEM_COLS_D2)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t t_lane = ((uint32_t)((warp & 3) * 32)) << 16;     // this warp's lane quarter
+    const uint32_t tD0 = tmem + (uint32_t)(wg * 2 * S::KD), tD1 = tD0 + (uint32_t)S::KD;   // the two accumulators
+
+    if (tid == 0) {   // B image: bulk copies of up to 32 KB, all completing on bar_b
+        mbar_arrive_expect_tx(bar_b, a.bbytes);
+        for (unsigned off = 0; off < a.bbytes; off += 32768u) {
+            const unsigned sz = a.bbytes - off < 32768u ? a.bbytes - off : 32768u;
+            bulk_g2s(smem_u32(sB + off), static_cast<const unsigned char *>(a.bimg) + off, sz, bar_b);
+        }
+    }
+    const uint32_t idesc = (1u << 4) | ((MODE == kModeTF32 ? 2u : 1u) << 7) | ((MODE == kModeTF32 ? 2u : 1u) << 10) |
+                           ((uint32_t)(S::KD >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+    // row m, 16-byte K chunk kc of image img: img * A_IMG_SMEM + kc * LBO_A + (m / 8) * 128 + (m % 8) * 16
+    const uint32_t a_base = smem_u32(sA);
+    const uint32_t a_row = a_base + (uint32_t)((m >> 3) * 128 + (m & 7) * 16);
+
+    float xd[2 * D];   // the row's inputs: real parts of amplitudes 0..D-1, then imaginary parts
+    long long fb_next = 0;
+    bool v_next = false;
+    auto load = [&](long long tile) {
+        const long long g = tile * kTcM + m;
+        v_next = g < a.n_groups;
+        fb_next = 0;
+        if (v_next) {
+            unsigned long long b = (unsigned long long)g;
+#pragma unroll
+            for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
+            fb_next = (long long)(((b >> 5) << 6) | (b & 31ull));
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                xd[j] = sv[fb_next + a.foff[j]];
+                xd[D + j] = sv[fb_next + a.foff[j] + 32];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2 * D; ++j) xd[j] = 0.f;
+        }
+    };
+    auto st16 = [](uint32_t addr, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w0), "r"(w1), "r"(w2), "r"(w3) : "memory");
+    };
+    auto build_a = [&]() {
+        if constexpr (MODE == kModeTF32) {
+#pragma unroll
+            for (int kc = 0; kc < S::KD / 4; ++kc)
+                st16(a_row + (uint32_t)(kc * S::LBO_A), f32_to_tf32(xd[4 * kc]), f32_to_tf32(xd[4 * kc + 1]),
+                     f32_to_tf32(xd[4 * kc + 2]), f32_to_tf32(xd[4 * kc + 3]));
+        } else {
+#pragma unroll
+            for (int kc = 0; kc < S::KD / 8; ++kc) {
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float x0 = xd[8 * kc + 2 * q], x1 = xd[8 * kc + 2 * q + 1];
+                    hi[q] = pack_bf16x2(x0, x1);   // element 2q in the low half
+                    const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xffff0000u);
+                    lo[q] = pack_bf16x2(x0 - h0, x1 - h1);
+                }
+                st16(a_row + (uint32_t)(kc * S::LBO_A), hi[0], hi[1], hi[2], hi[3]);
+                st16(a_row + (uint32_t)(S::A_IMG_SMEM + kc * S::LBO_A), lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+        fence_proxy_async();   // these generic-proxy writes are read by the tensor core (async proxy)
+    };
+    auto issue = [&](int slot) {   // one thread per warpgroup
+        const uint32_t b0 = smem_u32(sB);
+        constexpr int NSTEP = S::KD / S::KSTEP;
+        constexpr int CH = S::KSTEP / S::EPC;           // 16-byte chunks per instruction (2)
+        if constexpr (MODE == kModeTF32) {
+#pragma unroll
+            for (int st = 0; st < NSTEP; ++st)
+                mma<MODE>(slot ? tD1 : tD0, sdesc(a_base + st * CH * S::LBO_A, S::LBO_A, 128), sdesc(b0 + st * CH * S::LBO_B, S::LBO_B, 128),
+                          idesc, st > 0);
+        } else {
+            const uint32_t a_img[3] = {a_base, a_base, a_base + (uint32_t)S::A_IMG_SMEM};   // hi, hi, lo
+            const uint32_t b_img[3] = {b0, b0 + (uint32_t)S::B_IMG, b0};                    // hi, lo, hi
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int st = 0; st < NSTEP; ++st)
+                    mma<MODE>(slot ? tD1 : tD0, sdesc(a_img[p] + st * CH * S::LBO_A, S::LBO_A, 128),
+                              sdesc(b_img[p] + st * CH * S::LBO_B, S::LBO_B, 128), idesc, (p > 0 || st > 0));
+        }
+        mma_commit(slot ? bar_d1 : bar_d0);
+    };
+    auto epilogue = [&](int slot, long long fb, bool valid) {
+        const uint32_t td = (slot ? tD1 : tD0) + t_lane;
+#pragma unroll
+        for (int cb = 0; cb < S::KD / 16; ++cb) {
+            float v[16];
+            tmem_ld16(td + cb * 16, v);
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = cb * 16 + i;           // column (c', r): c' = col / D, r = col % D
+                    sv[fb + a.foff[col % D] + (col >= D ? 32 : 0)] = v[i];
+                }
+            }
+        }
+    };
+
+    const long long tstride = 2ll * gridDim.x;
+    long long tile = blockIdx.x + (long long)wg * gridDim.x;
+    const bool lead = m == 0;
+    uint32_t phase0 = 0u, phase1 = 0u;
+    int slot = 0;   // accumulator of the tile whose products are in flight
+    bool ok = true;
+    long long fb_cur = 0, fb_prev = 0;
+    bool v_cur = false, v_prev = false, have_prev = false;
+    if (tile < a.n_mma_tiles) {
+        load(tile);
+        fb_cur = fb_next;
+        v_cur = v_next;
+        build_a();
+        wg_sync(wg);
+        if (lead) {
+            tc_fence_after();
+            if (!mbar_wait_bounded(bar_b, 0)) status[wg] = 1;
+            else issue(0);
+        }
+        wg_sync(wg);
+        ok = status[wg] == 0;
+    }
+    while (ok && tile < a.n_mma_tiles) {
+        const long long nt = tile + tstride;
+        if (nt < a.n_mma_tiles) load(nt);                     // in flight during the epilogue and the wait
+        if (have_prev) epilogue(slot ^ 1, fb_prev, v_prev);   // overlaps the products of `tile`
+        if (lead && !mbar_wait_bounded(slot ? bar_d1 : bar_d0, slot ? phase1 : phase0)) status[wg] = 2;
+        tc_fence_before();
+        wg_sync(wg);
+        if (status[wg] != 0) { ok = false; break; }
+        if (slot) phase1 ^= 1u;
+        else phase0 ^= 1u;
+        tc_fence_after();
+        fb_prev = fb_cur;
+        v_prev = v_cur;
+        have_prev = true;
+        if (nt < a.n_mma_tiles) {
+            fb_cur = fb_next;
+            v_cur = v_next;
+            build_a();                                        // A is free: the products of `tile` are done
+            wg_sync(wg);
+            if (lead) {
+                tc_fence_after();
+                issue(slot ^ 1);                              // into the accumulator the epilogue emptied
+            }
+        }
+        slot ^= 1;
+        tile = nt;
+    }
+    if (ok && have_prev) epilogue(slot ^ 1, fb_prev, v_prev);
+    if (!ok && lead) atomicOr(a.err, status[wg] == 1 ? 0x10 : 0x20);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS_D2) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------------------------------- host
 uint16_t bf16_rn(double v)
 {
@@ -688,18 +905,21 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bimg = dtc;
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
-    auto kern = staged ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
-    const int smem = staged ? S::SMEM_STAGED : S::SMEM_DIRECT;
-    static bool attr_set[2] = {false, false};
+    const int variant = staged ? 1 : (kDirectSmemA && K == 6 && nlow == 0 ? 2 : 0);
+    auto kern = variant == 1 ? apply_tc_kernel<K, MODE, true>
+                             : (variant == 2 ? apply_tc_direct_kernel<K, MODE> : apply_tc_kernel<K, MODE, false>);
+    const int smem = variant == 1 ? S::SMEM_STAGED : (variant == 2 ? S::SMEM_DIRECT2 : S::SMEM_DIRECT);
+    const int tmem_cols = variant == 2 ? S::TMEM_COLS_D2 : S::TMEM_COLS;
+    static bool attr_set[3] = {false, false, false};
     {
         std::lock_guard<std::mutex> lk(g_tc_mu);
-        if (!attr_set[staged]) {
+        if (!attr_set[variant]) {
             SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr_set[staged] = true;
+            attr_set[variant] = true;
         }
     }
     // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
-    const int by_tmem = std::max(1, 512 / S::TMEM_COLS);
+    const int by_tmem = std::max(1, 512 / tmem_cols);
     const int by_smem = std::max(1, (227 * 1024) / (smem + 1024));
     const int per_sm = std::min(staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT, std::min(by_tmem, by_smem));
     const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
