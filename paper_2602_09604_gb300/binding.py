@@ -168,34 +168,46 @@ def sv_store(h, dst_ptr: int, on_host: bool) -> None:
 
 
 # --------------------------------------------------------------------------------------- fusion
+_GATE_DTYPE = np.dtype({"names": ["k", "targets", "n_controls", "controls", "mat"],
+                        "formats": [np.int32, (np.int32, MAX_K), np.int32, (np.int32, MAX_CONTROLS), np.uint64],
+                        "offsets": [sv_gate.k.offset, sv_gate.targets.offset, sv_gate.n_controls.offset,
+                                    sv_gate.controls.offset, sv_gate.mat.offset],
+                        "itemsize": ctypes.sizeof(sv_gate)})
+
+
 def gate_array(gates):
-    """ctypes array of sv_gate for gate objects with .targets/.controls/.matrix; returns
-    (array, keepalive) -- keep both alive for the duration of the call."""
+    """sv_gate records for gate objects with .targets/.controls/.matrix, built as one numpy
+    structured array laid out like the C struct (matrices packed into one complex128 buffer);
+    returns (pointer to the records, keepalive) -- keep both alive for the duration of the call."""
     gates = list(gates)
-    arr = (sv_gate * max(len(gates), 1))()
-    keep = []
-    for i, g in enumerate(gates):
-        if len(g.targets) > MAX_K or len(tuple(g.controls)) > MAX_CONTROLS:
+    n = len(gates)
+    rec = np.zeros(max(n, 1), dtype=_GATE_DTYPE)
+    tl = [tuple(int(q) for q in g.targets) for g in gates]
+    cl = [tuple(int(q) for q in g.controls) for g in gates]
+    for i, (t, c) in enumerate(zip(tl, cl)):
+        if len(t) > MAX_K or len(c) > MAX_CONTROLS:
             raise SvError(SV_EINVAL, f"gate {i}: sv_gate holds at most {MAX_K} targets and {MAX_CONTROLS} controls")
-        m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128))
-        keep.append(m)
-        arr[i].k = len(g.targets)
-        for j, t in enumerate(g.targets):
-            arr[i].targets[j] = int(t)
-        ctl = tuple(g.controls)
-        arr[i].n_controls = len(ctl)
-        for j, c in enumerate(ctl):
-            arr[i].controls[j] = int(c)
-        arr[i].mat = m.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    return arr, keep
+    mats = [np.asarray(g.matrix, dtype=np.complex128).reshape(-1) for g in gates]
+    buf = np.concatenate(mats) if mats else np.zeros(1, dtype=np.complex128)
+    if n:
+        rec["k"][:n] = [len(t) for t in tl]
+        rec["targets"][:n] = [t + (0,) * (MAX_K - len(t)) for t in tl]
+        rec["n_controls"][:n] = [len(c) for c in cl]
+        for i, c in enumerate(cl):
+            if c:
+                rec["controls"][i, :len(c)] = c
+        offs = np.cumsum([0] + [m.size for m in mats[:-1]], dtype=np.uint64)
+        rec["mat"][:n] = np.uint64(buf.ctypes.data) + np.uint64(16) * offs
+    return rec.ctypes.data_as(ctypes.POINTER(sv_gate)), (rec, buf)
 
 
 def sv_fuse_circuit(gates, n: int, max_k: int = 4, mode: int = FUSE_GREEDY, precision: int = PREC_FP32,
                     tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None) -> ctypes.c_void_p:
-    arr, keep = gate_array(gates)
+    gl = list(gates)
+    arr, keep = gate_array(gl)
     opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model)
     f = ctypes.c_void_p()
-    _check(lib.sv_fuse_circuit(arr, len(keep), n, ctypes.byref(opts), ctypes.byref(f)))
+    _check(lib.sv_fuse_circuit(arr, len(gl), n, ctypes.byref(opts), ctypes.byref(f)))
     return f
 
 

@@ -13,6 +13,7 @@
 // over the blocks before it that share no qubit with it (they commute) and merges into the first
 // block it meets whose union with it still has at most max_k qubits.
 #include <algorithm>
+#include <future>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -34,8 +35,10 @@ struct Block {
 };
 
 // mat (dim x dim, acting on qubit list T) <- G * mat, where G acts on qubits gq (local bit b of G
-// <-> gq[b], every gq[b] in T).  Column by column, each column is a vector over T and G is
-// applied to every group of its entries that differ only in G's bits.
+// <-> gq[b], every gq[b] in T).  G mixes the rows of mat whose indices differ only in G's bits:
+// for each such group of rows (visited through its all-zero member), the gd rows are replaced by
+// G times them, one whole row (every column) at a time so the inner loop runs over contiguous
+// memory.
 void left_multiply(std::vector<cplx> &mat, const std::vector<int> &T, const std::vector<cplx> &G,
                    const std::vector<int> &gq)
 {
@@ -56,18 +59,35 @@ void left_multiply(std::vector<cplx> &mat, const std::vector<int> &T, const std:
             if ((j >> b) & 1) o |= size_t(1) << pos[b];
         off[j] = o;
     }
-    std::vector<cplx> x(gd), y(gd);
-    for (size_t col = 0; col < dim; ++col) {
-        for (size_t base = 0; base < dim; ++base) {
-            if (base & gmask) continue;  // visit each group once, through its all-zero member
-            for (size_t j = 0; j < gd; ++j) x[j] = mat[(base | off[j]) * dim + col];
-            for (size_t r = 0; r < gd; ++r) {
-                cplx acc = 0.0;
-                const cplx *grow = &G[r * gd];
-                for (size_t j = 0; j < gd; ++j) acc += grow[j] * x[j];
-                y[r] = acc;
+    // rows as separate real / imaginary arrays so the column loop vectorises
+    std::vector<double> xr(gd * dim), xi(gd * dim), yr(dim), yi(dim);
+    double *m = reinterpret_cast<double *>(mat.data());
+    for (size_t base = 0; base < dim; ++base) {
+        if (base & gmask) continue;
+        for (size_t j = 0; j < gd; ++j) {
+            const double *row = m + 2 * (base | off[j]) * dim;
+            double *dr = &xr[j * dim], *di = &xi[j * dim];
+            for (size_t c = 0; c < dim; ++c) {
+                dr[c] = row[2 * c];
+                di[c] = row[2 * c + 1];
             }
-            for (size_t r = 0; r < gd; ++r) mat[(base | off[r]) * dim + col] = y[r];
+        }
+        for (size_t r = 0; r < gd; ++r) {
+            for (size_t c = 0; c < dim; ++c) yr[c] = yi[c] = 0.0;
+            for (size_t j = 0; j < gd; ++j) {
+                const double gr = G[r * gd + j].real(), gi = G[r * gd + j].imag();
+                if (gr == 0.0 && gi == 0.0) continue;
+                const double *sr = &xr[j * dim], *si = &xi[j * dim];
+                for (size_t c = 0; c < dim; ++c) {
+                    yr[c] += gr * sr[c] - gi * si[c];
+                    yi[c] += gr * si[c] + gi * sr[c];
+                }
+            }
+            double *row = m + 2 * (base | off[r]) * dim;
+            for (size_t c = 0; c < dim; ++c) {
+                row[2 * c] = yr[c];
+                row[2 * c + 1] = yi[c];
+            }
         }
     }
 }
@@ -422,7 +442,12 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             // learned: every greedy partition up to max_k, every allowed kernel path per fused
             // gate, scored by the cost model in one batched forward pass; keep the cheapest
             std::vector<std::vector<Block>> cand;
-            for (int k = 2; k <= std::max(2, opts.max_k); ++k) cand.push_back(greedy_partition(dense, n_qubits, k));
+            {   // the candidate partitions are independent: build them on host threads
+                std::vector<std::future<std::vector<Block>>> jobs;
+                for (int k = 2; k <= std::max(2, opts.max_k); ++k)
+                    jobs.push_back(std::async(std::launch::async, [&dense, n_qubits, k]() { return greedy_partition(dense, n_qubits, k); }));
+                for (auto &j : jobs) cand.push_back(j.get());
+            }
             std::vector<float> X;
             std::vector<int> row_path;
             std::vector<std::vector<std::pair<int, int>>> rows_of;   // per candidate, per block: [first row, count)
@@ -474,6 +499,10 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     } catch (const std::bad_alloc &) {
         delete f;
         set_error("sv_fuse_circuit: out of host memory");
+        return SV_ENOMEM;
+    } catch (const std::exception &e) {   // e.g. no host thread for a candidate partition
+        delete f;
+        set_error("sv_fuse_circuit: %s", e.what());
         return SV_ENOMEM;
     }
     *out = f;
