@@ -66,18 +66,41 @@ __device__ __forceinline__ unsigned long long bins0(unsigned long long x, int p)
 
 __device__ __forceinline__ long long boff(unsigned long long i) { return (long long)(((i >> 5) << 6) | (i & 31ull)); }
 
-// Apply one fused gate of K qubits to the state S (shared or global) of n <= 24 qubits with all
-// threads of the CTA; U (float2, row-major 2^K x 2^K) is in shared memory.  Offsets are 32-bit
-// and recomputed for the stores, so a thread holds only its group's 2^(K+1) values.
-template <int K, bool L2ONLY>
-__device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
+template <int V, bool L2ONLY>
+__device__ __forceinline__ void ld_v(const float *p, float (&v)[V])
+{
+    if constexpr (V == 4) {
+        const float4 t = L2ONLY ? __ldcg(reinterpret_cast<const float4 *>(p)) : *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (V == 2) {
+        const float2 t = L2ONLY ? __ldcg(reinterpret_cast<const float2 *>(p)) : *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = L2ONLY ? __ldcg(p) : *p;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st_v(float *p, const float (&v)[V])
+{
+    if constexpr (V == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else *p = v[0];
+}
+
+// Apply one fused gate of K qubits to groups [g_begin, g_end) of the state S (shared or global)
+// of n <= 24 qubits with all threads of the CTA; U (float2, row-major 2^K x 2^K) is in shared
+// memory.  A thread takes V consecutive groups at a time: with no target below log2(V) their
+// amplitudes are V consecutive positions of a block, moved with one V-wide access (and each
+// matrix element read once serves V groups).  Offsets are 32-bit and recomputed for the stores.
+template <int K, int V, bool L2ONLY>
+__device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
 {
     constexpr int D = 1 << K;
     unsigned bit[K];
 #pragma unroll
     for (int b = 0; b < K; ++b) bit[b] = 1u << g.targets[b];
-    (void)n;
-    for (unsigned grp = g_begin + threadIdx.x; grp < g_end; grp += blockDim.x) {
+    for (unsigned it = g_begin / V + threadIdx.x; it < g_end / V; it += blockDim.x) {
         // the matrix pointer goes through an opaque move each iteration: otherwise the 4^K
         // loop-invariant matrix loads are hoisted out of this loop into registers
         const float2 *Ui;
@@ -86,13 +109,13 @@ __device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__re
             asm volatile("mov.b64 %0, %0;" : "+l"(v));
             Ui = reinterpret_cast<const float2 *>(v);
         }
-        unsigned base = grp;
+        unsigned base = it * V;
 #pragma unroll
         for (int b = 0; b < K; ++b) {
             const unsigned low = base & (bit[b] - 1u);
             base = ((base - low) << 1) | low;
         }
-        float xr[D], xi[D];
+        float xr[D][V], xi[D][V];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             unsigned i = base;
@@ -100,45 +123,61 @@ __device__ void apply_in_cta(float *S, int n, const BGate &g, const float2 *__re
             for (int b = 0; b < K; ++b)
                 if ((j >> b) & 1) i |= bit[b];
             const unsigned o = ((i >> 5) << 6) | (i & 31u);
-            if constexpr (L2ONLY) {   // other CTAs wrote these: read through L2, not a stale L1 line
-                xr[j] = __ldcg(S + o);
-                xi[j] = __ldcg(S + o + 32);
-            } else {
-                xr[j] = S[o];
-                xi[j] = S[o + 32];
-            }
+            // L2ONLY: other CTAs wrote these, so read through L2 rather than a stale L1 line
+            ld_v<V, L2ONLY>(S + o, xr[j]);
+            ld_v<V, L2ONLY>(S + o + 32, xi[j]);
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            float yr = 0.f, yi = 0.f;
+            float yr[V], yi[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) yr[v] = yi[v] = 0.f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const float2 u = Ui[r * D + j];
-                yr = fmaf(u.x, xr[j], yr);
-                yr = fmaf(u.y, -xi[j], yr);
-                yi = fmaf(u.x, xi[j], yi);
-                yi = fmaf(u.y, xr[j], yi);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    yr[v] = fmaf(u.x, xr[j][v], yr[v]);
+                    yr[v] = fmaf(u.y, -xi[j][v], yr[v]);
+                    yi[v] = fmaf(u.x, xi[j][v], yi[v]);
+                    yi[v] = fmaf(u.y, xr[j][v], yi[v]);
+                }
             }
             unsigned i = base;
 #pragma unroll
             for (int b = 0; b < K; ++b)
                 if ((r >> b) & 1) i |= bit[b];
             const unsigned o = ((i >> 5) << 6) | (i & 31u);
-            S[o] = yr;
-            S[o + 32] = yi;
+            st_v<V>(S + o, yr);
+            st_v<V>(S + o + 32, yi);
         }
     }
 }
 
+// V: 4 when no target is below qubit 2, 2 when none is qubit 0, else 1; K = 4 keeps V = 1 (its
+// 2^5 inputs per group already fill the register budget); never more than the 2^(n-K) groups.
 template <bool L2ONLY>
 __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U, unsigned g_begin, unsigned g_end)
 {
+    const int t0 = g.targets[0];   // ascending
+    int v = t0 >= 2 ? 4 : (t0 == 1 ? 2 : 1);
+    if (g.k == 4) v = 1;
+    while (v > 1 && (1 << (n - g.k)) < v) v >>= 1;
+#define SV_BATCH_CASE(KK)                                                         \
+    case KK:                                                                      \
+        if (v == 4) apply_in_cta<KK, 4, L2ONLY>(S, g, U, g_begin, g_end);         \
+        else if (v == 2) apply_in_cta<KK, 2, L2ONLY>(S, g, U, g_begin, g_end);    \
+        else apply_in_cta<KK, 1, L2ONLY>(S, g, U, g_begin, g_end);                \
+        break;
     switch (g.k) {
-    case 1: apply_in_cta<1, L2ONLY>(S, n, g, U, g_begin, g_end); break;
-    case 2: apply_in_cta<2, L2ONLY>(S, n, g, U, g_begin, g_end); break;
-    case 3: apply_in_cta<3, L2ONLY>(S, n, g, U, g_begin, g_end); break;
-    default: apply_in_cta<4, L2ONLY>(S, n, g, U, g_begin, g_end); break;
+    SV_BATCH_CASE(1)
+    SV_BATCH_CASE(2)
+    SV_BATCH_CASE(3)
+    default:
+        apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+        break;
     }
+#undef SV_BATCH_CASE
 }
 
 // blocked-layout float count of an n-qubit state (at least one 64-float block)
