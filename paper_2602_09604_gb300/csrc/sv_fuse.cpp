@@ -221,7 +221,9 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         if (kept.empty()) {
             nb.mat = identity(size_t(1) << nb.qubits.size());
         } else {
-            nb.mat = expand(open[kept[0]].mat, open[kept[0]].qubits, nb.qubits);
+            // the first kept block's matrix moves over unchanged when the gate adds no qubit to it
+            if (open[kept[0]].qubits == nb.qubits) nb.mat = std::move(open[kept[0]].mat);
+            else nb.mat = expand(open[kept[0]].mat, open[kept[0]].qubits, nb.qubits);
             nb.n_src += open[kept[0]].n_src;
             for (size_t i = 1; i < kept.size(); ++i) {
                 left_multiply(nb.mat, nb.qubits, open[kept[i]].mat, open[kept[i]].qubits);
