@@ -154,14 +154,16 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
     }
 }
 
-// V: 4 when no target is below qubit 2, 2 when none is qubit 0, else 1; K = 4 keeps V = 1 (its
-// 2^5 inputs per group already fill the register budget); never more than the 2^(n-K) groups.
-template <bool L2ONLY>
+// V: 4 when no target is below qubit 2, 2 when none is qubit 0, else 1; never more than the
+// 2^(n-K) groups.  WIDE (CTAs of at most 256 threads, up to 255 registers a thread) allows K = 4
+// with V > 1; with 512-thread CTAs (128 registers) K = 4 keeps V = 1, whose 2^5 inputs per group
+// already fill the budget.
+template <bool L2ONLY, bool WIDE>
 __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U, unsigned g_begin, unsigned g_end)
 {
     const int t0 = g.targets[0];   // ascending
     int v = t0 >= 2 ? 4 : (t0 == 1 ? 2 : 1);
-    if (g.k == 4) v = 1;
+    if (g.k == 4 && !WIDE) v = 1;
     while (v > 1 && (1 << (n - g.k)) < v) v >>= 1;
 #define SV_BATCH_CASE(KK)                                                         \
     case KK:                                                                      \
@@ -174,7 +176,13 @@ __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U,
     SV_BATCH_CASE(2)
     SV_BATCH_CASE(3)
     default:
-        apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+        if constexpr (WIDE) {
+            if (v == 4) apply_in_cta<4, 4, L2ONLY>(S, g, U, g_begin, g_end);
+            else if (v == 2) apply_in_cta<4, 2, L2ONLY>(S, g, U, g_begin, g_end);
+            else apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+        } else {
+            apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+        }
         break;
     }
 #undef SV_BATCH_CASE
@@ -211,7 +219,8 @@ __device__ __forceinline__ void zero_floats(float *S, long long f0, long long f1
         reinterpret_cast<float4 *>(S)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A)
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float smem[];
     float2 *sU = reinterpret_cast<float2 *>(smem);                  // (1 << 2*kBatchMaxK) complex
@@ -238,7 +247,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A)
                 const BGate g = A.gates[C.gate_begin + gi];
                 stage_matrix(sU, A.mats, g);
                 __syncthreads();   // matrix staged; previous gate's writes visible
-                apply_gate_cta<false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                apply_gate_cta<false, (MAXT <= 256)>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
                 __syncthreads();
             }
             if (W.kind == kWhole) {
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchArgs A)
             const unsigned groups = 1u << (C.n - g.k);
             const unsigned g0 = (unsigned)W.tile << A.tile_log2;
             const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
-            apply_gate_cta<true>(G, C.n, g, sU, g0, g1);
+            apply_gate_cta<true, (MAXT <= 256)>(G, C.n, g, sU, g0, g1);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -432,7 +441,10 @@ int launch_batch(sv_batch *b)
     a.err = b->d_err;
     a.tile_log2 = b->opts.tile_log2;
     SV_CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, sizeof(int) * (2 + (size_t)b->n_counters), b->stream));
-    batch_kernel<<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
+    if (b->opts.threads <= 256)
+        batch_kernel<256><<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
+    else
+        batch_kernel<512><<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -565,7 +577,8 @@ extern "C" int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *o)
     clear_error();
     if (!b || !o) { set_error("sv_batch_set_opts: NULL argument"); return SV_EINVAL; }
     SV_TRY(check_opts(*o));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
     b->opts = *o;
     return SV_OK;
 }
@@ -583,7 +596,8 @@ extern "C" int sv_batch_run(sv_batch *b)
     clear_error();
     if (!b) { set_error("sv_batch_run: NULL batch"); return SV_EINVAL; }
     SV_TRY(check_opts(b->opts));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
     const bool relist = !b->d_items || b->list_cfg[0] != b->opts.smem_max_n || b->list_cfg[1] != b->opts.split_min_n ||
                         b->list_cfg[2] != b->opts.tile_log2 || b->list_cfg[3] != b->opts.wave_mb || b->list_stall != b->stall;
     if (relist) {
