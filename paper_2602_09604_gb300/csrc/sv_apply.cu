@@ -400,12 +400,20 @@ void fill_mat(T &m, const FusedGate &g, bool column_major)
     }
 }
 
+// Kernel attributes already set, as a bit per device (function attributes are per device).
 struct Occ {
-    int high[7] = {0};
-    int tile[7][4] = {};      // [K][gather + 2 * fixed]: attributes set
+    uint64_t high[7] = {0};
+    uint64_t tile[7][4] = {};   // [K][gather + 2 * fixed]
 };
 Occ g_occ;
 std::mutex g_occ_mu;
+
+uint64_t current_device_bit()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+}
 
 // One group per thread: the base index has a zero inserted at every target and control position
 // (ascending) and the control bits then set; the 2^K amplitudes are gathered, multiplied by U
@@ -483,10 +491,11 @@ int launch_high(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
     const size_t smem = K == 6 ? sizeof(float2) * 64 * 64 : 0;
     auto kern = apply_high_kernel<K>;
     {
+        const uint64_t bit = current_device_bit();
         std::lock_guard<std::mutex> lk(g_occ_mu);
-        if (!g_occ.high[K]) {
-            if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            g_occ.high[K] = 1;
+        if (!(g_occ.high[K] & bit) || !bit) {
+            if (smem > 48 * 1024) SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            g_occ.high[K] |= bit;
         }
     }
     (void)num_sms;
@@ -511,12 +520,14 @@ int launch_tile(float *sv, int n, const FusedGate &g, const float2 *umem, cudaSt
     auto kern = fixed ? (gather ? apply_tile_kernel<K, true, true> : apply_tile_kernel<K, false, true>)
                       : (gather ? apply_tile_kernel<K, true, false> : apply_tile_kernel<K, false, false>);
     {
+        const uint64_t bit = current_device_bit();
         std::lock_guard<std::mutex> lk(g_occ_mu);
-        int &slot = g_occ.tile[K][(gather ? 1 : 0) + (fixed ? 2 : 0)];
-        if (!slot) {
+        uint64_t &slot = g_occ.tile[K][(gather ? 1 : 0) + (fixed ? 2 : 0)];
+        if (!(slot & bit) || !bit) {
             if (smem > 48 * 1024 || K == 6)
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kTileWarps * (64u << 6) * sizeof(float) + sizeof(float2) * 64 * 64));
-            slot = 1;
+                SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(kTileWarps * (64u << 6) * sizeof(float) + sizeof(float2) * 64 * 64)));
+            slot |= bit;
         }
     }
     (void)num_sms;

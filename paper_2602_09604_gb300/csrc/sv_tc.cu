@@ -910,12 +910,15 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
                              : (variant == 2 ? apply_tc_direct_kernel<K, MODE> : apply_tc_kernel<K, MODE, false>);
     const int smem = variant == 1 ? S::SMEM_STAGED : (variant == 2 ? S::SMEM_DIRECT2 : S::SMEM_DIRECT);
     const int tmem_cols = variant == 2 ? S::TMEM_COLS_D2 : S::TMEM_COLS;
-    static bool attr_set[3] = {false, false, false};
+    static uint64_t attr_set[3] = {0, 0, 0};   // a bit per device (function attributes are per device)
     {
+        int dev = 0;
+        SV_CUDA_TRY(cudaGetDevice(&dev));
+        const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
         std::lock_guard<std::mutex> lk(g_tc_mu);
-        if (!attr_set[variant]) {
+        if (!(attr_set[variant] & bit) || !bit) {
             SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr_set[variant] = true;
+            attr_set[variant] |= bit;
         }
     }
     // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
