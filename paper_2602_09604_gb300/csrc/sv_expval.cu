@@ -24,7 +24,9 @@
 // (u - u0) of a 32-bit parity table of zu's low five bits, where zu is zb with the pair bit
 // deleted (b is u with a zero inserted there); these bits are the same in every lane.  The lane
 // part parity(lane & zl) is fixed per thread and applied once at the end.  Each string sums a
-// batch's signed terms in fp32, then adds the batch sum to its float-float accumulator.
+// batch's signed terms in fp32 (with four or more strings, through one 8-point Walsh-Hadamard
+// transform of the batch that serves every string), then adds the batch sum to its float-float
+// accumulator.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -44,6 +46,7 @@ struct EvArgs {
     int pair_bit;             // bit of the block index inserted as 0 to enumerate pairs; -1: no pairing
     unsigned long long zu[kEvMaxStrings];   // z >> 5 with the pair bit deleted (unit-index parity mask)
     unsigned ztab[kEvMaxStrings];           // bit i = parity(i & zu & 31), i < 32
+    unsigned zc[kEvMaxStrings];             // zu & 7: the Walsh-Hadamard entry of a batch of 8 units
     unsigned zl[kEvMaxStrings];             // z & 31
     unsigned pairpar[kEvMaxStrings];        // parity((x >> 5) & (z >> 5)): sign change to the paired block
     int comp[kEvMaxStrings];  // 0: accumulate the real part of the term, 1: the imaginary part
@@ -77,10 +80,33 @@ __device__ __forceinline__ unsigned long long ins_zero(unsigned long long v, int
 }
 
 constexpr int kEvBatch = 8;     // units per batch
+
+// in place: w[c] <- sum_i (-1)^popc(i & c) w[i]
+__device__ __forceinline__ void wht8(float (&w)[8])
+{
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (!(i & h)) {
+                const float x = w[i], y = w[i + h];
+                w[i] = x + y;
+                w[i + h] = x - y;
+            }
+}
+
+// w[c] for a warp-uniform c < 8 without indexing a register array (three levels of selects)
+__device__ __forceinline__ float sel8(const float (&w)[8], unsigned c)
+{
+    const float a0 = (c & 1u) ? w[1] : w[0], a1 = (c & 1u) ? w[3] : w[2];
+    const float a2 = (c & 1u) ? w[5] : w[4], a3 = (c & 1u) ? w[7] : w[6];
+    const float b0 = (c & 2u) ? a1 : a0, b1 = (c & 2u) ? a3 : a2;
+    return (c & 4u) ? b1 : b0;
+}
 constexpr int kEvRange = 32;    // units per warp range (one parity table)
 
 template <int M, bool PAIRED>
-__global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restrict__ sv, const __grid_constant__ EvArgs a,
+__global__ void __launch_bounds__(kEvThreads, M >= 4 ? 3 : 4) expval_kernel(const float *__restrict__ sv, const __grid_constant__ EvArgs a,
                                                            double *__restrict__ partials, unsigned *__restrict__ counter,
                                                            double *__restrict__ result)
 {
@@ -132,27 +158,51 @@ __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restr
                 }
             }
 #pragma unroll
-            for (int p = 0; p < M; ++p) {
-                // block-parity sign bits of the batch's units: warp-uniform; the lane's own parity
-                // (lane & zl) is applied once at the end
-                const unsigned tab = a.ztab[p] >> (bt * kEvBatch);
-                float sum = 0.f;
-                if (a.comp[p] == 0) {
-#pragma unroll
-                    for (int i = 0; i < kEvBatch; ++i) {
-                        const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
-                        sum += __uint_as_float(__float_as_uint(tr[i]) ^ sg);
-                        if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(sr[i]) ^ sg ^ (a.pairpar[p] << 31));
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kEvBatch; ++i) {
-                        const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
-                        sum += __uint_as_float(__float_as_uint(ti[i]) ^ sg);
-                        if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(si[i]) ^ sg ^ (a.pairpar[p] << 31));
-                    }
+            if constexpr (M >= 4) {
+                // many strings: an 8-point Walsh-Hadamard transform of the batch's terms gives,
+                // for every mask c of the batch's unit bits, the sum of the terms signed by
+                // parity(i & c); string p then takes entry zu & 7, signed by the batch's base parity
+                wht8(tr);
+                wht8(ti);
+                if constexpr (PAIRED) {
+                    wht8(sr);
+                    wht8(si);
                 }
-                ff_add(acc[p], sum);
+#pragma unroll
+                for (int p = 0; p < M; ++p) {
+                    const unsigned c = a.zc[p];
+                    const unsigned sg = sgn0[p] ^ (((a.ztab[p] >> (bt * kEvBatch)) & 1u) << 31);
+                    float v = a.comp[p] ? sel8(ti, c) : sel8(tr, c);
+                    if constexpr (PAIRED) {
+                        const float w = a.comp[p] ? sel8(si, c) : sel8(sr, c);
+                        v += __uint_as_float(__float_as_uint(w) ^ (a.pairpar[p] << 31));
+                    }
+                    ff_add(acc[p], __uint_as_float(__float_as_uint(v) ^ sg));
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < M; ++p) {
+                    // block-parity sign bits of the batch's units: warp-uniform; the lane's own
+                    // parity (lane & zl) is applied once at the end
+                    const unsigned tab = a.ztab[p] >> (bt * kEvBatch);
+                    float sum = 0.f;
+                    if (a.comp[p] == 0) {
+#pragma unroll
+                        for (int i = 0; i < kEvBatch; ++i) {
+                            const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
+                            sum += __uint_as_float(__float_as_uint(tr[i]) ^ sg);
+                            if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(sr[i]) ^ sg ^ (a.pairpar[p] << 31));
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kEvBatch; ++i) {
+                            const unsigned sg = sgn0[p] ^ (((tab >> i) & 1u) << 31);
+                            sum += __uint_as_float(__float_as_uint(ti[i]) ^ sg);
+                            if constexpr (PAIRED) sum += __uint_as_float(__float_as_uint(si[i]) ^ sg ^ (a.pairpar[p] << 31));
+                        }
+                    }
+                    ff_add(acc[p], sum);
+                }
             }
         }
     }
@@ -209,11 +259,20 @@ __global__ void __launch_bounds__(kEvThreads) expval_kernel(const float *__restr
     if (threadIdx.x == 0) *counter = 0u;   // ready for the next launch
 }
 
+// The grid is one wave of resident CTAs (occupancy x SMs), capped by the work and by max_grid:
+// every CTA then loops over an equal share of the ranges with no second, partly filled wave.
 template <int M>
-int launch_ev(const float *sv, const EvArgs &a, double *partials, unsigned *counter, double *result, int grid, cudaStream_t s)
+int launch_ev(const float *sv, const EvArgs &a, double *partials, unsigned *counter, double *result, long long work_ctas,
+              int num_sms, int max_grid, cudaStream_t s)
 {
-    if (a.pair_bit >= 0) expval_kernel<M, true><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
-    else expval_kernel<M, false><<<grid, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
+    auto kern = a.pair_bit >= 0 ? expval_kernel<M, true> : expval_kernel<M, false>;
+    int per_sm = 1;
+    SV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEvThreads, 0));
+    long long g = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
+    if (g > max_grid) g = max_grid;
+    if (g > work_ctas) g = work_ctas;
+    if (g < 1) g = 1;
+    kern<<<(unsigned)g, kEvThreads, 0, s>>>(sv, a, partials, counter, result);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -293,22 +352,21 @@ extern "C" int sv_expval_pauli(const sv_state *st_c, const uint64_t *x_masks, co
             unsigned tab = 0;
             for (unsigned i = 0; i < 32; ++i) tab |= (unsigned)(__builtin_popcountll(i & zu & 31ull) & 1) << i;
             a.ztab[p] = tab;
+            a.zc[p] = (unsigned)(zu & 7ull);
             a.zl[p] = (unsigned)(z_masks[s] & 31u);
             a.pairpar[p] = (unsigned)(__builtin_popcountll(a.xb & zb) & 1);
             a.comp[p] = __builtin_popcountll(x & z_masks[s]) & 1;
             slot_of[(size_t)s] = pos + p;
         }
         const long long ranges = (a.n_units + kEvRange - 1) / kEvRange;
-        long long g = (ranges * 32 + kEvThreads - 1) / kEvThreads;
-        if (g > max_grid) g = max_grid;
-        if (g < 1) g = 1;
+        const long long work = (ranges * 32 + kEvThreads - 1) / kEvThreads;   // CTAs with a range per warp
         const float *sv = st->d;
         double *res = results + pos;
         int rc;
-        if (m == 1) rc = launch_ev<1>(sv, a, partials, counter, res, (int)g, st->stream);
-        else if (m == 2) rc = launch_ev<2>(sv, a, partials, counter, res, (int)g, st->stream);
-        else if (m <= 4) rc = launch_ev<4>(sv, a, partials, counter, res, (int)g, st->stream);
-        else rc = launch_ev<8>(sv, a, partials, counter, res, (int)g, st->stream);
+        if (m == 1) rc = launch_ev<1>(sv, a, partials, counter, res, work, st->num_sms, max_grid, st->stream);
+        else if (m == 2) rc = launch_ev<2>(sv, a, partials, counter, res, work, st->num_sms, max_grid, st->stream);
+        else if (m <= 4) rc = launch_ev<4>(sv, a, partials, counter, res, work, st->num_sms, max_grid, st->stream);
+        else rc = launch_ev<8>(sv, a, partials, counter, res, work, st->num_sms, max_grid, st->stream);
         if (rc != SV_OK) return rc;
         pos += m;
     }
