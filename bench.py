@@ -32,6 +32,7 @@ UNIT = "s/circuit"
 N_QUBITS = 30
 N_SAMPLES = 1024
 WORKLOAD = "grid30: 5x6 grid random circuit, 20 cycles, 845 gates, seed 2, |0..0>, complex64"
+FP64_PEAK_TFLOPS = 1.20   # fp64 FMA throughput measured on this GPU (independent FMA chains, all SMs)
 
 
 def peaks():
@@ -317,6 +318,27 @@ def bench_ours(args):
             ctrl[f"k{k}_c{c}"] = {"us": us, "gbs": 16 * (1 << (n - c)) / (us * 1e-6) / 1e9,
                                   "bytes": 16 * (1 << (n - c))}
         next_rows["controlled_gate"] = ctrl
+        # complex128 states: the benchmark circuit in fp64 (bound by fp64 arithmetic, not HBM)
+        c128 = {}
+        st128 = DeviceState(n, stream=stream, c128=True)
+        for mk in (2, 3):
+            fc = B.sv_fuse_circuit(gates, n, max_k=mk)
+            ks = [B.sv_fused_get_info(fc, i)["k"] for i in range(B.sv_fused_count(fc))]
+            B.sv_init(st128.h, 0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.sv_init(st128.h, 0)
+            B.sv_apply_fused_gates(st128.h, fc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            flops = sum((8 * (1 << k) - 2) * (1 << n) for k in ks)
+            c128[f"greedy_k{mk}"] = {"s_per_circuit": sec, "fused_gates": len(ks), "tflops": flops / sec / 1e12,
+                                     "frac_of_fp64_peak": flops / sec / 1e12 / FP64_PEAK_TFLOPS}
+            B.sv_fused_free(fc)
+        st128.free()
+        next_rows["c128_grid30"] = c128
         circ = {"grover30_r3": wl.grover_circuit(n, 0x2C0FFEE1, 3), "qv30": wl.qv_circuit(n, seed=1)}
         for name, gl in circ.items():
             fcirc = B.sv_fuse_circuit(gl, n, **fuse_kw)

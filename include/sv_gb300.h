@@ -250,6 +250,22 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Complex128 states (no counterpart in the paper's single-precision runs).  The same operations
+ * in fp64: amplitudes are complex128 (16 bytes), stored in 512-byte blocks of 32 real then 32
+ * imaginary parts, and fused gates are applied with their fp64 matrices in fp64 arithmetic, so the
+ * result matches the complex128 definition up to summation order.  fp64 arithmetic bounds these
+ * kernels (about 1.2 TFLOP/s of fp64 FMA on GB300, 1/58 of fp32); small fusion sizes (2-3) are
+ * the cheapest.  On a complex128 state sv_init, sv_load / sv_store (interleaved complex128),
+ * sv_apply_fused_gates (every path, including kept controls, runs the fp64 kernel; the tensor-core
+ * and precision options are ignored), sv_norm and sv_sample work as documented above;
+ * sv_expval_pauli returns SV_EINVAL.
+ * ------------------------------------------------------------------------------------------- */
+/* Bytes of a complex128 n-qubit state: 16 * 2^n (at least one 512-byte block); 0 if n is out of range. */
+SV_API size_t sv_required_bytes_c128(int n_qubits);
+/* Like sv_alloc for a complex128 state: bytes >= sv_required_bytes_c128(n_qubits), 256-byte aligned. */
+SV_API int sv_alloc_c128(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out);
+
 /* Expectation values of Pauli strings (Section IV: the ExpectationValue routine runs the
  * ApplyGate group loop and reduces instead of storing).  String p is
  *     P_p = tensor product over qubits q of sigma_q,

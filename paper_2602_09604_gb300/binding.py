@@ -78,6 +78,8 @@ def _load():
     sig = {
         "sv_required_bytes": (ctypes.c_size_t, [I]),
         "sv_alloc": (I, [I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "sv_required_bytes_c128": (ctypes.c_size_t, [I]),
+        "sv_alloc_c128": (I, [I, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
         "sv_free": (None, [P]),
         "sv_init": (I, [P, ctypes.c_uint64]),
         "sv_load": (I, [P, P, I]),
@@ -148,6 +150,16 @@ def sv_required_bytes(n: int) -> int:
 def sv_alloc(n: int, dev_ptr: int, nbytes: int, stream: int = 0) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(lib.sv_alloc(n, ctypes.c_void_p(dev_ptr), nbytes, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_required_bytes_c128(n: int) -> int:
+    return int(lib.sv_required_bytes_c128(n))
+
+
+def sv_alloc_c128(n: int, dev_ptr: int, nbytes: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib.sv_alloc_c128(n, ctypes.c_void_p(dev_ptr), nbytes, ctypes.c_void_p(stream), ctypes.byref(h)))
     return h
 
 

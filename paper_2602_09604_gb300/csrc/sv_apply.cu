@@ -652,7 +652,7 @@ namespace {
 
 int upload_fused(sv_fused *f, int device)
 {
-    if (f->device == device) return SV_OK;
+    if (f->device == device && f->c64_ready) return SV_OK;
     if (f->device >= 0 && f->device != device) { set_error("sv_apply_fused_gates: fused circuit was uploaded to another device"); return SV_ESTATE; }
     // k = 6 CUDA-core gates read an interleaved fp32 matrix image from device memory
     std::vector<float> host;
@@ -673,6 +673,31 @@ int upload_fused(sv_fused *f, int device)
     }
     SV_TRY(build_tc_operands(f));
     f->device = device;
+    f->c64_ready = true;
+    return SV_OK;
+}
+
+// complex128 states read k >= 5 matrices from device memory in fp64 (built on first use)
+int upload_fused_c128(sv_fused *f, int device)
+{
+    if (f->device >= 0 && f->device != device) { set_error("sv_apply_fused_gates: fused circuit was uploaded to another device"); return SV_ESTATE; }
+    if (f->d_mats64 || !f->mat64_offset.empty()) return SV_OK;
+    std::vector<double> host;
+    f->mat64_offset.assign(f->gates.size(), SIZE_MAX);
+    for (size_t i = 0; i < f->gates.size(); ++i) {
+        const FusedGate &g = f->gates[i];
+        if (g.k < 5) continue;
+        f->mat64_offset[i] = host.size();
+        for (const cplx &c : g.mat) {
+            host.push_back(c.real());
+            host.push_back(c.imag());
+        }
+    }
+    if (!host.empty()) {
+        SV_CUDA_TRY(cudaMalloc(&f->d_mats64, host.size() * sizeof(double)));
+        SV_CUDA_TRY(cudaMemcpy(f->d_mats64, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    f->device = device;
     return SV_OK;
 }
 
@@ -684,7 +709,8 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
     if (!st || !fc) { set_error("sv_apply_fused_gates: NULL argument"); return SV_EINVAL; }
     sv_fused *f = const_cast<sv_fused *>(fc);
     if (f->n != st->n) { set_error("sv_apply_fused_gates: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
-    SV_TRY(upload_fused(f, st->device));
+    if (st->c128) SV_TRY(upload_fused_c128(f, st->device));
+    else SV_TRY(upload_fused(f, st->device));
     const size_t ng = f->gates.size();
     std::vector<cudaEvent_t> ev;
     if (timings && ng) {
@@ -694,11 +720,16 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
     int rc = SV_OK;
     for (size_t i = 0; i < ng && rc == SV_OK; ++i) {
         const FusedGate &g = f->gates[i];
-        const float *dm = f->mat_offset[i] != SIZE_MAX ? f->d_mats + f->mat_offset[i] : nullptr;
+        const float *dm = (i < f->mat_offset.size() && f->mat_offset[i] != SIZE_MAX) ? f->d_mats + f->mat_offset[i] : nullptr;
         const void *dt = (f->d_tc && i < f->tc_offset.size() && f->tc_offset[i] != SIZE_MAX)
                              ? static_cast<const char *>(f->d_tc) + f->tc_offset[i] : nullptr;
         if (timings) cudaEventRecord(ev[2 * i], st->stream);
-        rc = launch_fused_gate(st->d, st->n, g, dm, dt, st->stream, st->num_sms);
+        if (st->c128) {
+            const double *um = (f->d_mats64 && f->mat64_offset[i] != SIZE_MAX) ? f->d_mats64 + f->mat64_offset[i] : nullptr;
+            rc = c128_apply_gate(st, g, um);
+        } else {
+            rc = launch_fused_gate(st->d, st->n, g, dm, dt, st->stream, st->num_sms);
+        }
         if (timings) cudaEventRecord(ev[2 * i + 1], st->stream);
     }
     if (timings && ng) {
@@ -739,10 +770,11 @@ extern "C" int sv_device_status(void)
 extern "C" void sv_fused_free(sv_fused *f)
 {
     if (!f) return;
-    if (f->d_mats || f->d_tc) {
+    if (f->d_mats || f->d_tc || f->d_mats64) {
         cudaDeviceSynchronize();
         cudaFree(f->d_mats);
         cudaFree(f->d_tc);
+        cudaFree(f->d_mats64);
     }
     delete f;
 }

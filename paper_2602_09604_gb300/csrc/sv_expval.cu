@@ -297,6 +297,7 @@ extern "C" int sv_expval_pauli(const sv_state *st_c, const uint64_t *x_masks, co
     clear_error();
     sv_state *st = const_cast<sv_state *>(st_c);
     if (!st || count < 0 || (count > 0 && (!x_masks || !z_masks || !out))) { set_error("sv_expval_pauli: bad argument"); return SV_EINVAL; }
+    if (st->c128) { set_error("sv_expval_pauli: expectation values need a complex64 state"); return SV_EINVAL; }
     if (count == 0) return SV_OK;
     const int n = st->n;
     const uint64_t valid = n >= 64 ? ~0ull : ((1ull << n) - 1ull);

@@ -105,6 +105,13 @@ int mlp_fallback_k(const sv_mlp *m);
 // The current device's error word (allocated on first use); kernels that give up a bounded wait
 // write a nonzero code there.
 int device_err_word(int **out);
+// Complex128 states (sv_c128.cu): the same operations in fp64 on a 16-byte-per-amplitude layout.
+int c128_init(sv_state *st, uint64_t basis_index);
+int c128_load(sv_state *st, const void *src, int src_on_host);
+int c128_store(const sv_state *st, void *dst, int dst_on_host);
+int c128_norm(const sv_state *st, double *out);
+int c128_sample(sv_state *st, int n_samples);   // uniforms already in st->d_uniforms; results to st->d_samples
+int c128_apply_gate(sv_state *st, const FusedGate &g, const double *umem);
 // Reads and clears the current device's error word written by kernels whose bounded waits timed
 // out (0 = none).  Synchronous.
 int read_device_errors(int *code);
@@ -113,6 +120,7 @@ int read_device_errors(int *code);
 
 struct sv_state {
     int n = 0;
+    int c128 = 0;                   // nonzero: complex128 amplitudes (d points to doubles)
     float *d = nullptr;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
@@ -144,4 +152,7 @@ struct sv_fused {
     std::vector<size_t> mat_offset; // per gate offset in floats into d_mats, or SIZE_MAX
     void *d_tc = nullptr;           // tensor-core operand images
     std::vector<size_t> tc_offset;  // per gate byte offset into d_tc, or SIZE_MAX
+    bool c64_ready = false;         // the complex64 images above are uploaded
+    double *d_mats64 = nullptr;     // fp64 (re, im) images of k >= 5 gates, for complex128 states
+    std::vector<size_t> mat64_offset;
 };

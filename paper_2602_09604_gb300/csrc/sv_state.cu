@@ -269,7 +269,9 @@ extern "C" size_t sv_required_bytes(int n_qubits)
     return b < 256 ? 256 : b;
 }
 
-extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out)
+namespace {
+
+int alloc_state(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out, int c128)
 {
     clear_error();
     if (!out) { set_error("sv_alloc: out is NULL"); return SV_EINVAL; }
@@ -277,8 +279,9 @@ extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_st
     if (n_qubits < 1 || n_qubits > SV_MAX_QUBITS) { set_error("sv_alloc: n_qubits=%d outside [1, %d]", n_qubits, SV_MAX_QUBITS); return SV_EINVAL; }
     if (!dev_ptr) { set_error("sv_alloc: dev_ptr is NULL"); return SV_EINVAL; }
     if ((reinterpret_cast<uintptr_t>(dev_ptr) & 255u) != 0) { set_error("sv_alloc: dev_ptr must be 256-byte aligned"); return SV_EINVAL; }
-    if (bytes < sv_required_bytes(n_qubits)) {
-        set_error("sv_alloc: buffer of %zu bytes is smaller than the %zu an %d-qubit state needs", bytes, sv_required_bytes(n_qubits), n_qubits);
+    const size_t need = c128 ? sv_required_bytes_c128(n_qubits) : sv_required_bytes(n_qubits);
+    if (bytes < need) {
+        set_error("sv_alloc: buffer of %zu bytes is smaller than the %zu an %d-qubit state needs", bytes, need, n_qubits);
         return SV_ENOMEM;
     }
     cudaPointerAttributes attr{};
@@ -290,6 +293,7 @@ extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_st
     sv_state *st = new (std::nothrow) sv_state();
     if (!st) { set_error("sv_alloc: out of host memory"); return SV_ENOMEM; }
     st->n = n_qubits;
+    st->c128 = c128;
     st->d = static_cast<float *>(dev_ptr);
     st->bytes = bytes;
     st->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -318,6 +322,18 @@ extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_st
     return SV_OK;
 }
 
+}  // namespace
+
+extern "C" int sv_alloc(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out)
+{
+    return alloc_state(n_qubits, dev_ptr, bytes, cuda_stream, out, 0);
+}
+
+extern "C" int sv_alloc_c128(int n_qubits, void *dev_ptr, size_t bytes, void *cuda_stream, sv_state **out)
+{
+    return alloc_state(n_qubits, dev_ptr, bytes, cuda_stream, out, 1);
+}
+
 extern "C" void sv_free(sv_state *st)
 {
     if (!st) return;
@@ -335,6 +351,7 @@ extern "C" int sv_init(sv_state *st, uint64_t basis_index)
     clear_error();
     if (!st) { set_error("sv_init: state is NULL"); return SV_EINVAL; }
     if (basis_index >> st->n) { set_error("sv_init: basis index out of range for %d qubits", st->n); return SV_EINVAL; }
+    if (st->c128) return c128_init(st, basis_index);
     const size_t used = sv_required_bytes(st->n);
     SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, used, st->stream));
     set_basis_kernel<<<1, 1, 0, st->stream>>>(st->d, re_off(basis_index));
@@ -346,6 +363,7 @@ extern "C" int sv_load(sv_state *st, const void *src, int src_on_host)
 {
     clear_error();
     if (!st || !src) { set_error("sv_load: NULL argument"); return SV_EINVAL; }
+    if (st->c128) return c128_load(st, src, src_on_host);
     const size_t payload = size_t(8) << st->n;
     const long long nb = n_blocks_of(st->n);
     if (src_on_host) {
@@ -368,6 +386,7 @@ extern "C" int sv_store(const sv_state *st, void *dst, int dst_on_host)
 {
     clear_error();
     if (!st || !dst) { set_error("sv_store: NULL argument"); return SV_EINVAL; }
+    if (st->c128) return c128_store(st, dst, dst_on_host);
     const size_t payload = size_t(8) << st->n;
     const long long nb = n_blocks_of(st->n);
     const int g = grid_for(nb * 32, 256, st->num_sms, 8);
@@ -393,6 +412,7 @@ extern "C" int sv_norm(const sv_state *st, double *out)
 {
     clear_error();
     if (!st || !out) { set_error("sv_norm: NULL argument"); return SV_EINVAL; }
+    if (st->c128) return c128_norm(st, out);
     const long long nb = n_blocks_of(st->n);
     const int g = grid_for(nb * 8, kRedThreads, st->num_sms, 4);
     if (g > st->max_partials) { set_error("sv_norm: internal grid too large"); return SV_EINVAL; }
@@ -430,13 +450,17 @@ extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_sam
     double *sums = st->d_chunk;
     double *prefix = st->d_chunk + nc;
     SV_CUDA_TRY(cudaMemcpyAsync(st->d_uniforms, uniforms, sizeof(double) * size_t(n_samples), cudaMemcpyHostToDevice, st->stream));
-    chunk_sum_kernel<<<grid_for(nc * 32, 256, st->num_sms, 8), 256, 0, st->stream>>>(st->d, nc, chunk_blocks_log2, sums);
-    SV_CUDA_TRY(cudaGetLastError());
-    chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
-    SV_CUDA_TRY(cudaGetLastError());
-    const int wpb = 8;
-    sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms, n_samples, st->d_samples);
-    SV_CUDA_TRY(cudaGetLastError());
+    if (st->c128) {
+        SV_TRY(c128_sample(st, n_samples));
+    } else {
+        chunk_sum_kernel<<<grid_for(nc * 32, 256, st->num_sms, 8), 256, 0, st->stream>>>(st->d, nc, chunk_blocks_log2, sums);
+        SV_CUDA_TRY(cudaGetLastError());
+        chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
+        SV_CUDA_TRY(cudaGetLastError());
+        const int wpb = 8;
+        sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms, n_samples, st->d_samples);
+        SV_CUDA_TRY(cudaGetLastError());
+    }
     SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_samples, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, st->stream));
     SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
     return SV_OK;

@@ -38,6 +38,12 @@ def test_library_exports_every_declared_symbol(B):
         assert hasattr(B.lib, name), name
 
 
+def test_required_bytes_c128_is_sixteen_per_amplitude(B):
+    for n in range(5, 35):
+        assert B.sv_required_bytes_c128(n) == 2 ** (n + 4)
+    assert B.sv_required_bytes_c128(3) == 512 and B.sv_required_bytes_c128(0) == 0
+
+
 def test_required_bytes_is_eight_per_amplitude(B):
     # the artifact appendix: an N-qubit run needs 2^(N+3) bytes
     for n in range(5, 36):
