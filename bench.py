@@ -12,6 +12,9 @@ Prints one JSON line (rank 0).  `value` is seconds per circuit for the whole job
 slowest rank / circuits run by all ranks); `e2e` is the same metric measured through the C ABI
 with host buffers (fusion on the host, sample uniforms uploaded, samples and norm read back).
 `--impl reference` times the complex128 CPU oracle on a bounded sample of the same circuit.
+Outside the timed step the line also reports Pauli expectation passes on the circuit's state
+(`expval_pauli`) and the rows beyond the hot path (`next_rows`: the controlled-gate kernel,
+Grover and quantum-volume circuits, and the circuit on a complex128 state).
 """
 from __future__ import annotations
 
