@@ -1,7 +1,7 @@
 """Benchmark: one 30-qubit random grid circuit per step on the GB300 fused-gate path.
 
-A step is one pass of the hot path over one circuit: set |0...0>, apply every fused gate, take
-the fp64 norm and draw 1024 samples.  The circuit is the 5x6-grid random circuit (20 cycles of
+A step is one pass of the hot path over one circuit: set |0...0>, apply every fused gate, then
+one read pass that yields the fp64 norm and 1024 samples (sv_sample_norm).  The circuit is the 5x6-grid random circuit (20 cycles of
 sqrt(X)/sqrt(Y)/sqrt(W) plus fSim(pi/2, pi/6) on patterns ABCDCDAB, seed 2, 845 gates), fused
 on the host to at most --max-k qubits; fused gates of --tc-min-k or more qubits run on the tensor
 cores in --precision mode.  The complex64 state (8 GiB) is larger than L2, so no flush is needed
@@ -215,15 +215,14 @@ def bench_ours(args):
     def step(record):
         B.sv_init(st.h, 0)
         rec = B.sv_apply_fused_gates(st.h, fused, timings=record)
-        nrm = B.sv_norm(st.h)
-        smp = B.sv_sample(st.h, uniforms)
+        smp, nrm = B.sv_sample_norm(st.h, uniforms)   # norm and samples from one read pass
         return rec, nrm, smp
 
     for _ in range(args.warmup):
         step(False)
     # ---- device-timed region (events on the launching stream)
     kernel_us = {}
-    launches_per_step = 1 + n_fused + 1 + 3
+    launches_per_step = 1 + n_fused + 3   # basis, fused gates, chunk sums + scan + search
     norms = []
     with ClockSampler(dev) as clk:
         if ws > 1:
@@ -255,8 +254,7 @@ def bench_ours(args):
         f2 = B.sv_fuse_circuit(gates, n, **fuse_kw)
         B.sv_init(st.h, 0)
         B.sv_apply_fused_gates(st.h, f2)
-        smp = B.sv_sample(st.h, uniforms)
-        nrm = B.sv_norm(st.h)
+        smp, nrm = B.sv_sample_norm(st.h, uniforms)
         B.sv_fused_free(f2)
         e2e_times.append(time.perf_counter() - t0)
     mat_bytes = sum(2 * 4 * (1 << (2 * i["k"])) for i in infos)

@@ -249,6 +249,10 @@ SV_API int sv_norm(const sv_state *st, double *out);
  * Eq. 1: |c_i|^2 is the probability of observing basis state i).  Grows a workspace on the
  * state's device when n_samples exceeds the previous maximum.  Synchronises. */
 SV_API int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out);
+/* sv_sample and sv_norm from one read pass: the sampling's fp64 prefix sums end in the total
+ * probability, which is returned in *norm_out (the same fp64 sum as sv_norm up to summation order).
+ * n_samples may be 0 (norm only).  Synchronises. */
+SV_API int sv_sample_norm(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out, double *norm_out);
 
 /* ---------------------------------------------------------------------------------------------
  * Complex128 states (no counterpart in the paper's single-precision runs).  The same operations

@@ -92,6 +92,8 @@ def _load():
         "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
+        "sv_sample_norm": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_double)]),
         "sv_sample_noalloc": (I, [P, I, P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_device_status": (I, []),
         "sv_expval_pauli": (I, [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), I,
@@ -301,6 +303,16 @@ def sv_sample(h, uniforms) -> np.ndarray:
     _check(lib.sv_sample(h, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out
+
+
+def sv_sample_norm(h, uniforms):
+    """(samples, norm) from one read pass of the state."""
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    out = np.zeros(max(u.size, 1), dtype=np.uint64)
+    nrm = ctypes.c_double()
+    _check(lib.sv_sample_norm(h, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(nrm)))
+    return out[:u.size], nrm.value
 
 
 def sv_sample_noalloc(dev_state_ptr: int, n: int, stream: int, uniforms) -> np.ndarray:

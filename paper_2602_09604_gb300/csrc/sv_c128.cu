@@ -390,7 +390,8 @@ int c128_norm(const sv_state *st, double *out)
     return SV_OK;
 }
 
-// uniforms and out are host arrays; the state's sampling workspace is sized by the caller
+// chunk sums and their prefix (the total is the norm), then the samples if n_samples > 0; the
+// uniforms are already in st->d_uniforms and the samples go to st->d_samples
 int c128_sample(sv_state *st, int n_samples)
 {
     const int n = st->n;
@@ -403,10 +404,12 @@ int c128_sample(sv_state *st, int n_samples)
     SV_CUDA_TRY(cudaGetLastError());
     c128_chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
     SV_CUDA_TRY(cudaGetLastError());
-    const int wpb = 8;
-    c128_sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(sv, n, nc, chunk_log2, prefix, st->d_uniforms,
-                                                                                      n_samples, st->d_samples);
-    SV_CUDA_TRY(cudaGetLastError());
+    if (n_samples > 0) {
+        const int wpb = 8;
+        c128_sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(sv, n, nc, chunk_log2, prefix, st->d_uniforms,
+                                                                                          n_samples, st->d_samples);
+        SV_CUDA_TRY(cudaGetLastError());
+    }
     return SV_OK;
 }
 

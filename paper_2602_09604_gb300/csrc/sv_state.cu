@@ -423,14 +423,16 @@ extern "C" int sv_norm(const sv_state *st, double *out)
     return SV_OK;
 }
 
-extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_samples, uint64_t *out)
+namespace {
+
+// Chunk sums of |c_i|^2 (fp64), their exclusive prefix (whose last entry is the total, i.e. the
+// norm), then one warp per sample; norm_out (optional) receives that total.
+int sample_impl(sv_state *st, const double *uniforms, int n_samples, uint64_t *out, double *norm_out, const char *who)
 {
-    clear_error();
-    sv_state *st = const_cast<sv_state *>(st_c);
-    if (!st || (n_samples > 0 && (!uniforms || !out)) || n_samples < 0) { set_error("sv_sample: bad argument"); return SV_EINVAL; }
-    if (n_samples == 0) return SV_OK;
+    if (!st || n_samples < 0 || (n_samples > 0 && (!uniforms || !out))) { set_error("%s: bad argument", who); return SV_EINVAL; }
+    if (n_samples == 0 && !norm_out) return SV_OK;
     for (int s = 0; s < n_samples; ++s)
-        if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) { set_error("sv_sample: uniform %d = %g is not in [0, 1)", s, uniforms[s]); return SV_EINVAL; }
+        if (!(uniforms[s] >= 0.0 && uniforms[s] < 1.0)) { set_error("%s: uniform %d = %g is not in [0, 1)", who, s, uniforms[s]); return SV_EINVAL; }
     if (n_samples > st->sample_capacity) {
         cudaStreamSynchronize(st->stream);
         cudaFree(st->d_uniforms);
@@ -440,7 +442,7 @@ extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_sam
         st->sample_capacity = 0;
         cudaError_t e = cudaMalloc(&st->d_uniforms, sizeof(double) * size_t(n_samples));
         if (e == cudaSuccess) e = cudaMalloc(&st->d_samples, sizeof(unsigned long long) * size_t(n_samples));
-        if (e != cudaSuccess) { set_error("sv_sample: workspace allocation failed: %s", cudaGetErrorString(e)); return SV_ENOMEM; }
+        if (e != cudaSuccess) { set_error("%s: workspace allocation failed: %s", who, cudaGetErrorString(e)); return SV_ENOMEM; }
         st->sample_capacity = n_samples;
     }
     const int n = st->n;
@@ -449,7 +451,8 @@ extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_sam
     const long long nc = st->n_chunks;
     double *sums = st->d_chunk;
     double *prefix = st->d_chunk + nc;
-    SV_CUDA_TRY(cudaMemcpyAsync(st->d_uniforms, uniforms, sizeof(double) * size_t(n_samples), cudaMemcpyHostToDevice, st->stream));
+    if (n_samples > 0)
+        SV_CUDA_TRY(cudaMemcpyAsync(st->d_uniforms, uniforms, sizeof(double) * size_t(n_samples), cudaMemcpyHostToDevice, st->stream));
     if (st->c128) {
         SV_TRY(c128_sample(st, n_samples));
     } else {
@@ -457,13 +460,33 @@ extern "C" int sv_sample(const sv_state *st_c, const double *uniforms, int n_sam
         SV_CUDA_TRY(cudaGetLastError());
         chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
         SV_CUDA_TRY(cudaGetLastError());
-        const int wpb = 8;
-        sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms, n_samples, st->d_samples);
-        SV_CUDA_TRY(cudaGetLastError());
+        if (n_samples > 0) {
+            const int wpb = 8;
+            sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms,
+                                                                                        n_samples, st->d_samples);
+            SV_CUDA_TRY(cudaGetLastError());
+        }
     }
-    SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_samples, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, st->stream));
+    if (n_samples > 0)
+        SV_CUDA_TRY(cudaMemcpyAsync(out, st->d_samples, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, st->stream));
+    if (norm_out) SV_CUDA_TRY(cudaMemcpyAsync(norm_out, prefix + nc, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
     SV_CUDA_TRY(cudaStreamSynchronize(st->stream));
     return SV_OK;
+}
+
+}  // namespace
+
+extern "C" int sv_sample(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out)
+{
+    clear_error();
+    return sample_impl(const_cast<sv_state *>(st), uniforms, n_samples, out, nullptr, "sv_sample");
+}
+
+extern "C" int sv_sample_norm(const sv_state *st, const double *uniforms, int n_samples, uint64_t *out, double *norm_out)
+{
+    clear_error();
+    if (!norm_out) { set_error("sv_sample_norm: norm_out is NULL"); return SV_EINVAL; }
+    return sample_impl(const_cast<sv_state *>(st), uniforms, n_samples, out, norm_out, "sv_sample_norm");
 }
 
 // ================================================================== sampling without allocation
