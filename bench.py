@@ -1,7 +1,10 @@
 """Benchmark: one 30-qubit random grid circuit per step on the GB300 fused-gate path.
 
-A step is one pass of the hot path over one circuit: set |0...0>, apply every fused gate, then
-one read pass that yields the fp64 norm and 1024 samples (sv_sample_norm).  The circuit is the 5x6-grid random circuit (20 cycles of
+A step is one pass of the hot path over one circuit: set |0...0> and apply every fused gate
+(sv_init_apply: the first gates, while they name at most 24 qubits, run on the small state of
+those qubits, which is then written into the full state; --start plain uses sv_init then
+sv_apply_fused_gates, and the line reports the other start's time too), then one read pass that
+yields the fp64 norm and 1024 samples (sv_sample_norm).  The circuit is the 5x6-grid random circuit (20 cycles of
 sqrt(X)/sqrt(Y)/sqrt(W) plus fSim(pi/2, pi/6) on patterns ABCDCDAB, seed 2, 845 gates), fused
 on the host to at most --max-k qubits; fused gates of --tc-min-k or more qubits run on the tensor
 cores in --precision mode.  The complex64 state (8 GiB) is larger than L2, so no flush is needed
@@ -212,9 +215,13 @@ def bench_ours(args):
     rng = np.random.default_rng(1234 + rank)
     uniforms = rng.random(N_SAMPLES)
 
-    def step(record):
-        B.sv_init(st.h, 0)
-        rec = B.sv_apply_fused_gates(st.h, fused, timings=record)
+    def step(record, start=None):
+        start = start or args.start
+        if start == "lazy":   # gates run on the small state of the qubits named so far, then expand
+            rec = B.sv_init_apply(st.h, 0, fused, timings=record)
+        else:
+            B.sv_init(st.h, 0)
+            rec = B.sv_apply_fused_gates(st.h, fused, timings=record)
         smp, nrm = B.sv_sample_norm(st.h, uniforms)   # norm and samples from one read pass
         return rec, nrm, smp
 
@@ -222,7 +229,10 @@ def bench_ours(args):
         step(False)
     # ---- device-timed region (events on the launching stream)
     kernel_us = {}
-    launches_per_step = 1 + n_fused + 3   # basis, fused gates, chunk sums + scan + search
+    lazy_gates = 0
+    # per step: fused gates + chunk sums + scan + search, plus basis set (plain start) or small-state
+    # basis set + expansion (lazy start)
+    launches_per_step = n_fused + 3 + (2 if args.start == "lazy" else 1)
     norms = []
     with ClockSampler(dev) as clk:
         if ws > 1:
@@ -234,6 +244,9 @@ def bench_ours(args):
             rec, nrm, _ = step(True)
             norms.append(nrm)
             for info, r in zip(infos, rec):
+                if r["path"] == B.PATH_AUTO:   # ran on the small start state, not a full pass
+                    lazy_gates += 1
+                    continue
                 key = (B.PATH_NAMES[info["path"]], info["k"])
                 kernel_us.setdefault(key, []).append(r["us"])
         ev1.record(stream)
@@ -244,6 +257,16 @@ def bench_ours(args):
     from paper_2602_09604_gb300.dist import max_over_ranks
     elapsed_s = max_over_ranks(elapsed_s, device="cuda")   # the slowest rank defines the job time
     value = elapsed_s / (args.steps * ws)
+    # the other start, device-timed the same way, for comparison
+    other = "plain" if args.start == "lazy" else "lazy"
+    torch.cuda.synchronize()
+    e0o, e1o = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0o.record(stream)
+    for _ in range(3):
+        step(False, other)
+    e1o.record(stream)
+    torch.cuda.synchronize()
+    other_s = e0o.elapsed_time(e1o) / 3e3
 
     # ---- end to end through the C ABI with host buffers (host fusion included)
     e2e_times = []
@@ -252,8 +275,11 @@ def bench_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         f2 = B.sv_fuse_circuit(gates, n, **fuse_kw)
-        B.sv_init(st.h, 0)
-        B.sv_apply_fused_gates(st.h, f2)
+        if args.start == "lazy":
+            B.sv_init_apply(st.h, 0, f2)
+        else:
+            B.sv_init(st.h, 0)
+            B.sv_apply_fused_gates(st.h, f2)
         smp, nrm = B.sv_sample_norm(st.h, uniforms)
         B.sv_fused_free(f2)
         e2e_times.append(time.perf_counter() - t0)
@@ -368,7 +394,8 @@ def bench_ours(args):
     kernel_key = f"apply_{dom[0]}_k{dom[1]}_n{n}"
     traffic = read_traffic(kernel_key)
     all_us = sum(totals.values())
-    passes_gbs = n_fused * bytes_per_launch / (sum(totals.values()) / args.steps * 1e-6) / 1e9
+    full_passes = n_fused - lazy_gates // max(1, args.steps)   # gates that ran on the full state
+    passes_gbs = full_passes * bytes_per_launch / (sum(totals.values()) / args.steps * 1e-6) / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -377,7 +404,9 @@ def bench_ours(args):
         "config": {"workload": WORKLOAD, "n_qubits": n, "max_k": args.max_k, "precision": args.precision,
                    "tc_min_k": args.tc_min_k, "fusion": fusion, "fused_gates": n_fused,
                    "fused_k_histogram": {str(k): sum(1 for i in infos if i["k"] == k) for k in range(1, 7)}, "samples_per_step": N_SAMPLES,
-                   "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
+                   "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}",
+                   "start": args.start, "lazy_start_gates_per_step": lazy_gates // max(1, args.steps)},
+        f"s_per_circuit_{other}_start": other_s,
         "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
@@ -430,6 +459,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expval", action="store_true")
     ap.add_argument("--no-next-rows", action="store_true")
+    ap.add_argument("--start", choices=["lazy", "plain"], default="lazy",
+                    help="lazy: sv_init_apply (first gates on the small state of the qubits they name); "
+                         "plain: sv_init then sv_apply_fused_gates")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -122,7 +122,7 @@ typedef struct sv_fused_info {
 typedef struct sv_timing {
     float us;                /* device time of this fused gate's kernel, microseconds */
     int k;
-    int path;
+    int path;                /* the kernel path; SV_PATH_AUTO for a gate sv_init_apply ran on its small state */
     uint64_t target_mask;    /* bit q set <-> qubit q is a target */
 } sv_timing;
 
@@ -332,6 +332,15 @@ SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes)
  * fault, the states are left incomplete and sv_device_status returns SV_ETIMEOUT.  on = 0 undoes
  * it.  No effect when no circuit is split. */
 SV_API int sv_batch_inject_stall(sv_batch *b, int on);
+
+/* sv_init(st, basis_index) then sv_apply_fused_gates(st, f, timings), with the same result up to
+ * rounding order, computed with less memory traffic: while the gates applied so far name (as
+ * targets or controls) at most 24 qubits and fewer than n, every other qubit still holds its bit of
+ * basis_index, so those gates run on the small state of the named qubits (CUDA-core kernels, in a
+ * library-owned buffer of up to 128 MB grown on first use), which one kernel then writes into the
+ * zeroed full state; the remaining gates run as in sv_apply_fused_gates.  Complex128 states take
+ * the plain route.  Asynchronous unless timings are requested. */
+SV_API int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused *f, sv_timing *timings);
 
 /* SV_OK if no kernel on the current device has given up a bounded wait since the last call, else
  * SV_ETIMEOUT (the error is cleared by the call).  Synchronises the device. */

@@ -90,6 +90,7 @@ def _load():
         "sv_fused_get_info": (I, [P, I, ctypes.POINTER(sv_fused_info)]),
         "sv_fused_get_matrix": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
+        "sv_init_apply": (I, [P, ctypes.c_uint64, P, ctypes.POINTER(sv_timing)]),
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
         "sv_sample": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64)]),
         "sv_sample_norm": (I, [P, ctypes.POINTER(ctypes.c_double), I, ctypes.POINTER(ctypes.c_uint64),
@@ -250,6 +251,18 @@ def sv_fused_get_matrix(f, i: int) -> np.ndarray:
     out = np.zeros((1 << k, 1 << k), dtype=np.complex128)
     _check(lib.sv_fused_get_matrix(f, i, out.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def sv_init_apply(h, basis_index: int, f, timings: bool = False):
+    """sv_init followed by sv_apply_fused_gates, started on the small state of the named qubits."""
+    if not timings:
+        _check(lib.sv_init_apply(h, basis_index, f, None))
+        return None
+    n = sv_fused_count(f)
+    rec = (sv_timing * max(n, 1))()
+    _check(lib.sv_init_apply(h, basis_index, f, rec))
+    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "target_mask": rec[i].target_mask}
+            for i in range(n)]
 
 
 def sv_apply_fused_gates(h, f, timings: bool = False):

@@ -654,12 +654,13 @@ int upload_fused(sv_fused *f, int device)
 {
     if (f->device == device && f->c64_ready) return SV_OK;
     if (f->device >= 0 && f->device != device) { set_error("sv_apply_fused_gates: fused circuit was uploaded to another device"); return SV_ESTATE; }
-    // k = 6 CUDA-core gates read an interleaved fp32 matrix image from device memory
+    // k = 6 CUDA-core kernels read an interleaved fp32 matrix image from device memory (made for
+    // every k = 6 gate: sv_init_apply may run a tensor-core gate on CUDA cores on a small state)
     std::vector<float> host;
     f->mat_offset.assign(f->gates.size(), SIZE_MAX);
     for (size_t i = 0; i < f->gates.size(); ++i) {
         const FusedGate &g = f->gates[i];
-        if (g.k == 6 && g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) {
+        if (g.k == 6) {
             f->mat_offset[i] = host.size();
             for (size_t e = 0; e < g.ur.size(); ++e) {
                 host.push_back(g.ur[e]);
@@ -703,15 +704,106 @@ int upload_fused_c128(sv_fused *f, int device)
 
 }  // namespace
 
-extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing *timings)
+namespace svg {
+namespace {
+
+// Lazy start from a basis state (sv_init_apply): while the gates so far name at most
+// kCompactMaxQubits qubits A, every other qubit still holds its bit of x, so the state is
+// |x on the rest> (x) |small state on A>; those gates run on the 2^|A| small state, which one
+// kernel then writes into the zeroed full state.
+constexpr int kCompactMaxQubits = 24;
+
+struct ExpandArgs {
+    int pos[kCompactMaxQubits];   // ascending qubits of A: small-state bit b -> full-state bit pos[b]
+    int a;
+    unsigned long long rest;      // x on the qubits outside A
+    long long n_small;
+};
+
+__global__ void put_one_kernel(float *s, long long off) { s[off] = 1.0f; }
+
+__global__ void expand_compact_kernel(float *__restrict__ full, const float *__restrict__ small, const __grid_constant__ ExpandArgs e)
 {
-    clear_error();
-    if (!st || !fc) { set_error("sv_apply_fused_gates: NULL argument"); return SV_EINVAL; }
-    sv_fused *f = const_cast<sv_fused *>(fc);
-    if (f->n != st->n) { set_error("sv_apply_fused_gates: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < e.n_small; c += (long long)gridDim.x * blockDim.x) {
+        unsigned long long i = e.rest;
+        for (int b = 0; b < e.a; ++b)
+            if ((c >> b) & 1) i |= 1ull << e.pos[b];
+        const long long fo = (long long)(((i >> 5) << 6) | (i & 31ull));
+        const long long so = (long long)((((unsigned long long)c >> 5) << 6) | ((unsigned long long)c & 31ull));
+        full[fo] = small[so];
+        full[fo + 32] = small[so + 32];
+    }
+}
+
+}  // namespace
+}  // namespace svg
+
+namespace {
+
+int rank_in(uint64_t A, int q) { return __builtin_popcountll(A & ((1ull << q) - 1ull)); }
+
+// gate g re-expressed on the small state of the qubits in A (ascending order is kept, so the
+// matrix and its local index order are unchanged)
+FusedGate remap_gate(const FusedGate &g, uint64_t A, int a)
+{
+    FusedGate r;
+    r.k = g.k;
+    r.n_src = g.n_src;
+    for (int j = 0; j < g.k; ++j) {
+        r.targets[j] = rank_in(A, g.targets[j]);
+        r.mask |= 1ull << r.targets[j];
+        if (r.targets[j] < 32) r.mask_lo |= 1u << r.targets[j];
+    }
+    for (int q = 0; q < 64; ++q)
+        if ((g.cmask >> q) & 1) r.cmask |= 1ull << rank_in(A, q);
+    r.mat = g.mat;
+    r.ur = g.ur;
+    r.ui = g.ui;
+    r.path = classify_path(r, a, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO);   // CUDA cores on the small state
+    return r;
+}
+
+// Applies every fused gate of f to st; with m > 0 the first m run on the small state of the qubits
+// in A started from basis x (see above), which then replaces the whole state.
+int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, size_t m, uint64_t A, uint64_t x, const char *who)
+{
     if (st->c128) SV_TRY(upload_fused_c128(f, st->device));
     else SV_TRY(upload_fused(f, st->device));
     const size_t ng = f->gates.size();
+    const int a = __builtin_popcountll(A);
+    float *small = nullptr;
+    if (m > 0) {
+        const size_t bytes = sv_required_bytes(a);
+        if (bytes > st->compact_bytes) {
+            cudaStreamSynchronize(st->stream);
+            cudaFree(st->d_compact);
+            st->d_compact = nullptr;
+            st->compact_bytes = 0;
+            SV_CUDA_TRY(cudaMalloc(&st->d_compact, bytes));
+            st->compact_bytes = bytes;
+        }
+        small = st->d_compact;
+        uint64_t cx = 0;   // x restricted to A, packed
+        for (int q = 0, b = 0; q < 64; ++q)
+            if ((A >> q) & 1) cx |= ((x >> q) & 1ull) << b++;
+        SV_CUDA_TRY(cudaMemsetAsync(small, 0, bytes, st->stream));
+        put_one_kernel<<<1, 1, 0, st->stream>>>(small, (long long)(((cx >> 5) << 6) | (cx & 31ull)));
+        SV_CUDA_TRY(cudaGetLastError());
+    }
+    auto expand = [&]() -> int {
+        ExpandArgs e;
+        std::memset(&e, 0, sizeof(e));
+        for (int q = 0, b = 0; q < 64; ++q)
+            if ((A >> q) & 1) e.pos[b++] = q;
+        e.a = a;
+        e.rest = x & ~A;
+        e.n_small = 1ll << a;
+        SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, sv_required_bytes(st->n), st->stream));
+        const long long grid = std::min<long long>((e.n_small + 255) / 256, (long long)st->num_sms * 8);
+        expand_compact_kernel<<<(unsigned)grid, 256, 0, st->stream>>>(st->d, small, e);
+        SV_CUDA_TRY(cudaGetLastError());
+        return SV_OK;
+    };
     std::vector<cudaEvent_t> ev;
     if (timings && ng) {
         ev.resize(2 * ng);
@@ -719,12 +811,16 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
     }
     int rc = SV_OK;
     for (size_t i = 0; i < ng && rc == SV_OK; ++i) {
+        if (m > 0 && i == m) rc = expand();
+        if (rc != SV_OK) break;
         const FusedGate &g = f->gates[i];
         const float *dm = (i < f->mat_offset.size() && f->mat_offset[i] != SIZE_MAX) ? f->d_mats + f->mat_offset[i] : nullptr;
         const void *dt = (f->d_tc && i < f->tc_offset.size() && f->tc_offset[i] != SIZE_MAX)
                              ? static_cast<const char *>(f->d_tc) + f->tc_offset[i] : nullptr;
         if (timings) cudaEventRecord(ev[2 * i], st->stream);
-        if (st->c128) {
+        if (i < m) {
+            rc = launch_fused_gate(small, a, remap_gate(g, A, a), dm, nullptr, st->stream, st->num_sms);
+        } else if (st->c128) {
             const double *um = (f->d_mats64 && f->mat64_offset[i] != SIZE_MAX) ? f->d_mats64 + f->mat64_offset[i] : nullptr;
             rc = c128_apply_gate(st, g, um);
         } else {
@@ -732,6 +828,7 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
         }
         if (timings) cudaEventRecord(ev[2 * i + 1], st->stream);
     }
+    if (rc == SV_OK && m > 0 && m == ng) rc = expand();
     if (timings && ng) {
         cudaError_t e = cudaStreamSynchronize(st->stream);
         for (size_t i = 0; i < ng; ++i) {
@@ -740,18 +837,54 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
             const FusedGate &g = f->gates[i];
             timings[i].us = ms * 1000.f;
             timings[i].k = g.k;
-            timings[i].path = g.path;
+            timings[i].path = i < m ? SV_PATH_AUTO : g.path;   // AUTO: ran on the small state
             timings[i].target_mask = g.mask;
         }
-        for (auto &x : ev) cudaEventDestroy(x);
-        if (e != cudaSuccess && rc == SV_OK) { set_error("sv_apply_fused_gates: %s", cudaGetErrorString(e)); rc = SV_ECUDA; }
+        for (auto &xv : ev) cudaEventDestroy(xv);
+        if (e != cudaSuccess && rc == SV_OK) { set_error("%s: %s", who, cudaGetErrorString(e)); rc = SV_ECUDA; }
         int code = 0;
         if (rc == SV_OK && read_device_errors(&code) == SV_OK && code) {
-            set_error("sv_apply_fused_gates: a kernel gave up a bounded wait (device code 0x%x)", code);
+            set_error("%s: a kernel gave up a bounded wait (device code 0x%x)", who, code);
             rc = SV_ETIMEOUT;
         }
     }
     return rc;
+}
+
+}  // namespace
+
+extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing *timings)
+{
+    clear_error();
+    if (!st || !fc) { set_error("sv_apply_fused_gates: NULL argument"); return SV_EINVAL; }
+    sv_fused *f = const_cast<sv_fused *>(fc);
+    if (f->n != st->n) { set_error("sv_apply_fused_gates: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
+    return apply_core(st, f, timings, 0, 0, 0, "sv_apply_fused_gates");
+}
+
+extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused *fc, sv_timing *timings)
+{
+    clear_error();
+    if (!st || !fc) { set_error("sv_init_apply: NULL argument"); return SV_EINVAL; }
+    sv_fused *f = const_cast<sv_fused *>(fc);
+    if (f->n != st->n) { set_error("sv_init_apply: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
+    if (basis_index >> st->n) { set_error("sv_init_apply: basis index out of range for %d qubits", st->n); return SV_EINVAL; }
+    // the longest prefix of gates whose qubits (targets and controls) number at most the limit
+    const int limit = std::min(kCompactMaxQubits, st->n - 1);
+    uint64_t A = 0;
+    size_t m = 0;
+    if (!st->c128)
+        for (const FusedGate &g : f->gates) {
+            const uint64_t u = A | g.mask | g.cmask;
+            if (__builtin_popcountll(u) > limit) break;
+            A = u;
+            ++m;
+        }
+    if (m == 0) {
+        SV_TRY(sv_init(st, basis_index));
+        return apply_core(st, f, timings, 0, 0, 0, "sv_init_apply");
+    }
+    return apply_core(st, f, timings, m, A, basis_index, "sv_init_apply");
 }
 
 extern "C" int sv_device_status(void)

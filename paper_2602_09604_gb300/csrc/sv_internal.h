@@ -140,6 +140,9 @@ struct sv_state {
     // expectation-value workspace (library-owned, grown on demand): per-CTA partials, results, counter
     double *d_ev = nullptr;
     int ev_capacity = 0;
+    // small state for sv_init_apply's lazy start (library-owned, grown on demand)
+    float *d_compact = nullptr;
+    size_t compact_bytes = 0;
 };
 
 struct sv_fused {

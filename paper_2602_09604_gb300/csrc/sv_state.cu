@@ -343,6 +343,7 @@ extern "C" void sv_free(sv_state *st)
     cudaFree(st->d_uniforms);
     cudaFree(st->d_samples);
     cudaFree(st->d_ev);
+    cudaFree(st->d_compact);
     delete st;
 }
 

@@ -1,0 +1,93 @@
+"""sv_init_apply (gates run on the small state of the qubits named so far, then one expansion)
+gives the oracle's state: random circuits with kept controls at several sizes and fusion sizes,
+prefixes that cover the whole circuit, the 3xBF16 tensor-core path, Grover, nonzero basis states,
+timing records for every gate; and at 30 qubits it matches sv_init + sv_apply_fused_gates."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms
+from paper_2602_09604_gb300 import build as libbuild
+from paper_2602_09604_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    libbuild.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2602_09604_gb300 import binding
+    return binding
+
+
+def run(B, n, gates, x, timings=False, **kw):
+    from paper_2602_09604_gb300.state import DeviceState
+    f = B.sv_fuse_circuit(gates, n, **kw)
+    st = DeviceState(n)
+    rec = B.sv_init_apply(st.h, x, f, timings)
+    B.sv_device_status()
+    got = st.store()
+    cnt = B.sv_fused_count(f)
+    B.sv_fused_free(f)
+    st.free()
+    return got, rec, cnt
+
+
+@pytest.mark.parametrize("n,max_k,prec", [(6, 2, 0), (12, 4, 0), (20, 3, 0), (26, 6, 2), (27, 5, 2)])
+def test_random_circuits(B, n, max_k, prec):
+    rng = np.random.default_rng(n + max_k)
+    gates = []
+    for _ in range(90):
+        k = int(rng.integers(1, 4))
+        nc = int(rng.integers(0, 4)) if rng.random() < 0.3 else 0
+        qs = [int(q) for q in rng.permutation(n)]
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    x = int(rng.integers(0, 1 << n))
+    got, rec, cnt = run(B, n, gates, x, timings=True, max_k=max_k, precision=prec, tc_min_k=4)
+    assert len(rec) == cnt and all(r["us"] >= 0 for r in rec)
+    ref = oracle.run_circuit(n, gates, x, threads=oracle.default_threads())
+    assert oracle.fidelity(ref, got) >= 1 - 1e-6
+    assert oracle.l2_error(ref, got) <= 1e-4
+
+
+def test_prefix_covers_the_circuit(B):
+    n = 16
+    rng = np.random.default_rng(3)
+    gates = [wl.random_gate(n, 2, rng, targets=(1 + i % 5, 9 + i % 4)) for i in range(40)]   # 9 qubits named
+    x = 0b1010011100101101
+    got, _, _ = run(B, n, gates, x, max_k=4)
+    ref = oracle.run_circuit(n, gates, x)
+    assert np.max(np.abs(got - ref)) <= 2e-6
+
+
+def test_grover_from_basis(B):
+    n, marked, r = 18, 0x2B3C1, 4
+    got, _, _ = run(B, n, wl.grover_circuit(n, marked, r), 0, max_k=4)
+    a, b = closed_forms.grover_amplitudes(n, r)
+    assert abs(got[marked] - a) <= 2e-5
+    assert np.max(np.abs(np.delete(got, marked) - b)) <= 2e-6
+
+
+def test_bench_circuit_matches_plain_route(B):
+    import torch
+    from paper_2602_09604_gb300.state import DeviceState
+    n, gates = wl.circuit_30q_grid()
+    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4)
+    st = DeviceState(n)
+    B.sv_init_apply(st.h, 0, f, False)
+    lazy = st.buf.clone()
+    st.init(0)
+    st.apply(f)
+    B.sv_fused_free(f)
+    d = torch.zeros((), dtype=torch.float64, device="cuda")
+    ov = torch.zeros((), dtype=torch.float64, device="cuda")
+    step = 1 << 26
+    for lo in range(0, lazy.numel(), step):
+        a = lazy[lo:lo + step].double()
+        b = st.buf[lo:lo + step].double()
+        d += ((a - b) ** 2).sum()
+    assert float(d.sqrt()) <= 1e-4, float(d.sqrt())
+    assert abs(st.norm() - 1.0) <= 1e-4
+    st.free()
