@@ -334,12 +334,14 @@ SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes)
 SV_API int sv_batch_inject_stall(sv_batch *b, int on);
 
 /* sv_init(st, basis_index) then sv_apply_fused_gates(st, f, timings), with the same result up to
- * rounding order, computed with less memory traffic: while the gates applied so far name (as
- * targets or controls) at most 24 qubits and fewer than n, every other qubit still holds its bit of
- * basis_index, so those gates run on the small state of the named qubits (CUDA-core kernels, in a
- * library-owned buffer of up to 128 MB grown on first use), which one kernel then writes into the
- * zeroed full state; the remaining gates run as in sv_apply_fused_gates.  Complex128 states take
- * the plain route.  Asynchronous unless timings are requested. */
+ * rounding order, computed with less memory traffic.  One pass over the fused gates picks those
+ * that share no qubit with an earlier gate left out (so they commute past it) while the qubits they
+ * name, targets and controls, number at most 24 and fewer than n; every other qubit still holds its
+ * bit of basis_index, so the picked gates run first, in order, on the small state of the named
+ * qubits (CUDA-core kernels, in a library-owned buffer of up to 128 MB grown on first use), which
+ * one kernel then writes into the zeroed full state; the rest run, in order, as in
+ * sv_apply_fused_gates.  Timing records stay in circuit order.  Complex128 states take the plain
+ * route.  Asynchronous unless timings are requested. */
 SV_API int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused *f, sv_timing *timings);
 
 /* SV_OK if no kernel on the current device has given up a bounded wait since the last call, else

@@ -763,14 +763,20 @@ FusedGate remap_gate(const FusedGate &g, uint64_t A, int a)
     return r;
 }
 
-// Applies every fused gate of f to st; with m > 0 the first m run on the small state of the qubits
-// in A started from basis x (see above), which then replaces the whole state.
-int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, size_t m, uint64_t A, uint64_t x, const char *who)
+// Applies every fused gate of f to st.  With `lazy` (one flag per gate, a set closed under the
+// gates' order: no flagged gate shares a qubit with an earlier unflagged one) the flagged gates run
+// first, in order, on the small state of the qubits in A started from basis x (see above), which
+// then replaces the whole state; the others follow in order.  Moving a flagged gate ahead of
+// earlier unflagged ones is exact: they share no qubit, so they commute.
+int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<char> *lazy, uint64_t A, uint64_t x, const char *who)
 {
     if (st->c128) SV_TRY(upload_fused_c128(f, st->device));
     else SV_TRY(upload_fused(f, st->device));
     const size_t ng = f->gates.size();
     const int a = __builtin_popcountll(A);
+    size_t m = 0;   // gates run on the small state
+    if (lazy)
+        for (char c : *lazy) m += c != 0;
     float *small = nullptr;
     if (m > 0) {
         const size_t bytes = sv_required_bytes(a);
@@ -809,16 +815,25 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, size_t m, uint64_t
         ev.resize(2 * ng);
         for (auto &e : ev) SV_CUDA_TRY(cudaEventCreate(&e));
     }
+    // execution order: the small-state gates, then the rest (each in their original order)
+    std::vector<size_t> order;
+    order.reserve(ng);
+    for (size_t i = 0; i < ng; ++i)
+        if (m > 0 && (*lazy)[i]) order.push_back(i);
+    for (size_t i = 0; i < ng; ++i)
+        if (!(m > 0 && (*lazy)[i])) order.push_back(i);
     int rc = SV_OK;
-    for (size_t i = 0; i < ng && rc == SV_OK; ++i) {
-        if (m > 0 && i == m) rc = expand();
+    for (size_t oi = 0; oi < ng && rc == SV_OK; ++oi) {
+        if (m > 0 && oi == m) rc = expand();
         if (rc != SV_OK) break;
+        const size_t i = order[oi];
+        const bool on_small = oi < m;
         const FusedGate &g = f->gates[i];
         const float *dm = (i < f->mat_offset.size() && f->mat_offset[i] != SIZE_MAX) ? f->d_mats + f->mat_offset[i] : nullptr;
         const void *dt = (f->d_tc && i < f->tc_offset.size() && f->tc_offset[i] != SIZE_MAX)
                              ? static_cast<const char *>(f->d_tc) + f->tc_offset[i] : nullptr;
         if (timings) cudaEventRecord(ev[2 * i], st->stream);
-        if (i < m) {
+        if (on_small) {
             rc = launch_fused_gate(small, a, remap_gate(g, A, a), dm, nullptr, st->stream, st->num_sms);
         } else if (st->c128) {
             const double *um = (f->d_mats64 && f->mat64_offset[i] != SIZE_MAX) ? f->d_mats64 + f->mat64_offset[i] : nullptr;
@@ -837,7 +852,7 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, size_t m, uint64_t
             const FusedGate &g = f->gates[i];
             timings[i].us = ms * 1000.f;
             timings[i].k = g.k;
-            timings[i].path = i < m ? SV_PATH_AUTO : g.path;   // AUTO: ran on the small state
+            timings[i].path = (m > 0 && (*lazy)[i]) ? SV_PATH_AUTO : g.path;   // AUTO: ran on the small state
             timings[i].target_mask = g.mask;
         }
         for (auto &xv : ev) cudaEventDestroy(xv);
@@ -859,7 +874,7 @@ extern "C" int sv_apply_fused_gates(sv_state *st, const sv_fused *fc, sv_timing 
     if (!st || !fc) { set_error("sv_apply_fused_gates: NULL argument"); return SV_EINVAL; }
     sv_fused *f = const_cast<sv_fused *>(fc);
     if (f->n != st->n) { set_error("sv_apply_fused_gates: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
-    return apply_core(st, f, timings, 0, 0, 0, "sv_apply_fused_gates");
+    return apply_core(st, f, timings, nullptr, 0, 0, "sv_apply_fused_gates");
 }
 
 extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused *fc, sv_timing *timings)
@@ -869,22 +884,30 @@ extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused 
     sv_fused *f = const_cast<sv_fused *>(fc);
     if (f->n != st->n) { set_error("sv_init_apply: circuit is for %d qubits, state has %d", f->n, st->n); return SV_ESTATE; }
     if (basis_index >> st->n) { set_error("sv_init_apply: basis index out of range for %d qubits", st->n); return SV_EINVAL; }
-    // the longest prefix of gates whose qubits (targets and controls) number at most the limit
+    // gates for the small state, in one pass over the circuit: a gate qualifies if no earlier gate
+    // left out shares a qubit with it (so it commutes past those) and the qubits named so far, its
+    // own included, stay within the limit
     const int limit = std::min(kCompactMaxQubits, st->n - 1);
-    uint64_t A = 0;
+    std::vector<char> lazy(f->gates.size(), 0);
+    uint64_t A = 0, blocked = 0;
     size_t m = 0;
     if (!st->c128)
-        for (const FusedGate &g : f->gates) {
-            const uint64_t u = A | g.mask | g.cmask;
-            if (__builtin_popcountll(u) > limit) break;
-            A = u;
-            ++m;
+        for (size_t i = 0; i < f->gates.size(); ++i) {
+            const FusedGate &g = f->gates[i];
+            const uint64_t q = g.mask | g.cmask;
+            if (!(q & blocked) && __builtin_popcountll(A | q) <= limit) {
+                A |= q;
+                lazy[i] = 1;
+                ++m;
+            } else {
+                blocked |= q;
+            }
         }
     if (m == 0) {
         SV_TRY(sv_init(st, basis_index));
-        return apply_core(st, f, timings, 0, 0, 0, "sv_init_apply");
+        return apply_core(st, f, timings, nullptr, 0, 0, "sv_init_apply");
     }
-    return apply_core(st, f, timings, m, A, basis_index, "sv_init_apply");
+    return apply_core(st, f, timings, &lazy, A, basis_index, "sv_init_apply");
 }
 
 extern "C" int sv_device_status(void)
