@@ -13,6 +13,7 @@
 // over the blocks before it that share no qubit with it (they commute) and merges into the first
 // block it meets whose union with it still has at most max_k qubits.
 #include <algorithm>
+#include <array>
 #include <future>
 #include <cmath>
 #include <cstdarg>
@@ -32,13 +33,47 @@ struct Block {
     int n_src = 0;
     long long created = 0;
     uint64_t cmask = 0;       // a controlled gate kept whole (qubits = its targets); else 0
+    // single-qubit gates absorbed but not yet multiplied in: the block's operator is
+    // (product over pend of P_q) * mat; each is folded into the next gate on its qubit, or
+    // multiplied in when the block closes (saves a 2^k x 2^k update per single-qubit gate)
+    std::vector<std::pair<int, std::array<cplx, 4>>> pend;
 };
+
+// Rows r_j = base | off[j] (j < GD) of mat, each `dim` complex entries, replaced by G times them.
+// Every column's GD inputs are read before any output of that column is written, so no copy is
+// needed, and the column loop runs over contiguous memory.
+template <int GD>
+void mix_rows(double *m, size_t dim, size_t base, const size_t *off, const std::vector<cplx> &G)
+{
+    double gr[GD][GD], gi[GD][GD];
+    for (int r = 0; r < GD; ++r)
+        for (int j = 0; j < GD; ++j) {
+            gr[r][j] = G[(size_t)r * GD + j].real();
+            gi[r][j] = G[(size_t)r * GD + j].imag();
+        }
+    double *row[GD];
+    for (int j = 0; j < GD; ++j) row[j] = m + 2 * (base | off[j]) * dim;
+    for (size_t c = 0; c < dim; ++c) {
+        double xr[GD], xi[GD];
+        for (int j = 0; j < GD; ++j) {
+            xr[j] = row[j][2 * c];
+            xi[j] = row[j][2 * c + 1];
+        }
+        for (int r = 0; r < GD; ++r) {
+            double yr = 0.0, yi = 0.0;
+            for (int j = 0; j < GD; ++j) {
+                yr += gr[r][j] * xr[j] - gi[r][j] * xi[j];
+                yi += gr[r][j] * xi[j] + gi[r][j] * xr[j];
+            }
+            row[r][2 * c] = yr;
+            row[r][2 * c + 1] = yi;
+        }
+    }
+}
 
 // mat (dim x dim, acting on qubit list T) <- G * mat, where G acts on qubits gq (local bit b of G
 // <-> gq[b], every gq[b] in T).  G mixes the rows of mat whose indices differ only in G's bits:
-// for each such group of rows (visited through its all-zero member), the gd rows are replaced by
-// G times them, one whole row (every column) at a time so the inner loop runs over contiguous
-// memory.
+// each such group of rows (visited through its all-zero member) is replaced by G times it.
 void left_multiply(std::vector<cplx> &mat, const std::vector<int> &T, const std::vector<cplx> &G,
                    const std::vector<int> &gq)
 {
@@ -59,35 +94,16 @@ void left_multiply(std::vector<cplx> &mat, const std::vector<int> &T, const std:
             if ((j >> b) & 1) o |= size_t(1) << pos[b];
         off[j] = o;
     }
-    // rows as separate real / imaginary arrays so the column loop vectorises
-    std::vector<double> xr(gd * dim), xi(gd * dim), yr(dim), yi(dim);
     double *m = reinterpret_cast<double *>(mat.data());
     for (size_t base = 0; base < dim; ++base) {
         if (base & gmask) continue;
-        for (size_t j = 0; j < gd; ++j) {
-            const double *row = m + 2 * (base | off[j]) * dim;
-            double *dr = &xr[j * dim], *di = &xi[j * dim];
-            for (size_t c = 0; c < dim; ++c) {
-                dr[c] = row[2 * c];
-                di[c] = row[2 * c + 1];
-            }
-        }
-        for (size_t r = 0; r < gd; ++r) {
-            for (size_t c = 0; c < dim; ++c) yr[c] = yi[c] = 0.0;
-            for (size_t j = 0; j < gd; ++j) {
-                const double gr = G[r * gd + j].real(), gi = G[r * gd + j].imag();
-                if (gr == 0.0 && gi == 0.0) continue;
-                const double *sr = &xr[j * dim], *si = &xi[j * dim];
-                for (size_t c = 0; c < dim; ++c) {
-                    yr[c] += gr * sr[c] - gi * si[c];
-                    yi[c] += gr * si[c] + gi * sr[c];
-                }
-            }
-            double *row = m + 2 * (base | off[r]) * dim;
-            for (size_t c = 0; c < dim; ++c) {
-                row[2 * c] = yr[c];
-                row[2 * c + 1] = yi[c];
-            }
+        switch (kg) {
+        case 1: mix_rows<2>(m, dim, base, off.data(), G); break;
+        case 2: mix_rows<4>(m, dim, base, off.data(), G); break;
+        case 3: mix_rows<8>(m, dim, base, off.data(), G); break;
+        case 4: mix_rows<16>(m, dim, base, off.data(), G); break;
+        case 5: mix_rows<32>(m, dim, base, off.data(), G); break;
+        default: mix_rows<64>(m, dim, base, off.data(), G); break;
         }
     }
 }
@@ -127,6 +143,39 @@ std::vector<cplx> expand(const std::vector<cplx> &M, const std::vector<int> &S, 
         for (size_t r = 0; r < dS; ++r)
             for (size_t c = 0; c < dS; ++c) out[(depS[r] | depR[e]) * dT + (depS[c] | depR[e])] = M[r * dS + c];
     return out;
+}
+
+// multiplies every pending single-qubit gate of b into b.mat
+void flush_pending(Block &b)
+{
+    for (auto &pq : b.pend) {
+        const std::vector<cplx> P(pq.second.begin(), pq.second.end());
+        left_multiply(b.mat, b.qubits, P, std::vector<int>{pq.first});
+    }
+    b.pend.clear();
+}
+
+// G (acting on qubit list Q) <- G * P_q for every pending gate of b on a qubit of Q (P applied
+// first), and drops those from b.pend
+void fold_pending(std::vector<cplx> &G, const std::vector<int> &Q, Block &b)
+{
+    const size_t d = size_t(1) << Q.size();
+    for (size_t i = 0; i < b.pend.size();) {
+        const int q = b.pend[i].first;
+        const auto it = std::find(Q.begin(), Q.end(), q);
+        if (it == Q.end()) { ++i; continue; }
+        const size_t bit = size_t(1) << (it - Q.begin());
+        const std::array<cplx, 4> &P = b.pend[i].second;
+        for (size_t r = 0; r < d; ++r)
+            for (size_t c0 = 0; c0 < d; ++c0) {
+                if (c0 & bit) continue;
+                const size_t c1 = c0 | bit;
+                const cplx g0 = G[r * d + c0], g1 = G[r * d + c1];
+                G[r * d + c0] = g0 * P[0] + g1 * P[2];
+                G[r * d + c1] = g0 * P[1] + g1 * P[3];
+            }
+        b.pend.erase(b.pend.begin() + (long)i);
+    }
 }
 
 struct Dense {
@@ -172,7 +221,10 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
                 (t ? closed : rest).push_back(std::move(b));
             }
             std::sort(closed.begin(), closed.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
-            for (Block &b : closed) emitted.push_back(std::move(b));
+            for (Block &b : closed) {
+                flush_pending(b);
+                emitted.push_back(std::move(b));
+            }
             Block cb = controlled_block(dense[gi]);
             cb.created = stamp++;
             emitted.push_back(std::move(cb));
@@ -208,7 +260,28 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         std::sort(closed.begin(), closed.end(), [&](int a, int b) { return open[a].created < open[b].created; });
         std::vector<int> kept(touching.begin() + first_kept, touching.end());
         std::sort(kept.begin(), kept.end(), [&](int a, int b) { return open[a].created < open[b].created; });
-        for (int b : closed) emitted.push_back(std::move(open[b]));
+        for (int b : closed) {
+            flush_pending(open[b]);
+            emitted.push_back(std::move(open[b]));
+        }
+
+        // a single-qubit gate on a qubit of one open block stays pending there
+        if (Q.size() == 1 && kept.size() == 1 && touching.size() == 1) {
+            Block &kb = open[kept[0]];
+            const std::vector<cplx> &G = dense[gi].m;
+            std::array<cplx, 4> P = {G[0], G[1], G[2], G[3]};
+            for (size_t i = 0; i < kb.pend.size(); ++i)
+                if (kb.pend[i].first == Q[0]) {   // G * earlier pending
+                    const std::array<cplx, 4> &E = kb.pend[i].second;
+                    P = {G[0] * E[0] + G[1] * E[2], G[0] * E[1] + G[1] * E[3], G[2] * E[0] + G[3] * E[2], G[2] * E[1] + G[3] * E[3]};
+                    kb.pend.erase(kb.pend.begin() + (long)i);
+                    break;
+                }
+            kb.pend.push_back({Q[0], P});
+            kb.n_src += 1;
+            kb.created = stamp++;
+            continue;
+        }
 
         // merge kept blocks (disjoint, so they commute) and the gate into one block over the union
         uint64_t um = qmask;
@@ -218,6 +291,8 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         for (int q = 0; q < n_qubits; ++q)
             if ((um >> q) & 1) nb.qubits.push_back(q);
         nb.n_src = 1;
+        for (int b : kept)   // pending single-qubit gates carry over (their qubits stay disjoint)
+            for (auto &pq : open[b].pend) nb.pend.push_back(pq);
         if (kept.empty()) {
             nb.mat = identity(size_t(1) << nb.qubits.size());
         } else {
@@ -230,7 +305,11 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
                 nb.n_src += open[kept[i]].n_src;
             }
         }
-        left_multiply(nb.mat, nb.qubits, dense[gi].m, Q);
+        {
+            std::vector<cplx> G = dense[gi].m;
+            fold_pending(G, Q, nb);   // the pending gates on Q act before this gate
+            left_multiply(nb.mat, nb.qubits, G, Q);
+        }
         nb.created = stamp++;
         std::vector<char> drop(open.size(), 0);
         for (int b : touching) drop[b] = 1;
@@ -242,7 +321,10 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         open.swap(rest);
     }
     std::sort(open.begin(), open.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
-    for (Block &b : open) emitted.push_back(std::move(b));
+    for (Block &b : open) {
+        flush_pending(b);
+        emitted.push_back(std::move(b));
+    }
 
     // horizontal pass: move each block back over disjoint predecessors and merge where it fits
     std::vector<Block> merged;
