@@ -906,8 +906,9 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
     const int variant = staged ? 1 : (kDirectSmemA && K == 6 && nlow == 0 ? 2 : 0);
-    auto kern = variant == 1 ? apply_tc_kernel<K, MODE, true>
-                             : (variant == 2 ? apply_tc_direct_kernel<K, MODE> : apply_tc_kernel<K, MODE, false>);
+    void (*kern)(float *, const TcArgs) = variant == 1 ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
+    if constexpr (K == 6)   // the shared-memory-A kernel exists for k = 6 only
+        if (variant == 2) kern = apply_tc_direct_kernel<K, MODE>;
     const int smem = variant == 1 ? S::SMEM_STAGED : (variant == 2 ? S::SMEM_DIRECT2 : S::SMEM_DIRECT);
     const int tmem_cols = variant == 2 ? S::TMEM_COLS_D2 : S::TMEM_COLS;
     static uint64_t attr_set[3] = {0, 0, 0};   // a bit per device (function attributes are per device)
