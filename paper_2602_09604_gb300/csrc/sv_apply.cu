@@ -7,9 +7,9 @@
 //            blocks, so each thread loads its group straight into registers with 128-bit loads;
 //            a warp's loads cover whole 128-byte lines.  No shared memory.
 //   LOW   -- every target < 5, or more generally a tile whose blocks are contiguous.  A warp copies
-//            a tile of 2^f consecutive blocks into shared memory (cp.async, double-buffered so the
-//            next tile streams in while this one is computed), applies the gate to every group of
-//            the tile from shared memory, and writes the tile back with 128-bit stores.
+//            a tile of 2^f consecutive blocks into shared memory through registers (16-byte loads,
+//            XOR-swizzled stores), applies the gate to every group of the tile from shared memory,
+//            and writes the tile back with 16-byte stores.
 //   MIXED -- low and high targets.  Same as LOW, but the tile's 2^f blocks are gathered over the
 //            high target bits (plus the lowest free block bits, so copies stay >= 512 bytes).
 // Section IV-B's load buffering is kept: a thread reads its whole group into registers first and
@@ -220,13 +220,6 @@ __global__ void __launch_bounds__(kHighThreads, high_min_blocks<K>()) apply_high
 }
 
 // ------------------------------------------------------------------------------ LOW / MIXED
-__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gsrc)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Tile size in blocks (log2) for the fixed-size tile kernel: 2^F blocks = 32 * 2^F amplitudes,
 // so every lane of the warp owns 2^(F-K) >= 1 groups.
