@@ -58,14 +58,6 @@ struct BItem {
     int tile;
 };
 
-__device__ __forceinline__ unsigned long long bins0(unsigned long long x, int p)
-{
-    const unsigned long long low = x & ((1ull << p) - 1ull);
-    return ((x >> p) << (p + 1)) | low;
-}
-
-__device__ __forceinline__ long long boff(unsigned long long i) { return (long long)(((i >> 5) << 6) | (i & 31ull)); }
-
 template <int V, bool L2ONLY>
 __device__ __forceinline__ void ld_v(const float *p, float (&v)[V])
 {

@@ -157,7 +157,6 @@ __global__ void __launch_bounds__(kEvThreads, M >= 4 ? 3 : 4) expval_kernel(cons
                     ti[i] = fmaf(pr, ui[i], -(pi * ur[i]));
                 }
             }
-#pragma unroll
             if constexpr (M >= 4) {
                 // many strings: an 8-point Walsh-Hadamard transform of the batch's terms gives,
                 // for every mask c of the batch's unit bits, the sum of the terms signed by
