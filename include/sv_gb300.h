@@ -305,6 +305,16 @@ typedef struct sv_batch_opts {
     int tile_log2;      /* groups per tile of a split circuit's step: 2^tile_log2, 5..16 (default 12) */
     int wave_mb;        /* split circuits run in waves of at most this many MB of state, one wave
                            after another, so a wave's states stay in L2; 0 = one wave (default 0) */
+    int stage_log2;     /* 0 (default): a split circuit runs one fused gate per step over global
+                           memory.  8..14: a split circuit of at least 8 qubits runs in stages
+                           instead; a stage is a run of gates (a gate moves ahead only past gates on
+                           other qubits) whose qubits lie in one set of stage_log2 qubits that
+                           includes qubits 0-2, and each of its 2^(n - stage_log2) tiles (the
+                           amplitudes that agree on the other qubits) is loaded into shared memory
+                           once, gets every gate of the stage there and is stored once */
+    int stage_k;        /* staged circuits: each stage's gates are fused again (greedy, fp64
+                           products) into gates of at most stage_k qubits, 1..4; 0 = kept as given
+                           (default 0) */
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
@@ -317,20 +327,39 @@ SV_API int sv_batch_create(const sv_fused *const *circuits, int count, void *are
                            sv_batch **out);
 SV_API void sv_batch_free(sv_batch *b);
 /* Options take effect at the next sv_batch_run (which rebuilds the work list, synchronously, when
- * smem_max_n, split_min_n, tile_log2 or wave_mb changed).  SV_EINVAL for a value out of range. */
+ * smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2 or stage_k changed).  SV_EINVAL for a
+ * value out of range. */
 SV_API int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *opts);
 SV_API int sv_batch_get_opts(const sv_batch *b, sv_batch_opts *opts);
 /* Run every circuit from |0...0> into its state buffer: one persistent launch (asynchronous). */
 SV_API int sv_batch_run(sv_batch *b);
 /* The same work as one launch per fused gate, circuit after circuit (comparison baseline). */
 SV_API int sv_batch_run_loop(sv_batch *b);
+/* What the work list for the current options holds (built here if sv_batch_run has not built it
+ * yet, which needs the device).  traffic_bytes: the bytes the list moves to and from the state
+ * buffers in global memory if nothing stays in cache -- per whole circuit in shared memory one
+ * store of its state; per circuit run gate by gate (one CTA, or split into tiles) a write of the
+ * initial state and a read and a write per fused gate; per staged circuit a read and a write per
+ * stage, less the first stage's read. */
+typedef struct sv_batch_info {
+    int items;              /* work items */
+    int whole;              /* circuits held in shared memory */
+    int single;             /* circuits run by one CTA in global memory */
+    int split;              /* circuits split into tiles of each fused gate */
+    int staged;             /* circuits run in stages */
+    int stages;             /* stages of all staged circuits */
+    int stage_gates;        /* gates of all stages (after stage_k re-fusion) */
+    double traffic_bytes;
+} sv_batch_info;
+SV_API int sv_batch_get_info(sv_batch *b, sv_batch_info *out);
 /* Byte offset of circuit i's state inside the arena. */
 SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes);
 /* Test hook for the bounded waits.  on != 0: from the next sv_batch_run the first split circuit's
- * initialisation step counts one tile more than exists, so the tiles of its first gate wait on a
- * counter that never fills; each gives up after about a second, the launch ends early without a
- * fault, the states are left incomplete and sv_device_status returns SV_ETIMEOUT.  on = 0 undoes
- * it.  No effect when no circuit is split. */
+ * initialisation step (its first stage, when staged) counts one tile more than exists, so the
+ * tiles of the next step wait on a counter that never fills; each gives up after about a second,
+ * the launch ends early without a fault, the states are left incomplete and sv_device_status
+ * returns SV_ETIMEOUT.  on = 0 undoes it.  No effect when no circuit is split, or when the first
+ * split circuit is staged in a single stage. */
 SV_API int sv_batch_inject_stall(sv_batch *b, int on);
 
 /* sv_init(st, basis_index) then sv_apply_fused_gates(st, f, timings), with the same result up to

@@ -1,9 +1,9 @@
 """Batched uneven circuits in one persistent launch, with a project-written autotuner.
 
-The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..4), CTA
-size, the largest circuit kept in shared memory, the smallest circuit split into shared tiles, the
-tile size, the wave size (MB of split-circuit state per wave), and the persistent grid -- by
-coordinate descent
+The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..4), the
+stage tile size (or one pass per fused gate) and the stage re-fusion size, CTA size, the largest
+circuit kept in shared memory, the smallest circuit split across CTAs, the per-gate tile size, the
+wave size (MB of split-circuit state per wave), and the persistent grid -- by coordinate descent
 from a default, each candidate replayed from its captured CUDA graph and timed with CUDA events
 (median of repeats).  The winner is cached in a JSON file keyed by GPU name and a digest of the
 batch's circuit sizes and gate counts.
@@ -40,8 +40,10 @@ class Batch:
         self.fused = [B.sv_fuse_circuit(g, n, max_k=max_k) for n, g in circuits]
         self.h = B.sv_batch_create(self.fused, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
-    def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0):
-        B.sv_batch_set_opts(self.h, threads, smem_max_n, ctas, use_graph, split_min_n, tile_log2, wave_mb)
+    def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0, stage_log2=0,
+            stage_k=0):
+        B.sv_batch_set_opts(self.h, threads, smem_max_n, ctas, use_graph, split_min_n, tile_log2, wave_mb, stage_log2,
+                            stage_k)
 
     def run(self):
         B.sv_batch_run(self.h)
@@ -86,10 +88,18 @@ def digest(circuits) -> str:
     return h.hexdigest()[:16]
 
 
-def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)):
-    """Returns (best settings dict, trial log)."""
+FIELDS = ("threads", "smem_max_n", "ctas", "split_min_n", "tile_log2", "wave_mb", "stage_log2", "stage_k")
+
+
+def apply(b: "Batch", cfg: dict, use_graph: bool = True) -> None:
+    b.set(*(cfg[f] for f in FIELDS[:3]), use_graph, *(cfg[f] for f in FIELDS[3:]))
+
+
+def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4), rounds=2):
+    """Returns (best settings dict, trial log).  Coordinate descent over the fusion size and every
+    batch option, up to `rounds` sweeps (stopping early when a sweep changes nothing)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    key = f"v3|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
+    key = f"v4|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
     if use_cache and os.path.exists(cache):
         try:
             got = json.load(open(cache)).get(key)
@@ -98,43 +108,47 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4)
         except Exception:
             pass
     log = []
-    best = {"max_k": 4, "threads": 256, "smem_max_n": 12, "ctas": 2 * sms, "split_min_n": 15, "tile_log2": 12,
-            "wave_mb": 0}
+    best = {"max_k": 2, "threads": 512, "smem_max_n": 10, "ctas": 2 * sms, "split_min_n": 11, "tile_log2": 12,
+            "wave_mb": 0, "stage_log2": 14, "stage_k": 3}
+    batches = {}
 
-    def measure(cfg, batch=None):
-        own = batch is None
-        b = batch or Batch(circuits, cfg["max_k"])
-        b.set(cfg["threads"], cfg["smem_max_n"], cfg["ctas"], True, cfg["split_min_n"], cfg["tile_log2"], cfg["wave_mb"])
+    def measure(cfg):
+        if cfg["max_k"] not in batches:
+            batches[cfg["max_k"]] = Batch(circuits, cfg["max_k"])
+        b = batches[cfg["max_k"]]
+        apply(b, cfg)
         ms = b.time(b.run, repeats)
-        if own:
-            b.free()
         log.append(dict(cfg, ms=ms))
         return ms
 
-    best_ms = measure(best)
-    for k in k_range:                                   # fusion size
-        if k == best["max_k"]:
-            continue
-        cfg = dict(best, max_k=k)
-        ms = measure(cfg)
-        if ms < best_ms:
-            best, best_ms = cfg, ms
-    b = Batch(circuits, best["max_k"])
-    for field, values in (("threads", (128, 256, 512)), ("smem_max_n", (0, 11, 12, 13, 14)),
-                          ("split_min_n", (0, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
-                          ("wave_mb", (0, 24, 48, 96)),
-                          ("ctas", (sms, 2 * sms, 3 * sms, 4 * sms))):
-        for v in values:
-            if v == best[field]:
-                continue
-            cfg = dict(best, **{field: v})
-            try:
-                ms = measure(cfg, b)
-            except B.SvError:
-                continue
-            if ms < best_ms:
-                best, best_ms = cfg, ms
-    b.free()
+    space = (("max_k", k_range), ("stage_log2", (0, 11, 12, 13, 14)), ("stage_k", (0, 2, 3, 4)),
+             ("threads", (128, 256, 512)), ("smem_max_n", (0, 11, 12, 13, 14)),
+             ("split_min_n", (0, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
+             ("wave_mb", (0, 24, 48, 96)), ("ctas", (sms, 2 * sms, 3 * sms, 4 * sms)))
+    try:
+        best_ms = measure(best)
+        for _ in range(rounds):
+            changed = False
+            for field, values in space:
+                if field == "tile_log2" and best["stage_log2"] > 0:
+                    continue   # per-gate tiles only
+                if field == "stage_k" and best["stage_log2"] == 0:
+                    continue
+                for v in values:
+                    if v == best[field]:
+                        continue
+                    cfg = dict(best, **{field: v})
+                    try:
+                        ms = measure(cfg)
+                    except B.SvError:
+                        continue
+                    if ms < best_ms:
+                        best, best_ms, changed = cfg, ms, True
+            if not changed:
+                break
+    finally:
+        for b in batches.values():
+            b.free()
     best = dict(best, ms=best_ms)
     try:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
@@ -150,16 +164,30 @@ def report(count=256, seed=5):
     circuits = wl.hea_batch(count=count, seed=seed)
     best, log = autotune(circuits, use_cache=False)
     b = Batch(circuits, best["max_k"])
-    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, best["split_min_n"], best["tile_log2"], best["wave_mb"])
+    apply(b, best)
+    info = B.sv_batch_get_info(b.h)
     t_batch = b.time(b.run)
-    b.set(best["threads"], best["smem_max_n"], best["ctas"], True, 0, best["tile_log2"], best["wave_mb"])
+    apply(b, dict(best, stage_log2=0))
+    info_gate = B.sv_batch_get_info(b.h)
+    t_per_gate = b.time(b.run)
+    apply(b, dict(best, stage_log2=0, split_min_n=0))
     t_nosplit = b.time(b.run)
-    t_loop = b.time(b.run_loop, repeats=3)
-    traffic = sum(16 * (1 << n) * len([0 for _ in range(B.sv_fused_count(f))]) for n, f in zip(b.ns, b.fused))
+    t_loop_same_k = b.time(b.run_loop, repeats=3)
+    # the comparisons at their own best fusion size (k = 4 for one launch or one pass per gate)
+    b4 = Batch(circuits, 4)
+    apply(b4, dict(best, max_k=4, threads=256, smem_max_n=12, split_min_n=15, tile_log2=13, wave_mb=0, stage_log2=0,
+                   stage_k=0))
+    t_per_gate_k4 = b4.time(b4.run)
+    t_loop = b4.time(b4.run_loop, repeats=3)
+    b4.free()
     out = {"workload": f"{count} HEA circuits, n ~ U{{10..20}}, 8 layers RZ RY + CZ ladder, seed {seed}",
-           "batched_ms": t_batch, "batched_no_split_ms": t_nosplit, "loop_ms": t_loop, "speedup": t_loop / t_batch, "autotuned": best,
-           "trials": len(log), "fused_gates": sum(B.sv_fused_count(f) for f in b.fused),
-           "state_mb": b.nbytes / 1e6, "pass_traffic_gb": traffic / 1e9}
+           "batched_ms": t_batch, "batched_per_gate_tiles_ms": t_per_gate, "batched_no_split_ms": t_nosplit,
+           "batched_per_gate_tiles_k4_ms": t_per_gate_k4, "loop_ms": t_loop, "loop_same_k_ms": t_loop_same_k,
+           "speedup": t_loop / t_batch, "autotuned": best, "trials": len(log),
+           "fused_gates": sum(B.sv_fused_count(f) for f in b.fused), "state_mb": b.nbytes / 1e6,
+           "list": info, "traffic_gb": info["traffic_bytes"] / 1e9,
+           "traffic_gbs": info["traffic_bytes"] / (t_batch * 1e-3) / 1e9,
+           "per_gate_traffic_gb": info_gate["traffic_bytes"] / 1e9}
     b.free()
     return out
 

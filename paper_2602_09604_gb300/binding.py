@@ -60,7 +60,13 @@ class sv_mlp_stats(ctypes.Structure):
 class sv_batch_opts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("smem_max_n", ctypes.c_int), ("ctas", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("split_min_n", ctypes.c_int), ("tile_log2", ctypes.c_int),
-                ("wave_mb", ctypes.c_int)]
+                ("wave_mb", ctypes.c_int), ("stage_log2", ctypes.c_int), ("stage_k", ctypes.c_int)]
+
+
+class sv_batch_info(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int), ("whole", ctypes.c_int), ("single", ctypes.c_int), ("split", ctypes.c_int),
+                ("staged", ctypes.c_int), ("stages", ctypes.c_int), ("stage_gates", ctypes.c_int),
+                ("traffic_bytes", ctypes.c_double)]
 
 
 class sv_timing(ctypes.Structure):
@@ -108,6 +114,7 @@ def _load():
         "sv_batch_run_loop": (I, [P]),
         "sv_batch_state_offset": (I, [P, I, ctypes.POINTER(ctypes.c_size_t)]),
         "sv_batch_inject_stall": (I, [P, I]),
+        "sv_batch_get_info": (I, [P, ctypes.POINTER(sv_batch_info)]),
         "sv_mlp_num_params": (I, []),
         "sv_mlp_create": (I, [ctypes.c_uint64, P, ctypes.POINTER(P)]),
         "sv_mlp_free": (None, [P]),
@@ -453,8 +460,10 @@ def sv_batch_free(b) -> None:
 
 
 def sv_batch_set_opts(b, threads: int, smem_max_n: int, ctas: int, use_graph: bool = True,
-                      split_min_n: int = 15, tile_log2: int = 12, wave_mb: int = 0) -> None:
-    o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)), split_min_n, tile_log2, wave_mb)
+                      split_min_n: int = 15, tile_log2: int = 12, wave_mb: int = 0, stage_log2: int = 0,
+                      stage_k: int = 0) -> None:
+    o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)), split_min_n, tile_log2, wave_mb, stage_log2,
+                      stage_k)
     _check(lib.sv_batch_set_opts(b, ctypes.byref(o)))
 
 
@@ -462,6 +471,12 @@ def sv_batch_get_opts(b) -> dict:
     o = sv_batch_opts()
     _check(lib.sv_batch_get_opts(b, ctypes.byref(o)))
     return {f: getattr(o, f) for f, _ in sv_batch_opts._fields_}
+
+
+def sv_batch_get_info(b) -> dict:
+    o = sv_batch_info()
+    _check(lib.sv_batch_get_info(b, ctypes.byref(o)))
+    return {f: getattr(o, f) for f, _ in sv_batch_info._fields_}
 
 
 def sv_batch_run(b) -> None:

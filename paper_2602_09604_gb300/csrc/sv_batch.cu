@@ -12,7 +12,16 @@
 //     Items are dequeued in list order and a dequeued item is held by a running CTA, so the tiles
 //     waited on were taken earlier and finish (by induction on list position): no deadlock.  The
 //     list interleaves the large circuits step by step, so a wait overlaps other circuits' work,
-//     optionally in waves of at most `wave_mb` MB of state so that a wave stays in L2.
+//     optionally in waves of at most `wave_mb` MB of state so that a wave stays in L2;
+//   * or, with `stage_log2` = L set, a tile of one stage of a large circuit: the host cuts the
+//     circuit into stages, each a set of gates whose qubits all lie in one set S of L qubits
+//     (gates move ahead only past gates on other qubits, so the order of the circuit is kept).
+//     The tiles of a stage are the 2^(n-L) sets of amplitudes that agree on the qubits outside
+//     S; a CTA loads its tile into shared memory once, applies every gate of the stage there
+//     (targets renumbered inside S) and stores it once, so the state crosses memory once per
+//     stage instead of once per gate.  S always holds qubits 0-2, so every tile moves in whole
+//     32-byte runs.  The first stage writes |0...0> instead of loading.  A tile waits (bounded)
+//     for every tile of the previous stage, as the steps above do.
 // States use the library's blocked layout (32 reals then 32 imaginaries per 256-byte block).
 // The launch can be captured once in a CUDA graph and replayed.
 #include <algorithm>
@@ -41,15 +50,37 @@ struct BCirc {
     int n;
     int gate_begin;
     int gate_count;
-    int done_off;            // large circuits: first completion counter (one per step)
+    int done_off;            // large circuits: first completion counter (one per step or stage)
+    int stage_begin;         // staged circuits: first stage in the stage table
+    int n_stages;
 };
+
+// One stage of a staged circuit: its tiles hold the qubits of `lmask` (local qubit i = the i-th
+// set bit); its gates (in the stage gate table, naming local qubits) come in chunks whose
+// descriptors and matrices fit the shared-memory areas reserved for them.
+struct BStage {
+    unsigned lmask;
+    int chunk_begin;
+    int chunk_count;
+};
+
+struct BChunk {
+    int gate_begin;          // in the stage gate table
+    int gate_count;
+    int mat_begin;           // the chunk's matrices: one contiguous range of the stage matrix table
+    int mat_count;           // (float2 units)
+};
+
+constexpr int kStageMatCap = 4096;   // float2 of matrices per chunk (32 KB): 64 three-qubit gates
+constexpr int kStageGateCap = 64;    // gate descriptors per chunk
 
 // Work item kinds.  A circuit runs as one of them:
 //   kWhole  - circuit c entirely in one CTA's shared memory;
 //   kSingle - circuit c by one CTA in its global buffer, gate after gate;
 //   kTile   - tile `tile` of step `step` of circuit c, in its global buffer (step 0 writes |0...0>,
-//             step s >= 1 applies fused gate s-1 to 2^tile_log2 groups).
-enum : int { kWhole = 0, kSingle = 1, kTile = 2 };
+//             step s >= 1 applies fused gate s-1 to 2^tile_log2 groups);
+//   kStage  - tile `tile` of stage `step` of circuit c, through shared memory.
+enum : int { kWhole = 0, kSingle = 1, kTile = 2, kStage = 3 };
 
 struct BItem {
     int kind;
@@ -85,13 +116,26 @@ __device__ __forceinline__ void st_v(float *p, const float (&v)[V])
 // memory.  A thread takes V consecutive groups at a time: with no target below log2(V) their
 // amplitudes are V consecutive positions of a block, moved with one V-wide access (and each
 // matrix element read once serves V groups).  Offsets are 32-bit and recomputed for the stores.
-template <int K, int V, bool L2ONLY>
+//
+// XS (S in shared memory): with m targets below qubit 5, the 32 consecutive groups of one
+// shared-memory access phase lie in 2^m blocks, and for a fixed local index j all of them sit at
+// positions with the same low-target bits, so two blocks' halves would meet in the same banks.
+// Each thread therefore takes its amplitudes in the order j ^ s, s = the index of its block among
+// the 2^m: it holds x'[j] = x[j ^ s], forms y'[r] = sum_j U[r ^ s][j ^ s] x'[j] = y[r ^ s] and
+// stores it at the place of r ^ s.  The result is the same; the phase's accesses cover every bank
+// once.
+template <int K, int V, bool L2ONLY, bool XS>
 __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
 {
     constexpr int D = 1 << K;
     unsigned bit[K];
+    int nlow = 0;
 #pragma unroll
-    for (int b = 0; b < K; ++b) bit[b] = 1u << g.targets[b];
+    for (int b = 0; b < K; ++b) {
+        bit[b] = 1u << g.targets[b];
+        nlow += g.targets[b] < 5;
+    }
+    const unsigned fshift = 5u - (unsigned)nlow, smask = (1u << nlow) - 1u;
     for (unsigned it = g_begin / V + threadIdx.x; it < g_end / V; it += blockDim.x) {
         // the matrix pointer goes through an opaque move each iteration: otherwise the 4^K
         // loop-invariant matrix loads are hoisted out of this loop into registers
@@ -107,13 +151,19 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
             const unsigned low = base & (bit[b] - 1u);
             base = ((base - low) << 1) | low;
         }
+        unsigned s = 0u;   // XS: this thread's local-index offset (bits of the low targets)
+        if constexpr (XS) {
+            s = ((it * V) >> fshift) & smask;
+#pragma unroll
+            for (int b = 0; b < K; ++b) base |= ((s >> b) & 1u) ? bit[b] : 0u;   // base of index s
+        }
         float xr[D][V], xi[D][V];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             unsigned i = base;
 #pragma unroll
             for (int b = 0; b < K; ++b)
-                if ((j >> b) & 1) i |= bit[b];
+                if ((j >> b) & 1) i ^= bit[b];   // index j ^ s (plain j when s = 0)
             const unsigned o = ((i >> 5) << 6) | (i & 31u);
             // L2ONLY: other CTAs wrote these, so read through L2 rather than a stale L1 line
             ld_v<V, L2ONLY>(S + o, xr[j]);
@@ -124,9 +174,10 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
             float yr[V], yi[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) yr[v] = yi[v] = 0.f;
+            const float2 *Ur = Ui + ((unsigned)r ^ s) * D;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const float2 u = Ui[r * D + j];
+                const float2 u = XS ? Ur[(unsigned)j ^ s] : Ui[r * D + j];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     yr[v] = fmaf(u.x, xr[j][v], yr[v]);
@@ -138,7 +189,7 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
             unsigned i = base;
 #pragma unroll
             for (int b = 0; b < K; ++b)
-                if ((r >> b) & 1) i |= bit[b];
+                if ((r >> b) & 1) i ^= bit[b];
             const unsigned o = ((i >> 5) << 6) | (i & 31u);
             st_v<V>(S + o, yr);
             st_v<V>(S + o + 32, yi);
@@ -150,18 +201,18 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
 // 2^(n-K) groups.  WIDE (CTAs of at most 256 threads, up to 255 registers a thread) allows K = 4
 // with V > 1; with 512-thread CTAs (128 registers) K = 4 keeps V = 1, whose 2^5 inputs per group
 // already fill the budget.
-template <bool L2ONLY, bool WIDE>
+template <bool L2ONLY, bool WIDE, bool XS>
 __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U, unsigned g_begin, unsigned g_end)
 {
     const int t0 = g.targets[0];   // ascending
     int v = t0 >= 2 ? 4 : (t0 == 1 ? 2 : 1);
     if (g.k == 4 && !WIDE) v = 1;
     while (v > 1 && (1 << (n - g.k)) < v) v >>= 1;
-#define SV_BATCH_CASE(KK)                                                         \
-    case KK:                                                                      \
-        if (v == 4) apply_in_cta<KK, 4, L2ONLY>(S, g, U, g_begin, g_end);         \
-        else if (v == 2) apply_in_cta<KK, 2, L2ONLY>(S, g, U, g_begin, g_end);    \
-        else apply_in_cta<KK, 1, L2ONLY>(S, g, U, g_begin, g_end);                \
+#define SV_BATCH_CASE(KK)                                                             \
+    case KK:                                                                          \
+        if (v == 4) apply_in_cta<KK, 4, L2ONLY, XS>(S, g, U, g_begin, g_end);         \
+        else if (v == 2) apply_in_cta<KK, 2, L2ONLY, XS>(S, g, U, g_begin, g_end);    \
+        else apply_in_cta<KK, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);                \
         break;
     switch (g.k) {
     SV_BATCH_CASE(1)
@@ -169,11 +220,11 @@ __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U,
     SV_BATCH_CASE(3)
     default:
         if constexpr (WIDE) {
-            if (v == 4) apply_in_cta<4, 4, L2ONLY>(S, g, U, g_begin, g_end);
-            else if (v == 2) apply_in_cta<4, 2, L2ONLY>(S, g, U, g_begin, g_end);
-            else apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+            if (v == 4) apply_in_cta<4, 4, L2ONLY, XS>(S, g, U, g_begin, g_end);
+            else if (v == 2) apply_in_cta<4, 2, L2ONLY, XS>(S, g, U, g_begin, g_end);
+            else apply_in_cta<4, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);
         } else {
-            apply_in_cta<4, 1, L2ONLY>(S, g, U, g_begin, g_end);
+            apply_in_cta<4, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);
         }
         break;
     }
@@ -193,11 +244,46 @@ struct BatchArgs {
     int n_items;
     const BGate *gates;
     const float2 *mats;
+    const BStage *stages;    // staged circuits: stage table
+    const BChunk *chunks;    // their gate chunks
+    const BGate *sgates;     // stage gates (local targets)
+    const float2 *smats;     // their matrices
+    int mat_cap;             // float2 of the shared-memory matrix area (>= 4^kBatchMaxK)
+    int gate_cap;            // gate descriptors of the shared-memory descriptor area
     int *sync;         // [0] queue head, [1] abort flag, [2 + i] completion counter i
-    const int *need;   // tiles of each counted step
+    const int *need;   // tiles of each counted step or stage
     int *err;          // library-wide device error word
     int tile_log2;
+    int stage_log2;
 };
+
+// x's bits deposited, lowest first, into the set bits of mask
+__device__ __host__ __forceinline__ unsigned deposit_bits(unsigned x, unsigned mask)
+{
+    unsigned r = 0u;
+    for (unsigned m = mask; m != 0u; m &= m - 1u) {
+        if (x & 1u) r |= m & (0u - m);
+        x >>= 1;
+    }
+    return r;
+}
+
+// Bounded wait (thread 0) until counter d reaches want; false when it gave up or another CTA
+// already did (the abort flag), after raising the abort flag and the error word.
+__device__ bool wait_count(const BatchArgs &A, const int *d, int want)
+{
+    long long spin = 0;
+    while (*(const volatile int *)d < want) {
+        if (*(volatile int *)(A.sync + 1) || ++spin > kSpinLimit) {
+            atomicExch(A.sync + 1, 1);
+            atomicCAS(A.err, 0, kBatchErrCode);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    __threadfence();   // acquire: the counted tiles' writes before this tile's reads
+    return true;
+}
 
 __device__ __forceinline__ void stage_matrix(float2 *sU, const float2 *mats, const BGate &g)
 {
@@ -215,10 +301,12 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float smem[];
-    float2 *sU = reinterpret_cast<float2 *>(smem);                  // (1 << 2*kBatchMaxK) complex
-    float *sS = smem + 2 * (1 << (2 * kBatchMaxK));                   // state of a shared-memory circuit
+    float2 *sU = reinterpret_cast<float2 *>(smem);                  // matrix area: A.mat_cap complex
+    BGate *sG = reinterpret_cast<BGate *>(smem + 2 * A.mat_cap);     // staged: a chunk's descriptors
+    float *sS = smem + 2 * A.mat_cap + A.gate_cap * (int)(sizeof(BGate) / 4);   // circuit state or tile
     __shared__ int cur;
     __shared__ int ok;
+    __shared__ unsigned sT[96];   // staged tiles: deposits of local index bits 3-8 ([0, 64)) and 9-13
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(reinterpret_cast<unsigned *>(A.sync), 1u);
         __syncthreads();
@@ -229,6 +317,78 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
         const BCirc C = A.circ[W.c];
         float *G = A.arena + C.state_off;
         const long long nf = state_floats(C.n);
+        if (W.kind == kStage) {
+            int *done = A.sync + 2 + C.done_off;
+            const BStage St = A.stages[C.stage_begin + W.step];
+            const int L = C.n < A.stage_log2 ? C.n : A.stage_log2;   // tile qubits (>= 8)
+            const unsigned hmask = ((1u << C.n) - 1u) & ~St.lmask;
+            const unsigned tb = deposit_bits((unsigned)W.tile, hmask);   // the tile's fixed bits
+            // a chunk's gate descriptors and matrices into shared memory (the first chunk's copy
+            // overlaps the wait and the tile load)
+            auto load_chunk = [&](int ci) -> BChunk {
+                const BChunk ch = A.chunks[St.chunk_begin + ci];
+                const int *src = reinterpret_cast<const int *>(A.sgates + ch.gate_begin);
+                int *dst = reinterpret_cast<int *>(sG);
+                for (int i = threadIdx.x; i < ch.gate_count * (int)(sizeof(BGate) / 4); i += blockDim.x) dst[i] = src[i];
+                for (int i = threadIdx.x; i < ch.mat_count; i += blockDim.x) sU[i] = A.smats[ch.mat_begin + i];
+                return ch;
+            };
+            BChunk ch{};
+            if (St.chunk_count > 0) ch = load_chunk(0);
+            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, A.need[C.done_off + W.step - 1]);
+            for (unsigned i = threadIdx.x; i < 96u; i += blockDim.x)
+                sT[i] = i < 64u ? deposit_bits(i << 3, St.lmask) : deposit_bits((i - 64u) << 9, St.lmask);
+            __syncthreads();
+            if (!ok) break;
+            // local index l -> global index: bits 0-2 stay (S holds qubits 0-2), the rest deposit
+            // into S's higher qubits, the tile's bits fill the others.  A thread moves four
+            // amplitudes (16 bytes of real and of imaginary parts) at a time; eight consecutive
+            // local indices are one 32-byte run in global memory.
+            const int nq = 1 << (L - 2);
+            auto gofs = [&](unsigned l) -> unsigned {
+                const unsigned gi = (l & 7u) | sT[(l >> 3) & 63u] | sT[64 + (l >> 9)] | tb;
+                return ((gi >> 5) << 6) | (gi & 31u);
+            };
+            if (W.step == 0) {
+                zero_floats(sS, 0, 2ll << L);
+                __syncthreads();
+                if (W.tile == 0 && threadIdx.x == 0) sS[0] = 1.f;
+            } else {
+                for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                    const unsigned l = (unsigned)q << 2;
+                    const unsigned go = gofs(l), lo = ((l >> 5) << 6) | (l & 31u);
+                    // read through L2: other CTAs wrote these in the previous stage
+                    const float4 re = __ldcg(reinterpret_cast<const float4 *>(G + go));
+                    const float4 im = __ldcg(reinterpret_cast<const float4 *>(G + go + 32));
+                    *reinterpret_cast<float4 *>(sS + lo) = re;
+                    *reinterpret_cast<float4 *>(sS + lo + 32) = im;
+                }
+            }
+            __syncthreads();
+            for (int ci = 0; ci < St.chunk_count; ++ci) {
+                if (ci > 0) {   // the previous chunk's last gate ended with a barrier
+                    ch = load_chunk(ci);
+                    __syncthreads();
+                }
+                for (int gi = 0; gi < ch.gate_count; ++gi) {
+                    const BGate g = sG[gi];
+                    apply_gate_cta<false, (MAXT <= 256), true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
+                    __syncthreads();   // this gate's writes before the next gate's reads
+                }
+            }
+            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                const unsigned l = (unsigned)q << 2;
+                const unsigned go = gofs(l), lo = ((l >> 5) << 6) | (l & 31u);
+                *reinterpret_cast<float4 *>(G + go) = *reinterpret_cast<const float4 *>(sS + lo);
+                *reinterpret_cast<float4 *>(G + go + 32) = *reinterpret_cast<const float4 *>(sS + lo + 32);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();   // release: this tile's writes before the count
+                atomicAdd(done + W.step, 1);
+            }
+            continue;
+        }
         if (W.kind != kTile) {
             // whole circuit in one CTA: shared memory or the global buffer
             float *S = W.kind == kWhole ? sS : G;
@@ -239,7 +399,8 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                 const BGate g = A.gates[C.gate_begin + gi];
                 stage_matrix(sU, A.mats, g);
                 __syncthreads();   // matrix staged; previous gate's writes visible
-                apply_gate_cta<false, (MAXT <= 256)>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                if (W.kind == kWhole) apply_gate_cta<false, (MAXT <= 256), true>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                else apply_gate_cta<false, (MAXT <= 256), false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
                 __syncthreads();
             }
             if (W.kind == kWhole) {
@@ -251,24 +412,7 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
         }
         // one tile of one step of a large circuit
         int *done = A.sync + 2 + C.done_off;
-        if (threadIdx.x == 0) {
-            ok = 1;
-            if (W.step > 0) {
-                const volatile int *d = done + W.step - 1;
-                const int want = A.need[C.done_off + W.step - 1];
-                long long spin = 0;
-                while (*d < want) {
-                    if (*(volatile int *)(A.sync + 1) || ++spin > kSpinLimit) {
-                        ok = 0;
-                        atomicExch(A.sync + 1, 1);
-                        atomicCAS(A.err, 0, kBatchErrCode);
-                        break;
-                    }
-                    __nanosleep(128);
-                }
-                __threadfence();   // acquire: the previous step's writes before this step's reads
-            }
-        }
+        if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, A.need[C.done_off + W.step - 1]);
         __syncthreads();
         if (!ok) break;
         if (W.step == 0) {
@@ -284,7 +428,7 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
             const unsigned groups = 1u << (C.n - g.k);
             const unsigned g0 = (unsigned)W.tile << A.tile_log2;
             const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
-            apply_gate_cta<true, (MAXT <= 256)>(G, C.n, g, sU, g0, g1);
+            apply_gate_cta<true, (MAXT <= 256), false>(G, C.n, g, sU, g0, g1);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -309,6 +453,7 @@ struct sv_batch {
     std::vector<const sv_fused *> fused;
     std::vector<BCirc> hc;           // per circuit, largest first (device order)
     std::vector<BGate> hg;
+    std::vector<const FusedGate *> src;   // per entry of hg: the fused gate it came from
     BCirc *d_circ = nullptr;
     BGate *d_gates = nullptr;
     float2 *d_mats = nullptr;
@@ -316,24 +461,95 @@ struct sv_batch {
     BItem *d_items = nullptr;
     int *d_need = nullptr;
     int *d_sync = nullptr;
+    BStage *d_stages = nullptr;      // staged circuits (stage_log2 > 0): stages, chunks, gates, matrices
+    BChunk *d_chunks = nullptr;
+    BGate *d_sgates = nullptr;
+    float2 *d_smats = nullptr;
     int *d_err = nullptr;            // library's device error word (not owned)
     int n_items = 0;
     int n_counters = 0;
-    int list_cfg[4] = {-1, -1, -1, -1};   // smem_max_n, split_min_n, tile_log2, wave_mb
+    sv_batch_info info{};            // what the current list holds
+    int list_cfg[6] = {-1, -1, -1, -1, -1, -1};   // smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2, stage_k
     bool stall = false;              // test hook: first split step counts one tile too many
     bool list_stall = false;
     sv_batch_opts opts{};
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[6] = {0, 0, 0, 0, 0, 0};
+    int graph_cfg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
 
 size_t state_bytes(int n) { return sizeof(float) * (size_t)state_floats(n); }
 
+// shared-memory areas: matrices, gate descriptors, then the state of a whole circuit or a tile
+int mat_cap(const sv_batch_opts &o) { return o.stage_log2 > 0 ? kStageMatCap : 1 << (2 * kBatchMaxK); }
+int gate_cap(const sv_batch_opts &o) { return o.stage_log2 > 0 ? kStageGateCap : 0; }
+
 size_t smem_bytes(const sv_batch_opts &o)
 {
-    return sizeof(float) * 2 * (1 << (2 * kBatchMaxK)) + (o.smem_max_n > 0 ? state_bytes(o.smem_max_n) : 0);
+    const size_t whole = o.smem_max_n > 0 ? state_bytes(o.smem_max_n) : 0;
+    const size_t tile = o.stage_log2 > 0 ? state_bytes(o.stage_log2) : 0;
+    return sizeof(float2) * (size_t)mat_cap(o) + sizeof(BGate) * (size_t)gate_cap(o) + std::max(whole, tile);
+}
+
+constexpr int kStageMinN = 8;         // staged circuits have at least this many qubits
+constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
+
+// Cut circuit gates gs (global targets, n qubits) into stages of at most L local qubits and append
+// them to the stage tables: stage gates are re-fused to at most stage_k qubits (0: kept as they
+// are) and renumbered to local qubits.  Greedy: scan the gates not yet placed in circuit order;
+// a gate joins the stage when no earlier unplaced gate shares a qubit with it (so it commutes
+// past every gate it overtakes) and the stage's qubits with its own still number at most L;
+// otherwise its qubits are closed for the rest of the scan.  The local set is then filled up to
+// L qubits with the lowest unused ones (longer contiguous runs per tile).
+void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, std::vector<BStage> &st,
+                  std::vector<BChunk> &chunks, std::vector<BGate> &sg, std::vector<float2> &sm)
+{
+    std::vector<const FusedGate *> rest = gs;
+    bool first = true;
+    while (first || !rest.empty()) {
+        first = false;
+        unsigned S = kStageBase, blocked = 0u;
+        std::vector<const FusedGate *> taken, left;
+        for (const FusedGate *g : rest) {
+            const unsigned q = (unsigned)g->mask;
+            if (!(q & blocked) && __builtin_popcount(S | q) <= L) {
+                S |= q;
+                taken.push_back(g);
+            } else {
+                blocked |= q;
+                left.push_back(g);
+            }
+        }
+        for (int b = 0; b < n && __builtin_popcount(S) < L; ++b) S |= 1u << b;
+        BStage bs{};
+        bs.lmask = S;
+        bs.chunk_begin = (int)chunks.size();
+        std::vector<FusedGate> fused;
+        if (stage_k > 0) fused = refuse_gates(taken, n, stage_k);
+        auto emit = [&](const FusedGate &g) {
+            const int dd = (int)g.ur.size();
+            if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
+                chunks.back().mat_count + dd > kStageMatCap)
+                chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
+            BGate b{};
+            b.k = g.k;
+            for (int j = 0; j < g.k; ++j) b.targets[j] = __builtin_popcount(S & ((1u << g.targets[j]) - 1u));
+            b.mat_off = (int)sm.size();
+            for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g.ur[(size_t)e], g.ui[(size_t)e]));
+            sg.push_back(b);
+            chunks.back().gate_count += 1;
+            chunks.back().mat_count += dd;
+        };
+        if (stage_k > 0) {
+            for (const FusedGate &g : fused) emit(g);
+        } else {
+            for (const FusedGate *g : taken) emit(*g);
+        }
+        bs.chunk_count = (int)chunks.size() - bs.chunk_begin;
+        st.push_back(bs);
+        rest.swap(left);
+    }
 }
 
 // Work list: single-CTA circuits in global memory first (largest first: the rigid chains start
@@ -341,17 +557,40 @@ size_t smem_bytes(const sv_batch_opts &o)
 // held in shared memory (short; they fill the tail).
 int build_work_list(sv_batch *b)
 {
-    const int cfg[4] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb};
+    const int cfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                        b->opts.stage_k};
     if (b->d_items && std::memcmp(cfg, b->list_cfg, sizeof(cfg)) == 0 && b->list_stall == b->stall) return SV_OK;
     std::vector<BItem> items;
     std::vector<int> need;
     std::vector<BCirc> hc = b->hc;
     std::vector<int> split;
+    std::vector<BStage> hst;
+    std::vector<BChunk> hch;
+    std::vector<BGate> hsg;
+    std::vector<float2> hsm;
     for (int c = 0; c < (int)hc.size(); ++c) {
         const int n = hc[(size_t)c].n;
         hc[(size_t)c].done_off = 0;
+        hc[(size_t)c].stage_begin = 0;
+        hc[(size_t)c].n_stages = 0;
         if (n <= b->opts.smem_max_n) continue;
-        if (b->opts.split_min_n > 0 && n >= b->opts.split_min_n) {
+        if (b->opts.split_min_n > 0 && n >= b->opts.split_min_n && b->opts.stage_log2 > 0 && n >= kStageMinN) {
+            // staged: one counter per stage, 2^(n - L) tiles each
+            const int L = std::min(n, b->opts.stage_log2);
+            std::vector<const FusedGate *> gs;
+            for (int gi = 0; gi < hc[(size_t)c].gate_count; ++gi) gs.push_back(b->src[(size_t)(hc[(size_t)c].gate_begin + gi)]);
+            hc[(size_t)c].stage_begin = (int)hst.size();
+            try {
+                build_stages(gs, n, L, b->opts.stage_k, hst, hch, hsg, hsm);
+            } catch (const std::bad_alloc &) {
+                set_error("sv_batch: out of host memory building stages");
+                return SV_ENOMEM;
+            }
+            hc[(size_t)c].n_stages = (int)hst.size() - hc[(size_t)c].stage_begin;
+            hc[(size_t)c].done_off = (int)need.size();
+            for (int s = 0; s < hc[(size_t)c].n_stages; ++s) need.push_back(1 << (n - L));
+            split.push_back(c);
+        } else if (b->opts.split_min_n > 0 && n >= b->opts.split_min_n) {
             hc[(size_t)c].done_off = (int)need.size();
             const long long span = 2ll << (b->opts.tile_log2 + 3);
             need.push_back((int)((state_floats(n) + span - 1) / span));
@@ -385,10 +624,11 @@ int build_work_list(sv_batch *b)
         for (int s = 0;; ++s) {
             bool any = false;
             for (int c : wave) {
-                if (s > hc[(size_t)c].gate_count) continue;
+                const bool staged = hc[(size_t)c].n_stages > 0;
+                if (s >= (staged ? hc[(size_t)c].n_stages : hc[(size_t)c].gate_count + 1)) continue;
                 any = true;
                 const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
-                for (int i = 0; i < t; ++i) items.push_back(BItem{kTile, c, s, i});
+                for (int i = 0; i < t; ++i) items.push_back(BItem{staged ? kStage : kTile, c, s, i});
             }
             if (!any) break;
         }
@@ -398,16 +638,52 @@ int build_work_list(sv_batch *b)
     cudaFree(b->d_items);
     cudaFree(b->d_need);
     cudaFree(b->d_sync);
+    cudaFree(b->d_stages);
+    cudaFree(b->d_chunks);
+    cudaFree(b->d_sgates);
+    cudaFree(b->d_smats);
     b->d_items = nullptr;
     b->d_need = nullptr;
     b->d_sync = nullptr;
+    b->d_stages = nullptr;
+    b->d_chunks = nullptr;
+    b->d_sgates = nullptr;
+    b->d_smats = nullptr;
     b->n_items = (int)items.size();
     b->n_counters = (int)need.size();
+    {
+        sv_batch_info in{};
+        in.items = (int)items.size();
+        in.stages = (int)hst.size();
+        in.stage_gates = (int)hsg.size();
+        for (const BCirc &c : hc) {
+            const double sb = (double)state_bytes(c.n);
+            if (c.n <= b->opts.smem_max_n) {
+                ++in.whole;
+                in.traffic_bytes += sb;
+            } else if (c.n_stages > 0) {
+                ++in.staged;
+                in.traffic_bytes += sb * (2.0 * c.n_stages - 1.0);
+            } else {
+                ++(b->opts.split_min_n > 0 && c.n >= b->opts.split_min_n ? in.split : in.single);
+                in.traffic_bytes += sb * (1.0 + 2.0 * c.gate_count);
+            }
+        }
+        b->info = in;
+    }
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(BItem) * std::max<size_t>(items.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_need, sizeof(int) * std::max<size_t>(need.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, sizeof(int) * (2 + need.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_stages, sizeof(BStage) * std::max<size_t>(hst.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_chunks, sizeof(BChunk) * std::max<size_t>(hch.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sgates, sizeof(BGate) * std::max<size_t>(hsg.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_smats, sizeof(float2) * std::max<size_t>(hsm.size(), 1));
     if (e == cudaSuccess && !items.empty()) e = cudaMemcpy(b->d_items, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !need.empty()) e = cudaMemcpy(b->d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hst.empty()) e = cudaMemcpy(b->d_stages, hst.data(), sizeof(BStage) * hst.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hch.empty()) e = cudaMemcpy(b->d_chunks, hch.data(), sizeof(BChunk) * hch.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hsg.empty()) e = cudaMemcpy(b->d_sgates, hsg.data(), sizeof(BGate) * hsg.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !hsm.empty()) e = cudaMemcpy(b->d_smats, hsm.data(), sizeof(float2) * hsm.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_circ, hc.data(), sizeof(BCirc) * hc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         b->list_cfg[0] = -1;
@@ -428,10 +704,17 @@ int launch_batch(sv_batch *b)
     a.n_items = b->n_items;
     a.gates = b->d_gates;
     a.mats = b->d_mats;
+    a.stages = b->d_stages;
+    a.chunks = b->d_chunks;
+    a.mat_cap = mat_cap(b->opts);
+    a.gate_cap = gate_cap(b->opts);
+    a.sgates = b->d_sgates;
+    a.smats = b->d_smats;
     a.sync = b->d_sync;
     a.need = b->d_need;
     a.err = b->d_err;
     a.tile_log2 = b->opts.tile_log2;
+    a.stage_log2 = b->opts.stage_log2;
     SV_CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, sizeof(int) * (2 + (size_t)b->n_counters), b->stream));
     if (b->opts.threads <= 256)
         batch_kernel<256><<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
@@ -449,6 +732,8 @@ int check_opts(const sv_batch_opts &o)
     if (o.split_min_n < 0 || o.split_min_n > kBatchMaxN) { set_error("sv_batch: split_min_n must be in [0, %d]", kBatchMaxN); return SV_EINVAL; }
     if (o.tile_log2 < 5 || o.tile_log2 > 16) { set_error("sv_batch: tile_log2 must be in [5, 16]"); return SV_EINVAL; }
     if (o.wave_mb < 0 || o.wave_mb > (1 << 20)) { set_error("sv_batch: wave_mb must be in [0, 2^20]"); return SV_EINVAL; }
+    if (o.stage_log2 != 0 && (o.stage_log2 < kStageMinN || o.stage_log2 > 14)) { set_error("sv_batch: stage_log2 must be 0 or in [%d, 14]", kStageMinN); return SV_EINVAL; }
+    if (o.stage_k < 0 || o.stage_k > kBatchMaxK) { set_error("sv_batch: stage_k must be in [0, %d]", kBatchMaxK); return SV_EINVAL; }
     return SV_OK;
 }
 
@@ -505,6 +790,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     std::vector<BCirc> hc;
     std::vector<BGate> hg;
     std::vector<float2> hm;
+    std::vector<const FusedGate *> src;
     for (int i : order) {
         BCirc c{};
         c.state_off = b->off[(size_t)i];
@@ -517,6 +803,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
             bg.mat_off = (int)hm.size();
             for (size_t e = 0; e < g.ur.size(); ++e) hm.push_back(make_float2(g.ur[e], g.ui[e]));
             hg.push_back(bg);
+            src.push_back(&g);
         }
         c.gate_count = (int)hg.size() - c.gate_begin;
         hc.push_back(c);
@@ -533,6 +820,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     }
     b->hc = std::move(hc);
     b->hg = std::move(hg);
+    b->src = std::move(src);
     // the error word is allocated here, outside any later stream capture
     if (device_err_word(&b->d_err) != SV_OK) {
         sv_batch_free(b);
@@ -546,6 +834,8 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     b->opts.split_min_n = 15;
     b->opts.tile_log2 = 12;
     b->opts.wave_mb = 0;
+    b->opts.stage_log2 = 0;
+    b->opts.stage_k = 0;
     *out = b;
     return SV_OK;
 }
@@ -561,6 +851,10 @@ extern "C" void sv_batch_free(sv_batch *b)
     cudaFree(b->d_items);
     cudaFree(b->d_need);
     cudaFree(b->d_sync);
+    cudaFree(b->d_stages);
+    cudaFree(b->d_chunks);
+    cudaFree(b->d_sgates);
+    cudaFree(b->d_smats);
     delete b;
 }
 
@@ -590,8 +884,9 @@ extern "C" int sv_batch_run(sv_batch *b)
     SV_TRY(check_opts(b->opts));
     SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
     SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
-    const bool relist = !b->d_items || b->list_cfg[0] != b->opts.smem_max_n || b->list_cfg[1] != b->opts.split_min_n ||
-                        b->list_cfg[2] != b->opts.tile_log2 || b->list_cfg[3] != b->opts.wave_mb || b->list_stall != b->stall;
+    const int lcfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                         b->opts.stage_k};
+    const bool relist = !b->d_items || std::memcmp(lcfg, b->list_cfg, sizeof(lcfg)) != 0 || b->list_stall != b->stall;
     if (relist) {
         // the captured graph holds the old list's pointers
         SV_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -602,7 +897,8 @@ extern "C" int sv_batch_run(sv_batch *b)
         SV_TRY(build_work_list(b));
     }
     if (!b->opts.use_graph) return launch_batch(b);
-    const int cfg[6] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb};
+    const int cfg[8] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb,
+                        b->opts.stage_log2, b->opts.stage_k};
     if (b->graph && std::memcmp(cfg, b->graph_cfg, sizeof(cfg)) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -657,6 +953,25 @@ extern "C" int sv_batch_inject_stall(sv_batch *b, int on)
     clear_error();
     if (!b) { set_error("sv_batch_inject_stall: NULL batch"); return SV_EINVAL; }
     b->stall = on != 0;
+    return SV_OK;
+}
+
+extern "C" int sv_batch_get_info(sv_batch *b, sv_batch_info *out)
+{
+    clear_error();
+    if (!b || !out) { set_error("sv_batch_get_info: NULL argument"); return SV_EINVAL; }
+    SV_TRY(check_opts(b->opts));
+    const int lcfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                         b->opts.stage_k};
+    if (!b->d_items || std::memcmp(lcfg, b->list_cfg, sizeof(lcfg)) != 0 || b->list_stall != b->stall) {
+        SV_CUDA_TRY(cudaStreamSynchronize(b->stream));   // a captured graph may still run on the old list
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        SV_TRY(build_work_list(b));
+    }
+    *out = b->info;
     return SV_OK;
 }
 

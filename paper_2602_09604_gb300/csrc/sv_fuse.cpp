@@ -374,7 +374,47 @@ bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
     return true;
 }
 
+// Round a finished block into a fused gate (fp64 matrix kept, fp32 copies rounded once).
+FusedGate block_to_gate(Block &b)
+{
+    FusedGate fg;
+    fg.k = (int)b.qubits.size();
+    for (int j = 0; j < fg.k; ++j) {
+        fg.targets[j] = b.qubits[j];
+        fg.mask |= uint64_t(1) << b.qubits[j];
+        if (b.qubits[j] < 32) fg.mask_lo |= 1u << b.qubits[j];
+    }
+    fg.n_src = b.n_src;
+    fg.cmask = b.cmask;
+    fg.mat = std::move(b.mat);
+    const size_t d2 = fg.mat.size();
+    fg.ur.resize(d2);
+    fg.ui.resize(d2);
+    for (size_t i = 0; i < d2; ++i) {
+        fg.ur[i] = (float)fg.mat[i].real();
+        fg.ui[i] = (float)fg.mat[i].imag();
+    }
+    return fg;
+}
+
 }  // namespace
+
+std::vector<FusedGate> refuse_gates(const std::vector<const FusedGate *> &in, int n_qubits, int max_k)
+{
+    std::vector<Dense> dense(in.size());
+    for (size_t i = 0; i < in.size(); ++i) {
+        dense[i].q.assign(in[i]->targets, in[i]->targets + in[i]->k);
+        dense[i].m = in[i]->mat;
+    }
+    std::vector<Block> blocks = greedy_partition(dense, n_qubits, max_k);
+    std::vector<FusedGate> out;
+    out.reserve(blocks.size());
+    for (Block &b : blocks) {
+        out.push_back(block_to_gate(b));
+        out.back().path = SV_PATH_AUTO;
+    }
+    return out;
+}
 
 int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path)
 {
@@ -480,23 +520,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     f->precision = opts.precision;
 
     auto finish = [&](Block &b, int path) {
-        FusedGate fg;
-        fg.k = (int)b.qubits.size();
-        for (int j = 0; j < fg.k; ++j) {
-            fg.targets[j] = b.qubits[j];
-            fg.mask |= uint64_t(1) << b.qubits[j];
-            if (b.qubits[j] < 32) fg.mask_lo |= 1u << b.qubits[j];
-        }
-        fg.n_src = b.n_src;
-        fg.cmask = b.cmask;
-        fg.mat = std::move(b.mat);
-        const size_t d2 = fg.mat.size();
-        fg.ur.resize(d2);
-        fg.ui.resize(d2);
-        for (size_t i = 0; i < d2; ++i) {
-            fg.ur[i] = (float)fg.mat[i].real();
-            fg.ui[i] = (float)fg.mat[i].imag();
-        }
+        FusedGate fg = block_to_gate(b);
         fg.path = path >= 0 ? path : classify_path(fg, n_qubits, opts.precision, opts.tc_min_k, opts.force_path);
         f->gates.push_back(std::move(fg));
     };

@@ -81,6 +81,11 @@ struct TcOperands {
 
 // Classify the kernel path of a fused gate from its targets and the requested precision.
 int classify_path(const FusedGate &g, int n, int precision, int tc_min_k, int force_path);
+// Greedy fusion (the rules of SV_FUSE_GREEDY, horizontal pass included) of uncontrolled fused
+// gates, each taken as one input gate, into gates of at most max_k qubits (a larger input stays
+// whole); products in fp64, rounded once to fp32; global qubit numbers; path SV_PATH_AUTO.
+// Throws std::bad_alloc when host memory runs out.
+std::vector<FusedGate> refuse_gates(const std::vector<const FusedGate *> &in, int n_qubits, int max_k);
 
 // Device copy bookkeeping for fused circuits; defined in sv_apply.cu.
 struct DeviceMats;

@@ -70,11 +70,13 @@ def run_batch(a):
     circuits = wl.hea_batch(count=a.count, seed=a.seed)
     b = Batch(circuits, a.max_k)
     b.set(a.threads, a.smem_max_n, 2 * torch.cuda.get_device_properties(0).multi_processor_count, True,
-          a.split_min_n, a.tile_log2, a.wave_mb)
+          a.split_min_n, a.tile_log2, a.wave_mb, a.stage_log2, a.stage_k)
     us = _time(b.run, b.stream, a.warm, a.repeats)
     B.sv_device_status()
+    info = B.sv_batch_get_info(b.h)
     b.free()
-    return {"op": "batch", "count": a.count, "us": us}
+    return {"op": "batch", "count": a.count, "us": us, "list": info,
+            "traffic_gbs": info["traffic_bytes"] / (us * 1e-6) / 1e9}
 
 
 def main(argv=None):
@@ -92,6 +94,8 @@ def main(argv=None):
     ap.add_argument("--split-min-n", type=int, default=17)
     ap.add_argument("--tile-log2", type=int, default=12)
     ap.add_argument("--wave-mb", type=int, default=0)
+    ap.add_argument("--stage-log2", type=int, default=0)
+    ap.add_argument("--stage-k", type=int, default=0)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--warm", type=int, default=1)
     ap.add_argument("--repeats", type=int, default=3)

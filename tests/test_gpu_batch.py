@@ -1,6 +1,7 @@
 """Batched uneven circuits in one persistent (graph-captured) launch: every circuit's state equals
 the oracle in every item kind (shared-memory circuits, single-CTA global circuits, circuits split
-into tiles that all CTAs share, with tiles from 32 to 4096 groups and from 1 to many CTAs); graph
+into tiles that all CTAs share, with tiles from 32 to 4096 groups and from 1 to many CTAs,
+circuits run in stages of shared-memory tiles of 2^8 to 2^14 amplitudes); graph
 replays are deterministic; the per-circuit launch loop gives the same states; a wait that cannot
 be satisfied gives up and is reported without a fault."""
 import numpy as np
@@ -45,6 +46,77 @@ def test_batch_matches_oracle_every_tier(env):
                 assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
                 assert oracle.l2_error(ref, got) <= 1e-4, cfg
         b.free()
+
+
+def _random_circuit(n, count, rng):
+    """Gates of 1-3 qubits on random qubits (any position, low and high), random unitaries."""
+    gates = []
+    for _ in range(count):
+        k = int(rng.integers(1, min(3, n) + 1))
+        t = tuple(int(q) for q in rng.choice(n, size=k, replace=False))
+        gates.append(wl.Gate(t, wl.random_unitary(1 << k, rng)))
+    return gates
+
+
+def test_staged_batch_matches_oracle(env):
+    """Circuits run in stages of shared-memory tiles: every tile size, re-fusion size and CTA size
+    gives the oracle's states, for HEA circuits and for gates on random qubits (stages of up to
+    200 gates, loaded into shared memory in several chunks)."""
+    B, batch = env
+    rng = np.random.default_rng(21)
+    circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [16, 9, 8, 14, 12, 5, 15, 10]]
+    # 200 gates: a stage of the small ones holds more gates than one shared-memory chunk
+    circuits += [(int(n), _random_circuit(int(n), c, rng)) for n, c in [(13, 200), (16, 60), (11, 60), (8, 200)]]
+    circuits += [(12, [])]                                   # no gate: the first stage only
+    refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
+    # (threads, smem_max_n, ctas, split_min_n, stage_log2, stage_k)
+    configs = [(256, 0, 7, 1, 8, 0), (512, 0, 152, 8, 14, 4), (256, 9, 19, 9, 11, 2), (64, 0, 3, 10, 9, 1),
+               (128, 12, 40, 13, 10, 3), (256, 0, 304, 1, 13, 4), (512, 0, 1, 8, 12, 2)]
+    for max_k in (2, 4):
+        b = batch.Batch(circuits, max_k)
+        for threads, smem_n, ctas, split_n, sl, sk in configs:
+            b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk)
+            info = B.sv_batch_get_info(b.h)
+            want = sum(1 for n, _ in circuits if n > smem_n and n >= max(split_n, 8))
+            assert info["staged"] == want and info["stages"] >= want, (info, sl)
+            b.arena.fill_(float("nan"))
+            b.run()
+            B.sv_device_status()
+            for i, ref in enumerate(refs):
+                got = b.state(i)
+                cfg = (max_k, threads, smem_n, ctas, split_n, sl, sk, i)
+                assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
+                assert oracle.l2_error(ref, got) <= 1e-4, cfg
+        b.free()
+
+
+def test_staging_cuts_traffic_and_waves_keep_results(env):
+    """Stages move fewer bytes than one pass per fused gate; waves and a direct launch give the
+    same states as the graph replay."""
+    B, batch = env
+    circuits = wl.hea_batch(count=24, n_lo=14, n_hi=18, layers=4, seed=8)
+    b = batch.Batch(circuits, 2)
+    b.set(256, 0, 152, True, 14, 12, 0)
+    per_gate = B.sv_batch_get_info(b.h)
+    b.set(256, 0, 152, True, 14, 12, 0, 14, 4)
+    staged = B.sv_batch_get_info(b.h)
+    assert per_gate["split"] == len(circuits) and staged["staged"] == len(circuits)
+    assert staged["traffic_bytes"] < per_gate["traffic_bytes"] / 3, (staged, per_gate)
+    b.run()
+    first = b.arena.clone()
+    b.set(512, 0, 152, False, 14, 12, 16, 13, 3)   # waves of 16 MB, no graph, other tiles
+    b.arena.fill_(float("nan"))
+    b.run()
+    B.sv_device_status()
+    for i in range(len(circuits)):
+        off = B.sv_batch_state_offset(b.h, i) // 4
+        nf = 2 << circuits[i][0]
+        d = (first[off:off + nf] - b.arena[off:off + nf]).abs().max().item()
+        assert d <= 1e-5, (i, d)
+    for i in (0, 11, 23):
+        n, g = circuits[i]
+        assert oracle.fidelity(oracle.run_circuit(n, g, 0), b.state(i)) >= 1 - 1e-6
+    b.free()
 
 
 def test_graph_replay_is_deterministic_and_loop_agrees(env):
@@ -100,20 +172,23 @@ def test_stalled_wait_gives_up_and_is_reported(env):
     rng = np.random.default_rng(2)
     circuits = [(16, wl.hea_circuit(16, 2, rng)), (10, wl.hea_circuit(10, 2, rng))]
     b = batch.Batch(circuits, 3)
-    b.set(256, 12, 8, True, 15, 10)
-    B.sv_batch_inject_stall(b.h, True)
-    b.run()
-    torch.cuda.synchronize()
-    with pytest.raises(B.SvError) as e:
+    for stage_log2 in (0, 10):            # per-gate tiles, then stages
+        b.set(256, 12, 8, True, 15, 10, 0, stage_log2, 2)
+        if stage_log2:
+            assert B.sv_batch_get_info(b.h)["stages"] >= 2
+        B.sv_batch_inject_stall(b.h, True)
+        b.run()
+        torch.cuda.synchronize()
+        with pytest.raises(B.SvError) as e:
+            B.sv_device_status()
+        assert e.value.code == B.SV_ETIMEOUT, stage_log2
+        B.sv_device_status()              # the error word was cleared by the read
+        B.sv_batch_inject_stall(b.h, False)
+        b.arena.fill_(float("nan"))
+        b.run()
         B.sv_device_status()
-    assert e.value.code == B.SV_ETIMEOUT
-    B.sv_device_status()                  # the error word was cleared by the read
-    B.sv_batch_inject_stall(b.h, False)
-    b.arena.fill_(float("nan"))
-    b.run()
-    B.sv_device_status()
-    for i, (n, g) in enumerate(circuits):
-        assert oracle.fidelity(oracle.run_circuit(n, g, 0), b.state(i)) >= 1 - 1e-6
+        for i, (n, g) in enumerate(circuits):
+            assert oracle.fidelity(oracle.run_circuit(n, g, 0), b.state(i)) >= 1 - 1e-6
     b.free()
 
 
@@ -131,7 +206,7 @@ def test_batch_rejects_bad_input(env):
     assert e.value.code == B.SV_ENOMEM
     h = B.sv_batch_create([f2], buf.data_ptr(), buf.numel() * 4)
     for bad in (dict(threads=1024), dict(split_min_n=25), dict(tile_log2=4), dict(tile_log2=17), dict(smem_max_n=15),
-                dict(wave_mb=-1)):
+                dict(wave_mb=-1), dict(stage_log2=7), dict(stage_log2=15), dict(stage_k=5), dict(stage_k=-1)):
         kw = dict(threads=256, smem_max_n=12, ctas=8, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0)
         kw.update(bad)
         with pytest.raises(B.SvError) as e:
