@@ -71,7 +71,7 @@ struct BChunk {
     int mat_count;           // (float2 units)
 };
 
-constexpr int kStageMatCap = 4096;   // float2 of matrices per chunk (32 KB): 64 three-qubit gates
+constexpr int kStageMatCap = 4096;   // float2 of matrices per chunk (32 KB): 31 three-qubit gates (U and U')
 constexpr int kStageGateCap = 64;    // gate descriptors per chunk
 
 // Work item kinds.  A circuit runs as one of them:
@@ -128,11 +128,12 @@ template <int K, int V, bool L2ONLY, bool XS>
 __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
 {
     constexpr int D = 1 << K;
-    unsigned bit[K];
+    unsigned bit[K], obit[K];   // target bit of the index, and of the blocked-layout float offset
     int nlow = 0;
 #pragma unroll
     for (int b = 0; b < K; ++b) {
         bit[b] = 1u << g.targets[b];
+        obit[b] = g.targets[b] < 5 ? bit[b] : bit[b] << 1;
         nlow += g.targets[b] < 5;
     }
     const unsigned fshift = 5u - (unsigned)nlow, smask = (1u << nlow) - 1u;
@@ -157,14 +158,16 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
 #pragma unroll
             for (int b = 0; b < K; ++b) base |= ((s >> b) & 1u) ? bit[b] : 0u;   // base of index s
         }
+        // the float offset ((i >> 5) << 6) | (i & 31) moves index bits without mixing them, so
+        // the offset of index j ^ s is the base's offset with the targets' offset bits flipped
+        const unsigned obase = ((base >> 5) << 6) | (base & 31u);
         float xr[D][V], xi[D][V];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            unsigned i = base;
+            unsigned o = obase;
 #pragma unroll
             for (int b = 0; b < K; ++b)
-                if ((j >> b) & 1) i ^= bit[b];   // index j ^ s (plain j when s = 0)
-            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                if ((j >> b) & 1) o ^= obit[b];   // index j ^ s (plain j when s = 0)
             // L2ONLY: other CTAs wrote these, so read through L2 rather than a stale L1 line
             ld_v<V, L2ONLY>(S + o, xr[j]);
             ld_v<V, L2ONLY>(S + o + 32, xi[j]);
@@ -174,23 +177,30 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
             float yr[V], yi[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) yr[v] = yi[v] = 0.f;
-            const float2 *Ur = Ui + ((unsigned)r ^ s) * D;
+            // row r ^ s, two entries per 16-byte read: entries (j ^ s, (j + 1) ^ s) for even j are
+            // the pair at (j ^ s) & ~1 of U when s is even, and of the pair-swapped copy U' (stored
+            // right after U) when s is odd
+            const float4 *Ur = reinterpret_cast<const float4 *>(Ui + ((s & 1u) ? D * D : 0) + ((unsigned)r ^ s) * D);
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const float2 u = XS ? Ur[(unsigned)j ^ s] : Ui[r * D + j];
+            for (int jp = 0; jp < D / 2; ++jp) {
+                const float4 q = Ur[(unsigned)jp ^ (s >> 1)];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    yr[v] = fmaf(u.x, xr[j][v], yr[v]);
-                    yr[v] = fmaf(u.y, -xi[j][v], yr[v]);
-                    yi[v] = fmaf(u.x, xi[j][v], yi[v]);
-                    yi[v] = fmaf(u.y, xr[j][v], yi[v]);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * jp + h;
+                    const float ux = h ? q.z : q.x, uy = h ? q.w : q.y;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        yr[v] = fmaf(ux, xr[j][v], yr[v]);
+                        yr[v] = fmaf(uy, -xi[j][v], yr[v]);
+                        yi[v] = fmaf(ux, xi[j][v], yi[v]);
+                        yi[v] = fmaf(uy, xr[j][v], yi[v]);
+                    }
                 }
             }
-            unsigned i = base;
+            unsigned o = obase;
 #pragma unroll
             for (int b = 0; b < K; ++b)
-                if ((r >> b) & 1) i ^= bit[b];
-            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+                if ((r >> b) & 1) o ^= obit[b];
             st_v<V>(S + o, yr);
             st_v<V>(S + o + 32, yi);
         }
@@ -285,10 +295,16 @@ __device__ bool wait_count(const BatchArgs &A, const int *d, int want)
     return true;
 }
 
+// U (row-major) into sU[0, 4^k) and its pair-swapped copy U'[r][j] = U[r][j ^ 1] into
+// sU[4^k, 2 * 4^k) (read by threads whose XOR order s is odd)
 __device__ __forceinline__ void stage_matrix(float2 *sU, const float2 *mats, const BGate &g)
 {
     const int dd = 1 << (2 * g.k);
-    for (int i = threadIdx.x; i < dd; i += blockDim.x) sU[i] = mats[g.mat_off + i];
+    for (int i = threadIdx.x; i < dd; i += blockDim.x) {
+        const float2 u = mats[g.mat_off + i];
+        sU[i] = u;
+        sU[dd + (i ^ 1)] = u;
+    }
 }
 
 __device__ __forceinline__ void zero_floats(float *S, long long f0, long long f1)
@@ -482,7 +498,7 @@ namespace {
 size_t state_bytes(int n) { return sizeof(float) * (size_t)state_floats(n); }
 
 // shared-memory areas: matrices, gate descriptors, then the state of a whole circuit or a tile
-int mat_cap(const sv_batch_opts &o) { return o.stage_log2 > 0 ? kStageMatCap : 1 << (2 * kBatchMaxK); }
+int mat_cap(const sv_batch_opts &o) { return o.stage_log2 > 0 ? kStageMatCap : 2 << (2 * kBatchMaxK); }
 int gate_cap(const sv_batch_opts &o) { return o.stage_log2 > 0 ? kStageGateCap : 0; }
 
 size_t smem_bytes(const sv_batch_opts &o)
@@ -527,19 +543,26 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         bs.chunk_begin = (int)chunks.size();
         std::vector<FusedGate> fused;
         if (stage_k > 0) fused = refuse_gates(taken, n, stage_k);
+        // per gate: U then its pair-swapped copy U' (U'[r][j] = U[r][j ^ 1]), starting at an even
+        // offset of the chunk (16-byte aligned in shared memory)
         auto emit = [&](const FusedGate &g) {
             const int dd = (int)g.ur.size();
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
-                chunks.back().mat_count + dd > kStageMatCap)
+                chunks.back().mat_count + 1 + 2 * dd > kStageMatCap)
                 chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
+            if (chunks.back().mat_count & 1) {
+                sm.push_back(make_float2(0.f, 0.f));
+                chunks.back().mat_count += 1;
+            }
             BGate b{};
             b.k = g.k;
             for (int j = 0; j < g.k; ++j) b.targets[j] = __builtin_popcount(S & ((1u << g.targets[j]) - 1u));
             b.mat_off = (int)sm.size();
             for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g.ur[(size_t)e], g.ui[(size_t)e]));
+            for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g.ur[(size_t)(e ^ 1)], g.ui[(size_t)(e ^ 1)]));
             sg.push_back(b);
             chunks.back().gate_count += 1;
-            chunks.back().mat_count += dd;
+            chunks.back().mat_count += 2 * dd;
         };
         if (stage_k > 0) {
             for (const FusedGate &g : fused) emit(g);
