@@ -8,6 +8,7 @@ or ``python -m paper_2602_09604_gb300.build``) importing this module raises.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 
 import numpy as np
@@ -204,22 +205,34 @@ def gate_array(gates):
     gates = list(gates)
     n = len(gates)
     rec = np.zeros(max(n, 1), dtype=_GATE_DTYPE)
-    tl = [tuple(int(q) for q in g.targets) for g in gates]
-    cl = [tuple(int(q) for q in g.controls) for g in gates]
-    for i, (t, c) in enumerate(zip(tl, cl)):
-        if len(t) > MAX_K or len(c) > MAX_CONTROLS:
-            raise SvError(SV_EINVAL, f"gate {i}: sv_gate holds at most {MAX_K} targets and {MAX_CONTROLS} controls")
+    if n == 0:
+        buf = np.zeros(1, dtype=np.complex128)
+        return rec.ctypes.data_as(ctypes.POINTER(sv_gate)), (rec, buf)
+    tl = [g.targets for g in gates]
+    cl = [g.controls for g in gates]
+    ks = np.fromiter(map(len, tl), dtype=np.int32, count=n)
+    ncs = np.fromiter(map(len, cl), dtype=np.int32, count=n)
+    bad = np.flatnonzero((ks > MAX_K) | (ncs > MAX_CONTROLS))
+    if bad.size:
+        raise SvError(SV_EINVAL, f"gate {int(bad[0])}: sv_gate holds at most {MAX_K} targets and {MAX_CONTROLS} controls")
+
+    def scatter(field, lists, counts):
+        total = int(counts.sum())
+        if total == 0:
+            return
+        flat = np.fromiter(itertools.chain.from_iterable(lists), dtype=np.int32, count=total)
+        starts = np.repeat(np.cumsum(counts) - counts, counts)
+        rec[field][np.repeat(np.arange(n), counts), np.arange(total) - starts] = flat
+
+    rec["k"][:n] = ks
+    rec["n_controls"][:n] = ncs
+    scatter("targets", tl, ks)
+    scatter("controls", cl, ncs)
     mats = [np.asarray(g.matrix, dtype=np.complex128).reshape(-1) for g in gates]
-    buf = np.concatenate(mats) if mats else np.zeros(1, dtype=np.complex128)
-    if n:
-        rec["k"][:n] = [len(t) for t in tl]
-        rec["targets"][:n] = [t + (0,) * (MAX_K - len(t)) for t in tl]
-        rec["n_controls"][:n] = [len(c) for c in cl]
-        for i, c in enumerate(cl):
-            if c:
-                rec["controls"][i, :len(c)] = c
-        offs = np.cumsum([0] + [m.size for m in mats[:-1]], dtype=np.uint64)
-        rec["mat"][:n] = np.uint64(buf.ctypes.data) + np.uint64(16) * offs
+    buf = np.concatenate(mats)
+    sizes = np.fromiter((m.size for m in mats), dtype=np.uint64, count=n)
+    offs = np.cumsum(sizes) - sizes
+    rec["mat"][:n] = np.uint64(buf.ctypes.data) + np.uint64(16) * offs
     return rec.ctypes.data_as(ctypes.POINTER(sv_gate)), (rec, buf)
 
 

@@ -45,8 +45,9 @@ def _stale() -> bool:
 
 
 # Host C++ (fusion): complex products of finite matrix entries need no inf/NaN recovery, so they
-# compile to the plain (ac - bd, ad + bc) arithmetic inline instead of a library call per product.
-HOSTFLAGS = ["-Xcompiler", "-fcx-limited-range"]
+# compile to the plain (ac - bd, ad + bc) arithmetic inline instead of a library call per product;
+# no multiply-add contraction, so the fused matrices are bit-identical on x86-64 and aarch64.
+HOSTFLAGS = ["-Xcompiler", "-fcx-limited-range", "-Xcompiler", "-ffp-contract=off"]
 
 
 def _compile(src: str, verbose: bool) -> str:

@@ -41,7 +41,12 @@ struct Block {
 
 // Rows r_j = base | off[j] (j < GD) of mat, each `dim` complex entries, replaced by G times them.
 // Every column's GD inputs are read before any output of that column is written, so no copy is
-// needed, and the column loop runs over contiguous memory.
+// needed, and the column loop runs over contiguous memory.  A complex entry is one two-lane
+// vector (GCC's generic vector extension: two doubles per operation on any target); with
+// xs = (-Im x, Re x) the product G x is Re G * x + Im G * xs, the same sums in the same order as
+// the scalar form.
+typedef double v2d __attribute__((vector_size(16)));
+
 template <int GD>
 void mix_rows(double *m, size_t dim, size_t base, const size_t *off, const std::vector<cplx> &G)
 {
@@ -51,22 +56,18 @@ void mix_rows(double *m, size_t dim, size_t base, const size_t *off, const std::
             gr[r][j] = G[(size_t)r * GD + j].real();
             gi[r][j] = G[(size_t)r * GD + j].imag();
         }
-    double *row[GD];
-    for (int j = 0; j < GD; ++j) row[j] = m + 2 * (base | off[j]) * dim;
+    v2d *row[GD];
+    for (int j = 0; j < GD; ++j) row[j] = reinterpret_cast<v2d *>(m + 2 * (base | off[j]) * dim);
     for (size_t c = 0; c < dim; ++c) {
-        double xr[GD], xi[GD];
+        v2d x[GD], xs[GD];
         for (int j = 0; j < GD; ++j) {
-            xr[j] = row[j][2 * c];
-            xi[j] = row[j][2 * c + 1];
+            x[j] = row[j][c];
+            xs[j] = v2d{-x[j][1], x[j][0]};
         }
         for (int r = 0; r < GD; ++r) {
-            double yr = 0.0, yi = 0.0;
-            for (int j = 0; j < GD; ++j) {
-                yr += gr[r][j] * xr[j] - gi[r][j] * xi[j];
-                yi += gr[r][j] * xi[j] + gi[r][j] * xr[j];
-            }
-            row[r][2 * c] = yr;
-            row[r][2 * c + 1] = yi;
+            v2d y = {0.0, 0.0};
+            for (int j = 0; j < GD; ++j) y += gr[r][j] * x[j] + gi[r][j] * xs[j];
+            row[r][c] = y;
         }
     }
 }
