@@ -12,9 +12,17 @@
 // A second pass adds horizontal fusion across the emitted sequence: each emitted block moves back
 // over the blocks before it that share no qubit with it (they commute) and merges into the first
 // block it meets whose union with it still has at most max_k qubits.
+//
+// The partition depends only on the gates' qubits, never on matrix values, so the scan records
+// how each block's matrix is formed (a small expression: a starting block re-expressed over more
+// qubits, then left products by gates and by merged blocks) and the products run afterwards, for
+// the chosen partition only, one fused gate per host thread.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <future>
+#include <memory>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,9 +35,34 @@ namespace svg {
 
 namespace {
 
+// A block's matrix as recorded by the scan: base's matrix (identity when null) re-expressed over
+// `qubits`, then left-multiplied by each op in order -- a dense gate over op.gq, or (op.child set)
+// another block's matrix over child->qubits.
+struct MatNode;
+using NodeP = std::shared_ptr<MatNode>;
+struct MatOp {
+    std::vector<cplx> g;
+    std::vector<int> gq;
+    NodeP child;
+};
+struct MatNode {
+    std::vector<int> qubits;   // ascending
+    NodeP base;
+    std::vector<MatOp> ops;
+};
+
+NodeP new_node(const std::vector<int> &qubits, NodeP base)
+{
+    NodeP n = std::make_shared<MatNode>();
+    n->qubits = qubits;
+    n->base = std::move(base);
+    return n;
+}
+
 struct Block {
     std::vector<int> qubits;  // ascending
-    std::vector<cplx> mat;    // 2^|qubits| square, local bit j <-> qubits[j]
+    NodeP node;               // how the matrix is formed (greedy scan)
+    std::vector<cplx> mat;    // 2^|qubits| square, local bit j <-> qubits[j] (once evaluated)
     int n_src = 0;
     long long created = 0;
     uint64_t cmask = 0;       // a controlled gate kept whole (qubits = its targets); else 0
@@ -146,14 +179,62 @@ std::vector<cplx> expand(const std::vector<cplx> &M, const std::vector<int> &S, 
     return out;
 }
 
-// multiplies every pending single-qubit gate of b into b.mat
+// multiplies every pending single-qubit gate of b into b's matrix (recorded)
 void flush_pending(Block &b)
 {
-    for (auto &pq : b.pend) {
-        const std::vector<cplx> P(pq.second.begin(), pq.second.end());
-        left_multiply(b.mat, b.qubits, P, std::vector<int>{pq.first});
-    }
+    for (auto &pq : b.pend) b.node->ops.push_back(MatOp{std::vector<cplx>(pq.second.begin(), pq.second.end()), {pq.first}, nullptr});
     b.pend.clear();
+}
+
+std::vector<cplx> evaluate(const MatNode &n)
+{
+    std::vector<cplx> M = n.base ? expand(evaluate(*n.base), n.base->qubits, n.qubits) : identity(size_t(1) << n.qubits.size());
+    for (const MatOp &op : n.ops) {
+        if (op.child) left_multiply(M, n.qubits, evaluate(*op.child), op.child->qubits);
+        else left_multiply(M, n.qubits, op.g, op.gq);
+    }
+    return M;
+}
+
+// complex multiply-adds that evaluate(n) performs
+double eval_cost(const MatNode &n)
+{
+    const double d2 = std::ldexp(1.0, 2 * (int)n.qubits.size());
+    double c = n.base ? eval_cost(*n.base) + d2 : d2;
+    for (const MatOp &op : n.ops)
+        c += op.child ? eval_cost(*op.child) + d2 * std::ldexp(1.0, (int)op.child->qubits.size())
+                      : d2 * std::ldexp(1.0, (int)op.gq.size());
+    return c;
+}
+
+// Every block's matrix from its recorded expression; with `parallel`, blocks are shared out to
+// host threads (a shared counter hands out the next block), one thread per ~5e5 complex
+// multiply-adds (about half a millisecond: less would not pay for starting the thread), else
+// evaluated in order.
+void materialize(std::vector<Block> &blocks, bool parallel)
+{
+    std::atomic<size_t> next{0};
+    auto work = [&]() {
+        for (size_t i = next++; i < blocks.size(); i = next++) {
+            blocks[i].mat = evaluate(*blocks[i].node);
+            blocks[i].node.reset();
+        }
+    };
+    size_t nt = 1;
+    if (parallel) {
+        double cost = 0.0;
+        for (const Block &b : blocks) cost += eval_cost(*b.node);
+        nt = std::min<size_t>({blocks.size(), (size_t)std::max(1u, std::thread::hardware_concurrency()), (size_t)(cost / 5e5) + 1});
+    }
+    std::vector<std::future<void>> jobs;
+    if (nt > 1) {
+        try {
+            for (size_t t = 1; t < nt; ++t) jobs.push_back(std::async(std::launch::async, work));
+        } catch (const std::system_error &) {   // no more threads: the ones started and this one finish the work
+        }
+    }
+    work();
+    for (auto &j : jobs) j.get();   // rethrows a worker's exception (e.g. std::bad_alloc)
 }
 
 // G (acting on qubit list Q) <- G * P_q for every pending gate of b on a qubit of Q (P applied
@@ -191,8 +272,8 @@ Block controlled_block(const Dense &d)
     Block b;
     b.qubits = d.q;
     std::sort(b.qubits.begin(), b.qubits.end());
-    b.mat = identity(size_t(1) << b.qubits.size());
-    left_multiply(b.mat, b.qubits, d.m, d.q);
+    b.node = new_node(b.qubits, nullptr);
+    b.node->ops.push_back(MatOp{d.m, d.q, nullptr});
     b.n_src = 1;
     b.cmask = d.cmask;
     return b;
@@ -295,21 +376,21 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         for (int b : kept)   // pending single-qubit gates carry over (their qubits stay disjoint)
             for (auto &pq : open[b].pend) nb.pend.push_back(pq);
         if (kept.empty()) {
-            nb.mat = identity(size_t(1) << nb.qubits.size());
+            nb.node = new_node(nb.qubits, nullptr);
         } else {
-            // the first kept block's matrix moves over unchanged when the gate adds no qubit to it
-            if (open[kept[0]].qubits == nb.qubits) nb.mat = std::move(open[kept[0]].mat);
-            else nb.mat = expand(open[kept[0]].mat, open[kept[0]].qubits, nb.qubits);
+            // the first kept block's matrix carries over unchanged when the gate adds no qubit to it
+            if (open[kept[0]].qubits == nb.qubits) nb.node = std::move(open[kept[0]].node);
+            else nb.node = new_node(nb.qubits, std::move(open[kept[0]].node));
             nb.n_src += open[kept[0]].n_src;
             for (size_t i = 1; i < kept.size(); ++i) {
-                left_multiply(nb.mat, nb.qubits, open[kept[i]].mat, open[kept[i]].qubits);
+                nb.node->ops.push_back(MatOp{{}, {}, std::move(open[kept[i]].node)});
                 nb.n_src += open[kept[i]].n_src;
             }
         }
         {
             std::vector<cplx> G = dense[gi].m;
             fold_pending(G, Q, nb);   // the pending gates on Q act before this gate
-            left_multiply(nb.mat, nb.qubits, G, Q);
+            nb.node->ops.push_back(MatOp{std::move(G), Q, nullptr});
         }
         nb.created = stamp++;
         std::vector<char> drop(open.size(), 0);
@@ -355,9 +436,8 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         std::vector<int> U;
         for (int q = 0; q < n_qubits; ++q)
             if ((um >> q) & 1) U.push_back(q);
-        std::vector<cplx> M = expand(t.mat, t.qubits, U);   // earlier block first
-        left_multiply(M, U, b.mat, b.qubits);
-        t.mat = std::move(M);
+        if (U != t.qubits) t.node = new_node(U, std::move(t.node));   // earlier block first
+        t.node->ops.push_back(MatOp{{}, {}, std::move(b.node)});
         t.qubits = std::move(U);
         t.n_src += b.n_src;
     }
@@ -408,6 +488,7 @@ std::vector<FusedGate> refuse_gates(const std::vector<const FusedGate *> &in, in
         dense[i].m = in[i]->mat;
     }
     std::vector<Block> blocks = greedy_partition(dense, n_qubits, max_k);
+    materialize(blocks, false);
     std::vector<FusedGate> out;
     out.reserve(blocks.size());
     for (Block &b : blocks) {
@@ -532,6 +613,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             for (int gi = 0; gi < n_gates; ++gi) {
                 if (dense[gi].cmask) {
                     Block cb = controlled_block(dense[gi]);
+                    cb.mat = evaluate(*cb.node);
                     finish(cb, -1);
                     continue;
                 }
@@ -546,6 +628,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         } else if (opts.mode == SV_FUSE_GREEDY || !mlp_usable(opts.model, kMaxTrustedError)) {
             const int k = opts.mode == SV_FUSE_GREEDY ? opts.max_k : (opts.model ? mlp_fallback_k(opts.model) : opts.max_k);
             std::vector<Block> blocks = greedy_partition(dense, n_qubits, k);
+            materialize(blocks, true);
             for (Block &b : blocks) finish(b, -1);
         } else {
             // learned: every greedy partition up to max_k, every allowed kernel path per fused
@@ -603,6 +686,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 }
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
             }
+            materialize(cand[best], true);
             for (size_t i = 0; i < cand[best].size(); ++i) finish(cand[best][i], chosen[best][i]);
         }
     } catch (const std::bad_alloc &) {
