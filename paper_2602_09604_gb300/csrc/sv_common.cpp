@@ -1,10 +1,31 @@
 // Error reporting and small shared helpers.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <future>
+#include <system_error>
+#include <thread>
 
 #include "sv_internal.h"
 
 namespace svg {
+
+void host_parallel_for(size_t n, size_t threads, const std::function<void(size_t)> &fn)
+{
+    std::atomic<size_t> next{0};
+    auto work = [&]() {
+        for (size_t i = next++; i < n; i = next++) fn(i);
+    };
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min(std::min(threads, n), hw);
+    std::vector<std::future<void>> jobs;
+    try {
+        for (size_t t = 1; t < nt; ++t) jobs.push_back(std::async(std::launch::async, work));
+    } catch (const std::system_error &) {   // no more threads: the ones started and this one finish
+    }
+    work();
+    for (auto &j : jobs) j.get();   // rethrows a worker's exception (e.g. std::bad_alloc)
+}
 
 static thread_local char g_err[512] = "";
 

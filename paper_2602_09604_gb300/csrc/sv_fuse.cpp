@@ -19,10 +19,8 @@
 // the chosen partition only, one fused gate per host thread.
 #include <algorithm>
 #include <array>
-#include <atomic>
 #include <future>
 #include <memory>
-#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -208,33 +206,20 @@ double eval_cost(const MatNode &n)
 }
 
 // Every block's matrix from its recorded expression; with `parallel`, blocks are shared out to
-// host threads (a shared counter hands out the next block), one thread per ~5e5 complex
-// multiply-adds (about half a millisecond: less would not pay for starting the thread), else
-// evaluated in order.
+// host threads, one thread per ~5e5 complex multiply-adds (about half a millisecond: less would
+// not pay for starting the thread), else evaluated in order.
 void materialize(std::vector<Block> &blocks, bool parallel)
 {
-    std::atomic<size_t> next{0};
-    auto work = [&]() {
-        for (size_t i = next++; i < blocks.size(); i = next++) {
-            blocks[i].mat = evaluate(*blocks[i].node);
-            blocks[i].node.reset();
-        }
-    };
     size_t nt = 1;
     if (parallel) {
         double cost = 0.0;
         for (const Block &b : blocks) cost += eval_cost(*b.node);
-        nt = std::min<size_t>({blocks.size(), (size_t)std::max(1u, std::thread::hardware_concurrency()), (size_t)(cost / 5e5) + 1});
+        nt = (size_t)(cost / 5e5) + 1;
     }
-    std::vector<std::future<void>> jobs;
-    if (nt > 1) {
-        try {
-            for (size_t t = 1; t < nt; ++t) jobs.push_back(std::async(std::launch::async, work));
-        } catch (const std::system_error &) {   // no more threads: the ones started and this one finish the work
-        }
-    }
-    work();
-    for (auto &j : jobs) j.get();   // rethrows a worker's exception (e.g. std::bad_alloc)
+    host_parallel_for(blocks.size(), nt, [&](size_t i) {
+        blocks[i].mat = evaluate(*blocks[i].node);
+        blocks[i].node.reset();
+    });
 }
 
 // G (acting on qubit list Q) <- G * P_q for every pending gate of b on a qubit of Q (P applied

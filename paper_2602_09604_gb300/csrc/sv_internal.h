@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,10 @@ struct sv_mlp;
 namespace svg {
 
 void set_error(const char *fmt, ...);
+// fn(i) for every i in [0, n) on up to `threads` host threads (the caller's included; fewer when
+// the machine has fewer or no more can start), indices handed out through a shared counter.
+// Rethrows the first exception a worker raised, after every worker has finished.
+void host_parallel_for(size_t n, size_t threads, const std::function<void(size_t)> &fn);
 void clear_error();
 
 #define SV_CUDA_TRY(call)                                                                     \

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <mutex>
 
 #include "sv_internal.h"
@@ -821,9 +822,16 @@ uint32_t host_core_off(int row, int kk, int rows)
     return (uint32_t)((kc * (rows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + e * ESZ);
 }
 
-// B image(s) of one gate in the tcgen05 K-major no-swizzle layout: rows = output columns (c', r),
-// K = input columns (c, j).
-std::vector<unsigned char> make_b_image(const FusedGate &g, int mode)
+// Bytes of the B image(s) of a k-qubit gate in `mode`.
+size_t b_image_bytes(int k, int mode)
+{
+    const size_t KD = size_t(2) << k;
+    return mode == kModeTF32 ? KD * KD * 4 : 2 * KD * KD * 2;
+}
+
+// B image(s) of one gate in the tcgen05 K-major no-swizzle layout (rows = output columns (c', r),
+// K = input columns (c, j)), written to img (b_image_bytes(g.k, mode) bytes, every byte set).
+void write_b_image(const FusedGate &g, int mode, unsigned char *img)
 {
     const int D = 1 << g.k, KD = 2 * D;
     auto B = [&](int kk, int nn) -> double {
@@ -835,16 +843,14 @@ std::vector<unsigned char> make_b_image(const FusedGate &g, int mode)
         return u.real();
     };
     if (mode == kModeTF32) {
-        std::vector<unsigned char> img(size_t(KD) * KD * 4, 0);
         for (int nn = 0; nn < KD; ++nn)
             for (int kk = 0; kk < KD; ++kk) {
                 const uint32_t v = tf32_rna(B(kk, nn));
                 std::memcpy(&img[host_core_off<4>(nn, kk, KD)], &v, 4);
             }
-        return img;
+        return;
     }
     const size_t one = size_t(KD) * KD * 2;
-    std::vector<unsigned char> img(2 * one, 0);
     for (int nn = 0; nn < KD; ++nn)
         for (int kk = 0; kk < KD; ++kk) {
             const double v = B(kk, nn);
@@ -854,7 +860,6 @@ std::vector<unsigned char> make_b_image(const FusedGate &g, int mode)
             std::memcpy(&img[o], &hi, 2);
             std::memcpy(&img[one + o], &lo, 2);
         }
-    return img;
 }
 
 int *g_err_word[64] = {};
@@ -937,7 +942,8 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
 int build_tc_operands(sv_fused *f)
 {
     f->tc_offset.assign(f->gates.size(), SIZE_MAX);
-    std::vector<unsigned char> host;
+    std::vector<size_t> tc;   // tensor-core gates, each at a 128-byte aligned offset of one image
+    size_t total = 0;
     for (size_t i = 0; i < f->gates.size(); ++i) {
         const FusedGate &g = f->gates[i];
         if (g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) continue;
@@ -945,11 +951,21 @@ int build_tc_operands(sv_fused *f)
             set_error("tensor-core path handles fused gates of 4 to 6 qubits (gate %zu has %d)", i, g.k);
             return SV_EINVAL;
         }
-        const std::vector<unsigned char> img = make_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3);
-        const size_t off = (host.size() + 127) & ~size_t(127);
-        host.resize(off + img.size(), 0);
-        std::memcpy(&host[off], img.data(), img.size());
-        f->tc_offset[i] = off;
+        f->tc_offset[i] = (total + 127) & ~size_t(127);
+        total = f->tc_offset[i] + b_image_bytes(g.k, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3);
+        tc.push_back(i);
+    }
+    std::vector<unsigned char> host;
+    try {
+        host.assign(total, 0);
+        // the gates' images are independent: built on host threads (a k = 6 image is 32 K elements)
+        host_parallel_for(tc.size(), (tc.size() + 3) / 4, [&](size_t t) {
+            const FusedGate &g = f->gates[tc[t]];
+            write_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3, host.data() + f->tc_offset[tc[t]]);
+        });
+    } catch (const std::exception &e) {
+        set_error("tensor-core operand images: %s", e.what());
+        return SV_ENOMEM;
     }
     if (!host.empty()) {
         SV_CUDA_TRY(cudaMalloc(&f->d_tc, host.size()));
