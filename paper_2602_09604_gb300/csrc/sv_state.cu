@@ -201,14 +201,25 @@ __global__ void __launch_bounds__(1024) chunk_scan_kernel(const double *__restri
     }
 }
 
-// One warp per sample.  p_i = re^2 + im^2 in fp64 (products of widened floats are exact).
-__global__ void sample_search_kernel(const float *__restrict__ sv, int n, long long n_chunks, int chunk_log2,
-                                     const double *__restrict__ prefix, const double *__restrict__ uniforms,
-                                     int n_samples, unsigned long long *__restrict__ out)
+// One CTA of kSearchWarps warps per sample; p_i = re^2 + im^2 in fp64 (products of widened
+// floats are exact).  After the chunk holding the sample is found (binary search on the chunk
+// prefix sums), each warp sums p over its own part of the chunk with independent loads; thread 0
+// picks the part where the running total passes the target; one warp then walks that part 32
+// amplitudes at a time (warp scan) to the first index whose running total exceeds it, going on
+// into the next part if the walk's rounding leaves the target just past this part's end.
+constexpr int kSearchWarps = 8;
+
+__global__ void __launch_bounds__(32 * kSearchWarps) sample_search_kernel(const float *__restrict__ sv, int n, long long n_chunks,
+                                                                          int chunk_log2, const double *__restrict__ prefix,
+                                                                          const double *__restrict__ uniforms, int n_samples,
+                                                                          unsigned long long *__restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ double part[kSearchWarps];
+    __shared__ int s_part;
+    __shared__ double s_run;
+    const int s = blockIdx.x;
     if (s >= n_samples) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double total = prefix[n_chunks];
     const double target = uniforms[s] * total;
     // largest chunk c with prefix[c] <= target
@@ -218,12 +229,34 @@ __global__ void sample_search_kernel(const float *__restrict__ sv, int n, long l
         if (prefix[mid] <= target) lo = mid; else hi = mid - 1;
     }
     const unsigned long long N = 1ull << n;
-    const unsigned long long chunk_amps = 1ull << chunk_log2;
-    unsigned long long i0 = (unsigned long long)lo * chunk_amps;
-    double run = prefix[lo];
+    const unsigned long long i0 = (unsigned long long)lo << chunk_log2;
+    const unsigned long long part_amps = (1ull << chunk_log2) / kSearchWarps;
+    double acc = 0.0;
+    for (unsigned long long k = lane; k < part_amps; k += 32) {
+        const unsigned long long i = i0 + (unsigned long long)warp * part_amps + k;
+        if (i < N) {
+            const long long o = re_off(i);
+            const double re = (double)sv[o], im = (double)sv[o + 32];
+            acc += re * re + im * im;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = prefix[lo];
+        int p = 0;
+        while (p < kSearchWarps - 1 && run + part[p] <= target) run += part[p++];
+        s_part = p;
+        s_run = run;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    double run = s_run;
     unsigned long long answer = N - 1;
     bool found = false;
-    for (unsigned long long base = i0; base < N && !found; base += 32) {
+    for (unsigned long long base = i0 + (unsigned long long)s_part * part_amps; base < N && !found; base += 32) {
         const unsigned long long i = base + lane;
         double p = 0.0;
         if (i < N) {
@@ -462,9 +495,8 @@ int sample_impl(sv_state *st, const double *uniforms, int n_samples, uint64_t *o
         chunk_scan_kernel<<<1, 1024, 0, st->stream>>>(sums, prefix, nc);
         SV_CUDA_TRY(cudaGetLastError());
         if (n_samples > 0) {
-            const int wpb = 8;
-            sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms,
-                                                                                        n_samples, st->d_samples);
+            sample_search_kernel<<<n_samples, 32 * kSearchWarps, 0, st->stream>>>(st->d, n, nc, chunk_log2, prefix, st->d_uniforms,
+                                                                                 n_samples, st->d_samples);
             SV_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -564,8 +596,7 @@ extern "C" int sv_sample_noalloc(const void *dev_state, int n_qubits, void *cuda
     SV_CUDA_TRY(cudaGetLastError());
     chunk_scan_kernel<<<1, 1024, 0, stream>>>(sums, prefix, nc);
     SV_CUDA_TRY(cudaGetLastError());
-    const int wpb = 8;
-    sample_search_kernel<<<(n_samples + wpb - 1) / wpb, 32 * wpb, 0, stream>>>(sv, n, nc, chunk_log2, prefix, d_u, n_samples, d_out);
+    sample_search_kernel<<<n_samples, 32 * kSearchWarps, 0, stream>>>(sv, n, nc, chunk_log2, prefix, d_u, n_samples, d_out);
     SV_CUDA_TRY(cudaGetLastError());
     SV_CUDA_TRY(cudaMemcpyAsync(out, d_out, sizeof(unsigned long long) * size_t(n_samples), cudaMemcpyDeviceToHost, stream));
     SV_CUDA_TRY(cudaStreamSynchronize(stream));
