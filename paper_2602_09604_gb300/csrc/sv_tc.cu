@@ -42,11 +42,13 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;
 constexpr long long kWaitIters = 4000000;   // ~0.3 s with the backoff below
-// k = 6 gates with no target below qubit 5 use the shared-memory-A direct kernel (two accumulators
-// per warpgroup, so the products overlap the previous tile's stores): measured at n = 30 it beats
-// the tensor-memory-A direct variant there (5.80 vs 5.53 TB/s) but not with one or two low targets
-// (5.09 vs 5.32: its 192 KB of shared memory leaves little L1 for their partial-line accesses) nor
-// for k = 5 (6.17-6.26 vs 6.53-6.56: four warpgroups per SM already overlap the products).
+// k = 6 gates with no target below qubit 5, or one at qubit 3 or 4, use the shared-memory-A
+// direct kernel (two accumulators per warpgroup, so the products overlap the previous tile's
+// stores): measured at n = 30 it beats the tensor-memory-A direct variant there (no low target
+// 5.80 vs 5.53 TB/s; one at qubit 3 or 4: 5.81-5.86 vs 5.46-5.47) but not with a low target at
+// qubits 0-2 (5.09 vs 5.32: its 192 KB of shared memory leaves little L1 for the sub-sector
+// accesses those need) or two low targets (5.23 vs 5.26 for qubits 3 and 4), nor for k = 5
+// (6.17-6.26 vs 6.53-6.56: four warpgroups per SM already overlap the products).
 constexpr bool kDirectSmemA = true;
 
 enum : int { kModeTF32 = 0, kModeBF16X3 = 1 };
@@ -893,7 +895,11 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     // complementary parts come from L1 (measured at n = 30: k = 6 5.3-5.8 vs 4.3-4.4 TB/s staged,
     // k = 5 6.6 vs 5.0-5.2).  From three on, staging through shared memory wins.
     int nlow = 0;
-    for (int b = 0; b < K; ++b) nlow += g.targets[b] < 5;
+    int low_min = 32;   // lowest target
+    for (int b = 0; b < K; ++b) {
+        nlow += g.targets[b] < 5;
+        low_min = g.targets[b] < low_min ? g.targets[b] : low_min;
+    }
     const bool staged = nlow >= 3;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -910,7 +916,9 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bimg = dtc;
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
-    const int variant = staged ? 1 : (kDirectSmemA && K == 6 && nlow == 0 ? 2 : 0);
+    // shared-memory A for k = 6 when its accesses need no L1 reuse: no low target, or one at
+    // qubit 3 or 4 (a warp access then covers whole 32-byte sectors of two lines)
+    const int variant = staged ? 1 : (kDirectSmemA && K == 6 && (nlow == 0 || (nlow == 1 && low_min >= 3)) ? 2 : 0);
     void (*kern)(float *, const TcArgs) = variant == 1 ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
     if constexpr (K == 6)   // the shared-memory-A kernel exists for k = 6 only
         if (variant == 2) kern = apply_tc_direct_kernel<K, MODE>;

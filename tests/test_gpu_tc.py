@@ -82,6 +82,25 @@ def test_single_tc_gate(B, DS, mode, n):
             assert err <= GATE_L2[mode], (k, tg, err)
 
 
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_k6_every_kernel_variant(B, DS, mode):
+    """k = 6 gates reach every tensor-core kernel by their low targets (below qubit 5): none, or
+    one at qubit 3 or 4 (shared-memory-A direct kernel); one at qubits 0-2, or two (tensor-memory-A
+    direct); three or more (staged through shared memory).  Each matches the oracle."""
+    n = 13
+    rng = np.random.default_rng(606)
+    psi0 = wl.random_state(n, rng).astype(np.complex64)
+    for tg in [(5, 6, 7, 8, 9, 12), (3, 6, 7, 9, 10, 12), (4, 5, 8, 9, 11, 12), (1, 6, 7, 9, 10, 12),
+               (3, 4, 7, 9, 10, 12), (0, 2, 4, 8, 9, 12), (0, 1, 2, 3, 4, 12)]:
+        g = wl.random_gate(n, 6, rng, targets=tg)
+        ref = psi0.astype(np.complex128)
+        oracle.apply_gate(ref, n, g)
+        got, paths = run(B, DS, n, [g], 6, prec(B, mode), psi0=psi0)
+        assert paths == [B.PATH_TC_TF32 if mode == "tf32" else B.PATH_TC_BF16X3]
+        err = oracle.l2_error(ref, got)
+        assert err <= GATE_L2[mode], (tg, err)
+
+
 @pytest.mark.parametrize("max_k", [4, 5, 6])
 def test_tc_circuit_bf16x3_meets_fidelity_bar(B, DS, max_k):
     n, gates = wl.circuit_16q()
