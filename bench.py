@@ -2,8 +2,10 @@
 
 A step is one pass of the hot path over one circuit: set |0...0> and apply every fused gate
 (sv_init_apply: the first gates, while they name at most 24 qubits, run on the small state of
-those qubits, which is then written into the full state; --start plain uses sv_init then
-sv_apply_fused_gates, and the line reports the other start's time too), then one read pass that
+those qubits, which is then written into the full state; the fusion places the gates of the
+circuit's 24-qubit light cone first for it (--start-qubits); --start plain uses sv_init then
+sv_apply_fused_gates on the circuit fused as one, and the line reports the other start's time
+too), then one read pass that
 yields the fp64 norm and 1024 samples (sv_sample_norm).  The circuit is the 5x6-grid random circuit (20 cycles of
 sqrt(X)/sqrt(Y)/sqrt(W) plus fSim(pi/2, pi/6) on patterns ABCDCDAB, seed 2, 845 gates), fused
 on the host to at most --max-k qubits; fused gates of --tc-min-k or more qubits run on the tensor
@@ -206,7 +208,10 @@ def bench_ours(args):
             fusion = "greedy"
     mode = B.FUSE_LEARNED if fusion == "learned" else B.FUSE_GREEDY
     fuse_kw = dict(max_k=args.max_k, precision=prec, tc_min_k=args.tc_min_k, mode=mode, model=model)
-    fused = B.sv_fuse_circuit(gates, n, **fuse_kw)
+    # a start from |0...0> through sv_init_apply: the light cone on start_qubits qubits fused apart
+    start_kw = {"lazy": dict(start_qubits=args.start_qubits), "plain": {}}
+    fused_by_start = {m: B.sv_fuse_circuit(gates, n, **fuse_kw, **start_kw[m]) for m in ("lazy", "plain")}
+    fused = fused_by_start[args.start]
     n_fused = B.sv_fused_count(fused)
     infos = [B.sv_fused_get_info(fused, i) for i in range(n_fused)]
     stream = torch.cuda.Stream()
@@ -217,11 +222,12 @@ def bench_ours(args):
 
     def step(record, start=None):
         start = start or args.start
+        fc = fused_by_start[start]
         if start == "lazy":   # gates run on the small state of the qubits named so far, then expand
-            rec = B.sv_init_apply(st.h, 0, fused, timings=record)
+            rec = B.sv_init_apply(st.h, 0, fc, timings=record)
         else:
             B.sv_init(st.h, 0)
-            rec = B.sv_apply_fused_gates(st.h, fused, timings=record)
+            rec = B.sv_apply_fused_gates(st.h, fc, timings=record)
         smp, nrm = B.sv_sample_norm(st.h, uniforms)   # norm and samples from one read pass
         return rec, nrm, smp
 
@@ -274,7 +280,7 @@ def bench_ours(args):
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f2 = B.sv_fuse_circuit(gates, n, **fuse_kw)
+        f2 = B.sv_fuse_circuit(gates, n, **fuse_kw, **start_kw[args.start])
         if args.start == "lazy":
             B.sv_init_apply(st.h, 0, f2)
         else:
@@ -405,7 +411,8 @@ def bench_ours(args):
                    "tc_min_k": args.tc_min_k, "fusion": fusion, "fused_gates": n_fused,
                    "fused_k_histogram": {str(k): sum(1 for i in infos if i["k"] == k) for k in range(1, 7)}, "samples_per_step": N_SAMPLES,
                    "l2": "state 8 GiB > 129 MB L2, no flush", "parallelism": f"replicas x{ws}",
-                   "start": args.start, "lazy_start_gates_per_step": lazy_gates // max(1, args.steps)},
+                   "start": args.start, "start_qubits": args.start_qubits if args.start == "lazy" else 0,
+                   "lazy_start_gates_per_step": lazy_gates // max(1, args.steps)},
         f"s_per_circuit_{other}_start": other_s,
         "e2e": {"value": statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -431,7 +438,8 @@ def bench_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
                                 "sample": f"{args.cpu_gates} of the 845 gates (evenly spaced) applied once to the "
                                           f"2^30 complex128 state; s/circuit = mean s/gate ({per_gate:.3f}) x 845"}
-    B.sv_fused_free(fused)
+    for fc in fused_by_start.values():
+        B.sv_fused_free(fc)
     if model is not None:
         line["cost_model"] = {k: v for k, v in B.sv_mlp_get_stats(model).items() if k in ("val_mape", "steps")}
         B.sv_mlp_free(model)
@@ -459,6 +467,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expval", action="store_true")
     ap.add_argument("--no-next-rows", action="store_true")
+    ap.add_argument("--start-qubits", type=int, default=24,
+                    help="light cone fused apart for the lazy start (0 = fuse the circuit as one)")
     ap.add_argument("--start", choices=["lazy", "plain"], default="lazy",
                     help="lazy: sv_init_apply (first gates on the small state of the qubits they name); "
                          "plain: sv_init then sv_apply_fused_gates")

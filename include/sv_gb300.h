@@ -107,6 +107,15 @@ typedef struct sv_fuse_opts {
     int force_path;     /* enum sv_path; SV_PATH_AUTO lets the library choose (testing knob) */
     const sv_mlp *model;/* learned mode: trained cost model; NULL, untrained or a validation error
                            above 25% => greedy fusion at max_k (model's fallback k when present) */
+    int start_qubits;   /* 0 (default): fuse the circuit as one.  m in 1..24: the circuit will start
+                           from a basis state through sv_init_apply, so the gates of its light cone
+                           on m qubits (min(m, n - 1)) are fused apart and placed first: in circuit
+                           order, a qubit set S grows with each gate's qubits (targets and controls)
+                           while it has at most m; a gate joins the first part when no earlier gate
+                           left out shares a qubit with it and its qubits lie in S.  sv_init_apply
+                           then runs that part on its small state; applied with
+                           sv_apply_fused_gates the result is the same state, but may take more
+                           passes than fusing without the split.  Greedy and learned modes. */
 } sv_fuse_opts;
 
 /* Facts about one fused gate (introspection). */

@@ -39,7 +39,8 @@ class sv_gate(ctypes.Structure):
 
 class sv_fuse_opts(ctypes.Structure):
     _fields_ = [("max_k", ctypes.c_int), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tc_min_k", ctypes.c_int), ("force_path", ctypes.c_int), ("model", ctypes.c_void_p)]
+                ("tc_min_k", ctypes.c_int), ("force_path", ctypes.c_int), ("model", ctypes.c_void_p),
+                ("start_qubits", ctypes.c_int)]
 
 
 class sv_fused_info(ctypes.Structure):
@@ -237,10 +238,10 @@ def gate_array(gates):
 
 
 def sv_fuse_circuit(gates, n: int, max_k: int = 4, mode: int = FUSE_GREEDY, precision: int = PREC_FP32,
-                    tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None) -> ctypes.c_void_p:
+                    tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None, start_qubits: int = 0) -> ctypes.c_void_p:
     gl = list(gates)
     arr, keep = gate_array(gl)
-    opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model)
+    opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model, start_qubits)
     f = ctypes.c_void_p()
     _check(lib.sv_fuse_circuit(arr, len(gl), n, ctypes.byref(opts), ctypes.byref(f)))
     return f

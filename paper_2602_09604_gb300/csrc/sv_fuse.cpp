@@ -266,6 +266,7 @@ Block controlled_block(const Dense &d)
 
 constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above this validation error
 constexpr int kMaxControlledK = 3;          // targets of a gate kept controlled
+constexpr int kMaxStartQubits = 24;         // the small start state of sv_init_apply
 
 // Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
 std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k)
@@ -429,6 +430,38 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
     return merged;
 }
 
+// Light-cone split for a circuit that starts from a basis state (opts.start_qubits = m): the
+// qubit set S grows with each gate's qubits, in circuit order, while it has at most m qubits; a
+// gate joins the first part when no earlier gate left out shares a qubit with it (so it commutes
+// past all of them) and its qubits lie in S, else its qubits are closed.  The first part is fused
+// apart and placed first: a start from a basis state runs it on the small state of S's qubits.
+void split_light_cone(const std::vector<Dense> &dense, int m, std::vector<Dense> &first, std::vector<Dense> &rest)
+{
+    uint64_t S = 0, closed = 0;
+    for (const Dense &d : dense) {
+        uint64_t q = d.cmask;
+        for (int t : d.q) q |= uint64_t(1) << t;
+        if (!(q & closed) && __builtin_popcountll(S | q) <= m) {
+            S |= q;
+            first.push_back(d);
+        } else {
+            closed |= q;
+            rest.push_back(d);
+        }
+    }
+}
+
+// greedy_partition of the circuit, or of its light-cone part followed by the rest's
+std::vector<Block> partition(const std::vector<Dense> &dense, const std::vector<Dense> *first, const std::vector<Dense> *rest,
+                             int n_qubits, int max_k)
+{
+    if (!first) return greedy_partition(dense, n_qubits, max_k);
+    std::vector<Block> a = greedy_partition(*first, n_qubits, max_k);
+    std::vector<Block> b = greedy_partition(*rest, n_qubits, max_k);
+    for (Block &x : b) a.push_back(std::move(x));
+    return a;
+}
+
 bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
 {
     for (size_t i = 0; i < d; ++i)
@@ -522,6 +555,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     if (opts.tc_min_k < 1 || opts.tc_min_k > SV_MAX_K) { set_error("sv_fuse_circuit: tc_min_k=%d outside [1, 6]", opts.tc_min_k); return SV_EINVAL; }
     if (opts.force_path < SV_PATH_AUTO || opts.force_path > SV_PATH_TC_BF16X3) { set_error("sv_fuse_circuit: bad force_path"); return SV_EINVAL; }
     if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
+    if (opts.start_qubits < 0 || opts.start_qubits > kMaxStartQubits) { set_error("sv_fuse_circuit: start_qubits=%d outside [0, %d]", opts.start_qubits, kMaxStartQubits); return SV_EINVAL; }
 
     // ---- validate and densify every input gate (controls folded into the matrix where they fit
     // the fusion size; otherwise small gates stay controlled)
@@ -581,6 +615,20 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         dense[gi].m = std::move(M);
     }
 
+    // light-cone split for a start from a basis state (at most 24 qubits and fewer than n: the
+    // small state sv_init_apply runs them on)
+    const int start_m = std::min(opts.start_qubits, std::min(kMaxStartQubits, n_qubits - 1));
+    const bool split = opts.start_qubits > 0 && start_m > 0 && opts.mode != SV_FUSE_NONE;
+    std::vector<Dense> first, rest;
+    if (split) {
+        try {
+            split_light_cone(dense, start_m, first, rest);
+        } catch (const std::bad_alloc &) {
+            set_error("sv_fuse_circuit: out of host memory");
+            return SV_ENOMEM;
+        }
+    }
+
     sv_fused *f = new (std::nothrow) sv_fused();
     if (!f) { set_error("sv_fuse_circuit: out of host memory"); return SV_ENOMEM; }
     f->n = n_qubits;
@@ -612,7 +660,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             }
         } else if (opts.mode == SV_FUSE_GREEDY || !mlp_usable(opts.model, kMaxTrustedError)) {
             const int k = opts.mode == SV_FUSE_GREEDY ? opts.max_k : (opts.model ? mlp_fallback_k(opts.model) : opts.max_k);
-            std::vector<Block> blocks = greedy_partition(dense, n_qubits, k);
+            std::vector<Block> blocks = partition(dense, split ? &first : nullptr, &rest, n_qubits, k);
             materialize(blocks, true);
             for (Block &b : blocks) finish(b, -1);
         } else {
@@ -621,8 +669,9 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             std::vector<std::vector<Block>> cand;
             {   // the candidate partitions are independent: build them on host threads
                 std::vector<std::future<std::vector<Block>>> jobs;
+                const std::vector<Dense> *fp = split ? &first : nullptr;
                 for (int k = 2; k <= std::max(2, opts.max_k); ++k)
-                    jobs.push_back(std::async(std::launch::async, [&dense, n_qubits, k]() { return greedy_partition(dense, n_qubits, k); }));
+                    jobs.push_back(std::async(std::launch::async, [&dense, fp, &rest, n_qubits, k]() { return partition(dense, fp, &rest, n_qubits, k); }));
                 for (auto &j : jobs) cand.push_back(j.get());
             }
             std::vector<float> X;

@@ -1,5 +1,6 @@
 """The benchmark configuration itself at full size (30-qubit 5x6 grid, 20 cycles, 845 gates,
-learned fusion, 3xBF16 tensor cores, the launch configuration bench.py times), checked by
+learned fusion with the 24-qubit light cone fused apart, started through sv_init_apply, 3xBF16
+tensor cores: the launch configuration bench.py times), checked by
 properties that hold at any size: the circuit followed by its inverse returns |0...0>, the norm
 stays 1, and the state agrees with the independent fp32 CUDA-core path (greedy K = 4, no tensor
 cores) to the accuracy bar; sampled bitstrings are valid indices of nonzero probability."""
@@ -34,10 +35,9 @@ def test_bench_configuration_full_size(B):
     kw = dict(max_k=6, precision=B.PREC_BF16X3, tc_min_k=4,
               mode=B.FUSE_LEARNED if model is not None else B.FUSE_GREEDY, model=model)
     st = DeviceState(n)
-    # bench path
-    f = B.sv_fuse_circuit(gates, n, **kw)
-    st.init(0)
-    st.apply(f)
+    # bench path: the 24-qubit light cone fused apart, started from |0...0> through sv_init_apply
+    f = B.sv_fuse_circuit(gates, n, **kw, start_qubits=24)
+    B.sv_init_apply(st.h, 0, f, False)
     B.sv_device_status()
     assert abs(st.norm() - 1.0) <= 1e-4
     u = np.random.default_rng(3).random(256)
@@ -71,8 +71,7 @@ def test_bench_configuration_full_size(B):
     del tc
     # circuit then its inverse through the bench path returns |0...0>
     fi = B.sv_fuse_circuit(wl.inverse(gates), n, **kw)
-    st.init(0)
-    st.apply(f)
+    B.sv_init_apply(st.h, 0, f, False)
     st.apply(fi)
     B.sv_device_status()
     amp0 = complex(st.buf[0].item(), st.buf[32].item())

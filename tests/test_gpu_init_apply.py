@@ -70,14 +70,49 @@ def test_grover_from_basis(B):
     assert np.max(np.abs(np.delete(got, marked) - b)) <= 2e-6
 
 
+@pytest.mark.parametrize("n,m,max_k,prec", [(12, 8, 4, 0), (20, 14, 3, 0), (26, 24, 6, 2), (27, 20, 5, 2)])
+def test_light_cone_fusion(B, n, m, max_k, prec):
+    """Fusion with the light cone on m qubits fused apart: sv_init_apply runs at least that part on
+    its small state, and the state is the oracle's."""
+    rng = np.random.default_rng(7 * n + m)
+    gates = []
+    for _ in range(120):
+        k = int(rng.integers(1, 3))
+        nc = int(rng.integers(0, 3)) if rng.random() < 0.2 else 0
+        qs = [int(q) for q in rng.permutation(n)]
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    x = int(rng.integers(0, 1 << n))
+    got, rec, cnt = run(B, n, gates, x, timings=True, max_k=max_k, precision=prec, tc_min_k=4, start_qubits=m)
+    small = sum(1 for r in rec if r["path"] == B.PATH_AUTO)
+    # the light-cone part alone, fused the same way, is what the small state must cover
+    S, closed, part = 0, 0, []
+    for g in gates:
+        q = sum(1 << t for t in tuple(g.targets) + tuple(g.controls))
+        if not (q & closed) and bin(S | q).count("1") <= min(m, n - 1):
+            S |= q
+            part.append(g)
+        else:
+            closed |= q
+    fp = B.sv_fuse_circuit(part, n, max_k=max_k, precision=prec, tc_min_k=4)
+    assert small >= B.sv_fused_count(fp) > 0
+    B.sv_fused_free(fp)
+    ref = oracle.run_circuit(n, gates, x, threads=oracle.default_threads())
+    assert oracle.fidelity(ref, got) >= 1 - 1e-6
+    assert oracle.l2_error(ref, got) <= 1e-4
+
+
 def test_bench_circuit_matches_plain_route(B):
+    """The bench's lazy route (light cone fused apart, sv_init_apply) against the plain route
+    (the circuit fused as one, sv_init then sv_apply_fused_gates)."""
     import torch
     from paper_2602_09604_gb300.state import DeviceState
     n, gates = wl.circuit_30q_grid()
-    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4, start_qubits=24)
     st = DeviceState(n)
     B.sv_init_apply(st.h, 0, f, False)
     lazy = st.buf.clone()
+    B.sv_fused_free(f)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4)
     st.init(0)
     st.apply(f)
     B.sv_fused_free(f)

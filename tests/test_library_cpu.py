@@ -66,8 +66,8 @@ def fused_as_gates(B, f):
     return out
 
 
-def check_fusion(B, n, gates, max_k, init=0):
-    f = B.sv_fuse_circuit(gates, n, max_k=max_k)
+def check_fusion(B, n, gates, max_k, init=0, **kw):
+    f = B.sv_fuse_circuit(gates, n, max_k=max_k, **kw)
     try:
         infos = [B.sv_fused_get_info(f, i) for i in range(B.sv_fused_count(f))]
         biggest = max(len(g.targets) + len(g.controls) for g in gates)
@@ -89,6 +89,51 @@ def test_fusion_is_exact_on_grid_circuit(B, max_k):
     infos = check_fusion(B, n, gates, max_k)
     if max_k >= 2:
         assert len(infos) < len(gates)
+
+
+@pytest.mark.parametrize("max_k,m", [(2, 4), (4, 6), (6, 8), (3, 24)])
+def test_light_cone_split_is_exact_and_first(B, max_k, m):
+    """start_qubits = m: the fused circuit is still exact, and its first fused gates name at most
+    min(m, n - 1) qubits together and commute past every later gate they overtake (so a start
+    from a basis state can run them on a small state)."""
+    rng = np.random.default_rng(40 + m)
+    n = 10
+    gates = []
+    for _ in range(60):
+        k = int(rng.integers(1, 3))
+        qs = [int(q) for q in rng.permutation(n)]
+        nc = 1 if rng.random() < 0.15 else 0
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    infos = check_fusion(B, n, gates, max_k, init=5, start_qubits=m)
+    lim = min(m, n - 1)
+    plain = check_fusion(B, n, gates, max_k, init=5)
+    # the light-cone part of the input gates (the fuser's rule), fused alone
+    S, closed, part = 0, 0, []
+    for g in gates:
+        q = sum(1 << t for t in tuple(g.targets) + tuple(g.controls))
+        if not (q & closed) and bin(S | q).count("1") <= lim:
+            S |= q
+            part.append(g)
+        else:
+            closed |= q
+    fp = B.sv_fuse_circuit(part, n, max_k=max_k)
+    head = [B.sv_fused_get_info(fp, i) for i in range(B.sv_fused_count(fp))]
+    B.sv_fused_free(fp)
+    assert [x["targets"] for x in infos[:len(head)]] == [x["targets"] for x in head]
+    named = 0
+    for x in head:
+        for q in tuple(x["targets"]) + tuple(x["controls"]):
+            named |= 1 << q
+    assert named & ~S == 0 and bin(named).count("1") <= lim
+    assert sum(x["n_source_gates"] for x in infos) == sum(x["n_source_gates"] for x in plain) == len(gates)
+
+
+def test_light_cone_option_validated(B):
+    U = wl.random_unitary(2, np.random.default_rng(1))
+    for bad in (-1, 25):
+        with pytest.raises(B.SvError) as e:
+            B.sv_fuse_circuit([wl.Gate((0,), U)], 4, start_qubits=bad)
+        assert e.value.code == B.SV_EINVAL
 
 
 @pytest.mark.parametrize("max_k", [2, 4, 6])
