@@ -649,23 +649,60 @@ int upload_fused(sv_fused *f, int device)
     if (f->device >= 0 && f->device != device) { set_error("sv_apply_fused_gates: fused circuit was uploaded to another device"); return SV_ESTATE; }
     // k = 6 CUDA-core kernels read an interleaved fp32 matrix image from device memory (made for
     // every k = 6 gate: sv_init_apply may run a tensor-core gate on CUDA cores on a small state)
-    std::vector<float> host;
+    // one device buffer (from the library's cache) for both image kinds: fp32 (ur, ui) images
+    // of the k = 6 gates, then the tensor-core images at a 256-byte aligned offset; built in a
+    // pinned staging buffer and copied once
     f->mat_offset.assign(f->gates.size(), SIZE_MAX);
-    for (size_t i = 0; i < f->gates.size(); ++i) {
-        const FusedGate &g = f->gates[i];
-        if (g.k == 6) {
-            f->mat_offset[i] = host.size();
-            for (size_t e = 0; e < g.ur.size(); ++e) {
-                host.push_back(g.ur[e]);
-                host.push_back(g.ui[e]);
+    size_t mat_floats = 0;
+    for (size_t i = 0; i < f->gates.size(); ++i)
+        if (f->gates[i].k == 6) {
+            f->mat_offset[i] = mat_floats;
+            mat_floats += 2 * f->gates[i].ur.size();
+        }
+    size_t tc_bytes = 0;
+    SV_TRY(plan_tc_operands(f, &tc_bytes));
+    const size_t mat_bytes = mat_floats * sizeof(float);
+    const size_t tc_off = (mat_bytes + 255) & ~size_t(255);
+    const size_t total = tc_off + tc_bytes;
+    if (total > 0) {
+        void *buf = nullptr;
+        size_t got = 0;
+        SV_TRY(dev_buffer_get(device, total, &buf, &got));
+        std::unique_lock<std::mutex> lk;
+        unsigned char *img = nullptr;
+        int rc = pinned_staging(total, &img, lk);
+        if (rc == SV_OK) {
+            // every byte is written: the fp32 images, the gap to tc_off, the tensor-core images
+            // (whole multiples of 128 bytes, so contiguous)
+            std::memset(img + mat_bytes, 0, tc_off - mat_bytes);
+            float *m = reinterpret_cast<float *>(img);
+            for (size_t i = 0; i < f->gates.size(); ++i) {
+                if (f->mat_offset[i] == SIZE_MAX) continue;
+                const FusedGate &g = f->gates[i];
+                float *d = m + f->mat_offset[i];
+                for (size_t e = 0; e < g.ur.size(); ++e) {
+                    d[2 * e] = g.ur[e];
+                    d[2 * e + 1] = g.ui[e];
+                }
+            }
+            if (tc_bytes) rc = write_tc_operands(f, img + tc_off);
+        }
+        if (rc == SV_OK) {
+            const cudaError_t e = cudaMemcpy(buf, img, total, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                set_error("sv_apply_fused_gates: image upload: %s", cudaGetErrorString(e));
+                rc = SV_ECUDA;
             }
         }
+        if (rc != SV_OK) {
+            dev_buffer_put(device, buf, got);
+            return rc;
+        }
+        f->d_buf = buf;
+        f->d_buf_bytes = got;
+        f->d_mats = mat_bytes ? static_cast<float *>(buf) : nullptr;
+        f->d_tc = tc_bytes ? static_cast<unsigned char *>(buf) + tc_off : nullptr;
     }
-    if (!host.empty()) {
-        SV_CUDA_TRY(cudaMalloc(&f->d_mats, host.size() * sizeof(float)));
-        SV_CUDA_TRY(cudaMemcpy(f->d_mats, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
-    }
-    SV_TRY(build_tc_operands(f));
     f->device = device;
     f->c64_ready = true;
     return SV_OK;
@@ -919,11 +956,16 @@ extern "C" int sv_device_status(void)
 extern "C" void sv_fused_free(sv_fused *f)
 {
     if (!f) return;
-    if (f->d_mats || f->d_tc || f->d_mats64) {
+    if (f->d_buf || f->d_mats64) {
+        // kernels of any stream may still read the images: wait for the device, then return the
+        // buffer to the library's cache
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (f->device >= 0 && cur != f->device) cudaSetDevice(f->device);
         cudaDeviceSynchronize();
-        cudaFree(f->d_mats);
-        cudaFree(f->d_tc);
+        dev_buffer_put(f->device, f->d_buf, f->d_buf_bytes);
         cudaFree(f->d_mats64);
+        if (f->device >= 0 && cur >= 0 && cur != f->device) cudaSetDevice(cur);
     }
     delete f;
 }

@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdint>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -104,7 +105,20 @@ int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, c
 int device_sm_count(int device);
 
 // Tensor-core path (sv_tc.cu): host-side operand images and the launcher.
-int build_tc_operands(sv_fused *f);
+// Tensor-core operand images of f's tensor-core gates: plan_tc_operands sets f->tc_offset (byte
+// offsets, 128-byte aligned) and the total size; write_tc_operands writes every image at
+// dst + offset (the gaps between images are left as they are).
+int plan_tc_operands(sv_fused *f, size_t *bytes);
+int write_tc_operands(const sv_fused *f, unsigned char *dst);
+// A pinned host staging buffer of at least `bytes` (library-owned, grown on demand), held with
+// its lock: the caller fills it and copies from it while holding `lock`.
+int pinned_staging(size_t bytes, unsigned char **out, std::unique_lock<std::mutex> &lock);
+// Device buffers for fused-circuit images, reused across fused circuits: dev_buffer_get hands out
+// a cached buffer of this device that fits (at most 4x the request) or allocates one;
+// dev_buffer_put takes one back (the caller has synchronised the device: nothing still reads it)
+// and frees what the cache does not keep (at most 8 buffers, 256 MB per device).
+int dev_buffer_get(int device, size_t bytes, void **out, size_t *got_bytes);
+void dev_buffer_put(int device, void *p, size_t bytes);
 int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms);
 // Cost model (sv_mlp.cu): feature vector, batched prediction in microseconds, trust test.
 void mlp_features(int k, const int *targets_sorted, int path, int n, float *f);
@@ -165,6 +179,8 @@ struct sv_fused {
     std::vector<size_t> mat_offset; // per gate offset in floats into d_mats, or SIZE_MAX
     void *d_tc = nullptr;           // tensor-core operand images
     std::vector<size_t> tc_offset;  // per gate byte offset into d_tc, or SIZE_MAX
+    void *d_buf = nullptr;          // one device buffer holding d_mats and d_tc
+    size_t d_buf_bytes = 0;
     bool c64_ready = false;         // the complex64 images above are uploaded
     double *d_mats64 = nullptr;     // fp64 (re, im) images of k >= 5 gates, for complex128 states
     std::vector<size_t> mat64_offset;

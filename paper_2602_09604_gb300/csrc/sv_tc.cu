@@ -824,7 +824,7 @@ uint32_t host_core_off(int row, int kk, int rows)
     return (uint32_t)((kc * (rows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + e * ESZ);
 }
 
-// Bytes of the B image(s) of a k-qubit gate in `mode`.
+// Bytes of the B image(s) of a k-qubit gate in `mode` (a multiple of 128 for k >= 4).
 size_t b_image_bytes(int k, int mode)
 {
     const size_t KD = size_t(2) << k;
@@ -947,11 +947,10 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
 
 }  // namespace
 
-int build_tc_operands(sv_fused *f)
+int plan_tc_operands(sv_fused *f, size_t *bytes)
 {
     f->tc_offset.assign(f->gates.size(), SIZE_MAX);
-    std::vector<size_t> tc;   // tensor-core gates, each at a 128-byte aligned offset of one image
-    size_t total = 0;
+    size_t total = 0;   // each tensor-core gate's images at a 128-byte aligned offset
     for (size_t i = 0; i < f->gates.size(); ++i) {
         const FusedGate &g = f->gates[i];
         if (g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) continue;
@@ -961,23 +960,25 @@ int build_tc_operands(sv_fused *f)
         }
         f->tc_offset[i] = (total + 127) & ~size_t(127);
         total = f->tc_offset[i] + b_image_bytes(g.k, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3);
-        tc.push_back(i);
     }
-    std::vector<unsigned char> host;
+    *bytes = total;
+    return SV_OK;
+}
+
+int write_tc_operands(const sv_fused *f, unsigned char *dst)
+{
+    std::vector<size_t> tc;
+    for (size_t i = 0; i < f->gates.size(); ++i)
+        if (f->tc_offset[i] != SIZE_MAX) tc.push_back(i);
     try {
-        host.assign(total, 0);
         // the gates' images are independent: built on host threads (a k = 6 image is 32 K elements)
         host_parallel_for(tc.size(), (tc.size() + 3) / 4, [&](size_t t) {
             const FusedGate &g = f->gates[tc[t]];
-            write_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3, host.data() + f->tc_offset[tc[t]]);
+            write_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3, dst + f->tc_offset[tc[t]]);
         });
     } catch (const std::exception &e) {
         set_error("tensor-core operand images: %s", e.what());
         return SV_ENOMEM;
-    }
-    if (!host.empty()) {
-        SV_CUDA_TRY(cudaMalloc(&f->d_tc, host.size()));
-        SV_CUDA_TRY(cudaMemcpy(f->d_tc, host.data(), host.size(), cudaMemcpyHostToDevice));
     }
     return SV_OK;
 }
