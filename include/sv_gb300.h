@@ -376,7 +376,8 @@ SV_API int sv_batch_inject_stall(sv_batch *b, int on);
  * that share no qubit with an earlier gate left out (so they commute past it) while the qubits they
  * name, targets and controls, number at most 24 and fewer than n; every other qubit still holds its
  * bit of basis_index, so the picked gates run first, in order, on the small state of the named
- * qubits (CUDA-core kernels, in a library-owned buffer of up to 128 MB grown on first use), which
+ * qubits (in a library-owned buffer of up to 128 MB grown on first use; tensor-core gates stay on
+ * the tensor cores when the small state has at least k + 5 qubits, the others run on CUDA cores), which
  * one kernel then writes into the zeroed full state; the rest run, in order, as in
  * sv_apply_fused_gates.  Timing records stay in circuit order.  Complex128 states take the plain
  * route.  Asynchronous unless timings are requested. */

@@ -773,7 +773,9 @@ namespace {
 int rank_in(uint64_t A, int q) { return __builtin_popcountll(A & ((1ull << q) - 1ull)); }
 
 // gate g re-expressed on the small state of the qubits in A (ascending order is kept, so the
-// matrix and its local index order are unchanged)
+// matrix, its local index order and its tensor-core operand image are unchanged): a tensor-core
+// gate stays on the tensor cores when the small state is large enough for them (a >= k + 5),
+// every other gate takes the CUDA-core path its new targets call for
 FusedGate remap_gate(const FusedGate &g, uint64_t A, int a)
 {
     FusedGate r;
@@ -789,7 +791,8 @@ FusedGate remap_gate(const FusedGate &g, uint64_t A, int a)
     r.mat = g.mat;
     r.ur = g.ur;
     r.ui = g.ui;
-    r.path = classify_path(r, a, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO);   // CUDA cores on the small state
+    const bool tc = (g.path == SV_PATH_TC_TF32 || g.path == SV_PATH_TC_BF16X3) && a >= g.k + 5;
+    r.path = tc ? g.path : classify_path(r, a, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO);
     return r;
 }
 
@@ -864,7 +867,9 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
                              ? static_cast<const char *>(f->d_tc) + f->tc_offset[i] : nullptr;
         if (timings) cudaEventRecord(ev[2 * i], st->stream);
         if (on_small) {
-            rc = launch_fused_gate(small, a, remap_gate(g, A, a), dm, nullptr, st->stream, st->num_sms);
+            const FusedGate rg = remap_gate(g, A, a);
+            const bool tc = rg.path == SV_PATH_TC_TF32 || rg.path == SV_PATH_TC_BF16X3;
+            rc = launch_fused_gate(small, a, rg, dm, tc ? dt : nullptr, st->stream, st->num_sms);
         } else if (st->c128) {
             const double *um = (f->d_mats64 && f->mat64_offset[i] != SIZE_MAX) ? f->d_mats64 + f->mat64_offset[i] : nullptr;
             rc = c128_apply_gate(st, g, um);
