@@ -266,7 +266,7 @@ Block controlled_block(const Dense &d)
 
 constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above this validation error
 constexpr int kMaxControlledK = 3;          // targets of a gate kept controlled
-constexpr int kMaxStartQubits = 24;         // the small start state of sv_init_apply
+constexpr int kMaxStartQubits = 26;         // the small start state of sv_init_apply
 
 // Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
 std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k)
@@ -615,7 +615,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         dense[gi].m = std::move(M);
     }
 
-    // light-cone split for a start from a basis state (at most 24 qubits and fewer than n: the
+    // light-cone split for a start from a basis state (at most 26 qubits and fewer than n: the
     // small state sv_init_apply runs them on)
     const int start_m = std::min(opts.start_qubits, std::min(kMaxStartQubits, n_qubits - 1));
     const bool split = opts.start_qubits > 0 && start_m > 0 && opts.mode != SV_FUSE_NONE;

@@ -130,7 +130,7 @@ def test_light_cone_split_is_exact_and_first(B, max_k, m):
 
 def test_light_cone_option_validated(B):
     U = wl.random_unitary(2, np.random.default_rng(1))
-    for bad in (-1, 25):
+    for bad in (-1, 27):
         with pytest.raises(B.SvError) as e:
             B.sv_fuse_circuit([wl.Gate((0,), U)], 4, start_qubits=bad)
         assert e.value.code == B.SV_EINVAL
