@@ -746,15 +746,35 @@ constexpr int kCompactMaxQubits = 26;
 struct ExpandArgs {
     int pos[kCompactMaxQubits];   // ascending qubits of A: small-state bit b -> full-state bit pos[b]
     int a;
+    int l0;                       // pos[b] == b for b < l0 (A's lowest qubits are 0 .. l0 - 1)
     unsigned long long rest;      // x on the qubits outside A
     long long n_small;
 };
 
 __global__ void put_one_kernel(float *s, long long off) { s[off] = 1.0f; }
 
+// Small-state amplitude c goes to full index rest | (bit b of c placed at pos[b]).  When A's
+// lowest qubits are 0 .. l0 - 1 (l0 >= 2), the low l0 bits of c stay in place: a thread moves four
+// amplitudes at a time (16-byte loads and stores of real and imaginary parts) and deposits only
+// the bits above l0; otherwise one amplitude at a time with every bit deposited.
 __global__ void expand_compact_kernel(float *__restrict__ full, const float *__restrict__ small, const __grid_constant__ ExpandArgs e)
 {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < e.n_small; c += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (e.l0 >= 2) {
+        const unsigned long long lowmask = (1ull << e.l0) - 1ull;
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (e.n_small >> 2); t += stride) {
+            const unsigned long long c = (unsigned long long)t << 2;
+            unsigned long long i = e.rest | (c & lowmask);
+            for (int b = e.l0; b < e.a; ++b)
+                if ((c >> b) & 1) i |= 1ull << e.pos[b];
+            const long long fo = (long long)(((i >> 5) << 6) | (i & 31ull));
+            const long long so = (long long)(((c >> 5) << 6) | (c & 31ull));
+            *reinterpret_cast<float4 *>(full + fo) = *reinterpret_cast<const float4 *>(small + so);
+            *reinterpret_cast<float4 *>(full + fo + 32) = *reinterpret_cast<const float4 *>(small + so + 32);
+        }
+        return;
+    }
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < e.n_small; c += stride) {
         unsigned long long i = e.rest;
         for (int b = 0; b < e.a; ++b)
             if ((c >> b) & 1) i |= 1ull << e.pos[b];
@@ -835,6 +855,9 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
         for (int q = 0, b = 0; q < 64; ++q)
             if ((A >> q) & 1) e.pos[b++] = q;
         e.a = a;
+        e.l0 = 0;
+        while (e.l0 < a && e.pos[e.l0] == e.l0) ++e.l0;
+        if (a < 2) e.l0 = 0;   // fewer than four amplitudes: one at a time
         e.rest = x & ~A;
         e.n_small = 1ll << a;
         SV_CUDA_TRY(cudaMemsetAsync(st->d, 0, sv_required_bytes(st->n), st->stream));
