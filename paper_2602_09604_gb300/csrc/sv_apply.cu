@@ -878,9 +878,22 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
         if (m > 0 && (*lazy)[i]) order.push_back(i);
     for (size_t i = 0; i < ng; ++i)
         if (!(m > 0 && (*lazy)[i])) order.push_back(i);
+    // The first full-state gate after the small ones can read the small state itself (amplitudes
+    // outside it read as zero) and write every amplitude, which saves the zeroing pass and the
+    // copy: when it runs on a direct tensor-core kernel and A is qubits 0 .. a - 1 (a >= 5, so the
+    // basis bits outside A lie above the block bits and offsets split cleanly).
+    const uint64_t amask = a >= 64 ? ~0ull : ((1ull << a) - 1ull);
+    const uint64_t nmask = st->n >= 64 ? ~0ull : ((1ull << st->n) - 1ull);
+    bool first_reads_small = false;
+    if (m > 0 && m < ng && !st->c128 && A == amask && a >= 5) {
+        const size_t i0 = order[m];
+        const FusedGate &g0 = f->gates[i0];
+        first_reads_small = tc_gate_is_direct(g0) && f->d_tc && i0 < f->tc_offset.size() && f->tc_offset[i0] != SIZE_MAX &&
+                            st->n >= g0.k + 5;
+    }
     int rc = SV_OK;
     for (size_t oi = 0; oi < ng && rc == SV_OK; ++oi) {
-        if (m > 0 && oi == m) rc = expand();
+        if (m > 0 && oi == m && !first_reads_small) rc = expand();
         if (rc != SV_OK) break;
         const size_t i = order[oi];
         const bool on_small = oi < m;
@@ -896,6 +909,10 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
         } else if (st->c128) {
             const double *um = (f->d_mats64 && f->mat64_offset[i] != SIZE_MAX) ? f->d_mats64 + f->mat64_offset[i] : nullptr;
             rc = c128_apply_gate(st, g, um);
+        } else if (first_reads_small && oi == m) {
+            const uint64_t rest = x & ~A & nmask;
+            const TcSource vs{small, nmask & ~amask, rest, (long long)((rest >> 5) << 6)};
+            rc = launch_tc_gate(st->d, st->n, g, dt, st->stream, st->num_sms, &vs);
         } else {
             rc = launch_fused_gate(st->d, st->n, g, dm, dt, st->stream, st->num_sms);
         }

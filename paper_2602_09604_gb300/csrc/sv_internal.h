@@ -119,7 +119,20 @@ int pinned_staging(size_t bytes, unsigned char **out, std::unique_lock<std::mute
 // and frees what the cache does not keep (at most 8 buffers, 256 MB per device).
 int dev_buffer_get(int device, size_t bytes, void **out, size_t *got_bytes);
 void dev_buffer_put(int device, void *p, size_t bytes);
-int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms);
+// A gate's inputs read from another buffer: input amplitude i is src[offset(i) - off] when
+// (i & mask) == rest and 0 otherwise (offset = the blocked-layout float offset); the outputs still
+// cover the whole state.  Used for the first full-state gate after a lazy start: src is the small
+// state of qubits 0 .. a-1, mask the bits from a up, rest the basis bits there.
+struct TcSource {
+    const float *src;
+    unsigned long long mask, rest;
+    long long off;
+};
+int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms,
+                   const TcSource *vs = nullptr);
+// The gate runs on a direct tensor-core kernel (at most two targets below qubit 5), the kernels
+// that take a TcSource.
+bool tc_gate_is_direct(const FusedGate &g);
 // Cost model (sv_mlp.cu): feature vector, batched prediction in microseconds, trust test.
 void mlp_features(int k, const int *targets_sorted, int path, int n, float *f);
 int mlp_predict_us(sv_mlp *m, const float *X, int rows, double *out_us);

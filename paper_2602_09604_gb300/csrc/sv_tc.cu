@@ -64,6 +64,14 @@ struct TcArgs {
     int *err;                  // device error word (bounded-wait time-outs)
 };
 
+// Virtual source (direct kernels with VS): input amplitude i is src[offset(i) - off] when
+// (i & mask) == rest and 0 otherwise; the outputs go to sv as usual.
+struct VsArgs {
+    const float *src;
+    unsigned long long mask, rest;
+    long long off;
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
@@ -277,8 +285,10 @@ __device__ __forceinline__ float4 xor_perm4(float4 v, unsigned sw)
 //      group reads), and each lane streams its A row, 32 tensor-memory columns at a time, into
 //      the warpgroup's A region (tcgen05.st);
 //   4. one thread per warpgroup issues the MMAs (A from tensor memory, B from shared memory).
-template <int K, int MODE, bool STAGED>
-__global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN_BLOCKS_STAGED : TcShape<K, MODE>::MIN_BLOCKS_DIRECT) apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+// VS (direct variant only): inputs from the virtual source v instead of sv.  The body is inlined
+// into two entry points so the kernels without a virtual source keep their own parameter block.
+template <int K, int MODE, bool STAGED, bool VS>
+__device__ __forceinline__ void tc_kernel_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
 {
     using S = TcShape<K, MODE>;
     constexpr int D = S::D;
@@ -371,8 +381,18 @@ __global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN
                 fb_next = (long long)(((b >> 5) << 6) | (b & 31ull));
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    xd[j] = sv[fb_next + a.foff[j]];
-                    xd[D + j] = sv[fb_next + a.foff[j] + 32];
+                    if constexpr (VS) {
+                        unsigned long long ij = b;   // index of local amplitude j
+#pragma unroll
+                        for (int i = 0; i < K; ++i)
+                            if ((j >> i) & 1) ij |= 1ull << a.tpos[i];
+                        const bool in = (ij & v.mask) == v.rest;
+                        xd[j] = in ? v.src[fb_next + a.foff[j] - v.off] : 0.f;
+                        xd[D + j] = in ? v.src[fb_next + a.foff[j] + 32 - v.off] : 0.f;
+                    } else {
+                        xd[j] = sv[fb_next + a.foff[j]];
+                        xd[D + j] = sv[fb_next + a.foff[j] + 32];
+                    }
                 }
             } else {
 #pragma unroll
@@ -584,6 +604,20 @@ __global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN
     }
 }
 
+template <int K, int MODE, bool STAGED>
+__global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN_BLOCKS_STAGED : TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
+    apply_tc_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    tc_kernel_body<K, MODE, STAGED, false>(sv, a, VsArgs{});
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
+    apply_tc_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
+{
+    tc_kernel_body<K, MODE, false, true>(sv, a, v);
+}
+
 // Direct kernel, shared-memory A form (used for k = 6 with no target below qubit 5).  Like the direct
 // variant above, lane m of a warpgroup owns group 128 t + m of its tile t and moves its amplitudes
 // straight between registers and global memory, but the tile's A operand is written to shared
@@ -592,9 +626,8 @@ __global__ void __launch_bounds__(2 * kTcThreads, STAGED ? TcShape<K, MODE>::MIN
 // warpgroup stores the results of tile t - 1:
 //   load(t+1) -> epilogue(t-1) from the other accumulator -> wait MMA(t) -> build A(t+1)
 //   -> MMA(t+1) into the accumulator epilogue(t-1) just emptied.
-template <int K, int MODE>
-__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
-    apply_tc_direct_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+template <int K, int MODE, bool VS>
+__device__ __forceinline__ void tc_direct_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
 {
     using S = TcShape<K, MODE>;
     constexpr int D = S::D;
@@ -658,8 +691,18 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_D
             fb_next = (long long)(((b >> 5) << 6) | (b & 31ull));
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                xd[j] = sv[fb_next + a.foff[j]];
-                xd[D + j] = sv[fb_next + a.foff[j] + 32];
+                if constexpr (VS) {
+                    unsigned long long ij = b;   // index of local amplitude j
+#pragma unroll
+                    for (int i = 0; i < K; ++i)
+                        if ((j >> i) & 1) ij |= 1ull << a.tpos[i];
+                    const bool in = (ij & v.mask) == v.rest;
+                    xd[j] = in ? v.src[fb_next + a.foff[j] - v.off] : 0.f;
+                    xd[D + j] = in ? v.src[fb_next + a.foff[j] + 32 - v.off] : 0.f;
+                } else {
+                    xd[j] = sv[fb_next + a.foff[j]];
+                    xd[D + j] = sv[fb_next + a.foff[j] + 32];
+                }
             }
         } else {
 #pragma unroll
@@ -788,6 +831,20 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_D
     }
 }
 
+template <int K, int MODE>
+__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
+    apply_tc_direct_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    tc_direct_body<K, MODE, false>(sv, a, VsArgs{});
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
+    apply_tc_direct_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
+{
+    tc_direct_body<K, MODE, true>(sv, a, v);
+}
+
 // ---------------------------------------------------------------------------------------- host
 uint16_t bf16_rn(double v)
 {
@@ -886,7 +943,7 @@ int device_err_word(int **out)
 namespace {
 
 template <int K, int MODE>
-int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)
+int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms, const TcSource *vs)
 {
     using S = TcShape<K, MODE>;
     if (n < K + 5) { set_error("tensor-core path needs n >= k + 5 (n=%d, k=%d)", n, K); return SV_EINVAL; }
@@ -919,20 +976,30 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     // shared-memory A for k = 6 when its accesses need no L1 reuse: no low target, or one at
     // qubit 3 or 4 (a warp access then covers whole 32-byte sectors of two lines)
     const int variant = staged ? 1 : (kDirectSmemA && K == 6 && (nlow == 0 || (nlow == 1 && low_min >= 3)) ? 2 : 0);
+    if (vs && staged) { set_error("tensor-core gate: a virtual source needs a direct variant"); return SV_EINVAL; }
+    VsArgs v{};
+    if (vs) v = VsArgs{vs->src, vs->mask, vs->rest, vs->off};
     void (*kern)(float *, const TcArgs) = variant == 1 ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
-    if constexpr (K == 6)   // the shared-memory-A kernel exists for k = 6 only
-        if (variant == 2) kern = apply_tc_direct_kernel<K, MODE>;
+    void (*kern_vs)(float *, const TcArgs, const VsArgs) = apply_tc_kernel_vs<K, MODE>;
+    if constexpr (K == 6) {   // the shared-memory-A kernel exists for k = 6 only
+        if (variant == 2) {
+            kern = apply_tc_direct_kernel<K, MODE>;
+            kern_vs = apply_tc_direct_kernel_vs<K, MODE>;
+        }
+    }
+    const int akey = variant + (vs ? 3 : 0);   // function-attribute slot
     const int smem = variant == 1 ? S::SMEM_STAGED : (variant == 2 ? S::SMEM_DIRECT2 : S::SMEM_DIRECT);
     const int tmem_cols = variant == 2 ? S::TMEM_COLS_D2 : S::TMEM_COLS;
-    static uint64_t attr_set[3] = {0, 0, 0};   // a bit per device (function attributes are per device)
+    static uint64_t attr_set[6] = {0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
     {
         int dev = 0;
         SV_CUDA_TRY(cudaGetDevice(&dev));
         const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
         std::lock_guard<std::mutex> lk(g_tc_mu);
-        if (!(attr_set[variant] & bit) || !bit) {
-            SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr_set[variant] |= bit;
+        if (!(attr_set[akey] & bit) || !bit) {
+            if (vs) SV_CUDA_TRY(cudaFuncSetAttribute(kern_vs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            else SV_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr_set[akey] |= bit;
         }
     }
     // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
@@ -940,7 +1007,8 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     const int by_smem = std::max(1, (227 * 1024) / (smem + 1024));
     const int per_sm = std::min(staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT, std::min(by_tmem, by_smem));
     const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
-    kern<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a);
+    if (vs) kern_vs<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a, v);
+    else kern<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -983,14 +1051,21 @@ int write_tc_operands(const sv_fused *f, unsigned char *dst)
     return SV_OK;
 }
 
-int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms)
+bool tc_gate_is_direct(const FusedGate &g)
+{
+    int nlow = 0;
+    for (int b = 0; b < g.k; ++b) nlow += g.targets[b] < 5;
+    return (g.path == SV_PATH_TC_TF32 || g.path == SV_PATH_TC_BF16X3) && g.k >= 4 && g.k <= 6 && nlow < 3;
+}
+
+int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms, const TcSource *vs)
 {
     if (!dtc) { set_error("tensor-core gate has no device operand image"); return SV_EINVAL; }
     const bool tf = g.path == SV_PATH_TC_TF32;
     switch (g.k) {
-    case 4: return tf ? launch_tc_t<4, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<4, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
-    case 5: return tf ? launch_tc_t<5, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<5, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
-    case 6: return tf ? launch_tc_t<6, kModeTF32>(sv, n, g, dtc, stream, num_sms) : launch_tc_t<6, kModeBF16X3>(sv, n, g, dtc, stream, num_sms);
+    case 4: return tf ? launch_tc_t<4, kModeTF32>(sv, n, g, dtc, stream, num_sms, vs) : launch_tc_t<4, kModeBF16X3>(sv, n, g, dtc, stream, num_sms, vs);
+    case 5: return tf ? launch_tc_t<5, kModeTF32>(sv, n, g, dtc, stream, num_sms, vs) : launch_tc_t<5, kModeBF16X3>(sv, n, g, dtc, stream, num_sms, vs);
+    case 6: return tf ? launch_tc_t<6, kModeTF32>(sv, n, g, dtc, stream, num_sms, vs) : launch_tc_t<6, kModeBF16X3>(sv, n, g, dtc, stream, num_sms, vs);
     default: set_error("tensor-core path handles k = 4..6, got %d", g.k); return SV_EINVAL;
     }
 }

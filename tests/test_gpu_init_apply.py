@@ -101,6 +101,28 @@ def test_light_cone_fusion(B, n, m, max_k, prec):
     assert oracle.l2_error(ref, got) <= 1e-4
 
 
+@pytest.mark.parametrize("tg", [(3, 7, 12, 24, 25, 20), (0, 9, 14, 24, 25, 17), (8, 11, 24, 25, 19),
+                                (1, 2, 24, 25), (5, 6, 7, 24, 25, 16)])
+def test_first_full_gate_reads_the_small_state(B, tg):
+    """After a light cone on qubits 0-23 the first full-state gate is a direct tensor-core gate
+    (shared-memory-A k = 6, tensor-memory-A k = 6 with a target at qubit 0, k = 5, k = 4 with two
+    low targets, k = 6 without low targets): it reads the small state in place of the zeroed full
+    state.  Basis bits above the light cone are set.  The state is the oracle's."""
+    n = 26
+    rng = np.random.default_rng(sum(tg))
+    gates = [wl.random_gate(n, 1, rng, targets=(q,)) for q in range(24)]
+    gates += [wl.random_gate(n, 2, rng, targets=(q, q + 1)) for q in range(0, 23, 2)]
+    gates += [wl.random_gate(n, len(tg), rng, targets=tuple(tg))]
+    gates += [wl.random_gate(n, 2, rng, targets=(24, 25)), wl.random_gate(n, 2, rng, targets=(2, 13))]
+    x = (1 << 24) | (1 << 25) | 0b1011
+    got, rec, cnt = run(B, n, gates, x, timings=True, max_k=6, precision=2, tc_min_k=4, start_qubits=24)
+    small = sum(1 for r in rec if r["path"] == B.PATH_AUTO)
+    assert 0 < small < cnt
+    ref = oracle.run_circuit(n, gates, x, threads=oracle.default_threads())
+    assert oracle.fidelity(ref, got) >= 1 - 1e-6
+    assert oracle.l2_error(ref, got) <= 1e-4
+
+
 def test_bench_circuit_matches_plain_route(B):
     """The bench's lazy route (light cone fused apart, sv_init_apply) against the plain route
     (the circuit fused as one, sv_init then sv_apply_fused_gates)."""
