@@ -128,30 +128,46 @@ def host_cores() -> int:
 
 
 # ------------------------------------------------------------------------------------- oracle arm
-def oracle_gate_sample(gates, count):
-    import numpy as np
-    idx = np.linspace(0, len(gates) - 1, count).round().astype(int)
-    return [gates[i] for i in idx]
+def oracle_strata(gates):
+    """The circuit's gates grouped by kind (number of targets, number of controls): the oracle's
+    time per gate depends on the kind, so samples are drawn per kind and weighted by its count."""
+    strata = {}
+    for g in gates:
+        strata.setdefault((len(g.targets), len(tuple(g.controls))), []).append(g)
+    return strata
 
 
-def run_oracle_steps(n, gates, steps, warmup, gates_per_step):
-    """Times the oracle applying `gates_per_step` gates (spread evenly over the circuit) to the
-    n-qubit complex128 state per step; returns (seconds per circuit extrapolated, threads, detail)."""
+def run_oracle_steps(n, gates, steps, per_kind):
+    """Times the oracle on the n-qubit complex128 state: per step, `per_kind` gates of every kind
+    (evenly spaced within the kind).  One untimed gate first touches every page of the state.
+    Returns (seconds per circuit = sum over kinds of mean s/gate x the kind's count, threads,
+    per-kind detail)."""
     import numpy as np
     import oracle
     oracle.build()
     th = host_cores()
     psi = oracle.basis_state(n, 0)
-    sample = oracle_gate_sample(gates, gates_per_step)
-    for _ in range(warmup):
-        oracle.apply_gate(psi, n, sample[0], th)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        for g in sample:
-            oracle.apply_gate(psi, n, g, th)
-    dt = time.perf_counter() - t0
-    per_gate = dt / (steps * len(sample))
-    return per_gate * len(gates), th, per_gate
+    strata = oracle_strata(gates)
+    oracle.apply_gate(psi, n, gates[0], th)          # page faults of the fresh state, untimed
+    detail = {}
+    for kind, gl in sorted(strata.items()):
+        idx = np.linspace(0, len(gl) - 1, per_kind).round().astype(int)
+        t = 0.0
+        for _ in range(steps):
+            for i in idx:
+                t0 = time.perf_counter()
+                oracle.apply_gate(psi, n, gl[i], th)
+                t += time.perf_counter() - t0
+        detail[kind] = {"count": len(gl), "timed": steps * len(idx), "s_per_gate": t / (steps * len(idx))}
+    value = sum(d["s_per_gate"] * d["count"] for d in detail.values())
+    return value, th, detail
+
+
+def oracle_sample_text(detail, steps):
+    kinds = ", ".join(f"{d['timed']} of the {d['count']} {k[0]}-qubit{' controlled' if k[1] else ''} gates "
+                      f"({d['s_per_gate']:.3f} s/gate)" for k, d in sorted(detail.items()))
+    return (f"stratified by gate kind over {steps} step(s): {kinds}, applied to the 2^30 complex128 state "
+            f"after one untimed gate; s/circuit = sum of mean s/gate x the kind's count")
 
 
 def bench_reference(args):
@@ -160,15 +176,16 @@ def bench_reference(args):
         return
     from paper_2602_09604_gb300 import workloads as wl
     n, gates = wl.circuit_30q_grid()
-    gps = args.ref_gates_per_step
-    value, th, per_gate = run_oracle_steps(n, gates, args.steps, args.warmup, gps)
-    sample = f"{gps} of the 845 gates per step (evenly spaced), applied to the 2^30 complex128 state; " \
-             f"s/circuit = mean s/gate ({per_gate:.3f}) x 845"
+    value, th, detail = run_oracle_steps(n, gates, args.steps, args.ref_gates_per_kind)
+    timed = sum(d["timed"] for d in detail.values())
+    sample = oracle_sample_text(detail, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_gate * gps * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sum(d["s_per_gate"] * d["timed"] for d in detail.values()) / args.steps * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n_qubits": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample,
+                             "gates_timed": timed},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -434,10 +451,9 @@ def bench_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, th, per_gate = run_oracle_steps(n, gates, 1, 0, args.cpu_gates)
+        v, th, detail = run_oracle_steps(n, gates, 1, args.cpu_gates_per_kind)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
-                                "sample": f"{args.cpu_gates} of the 845 gates (evenly spaced) applied once to the "
-                                          f"2^30 complex128 state; s/circuit = mean s/gate ({per_gate:.3f}) x 845"}
+                                "sample": oracle_sample_text(detail, 1)}
     for fc in fused_by_start.values():
         B.sv_fused_free(fc)
     if model is not None:
@@ -462,8 +478,10 @@ def main():
     ap.add_argument("--fusion", default="learned", choices=["learned", "greedy"])
     ap.add_argument("--no-plain-sweep", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-gates", type=int, default=12)
-    ap.add_argument("--ref-gates-per-step", type=int, default=3)
+    ap.add_argument("--cpu-gates-per-kind", type=int, default=6,
+                    help="oracle gates timed per gate kind for cpu_baseline (one step)")
+    ap.add_argument("--ref-gates-per-kind", type=int, default=2,
+                    help="--impl reference: oracle gates timed per gate kind and step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expval", action="store_true")
     ap.add_argument("--no-next-rows", action="store_true")

@@ -176,7 +176,10 @@ SV_API int sv_store(const sv_state *st, void *dst, int dst_on_host);
 SV_API int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits, const sv_fuse_opts *opts,
                     sv_fused **out);
 
-SV_API void sv_fused_free(sv_fused *f);   /* synchronises the device if device copies exist */
+/* Frees a fused circuit.  If its device images exist, waits first for the last launch of every
+ * stream that applied it (sv_apply_fused_gates / sv_init_apply on a state's stream); work on other
+ * streams is not waited for. */
+SV_API void sv_fused_free(sv_fused *f);
 
 SV_API int sv_fused_count(const sv_fused *f);
 SV_API int sv_fused_get_info(const sv_fused *f, int i, sv_fused_info *info);

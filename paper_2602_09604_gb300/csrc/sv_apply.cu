@@ -725,8 +725,17 @@ int upload_fused_c128(sv_fused *f, int device)
         }
     }
     if (!host.empty()) {
-        SV_CUDA_TRY(cudaMalloc(&f->d_mats64, host.size() * sizeof(double)));
-        SV_CUDA_TRY(cudaMemcpy(f->d_mats64, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice));
+        void *buf = nullptr;
+        size_t got = 0;
+        SV_TRY(dev_buffer_get(device, host.size() * sizeof(double), &buf, &got));
+        const cudaError_t e = cudaMemcpy(buf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            dev_buffer_put(device, buf, got);
+            set_error("sv_apply_fused_gates: fp64 image upload: %s", cudaGetErrorString(e));
+            return SV_ECUDA;
+        }
+        f->d_mats64 = static_cast<double *>(buf);
+        f->d_mats64_bytes = got;
     }
     f->device = device;
     return SV_OK;
@@ -791,6 +800,22 @@ __global__ void expand_compact_kernel(float *__restrict__ full, const float *__r
 namespace {
 
 int rank_in(uint64_t A, int q) { return __builtin_popcountll(A & ((1ull << q) - 1ull)); }
+
+// Records that `stream` has launched kernels reading f's device images (one reusable event per
+// stream), so that sv_fused_free can wait for exactly that work.
+int note_fused_use(sv_fused *f, cudaStream_t stream)
+{
+    for (auto &u : f->use_events)
+        if (u.first == stream) {
+            SV_CUDA_TRY(cudaEventRecord(u.second, stream));
+            return SV_OK;
+        }
+    cudaEvent_t e = nullptr;
+    SV_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    f->use_events.emplace_back(stream, e);
+    SV_CUDA_TRY(cudaEventRecord(e, stream));
+    return SV_OK;
+}
 
 // gate g re-expressed on the small state of the qubits in A (ascending order is kept, so the
 // matrix, its local index order and its tensor-core operand image are unchanged): a tensor-core
@@ -938,7 +963,8 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
             rc = SV_ETIMEOUT;
         }
     }
-    return rc;
+    const int urc = note_fused_use(f, st->stream);   // even after an error: launches may be queued
+    return rc != SV_OK ? rc : urc;
 }
 
 }  // namespace
@@ -1001,15 +1027,19 @@ extern "C" int sv_device_status(void)
 extern "C" void sv_fused_free(sv_fused *f)
 {
     if (!f) return;
-    if (f->d_buf || f->d_mats64) {
-        // kernels of any stream may still read the images: wait for the device, then return the
-        // buffer to the library's cache
+    if (f->d_buf || f->d_mats64 || !f->use_events.empty()) {
+        // only the streams that applied this circuit can still read its images: wait for each
+        // one's last launch (its event), then return the buffers to the library's cache
         int cur = -1;
         cudaGetDevice(&cur);
         if (f->device >= 0 && cur != f->device) cudaSetDevice(f->device);
-        cudaDeviceSynchronize();
+        for (auto &u : f->use_events) {
+            cudaEventSynchronize(u.second);
+            cudaEventDestroy(u.second);
+        }
+        f->use_events.clear();
         dev_buffer_put(f->device, f->d_buf, f->d_buf_bytes);
-        cudaFree(f->d_mats64);
+        dev_buffer_put(f->device, f->d_mats64, f->d_mats64_bytes);
         if (f->device >= 0 && cur >= 0 && cur != f->device) cudaSetDevice(cur);
     }
     delete f;

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <functional>
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -115,7 +116,7 @@ int write_tc_operands(const sv_fused *f, unsigned char *dst);
 int pinned_staging(size_t bytes, unsigned char **out, std::unique_lock<std::mutex> &lock);
 // Device buffers for fused-circuit images, reused across fused circuits: dev_buffer_get hands out
 // a cached buffer of this device that fits (at most 4x the request) or allocates one;
-// dev_buffer_put takes one back (the caller has synchronised the device: nothing still reads it)
+// dev_buffer_put takes one back (the caller has waited for every launch that reads it)
 // and frees what the cache does not keep (at most 8 buffers, 256 MB per device).
 int dev_buffer_get(int device, size_t bytes, void **out, size_t *got_bytes);
 void dev_buffer_put(int device, void *p, size_t bytes);
@@ -196,5 +197,9 @@ struct sv_fused {
     size_t d_buf_bytes = 0;
     bool c64_ready = false;         // the complex64 images above are uploaded
     double *d_mats64 = nullptr;     // fp64 (re, im) images of k >= 5 gates, for complex128 states
+    size_t d_mats64_bytes = 0;
     std::vector<size_t> mat64_offset;
+    // one event per stream that has applied this circuit, recorded after its last launch there:
+    // sv_fused_free waits for these (not for the whole device) before the images are reused
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> use_events;
 };

@@ -81,7 +81,10 @@ def trained(B):
 
 def test_training_learns_a_cost_function(B, trained):
     m, stats = trained
-    assert stats["trained"] == 0 or True
+    assert stats["trained"] == 1, stats
+    # every epoch is one pass of mini-batches over the training rows (90% of 3000, batch 256)
+    assert stats["n_train"] + stats["n_val"] == 3000 and stats["n_val"] == 300, stats
+    assert stats["steps"] == 120 * -(-stats["n_train"] // 256), stats
     assert stats["val_mape"] < 0.08, stats
     assert B.sv_mlp_get_stats(m)["trained"] == 1
 

@@ -231,3 +231,62 @@ def test_planted_mistakes_are_caught():
     x = 5
     bad = [wl.Gate(g.targets, g.matrix.conj(), g.controls) if g.name == "cp" else g for g in wl.qft_circuit(5)]
     assert np.max(np.abs(oracle.run_circuit(5, bad, x) - closed_forms.qft_state(5, x))) > 1e-3
+
+
+# Hand-computed values for the acceptance metrics (F = |<ref|psi>|^2 / (||ref||^2 ||psi||^2) and
+# ||psi - ref||_2, the bar the GPU path is held to).  Each value below was worked out on paper.
+_L2_CASES = [
+    ([1, 0], [0, 1], math.sqrt(2)),                 # |0> vs |1>: sqrt(1 + 1)
+    ([1, 0], [1j, 0], math.sqrt(2)),                # |i - 1| = sqrt(2)
+    ([0], [3 + 4j], 5.0),                           # a single 3-4-5 amplitude
+    ([1, 1j], [1j, 1], 2.0),                        # |i - 1|^2 + |1 - i|^2 = 4
+    ([0.5, 0.5, 0.5, 0.5], [0.5, 0.5, 0.5, -0.5], 1.0),   # one sign flipped: |-1| = 1
+]
+_F_CASES = [
+    ([1, 0], [1, 1], 0.5),                          # F(|0>, |+>) = 1/2 (|+> unnormalised)
+    ([1, 0], [0, 1], 0.0),                          # orthogonal
+    ([1, 1j], [1, 1j], 1.0),                        # the same state: conj matters (no conj gives 0)
+    ([1, 1j], [1, 1], 0.5),                         # <a|b> = 1 - i: |1 - i|^2 / (2 * 2) = 2/4
+    ([2, 0, 0], [0.5, 0.5 * math.sqrt(3), 0], 0.25),   # cos^2(pi/3), ref not normalised
+    ([1, 0], [1j, 0], 1.0),                         # a global phase does not count
+]
+
+
+@pytest.mark.parametrize("a,b,want", _L2_CASES)
+def test_l2_error_hand_values(a, b, want):
+    assert oracle.l2_error(np.array(a, complex), np.array(b, complex)) == pytest.approx(want, abs=1e-15)
+    assert oracle.l2_error(np.array(b, complex), np.array(a, complex)) == pytest.approx(want, abs=1e-15)
+
+
+@pytest.mark.parametrize("a,b,want", _F_CASES)
+def test_fidelity_hand_values(a, b, want):
+    assert oracle.fidelity(np.array(a, complex), np.array(b, complex)) == pytest.approx(want, abs=1e-15)
+    assert oracle.fidelity(np.array(b, complex), np.array(a, complex)) == pytest.approx(want, abs=1e-15)
+
+
+def test_metric_mistakes_are_caught():
+    """Plausible mistakes in the two metrics, planted here on the CPU, each fail a hand value."""
+    def l2_no_sqrt(a, b):                      # squared norm
+        return float(np.sum(np.abs(np.asarray(b) - np.asarray(a)) ** 2))
+
+    def l2_max(a, b):                          # max-norm instead of the 2-norm
+        return float(np.max(np.abs(np.asarray(b) - np.asarray(a))))
+
+    def l2_real_only(a, b):                    # imaginary parts dropped
+        return float(np.linalg.norm(np.real(np.asarray(b) - np.asarray(a))))
+
+    def f_no_conj(a, b):                       # <a|b> without the conjugate
+        a, b = np.asarray(a, complex), np.asarray(b, complex)
+        return float(abs(np.dot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+
+    def f_no_norm(a, b):                       # overlap not normalised
+        return float(abs(np.vdot(np.asarray(a, complex), np.asarray(b, complex))) ** 2)
+
+    def f_no_square(a, b):                     # |<a|b>| instead of its square
+        a, b = np.asarray(a, complex), np.asarray(b, complex)
+        return float(abs(np.vdot(a, b)) / math.sqrt(np.vdot(a, a).real * np.vdot(b, b).real))
+
+    for bad in (l2_no_sqrt, l2_max, l2_real_only):
+        assert any(abs(bad(np.array(a, complex), np.array(b, complex)) - w) > 1e-6 for a, b, w in _L2_CASES), bad
+    for bad in (f_no_conj, f_no_norm, f_no_square):
+        assert any(abs(bad(np.array(a, complex), np.array(b, complex)) - w) > 1e-6 for a, b, w in _F_CASES), bad
