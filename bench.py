@@ -18,8 +18,13 @@ slowest rank / circuits run by all ranks); `e2e` is the same metric measured thr
 with host buffers (fusion on the host, sample uniforms uploaded, samples and norm read back).
 `--impl reference` times the complex128 CPU oracle on a bounded sample of the same circuit.
 Outside the timed step the line also reports Pauli expectation passes on the circuit's state
-(`expval_pauli`) and the rows beyond the hot path (`next_rows`: the controlled-gate kernel,
-Grover and quantum-volume circuits, and the circuit on a complex128 state).
+(`expval_pauli`), the rows beyond the hot path (`next_rows`: the controlled-gate kernel,
+Grover and quantum-volume circuits, and the circuit on a complex128 state), the step's accuracy
+against that complex128 state (`accuracy`: fidelity and l2 distance), and the larger workloads
+(`large_configs`: the 33-qubit grid and 34-qubit QFT, learned partition vs fixed greedy fusion at
+every max size, and the 256-circuit HEA batch in one persistent launch vs the per-circuit loop).
+`dtype` names the arithmetic: complex64 state, 3xBF16 (or TF32) tensor-core products with fp32
+accumulation for fused gates of --tc-min-k or more qubits.
 """
 from __future__ import annotations
 
@@ -40,6 +45,8 @@ UNIT = "s/circuit"
 N_QUBITS = 30
 N_SAMPLES = 1024
 WORKLOAD = "grid30: 5x6 grid random circuit, 20 cycles, 845 gates, seed 2, |0..0>, complex64"
+DTYPES = {"bf16x3": "c64 (3xbf16 products, fp32 accumulate)", "tf32": "c64 (tf32 products, fp32 accumulate)",
+          "fp32": "c64 (fp32)"}
 FP64_PEAK_TFLOPS = 1.20   # fp64 FMA throughput measured on this GPU (independent FMA chains, all SMs)
 
 
@@ -125,6 +132,70 @@ def dist_env():
 
 def host_cores() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def device_state_metrics(ref_buf, buf, chunk_blocks=1 << 21):
+    """Fidelity and l2 distance (fp64, on the device) between two states in the blocked layout:
+    blocks of 32 real then 32 imaginary parts, fp32 or fp64 (complex64 or complex128 states)."""
+    import torch
+    a_all, b_all = ref_buf.view(-1, 2, 32), buf.view(-1, 2, 32)
+    ov = torch.zeros((), dtype=torch.complex128, device=ref_buf.device)
+    d2 = torch.zeros((), dtype=torch.float64, device=ref_buf.device)
+    na = torch.zeros_like(d2)
+    nb = torch.zeros_like(d2)
+    for lo in range(0, a_all.shape[0], chunk_blocks):
+        a = a_all[lo:lo + chunk_blocks].double()
+        b = b_all[lo:lo + chunk_blocks].double()
+        ca, cb = torch.complex(a[:, 0], a[:, 1]), torch.complex(b[:, 0], b[:, 1])
+        ov += (ca.conj() * cb).sum()
+        d2 += ((cb - ca).abs() ** 2).sum()
+        na += (ca.abs() ** 2).sum()
+        nb += (cb.abs() ** 2).sum()
+    return float(ov.abs() ** 2 / (na * nb)), float(d2.sqrt())
+
+
+def large_configs(B, wl, model, stream):
+    """The 33-qubit grid circuit (6x6 minus 3 sites, 24 cycles, seed 4; 64 GiB state) and the
+    34-qubit QFT of a seeded basis state (128 GiB): learned partition vs fixed greedy fusion at
+    every max size (3xBF16 tensor cores for 4+ qubit gates) and the plain fp32 CUDA-core K = 4,
+    device time of one circuit each (apply only; the state is set before each timing).  Then the
+    256-circuit HEA batch: one persistent graph launch (autotuned) vs the per-circuit launch loop."""
+    import torch
+    from paper_2602_09604_gb300.state import DeviceState
+    out = {}
+    for name, n, gates, x in (("grid33_24c", wl.GRID_33.n, wl.random_grid_circuit(wl.GRID_33, 24, seed=4), 0),
+                              ("qft34", 34, wl.qft_circuit(34), wl.qft_basis_index(34, seed=34))):
+        st = DeviceState(n, stream=stream)
+        res = {}
+        variants = [("learned_bf16x3", dict(max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4, model=model)),
+                    ("plain_fp32_k4", dict(max_k=4))]
+        variants += [(f"greedy_k{k}_bf16x3", dict(max_k=k, precision=B.PREC_BF16X3, tc_min_k=4)) for k in range(2, 7)]
+        for label, kw in variants:
+            if kw.get("model", 1) is None:
+                continue
+            f = B.sv_fuse_circuit(gates, n, **kw)
+            B.sv_init(st.h, x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.sv_apply_fused_gates(st.h, f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[label] = {"s": e0.elapsed_time(e1) / 1e3, "fused_gates": B.sv_fused_count(f)}
+            B.sv_fused_free(f)
+        B.sv_device_status()
+        st.free()
+        del st
+        torch.cuda.empty_cache()
+        best = min((v["s"], k) for k, v in res.items() if k.startswith("greedy"))
+        out[name] = {"n_qubits": n, "gates": len(gates), "variants": res, "best_fixed": best[1],
+                     "learned_over_best_fixed": res["learned_bf16x3"]["s"] / best[0] if "learned_bf16x3" in res else None}
+    from paper_2602_09604_gb300 import batch as bt
+    rep = bt.report()
+    out["hea256_batch"] = {k: rep[k] for k in ("workload", "batched_ms", "loop_ms", "speedup", "batched_per_gate_tiles_k4_ms",
+                                               "traffic_gb", "fused_gates", "state_mb")}
+    out["hea256_batch"]["autotuned"] = {k: rep["autotuned"][k] for k in ("max_k", "stage_log2", "stage_k", "threads", "ctas")}
+    return out
 
 
 # ------------------------------------------------------------------------------------- oracle arm
@@ -355,6 +426,7 @@ def bench_ours(args):
 
     # ---- NEXT rows on the same state buffer: controlled-gate kernel, Grover and quantum volume
     next_rows = {}
+    accuracy = None
     if not args.no_next_rows:
         rng2 = np.random.default_rng(77)
         ctrl = {}
@@ -387,6 +459,13 @@ def bench_ours(args):
             c128[f"greedy_k{mk}"] = {"s_per_circuit": sec, "fused_gates": len(ks), "tflops": flops / sec / 1e12,
                                      "frac_of_fp64_peak": flops / sec / 1e12 / FP64_PEAK_TFLOPS}
             B.sv_fused_free(fc)
+        # the timed step's state (same fused circuit, same start) against the complex128 state
+        step(False)
+        torch.cuda.synchronize()
+        fid, l2 = device_state_metrics(st128.buf, st.buf)
+        accuracy = {"fidelity": fid, "one_minus_fidelity": 1.0 - fid, "l2_error": l2,
+                    "reference": "complex128 GPU state of the same circuit (fp64, greedy K = 3)",
+                    "bar": "F >= 1 - 1e-6 and l2 <= 1e-4"}
         st128.free()
         next_rows["c128_grid30"] = c128
         circ = {"grover30_r3": wl.grover_circuit(n, 0x2C0FFEE1, 3), "qv30": wl.qv_circuit(n, seed=1)}
@@ -423,7 +502,7 @@ def bench_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_qubits": n, "max_k": args.max_k, "precision": args.precision,
                    "tc_min_k": args.tc_min_k, "fusion": fusion, "fused_gates": n_fused,
                    "fused_k_histogram": {str(k): sum(1 for i in infos if i["k"] == k) for k in range(1, 7)}, "samples_per_step": N_SAMPLES,
@@ -448,6 +527,7 @@ def bench_ours(args):
         "norm": norms[-1] if norms else None,
         "expval_pauli": expval or None,
         "next_rows": next_rows or None,
+        "accuracy": accuracy,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -456,10 +536,14 @@ def bench_ours(args):
                                 "sample": oracle_sample_text(detail, 1)}
     for fc in fused_by_start.values():
         B.sv_fused_free(fc)
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+    if not args.no_large and ws == 1:
+        line["large_configs"] = large_configs(B, wl, model, stream)
     if model is not None:
         line["cost_model"] = {k: v for k, v in B.sv_mlp_get_stats(model).items() if k in ("val_mape", "steps")}
         B.sv_mlp_free(model)
-    st.free()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -485,6 +569,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expval", action="store_true")
     ap.add_argument("--no-next-rows", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 33-qubit grid, 34-qubit QFT and HEA batch comparisons (run after the timed step)")
     ap.add_argument("--start-qubits", type=int, default=26,
                     help="light cone fused apart for the lazy start (0 = fuse the circuit as one)")
     ap.add_argument("--start", choices=["lazy", "plain"], default="lazy",

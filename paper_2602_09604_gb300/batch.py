@@ -9,6 +9,12 @@ from a default, each candidate replayed from its captured CUDA graph and timed w
 batch's circuit sizes and gate counts.
 
     python -m paper_2602_09604_gb300.batch --report     # HEA batch: 256 circuits, n ~ U{10..20}
+
+Several GPUs (one process each, launched by torchrun) split the batch by circuit with no data
+exchange: each rank autotunes and runs its balanced share in one persistent launch, and the job
+time is the slowest rank's (``dist.sharded_batch_time``):
+
+    python -m torch.distributed.run --nproc-per-node N -m paper_2602_09604_gb300.batch --shard
 """
 from __future__ import annotations
 
@@ -192,10 +198,51 @@ def report(count=256, seed=5):
     return out
 
 
+def run_sharded(count=256, seed=5, repeats=5):
+    """This process's rank (RANK / LOCAL_RANK / WORLD_SIZE from torchrun; one GPU each) runs its
+    share of the HEA batch; rank 0 returns the job line, the others None."""
+    import torch.distributed as tdist
+    from . import dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl")
+    circuits = wl.hea_batch(count=count, seed=seed)
+    tuned = {}
+
+    def time_share(share):
+        best, _ = autotune(share)
+        b = Batch(share, best["max_k"])
+        try:
+            apply(b, best)
+            ms = b.time(b.run, repeats)
+            B.sv_device_status()
+        finally:
+            b.free()
+        tuned.update(best)
+        return ms
+
+    idx, job_ms = dist.sharded_batch_time(circuits, rank, world, time_share, device="cuda")
+    if world > 1:
+        tdist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"workload": f"{count} HEA circuits, n ~ U{{10..20}}, seed {seed}", "ranks": world,
+            "job_ms": job_ms, "rank0_circuits": len(idx), "rank0_autotuned": tuned}
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--report", action="store_true")
+    ap.add_argument("--shard", action="store_true", help="one rank per GPU under torchrun, batch split by circuit")
     ap.add_argument("--count", type=int, default=256)
     a = ap.parse_args()
     import __graft_entry__  # noqa: F401  (build)
-    print(json.dumps(report(a.count)))
+    if a.shard:
+        line = run_sharded(a.count)
+        if line is not None:
+            print(json.dumps(line))
+    else:
+        print(json.dumps(report(a.count)))

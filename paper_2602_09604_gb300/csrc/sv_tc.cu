@@ -13,17 +13,17 @@
 //             hi*hi + hi*lo + lo*hi accumulated in fp32; the dropped lo*lo term and the split
 //             remainders are ~2^-16 relative.
 //
-// Kernel structure (persistent, one CTA of 4 warps per SM slot):
-//   * B (the gate's real block matrix, pre-split and pre-laid-out on the host in the tcgen05
-//     K-major no-swizzle core-matrix layout) is copied once per CTA into shared memory with a
-//     bulk asynchronous copy (TMA engine) completing on an mbarrier;
-//   * thread m owns group row m of a tile: it loads its group's 2^k amplitudes (the next tile's
-//     loads are issued before the current tile's epilogue so they overlap), converts them and
-//     writes its A row into one of two shared-memory stages;
-//   * thread 0 issues the tcgen05.mma chain for the tile into one of two TMEM accumulators and
-//     commits it to an mbarrier;
-//   * after the mbarrier completes every thread reads its TMEM lane (tcgen05.ld.32x32b) and
-//     stores the group's 2^k outputs back in place.
+// Kernel forms (all persistent; B -- the gate's real block matrix, pre-split and pre-laid-out on the
+// host in the tcgen05 K-major no-swizzle core-matrix layout -- is copied once per CTA into shared
+// memory with a bulk asynchronous copy (TMA engine) completing on an mbarrier):
+//   * two-warpgroup kernels (k = 4..6): each warpgroup is a pipeline over every other MMA tile of
+//     the CTA: its threads load a tile's groups (direct: lane m owns group 128 t + m; staged:
+//     through per-warp shared-memory tiles), write the A operand into tensor memory, one thread
+//     issues the tcgen05.mma chain and commits it to an mbarrier, and the threads read the
+//     accumulator back (tcgen05.ld) and store the outputs in place;
+//   * the warp-specialised kernel (k = 6 without low targets, or one at qubit 3 or 4): loader
+//     warps, one MMA thread and epilogue warps connected by mbarriers, with A in a two-stage
+//     shared-memory ring and four accumulators in tensor memory (see that kernel).
 // Every mbarrier wait is bounded: on time-out the kernel records an error code in a device word,
 // frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -845,6 +845,313 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_D
     tc_direct_body<K, MODE, true>(sv, a, v);
 }
 
+// ------------------------------------------------------------------------ warp-specialised kernel
+// k = 6 gates on the direct (lane-per-group) access pattern, with the work split by role so that
+// loads are always in flight.  One persistent CTA per SM walks its MMA tiles i = 0, 1, ...
+// (tile blockIdx.x + i * gridDim.x, 128 groups each):
+//   * LW loader warps: warp w owns rows 32 (w % 4) .. +31 of every tile and a slice of each row's
+//     amplitudes; per tile it converts its registers (bf16 hi/lo split, or tf32) into the A image of
+//     shared-memory stage i % 2 (K-major core-matrix layout) and, chunk by chunk, reloads them with
+//     the next tile's amplitudes, so the next tile's loads are in flight while this one converts
+//     and while the warp waits for a free stage;
+//   * one MMA thread: per tile it waits for the stage and for a free accumulator (four in tensor
+//     memory, 128 columns each), issues the products and commits them to the stage's "empty" and
+//     the accumulator's "full" barriers;
+//   * EW epilogue warps (warp index % 4 = the tensor-memory lane quarter they may read): per tile
+//     they read the accumulator (tcgen05.ld) and store the outputs in place, then free it.
+// A tile depends only on earlier tiles' barrier phases, so the pipeline cannot deadlock.  Every
+// wait is bounded; a role that gives up sets a shared abort flag (the others stop at their next
+// wait) and the device error word; the MMA thread then waits (bounded) for its products to
+// complete before tensor memory is freed.
+constexpr int kWsStages = 2;   // A stages in shared memory (64 KB each)
+constexpr int kWsAcc = 4;      // accumulators in tensor memory (4 x 128 columns: all 512)
+
+template <int MODE>
+struct WsShape {
+    using S = TcShape<6, MODE>;
+    static constexpr int A_STAGE = S::A_SMEM;
+    static constexpr int OFF_A = S::B_BYTES;
+    static constexpr int OFF_BAR = S::B_BYTES + kWsStages * A_STAGE;
+    static constexpr int N_BAR = 1 + 2 * kWsStages + 2 * kWsAcc + 1;   // b, a full/empty, acc full/empty, drain
+    static constexpr int SMEM = OFF_BAR + N_BAR * 8 + 16;
+    static constexpr int TMEM_COLS = kWsAcc * S::KD;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MODE, bool VS, int LW, int EW>
+__device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
+{
+    using S = TcShape<6, MODE>;
+    using W = WsShape<MODE>;
+    constexpr int K = 6, D = 64;
+    constexpr int MMA_WARP = LW + EW;
+    static_assert(LW % 4 == 0 && (D / (LW / 4)) % 8 == 0, "loader warps: whole row quarters, 8-amplitude chunks");
+    static_assert(EW == 4 || EW == 8, "epilogue warps: one or two per lane quarter");
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + W::OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + W::N_BAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const uint32_t bar_b = smem_u32(&bars[0]);
+    const uint32_t bar_afull = smem_u32(&bars[1]);                            // + 8 s
+    const uint32_t bar_aempty = smem_u32(&bars[1 + kWsStages]);               // + 8 s
+    const uint32_t bar_accfull = smem_u32(&bars[1 + 2 * kWsStages]);          // + 8 c
+    const uint32_t bar_accempty = smem_u32(&bars[1 + 2 * kWsStages + kWsAcc]);   // + 8 c
+    const uint32_t bar_drain = smem_u32(&bars[W::N_BAR - 1]);
+    const uint32_t sA0 = smem_u32(smem + W::OFF_A);
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_b, 1);
+        for (int s = 0; s < kWsStages; ++s) {
+            mbar_init(bar_afull + 8 * s, LW * 32);
+            mbar_init(bar_aempty + 8 * s, 1);
+        }
+        for (int c = 0; c < kWsAcc; ++c) {
+            mbar_init(bar_accfull + 8 * c, 1);
+            mbar_init(bar_accempty + 8 * c, EW * 32);
+        }
+        mbar_init(bar_drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)W::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const long long ntile = a.n_mma_tiles;
+    const long long cnt = (long long)blockIdx.x < ntile ? (ntile - 1 - (long long)blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](long long i) -> long long { return (long long)blockIdx.x + i * (long long)gridDim.x; };
+    // bounded wait; gives up early once another role has given up
+    auto wait = [&](uint32_t bar, uint32_t parity, int code) -> bool {
+        for (long long it = 0; it < kWaitIters; ++it) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if (*abort_flag) return false;
+            if (it > 32) __nanosleep(64);
+        }
+        *abort_flag = 1;
+        atomicOr(a.err, code);
+        return false;
+    };
+    // group 128 * tile + m: index with zeros at the targets (b) and its float offset (fb)
+    auto group_base = [&](long long tile, int m, unsigned long long &b, long long &fb) -> bool {
+        const long long g = tile * kTcM + m;
+        b = (unsigned long long)g;
+#pragma unroll
+        for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
+        fb = (long long)(((b >> 5) << 6) | (b & 31ull));
+        return g < a.n_groups;
+    };
+
+    if (warp < LW) {
+        // ------------------------------------------------------------------ loaders
+        constexpr int AMPS = D / (LW / 4);   // amplitudes of a row this lane converts
+        constexpr int CH = AMPS / 8;         // chunks of 8 amplitudes (16 floats in registers each)
+        const int m = 32 * (warp & 3) + lane;
+        const int j_lo = (warp >> 2) * AMPS;
+        const uint32_t row_off = (uint32_t)((m >> 3) * 128 + (m & 7) * 16);
+        float xr[CH][16];
+        auto load_chunk = [&](bool valid, unsigned long long b, long long fb, int c) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = j_lo + 8 * c + e;
+                if constexpr (VS) {
+                    const long long fo = a.foff[j];
+                    const unsigned long long ij = b | ((unsigned long long)(fo >> 6) << 5) | (unsigned long long)(fo & 31);
+                    const bool in = valid && (ij & v.mask) == v.rest;
+                    xr[c][e] = in ? v.src[fb + fo - v.off] : 0.f;
+                    xr[c][8 + e] = in ? v.src[fb + fo + 32 - v.off] : 0.f;
+                } else {
+                    xr[c][e] = valid ? sv[fb + a.foff[j]] : 0.f;
+                    xr[c][8 + e] = valid ? sv[fb + a.foff[j] + 32] : 0.f;
+                }
+            }
+        };
+        auto st16 = [](uint32_t addr, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w0), "r"(w1), "r"(w2), "r"(w3) : "memory");
+        };
+        // chunk c of this lane's row into the A image(s) at stage base sa: element kk of the row is
+        // the real part of amplitude kk (kk < 64) or the imaginary part of amplitude kk - 64
+        auto convert_chunk = [&](int c, uint32_t sa) {
+            const int j0 = j_lo + 8 * c;
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {   // real, imaginary
+                if constexpr (MODE == kModeTF32) {
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        const int kc = (64 * part + j0 + 4 * hf) / 4;
+                        const float *x = &xr[c][8 * part + 4 * hf];
+                        st16(sa + (uint32_t)(kc * S::LBO_A) + row_off, f32_to_tf32(x[0]), f32_to_tf32(x[1]),
+                             f32_to_tf32(x[2]), f32_to_tf32(x[3]));
+                    }
+                } else {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float x0 = xr[c][8 * part + 2 * q], x1 = xr[c][8 * part + 2 * q + 1];
+                        hi[q] = pack_bf16x2(x0, x1);   // element 2q in the low half
+                        const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xffff0000u);
+                        lo[q] = pack_bf16x2(x0 - h0, x1 - h1);
+                    }
+                    const uint32_t o = (uint32_t)(((64 * part + j0) / 8) * S::LBO_A) + row_off;
+                    st16(sa + o, hi[0], hi[1], hi[2], hi[3]);
+                    st16(sa + (uint32_t)S::A_IMG_SMEM + o, lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+        };
+        unsigned long long b_n = 0;
+        long long fb_n = 0;
+        bool v_n = false;
+        if (cnt > 0) {
+            v_n = group_base(tile_of(0), m, b_n, fb_n);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) load_chunk(v_n, b_n, fb_n, c);
+        }
+        for (long long i = 0; i < cnt; ++i) {
+            const int s = (int)(i % kWsStages);
+            const bool more = i + 1 < cnt;
+            if (more) v_n = group_base(tile_of(i + 1), m, b_n, fb_n);
+            if (i >= kWsStages && !wait(bar_aempty + 8 * s, (uint32_t)((i / kWsStages - 1) & 1), 0x40)) break;
+            const uint32_t sa = sA0 + (uint32_t)(s * W::A_STAGE);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                convert_chunk(c, sa);
+                if (more) load_chunk(v_n, b_n, fb_n, c);   // the next tile's chunk, in flight from here
+            }
+            fence_proxy_async();   // generic-proxy stores -> read by the tensor core (async proxy)
+            mbar_arrive(bar_afull + 8 * s);
+        }
+    } else if (warp < MMA_WARP) {
+        // ------------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int part = (warp - LW) >> 2;   // EW = 8: which half of the columns
+        const int m = 32 * quarter + lane;
+        const uint32_t t_lane = ((uint32_t)(quarter * 32)) << 16;
+        for (long long i = 0; i < cnt; ++i) {
+            const int c = (int)(i % kWsAcc);
+            if (!wait(bar_accfull + 8 * c, (uint32_t)((i / kWsAcc) & 1), 0x20)) break;
+            tc_fence_after();
+            unsigned long long b;
+            long long fb;
+            const bool valid = group_base(tile_of(i), m, b, fb);
+            const uint32_t td = tmem + (uint32_t)(c * S::KD) + t_lane;
+            constexpr int NB = EW == 4 ? 4 : 2;   // 32-column blocks this warp reads
+#pragma unroll
+            for (int cb = 0; cb < NB; ++cb) {
+                // EW = 4: blocks 0..3 (columns 0..127); EW = 8: real block `part`, imaginary block 2 + part
+                const int blk = EW == 4 ? cb : (cb == 0 ? part : 2 + part);
+                float o[32];
+                tmem_ld32(td + (uint32_t)(32 * blk), o);
+                if (valid) {
+#pragma unroll
+                    for (int x = 0; x < 32; ++x) {
+                        const int col = 32 * blk + x;   // (c', r): c' = col / 64, r = col % 64
+                        sv[fb + a.foff[col % D] + (col >= D ? 32 : 0)] = o[x];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(bar_accempty + 8 * c);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issue
+        const uint32_t idesc = (1u << 4) | ((MODE == kModeTF32 ? 2u : 1u) << 7) | ((MODE == kModeTF32 ? 2u : 1u) << 10) |
+                               ((uint32_t)(S::KD >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+        const uint32_t b0 = smem_u32(smem);
+        bool b_done = false;
+        if (cnt > 0) {   // B image: bulk copies of up to 32 KB, all completing on bar_b
+            mbar_arrive_expect_tx(bar_b, a.bbytes);
+            for (unsigned off = 0; off < a.bbytes; off += 32768u) {
+                const unsigned sz = a.bbytes - off < 32768u ? a.bbytes - off : 32768u;
+                bulk_g2s(b0 + off, static_cast<const unsigned char *>(a.bimg) + off, sz, bar_b);
+            }
+            b_done = wait(bar_b, 0, 0x10);
+        }
+        for (long long i = 0; b_done && i < cnt; ++i) {
+            const int s = (int)(i % kWsStages), c = (int)(i % kWsAcc);
+            if (!wait(bar_afull + 8 * s, (uint32_t)((i / kWsStages) & 1), 0x20)) break;
+            if (i >= kWsAcc && !wait(bar_accempty + 8 * c, (uint32_t)((i / kWsAcc - 1) & 1), 0x20)) break;
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(c * S::KD);
+            const uint32_t sa = sA0 + (uint32_t)(s * W::A_STAGE);
+            constexpr int NSTEP = S::KD / S::KSTEP;
+            constexpr int CHS = S::KSTEP / S::EPC;   // 16-byte chunks per instruction (2)
+            if constexpr (MODE == kModeTF32) {
+#pragma unroll
+                for (int st = 0; st < NSTEP; ++st)
+                    mma<MODE>(d, sdesc(sa + st * CHS * S::LBO_A, S::LBO_A, 128), sdesc(b0 + st * CHS * S::LBO_B, S::LBO_B, 128),
+                              idesc, st > 0);
+            } else {
+                const uint32_t a_img[3] = {sa, sa, sa + (uint32_t)S::A_IMG_SMEM};   // hi, hi, lo
+                const uint32_t b_img[3] = {b0, b0 + (uint32_t)S::B_IMG, b0};        // hi, lo, hi
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int st = 0; st < NSTEP; ++st)
+                        mma<MODE>(d, sdesc(a_img[p] + st * CHS * S::LBO_A, S::LBO_A, 128),
+                                  sdesc(b_img[p] + st * CHS * S::LBO_B, S::LBO_B, 128), idesc, (p > 0 || st > 0));
+            }
+            mma_commit(bar_aempty + 8 * s);   // the stage may be overwritten once these products are done
+            mma_commit(bar_accfull + 8 * c);
+        }
+        // every product issued above completes before tensor memory is freed, and the B copy
+        // before its shared memory is released (bounded: the error word records a give-up)
+        mma_commit(bar_drain);
+        if (!mbar_wait_bounded(bar_drain, 0)) atomicOr(a.err, 0x80);
+        if (cnt > 0 && !b_done && !mbar_wait_bounded(bar_b, 0)) atomicOr(a.err, 0x80);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)W::TMEM_COLS) : "memory");
+    }
+}
+
+constexpr int kWsLoadWarps = 8;
+constexpr int kWsEpiWarps = 4;
+constexpr int kWsThreads = (kWsLoadWarps + kWsEpiWarps + 1) * 32;
+
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1) apply_tc_ws_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps>(sv, a, VsArgs{});
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    apply_tc_ws_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
+{
+    tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps>(sv, a, v);
+}
+
 // ---------------------------------------------------------------------------------------- host
 uint16_t bf16_rn(double v)
 {
@@ -942,22 +1249,34 @@ int device_err_word(int **out)
 
 namespace {
 
+// Kernel form of a tensor-core gate, decided by its targets below qubit 5 (they lie inside a
+// 32-amplitude block).  One function decides for the launcher and for tc_gate_is_direct.
+//   1 (staged): three or more such targets -- the direct accesses would span >= 8 lines, so data
+//     moves through the per-warp shared-memory tiles (measured at n = 30 with three: direct
+//     2.3-3.9 vs staged 4.4-5.8 TB/s);
+//   2 (warp-specialised, k = 6): no such target, or one at qubit 3 or 4 (a warp access then covers
+//     whole 32-byte sectors of two lines);
+//   0 (direct, A in tensor memory): the rest -- one or two such targets, where the accesses need
+//     the L1 reuse that the warp-specialised kernel's 192 KB of shared memory would crowd out.
+int tc_variant(const FusedGate &g)
+{
+    int nlow = 0, low_min = 32;
+    for (int b = 0; b < g.k; ++b) {
+        nlow += g.targets[b] < 5;
+        low_min = g.targets[b] < low_min ? g.targets[b] : low_min;
+    }
+    if (nlow >= 3) return 1;
+    if (g.k == 6 && (nlow == 0 || (nlow == 1 && low_min >= 3))) return 2;
+    return 0;
+}
+
 template <int K, int MODE>
 int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms, const TcSource *vs)
 {
     using S = TcShape<K, MODE>;
     if (n < K + 5) { set_error("tensor-core path needs n >= k + 5 (n=%d, k=%d)", n, K); return SV_EINVAL; }
-    // Targets below qubit 5 lie inside a 32-amplitude block.  With at most two of them the direct
-    // variant still wins: a warp's accesses for one amplitude span at most four lines and the
-    // complementary parts come from L1 (measured at n = 30: k = 6 5.3-5.8 vs 4.3-4.4 TB/s staged,
-    // k = 5 6.6 vs 5.0-5.2).  From three on, staging through shared memory wins.
-    int nlow = 0;
-    int low_min = 32;   // lowest target
-    for (int b = 0; b < K; ++b) {
-        nlow += g.targets[b] < 5;
-        low_min = g.targets[b] < low_min ? g.targets[b] : low_min;
-    }
-    const bool staged = nlow >= 3;
+    const int variant = tc_variant(g);
+    const bool staged = variant == 1;
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
     SV_TRY(make_tile_map(g, n, K, &a.t));
@@ -973,23 +1292,26 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bimg = dtc;
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
-    // shared-memory A for k = 6 when its accesses need no L1 reuse: no low target, or one at
-    // qubit 3 or 4 (a warp access then covers whole 32-byte sectors of two lines)
-    const int variant = staged ? 1 : (kDirectSmemA && K == 6 && (nlow == 0 || (nlow == 1 && low_min >= 3)) ? 2 : 0);
     if (vs && staged) { set_error("tensor-core gate: a virtual source needs a direct variant"); return SV_EINVAL; }
     VsArgs v{};
     if (vs) v = VsArgs{vs->src, vs->mask, vs->rest, vs->off};
-    void (*kern)(float *, const TcArgs) = variant == 1 ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
+    void (*kern)(float *, const TcArgs) = staged ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
     void (*kern_vs)(float *, const TcArgs, const VsArgs) = apply_tc_kernel_vs<K, MODE>;
-    if constexpr (K == 6) {   // the shared-memory-A kernel exists for k = 6 only
+    int smem = staged ? S::SMEM_STAGED : S::SMEM_DIRECT;
+    int tmem_cols = S::TMEM_COLS;
+    int threads = 2 * kTcThreads;
+    int per_sm_regs = staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT;
+    if constexpr (K == 6) {   // the warp-specialised kernel exists for k = 6 only
         if (variant == 2) {
-            kern = apply_tc_direct_kernel<K, MODE>;
-            kern_vs = apply_tc_direct_kernel_vs<K, MODE>;
+            kern = apply_tc_ws_kernel<MODE>;
+            kern_vs = apply_tc_ws_kernel_vs<MODE>;
+            smem = WsShape<MODE>::SMEM;
+            tmem_cols = WsShape<MODE>::TMEM_COLS;
+            threads = kWsThreads;
+            per_sm_regs = 1;
         }
     }
     const int akey = variant + (vs ? 3 : 0);   // function-attribute slot
-    const int smem = variant == 1 ? S::SMEM_STAGED : (variant == 2 ? S::SMEM_DIRECT2 : S::SMEM_DIRECT);
-    const int tmem_cols = variant == 2 ? S::TMEM_COLS_D2 : S::TMEM_COLS;
     static uint64_t attr_set[6] = {0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
     {
         int dev = 0;
@@ -1002,13 +1324,15 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
             attr_set[akey] |= bit;
         }
     }
-    // CTAs per SM bounded by registers (MIN_BLOCKS), shared memory and tensor memory (512 columns)
+    // CTAs per SM bounded by registers, shared memory and tensor memory (512 columns)
     const int by_tmem = std::max(1, 512 / tmem_cols);
     const int by_smem = std::max(1, (227 * 1024) / (smem + 1024));
-    const int per_sm = std::min(staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT, std::min(by_tmem, by_smem));
-    const long long grid = std::min<long long>((a.n_mma_tiles + 1) / 2, (long long)num_sms * per_sm);
-    if (vs) kern_vs<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a, v);
-    else kern<<<(unsigned)grid, 2 * kTcThreads, smem, stream>>>(sv, a);
+    const int per_sm = std::min(per_sm_regs, std::min(by_tmem, by_smem));
+    // the two-warpgroup kernels take two MMA tiles per CTA round, the warp-specialised one one
+    const long long tiles_per_cta = variant == 2 ? 1 : 2;
+    const long long grid = std::min<long long>((a.n_mma_tiles + tiles_per_cta - 1) / tiles_per_cta, (long long)num_sms * per_sm);
+    if (vs) kern_vs<<<(unsigned)grid, threads, smem, stream>>>(sv, a, v);
+    else kern<<<(unsigned)grid, threads, smem, stream>>>(sv, a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -1053,9 +1377,7 @@ int write_tc_operands(const sv_fused *f, unsigned char *dst)
 
 bool tc_gate_is_direct(const FusedGate &g)
 {
-    int nlow = 0;
-    for (int b = 0; b < g.k; ++b) nlow += g.targets[b] < 5;
-    return (g.path == SV_PATH_TC_TF32 || g.path == SV_PATH_TC_BF16X3) && g.k >= 4 && g.k <= 6 && nlow < 3;
+    return (g.path == SV_PATH_TC_TF32 || g.path == SV_PATH_TC_BF16X3) && g.k >= 4 && g.k <= 6 && tc_variant(g) != 1;
 }
 
 int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaStream_t stream, int num_sms, const TcSource *vs)

@@ -37,3 +37,21 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_circuits(circuits, rank: int, world: int):
+    """`rank`'s share of a batch of (n_qubits, gates) circuits: every circuit goes to exactly one
+    rank, balanced by the work of one pass per gate (2^n amplitudes x gate count).  Returns
+    (indices into `circuits`, the circuits)."""
+    cost = [float(1 << int(n)) * max(1, len(g)) for n, g in circuits]
+    idx = shard_balanced(cost, rank, world)
+    return idx, [circuits[i] for i in idx]
+
+
+def sharded_batch_time(circuits, rank: int, world: int, time_share, device=None):
+    """Runs this rank's share through `time_share(share) -> milliseconds` and returns
+    (indices of the share, job milliseconds = the slowest rank's).  No circuit data crosses
+    ranks: only the one float of the timing reduction."""
+    idx, share = shard_circuits(circuits, rank, world)
+    ms = time_share(share) if share else 0.0
+    return idx, max_over_ranks(ms, device=device)
