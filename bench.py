@@ -323,6 +323,7 @@ def bench_ours(args):
         step(False)
     # ---- device-timed region (events on the launching stream)
     kernel_us = {}
+    small_source_us = []
     lazy_gates = 0
     # per step: fused gates + chunk sums + scan + search, plus basis set (plain start) or small-state
     # basis set + expansion (lazy start)
@@ -340,6 +341,10 @@ def bench_ours(args):
             for info, r in zip(infos, rec):
                 if r["path"] == B.PATH_AUTO:   # ran on the small start state, not a full pass
                     lazy_gates += 1
+                    continue
+                if r["flags"] & B.TIMING_SMALL_SOURCE:   # read only the small state: its own class
+                    key = (B.PATH_NAMES[info["path"]] + "_small_source", info["k"])
+                    small_source_us.append(r["us"])
                     continue
                 key = (B.PATH_NAMES[info["path"]], info["k"])
                 kernel_us.setdefault(key, []).append(r["us"])
@@ -496,7 +501,8 @@ def bench_ours(args):
     kernel_key = f"apply_{dom[0]}_k{dom[1]}_n{n}"
     traffic = read_traffic(kernel_key)
     all_us = sum(totals.values())
-    full_passes = n_fused - lazy_gates // max(1, args.steps)   # gates that ran on the full state
+    # full passes: gates that ran on the full state, less the one that read the small state
+    full_passes = n_fused - (lazy_gates + len(small_source_us)) // max(1, args.steps)
     passes_gbs = full_passes * bytes_per_launch / (sum(totals.values()) / args.steps * 1e-6) / 1e9
 
     line = {
@@ -521,6 +527,7 @@ def bench_ours(args):
         "per_kernel_class": {f"{p}_k{k}": {"launches": len(v), "avg_us": statistics.mean(v),
                                            "gbs": bytes_per_launch / (statistics.mean(v) * 1e-6) / 1e9}
                              for (p, k), v in sorted(kernel_us.items())},
+        "small_source_gate_us": statistics.mean(small_source_us) if small_source_us else None,
         "plain_fusion_fp32": plain,
         "plain_best_s": min((v["s_per_circuit"] for v in plain.values()), default=None),
         "speedup_vs_best_plain": (min(v["s_per_circuit"] for v in plain.values()) / value) if plain else None,

@@ -132,8 +132,15 @@ typedef struct sv_timing {
     float us;                /* device time of this fused gate's kernel, microseconds */
     int k;
     int path;                /* the kernel path; SV_PATH_AUTO for a gate sv_init_apply ran on its small state */
+    int flags;               /* SV_TIMING_* bits */
     uint64_t target_mask;    /* bit q set <-> qubit q is a target */
 } sv_timing;
+
+/* sv_timing.flags: the gate read its inputs from sv_init_apply's small start state (the first
+ * full-state gate after a lazy start, when it runs on a direct tensor-core kernel): it wrote the
+ * whole state but read only the small state's 2^a amplitudes, so its time is not that of a full
+ * pass and is no sample of the kernel's usual cost. */
+#define SV_TIMING_SMALL_SOURCE 1
 
 /* ---------------------------------------------------------------------------------------------
  * State
@@ -394,7 +401,11 @@ SV_API int sv_device_status(void);
  *
  * Same result as sv_sample, bit for bit, but it needs no sv_state and calls no cudaMalloc,
  * cudaFree or allocating library routine: every intermediate lives in one fixed array compiled
- * into the library (about 1.1 MB per GPU, held from library load until process exit).  This is
+ * into the library (about 1.1 MB per GPU, held until process exit).  The array is placed on a GPU
+ * when the library's module is loaded there; CUDA loads modules lazily by default, i.e. at the
+ * first launch of one of the library's kernels on that GPU (at the latest, the first call of this
+ * function), so a caller that lets its own pool claim the GPU afterwards should make one warm-up
+ * call (any size) first.  This is
  * for callers that own all device memory up front and must not let a library grow it (a serving
  * process whose pool already claims the GPU, where cudaMalloc would fail or fragment), and for
  * callers that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may cause.

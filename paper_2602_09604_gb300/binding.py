@@ -71,8 +71,11 @@ class sv_batch_info(ctypes.Structure):
                 ("traffic_bytes", ctypes.c_double)]
 
 
+TIMING_SMALL_SOURCE = 1   # sv_timing.flags: inputs read from the lazy start's small state
+
+
 class sv_timing(ctypes.Structure):
-    _fields_ = [("us", ctypes.c_float), ("k", ctypes.c_int), ("path", ctypes.c_int),
+    _fields_ = [("us", ctypes.c_float), ("k", ctypes.c_int), ("path", ctypes.c_int), ("flags", ctypes.c_int),
                 ("target_mask", ctypes.c_uint64)]
 
 
@@ -282,8 +285,8 @@ def sv_init_apply(h, basis_index: int, f, timings: bool = False):
     n = sv_fused_count(f)
     rec = (sv_timing * max(n, 1))()
     _check(lib.sv_init_apply(h, basis_index, f, rec))
-    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "target_mask": rec[i].target_mask}
-            for i in range(n)]
+    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "flags": rec[i].flags,
+             "target_mask": rec[i].target_mask} for i in range(n)]
 
 
 def sv_apply_fused_gates(h, f, timings: bool = False):
@@ -293,8 +296,8 @@ def sv_apply_fused_gates(h, f, timings: bool = False):
     n = sv_fused_count(f)
     rec = (sv_timing * max(n, 1))()
     _check(lib.sv_apply_fused_gates(h, f, rec))
-    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "target_mask": rec[i].target_mask}
-            for i in range(n)]
+    return [{"us": rec[i].us, "k": rec[i].k, "path": rec[i].path, "flags": rec[i].flags,
+             "target_mask": rec[i].target_mask} for i in range(n)]
 
 
 # --------------------------------------------------------------------------------------- reductions

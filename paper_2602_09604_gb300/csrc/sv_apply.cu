@@ -953,6 +953,7 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
             timings[i].us = ms * 1000.f;
             timings[i].k = g.k;
             timings[i].path = (m > 0 && (*lazy)[i]) ? SV_PATH_AUTO : g.path;   // AUTO: ran on the small state
+            timings[i].flags = (first_reads_small && m < ng && i == order[m]) ? SV_TIMING_SMALL_SOURCE : 0;
             timings[i].target_mask = g.mask;
         }
         for (auto &xv : ev) cudaEventDestroy(xv);

@@ -21,8 +21,8 @@
 //     through per-warp shared-memory tiles), write the A operand into tensor memory, one thread
 //     issues the tcgen05.mma chain and commits it to an mbarrier, and the threads read the
 //     accumulator back (tcgen05.ld) and store the outputs in place;
-//   * the warp-specialised kernel (k = 6 without low targets, or one at qubit 3 or 4): loader
-//     warps, one MMA thread and epilogue warps connected by mbarriers, with A in a two-stage
+//   * the warp-specialised kernel (k = 6 with at most two targets below qubit 5): loader warps,
+//     one MMA thread and epilogue warps connected by mbarriers, with A in a two-stage
 //     shared-memory ring and four accumulators in tensor memory (see that kernel).
 // Every mbarrier wait is bounded: on time-out the kernel records an error code in a device word,
 // frees its tensor memory and returns.
@@ -42,14 +42,6 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;
 constexpr long long kWaitIters = 4000000;   // ~0.3 s with the backoff below
-// k = 6 gates with no target below qubit 5, or one at qubit 3 or 4, use the shared-memory-A
-// direct kernel (two accumulators per warpgroup, so the products overlap the previous tile's
-// stores): measured at n = 30 it beats the tensor-memory-A direct variant there (no low target
-// 5.80 vs 5.53 TB/s; one at qubit 3 or 4: 5.81-5.86 vs 5.46-5.47) but not with a low target at
-// qubits 0-2 (5.09 vs 5.32: its 192 KB of shared memory leaves little L1 for the sub-sector
-// accesses those need) or two low targets (5.23 vs 5.26 for qubits 3 and 4), nor for k = 5
-// (6.17-6.26 vs 6.53-6.56: four warpgroups per SM already overlap the products).
-constexpr bool kDirectSmemA = true;
 
 enum : int { kModeTF32 = 0, kModeBF16X3 = 1 };
 
@@ -206,13 +198,11 @@ struct TcShape {
     static constexpr int WG_COLS = NIMG * A_COLS + KD;                 // A image(s) + accumulator
     static constexpr int TMEM_COLS = 2 * WG_COLS < 32 ? 32 : 2 * WG_COLS;   // two warpgroups
     static constexpr int KSTEP = MODE == kModeTF32 ? 8 : 16;           // K per instruction
-    // direct kernel with A in shared memory: per warpgroup the A image(s) for M = 128 rows in the
-    // K-major no-swizzle core-matrix layout, two accumulators in tensor memory
+    // warp-specialised kernel: A image(s) of one M = 128 tile in shared memory, K-major no-swizzle
+    // core-matrix layout
     static constexpr int A_IMG_SMEM = kTcM * KD * ESZ;
     static constexpr int A_SMEM = NIMG * A_IMG_SMEM;
     static constexpr int LBO_A = (kTcM / 8) * 128;                     // next 16-byte K chunk of A
-    static constexpr int SMEM_DIRECT2 = B_BYTES + 2 * A_SMEM + 256;
-    static constexpr int TMEM_COLS_D2 = 4 * KD < 32 ? 32 : 4 * KD;     // 2 warpgroups x 2 accumulators
     // CTAs per SM the registers allow: the direct variant gains from more concurrent warpgroup
     // pipelines; the staged one needs more registers (its shared-memory traffic) and spills if capped
     static constexpr int MIN_BLOCKS_DIRECT = K == 6 ? 1 : (K == 5 ? 2 : 3);
@@ -618,233 +608,6 @@ __global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_D
     tc_kernel_body<K, MODE, false, true>(sv, a, v);
 }
 
-// Direct kernel, shared-memory A form (used for k = 6 with no target below qubit 5).  Like the direct
-// variant above, lane m of a warpgroup owns group 128 t + m of its tile t and moves its amplitudes
-// straight between registers and global memory, but the tile's A operand is written to shared
-// memory (16-byte stores in the K-major core-matrix layout) instead of tensor memory.  That frees
-// tensor memory for two accumulators per warpgroup, so the products of tile t run while the
-// warpgroup stores the results of tile t - 1:
-//   load(t+1) -> epilogue(t-1) from the other accumulator -> wait MMA(t) -> build A(t+1)
-//   -> MMA(t+1) into the accumulator epilogue(t-1) just emptied.
-template <int K, int MODE, bool VS>
-__device__ __forceinline__ void tc_direct_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
-{
-    using S = TcShape<K, MODE>;
-    constexpr int D = S::D;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x;
-    const int wg = tid >> 7;
-    const int warp = tid >> 5;
-    const int m = tid & 127;   // this thread's row in the warpgroup's tiles
-    unsigned char *sB = smem;
-    unsigned char *sA = smem + S::B_BYTES + wg * S::A_SMEM;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + S::B_BYTES + 2 * S::A_SMEM);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 5);
-    volatile int *status = reinterpret_cast<volatile int *>(tslot + 1);   // [0], [1]: per warpgroup
-    const uint32_t bar_b = smem_u32(&bars[0]);
-    const uint32_t bar_d0 = smem_u32(&bars[1 + 2 * wg]), bar_d1 = smem_u32(&bars[2 + 2 * wg]);
-
-    if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
-        status[0] = 0;
-        status[1] = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_proxy_async();
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"((uint32_t)S::TMEM_COLS_D2)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t t_lane = ((uint32_t)((warp & 3) * 32)) << 16;     // this warp's lane quarter
-    const uint32_t tD0 = tmem + (uint32_t)(wg * 2 * S::KD), tD1 = tD0 + (uint32_t)S::KD;   // the two accumulators
-
-    if (tid == 0) {   // B image: bulk copies of up to 32 KB, all completing on bar_b
-        mbar_arrive_expect_tx(bar_b, a.bbytes);
-        for (unsigned off = 0; off < a.bbytes; off += 32768u) {
-            const unsigned sz = a.bbytes - off < 32768u ? a.bbytes - off : 32768u;
-            bulk_g2s(smem_u32(sB + off), static_cast<const unsigned char *>(a.bimg) + off, sz, bar_b);
-        }
-    }
-    const uint32_t idesc = (1u << 4) | ((MODE == kModeTF32 ? 2u : 1u) << 7) | ((MODE == kModeTF32 ? 2u : 1u) << 10) |
-                           ((uint32_t)(S::KD >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-    // row m, 16-byte K chunk kc of image img: img * A_IMG_SMEM + kc * LBO_A + (m / 8) * 128 + (m % 8) * 16
-    const uint32_t a_base = smem_u32(sA);
-    const uint32_t a_row = a_base + (uint32_t)((m >> 3) * 128 + (m & 7) * 16);
-
-    float xd[2 * D];   // the row's inputs: real parts of amplitudes 0..D-1, then imaginary parts
-    long long fb_next = 0;
-    bool v_next = false;
-    auto load = [&](long long tile) {
-        const long long g = tile * kTcM + m;
-        v_next = g < a.n_groups;
-        fb_next = 0;
-        if (v_next) {
-            unsigned long long b = (unsigned long long)g;
-#pragma unroll
-            for (int i = 0; i < K; ++i) b = ins0(b, a.tpos[i]);
-            fb_next = (long long)(((b >> 5) << 6) | (b & 31ull));
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                if constexpr (VS) {
-                    unsigned long long ij = b;   // index of local amplitude j
-#pragma unroll
-                    for (int i = 0; i < K; ++i)
-                        if ((j >> i) & 1) ij |= 1ull << a.tpos[i];
-                    const bool in = (ij & v.mask) == v.rest;
-                    xd[j] = in ? v.src[fb_next + a.foff[j] - v.off] : 0.f;
-                    xd[D + j] = in ? v.src[fb_next + a.foff[j] + 32 - v.off] : 0.f;
-                } else {
-                    xd[j] = sv[fb_next + a.foff[j]];
-                    xd[D + j] = sv[fb_next + a.foff[j] + 32];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 2 * D; ++j) xd[j] = 0.f;
-        }
-    };
-    auto st16 = [](uint32_t addr, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w0), "r"(w1), "r"(w2), "r"(w3) : "memory");
-    };
-    auto build_a = [&]() {
-        if constexpr (MODE == kModeTF32) {
-#pragma unroll
-            for (int kc = 0; kc < S::KD / 4; ++kc)
-                st16(a_row + (uint32_t)(kc * S::LBO_A), f32_to_tf32(xd[4 * kc]), f32_to_tf32(xd[4 * kc + 1]),
-                     f32_to_tf32(xd[4 * kc + 2]), f32_to_tf32(xd[4 * kc + 3]));
-        } else {
-#pragma unroll
-            for (int kc = 0; kc < S::KD / 8; ++kc) {
-                uint32_t hi[4], lo[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float x0 = xd[8 * kc + 2 * q], x1 = xd[8 * kc + 2 * q + 1];
-                    hi[q] = pack_bf16x2(x0, x1);   // element 2q in the low half
-                    const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xffff0000u);
-                    lo[q] = pack_bf16x2(x0 - h0, x1 - h1);
-                }
-                st16(a_row + (uint32_t)(kc * S::LBO_A), hi[0], hi[1], hi[2], hi[3]);
-                st16(a_row + (uint32_t)(S::A_IMG_SMEM + kc * S::LBO_A), lo[0], lo[1], lo[2], lo[3]);
-            }
-        }
-        fence_proxy_async();   // these generic-proxy writes are read by the tensor core (async proxy)
-    };
-    auto issue = [&](int slot) {   // one thread per warpgroup
-        const uint32_t b0 = smem_u32(sB);
-        constexpr int NSTEP = S::KD / S::KSTEP;
-        constexpr int CH = S::KSTEP / S::EPC;           // 16-byte chunks per instruction (2)
-        if constexpr (MODE == kModeTF32) {
-#pragma unroll
-            for (int st = 0; st < NSTEP; ++st)
-                mma<MODE>(slot ? tD1 : tD0, sdesc(a_base + st * CH * S::LBO_A, S::LBO_A, 128), sdesc(b0 + st * CH * S::LBO_B, S::LBO_B, 128),
-                          idesc, st > 0);
-        } else {
-            const uint32_t a_img[3] = {a_base, a_base, a_base + (uint32_t)S::A_IMG_SMEM};   // hi, hi, lo
-            const uint32_t b_img[3] = {b0, b0 + (uint32_t)S::B_IMG, b0};                    // hi, lo, hi
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int st = 0; st < NSTEP; ++st)
-                    mma<MODE>(slot ? tD1 : tD0, sdesc(a_img[p] + st * CH * S::LBO_A, S::LBO_A, 128),
-                              sdesc(b_img[p] + st * CH * S::LBO_B, S::LBO_B, 128), idesc, (p > 0 || st > 0));
-        }
-        mma_commit(slot ? bar_d1 : bar_d0);
-    };
-    auto epilogue = [&](int slot, long long fb, bool valid) {
-        const uint32_t td = (slot ? tD1 : tD0) + t_lane;
-#pragma unroll
-        for (int cb = 0; cb < S::KD / 16; ++cb) {
-            float v[16];
-            tmem_ld16(td + cb * 16, v);
-            if (valid) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = cb * 16 + i;           // column (c', r): c' = col / D, r = col % D
-                    sv[fb + a.foff[col % D] + (col >= D ? 32 : 0)] = v[i];
-                }
-            }
-        }
-    };
-
-    const long long tstride = 2ll * gridDim.x;
-    long long tile = blockIdx.x + (long long)wg * gridDim.x;
-    const bool lead = m == 0;
-    uint32_t phase0 = 0u, phase1 = 0u;
-    int slot = 0;   // accumulator of the tile whose products are in flight
-    bool ok = true;
-    long long fb_cur = 0, fb_prev = 0;
-    bool v_cur = false, v_prev = false, have_prev = false;
-    if (tile < a.n_mma_tiles) {
-        load(tile);
-        fb_cur = fb_next;
-        v_cur = v_next;
-        build_a();
-        wg_sync(wg);
-        if (lead) {
-            tc_fence_after();
-            if (!mbar_wait_bounded(bar_b, 0)) status[wg] = 1;
-            else issue(0);
-        }
-        wg_sync(wg);
-        ok = status[wg] == 0;
-    }
-    while (ok && tile < a.n_mma_tiles) {
-        const long long nt = tile + tstride;
-        if (nt < a.n_mma_tiles) load(nt);                     // in flight during the epilogue and the wait
-        if (have_prev) epilogue(slot ^ 1, fb_prev, v_prev);   // overlaps the products of `tile`
-        if (lead && !mbar_wait_bounded(slot ? bar_d1 : bar_d0, slot ? phase1 : phase0)) status[wg] = 2;
-        tc_fence_before();
-        wg_sync(wg);
-        if (status[wg] != 0) { ok = false; break; }
-        if (slot) phase1 ^= 1u;
-        else phase0 ^= 1u;
-        tc_fence_after();
-        fb_prev = fb_cur;
-        v_prev = v_cur;
-        have_prev = true;
-        if (nt < a.n_mma_tiles) {
-            fb_cur = fb_next;
-            v_cur = v_next;
-            build_a();                                        // A is free: the products of `tile` are done
-            wg_sync(wg);
-            if (lead) {
-                tc_fence_after();
-                issue(slot ^ 1);                              // into the accumulator the epilogue emptied
-            }
-        }
-        slot ^= 1;
-        tile = nt;
-    }
-    if (ok && have_prev) epilogue(slot ^ 1, fb_prev, v_prev);
-    if (!ok && lead) atomicOr(a.err, status[wg] == 1 ? 0x10 : 0x20);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS_D2) : "memory");
-    }
-}
-
-template <int K, int MODE>
-__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
-    apply_tc_direct_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
-{
-    tc_direct_body<K, MODE, false>(sv, a, VsArgs{});
-}
-
-template <int K, int MODE>
-__global__ void __launch_bounds__(2 * kTcThreads, TcShape<K, MODE>::MIN_BLOCKS_DIRECT)
-    apply_tc_direct_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
-{
-    tc_direct_body<K, MODE, true>(sv, a, v);
-}
-
 // ------------------------------------------------------------------------ warp-specialised kernel
 // k = 6 gates on the direct (lane-per-group) access pattern, with the work split by role so that
 // loads are always in flight.  One persistent CTA per SM walks its MMA tiles i = 0, 1, ...
@@ -899,7 +662,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int MODE, bool VS, int LW, int EW>
+template <int MODE, bool VS, int LW, int EW, int WIN>
 __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
 {
     using S = TcShape<6, MODE>;
@@ -977,8 +740,8 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
         const int m = 32 * (warp & 3) + lane;
         const int j_lo = (warp >> 2) * AMPS;
         const uint32_t row_off = (uint32_t)((m >> 3) * 128 + (m & 7) * 16);
-        float xr[CH][16];
-        auto load_chunk = [&](bool valid, unsigned long long b, long long fb, int c) {
+        float xr[WIN][CH][16];   // WIN tiles' slices in flight
+        auto load_chunk = [&](float (&x)[CH][16], bool valid, unsigned long long b, long long fb, int c) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int j = j_lo + 8 * c + e;
@@ -986,11 +749,11 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                     const long long fo = a.foff[j];
                     const unsigned long long ij = b | ((unsigned long long)(fo >> 6) << 5) | (unsigned long long)(fo & 31);
                     const bool in = valid && (ij & v.mask) == v.rest;
-                    xr[c][e] = in ? v.src[fb + fo - v.off] : 0.f;
-                    xr[c][8 + e] = in ? v.src[fb + fo + 32 - v.off] : 0.f;
+                    x[c][e] = in ? v.src[fb + fo - v.off] : 0.f;
+                    x[c][8 + e] = in ? v.src[fb + fo + 32 - v.off] : 0.f;
                 } else {
-                    xr[c][e] = valid ? sv[fb + a.foff[j]] : 0.f;
-                    xr[c][8 + e] = valid ? sv[fb + a.foff[j] + 32] : 0.f;
+                    x[c][e] = valid ? sv[fb + a.foff[j]] : 0.f;
+                    x[c][8 + e] = valid ? sv[fb + a.foff[j] + 32] : 0.f;
                 }
             }
         };
@@ -999,7 +762,7 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
         };
         // chunk c of this lane's row into the A image(s) at stage base sa: element kk of the row is
         // the real part of amplitude kk (kk < 64) or the imaginary part of amplitude kk - 64
-        auto convert_chunk = [&](int c, uint32_t sa) {
+        auto convert_chunk = [&](const float (&x)[CH][16], int c, uint32_t sa) {
             const int j0 = j_lo + 8 * c;
 #pragma unroll
             for (int part = 0; part < 2; ++part) {   // real, imaginary
@@ -1007,15 +770,15 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
 #pragma unroll
                     for (int hf = 0; hf < 2; ++hf) {
                         const int kc = (64 * part + j0 + 4 * hf) / 4;
-                        const float *x = &xr[c][8 * part + 4 * hf];
-                        st16(sa + (uint32_t)(kc * S::LBO_A) + row_off, f32_to_tf32(x[0]), f32_to_tf32(x[1]),
-                             f32_to_tf32(x[2]), f32_to_tf32(x[3]));
+                        const float *xx = &x[c][8 * part + 4 * hf];
+                        st16(sa + (uint32_t)(kc * S::LBO_A) + row_off, f32_to_tf32(xx[0]), f32_to_tf32(xx[1]),
+                             f32_to_tf32(xx[2]), f32_to_tf32(xx[3]));
                     }
                 } else {
                     uint32_t hi[4], lo[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float x0 = xr[c][8 * part + 2 * q], x1 = xr[c][8 * part + 2 * q + 1];
+                        const float x0 = x[c][8 * part + 2 * q], x1 = x[c][8 * part + 2 * q + 1];
                         hi[q] = pack_bf16x2(x0, x1);   // element 2q in the low half
                         const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xffff0000u);
                         lo[q] = pack_bf16x2(x0 - h0, x1 - h1);
@@ -1029,24 +792,35 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
         unsigned long long b_n = 0;
         long long fb_n = 0;
         bool v_n = false;
-        if (cnt > 0) {
-            v_n = group_base(tile_of(0), m, b_n, fb_n);
 #pragma unroll
-            for (int c = 0; c < CH; ++c) load_chunk(v_n, b_n, fb_n, c);
-        }
-        for (long long i = 0; i < cnt; ++i) {
-            const int s = (int)(i % kWsStages);
-            const bool more = i + 1 < cnt;
-            if (more) v_n = group_base(tile_of(i + 1), m, b_n, fb_n);
-            if (i >= kWsStages && !wait(bar_aempty + 8 * s, (uint32_t)((i / kWsStages - 1) & 1), 0x40)) break;
-            const uint32_t sa = sA0 + (uint32_t)(s * W::A_STAGE);
+        for (int w = 0; w < WIN; ++w)   // the first WIN tiles' loads
+            if (w < cnt) {
+                v_n = group_base(tile_of(w), m, b_n, fb_n);
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                convert_chunk(c, sa);
-                if (more) load_chunk(v_n, b_n, fb_n, c);   // the next tile's chunk, in flight from here
+                for (int c = 0; c < CH; ++c) load_chunk(xr[w], v_n, b_n, fb_n, c);
             }
-            fence_proxy_async();   // generic-proxy stores -> read by the tensor core (async proxy)
-            mbar_arrive(bar_afull + 8 * s);
+        bool go = true;
+        for (long long i0 = 0; go && i0 < cnt; i0 += WIN) {
+#pragma unroll
+            for (int w = 0; w < WIN; ++w) {
+                const long long i = i0 + w;
+                if (!go || i >= cnt) break;
+                const int s = (int)(i % kWsStages);
+                const bool more = i + WIN < cnt;
+                if (more) v_n = group_base(tile_of(i + WIN), m, b_n, fb_n);
+                if (i >= kWsStages && !wait(bar_aempty + 8 * s, (uint32_t)((i / kWsStages - 1) & 1), 0x40)) {
+                    go = false;
+                    break;
+                }
+                const uint32_t sa = sA0 + (uint32_t)(s * W::A_STAGE);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    convert_chunk(xr[w], c, sa);
+                    if (more) load_chunk(xr[w], v_n, b_n, fb_n, c);   // tile i + WIN's chunk, in flight from here
+                }
+                fence_proxy_async();   // generic-proxy stores -> read by the tensor core (async proxy)
+                mbar_arrive(bar_afull + 8 * s);
+            }
         }
     } else if (warp < MMA_WARP) {
         // ------------------------------------------------------------------ epilogue
@@ -1135,21 +909,22 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
     }
 }
 
-constexpr int kWsLoadWarps = 8;
+constexpr int kWsLoadWarps = 16;
 constexpr int kWsEpiWarps = 4;
+constexpr int kWsWindow = 1;   // tiles whose loads each loader lane keeps in flight
 constexpr int kWsThreads = (kWsLoadWarps + kWsEpiWarps + 1) * 32;
 
 template <int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1) apply_tc_ws_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
-    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps>(sv, a, VsArgs{});
+    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps, kWsWindow>(sv, a, VsArgs{});
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1)
     apply_tc_ws_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
 {
-    tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps>(sv, a, v);
+    tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps, kWsWindow>(sv, a, v);
 }
 
 // ---------------------------------------------------------------------------------------- host
@@ -1251,23 +1026,20 @@ namespace {
 
 // Kernel form of a tensor-core gate, decided by its targets below qubit 5 (they lie inside a
 // 32-amplitude block).  One function decides for the launcher and for tc_gate_is_direct.
-//   1 (staged): three or more such targets -- the direct accesses would span >= 8 lines, so data
-//     moves through the per-warp shared-memory tiles (measured at n = 30 with three: direct
-//     2.3-3.9 vs staged 4.4-5.8 TB/s);
-//   2 (warp-specialised, k = 6): no such target, or one at qubit 3 or 4 (a warp access then covers
-//     whole 32-byte sectors of two lines);
-//   0 (direct, A in tensor memory): the rest -- one or two such targets, where the accesses need
-//     the L1 reuse that the warp-specialised kernel's 192 KB of shared memory would crowd out.
+//   1 (staged): three or more such targets -- lane-per-group accesses would span >= 8 lines, so
+//     data moves through the per-warp shared-memory tiles (measured at n = 30, k = 6: staged 4.47
+//     TB/s, warp-specialised 2.66, two-warpgroup direct 2.3-3.9);
+//   2 (warp-specialised, k = 6): at most two such targets (k = 6 at n = 30: no low target
+//     6.54-6.75 TB/s against 5.83-6.15 for the two-warpgroup kernel with A in shared memory; one
+//     at qubit 0: 6.51 vs 5.54; two: 6.00 vs 5.35);
+//   0 (two-warpgroup direct, A in tensor memory): k = 4 and 5 with at most two such targets
+//     (6.4-6.6 TB/s: four warpgroup pipelines per SM already hide the latency there).
 int tc_variant(const FusedGate &g)
 {
-    int nlow = 0, low_min = 32;
-    for (int b = 0; b < g.k; ++b) {
-        nlow += g.targets[b] < 5;
-        low_min = g.targets[b] < low_min ? g.targets[b] : low_min;
-    }
+    int nlow = 0;
+    for (int b = 0; b < g.k; ++b) nlow += g.targets[b] < 5;
     if (nlow >= 3) return 1;
-    if (g.k == 6 && (nlow == 0 || (nlow == 1 && low_min >= 3))) return 2;
-    return 0;
+    return g.k == 6 ? 2 : 0;
 }
 
 template <int K, int MODE>
