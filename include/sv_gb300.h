@@ -75,7 +75,13 @@ enum sv_precision {
 
 enum sv_fuse_mode {
     SV_FUSE_GREEDY = 0,   /* greedy fusion up to max_k qubits */
-    SV_FUSE_LEARNED = 1,  /* partition chosen by a learned cost model (see sv_mlp_*) */
+    SV_FUSE_LEARNED = 1,  /* partition chosen by a cost model (the learned sv_mlp, or a caller's cost
+                             function): candidates are greedy partitions at every max size 2..max_k
+                             under three rules for which blocks a gate closes, each improved by
+                             cost-guided merging (two blocks merge when their union has <= max_k
+                             qubits, one commutes past the blocks between them, and the merged gate
+                             is predicted 2% faster than the two); the candidate with the least
+                             predicted time wins, each fused gate on its cheapest predicted path */
     SV_FUSE_NONE = 2      /* no fusion: every input gate becomes its own dense gate (timing, baselines) */
 };
 
@@ -116,6 +122,13 @@ typedef struct sv_fuse_opts {
                            then runs that part on its small state; applied with
                            sv_apply_fused_gates the result is the same state, but may take more
                            passes than fusing without the split.  Greedy and learned modes. */
+    /* Learned mode with a caller's cost model instead of `model` (used when non-NULL): predicted
+     * microseconds of one fused gate of k qubits (targets ascending) run on kernel path `path` in an
+     * n-qubit state.  Called on the calling thread during sv_fuse_circuit, once per candidate fused
+     * gate and path; it must not call back into the library.  A negative or non-finite result makes
+     * sv_fuse_circuit fail with SV_EINVAL.  cost_ctx is passed through. */
+    double (*cost_us)(int k, const int *targets, int path, int n_qubits, void *cost_ctx);
+    void *cost_ctx;
 } sv_fuse_opts;
 
 /* Facts about one fused gate (introspection). */

@@ -37,10 +37,14 @@ class sv_gate(ctypes.Structure):
                 ("controls", ctypes.c_int * MAX_CONTROLS), ("mat", ctypes.POINTER(ctypes.c_double))]
 
 
+COST_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p)
+
+
 class sv_fuse_opts(ctypes.Structure):
     _fields_ = [("max_k", ctypes.c_int), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tc_min_k", ctypes.c_int), ("force_path", ctypes.c_int), ("model", ctypes.c_void_p),
-                ("start_qubits", ctypes.c_int)]
+                ("start_qubits", ctypes.c_int), ("cost_us", COST_FN), ("cost_ctx", ctypes.c_void_p)]
 
 
 class sv_fused_info(ctypes.Structure):
@@ -241,10 +245,13 @@ def gate_array(gates):
 
 
 def sv_fuse_circuit(gates, n: int, max_k: int = 4, mode: int = FUSE_GREEDY, precision: int = PREC_FP32,
-                    tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None, start_qubits: int = 0) -> ctypes.c_void_p:
+                    tc_min_k: int = 5, force_path: int = PATH_AUTO, model=None, start_qubits: int = 0,
+                    cost_fn=None) -> ctypes.c_void_p:
+    """cost_fn (learned mode, instead of a model): cost_fn(k, targets tuple, path, n) -> microseconds."""
     gl = list(gates)
     arr, keep = gate_array(gl)
-    opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model, start_qubits)
+    cb = COST_FN(lambda k, t, p, nq, ctx: float(cost_fn(k, tuple(t[i] for i in range(k)), p, nq))) if cost_fn else COST_FN()
+    opts = sv_fuse_opts(max_k, mode, precision, tc_min_k, force_path, model, start_qubits, cb, None)
     f = ctypes.c_void_p()
     _check(lib.sv_fuse_circuit(arr, len(gl), n, ctypes.byref(opts), ctypes.byref(f)))
     return f

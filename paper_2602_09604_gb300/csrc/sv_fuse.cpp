@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 
 #include "sv_internal.h"
 
@@ -268,8 +269,14 @@ constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above thi
 constexpr int kMaxControlledK = 3;          // targets of a gate kept controlled
 constexpr int kMaxStartQubits = 26;         // the small start state of sv_init_apply
 
+// Which touching blocks a gate that does not fit closes first (the greedy rule leaves this open;
+// the learned partitioner tries all three): kCloseOutside -- the most qubits outside the gate
+// (the library's default), kCloseOldest -- the least recently extended, kCloseLargest -- the most
+// qubits.
+enum CloseRule : int { kCloseOutside = 0, kCloseOldest = 1, kCloseLargest = 2, kCloseRules = 3 };
+
 // Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
-std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k)
+std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k, int rule = kCloseOutside)
 {
     std::vector<Block> open, emitted;
     long long stamp = 0;
@@ -311,8 +318,13 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
             return c;
         };
         std::sort(touching.begin(), touching.end(), [&](int a, int b) {
-            int oa = outside(a), ob = outside(b);
-            return oa != ob ? oa > ob : open[a].created < open[b].created;
+            if (rule == kCloseLargest && open[a].qubits.size() != open[b].qubits.size())
+                return open[a].qubits.size() > open[b].qubits.size();
+            if (rule == kCloseOutside) {
+                const int oa = outside(a), ob = outside(b);
+                if (oa != ob) return oa > ob;
+            }
+            return open[a].created < open[b].created;
         });
         auto union_size = [&](size_t from) {
             uint64_t m = qmask;
@@ -451,15 +463,218 @@ void split_light_cone(const std::vector<Dense> &dense, int m, std::vector<Dense>
     }
 }
 
-// greedy_partition of the circuit, or of its light-cone part followed by the rest's
+// greedy_partition of the circuit, or of its light-cone part followed by the rest's (*split_at:
+// the number of blocks of the first part, 0 without a split)
 std::vector<Block> partition(const std::vector<Dense> &dense, const std::vector<Dense> *first, const std::vector<Dense> *rest,
-                             int n_qubits, int max_k)
+                             int n_qubits, int max_k, int rule = kCloseOutside, size_t *split_at = nullptr)
 {
-    if (!first) return greedy_partition(dense, n_qubits, max_k);
-    std::vector<Block> a = greedy_partition(*first, n_qubits, max_k);
-    std::vector<Block> b = greedy_partition(*rest, n_qubits, max_k);
+    if (split_at) *split_at = 0;
+    if (!first) return greedy_partition(dense, n_qubits, max_k, rule);
+    std::vector<Block> a = greedy_partition(*first, n_qubits, max_k, rule);
+    if (split_at) *split_at = a.size();
+    std::vector<Block> b = greedy_partition(*rest, n_qubits, max_k, rule);
     for (Block &x : b) a.push_back(std::move(x));
     return a;
+}
+
+uint64_t block_mask(const Block &b)
+{
+    uint64_t m = b.cmask;
+    for (int q : b.qubits) m |= uint64_t(1) << q;
+    return m;
+}
+
+// Predicted device time of a fused gate by its qubit set: the cheapest kernel path it may take
+// (its CUDA-core path, and its tensor-core path when the precision allows one), from the trained
+// model or the caller's cost function.  Predictions are kept, so a qubit set is scored once.
+class GateCost {
+public:
+    GateCost(const sv_fuse_opts &o, int n) : o_(o), n_(n) {}
+
+    // scores every set in `masks` not scored yet (one batched model call)
+    int ensure(const std::vector<uint64_t> &masks)
+    {
+        std::vector<uint64_t> todo;
+        for (uint64_t m : masks)
+            if (!known_.count(m)) {
+                known_[m] = {0.0, SV_PATH_AUTO};
+                todo.push_back(m);
+            }
+        if (todo.empty()) return SV_OK;
+        std::vector<float> X;
+        std::vector<std::pair<size_t, int>> rows;   // (index into todo, path)
+        std::vector<std::array<int, SV_MAX_K>> tg(todo.size());
+        for (size_t t = 0; t < todo.size(); ++t) {
+            FusedGate g;
+            for (int q = 0; q < 64; ++q)
+                if ((todo[t] >> q) & 1) g.targets[g.k++] = q;
+            std::copy(g.targets, g.targets + SV_MAX_K, tg[t].begin());
+            std::vector<int> paths = {classify_path(g, n_, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO)};
+            if (o_.precision != SV_PREC_FP32 && g.k >= 4 && n_ >= g.k + 5)
+                paths.push_back(o_.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3);
+            for (int p : paths) {
+                rows.push_back({t, p});
+                if (!o_.cost_us) {
+                    float feat[16];
+                    mlp_features(g.k, g.targets, p, n_, feat);
+                    X.insert(X.end(), feat, feat + 16);
+                }
+            }
+        }
+        std::vector<double> us(rows.size());
+        if (o_.cost_us) {
+            for (size_t r = 0; r < rows.size(); ++r) {
+                const size_t t = rows[r].first;
+                us[r] = o_.cost_us(__builtin_popcountll(todo[t]), tg[t].data(), rows[r].second, n_, o_.cost_ctx);
+                if (!(us[r] >= 0.0) || !std::isfinite(us[r])) {
+                    set_error("sv_fuse_circuit: the cost function returned %g", us[r]);
+                    return SV_EINVAL;
+                }
+            }
+        } else {
+            SV_TRY(mlp_predict_us(const_cast<sv_mlp *>(o_.model), X.data(), (int)rows.size(), us.data()));
+        }
+        std::vector<char> seen(todo.size(), 0);
+        for (size_t r = 0; r < rows.size(); ++r) {
+            auto &k = known_[todo[rows[r].first]];
+            if (!seen[rows[r].first] || us[r] < k.first) k = {us[r], rows[r].second};
+            seen[rows[r].first] = 1;
+        }
+        return SV_OK;
+    }
+    double us(uint64_t m) const { return known_.at(m).first; }
+    int path(uint64_t m) const { return known_.at(m).second; }
+
+private:
+    const sv_fuse_opts &o_;
+    int n_;
+    std::unordered_map<uint64_t, std::pair<double, int>> known_;
+};
+
+// A candidate partition for the learned search: blocks in order, the light-cone part first.
+struct Candidate {
+    std::vector<Block> blocks;
+    size_t split_at = 0;   // blocks before this index are the light-cone part
+};
+
+// One merge of blocks i < j into a block over the union u, placed at pos (i: block j moves back
+// over the blocks between them; j: block i moves forward), predicted to save `gain` microseconds.
+struct Merge {
+    int i, j, pos;
+    uint64_t u;
+    double gain;
+};
+
+constexpr int kMergeWindow = 32;       // blocks apart at most
+constexpr double kMergeMargin = 0.02;  // a merge must save 2% of the two blocks' predicted time
+
+// Every merge allowed in c: the union has at most max_k qubits, neither block is controlled, both
+// lie in the same part, and one of them commutes with every block between them (no shared qubit).
+std::vector<Merge> merge_options(const Candidate &c, int max_k)
+{
+    std::vector<Merge> out;
+    const int nb = (int)c.blocks.size();
+    std::vector<uint64_t> m(nb);
+    for (int i = 0; i < nb; ++i) m[i] = block_mask(c.blocks[i]);
+    for (int i = 0; i < nb; ++i) {
+        if (c.blocks[i].cmask) continue;
+        uint64_t between = 0;   // union of the blocks strictly between i and j
+        for (int j = i + 1; j < nb && j <= i + kMergeWindow; ++j) {
+            if ((size_t)i < c.split_at && (size_t)j >= c.split_at) break;
+            if (!c.blocks[j].cmask) {
+                const uint64_t u = m[i] | m[j];
+                if (__builtin_popcountll(u) <= max_k) {
+                    if (!(between & m[j])) out.push_back(Merge{i, j, i, u, 0.0});
+                    else if (!(between & m[i])) out.push_back(Merge{i, j, j, u, 0.0});
+                }
+            }
+            between |= m[j];
+        }
+    }
+    return out;
+}
+
+// Applies the chosen merges (pairwise disjoint index ranges) to c.
+void apply_merges(Candidate &c, const std::vector<Merge> &ms, int n_qubits)
+{
+    const int nb = (int)c.blocks.size();
+    std::vector<int> at_pos(nb, -1), dropped(nb, 0);
+    for (size_t t = 0; t < ms.size(); ++t) {
+        at_pos[ms[t].pos] = (int)t;
+        dropped[ms[t].pos == ms[t].i ? ms[t].j : ms[t].i] = 1;
+    }
+    std::vector<Block> out;
+    out.reserve(nb);
+    size_t split = 0;
+    for (int b = 0; b < nb; ++b) {
+        if ((size_t)b == c.split_at) split = out.size();
+        if (dropped[b]) continue;
+        if (at_pos[b] < 0) {
+            out.push_back(std::move(c.blocks[b]));
+            continue;
+        }
+        const Merge &mg = ms[(size_t)at_pos[b]];
+        Block &a = c.blocks[mg.i];   // earlier in the circuit: its matrix acts first
+        Block &z = c.blocks[mg.j];
+        Block nbk;
+        for (int q = 0; q < n_qubits; ++q)
+            if ((mg.u >> q) & 1) nbk.qubits.push_back(q);
+        nbk.node = nbk.qubits == a.qubits ? std::move(a.node) : new_node(nbk.qubits, std::move(a.node));
+        nbk.node->ops.push_back(MatOp{{}, {}, std::move(z.node)});
+        nbk.n_src = a.n_src + z.n_src;
+        nbk.created = a.created;
+        out.push_back(std::move(nbk));
+    }
+    if (c.split_at >= (size_t)nb) split = out.size();
+    c.blocks.swap(out);
+    c.split_at = c.split_at == 0 ? 0 : split;
+}
+
+// Cost-guided merging of every candidate: rounds in which each candidate takes, largest predicted
+// saving first, merges whose index ranges do not overlap (a merge then cannot invalidate
+// another's commutation check), until no allowed merge is predicted to save time.
+int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, int max_k)
+{
+    for (int round = 0; round < 16; ++round) {
+        std::vector<std::vector<Merge>> opts(cands.size());
+        std::vector<uint64_t> need;
+        for (size_t c = 0; c < cands.size(); ++c) {
+            opts[c] = merge_options(cands[c], max_k);
+            for (const Merge &m : opts[c]) {
+                need.push_back(m.u);
+                need.push_back(block_mask(cands[c].blocks[m.i]));
+                need.push_back(block_mask(cands[c].blocks[m.j]));
+            }
+        }
+        SV_TRY(cost.ensure(need));
+        bool any = false;
+        for (size_t c = 0; c < cands.size(); ++c) {
+            std::vector<Merge> good;
+            for (Merge m : opts[c]) {
+                const double two = cost.us(block_mask(cands[c].blocks[m.i])) + cost.us(block_mask(cands[c].blocks[m.j]));
+                m.gain = two - cost.us(m.u);
+                if (m.gain > kMergeMargin * two) good.push_back(m);
+            }
+            std::sort(good.begin(), good.end(), [](const Merge &a, const Merge &b) {
+                return a.gain != b.gain ? a.gain > b.gain : (a.i != b.i ? a.i < b.i : a.j < b.j);
+            });
+            std::vector<char> used(cands[c].blocks.size(), 0);
+            std::vector<Merge> pick;
+            for (const Merge &m : good) {
+                bool free_range = true;
+                for (int b = m.i; b <= m.j && free_range; ++b) free_range = !used[(size_t)b];
+                if (!free_range) continue;
+                for (int b = m.i; b <= m.j; ++b) used[(size_t)b] = 1;
+                pick.push_back(m);
+            }
+            if (!pick.empty()) {
+                apply_merges(cands[c], pick, n_qubits);
+                any = true;
+            }
+        }
+        if (!any) break;
+    }
+    return SV_OK;
 }
 
 bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
@@ -658,70 +873,47 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 b.n_src = 1;
                 finish(b, -1);
             }
-        } else if (opts.mode == SV_FUSE_GREEDY || !mlp_usable(opts.model, kMaxTrustedError)) {
+        } else if (opts.mode == SV_FUSE_GREEDY || (!opts.cost_us && !mlp_usable(opts.model, kMaxTrustedError))) {
             const int k = opts.mode == SV_FUSE_GREEDY ? opts.max_k : (opts.model ? mlp_fallback_k(opts.model) : opts.max_k);
             std::vector<Block> blocks = partition(dense, split ? &first : nullptr, &rest, n_qubits, k);
             materialize(blocks, true);
             for (Block &b : blocks) finish(b, -1);
         } else {
-            // learned: every greedy partition up to max_k, every allowed kernel path per fused
-            // gate, scored by the cost model in one batched forward pass; keep the cheapest
-            std::vector<std::vector<Block>> cand;
+            // learned: candidate partitions -- greedy at every max size 2..max_k under each rule
+            // for which blocks a gate closes -- each improved by cost-guided merging, then scored
+            // by the predicted time of its fused gates (each on its cheapest path); the cheapest
+            // candidate wins
+            std::vector<Candidate> cand;
             {   // the candidate partitions are independent: build them on host threads
-                std::vector<std::future<std::vector<Block>>> jobs;
+                std::vector<std::future<Candidate>> jobs;
                 const std::vector<Dense> *fp = split ? &first : nullptr;
                 for (int k = 2; k <= std::max(2, opts.max_k); ++k)
-                    jobs.push_back(std::async(std::launch::async, [&dense, fp, &rest, n_qubits, k]() { return partition(dense, fp, &rest, n_qubits, k); }));
+                    for (int rule = 0; rule < kCloseRules; ++rule)
+                        jobs.push_back(std::async(std::launch::async, [&dense, fp, &rest, n_qubits, k, rule]() {
+                            Candidate c;
+                            c.blocks = partition(dense, fp, &rest, n_qubits, k, rule, &c.split_at);
+                            return c;
+                        }));
                 for (auto &j : jobs) cand.push_back(j.get());
             }
-            std::vector<float> X;
-            std::vector<int> row_path;
-            std::vector<std::vector<std::pair<int, int>>> rows_of;   // per candidate, per block: [first row, count)
-            for (auto &c : cand) {
-                rows_of.emplace_back();
-                for (Block &b : c) {
-                    if (b.cmask) {   // the same in every candidate: not scored
-                        rows_of.back().push_back({(int)row_path.size(), 0});
-                        continue;
-                    }
-                    FusedGate g;
-                    g.k = (int)b.qubits.size();
-                    for (int j = 0; j < g.k; ++j) g.targets[j] = b.qubits[j];
-                    std::vector<int> paths = {classify_path(g, n_qubits, SV_PREC_FP32, 7, SV_PATH_AUTO)};
-                    if (opts.precision != SV_PREC_FP32 && g.k >= 4 && n_qubits >= g.k + 5)
-                        paths.push_back(opts.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3);
-                    rows_of.back().push_back({(int)row_path.size(), (int)paths.size()});
-                    for (int p : paths) {
-                        float feat[16];
-                        mlp_features(g.k, g.targets, p, n_qubits, feat);
-                        X.insert(X.end(), feat, feat + 16);
-                        row_path.push_back(p);
-                    }
-                }
-            }
-            std::vector<double> us(row_path.size());
-            const int rc = mlp_predict_us(const_cast<sv_mlp *>(opts.model), X.data(), (int)row_path.size(), us.data());
+            GateCost cost(opts, n_qubits);
+            int rc = merge_search(cand, cost, n_qubits, std::max(2, opts.max_k));
+            std::vector<uint64_t> all;
+            for (const Candidate &c : cand)
+                for (const Block &b : c.blocks)
+                    if (!b.cmask) all.push_back(block_mask(b));
+            if (rc == SV_OK) rc = cost.ensure(all);
             if (rc != SV_OK) { delete f; return rc; }
             size_t best = 0;
             double best_t = 0.0;
-            std::vector<std::vector<int>> chosen(cand.size());
             for (size_t c = 0; c < cand.size(); ++c) {
                 double tot = 0.0;
-                for (auto &rr : rows_of[c]) {
-                    if (rr.second == 0) {
-                        chosen[c].push_back(SV_PATH_CONTROLLED);
-                        continue;
-                    }
-                    int bp = rr.first;
-                    for (int r = rr.first; r < rr.first + rr.second; ++r)
-                        if (us[size_t(r)] < us[size_t(bp)]) bp = r;
-                    tot += us[size_t(bp)];
-                    chosen[c].push_back(row_path[size_t(bp)]);
-                }
+                for (const Block &b : cand[c].blocks)
+                    if (!b.cmask) tot += cost.us(block_mask(b));   // kept controlled gates: the same in every candidate
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
             }
-            materialize(cand[best], true);
-            for (size_t i = 0; i < cand[best].size(); ++i) finish(cand[best][i], chosen[best][i]);
+            materialize(cand[best].blocks, true);
+            for (Block &b : cand[best].blocks) finish(b, b.cmask ? SV_PATH_CONTROLLED : cost.path(block_mask(b)));
         }
     } catch (const std::bad_alloc &) {
         delete f;

@@ -277,3 +277,88 @@ def test_no_fusion_mode_keeps_every_gate(B):
         assert np.max(np.abs(got - oracle.run_circuit(n, gates, 9))) < 1e-13
     finally:
         B.sv_fused_free(f)
+
+
+# ---------------------------------------------------------------------- learned partition search
+def _random_cost(seed):
+    """A deterministic but arbitrary cost per (k, targets, path): whatever candidate or merge the
+    search then prefers, the fused circuit must stay exact."""
+    def cost(k, targets, path, n):
+        h = hash((k, tuple(targets), path, n, seed)) & 0xFFFF
+        return 1.0 + h / 65536.0 * (1 + k)
+    return cost
+
+
+def _pass_cost(B):
+    """One unit per pass over the state; CUDA-core gates of 4+ qubits are arithmetic-bound (slower)."""
+    def cost(k, targets, path, n):
+        if path in (B.PATH_TC_BF16X3, B.PATH_TC_TF32):
+            return 1.0 + 0.4 * (sum(1 for t in targets if t < 5) >= 3)
+        return max(1.0, (8 * 2 ** k - 2) / 60.0)
+    return cost
+
+
+def _random_controlled_circuit(n, count, rng):
+    gates = []
+    for _ in range(count):
+        k = int(rng.integers(1, 3))
+        qs = [int(q) for q in rng.permutation(n)]
+        nc = 1 if rng.random() < 0.1 else 0
+        gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng), tuple(qs[k:k + nc])))
+    return gates
+
+
+@pytest.mark.parametrize("max_k,seed,start", [(3, 1, 0), (4, 2, 0), (5, 3, 6), (6, 4, 0), (6, 5, 8), (4, 6, 5)])
+def test_learned_search_is_exact(B, max_k, seed, start):
+    """The learned search (greedy candidates under every closing rule, then cost-guided merging)
+    with a caller's cost function: exact algebra whatever the costs prefer, with kept controlled
+    gates and with the light-cone split."""
+    rng = np.random.default_rng(seed)
+    n = 10
+    gates = _random_controlled_circuit(n, 70, rng)
+    for cost in (_random_cost(seed), _pass_cost(B)):
+        check_fusion(B, n, gates, max_k, init=3, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4,
+                     cost_fn=cost, start_qubits=start)
+
+
+def _fused_cost(B, f, n, cost):
+    tot = 0.0
+    for i in range(B.sv_fused_count(f)):
+        info = B.sv_fused_get_info(f, i)
+        if info["controls"]:
+            continue
+        tot += cost(info["k"], info["targets"], info["path"], n)
+    return tot
+
+
+@pytest.mark.parametrize("name", ["grid", "qft", "qv", "random"])
+def test_learned_search_is_never_worse_than_greedy(B, name):
+    """Scored by the same cost function, the learned partition costs no more than greedy fusion at
+    any max size (greedy partitions are among its candidates), and its kernel paths are the
+    cheapest the cost function allows."""
+    rng = np.random.default_rng(11)
+    n, gates = {"grid": (12, wl.random_grid_circuit(wl.Grid(3, 4), 8, seed=3)), "qft": (12, wl.qft_circuit(12)),
+                "qv": (12, wl.qv_circuit(12, seed=2)), "random": (12, _random_controlled_circuit(12, 120, rng))}[name]
+    cost = _pass_cost(B)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4, cost_fn=cost)
+    learned = _fused_cost(B, f, n, cost)
+    for i in range(B.sv_fused_count(f)):
+        info = B.sv_fused_get_info(f, i)
+        if info["controls"]:
+            continue
+        alt = [B.PATH_TC_BF16X3] if info["k"] >= 4 else []
+        assert cost(info["k"], info["targets"], info["path"], n) <= min(
+            [cost(info["k"], info["targets"], p, n) for p in alt] + [cost(info["k"], info["targets"], info["path"], n)])
+    B.sv_fused_free(f)
+    for k in range(2, 7):
+        g = B.sv_fuse_circuit(gates, n, max_k=k, precision=B.PREC_BF16X3, tc_min_k=4)
+        greedy = _fused_cost(B, g, n, lambda kk, t, p, nn: min(cost(kk, t, p, nn), cost(kk, t, B.PATH_TC_BF16X3, nn))
+                             if kk >= 4 else cost(kk, t, p, nn))
+        B.sv_fused_free(g)
+        assert learned <= greedy + 1e-9, (k, learned, greedy)
+
+
+def test_learned_search_rejects_a_bad_cost(B):
+    n, gates = 8, wl.qft_circuit(8)
+    with pytest.raises(B.SvError):
+        B.sv_fuse_circuit(gates, n, max_k=4, mode=B.FUSE_LEARNED, cost_fn=lambda k, t, p, nn: -1.0)
