@@ -134,6 +134,15 @@ def host_cores() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
+def kernel_class(B, info):
+    """Kernel path of a fused gate, with the tensor-core gates that stage through shared memory
+    (three or more targets below qubit 5) as their own class: they run a different kernel."""
+    name = B.PATH_NAMES[info["path"]]
+    if info["path"] in (B.PATH_TC_BF16X3, B.PATH_TC_TF32) and sum(1 for t in info["targets"] if t < 5) >= 3:
+        name += "_staged"
+    return name
+
+
 def device_state_metrics(ref_buf, buf, chunk_blocks=1 << 21):
     """Fidelity and l2 distance (fp64, on the device) between two states in the blocked layout:
     blocks of 32 real then 32 imaginary parts, fp32 or fp64 (complex64 or complex128 states)."""
@@ -343,10 +352,10 @@ def bench_ours(args):
                     lazy_gates += 1
                     continue
                 if r["flags"] & B.TIMING_SMALL_SOURCE:   # read only the small state: its own class
-                    key = (B.PATH_NAMES[info["path"]] + "_small_source", info["k"])
+                    key = (kernel_class(B, info) + "_small_source", info["k"])
                     small_source_us.append(r["us"])
                     continue
-                key = (B.PATH_NAMES[info["path"]], info["k"])
+                key = (kernel_class(B, info), info["k"])
                 kernel_us.setdefault(key, []).append(r["us"])
         ev1.record(stream)
         torch.cuda.synchronize()

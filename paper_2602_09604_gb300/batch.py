@@ -1,7 +1,8 @@
 """Batched uneven circuits in one persistent launch, with a project-written autotuner.
 
-The autotuner times the real batch on the GPU for candidate settings -- fusion size (2..4), the
-stage tile size (or one pass per fused gate) and the stage re-fusion size, CTA size, the largest
+The autotuner times the real batch on the GPU for candidate settings -- the circuits' fusion size
+(2..4, or none: then staged circuits are fused per stage and their diagonal +-1 gates become sign
+runs), the stage tile size (or one pass per fused gate) and the stage re-fusion size, CTA size, the largest
 circuit kept in shared memory, the smallest circuit split across CTAs, the per-gate tile size, the
 wave size (MB of split-circuit state per wave), and the persistent grid -- by coordinate descent
 from a default, each candidate replayed from its captured CUDA graph and timed with CUDA events
@@ -34,7 +35,9 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "batc
 
 
 class Batch:
-    """Device arena + fused circuits + sv_batch handle for one fusion size."""
+    """Device arena + fused circuits + sv_batch handle for one fusion size (max_k = 0: every gate
+    kept as it is, so staged circuits are fused per stage, with their diagonal +-1 gates -- CZ, Z --
+    applied as sign runs instead of dense matrices)."""
 
     def __init__(self, circuits, max_k: int, stream: torch.cuda.Stream | None = None):
         self.circuits = circuits
@@ -43,7 +46,8 @@ class Batch:
         self.stream = stream or torch.cuda.current_stream()
         self.nbytes = B.sv_batch_arena_bytes(self.ns)
         self.arena = torch.empty(self.nbytes // 4, dtype=torch.float32, device="cuda")
-        self.fused = [B.sv_fuse_circuit(g, n, max_k=max_k) for n, g in circuits]
+        self.fused = [B.sv_fuse_circuit(g, n, max_k=max_k) if max_k > 0 else
+                      B.sv_fuse_circuit(g, n, max_k=4, mode=B.FUSE_NONE) for n, g in circuits]
         self.h = B.sv_batch_create(self.fused, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
     def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0, stage_log2=0,
@@ -101,11 +105,11 @@ def apply(b: "Batch", cfg: dict, use_graph: bool = True) -> None:
     b.set(*(cfg[f] for f in FIELDS[:3]), use_graph, *(cfg[f] for f in FIELDS[3:]))
 
 
-def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(2, 3, 4), rounds=2):
+def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3, 4), rounds=2):
     """Returns (best settings dict, trial log).  Coordinate descent over the fusion size and every
     batch option, up to `rounds` sweeps (stopping early when a sweep changes nothing)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    key = f"v4|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
+    key = f"v5|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
     if use_cache and os.path.exists(cache):
         try:
             got = json.load(open(cache)).get(key)

@@ -71,7 +71,7 @@ struct CtrlArgs {
 };
 
 template <int K>
-__host__ __device__ constexpr int high_vec() { return K <= 2 ? 4 : (K == 3 ? 2 : 1); }
+__host__ __device__ constexpr int high_vec() { return K <= 2 ? 4 : (K <= 4 ? 2 : 1); }
 
 // Minimum resident CTAs per SM handed to __launch_bounds__: caps registers per thread so the
 // unrolled mat-vec cannot trade occupancy (memory parallelism) for scheduling freedom.
@@ -311,14 +311,16 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
 #pragma unroll
         for (int b = 0; b < K; ++b) base = (unsigned)insert_zero(base, a.t.ltpos[b]);
         const unsigned sg = a.t.gswz[(g >> a.t.lsh) & a.t.lmask];
+        // member j's float offset: the layout map moves index bits and the swizzle XORs in-block
+        // bits, both bitwise, and the base has zeros at the targets, so one XOR per member
+        const unsigned ob = ((base >> 5) << 6) | ((base & 31u) ^ sg);
         if constexpr (K <= 5) {
             float yr[D], yi[D];
 #pragma unroll
             for (int r = 0; r < D; ++r) { yr[r] = 0.f; yi[r] = 0.f; }
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned i = base + (unsigned)a.t.loff[j];
-                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
+                const unsigned o = ob ^ (unsigned)a.t.loffo[j];
                 const float xr = buf[o], xi = buf[o + 32];
 #pragma unroll
                 for (int r = 0; r < D; ++r) {
@@ -332,8 +334,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
             // Groups of different lanes are disjoint, so no lane synchronisation is needed here.
 #pragma unroll
             for (int r = 0; r < D; ++r) {
-                const unsigned i = base + (unsigned)a.t.loff[r];
-                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
+                const unsigned o = ob ^ (unsigned)a.t.loffo[r];
                 buf[o] = yr[r];
                 buf[o + 32] = yi[r];
             }
@@ -341,18 +342,16 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<K>()) apply_tile
             float xr[D][1], xi[D][1];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned i = base + (unsigned)a.t.loff[j];
-                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
+                const unsigned o = ob ^ (unsigned)a.t.loffo[j];
                 xr[j][0] = buf[o];
                 xi[j][0] = buf[o + 32];
             }
-            const unsigned obase = opaque(base);
+            const unsigned obo = opaque(ob);
 #pragma unroll 1
             for (int r = 0; r < D; ++r) {
                 float yr[1], yi[1];
                 row_smem<K, 1>(s_u, r, xr, xi, yr, yi);
-                const unsigned i = obase + (unsigned)a.t.loff[r];
-                const unsigned o = ((i >> 5) << 6) | ((i & 31u) ^ sg);
+                const unsigned o = obo ^ (unsigned)a.t.loffo[r];
                 buf[o] = yr[0];
                 buf[o + 32] = yi[0];
             }
@@ -578,6 +577,7 @@ int make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
         for (int b = 0; b < K; ++b)
             if ((j >> b) & 1) o |= 1 << m->ltpos[b];
         m->loff[j] = o;
+        m->loffo[j] = ((o >> 5) << 6) | (o & 31);
     }
     // swizzle: deposit the lowest L non-target tile-block bits onto the L low target positions
     int lowt[5], L = 0;

@@ -39,10 +39,22 @@ namespace {
 constexpr int kBatchMaxK = 4;
 constexpr int kBatchMaxN = 24;   // states up to 2^25 floats: 32-bit offsets
 
+// A fused gate of the batch.  Stage gates may carry a sign run: diagonal gates with entries +-1 on
+// one or two qubits (CZ, Z, ...) that come right before the gate and are applied to its inputs:
+// amplitude i is negated when gsign + popc(i & zmask) + sum_d popc(i & (i >> dist[d]) & dmask[d])
+// is odd (any +-1 diagonal on at most two qubits is such a quadratic form over GF(2)).  k = 0 is a
+// sign-only sweep (a run with no gate after it in its stage, or before a 4-qubit gate).
+constexpr int kSignDist = 4;   // distinct qubit distances of the pair terms of one run
+
 struct BGate {
     int k;
     int targets[SV_MAX_K];   // ascending
     int mat_off;             // in float2 units into the matrix table
+    int nd;                  // pair-term distances in use
+    unsigned gsign;          // 0 or 1
+    unsigned zmask;          // single-qubit terms
+    unsigned dmask[kSignDist];   // pair terms (a, a + dist[d]): bit a
+    int dist[kSignDist];
 };
 
 struct BCirc {
@@ -111,6 +123,36 @@ __device__ __forceinline__ void st_v(float *p, const float (&v)[V])
     else *p = v[0];
 }
 
+// The sign run of g at local index i: true when the amplitude is negated.
+__device__ __forceinline__ bool sign_odd(const BGate &g, unsigned i)
+{
+    unsigned p = g.gsign + (unsigned)__popc(i & g.zmask);
+#pragma unroll
+    for (int d = 0; d < kSignDist; ++d)
+        if (d < g.nd) p += (unsigned)__popc(i & (i >> g.dist[d]) & g.dmask[d]);
+    return (p & 1u) != 0u;
+}
+
+// A sign-only sweep over a 2^n-amplitude state in shared memory (four amplitudes per thread).
+__device__ void sign_sweep(float *S, int n, const BGate &g)
+{
+    const unsigned count = n >= 2 ? (1u << n) >> 2 : 1u;
+    for (unsigned q = threadIdx.x; q < count; q += blockDim.x) {
+        const unsigned i0 = q << 2;
+        const unsigned o = ((i0 >> 5) << 6) | (i0 & 31u);
+        float4 re = *reinterpret_cast<float4 *>(S + o), im = *reinterpret_cast<float4 *>(S + o + 32);
+        float *r = &re.x, *m = &im.x;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if ((n >= 2 || (unsigned)v < (1u << n)) && sign_odd(g, i0 + (unsigned)v)) {
+                r[v] = -r[v];
+                m[v] = -m[v];
+            }
+        *reinterpret_cast<float4 *>(S + o) = re;
+        *reinterpret_cast<float4 *>(S + o + 32) = im;
+    }
+}
+
 // Apply one fused gate of K qubits to groups [g_begin, g_end) of the state S (shared or global)
 // of n <= 24 qubits with all threads of the CTA; U (float2, row-major 2^K x 2^K) is in shared
 // memory.  A thread takes V consecutive groups at a time: with no target below log2(V) their
@@ -124,7 +166,7 @@ __device__ __forceinline__ void st_v(float *p, const float (&v)[V])
 // the 2^m: it holds x'[j] = x[j ^ s], forms y'[r] = sum_j U[r ^ s][j ^ s] x'[j] = y[r ^ s] and
 // stores it at the place of r ^ s.  The result is the same; the phase's accesses cover every bank
 // once.
-template <int K, int V, bool L2ONLY, bool XS>
+template <int K, int V, bool L2ONLY, bool XS, bool SG>
 __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict__ U, unsigned g_begin, unsigned g_end)
 {
     constexpr int D = 1 << K;
@@ -171,6 +213,20 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
             // L2ONLY: other CTAs wrote these, so read through L2 rather than a stale L1 line
             ld_v<V, L2ONLY>(S + o, xr[j]);
             ld_v<V, L2ONLY>(S + o + 32, xi[j]);
+            if constexpr (SG && K <= 3) {   // stage gates: the sign run before this gate, on its inputs
+                if (g.nd | g.zmask | g.gsign) {
+                    unsigned ij = base;   // index of member j (j ^ s in the XS order) of group v = 0
+#pragma unroll
+                    for (int b = 0; b < K; ++b)
+                        if ((j >> b) & 1) ij ^= bit[b];
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (sign_odd(g, ij + (unsigned)v)) {
+                            xr[j][v] = -xr[j][v];
+                            xi[j][v] = -xi[j][v];
+                        }
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
@@ -211,7 +267,7 @@ __device__ void apply_in_cta(float *S, const BGate &g, const float2 *__restrict_
 // 2^(n-K) groups.  WIDE (CTAs of at most 256 threads, up to 255 registers a thread) allows K = 4
 // with V > 1; with 512-thread CTAs (128 registers) K = 4 keeps V = 1, whose 2^5 inputs per group
 // already fill the budget.
-template <bool L2ONLY, bool WIDE, bool XS>
+template <bool L2ONLY, bool WIDE, bool XS, bool SG>
 __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U, unsigned g_begin, unsigned g_end)
 {
     const int t0 = g.targets[0];   // ascending
@@ -220,9 +276,9 @@ __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U,
     while (v > 1 && (1 << (n - g.k)) < v) v >>= 1;
 #define SV_BATCH_CASE(KK)                                                             \
     case KK:                                                                          \
-        if (v == 4) apply_in_cta<KK, 4, L2ONLY, XS>(S, g, U, g_begin, g_end);         \
-        else if (v == 2) apply_in_cta<KK, 2, L2ONLY, XS>(S, g, U, g_begin, g_end);    \
-        else apply_in_cta<KK, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);                \
+        if (v == 4) apply_in_cta<KK, 4, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);         \
+        else if (v == 2) apply_in_cta<KK, 2, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);    \
+        else apply_in_cta<KK, 1, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);                \
         break;
     switch (g.k) {
     SV_BATCH_CASE(1)
@@ -230,11 +286,11 @@ __device__ void apply_gate_cta(float *S, int n, const BGate &g, const float2 *U,
     SV_BATCH_CASE(3)
     default:
         if constexpr (WIDE) {
-            if (v == 4) apply_in_cta<4, 4, L2ONLY, XS>(S, g, U, g_begin, g_end);
-            else if (v == 2) apply_in_cta<4, 2, L2ONLY, XS>(S, g, U, g_begin, g_end);
-            else apply_in_cta<4, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);
+            if (v == 4) apply_in_cta<4, 4, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);
+            else if (v == 2) apply_in_cta<4, 2, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);
+            else apply_in_cta<4, 1, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);
         } else {
-            apply_in_cta<4, 1, L2ONLY, XS>(S, g, U, g_begin, g_end);
+            apply_in_cta<4, 1, L2ONLY, XS, SG>(S, g, U, g_begin, g_end);
         }
         break;
     }
@@ -387,8 +443,9 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                     __syncthreads();
                 }
                 for (int gi = 0; gi < ch.gate_count; ++gi) {
-                    const BGate g = sG[gi];
-                    apply_gate_cta<false, (MAXT <= 256), true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
+                    const BGate &g = sG[gi];   // read in place: the sign fields stay in shared memory
+                    if (g.k == 0) sign_sweep(sS, L, g);
+                    else apply_gate_cta<false, (MAXT <= 256), true, true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
                     __syncthreads();   // this gate's writes before the next gate's reads
                 }
             }
@@ -415,8 +472,8 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                 const BGate g = A.gates[C.gate_begin + gi];
                 stage_matrix(sU, A.mats, g);
                 __syncthreads();   // matrix staged; previous gate's writes visible
-                if (W.kind == kWhole) apply_gate_cta<false, (MAXT <= 256), true>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
-                else apply_gate_cta<false, (MAXT <= 256), false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                if (W.kind == kWhole) apply_gate_cta<false, (MAXT <= 256), true, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                else apply_gate_cta<false, (MAXT <= 256), false, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
                 __syncthreads();
             }
             if (W.kind == kWhole) {
@@ -444,7 +501,7 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
             const unsigned groups = 1u << (C.n - g.k);
             const unsigned g0 = (unsigned)W.tile << A.tile_log2;
             const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
-            apply_gate_cta<true, (MAXT <= 256), false>(G, C.n, g, sU, g0, g1);
+            apply_gate_cta<true, (MAXT <= 256), false, false>(G, C.n, g, sU, g0, g1);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -509,6 +566,81 @@ size_t smem_bytes(const sv_batch_opts &o)
 }
 
 constexpr int kStageMinN = 8;         // staged circuits have at least this many qubits
+
+// A diagonal gate with entries +-1 on one or two qubits, as its signs bit[x] (1 = -1) over the
+// local index x; false for any other gate.
+bool sign_pattern(const FusedGate &g, int (&bits)[4])
+{
+    if (g.cmask || g.k < 1 || g.k > 2) return false;
+    const int D = 1 << g.k;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const cplx u = g.mat[(size_t)(r * D + c)];
+            if (r != c) {
+                if (std::abs(u) > 1e-12) return false;
+            } else if (std::abs(u - 1.0) <= 1e-12) {
+                bits[r] = 0;
+            } else if (std::abs(u + 1.0) <= 1e-12) {
+                bits[r] = 1;
+            } else {
+                return false;
+            }
+        }
+    return true;
+}
+
+// Product of sign gates as a quadratic form over GF(2) in the local index bits (see BGate).
+struct SignRun {
+    unsigned gsign = 0, zmask = 0;
+    std::vector<std::pair<int, unsigned>> pairs;   // (distance, mask of the lower qubits)
+    bool empty() const
+    {
+        if (gsign || zmask) return false;
+        for (const auto &p : pairs)
+            if (p.second) return false;
+        return true;
+    }
+    template <typename Local>
+    bool fits(const FusedGate &g, Local local) const
+    {
+        if (g.k < 2) return true;
+        const int d = local(g.targets[1]) - local(g.targets[0]);
+        for (const auto &p : pairs)
+            if (p.first == d) return true;
+        return pairs.size() < (size_t)kSignDist;
+    }
+    // s(x) = s00 + (s00 ^ s10) x_a + (s00 ^ s01) x_b + (s00 ^ s10 ^ s01 ^ s11) x_a x_b over GF(2)
+    template <typename Local>
+    void add(const FusedGate &g, const int (&s)[4], Local local)
+    {
+        const int a = local(g.targets[0]);
+        gsign ^= (unsigned)s[0];
+        if (s[0] ^ s[1]) zmask ^= 1u << a;
+        if (g.k < 2) return;
+        const int b = local(g.targets[1]);
+        if (s[0] ^ s[2]) zmask ^= 1u << b;
+        if (s[0] ^ s[1] ^ s[2] ^ s[3]) {
+            for (auto &p : pairs)
+                if (p.first == b - a) {
+                    p.second ^= 1u << a;
+                    return;
+                }
+            pairs.push_back({b - a, 1u << a});
+        }
+    }
+    void fill(BGate &b) const
+    {
+        b.gsign = gsign;
+        b.zmask = zmask;
+        b.nd = 0;
+        for (const auto &p : pairs)
+            if (p.second) {
+                b.dist[b.nd] = p.first;
+                b.dmask[b.nd] = p.second;
+                ++b.nd;
+            }
+    }
+};
 constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
 
 // Cut circuit gates gs (global targets, n qubits) into stages of at most L local qubits and append
@@ -541,12 +673,12 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         BStage bs{};
         bs.lmask = S;
         bs.chunk_begin = (int)chunks.size();
-        std::vector<FusedGate> fused;
-        if (stage_k > 0) fused = refuse_gates(taken, n, stage_k);
+        auto local = [&](int q) { return __builtin_popcount(S & ((1u << q) - 1u)); };
         // per gate: U then its pair-swapped copy U' (U'[r][j] = U[r][j ^ 1]), starting at an even
-        // offset of the chunk (16-byte aligned in shared memory)
-        auto emit = [&](const FusedGate &g) {
-            const int dd = (int)g.ur.size();
+        // offset of the chunk (16-byte aligned in shared memory); a sign run rides on the gate
+        // (k = 0: a sign-only sweep)
+        auto emit = [&](const FusedGate *g, const SignRun &run) {
+            const int dd = g ? (int)g->ur.size() : 0;
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
                 chunks.back().mat_count + 1 + 2 * dd > kStageMatCap)
                 chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
@@ -555,20 +687,55 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
                 chunks.back().mat_count += 1;
             }
             BGate b{};
-            b.k = g.k;
-            for (int j = 0; j < g.k; ++j) b.targets[j] = __builtin_popcount(S & ((1u << g.targets[j]) - 1u));
+            run.fill(b);
             b.mat_off = (int)sm.size();
-            for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g.ur[(size_t)e], g.ui[(size_t)e]));
-            for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g.ur[(size_t)(e ^ 1)], g.ui[(size_t)(e ^ 1)]));
+            if (g) {
+                b.k = g->k;
+                for (int j = 0; j < g->k; ++j) b.targets[j] = local(g->targets[j]);
+                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)e], g->ui[(size_t)e]));
+                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)(e ^ 1)], g->ui[(size_t)(e ^ 1)]));
+            }
             sg.push_back(b);
             chunks.back().gate_count += 1;
             chunks.back().mat_count += 2 * dd;
         };
-        if (stage_k > 0) {
-            for (const FusedGate &g : fused) emit(g);
-        } else {
-            for (const FusedGate *g : taken) emit(*g);
+        // The stage's gates in order: dense gates collect in a run that is re-fused (stage_k) when
+        // it ends; diagonal +-1 gates on at most two qubits collect in a sign run that is applied to
+        // the inputs of the first gate emitted after it.  A sign gate that shares a qubit with the
+        // dense run ends that run first (the sign run so far, which precedes the dense run, rides on
+        // the run's first gate); one that does not commutes past the dense run into the sign run.
+        SignRun run;
+        std::vector<const FusedGate *> dense_run;
+        uint64_t dense_q = 0;
+        auto flush = [&]() {
+            if (!dense_run.empty()) {
+                std::vector<FusedGate> fused;
+                if (stage_k > 0) fused = refuse_gates(dense_run, n, stage_k);
+                for (size_t i = 0; i < (stage_k > 0 ? fused.size() : dense_run.size()); ++i) {
+                    const FusedGate *g = stage_k > 0 ? &fused[i] : dense_run[i];
+                    // the kernel applies a run on the inputs of gates of up to three qubits (a
+                    // 4-qubit gate's 16 inputs leave no registers for it): else a sweep of its own
+                    if (i == 0 && g->k > 3 && !run.empty()) emit(nullptr, run);
+                    emit(g, i == 0 && g->k <= 3 ? run : SignRun{});
+                }
+            } else if (!run.empty()) {
+                emit(nullptr, run);
+            }
+            run = SignRun{};
+            dense_run.clear();
+            dense_q = 0;
+        };
+        for (const FusedGate *g : taken) {
+            int sg_bits[4];
+            if (sign_pattern(*g, sg_bits)) {
+                if ((g->mask & dense_q) || !run.fits(*g, local)) flush();
+                run.add(*g, sg_bits, local);
+            } else {
+                dense_run.push_back(g);
+                dense_q |= g->mask;
+            }
         }
+        flush();
         bs.chunk_count = (int)chunks.size() - bs.chunk_begin;
         st.push_back(bs);
         rest.swap(left);

@@ -567,6 +567,8 @@ struct Merge {
 
 constexpr int kMergeWindow = 32;       // blocks apart at most
 constexpr double kMergeMargin = 0.02;  // a merge must save 2% of the two blocks' predicted time
+constexpr double kMergeWithin = 0.15;  // candidates within 15% of the best predicted time are merged
+constexpr int kMergeRounds = 6;
 
 // Every merge allowed in c: the union has at most max_k qubits, neither block is controlled, both
 // lie in the same part, and one of them commutes with every block between them (no shared qubit).
@@ -635,7 +637,7 @@ void apply_merges(Candidate &c, const std::vector<Merge> &ms, int n_qubits)
 // another's commutation check), until no allowed merge is predicted to save time.
 int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, int max_k)
 {
-    for (int round = 0; round < 16; ++round) {
+    for (int round = 0; round < kMergeRounds; ++round) {
         std::vector<std::vector<Merge>> opts(cands.size());
         std::vector<uint64_t> need;
         for (size_t c = 0; c < cands.size(); ++c) {
@@ -896,20 +898,52 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                         }));
                 for (auto &j : jobs) cand.push_back(j.get());
             }
+            // identical partitions (different rules often agree) are scored once
+            {
+                std::vector<Candidate> uniq;
+                std::vector<std::vector<uint64_t>> seen;
+                for (Candidate &c : cand) {
+                    std::vector<uint64_t> key;
+                    for (const Block &b : c.blocks) key.push_back(block_mask(b));
+                    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+                    seen.push_back(std::move(key));
+                    uniq.push_back(std::move(c));
+                }
+                cand.swap(uniq);
+            }
             GateCost cost(opts, n_qubits);
-            int rc = merge_search(cand, cost, n_qubits, std::max(2, opts.max_k));
-            std::vector<uint64_t> all;
-            for (const Candidate &c : cand)
+            auto total = [&](const Candidate &c) {
+                double tot = 0.0;
                 for (const Block &b : c.blocks)
-                    if (!b.cmask) all.push_back(block_mask(b));
-            if (rc == SV_OK) rc = cost.ensure(all);
+                    if (!b.cmask) tot += cost.us(block_mask(b));   // kept controlled gates: the same in every candidate
+                return tot;
+            };
+            auto score_all = [&]() -> int {
+                std::vector<uint64_t> all;
+                for (const Candidate &c : cand)
+                    for (const Block &b : c.blocks)
+                        if (!b.cmask) all.push_back(block_mask(b));
+                return cost.ensure(all);
+            };
+            int rc = score_all();
+            if (rc == SV_OK) {
+                // merging searches the candidates within kMergeWithin of the best one as it stands
+                // (a merge saves at most one gate's time, so far worse partitions cannot catch up)
+                double best0 = 0.0;
+                for (size_t c = 0; c < cand.size(); ++c) best0 = c == 0 ? total(cand[c]) : std::min(best0, total(cand[c]));
+                std::vector<Candidate> near, far;
+                for (Candidate &c : cand) (total(c) <= (1.0 + kMergeWithin) * best0 ? near : far).push_back(std::move(c));
+                rc = merge_search(near, cost, n_qubits, std::max(2, opts.max_k));
+                cand.clear();
+                for (Candidate &c : near) cand.push_back(std::move(c));
+                for (Candidate &c : far) cand.push_back(std::move(c));
+            }
+            if (rc == SV_OK) rc = score_all();
             if (rc != SV_OK) { delete f; return rc; }
             size_t best = 0;
             double best_t = 0.0;
             for (size_t c = 0; c < cand.size(); ++c) {
-                double tot = 0.0;
-                for (const Block &b : cand[c].blocks)
-                    if (!b.cmask) tot += cost.us(block_mask(b));   // kept controlled gates: the same in every candidate
+                const double tot = total(cand[c]);
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
             }
             materialize(cand[best].blocks, true);

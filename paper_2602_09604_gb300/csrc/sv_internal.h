@@ -67,6 +67,8 @@ struct TileMap {
     long long fblk[1 << kMaxTileF];   // block offset of tile block phi (deposit of phi into the F bits)
     int fpos[kMaxTileF];              // ascending block-bit positions of F
     int loff[64];             // tile-local amplitude offset of local index j
+    int loffo[64];            // the same in the blocked layout's float offsets: a group's member j sits at
+                              // float offset (group base's offset, swizzled) ^ loffo[j] (disjoint bits)
     int ltpos[6];             // ascending tile-local target positions
     int f;                    // a tile is 2^f blocks
     int lsh;                  // 5 - (number of targets below 5)

@@ -337,9 +337,8 @@ __device__ __forceinline__ void tc_kernel_body(float *__restrict__ sv, const TcA
     const unsigned gsw = a.t.gswz[(lane >> a.t.lsh) & a.t.lmask];
     // shared-memory float offset of the group's real part j (gb: gbase through an opaque move,
     // so the offsets are recomputed per use rather than held in registers across the tile loop)
-    auto spos = [&](unsigned gb, int j) -> unsigned {
-        const unsigned i = gb + (unsigned)a.t.loff[j];
-        return ((i >> 5) << 6) | ((i & 31u) ^ gsw);
+    auto spos = [&](unsigned gb, int j) -> unsigned {   // bitwise maps on disjoint bits: one XOR
+        return (((gb >> 5) << 6) | ((gb & 31u) ^ gsw)) ^ (unsigned)a.t.loffo[j];
     };
     auto tile_block0 = [&](long long wt) -> unsigned long long {
         unsigned long long b0 = (unsigned long long)wt;

@@ -90,6 +90,59 @@ def test_staged_batch_matches_oracle(env):
         b.free()
 
 
+_SIGN_DIAGS = [np.diag([1, 1, 1, -1]), np.diag([1, -1, -1, 1]), np.diag([-1, 1, 1, 1]), np.diag([1, -1, 1, 1]),
+               np.diag([1, -1]), np.diag([-1, 1]), np.diag([-1, -1])]
+
+
+def _sign_circuit(n, count, rng):
+    """Dense one- and two-qubit gates mixed with +-1 diagonals on one or two qubits at every
+    distance (CZ, ZZ, -|00><00|-style, Z, -Z, -I), so stages carry sign runs with pair terms of up
+    to several distances, linear terms, global signs, and runs with no gate after them."""
+    gates = []
+    for _ in range(count):
+        r = rng.random()
+        if r < 0.45:
+            d = _SIGN_DIAGS[int(rng.integers(0, len(_SIGN_DIAGS)))].astype(np.complex128)
+            k = 1 if d.shape[0] == 2 else 2
+            t = tuple(int(q) for q in rng.choice(n, size=k, replace=False))
+            gates.append(wl.Gate(t, d))
+        else:
+            k = int(rng.integers(1, 3))
+            t = tuple(int(q) for q in rng.choice(n, size=k, replace=False))
+            gates.append(wl.Gate(t, wl.random_unitary(1 << k, rng)))
+    gates += [wl.Gate((q, (q + 3) % n), np.diag([1, 1, 1, -1]).astype(np.complex128)) for q in range(n)]
+    return gates
+
+
+def test_sign_runs_match_oracle(env):
+    """Circuits kept unfused (fusion size 0), so each stage re-fuses its dense gates and applies
+    its +-1 diagonals as sign runs on the inputs of the next gate (or as a sweep of their own):
+    HEA circuits (CZ ladders) and circuits dense in sign gates, at every stage tile size,
+    re-fusion size and CTA size, against the oracle."""
+    B, batch = env
+    rng = np.random.default_rng(31)
+    circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [16, 9, 14, 12, 11]]
+    circuits += [(int(n), _sign_circuit(int(n), c, rng)) for n, c in [(13, 150), (16, 80), (10, 200), (8, 60)]]
+    refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
+    # (threads, smem_max_n, ctas, split_min_n, stage_log2, stage_k)
+    configs = [(256, 0, 7, 1, 8, 0), (512, 0, 152, 8, 14, 4), (256, 0, 19, 8, 11, 2), (128, 0, 40, 8, 10, 3),
+               (512, 0, 304, 1, 13, 3), (256, 0, 1, 8, 12, 1)]
+    b = batch.Batch(circuits, 0)
+    for threads, smem_n, ctas, split_n, sl, sk in configs:
+        b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk)
+        info = B.sv_batch_get_info(b.h)
+        assert info["staged"] == len(circuits), info
+        b.arena.fill_(float("nan"))
+        b.run()
+        B.sv_device_status()
+        for i, ref in enumerate(refs):
+            got = b.state(i)
+            cfg = (threads, ctas, sl, sk, i)
+            assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
+            assert oracle.l2_error(ref, got) <= 1e-4, cfg
+    b.free()
+
+
 def test_staging_cuts_traffic_and_waves_keep_results(env):
     """Stages move fewer bytes than one pass per fused gate; waves and a direct launch give the
     same states as the graph replay."""
