@@ -1,9 +1,9 @@
 """Benchmark: one 30-qubit random grid circuit per step on the GB300 fused-gate path.
 
 A step is one pass of the hot path over one circuit: set |0...0> and apply every fused gate
-(sv_init_apply: the first gates, while they name at most 26 qubits, run on the small state of
+(sv_init_apply: the first gates, while they name at most 28 qubits, run on the small state of
 those qubits, which is then written into the full state; the fusion places the gates of the
-circuit's 26-qubit light cone first for it (--start-qubits); --start plain uses sv_init then
+circuit's 28-qubit light cone first for it (--start-qubits); --start plain uses sv_init then
 sv_apply_fused_gates on the circuit fused as one, and the line reports the other start's time
 too), then one read pass that
 yields the fp64 norm and 1024 samples (sv_sample_norm).  The circuit is the 5x6-grid random circuit (20 cycles of
@@ -587,7 +587,7 @@ def main():
     ap.add_argument("--no-next-rows", action="store_true")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 33-qubit grid, 34-qubit QFT and HEA batch comparisons (run after the timed step)")
-    ap.add_argument("--start-qubits", type=int, default=26,
+    ap.add_argument("--start-qubits", type=int, default=28,
                     help="light cone fused apart for the lazy start (0 = fuse the circuit as one)")
     ap.add_argument("--start", choices=["lazy", "plain"], default="lazy",
                     help="lazy: sv_init_apply (first gates on the small state of the qubits they name); "

@@ -113,7 +113,7 @@ typedef struct sv_fuse_opts {
     int force_path;     /* enum sv_path; SV_PATH_AUTO lets the library choose (testing knob) */
     const sv_mlp *model;/* learned mode: trained cost model; NULL, untrained or a validation error
                            above 25% => greedy fusion at max_k (model's fallback k when present) */
-    int start_qubits;   /* 0 (default): fuse the circuit as one.  m in 1..26: the circuit will start
+    int start_qubits;   /* 0 (default): fuse the circuit as one.  m in 1..28: the circuit will start
                            from a basis state through sv_init_apply, so the gates of its light cone
                            on m qubits (min(m, n - 1)) are fused apart and placed first: in circuit
                            order, a qubit set S grows with each gate's qubits (targets and controls)
@@ -397,9 +397,9 @@ SV_API int sv_batch_inject_stall(sv_batch *b, int on);
 /* sv_init(st, basis_index) then sv_apply_fused_gates(st, f, timings), with the same result up to
  * rounding order, computed with less memory traffic.  One pass over the fused gates picks those
  * that share no qubit with an earlier gate left out (so they commute past it) while the qubits they
- * name, targets and controls, number at most 26 and fewer than n; every other qubit still holds its
+ * name, targets and controls, number at most 28 and fewer than n; every other qubit still holds its
  * bit of basis_index, so the picked gates run first, in order, on the small state of the named
- * qubits (in a library-owned buffer of up to 512 MB grown on first use; tensor-core gates stay on
+ * qubits (in a library-owned buffer of up to 2 GiB grown on first use; tensor-core gates stay on
  * the tensor cores when the small state has at least k + 5 qubits, the others run on CUDA cores), which
  * one kernel then writes into the zeroed full state; the rest run, in order, as in
  * sv_apply_fused_gates.  Timing records stay in circuit order.  Complex128 states take the plain

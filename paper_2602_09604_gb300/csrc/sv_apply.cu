@@ -750,7 +750,7 @@ namespace {
 // kCompactMaxQubits qubits A, every other qubit still holds its bit of x, so the state is
 // |x on the rest> (x) |small state on A>; those gates run on the 2^|A| small state, which one
 // kernel then writes into the zeroed full state.
-constexpr int kCompactMaxQubits = 26;
+constexpr int kCompactMaxQubits = 28;   // a 2 GiB small state
 
 struct ExpandArgs {
     int pos[kCompactMaxQubits];   // ascending qubits of A: small-state bit b -> full-state bit pos[b]

@@ -267,7 +267,7 @@ Block controlled_block(const Dense &d)
 
 constexpr double kMaxTrustedError = 0.25;   // learned mode falls back above this validation error
 constexpr int kMaxControlledK = 3;          // targets of a gate kept controlled
-constexpr int kMaxStartQubits = 26;         // the small start state of sv_init_apply
+constexpr int kMaxStartQubits = 28;         // the small start state of sv_init_apply
 
 // Which touching blocks a gate that does not fit closes first (the greedy rule leaves this open;
 // the learned partitioner tries all three): kCloseOutside -- the most qubits outside the gate
@@ -832,7 +832,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
         dense[gi].m = std::move(M);
     }
 
-    // light-cone split for a start from a basis state (at most 26 qubits and fewer than n: the
+    // light-cone split for a start from a basis state (at most 28 qubits and fewer than n: the
     // small state sv_init_apply runs them on)
     const int start_m = std::min(opts.start_qubits, std::min(kMaxStartQubits, n_qubits - 1));
     const bool split = opts.start_qubits > 0 && start_m > 0 && opts.mode != SV_FUSE_NONE;

@@ -1,5 +1,5 @@
 """The benchmark configuration itself at full size (30-qubit 5x6 grid, 20 cycles, 845 gates,
-learned fusion with the 26-qubit light cone fused apart, started through sv_init_apply, 3xBF16
+learned fusion with the 28-qubit light cone fused apart, started through sv_init_apply, 3xBF16
 tensor cores: the launch configuration bench.py times), checked by
 properties that hold at any size: the circuit followed by its inverse returns |0...0>, the norm
 stays 1, and the state agrees with the independent fp32 CUDA-core path (greedy K = 4, no tensor
@@ -35,8 +35,8 @@ def test_bench_configuration_full_size(B):
     kw = dict(max_k=6, precision=B.PREC_BF16X3, tc_min_k=4,
               mode=B.FUSE_LEARNED if model is not None else B.FUSE_GREEDY, model=model)
     st = DeviceState(n)
-    # bench path: the 26-qubit light cone fused apart, started from |0...0> through sv_init_apply
-    f = B.sv_fuse_circuit(gates, n, **kw, start_qubits=26)
+    # bench path: the 28-qubit light cone fused apart, started from |0...0> through sv_init_apply
+    f = B.sv_fuse_circuit(gates, n, **kw, start_qubits=28)
     B.sv_init_apply(st.h, 0, f, False)
     B.sv_device_status()
     assert abs(st.norm() - 1.0) <= 1e-4

@@ -70,7 +70,7 @@ def test_grover_from_basis(B):
     assert np.max(np.abs(np.delete(got, marked) - b)) <= 2e-6
 
 
-@pytest.mark.parametrize("n,m,max_k,prec", [(12, 8, 4, 0), (20, 14, 3, 0), (26, 24, 6, 2), (27, 26, 5, 2)])
+@pytest.mark.parametrize("n,m,max_k,prec", [(12, 8, 4, 0), (20, 14, 3, 0), (26, 24, 6, 2), (27, 26, 5, 2), (28, 27, 6, 2)])
 def test_light_cone_fusion(B, n, m, max_k, prec):
     """Fusion with the light cone on m qubits fused apart: sv_init_apply runs at least that part on
     its small state, and the state is the oracle's."""
@@ -142,7 +142,7 @@ def test_bench_circuit_matches_plain_route(B):
     import torch
     from paper_2602_09604_gb300.state import DeviceState
     n, gates = wl.circuit_30q_grid()
-    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4, start_qubits=26)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, precision=B.PREC_BF16X3, tc_min_k=4, start_qubits=28)
     st = DeviceState(n)
     B.sv_init_apply(st.h, 0, f, False)
     lazy = st.buf.clone()

@@ -139,9 +139,12 @@ def test_untrusted_model_falls_back_to_greedy(B):
 
 
 @pytest.mark.skipif(not os.path.exists(MODEL), reason="trained GB300 cost model not present")
-def test_learned_fusion_gain_28q(B):
+def test_learned_fusion_against_fixed_28q(B):
     """The trained model's partition against fixed greedy fusion on the same GPU, same accuracy
-    class (3xBF16 tensor cores meet the fidelity bar), 28-qubit grid circuit."""
+    class (3xBF16 tensor cores meet the fidelity bar), 28-qubit grid circuit.  Without timing any
+    candidate, the model's choice must be within 3% of the best of the five fixed sizes (each of
+    which a sweep would have to run) and well ahead of the plain method (fixed size 4 on CUDA
+    cores, the paper's setting); the measured times are reported."""
     m = B.sv_mlp_load(MODEL)
     n, gates = wl.GRID_28.n, wl.random_grid_circuit(wl.GRID_28, 20, seed=3)
 
@@ -160,5 +163,5 @@ def test_learned_fusion_gain_28q(B):
             json.dump(report, fh, indent=1)
     print(json.dumps(report))
     assert learned < 0.8 * plain
-    assert learned <= 1.1 * min(fixed.values())
+    assert learned <= 1.03 * min(fixed.values()), (learned, fixed)
     B.sv_mlp_free(m)

@@ -4,7 +4,7 @@
   CUDA cores and 3xBF16 tensor cores must meet F >= 1 - 1e-6 and ||psi - psi_ref||_2 <= 1e-4;
   TF32 is the fast, lower-precision mode and is reported (its per-gate error is ~3e-4).
 * 28 qubits, the exact launch configuration the benchmark times (learned fusion with the light
-  cone on n - 4 qubits fused apart, started from |0...0> through sv_init_apply, 3xBF16 tensor cores
+  cone on n - 2 qubits fused apart, started from |0...0> through sv_init_apply, 3xBF16 tensor cores
   for fused gates of 4 or more qubits), element by element against the oracle.
 * 32 qubits (4x8 grid, seed 6; a 32 GiB complex64 state): the same modes and sizes against the
   library's complex128 state (64 GiB, fp64 arithmetic; it matches the oracle to 1e-12 wherever
@@ -90,7 +90,7 @@ def test_bench_path_28q_vs_oracle(B, grid28):
     model = B.sv_mlp_load(MODEL) if os.path.exists(MODEL) else None
     kw = dict(max_k=6, precision=B.PREC_BF16X3, tc_min_k=4,
               mode=B.FUSE_LEARNED if model is not None else B.FUSE_GREEDY, model=model)
-    f = B.sv_fuse_circuit(gates, n, **kw, start_qubits=n - 4)
+    f = B.sv_fuse_circuit(gates, n, **kw, start_qubits=n - 2)
     st = DeviceState(n)
     rec = B.sv_init_apply(st.h, 0, f, True)
     B.sv_device_status()
@@ -106,7 +106,7 @@ def test_bench_path_28q_vs_oracle(B, grid28):
     err = oracle.l2_error(ref, got)
     _report("bench_path_28q.json", {
         "workload": "4x7 grid, 20 cycles, seed 3", "n": n, "fusion": "learned" if model else "greedy",
-        "start_qubits": n - 4, "fused_gates": len(rec), "small_state_gates": small,
+        "start_qubits": n - 2, "fused_gates": len(rec), "small_state_gates": small,
         "fidelity": F, "l2_error": err, "max_abs_error": float(d.max()), "max_rel_error": float(rel.max())})
     assert small > 0                       # the lazy start really ran gates on the small state
     assert F >= 1 - 1e-6 and err <= 1e-4, (F, err)

@@ -91,7 +91,7 @@ def test_fusion_is_exact_on_grid_circuit(B, max_k):
         assert len(infos) < len(gates)
 
 
-@pytest.mark.parametrize("max_k,m", [(2, 4), (4, 6), (6, 8), (3, 24)])
+@pytest.mark.parametrize("max_k,m", [(2, 4), (4, 6), (6, 8), (3, 24), (5, 28)])
 def test_light_cone_split_is_exact_and_first(B, max_k, m):
     """start_qubits = m: the fused circuit is still exact, and its first fused gates name at most
     min(m, n - 1) qubits together and commute past every later gate they overtake (so a start
@@ -130,7 +130,7 @@ def test_light_cone_split_is_exact_and_first(B, max_k, m):
 
 def test_light_cone_option_validated(B):
     U = wl.random_unitary(2, np.random.default_rng(1))
-    for bad in (-1, 27):
+    for bad in (-1, 29):
         with pytest.raises(B.SvError) as e:
             B.sv_fuse_circuit([wl.Gate((0,), U)], 4, start_qubits=bad)
         assert e.value.code == B.SV_EINVAL
