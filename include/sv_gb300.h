@@ -121,7 +121,9 @@ typedef struct sv_fuse_opts {
                            left out shares a qubit with it and its qubits lie in S.  sv_init_apply
                            then runs that part on its small state; applied with
                            sv_apply_fused_gates the result is the same state, but may take more
-                           passes than fusing without the split.  Greedy and learned modes. */
+                           passes than fusing without the split.  Greedy and learned modes; the
+                           learned mode also scores light cones of m - 1 .. m - 4 qubits (their gates
+                           costed on the smaller start state) and keeps the cheapest. */
     /* Learned mode with a caller's cost model instead of `model` (used when non-NULL): predicted
      * microseconds of one fused gate of k qubits (targets ascending) run on kernel path `path` in an
      * n-qubit state.  Called on the calling thread during sv_fuse_circuit, once per candidate fused
@@ -397,7 +399,8 @@ SV_API int sv_batch_inject_stall(sv_batch *b, int on);
 /* sv_init(st, basis_index) then sv_apply_fused_gates(st, f, timings), with the same result up to
  * rounding order, computed with less memory traffic.  One pass over the fused gates picks those
  * that share no qubit with an earlier gate left out (so they commute past it) while the qubits they
- * name, targets and controls, number at most 28 and fewer than n; every other qubit still holds its
+ * name, targets and controls, number at most L and fewer than n (L: the qubits the light-cone part
+ * names when f was fused with start_qubits, else 26); every other qubit still holds its
  * bit of basis_index, so the picked gates run first, in order, on the small state of the named
  * qubits (in a library-owned buffer of up to 2 GiB grown on first use; tensor-core gates stay on
  * the tensor cores when the small state has at least k + 5 qubits, the others run on CUDA cores), which

@@ -133,7 +133,7 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3,
 
     space = (("max_k", k_range), ("stage_log2", (0, 11, 12, 13, 14)), ("stage_k", (0, 2, 3, 4)),
              ("threads", (128, 256, 512)), ("smem_max_n", (0, 11, 12, 13, 14)),
-             ("split_min_n", (0, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
+             ("split_min_n", (0, 8, 10, 11, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
              ("wave_mb", (0, 24, 48, 96)), ("ctas", (sms, 2 * sms, 3 * sms, 4 * sms)))
     try:
         best_ms = measure(best)

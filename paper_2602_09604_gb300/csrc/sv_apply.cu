@@ -751,6 +751,7 @@ namespace {
 // |x on the rest> (x) |small state on A>; those gates run on the 2^|A| small state, which one
 // kernel then writes into the zeroed full state.
 constexpr int kCompactMaxQubits = 28;   // a 2 GiB small state
+constexpr int kDefaultLazyQubits = 26;  // circuits fused without a light-cone split: a 512 MB small state
 
 struct ExpandArgs {
     int pos[kCompactMaxQubits];   // ascending qubits of A: small-state bit b -> full-state bit pos[b]
@@ -989,7 +990,8 @@ extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused 
     // gates for the small state, in one pass over the circuit: a gate qualifies if no earlier gate
     // left out shares a qubit with it (so it commutes past those) and the qubits named so far, its
     // own included, stay within the limit
-    const int limit = std::min(kCompactMaxQubits, st->n - 1);
+    // the light-cone part the fuser placed first (its qubit count), else the default
+    const int limit = std::min(f->lazy_limit > 0 ? std::min(f->lazy_limit, kCompactMaxQubits) : kDefaultLazyQubits, st->n - 1);
     std::vector<char> lazy(f->gates.size(), 0);
     uint64_t A = 0, blocked = 0;
     size_t m = 0;

@@ -484,39 +484,44 @@ uint64_t block_mask(const Block &b)
     return m;
 }
 
-// Predicted device time of a fused gate by its qubit set: the cheapest kernel path it may take
-// (its CUDA-core path, and its tensor-core path when the precision allows one), from the trained
-// model or the caller's cost function.  Predictions are kept, so a qubit set is scored once.
+// Predicted device time of a fused gate by its qubit set and the size of the state it runs on:
+// the cheapest kernel path it may take (its CUDA-core path, and its tensor-core path when the
+// precision allows one), from the trained model or the caller's cost function.  Predictions are
+// kept, so a (qubit set, state size) is scored once.  Keys: the mask with the state size in the top
+// bits (masks have at most 34 bits).
+uint64_t cost_key(uint64_t mask, int n) { return mask | ((uint64_t)n << 56); }
+
 class GateCost {
 public:
-    GateCost(const sv_fuse_opts &o, int n) : o_(o), n_(n) {}
+    explicit GateCost(const sv_fuse_opts &o) : o_(o) {}
 
-    // scores every set in `masks` not scored yet (one batched model call)
-    int ensure(const std::vector<uint64_t> &masks)
+    // scores every key not scored yet (one batched model call)
+    int ensure(const std::vector<uint64_t> &keys)
     {
         std::vector<uint64_t> todo;
-        for (uint64_t m : masks)
-            if (!known_.count(m)) {
-                known_[m] = {0.0, SV_PATH_AUTO};
-                todo.push_back(m);
+        for (uint64_t key : keys)
+            if (!known_.count(key)) {
+                known_[key] = {0.0, SV_PATH_AUTO};
+                todo.push_back(key);
             }
         if (todo.empty()) return SV_OK;
         std::vector<float> X;
         std::vector<std::pair<size_t, int>> rows;   // (index into todo, path)
         std::vector<std::array<int, SV_MAX_K>> tg(todo.size());
         for (size_t t = 0; t < todo.size(); ++t) {
+            const int n = (int)(todo[t] >> 56);
             FusedGate g;
-            for (int q = 0; q < 64; ++q)
+            for (int q = 0; q < 56; ++q)
                 if ((todo[t] >> q) & 1) g.targets[g.k++] = q;
             std::copy(g.targets, g.targets + SV_MAX_K, tg[t].begin());
-            std::vector<int> paths = {classify_path(g, n_, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO)};
-            if (o_.precision != SV_PREC_FP32 && g.k >= 4 && n_ >= g.k + 5)
+            std::vector<int> paths = {classify_path(g, n, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO)};
+            if (o_.precision != SV_PREC_FP32 && g.k >= 4 && n >= g.k + 5)
                 paths.push_back(o_.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3);
             for (int p : paths) {
                 rows.push_back({t, p});
                 if (!o_.cost_us) {
                     float feat[16];
-                    mlp_features(g.k, g.targets, p, n_, feat);
+                    mlp_features(g.k, g.targets, p, n, feat);
                     X.insert(X.end(), feat, feat + 16);
                 }
             }
@@ -525,7 +530,8 @@ public:
         if (o_.cost_us) {
             for (size_t r = 0; r < rows.size(); ++r) {
                 const size_t t = rows[r].first;
-                us[r] = o_.cost_us(__builtin_popcountll(todo[t]), tg[t].data(), rows[r].second, n_, o_.cost_ctx);
+                const uint64_t mask = todo[t] & ((uint64_t(1) << 56) - 1);
+                us[r] = o_.cost_us(__builtin_popcountll(mask), tg[t].data(), rows[r].second, (int)(todo[t] >> 56), o_.cost_ctx);
                 if (!(us[r] >= 0.0) || !std::isfinite(us[r])) {
                     set_error("sv_fuse_circuit: the cost function returned %g", us[r]);
                     return SV_EINVAL;
@@ -542,19 +548,37 @@ public:
         }
         return SV_OK;
     }
-    double us(uint64_t m) const { return known_.at(m).first; }
-    int path(uint64_t m) const { return known_.at(m).second; }
+    double us(uint64_t key) const { return known_.at(key).first; }
+    int path(uint64_t key) const { return known_.at(key).second; }
 
 private:
     const sv_fuse_opts &o_;
-    int n_;
     std::unordered_map<uint64_t, std::pair<double, int>> known_;
 };
 
-// A candidate partition for the learned search: blocks in order, the light-cone part first.
+// A candidate partition for the learned search: blocks in order, the light-cone part first.  A
+// start from a basis state (sv_init_apply) runs the light-cone part on the small state of the
+// qubits that part names (a_mask), with targets renumbered inside it: those blocks are costed on
+// that state.
 struct Candidate {
     std::vector<Block> blocks;
     size_t split_at = 0;   // blocks before this index are the light-cone part
+    uint64_t a_mask = 0;   // qubits the light-cone part names (0 without a split)
+    int n = 0;             // full state's qubits
+
+    // cost key of block i's gate if it had qubit set `mask`
+    uint64_t key(size_t i, uint64_t mask) const
+    {
+        if (i >= split_at || !a_mask) return cost_key(mask, n);
+        uint64_t r = 0;
+        int b = 0;
+        for (int q = 0; q < 64; ++q)
+            if ((a_mask >> q) & 1) {
+                if ((mask >> q) & 1) r |= uint64_t(1) << b;
+                ++b;
+            }
+        return cost_key(r, b);
+    }
 };
 
 // One merge of blocks i < j into a block over the union u, placed at pos (i: block j moves back
@@ -569,6 +593,7 @@ constexpr int kMergeWindow = 32;       // blocks apart at most
 constexpr double kMergeMargin = 0.02;  // a merge must save 2% of the two blocks' predicted time
 constexpr double kMergeWithin = 0.15;  // candidates within 15% of the best predicted time are merged
 constexpr int kMergeRounds = 6;
+constexpr int kLightConeTries = 4;     // learned mode also scores light cones of m - 1 .. m - 4 qubits
 
 // Every merge allowed in c: the union has at most max_k qubits, neither block is controlled, both
 // lie in the same part, and one of them commutes with every block between them (no shared qubit).
@@ -641,20 +666,23 @@ int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, in
         std::vector<std::vector<Merge>> opts(cands.size());
         std::vector<uint64_t> need;
         for (size_t c = 0; c < cands.size(); ++c) {
-            opts[c] = merge_options(cands[c], max_k);
+            const Candidate &cd = cands[c];
+            opts[c] = merge_options(cd, max_k);
             for (const Merge &m : opts[c]) {
-                need.push_back(m.u);
-                need.push_back(block_mask(cands[c].blocks[m.i]));
-                need.push_back(block_mask(cands[c].blocks[m.j]));
+                need.push_back(cd.key((size_t)m.i, m.u));
+                need.push_back(cd.key((size_t)m.i, block_mask(cd.blocks[m.i])));
+                need.push_back(cd.key((size_t)m.j, block_mask(cd.blocks[m.j])));
             }
         }
         SV_TRY(cost.ensure(need));
         bool any = false;
         for (size_t c = 0; c < cands.size(); ++c) {
+            const Candidate &cd = cands[c];
             std::vector<Merge> good;
             for (Merge m : opts[c]) {
-                const double two = cost.us(block_mask(cands[c].blocks[m.i])) + cost.us(block_mask(cands[c].blocks[m.j]));
-                m.gain = two - cost.us(m.u);
+                const double two = cost.us(cd.key((size_t)m.i, block_mask(cd.blocks[m.i]))) +
+                                   cost.us(cd.key((size_t)m.j, block_mask(cd.blocks[m.j])));
+                m.gain = two - cost.us(cd.key((size_t)m.i, m.u));   // both blocks lie in the same part
                 if (m.gain > kMergeMargin * two) good.push_back(m);
             }
             std::sort(good.begin(), good.end(), [](const Merge &a, const Merge &b) {
@@ -877,7 +905,11 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             }
         } else if (opts.mode == SV_FUSE_GREEDY || (!opts.cost_us && !mlp_usable(opts.model, kMaxTrustedError))) {
             const int k = opts.mode == SV_FUSE_GREEDY ? opts.max_k : (opts.model ? mlp_fallback_k(opts.model) : opts.max_k);
-            std::vector<Block> blocks = partition(dense, split ? &first : nullptr, &rest, n_qubits, k);
+            size_t split_at = 0;
+            std::vector<Block> blocks = partition(dense, split ? &first : nullptr, &rest, n_qubits, k, kCloseOutside, &split_at);
+            uint64_t a_mask = 0;
+            for (size_t i = 0; i < split_at; ++i) a_mask |= block_mask(blocks[i]);
+            f->lazy_limit = __builtin_popcountll(a_mask);
             materialize(blocks, true);
             for (Block &b : blocks) finish(b, -1);
         } else {
@@ -885,17 +917,39 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             // for which blocks a gate closes -- each improved by cost-guided merging, then scored
             // by the predicted time of its fused gates (each on its cheapest path); the cheapest
             // candidate wins
+            // With a light-cone split (a start from a basis state) the split size is a candidate
+            // too: the light cone on m' <= m qubits, its gates costed on the 2^|A| small state.
+            // A larger light cone moves more gates off the full state but makes every small-state
+            // gate dearer, so smaller ones are scored at the largest fusion size.
+            struct Split {
+                int m;
+                std::vector<Dense> first, rest;
+            };
+            std::vector<Split> splits;
+            if (split) {
+                splits.push_back(Split{start_m, first, rest});
+                for (int mm = start_m - 1; mm >= std::max(1, start_m - kLightConeTries); --mm) {
+                    Split sp{mm, {}, {}};
+                    split_light_cone(dense, mm, sp.first, sp.rest);
+                    splits.push_back(std::move(sp));
+                }
+            }
             std::vector<Candidate> cand;
             {   // the candidate partitions are independent: build them on host threads
                 std::vector<std::future<Candidate>> jobs;
-                const std::vector<Dense> *fp = split ? &first : nullptr;
+                auto job = [&](const Split *sp, int k, int rule) {
+                    return std::async(std::launch::async, [&dense, sp, n_qubits, k, rule]() {
+                        Candidate c;
+                        c.n = n_qubits;
+                        c.blocks = partition(dense, sp ? &sp->first : nullptr, sp ? &sp->rest : nullptr, n_qubits, k, rule,
+                                             &c.split_at);
+                        for (size_t i = 0; i < c.split_at; ++i) c.a_mask |= block_mask(c.blocks[i]);
+                        return c;
+                    });
+                };
                 for (int k = 2; k <= std::max(2, opts.max_k); ++k)
-                    for (int rule = 0; rule < kCloseRules; ++rule)
-                        jobs.push_back(std::async(std::launch::async, [&dense, fp, &rest, n_qubits, k, rule]() {
-                            Candidate c;
-                            c.blocks = partition(dense, fp, &rest, n_qubits, k, rule, &c.split_at);
-                            return c;
-                        }));
+                    for (int rule = 0; rule < kCloseRules; ++rule) jobs.push_back(job(split ? &splits[0] : nullptr, k, rule));
+                for (size_t i = 1; i < splits.size(); ++i) jobs.push_back(job(&splits[i], std::max(2, opts.max_k), kCloseOutside));
                 for (auto &j : jobs) cand.push_back(j.get());
             }
             // identical partitions (different rules often agree) are scored once
@@ -903,7 +957,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 std::vector<Candidate> uniq;
                 std::vector<std::vector<uint64_t>> seen;
                 for (Candidate &c : cand) {
-                    std::vector<uint64_t> key;
+                    std::vector<uint64_t> key = {c.a_mask, (uint64_t)c.split_at};
                     for (const Block &b : c.blocks) key.push_back(block_mask(b));
                     if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
                     seen.push_back(std::move(key));
@@ -911,18 +965,21 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 }
                 cand.swap(uniq);
             }
-            GateCost cost(opts, n_qubits);
+            GateCost cost(opts);
             auto total = [&](const Candidate &c) {
                 double tot = 0.0;
-                for (const Block &b : c.blocks)
-                    if (!b.cmask) tot += cost.us(block_mask(b));   // kept controlled gates: the same in every candidate
+                for (size_t i = 0; i < c.blocks.size(); ++i)   // kept controlled gates: the same in every candidate
+                    if (!c.blocks[i].cmask) tot += cost.us(c.key(i, block_mask(c.blocks[i])));
                 return tot;
             };
             auto score_all = [&]() -> int {
                 std::vector<uint64_t> all;
                 for (const Candidate &c : cand)
-                    for (const Block &b : c.blocks)
-                        if (!b.cmask) all.push_back(block_mask(b));
+                    for (size_t i = 0; i < c.blocks.size(); ++i)
+                        if (!c.blocks[i].cmask) {
+                            all.push_back(c.key(i, block_mask(c.blocks[i])));
+                            if (i < c.split_at) all.push_back(cost_key(block_mask(c.blocks[i]), n_qubits));   // its full-state path
+                        }
                 return cost.ensure(all);
             };
             int rc = score_all();
@@ -946,8 +1003,10 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 const double tot = total(cand[c]);
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
             }
+            f->lazy_limit = __builtin_popcountll(cand[best].a_mask);
             materialize(cand[best].blocks, true);
-            for (Block &b : cand[best].blocks) finish(b, b.cmask ? SV_PATH_CONTROLLED : cost.path(block_mask(b)));
+            // each gate's path for the full state (sv_init_apply re-picks it on the small state)
+            for (Block &b : cand[best].blocks) finish(b, b.cmask ? SV_PATH_CONTROLLED : cost.path(cost_key(block_mask(b), n_qubits)));
         }
     } catch (const std::bad_alloc &) {
         delete f;

@@ -188,6 +188,8 @@ struct sv_state {
 struct sv_fused {
     int n = 0;
     int precision = SV_PREC_FP32;
+    int lazy_limit = 0;             // fused with a light-cone split: the qubits its light-cone part
+                                    // names (sv_init_apply's small-state limit); 0 = the default
     std::vector<svg::FusedGate> gates;
     // device images (lazily uploaded on the first apply)
     int device = -1;

@@ -362,3 +362,32 @@ def test_learned_search_rejects_a_bad_cost(B):
     n, gates = 8, wl.qft_circuit(8)
     with pytest.raises(B.SvError):
         B.sv_fuse_circuit(gates, n, max_k=4, mode=B.FUSE_LEARNED, cost_fn=lambda k, t, p, nn: -1.0)
+
+
+def test_learned_search_scores_smaller_light_cones(B):
+    """With a light-cone split the learned search also scores smaller light cones (their gates costed
+    on the smaller start state).  A cost that makes small-state gates dear drives it to the smallest
+    one tried, a cost that makes them cheap keeps the largest; both stay exact."""
+    rng = np.random.default_rng(23)
+    n = 10
+    gates = _random_controlled_circuit(n, 80, rng)
+    dear = lambda k, t, p, nn: 1.0 if nn == n else 1e3       # small-state gates dear
+    cheap = lambda k, t, p, nn: 2.0 ** nn                      # proportional to the state size
+    counts = {}
+    for name, cost in (("dear", dear), ("cheap", cheap)):
+        infos = check_fusion(B, n, gates, 4, init=5, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4,
+                             cost_fn=cost, start_qubits=8)
+        counts[name] = infos
+    # the light-cone part comes first: count the leading fused gates whose qubits stay within a set
+    # of at most m qubits, m = 8 (cheap) or 4 (dear: the smallest of 8 - 1 .. 8 - 4)
+    def lead(infos, m):
+        S, c = 0, 0
+        for x in infos:
+            q = sum(1 << t for t in x["targets"]) | sum(1 << t for t in x["controls"])
+            if bin(S | q).count("1") > m:
+                break
+            S |= q
+            c += 1
+        return c
+    assert lead(counts["dear"], 4) >= 1
+    assert lead(counts["cheap"], 8) >= lead(counts["dear"], 8)
