@@ -252,14 +252,17 @@ struct Dense {
     uint64_t cmask = 0;        // controls kept as controls (the gate is not fused); else 0
 };
 
-// A controlled gate as its own block over its ascending targets.
-Block controlled_block(const Dense &d)
+// A controlled gate as its own block over its ascending targets (the matrix expression only with
+// `nodes`).
+Block controlled_block(const Dense &d, bool nodes = true)
 {
     Block b;
     b.qubits = d.q;
     std::sort(b.qubits.begin(), b.qubits.end());
-    b.node = new_node(b.qubits, nullptr);
-    b.node->ops.push_back(MatOp{d.m, d.q, nullptr});
+    if (nodes) {
+        b.node = new_node(b.qubits, nullptr);
+        b.node->ops.push_back(MatOp{d.m, d.q, nullptr});
+    }
     b.n_src = 1;
     b.cmask = d.cmask;
     return b;
@@ -276,7 +279,10 @@ constexpr int kMaxStartQubits = 28;         // the small start state of sv_init_
 enum CloseRule : int { kCloseOutside = 0, kCloseOldest = 1, kCloseLargest = 2, kCloseRules = 3 };
 
 // Greedy fusion to at most max_k qubits (larger single gates stay whole), then the horizontal pass.
-std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k, int rule = kCloseOutside)
+// With `nodes` false only the partition is planned (qubit sets, no matrix expressions): the
+// decisions depend on qubit sets alone, so the plan equals the partition built with nodes.
+std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubits, int max_k, int rule = kCloseOutside,
+                                    bool nodes = true)
 {
     std::vector<Block> open, emitted;
     long long stamp = 0;
@@ -297,10 +303,10 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
             }
             std::sort(closed.begin(), closed.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
             for (Block &b : closed) {
-                flush_pending(b);
+                if (nodes) flush_pending(b);
                 emitted.push_back(std::move(b));
             }
-            Block cb = controlled_block(dense[gi]);
+            Block cb = controlled_block(dense[gi], nodes);
             cb.created = stamp++;
             emitted.push_back(std::move(cb));
             open.swap(rest);
@@ -341,23 +347,25 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         std::vector<int> kept(touching.begin() + first_kept, touching.end());
         std::sort(kept.begin(), kept.end(), [&](int a, int b) { return open[a].created < open[b].created; });
         for (int b : closed) {
-            flush_pending(open[b]);
+            if (nodes) flush_pending(open[b]);
             emitted.push_back(std::move(open[b]));
         }
 
         // a single-qubit gate on a qubit of one open block stays pending there
         if (Q.size() == 1 && kept.size() == 1 && touching.size() == 1) {
             Block &kb = open[kept[0]];
-            const std::vector<cplx> &G = dense[gi].m;
-            std::array<cplx, 4> P = {G[0], G[1], G[2], G[3]};
-            for (size_t i = 0; i < kb.pend.size(); ++i)
-                if (kb.pend[i].first == Q[0]) {   // G * earlier pending
-                    const std::array<cplx, 4> &E = kb.pend[i].second;
-                    P = {G[0] * E[0] + G[1] * E[2], G[0] * E[1] + G[1] * E[3], G[2] * E[0] + G[3] * E[2], G[2] * E[1] + G[3] * E[3]};
-                    kb.pend.erase(kb.pend.begin() + (long)i);
-                    break;
-                }
-            kb.pend.push_back({Q[0], P});
+            if (nodes) {
+                const std::vector<cplx> &G = dense[gi].m;
+                std::array<cplx, 4> P = {G[0], G[1], G[2], G[3]};
+                for (size_t i = 0; i < kb.pend.size(); ++i)
+                    if (kb.pend[i].first == Q[0]) {   // G * earlier pending
+                        const std::array<cplx, 4> &E = kb.pend[i].second;
+                        P = {G[0] * E[0] + G[1] * E[2], G[0] * E[1] + G[1] * E[3], G[2] * E[0] + G[3] * E[2], G[2] * E[1] + G[3] * E[3]};
+                        kb.pend.erase(kb.pend.begin() + (long)i);
+                        break;
+                    }
+                kb.pend.push_back({Q[0], P});
+            }
             kb.n_src += 1;
             kb.created = stamp++;
             continue;
@@ -373,7 +381,9 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         nb.n_src = 1;
         for (int b : kept)   // pending single-qubit gates carry over (their qubits stay disjoint)
             for (auto &pq : open[b].pend) nb.pend.push_back(pq);
-        if (kept.empty()) {
+        if (!nodes) {
+            for (int b : kept) nb.n_src += open[b].n_src;
+        } else if (kept.empty()) {
             nb.node = new_node(nb.qubits, nullptr);
         } else {
             // the first kept block's matrix carries over unchanged when the gate adds no qubit to it
@@ -385,7 +395,7 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
                 nb.n_src += open[kept[i]].n_src;
             }
         }
-        {
+        if (nodes) {
             std::vector<cplx> G = dense[gi].m;
             fold_pending(G, Q, nb);   // the pending gates on Q act before this gate
             nb.node->ops.push_back(MatOp{std::move(G), Q, nullptr});
@@ -402,7 +412,7 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
     }
     std::sort(open.begin(), open.end(), [](const Block &a, const Block &b) { return a.created < b.created; });
     for (Block &b : open) {
-        flush_pending(b);
+        if (nodes) flush_pending(b);
         emitted.push_back(std::move(b));
     }
 
@@ -434,8 +444,10 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         std::vector<int> U;
         for (int q = 0; q < n_qubits; ++q)
             if ((um >> q) & 1) U.push_back(q);
-        if (U != t.qubits) t.node = new_node(U, std::move(t.node));   // earlier block first
-        t.node->ops.push_back(MatOp{{}, {}, std::move(b.node)});
+        if (nodes) {
+            if (U != t.qubits) t.node = new_node(U, std::move(t.node));   // earlier block first
+            t.node->ops.push_back(MatOp{{}, {}, std::move(b.node)});
+        }
         t.qubits = std::move(U);
         t.n_src += b.n_src;
     }
@@ -463,16 +475,61 @@ void split_light_cone(const std::vector<Dense> &dense, int m, std::vector<Dense>
     }
 }
 
+// An equivalent gate order for the learned search: each diagonal gate (not kept controlled) moves
+// later, to just before the next gate on one of its qubits that is not diagonal (diagonal gates
+// commute with each other, and every gate commutes with gates on other qubits); the rest keep their
+// order.  Kept controlled gates count as not diagonal.  Returns false when nothing moves.
+bool is_diagonal(const Dense &d)
+{
+    if (d.cmask) return false;
+    const size_t D = size_t(1) << d.q.size();
+    for (size_t r = 0; r < D; ++r)
+        for (size_t c = 0; c < D; ++c)
+            if (r != c && std::abs(d.m[r * D + c]) > 1e-12) return false;
+    return true;
+}
+
+bool defer_diagonals(const std::vector<Dense> &in, std::vector<Dense> &out)
+{
+    std::vector<char> diag(in.size());
+    for (size_t i = 0; i < in.size(); ++i) diag[i] = is_diagonal(in[i]);
+    std::vector<size_t> order, pending;
+    for (size_t i = 0; i < in.size(); ++i) {
+        if (diag[i]) {
+            pending.push_back(i);
+            continue;
+        }
+        uint64_t q = in[i].cmask;
+        for (int t : in[i].q) q |= uint64_t(1) << t;
+        std::vector<size_t> keep;
+        for (size_t p : pending) {
+            uint64_t pq = 0;
+            for (int t : in[p].q) pq |= uint64_t(1) << t;
+            if (pq & q) order.push_back(p);
+            else keep.push_back(p);
+        }
+        pending.swap(keep);
+        order.push_back(i);
+    }
+    for (size_t p : pending) order.push_back(p);
+    bool moved = false;
+    for (size_t i = 0; i < order.size(); ++i) moved = moved || order[i] != i;
+    out.clear();
+    out.reserve(in.size());
+    for (size_t i : order) out.push_back(in[i]);
+    return moved;
+}
+
 // greedy_partition of the circuit, or of its light-cone part followed by the rest's (*split_at:
 // the number of blocks of the first part, 0 without a split)
 std::vector<Block> partition(const std::vector<Dense> &dense, const std::vector<Dense> *first, const std::vector<Dense> *rest,
-                             int n_qubits, int max_k, int rule = kCloseOutside, size_t *split_at = nullptr)
+                             int n_qubits, int max_k, int rule = kCloseOutside, size_t *split_at = nullptr, bool nodes = true)
 {
     if (split_at) *split_at = 0;
-    if (!first) return greedy_partition(dense, n_qubits, max_k, rule);
-    std::vector<Block> a = greedy_partition(*first, n_qubits, max_k, rule);
+    if (!first) return greedy_partition(dense, n_qubits, max_k, rule, nodes);
+    std::vector<Block> a = greedy_partition(*first, n_qubits, max_k, rule, nodes);
     if (split_at) *split_at = a.size();
-    std::vector<Block> b = greedy_partition(*rest, n_qubits, max_k, rule);
+    std::vector<Block> b = greedy_partition(*rest, n_qubits, max_k, rule, nodes);
     for (Block &x : b) a.push_back(std::move(x));
     return a;
 }
@@ -560,11 +617,18 @@ private:
 // start from a basis state (sv_init_apply) runs the light-cone part on the small state of the
 // qubits that part names (a_mask), with targets renumbered inside it: those blocks are costed on
 // that state.
+struct Merge;
 struct Candidate {
     std::vector<Block> blocks;
     size_t split_at = 0;   // blocks before this index are the light-cone part
     uint64_t a_mask = 0;   // qubits the light-cone part names (0 without a split)
     int n = 0;             // full state's qubits
+    // how it was made, to rebuild the winner with matrix expressions: gate order, light-cone split
+    // (first / rest parts, or none), max size, closing rule, then the merges of each round
+    const std::vector<Dense> *order = nullptr;
+    const std::vector<Dense> *first = nullptr, *rest = nullptr;
+    int k = 0, rule = 0;
+    std::vector<std::vector<Merge>> merges;
 
     // cost key of block i's gate if it had qubit set `mask`
     uint64_t key(size_t i, uint64_t mask) const
@@ -646,8 +710,10 @@ void apply_merges(Candidate &c, const std::vector<Merge> &ms, int n_qubits)
         Block nbk;
         for (int q = 0; q < n_qubits; ++q)
             if ((mg.u >> q) & 1) nbk.qubits.push_back(q);
-        nbk.node = nbk.qubits == a.qubits ? std::move(a.node) : new_node(nbk.qubits, std::move(a.node));
-        nbk.node->ops.push_back(MatOp{{}, {}, std::move(z.node)});
+        if (a.node) {   // planned candidates carry no matrix expressions
+            nbk.node = nbk.qubits == a.qubits ? std::move(a.node) : new_node(nbk.qubits, std::move(a.node));
+            nbk.node->ops.push_back(MatOp{{}, {}, std::move(z.node)});
+        }
         nbk.n_src = a.n_src + z.n_src;
         nbk.created = a.created;
         out.push_back(std::move(nbk));
@@ -699,6 +765,7 @@ int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, in
             }
             if (!pick.empty()) {
                 apply_merges(cands[c], pick, n_qubits);
+                cands[c].merges.push_back(std::move(pick));
                 any = true;
             }
         }
@@ -934,23 +1001,35 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                     splits.push_back(std::move(sp));
                 }
             }
+            std::vector<Dense> deferred;
+            Split dsplit{start_m, {}, {}};
+            if (!defer_diagonals(dense, deferred)) deferred.clear();
+            else if (split) split_light_cone(deferred, start_m, dsplit.first, dsplit.rest);
             std::vector<Candidate> cand;
-            {   // the candidate partitions are independent: build them on host threads
-                std::vector<std::future<Candidate>> jobs;
-                auto job = [&](const Split *sp, int k, int rule) {
-                    return std::async(std::launch::async, [&dense, sp, n_qubits, k, rule]() {
-                        Candidate c;
-                        c.n = n_qubits;
-                        c.blocks = partition(dense, sp ? &sp->first : nullptr, sp ? &sp->rest : nullptr, n_qubits, k, rule,
-                                             &c.split_at);
-                        for (size_t i = 0; i < c.split_at; ++i) c.a_mask |= block_mask(c.blocks[i]);
-                        return c;
-                    });
+            {   // candidates are planned on qubit sets only (no matrix expressions), on host threads
+                auto plan = [&](const std::vector<Dense> *order, const std::vector<Dense> *fp, const std::vector<Dense> *rp, int k, int rule) {
+                    Candidate c;
+                    c.n = n_qubits;
+                    c.order = order;
+                    c.first = fp;
+                    c.rest = rp;
+                    c.k = k;
+                    c.rule = rule;
+                    cand.push_back(std::move(c));
                 };
-                for (int k = 2; k <= std::max(2, opts.max_k); ++k)
-                    for (int rule = 0; rule < kCloseRules; ++rule) jobs.push_back(job(split ? &splits[0] : nullptr, k, rule));
-                for (size_t i = 1; i < splits.size(); ++i) jobs.push_back(job(&splits[i], std::max(2, opts.max_k), kCloseOutside));
-                for (auto &j : jobs) cand.push_back(j.get());
+                const int kmax = std::max(2, opts.max_k);
+                for (int k = 2; k <= kmax; ++k)
+                    for (int rule = 0; rule < kCloseRules; ++rule)
+                        plan(&dense, split ? &splits[0].first : nullptr, split ? &splits[0].rest : nullptr, k, rule);
+                for (size_t i = 1; i < splits.size(); ++i) plan(&dense, &splits[i].first, &splits[i].rest, kmax, kCloseOutside);
+                if (!deferred.empty())   // the equivalent order with diagonal gates deferred, at every max size
+                    for (int k = 2; k <= kmax; ++k)
+                        plan(&deferred, split ? &dsplit.first : nullptr, split ? &dsplit.rest : nullptr, k, kCloseOutside);
+                host_parallel_for(cand.size(), std::min<size_t>(cand.size(), 8), [&](size_t i) {
+                    Candidate &c = cand[i];
+                    c.blocks = partition(*c.order, c.first, c.rest, n_qubits, c.k, c.rule, &c.split_at, false);
+                    for (size_t j = 0; j < c.split_at; ++j) c.a_mask |= block_mask(c.blocks[j]);
+                });
             }
             // identical partitions (different rules often agree) are scored once
             {
@@ -1004,9 +1083,19 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
             }
             f->lazy_limit = __builtin_popcountll(cand[best].a_mask);
-            materialize(cand[best].blocks, true);
+            // the winner again, with matrix expressions, and its merges replayed: the same blocks
+            const Candidate &w = cand[best];
+            Candidate win;
+            win.n = n_qubits;
+            win.blocks = partition(*w.order, w.first, w.rest, n_qubits, w.k, w.rule, &win.split_at, true);
+            win.a_mask = w.a_mask;
+            for (const std::vector<Merge> &pick : w.merges) apply_merges(win, pick, n_qubits);
+            bool same = win.blocks.size() == w.blocks.size();
+            for (size_t i = 0; same && i < w.blocks.size(); ++i) same = block_mask(win.blocks[i]) == block_mask(w.blocks[i]);
+            if (!same) { delete f; set_error("sv_fuse_circuit: internal error (learned partition rebuilt differently)"); return SV_EINVAL; }
+            materialize(win.blocks, true);
             // each gate's path for the full state (sv_init_apply re-picks it on the small state)
-            for (Block &b : cand[best].blocks) finish(b, b.cmask ? SV_PATH_CONTROLLED : cost.path(cost_key(block_mask(b), n_qubits)));
+            for (Block &b : win.blocks) finish(b, b.cmask ? SV_PATH_CONTROLLED : cost.path(cost_key(block_mask(b), n_qubits)));
         }
     } catch (const std::bad_alloc &) {
         delete f;

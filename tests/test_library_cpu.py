@@ -391,3 +391,42 @@ def test_learned_search_scores_smaller_light_cones(B):
         return c
     assert lead(counts["dear"], 4) >= 1
     assert lead(counts["cheap"], 8) >= lead(counts["dear"], 8)
+
+
+def _diagonal_mix(n, count, rng):
+    """Dense gates mixed with diagonal ones (RZ, CZ, controlled phases, a phase on three qubits,
+    and some kept as controlled gates), so diagonal gates move past each other."""
+    gates = []
+    for _ in range(count):
+        r = rng.random()
+        qs = [int(q) for q in rng.permutation(n)]
+        if r < 0.2:
+            gates.append(wl.Gate((qs[0],), wl.rz(float(rng.uniform(0, 6.3)))))
+        elif r < 0.35:
+            gates.append(wl.Gate((qs[0], qs[1]), wl.CZ))
+        elif r < 0.5:
+            gates.append(wl.Gate((qs[0], qs[1]), wl.cphase(float(rng.uniform(0, 6.3)))))
+        elif r < 0.55:
+            gates.append(wl.Gate((qs[0], qs[1], qs[2]), np.diag(np.exp(1j * rng.uniform(0, 6.3, 8)))))
+        elif r < 0.6:
+            gates.append(wl.Gate((qs[0],), wl.Z, (qs[1], qs[2])))      # controlled: kept or folded
+        else:
+            k = int(rng.integers(1, 3))
+            gates.append(wl.Gate(tuple(qs[:k]), wl.random_unitary(1 << k, rng)))
+    return gates
+
+
+@pytest.mark.parametrize("name,max_k,start", [("qft", 6, 0), ("qft", 4, 7), ("mix", 6, 0), ("mix", 3, 0), ("mix", 5, 8)])
+def test_learned_search_defers_diagonals_exactly(B, name, max_k, start):
+    """Learned mode also tries the equivalent order with diagonal gates moved later (to just before
+    the next non-diagonal gate on one of their qubits): the fused circuit stays exact, and scored by
+    the same cost it has no more passes than greedy fusion at max_k."""
+    n = 10
+    gates = wl.qft_circuit(n) if name == "qft" else _diagonal_mix(n, 90, np.random.default_rng(max_k + start))
+    cost = lambda k, t, p, nn: 2.0 ** nn
+    infos = check_fusion(B, n, gates, max_k, init=37, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4,
+                         cost_fn=cost, start_qubits=start)
+    if start == 0:
+        g = B.sv_fuse_circuit(gates, n, max_k=max_k, precision=B.PREC_BF16X3, tc_min_k=4)
+        assert len(infos) <= B.sv_fused_count(g)
+        B.sv_fused_free(g)
