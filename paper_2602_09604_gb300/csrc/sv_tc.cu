@@ -661,7 +661,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int MODE, bool VS, int LW, int EW, int WIN>
+template <int MODE, bool VS, int LW, int EW, int WIN, bool V4>
 __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
 {
     using S = TcShape<6, MODE>;
@@ -750,6 +750,17 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                     const bool in = valid && (ij & v.mask) == v.rest;
                     x[c][e] = in ? v.src[fb + fo - v.off] : 0.f;
                     x[c][8 + e] = in ? v.src[fb + fo + 32 - v.off] : 0.f;
+                } else if constexpr (V4) {
+                    // targets 0 and 1: members j .. j + 3 are four consecutive floats (16-byte aligned)
+                    if (e % 4 == 0) {
+                        float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
+                        if (valid) {
+                            re = *reinterpret_cast<const float4 *>(sv + fb + a.foff[j]);
+                            im = *reinterpret_cast<const float4 *>(sv + fb + a.foff[j] + 32);
+                        }
+                        x[c][e] = re.x; x[c][e + 1] = re.y; x[c][e + 2] = re.z; x[c][e + 3] = re.w;
+                        x[c][8 + e] = im.x; x[c][9 + e] = im.y; x[c][10 + e] = im.z; x[c][11 + e] = im.w;
+                    }
                 } else {
                     x[c][e] = valid ? sv[fb + a.foff[j]] : 0.f;
                     x[c][8 + e] = valid ? sv[fb + a.foff[j] + 32] : 0.f;
@@ -913,17 +924,19 @@ constexpr int kWsEpiWarps = 4;
 constexpr int kWsWindow = 1;   // tiles whose loads each loader lane keeps in flight
 constexpr int kWsThreads = (kWsLoadWarps + kWsEpiWarps + 1) * 32;
 
-template <int MODE>
+// V4: the gate's two lowest targets are qubits 0 and 1, so the loaders move four members of a group
+// with one 16-byte access (a warp's accesses are then whole lines)
+template <int MODE, bool V4>
 __global__ void __launch_bounds__(kWsThreads, 1) apply_tc_ws_kernel(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
-    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps, kWsWindow>(sv, a, VsArgs{});
+    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps, kWsWindow, V4>(sv, a, VsArgs{});
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kWsThreads, 1)
     apply_tc_ws_kernel_vs(float *__restrict__ sv, const __grid_constant__ TcArgs a, const __grid_constant__ VsArgs v)
 {
-    tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps, kWsWindow>(sv, a, v);
+    tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps, kWsWindow, false>(sv, a, v);
 }
 
 // ---------------------------------------------------------------------------------------- host
@@ -1074,7 +1087,8 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     int per_sm_regs = staged ? S::MIN_BLOCKS_STAGED : S::MIN_BLOCKS_DIRECT;
     if constexpr (K == 6) {   // the warp-specialised kernel exists for k = 6 only
         if (variant == 2) {
-            kern = apply_tc_ws_kernel<MODE>;
+            const bool v4 = g.targets[0] == 0 && g.targets[1] == 1;
+            kern = v4 ? apply_tc_ws_kernel<MODE, true> : apply_tc_ws_kernel<MODE, false>;
             kern_vs = apply_tc_ws_kernel_vs<MODE>;
             smem = WsShape<MODE>::SMEM;
             tmem_cols = WsShape<MODE>::TMEM_COLS;
@@ -1082,8 +1096,9 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
             per_sm_regs = 1;
         }
     }
-    const int akey = variant + (vs ? 3 : 0);   // function-attribute slot
-    static uint64_t attr_set[6] = {0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
+    // function-attribute slot: variant, virtual source, 16-byte loaders
+    const int akey = variant + (vs ? 3 : 0) + (variant == 2 && !vs && g.targets[0] == 0 && g.targets[1] == 1 ? 6 : 0);
+    static uint64_t attr_set[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
     {
         int dev = 0;
         SV_CUDA_TRY(cudaGetDevice(&dev));

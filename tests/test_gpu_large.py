@@ -4,7 +4,8 @@ greedy fusion at every max size, with correctness from properties that hold at a
 * 33 qubits: 6x6 grid minus sites (5,3), (5,4), (5,5), 24 cycles.  The circuit followed by its
   inverse must return |0...0> (unitarity).
 * 34 qubits: QFT of a seeded basis state; sampled amplitudes against the closed form
-  2^(-n/2) exp(2 pi i x y / 2^n), and the norm.
+  2^(-n/2) exp(2 pi i x y / 2^n), and the norm.  The learned partition must beat the best fixed
+  size by at least 3% here (the deferred-diagonal order gives fewer passes).
 With SV_REPORT_DIR set, the timings go to <SV_REPORT_DIR>/large_runs.json.
 """
 import json
@@ -128,5 +129,8 @@ def test_34q_qft_learned_vs_fixed(env):
     assert checks["plain_fp32_k4"]["max_rel_amp_error"] < 1e-4, checks
     assert checks["learned_bf16x3"]["l2_estimate"] <= 1e-4, checks
     assert checks["learned_bf16x3"]["max_rel_amp_error"] < 2e-4, checks
+    # the learned search gains here: its candidates include the order with the controlled phases
+    # (diagonal) deferred, which fuses into fewer passes than any fixed greedy size (105 vs 118)
     best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
-    assert res["learned_bf16x3"]["device_s"] <= 1.03 * best_fixed, res
+    assert res["learned_bf16x3"]["fused_gates"] < res["greedy_k6_bf16x3"]["fused_gates"], res
+    assert res["learned_bf16x3"]["device_s"] <= 0.97 * best_fixed, res
