@@ -84,14 +84,16 @@ def test_single_tc_gate(B, DS, mode, n):
 
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
 def test_k6_every_kernel_variant(B, DS, mode):
-    """k = 6 gates reach every tensor-core kernel by their low targets (below qubit 5): none, or
-    one at qubit 3 or 4 (shared-memory-A direct kernel); one at qubits 0-2, or two (tensor-memory-A
-    direct); three or more (staged through shared memory).  Each matches the oracle."""
+    """k = 6 gates reach every tensor-core kernel form by their low targets (below qubit 5): up to
+    two -- none, one at qubits 0-4, two, or exactly qubits 0 and 1 (16-byte loaders) -- run on the
+    warp-specialised kernel, three or more are staged through shared memory.  Each matches the
+    oracle."""
     n = 13
     rng = np.random.default_rng(606)
     psi0 = wl.random_state(n, rng).astype(np.complex64)
     for tg in [(5, 6, 7, 8, 9, 12), (3, 6, 7, 9, 10, 12), (4, 5, 8, 9, 11, 12), (1, 6, 7, 9, 10, 12),
-               (3, 4, 7, 9, 10, 12), (0, 2, 4, 8, 9, 12), (0, 1, 2, 3, 4, 12)]:
+               (3, 4, 7, 9, 10, 12), (0, 1, 7, 9, 10, 12), (0, 1, 5, 6, 7, 8), (0, 5, 6, 7, 8, 9),
+               (0, 2, 4, 8, 9, 12), (0, 1, 2, 3, 4, 12)]:
         g = wl.random_gate(n, 6, rng, targets=tg)
         ref = psi0.astype(np.complex128)
         oracle.apply_gate(ref, n, g)
