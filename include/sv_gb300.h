@@ -349,6 +349,11 @@ typedef struct sv_batch_opts {
     int stage_k;        /* staged circuits: each stage's gates are fused again (greedy, fp64
                            products) into gates of at most stage_k qubits, 1..4; 0 = kept as given
                            (default 0) */
+    int stage_layers;   /* staged circuits: nonzero = a run of one-qubit gates in a stage (between
+                           two gates on more qubits) is applied as one layer -- each qubit's 2x2
+                           product -- in register phases of up to five qubits, one shared-memory
+                           round trip per phase, instead of being fused into stage_k-qubit gates
+                           (default 0) */
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte
@@ -361,7 +366,7 @@ SV_API int sv_batch_create(const sv_fused *const *circuits, int count, void *are
                            sv_batch **out);
 SV_API void sv_batch_free(sv_batch *b);
 /* Options take effect at the next sv_batch_run (which rebuilds the work list, synchronously, when
- * smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2 or stage_k changed).  SV_EINVAL for a
+ * smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2, stage_k or stage_layers changed).  SV_EINVAL for a
  * value out of range. */
 SV_API int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *opts);
 SV_API int sv_batch_get_opts(const sv_batch *b, sv_batch_opts *opts);

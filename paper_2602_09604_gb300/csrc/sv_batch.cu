@@ -25,6 +25,7 @@
 // States use the library's blocked layout (32 reals then 32 imaginaries per 256-byte block).
 // The launch can be captured once in a CUDA graph and replayed.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -43,7 +44,8 @@ constexpr int kBatchMaxN = 24;   // states up to 2^25 floats: 32-bit offsets
 // one or two qubits (CZ, Z, ...) that come right before the gate and are applied to its inputs:
 // amplitude i is negated when gsign + popc(i & zmask) + sum_d popc(i & (i >> dist[d]) & dmask[d])
 // is odd (any +-1 diagonal on at most two qubits is such a quadratic form over GF(2)).  k = 0 is a
-// sign-only sweep (a run with no gate after it in its stage, or before a 4-qubit gate).
+// sign-only sweep (a run with no gate after it in its stage, or before a 4-qubit gate); k < 0 is a
+// layer: one-qubit gates on the qubits of lmask, one 2x2 matrix each.
 constexpr int kSignDist = 4;   // distinct qubit distances of the pair terms of one run
 
 struct BGate {
@@ -55,6 +57,7 @@ struct BGate {
     unsigned zmask;          // single-qubit terms
     unsigned dmask[kSignDist];   // pair terms (a, a + dist[d]): bit a
     int dist[kSignDist];
+    unsigned lmask;          // k < 0 (a layer): its qubits; their 2x2 matrices follow at mat_off, ascending
 };
 
 struct BCirc {
@@ -123,6 +126,17 @@ __device__ __forceinline__ void st_v(float *p, const float (&v)[V])
     else *p = v[0];
 }
 
+// x's bits deposited, lowest first, into the set bits of mask
+__device__ __host__ __forceinline__ unsigned deposit_bits(unsigned x, unsigned mask)
+{
+    unsigned r = 0u;
+    for (unsigned m = mask; m != 0u; m &= m - 1u) {
+        if (x & 1u) r |= m & (0u - m);
+        x >>= 1;
+    }
+    return r;
+}
+
 // The sign run of g at local index i: true when the amplitude is negated.
 __device__ __forceinline__ bool sign_odd(const BGate &g, unsigned i)
 {
@@ -151,6 +165,124 @@ __device__ void sign_sweep(float *S, int n, const BGate &g)
         *reinterpret_cast<float4 *>(S + o) = re;
         *reinterpret_cast<float4 *>(S + o + 32) = im;
     }
+}
+
+// One phase of a layer (k < 0) on a 2^n-amplitude state in shared memory.  Every qubit of the layer
+// gets its own 2x2 matrix and they all commute, so the layer runs in phases: lane p of a warp holds
+// in-block position p of the 2^R amplitudes that differ only in the phase's R high qubits (qpos,
+// ascending; their matrices at uhi) and agree with the warp's set s on the other bits -- scalar
+// shared-memory accesses, consecutive lanes on consecutive floats, no bank conflicts.  The high
+// qubits' gates run on register pairs; with `low` set the in-block qubits of the layer (lomask, their
+// matrices at ulo) run too, each pair exchanged between lanes by a warp shuffle; with `sign` the
+// gate's sign run applies as the amplitudes are loaded.
+template <int R>
+__device__ void layer_phase(float *S, int n, const BGate &g, const int (&qpos)[5], const float2 *__restrict__ uhi,
+                            unsigned lomask, const float2 *__restrict__ ulo, bool sign)
+{
+    constexpr int M = 1 << R;
+    const int lane = threadIdx.x & 31;
+    const unsigned nsets = 1u << (n - 5 - R);
+    unsigned hmask = 0u;   // the phase's high qubits
+#pragma unroll
+    for (int r = 0; r < R; ++r) hmask |= 1u << qpos[r];
+    const unsigned cmask = ((1u << n) - 1u) & ~31u & ~hmask;   // the set's bits
+    const unsigned warps = blockDim.x >> 5;
+    for (unsigned s = threadIdx.x >> 5; s < nsets; s += warps) {
+        const unsigned base = deposit_bits(s, cmask) | (unsigned)lane;
+        float xr[M], xi[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            unsigned i = base;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if ((m >> r) & 1) i |= 1u << qpos[r];
+            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+            xr[m] = S[o];
+            xi[m] = S[o + 32];
+            if (sign && sign_odd(g, i)) {
+                xr[m] = -xr[m];
+                xi[m] = -xi[m];
+            }
+        }
+        // high qubits: pairs of registers
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 u00 = uhi[4 * r], u01 = uhi[4 * r + 1], u10 = uhi[4 * r + 2], u11 = uhi[4 * r + 3];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                if ((m >> r) & 1) continue;
+                const int m1 = m | (1 << r);
+                const float ar = xr[m], ai = xi[m], br = xr[m1], bi = xi[m1];
+                xr[m] = u00.x * ar - u00.y * ai + u01.x * br - u01.y * bi;
+                xi[m] = u00.x * ai + u00.y * ar + u01.x * bi + u01.y * br;
+                xr[m1] = u10.x * ar - u10.y * ai + u11.x * br - u11.y * bi;
+                xi[m1] = u10.x * ai + u10.y * ar + u11.x * bi + u11.y * br;
+            }
+        }
+        // in-block qubits: the partner amplitude lives in lane p ^ 2^q
+        int t = 0;
+        for (unsigned lm = lomask; lm; lm &= lm - 1u, ++t) {
+            const int q = __ffs((int)lm) - 1;
+            const bool hi_half = (lane >> q) & 1;
+            // own coefficient and partner coefficient of this lane's output row
+            const float2 a = hi_half ? ulo[4 * t + 3] : ulo[4 * t], b = hi_half ? ulo[4 * t + 2] : ulo[4 * t + 1];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const float pr = __shfl_xor_sync(0xffffffffu, xr[m], 1 << q);
+                const float pi = __shfl_xor_sync(0xffffffffu, xi[m], 1 << q);
+                const float yr = a.x * xr[m] - a.y * xi[m] + b.x * pr - b.y * pi;
+                const float yi = a.x * xi[m] + a.y * xr[m] + b.x * pi + b.y * pr;
+                xr[m] = yr;
+                xi[m] = yi;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            unsigned i = base;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if ((m >> r) & 1) i |= 1u << qpos[r];
+            const unsigned o = ((i >> 5) << 6) | (i & 31u);
+            S[o] = xr[m];
+            S[o + 32] = xi[m];
+        }
+    }
+}
+
+// A layer: its high qubits (local bit >= 5) in phases of up to MAXR (five; four in the 512-thread
+// form, whose 128-register budget holds 2 x 16 amplitudes), the first phase also taking the
+// in-block qubits (shuffles) and the sign run; a barrier between phases.
+template <int MAXR>
+__device__ void apply_layer(float *S, int n, const BGate &g, const float2 *__restrict__ U)
+{
+    const unsigned lo = g.lmask & 31u;
+    unsigned hi = g.lmask & ~31u;
+    const int nlo = __popc(lo);
+    const float2 *uhi = U + 4 * nlo;   // matrices ascending by qubit: the in-block ones first
+    bool first = true;
+    do {
+        int qpos[5] = {0, 0, 0, 0, 0};
+        int r = 0;
+        while (hi && r < MAXR && r < n - 5) {
+            qpos[r++] = __ffs((int)hi) - 1;
+            hi &= hi - 1u;
+        }
+        const unsigned lom = first ? lo : 0u;
+        const bool sg = first && (g.nd | g.zmask | g.gsign);
+        switch (r) {
+        case 0: layer_phase<0>(S, n, g, qpos, uhi, lom, U, sg); break;
+        case 1: layer_phase<1>(S, n, g, qpos, uhi, lom, U, sg); break;
+        case 2: layer_phase<2>(S, n, g, qpos, uhi, lom, U, sg); break;
+        case 3: layer_phase<3>(S, n, g, qpos, uhi, lom, U, sg); break;
+        case 4: layer_phase<4>(S, n, g, qpos, uhi, lom, U, sg); break;
+        default:
+            if constexpr (MAXR >= 5) layer_phase<5>(S, n, g, qpos, uhi, lom, U, sg);
+            break;
+        }
+        uhi += 4 * r;
+        first = false;
+        if (hi) __syncthreads();   // this phase's writes before the next phase's reads
+    } while (hi);
 }
 
 // Apply one fused gate of K qubits to groups [g_begin, g_end) of the state S (shared or global)
@@ -323,16 +455,6 @@ struct BatchArgs {
     int stage_log2;
 };
 
-// x's bits deposited, lowest first, into the set bits of mask
-__device__ __host__ __forceinline__ unsigned deposit_bits(unsigned x, unsigned mask)
-{
-    unsigned r = 0u;
-    for (unsigned m = mask; m != 0u; m &= m - 1u) {
-        if (x & 1u) r |= m & (0u - m);
-        x >>= 1;
-    }
-    return r;
-}
 
 // Bounded wait (thread 0) until counter d reaches want; false when it gave up or another CTA
 // already did (the abort flag), after raising the abort flag and the error word.
@@ -444,7 +566,8 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                 }
                 for (int gi = 0; gi < ch.gate_count; ++gi) {
                     const BGate &g = sG[gi];   // read in place: the sign fields stay in shared memory
-                    if (g.k == 0) sign_sweep(sS, L, g);
+                    if (g.k < 0) apply_layer<(MAXT <= 256 ? 5 : 4)>(sS, L, g, sU + (g.mat_off - ch.mat_begin));
+                    else if (g.k == 0) sign_sweep(sS, L, g);
                     else apply_gate_cta<false, (MAXT <= 256), true, true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
                     __syncthreads();   // this gate's writes before the next gate's reads
                 }
@@ -542,12 +665,12 @@ struct sv_batch {
     int n_items = 0;
     int n_counters = 0;
     sv_batch_info info{};            // what the current list holds
-    int list_cfg[6] = {-1, -1, -1, -1, -1, -1};   // smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2, stage_k
+    int list_cfg[7] = {-1, -1, -1, -1, -1, -1, -1};   // smem_max_n, split_min_n, tile_log2, wave_mb, stage_log2, stage_k, stage_layers
     bool stall = false;              // test hook: first split step counts one tile too many
     bool list_stall = false;
     sv_batch_opts opts{};
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int graph_cfg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -650,7 +773,7 @@ constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
 // past every gate it overtakes) and the stage's qubits with its own still number at most L;
 // otherwise its qubits are closed for the rest of the scan.  The local set is then filled up to
 // L qubits with the lowest unused ones (longer contiguous runs per tile).
-void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, std::vector<BStage> &st,
+void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, bool layers, std::vector<BStage> &st,
                   std::vector<BChunk> &chunks, std::vector<BGate> &sg, std::vector<float2> &sm)
 {
     std::vector<const FusedGate *> rest = gs;
@@ -707,8 +830,47 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         SignRun run;
         std::vector<const FusedGate *> dense_run;
         uint64_t dense_q = 0;
+        // a run of one-qubit gates as one layer: per qubit the product of its gates, in order
+        auto emit_layer = [&](const SignRun &r) {
+            std::vector<std::array<cplx, 4>> U(32);
+            unsigned lm = 0u;
+            for (const FusedGate *g : dense_run) {
+                const int q = local(g->targets[0]);
+                const cplx *G = g->mat.data();
+                std::array<cplx, 4> &P = U[(size_t)q];
+                if (!((lm >> q) & 1u)) {
+                    P = {G[0], G[1], G[2], G[3]};
+                    lm |= 1u << q;
+                } else {
+                    P = {G[0] * P[0] + G[1] * P[2], G[0] * P[1] + G[1] * P[3], G[2] * P[0] + G[3] * P[2], G[2] * P[1] + G[3] * P[3]};
+                }
+            }
+            const int dd = 4 * __builtin_popcount(lm);
+            if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
+                chunks.back().mat_count + 1 + dd > kStageMatCap)
+                chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
+            if (chunks.back().mat_count & 1) {
+                sm.push_back(make_float2(0.f, 0.f));
+                chunks.back().mat_count += 1;
+            }
+            BGate b{};
+            r.fill(b);
+            b.k = -1;
+            b.lmask = lm;
+            b.mat_off = (int)sm.size();
+            for (int q = 0; q < 32; ++q)
+                if ((lm >> q) & 1u)
+                    for (int e = 0; e < 4; ++e) sm.push_back(make_float2((float)U[(size_t)q][e].real(), (float)U[(size_t)q][e].imag()));
+            sg.push_back(b);
+            chunks.back().gate_count += 1;
+            chunks.back().mat_count += dd;
+        };
         auto flush = [&]() {
-            if (!dense_run.empty()) {
+            bool one_qubit = layers && !dense_run.empty();
+            for (const FusedGate *g : dense_run) one_qubit = one_qubit && g->k == 1;
+            if (one_qubit) {
+                emit_layer(run);
+            } else if (!dense_run.empty()) {
                 std::vector<FusedGate> fused;
                 if (stage_k > 0) fused = refuse_gates(dense_run, n, stage_k);
                 for (size_t i = 0; i < (stage_k > 0 ? fused.size() : dense_run.size()); ++i) {
@@ -747,8 +909,8 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
 // held in shared memory (short; they fill the tail).
 int build_work_list(sv_batch *b)
 {
-    const int cfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
-                        b->opts.stage_k};
+    const int cfg[7] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                        b->opts.stage_k, b->opts.stage_layers};
     if (b->d_items && std::memcmp(cfg, b->list_cfg, sizeof(cfg)) == 0 && b->list_stall == b->stall) return SV_OK;
     std::vector<BItem> items;
     std::vector<int> need;
@@ -771,7 +933,7 @@ int build_work_list(sv_batch *b)
             for (int gi = 0; gi < hc[(size_t)c].gate_count; ++gi) gs.push_back(b->src[(size_t)(hc[(size_t)c].gate_begin + gi)]);
             hc[(size_t)c].stage_begin = (int)hst.size();
             try {
-                build_stages(gs, n, L, b->opts.stage_k, hst, hch, hsg, hsm);
+                build_stages(gs, n, L, b->opts.stage_k, b->opts.stage_layers != 0, hst, hch, hsg, hsm);
             } catch (const std::bad_alloc &) {
                 set_error("sv_batch: out of host memory building stages");
                 return SV_ENOMEM;
@@ -924,6 +1086,7 @@ int check_opts(const sv_batch_opts &o)
     if (o.wave_mb < 0 || o.wave_mb > (1 << 20)) { set_error("sv_batch: wave_mb must be in [0, 2^20]"); return SV_EINVAL; }
     if (o.stage_log2 != 0 && (o.stage_log2 < kStageMinN || o.stage_log2 > 14)) { set_error("sv_batch: stage_log2 must be 0 or in [%d, 14]", kStageMinN); return SV_EINVAL; }
     if (o.stage_k < 0 || o.stage_k > kBatchMaxK) { set_error("sv_batch: stage_k must be in [0, %d]", kBatchMaxK); return SV_EINVAL; }
+    if (o.stage_layers != 0 && o.stage_layers != 1) { set_error("sv_batch: stage_layers must be 0 or 1"); return SV_EINVAL; }
     return SV_OK;
 }
 
@@ -1026,6 +1189,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     b->opts.wave_mb = 0;
     b->opts.stage_log2 = 0;
     b->opts.stage_k = 0;
+    b->opts.stage_layers = 0;
     *out = b;
     return SV_OK;
 }
@@ -1074,8 +1238,8 @@ extern "C" int sv_batch_run(sv_batch *b)
     SV_TRY(check_opts(b->opts));
     SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
     SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
-    const int lcfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
-                         b->opts.stage_k};
+    const int lcfg[7] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                         b->opts.stage_k, b->opts.stage_layers};
     const bool relist = !b->d_items || std::memcmp(lcfg, b->list_cfg, sizeof(lcfg)) != 0 || b->list_stall != b->stall;
     if (relist) {
         // the captured graph holds the old list's pointers
@@ -1087,8 +1251,8 @@ extern "C" int sv_batch_run(sv_batch *b)
         SV_TRY(build_work_list(b));
     }
     if (!b->opts.use_graph) return launch_batch(b);
-    const int cfg[8] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb,
-                        b->opts.stage_log2, b->opts.stage_k};
+    const int cfg[9] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb,
+                        b->opts.stage_log2, b->opts.stage_k, b->opts.stage_layers};
     if (b->graph && std::memcmp(cfg, b->graph_cfg, sizeof(cfg)) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -1151,8 +1315,8 @@ extern "C" int sv_batch_get_info(sv_batch *b, sv_batch_info *out)
     clear_error();
     if (!b || !out) { set_error("sv_batch_get_info: NULL argument"); return SV_EINVAL; }
     SV_TRY(check_opts(b->opts));
-    const int lcfg[6] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
-                         b->opts.stage_k};
+    const int lcfg[7] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
+                         b->opts.stage_k, b->opts.stage_layers};
     if (!b->d_items || std::memcmp(lcfg, b->list_cfg, sizeof(lcfg)) != 0 || b->list_stall != b->stall) {
         SV_CUDA_TRY(cudaStreamSynchronize(b->stream));   // a captured graph may still run on the old list
         if (b->graph) {

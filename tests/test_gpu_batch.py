@@ -114,11 +114,14 @@ def _sign_circuit(n, count, rng):
     return gates
 
 
-def test_sign_runs_match_oracle(env):
+@pytest.mark.parametrize("layers", [0, 1])
+def test_sign_runs_match_oracle(env, layers):
     """Circuits kept unfused (fusion size 0), so each stage re-fuses its dense gates and applies
     its +-1 diagonals as sign runs on the inputs of the next gate (or as a sweep of their own):
     HEA circuits (CZ ladders) and circuits dense in sign gates, at every stage tile size,
-    re-fusion size and CTA size, against the oracle."""
+    re-fusion size and CTA size, against the oracle.  With layers, runs of one-qubit gates go
+    through register phases (in-block qubits by warp shuffles, up to four or five higher qubits in
+    registers)."""
     B, batch = env
     rng = np.random.default_rng(31)
     circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [16, 9, 14, 12, 11]]
@@ -129,7 +132,7 @@ def test_sign_runs_match_oracle(env):
                (512, 0, 304, 1, 13, 3), (256, 0, 1, 8, 12, 1)]
     b = batch.Batch(circuits, 0)
     for threads, smem_n, ctas, split_n, sl, sk in configs:
-        b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk)
+        b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk, layers)
         info = B.sv_batch_get_info(b.h)
         assert info["staged"] == len(circuits), info
         b.arena.fill_(float("nan"))
@@ -137,7 +140,7 @@ def test_sign_runs_match_oracle(env):
         B.sv_device_status()
         for i, ref in enumerate(refs):
             got = b.state(i)
-            cfg = (threads, ctas, sl, sk, i)
+            cfg = (threads, ctas, sl, sk, layers, i)
             assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
             assert oracle.l2_error(ref, got) <= 1e-4, cfg
     b.free()
