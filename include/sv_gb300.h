@@ -349,11 +349,17 @@ typedef struct sv_batch_opts {
     int stage_k;        /* staged circuits: each stage's gates are fused again (greedy, fp64
                            products) into gates of at most stage_k qubits, 1..4; 0 = kept as given
                            (default 0) */
-    int stage_layers;   /* staged circuits: nonzero = a run of one-qubit gates in a stage (between
-                           two gates on more qubits) is applied as one layer -- each qubit's 2x2
-                           product -- in register phases of up to five qubits, one shared-memory
-                           round trip per phase, instead of being fused into stage_k-qubit gates
-                           (default 0) */
+    int stage_layers;   /* staged circuits with tiles of 10 or more qubits: nonzero = a run of
+                           one-qubit gates in a stage (between two gates on more qubits) is one
+                           layer -- each qubit's 2x2 product -- and the layers and the +-1 sign
+                           runs between them are applied in register phases: windows of five
+                           local qubits held in registers, one shared-memory round trip per
+                           phase, instead of stage_k-qubit gates (default 0) */
+    int ctas_per_sm;    /* 0 or 1 (default 1): one CTA per SM; 2: two CTAs share each SM (CTAs of at most 256 threads,
+                           128 registers a thread), so that one CTA's memory traffic, waits and
+                           barriers overlap the other's arithmetic; SV_EINVAL unless two CTAs'
+                           shared memory (matrix area, descriptors and the larger of the
+                           smem_max_n state and the stage tile) fits on one SM */
 } sv_batch_opts;
 
 /* Bytes of the state arena for these circuit sizes: each state in the blocked layout, 256-byte

@@ -51,9 +51,9 @@ class Batch:
         self.h = B.sv_batch_create(self.fused, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
     def set(self, threads, smem_max_n, ctas, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0, stage_log2=0,
-            stage_k=0, stage_layers=0):
+            stage_k=0, stage_layers=0, ctas_per_sm=1):
         B.sv_batch_set_opts(self.h, threads, smem_max_n, ctas, use_graph, split_min_n, tile_log2, wave_mb, stage_log2,
-                            stage_k, stage_layers)
+                            stage_k, stage_layers, ctas_per_sm)
 
     def run(self):
         B.sv_batch_run(self.h)
@@ -99,7 +99,7 @@ def digest(circuits) -> str:
 
 
 FIELDS = ("threads", "smem_max_n", "ctas", "split_min_n", "tile_log2", "wave_mb", "stage_log2", "stage_k",
-          "stage_layers")
+          "stage_layers", "ctas_per_sm")
 
 
 def apply(b: "Batch", cfg: dict, use_graph: bool = True) -> None:
@@ -110,7 +110,7 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3,
     """Returns (best settings dict, trial log).  Coordinate descent over the fusion size and every
     batch option, up to `rounds` sweeps (stopping early when a sweep changes nothing)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    key = f"v6|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
+    key = f"v7|{torch.cuda.get_device_name(0)}|{digest(circuits)}"
     if use_cache and os.path.exists(cache):
         try:
             got = json.load(open(cache)).get(key)
@@ -119,8 +119,8 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3,
         except Exception:
             pass
     log = []
-    best = {"max_k": 2, "threads": 512, "smem_max_n": 10, "ctas": 2 * sms, "split_min_n": 11, "tile_log2": 12,
-            "wave_mb": 0, "stage_log2": 14, "stage_k": 3, "stage_layers": 0}
+    best = {"max_k": 0, "threads": 512, "smem_max_n": 0, "ctas": sms, "split_min_n": 8, "tile_log2": 12,
+            "wave_mb": 48, "stage_log2": 14, "stage_k": 2, "stage_layers": 1, "ctas_per_sm": 1}
     batches = {}
 
     def measure(cfg):
@@ -132,8 +132,22 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3,
         log.append(dict(cfg, ms=ms))
         return ms
 
+    # "form": threads per CTA and CTAs per SM together (two per SM take at most 256 threads and
+    # shared memory for two, so stage tiles of at most 13 qubits and at least 2 x SMs CTAs)
+    forms = ((512, 1), (256, 1), (128, 1), (256, 2), (128, 2))
+
+    def variant(cfg, field, v):
+        if field != "form":
+            return dict(cfg, **{field: v})
+        c = dict(cfg, threads=v[0], ctas_per_sm=v[1])
+        if v[1] == 2:
+            c["stage_log2"] = min(c["stage_log2"], 13)
+            c["smem_max_n"] = min(c["smem_max_n"], 13)
+            c["ctas"] = max(c["ctas"], 2 * sms)
+        return c
+
     space = (("max_k", k_range), ("stage_log2", (0, 11, 12, 13, 14)), ("stage_k", (0, 2, 3, 4)), ("stage_layers", (0, 1)),
-             ("threads", (128, 256, 512)), ("smem_max_n", (0, 11, 12, 13, 14)),
+             ("form", forms), ("smem_max_n", (0, 11, 12, 13, 14)),
              ("split_min_n", (0, 8, 10, 11, 13, 14, 15, 16, 17)), ("tile_log2", (10, 11, 12, 13, 14)),
              ("wave_mb", (0, 24, 48, 96)), ("ctas", (sms, 2 * sms, 3 * sms, 4 * sms)))
     try:
@@ -146,9 +160,9 @@ def autotune(circuits, repeats=5, cache=CACHE, use_cache=True, k_range=(0, 2, 3,
                 if field in ("stage_k", "stage_layers") and best["stage_log2"] == 0:
                     continue
                 for v in values:
-                    if v == best[field]:
+                    if v == (best[field] if field != "form" else (best["threads"], best["ctas_per_sm"])):
                         continue
-                    cfg = dict(best, **{field: v})
+                    cfg = variant(best, field, v)
                     try:
                         ms = measure(cfg)
                     except B.SvError:
@@ -187,7 +201,7 @@ def report(count=256, seed=5):
     # the comparisons at their own best fusion size (k = 4 for one launch or one pass per gate)
     b4 = Batch(circuits, 4)
     apply(b4, dict(best, max_k=4, threads=256, smem_max_n=12, split_min_n=15, tile_log2=13, wave_mb=0, stage_log2=0,
-                   stage_k=0, stage_layers=0))
+                   stage_k=0, stage_layers=0, ctas_per_sm=1))
     t_per_gate_k4 = b4.time(b4.run)
     t_loop = b4.time(b4.run_loop, repeats=3)
     b4.free()

@@ -67,7 +67,7 @@ class sv_batch_opts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("smem_max_n", ctypes.c_int), ("ctas", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("split_min_n", ctypes.c_int), ("tile_log2", ctypes.c_int),
                 ("wave_mb", ctypes.c_int), ("stage_log2", ctypes.c_int), ("stage_k", ctypes.c_int),
-                ("stage_layers", ctypes.c_int)]
+                ("stage_layers", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 class sv_batch_info(ctypes.Structure):
@@ -486,9 +486,9 @@ def sv_batch_free(b) -> None:
 
 def sv_batch_set_opts(b, threads: int, smem_max_n: int, ctas: int, use_graph: bool = True,
                       split_min_n: int = 15, tile_log2: int = 12, wave_mb: int = 0, stage_log2: int = 0,
-                      stage_k: int = 0, stage_layers: int = 0) -> None:
+                      stage_k: int = 0, stage_layers: int = 0, ctas_per_sm: int = 1) -> None:
     o = sv_batch_opts(threads, smem_max_n, ctas, int(bool(use_graph)), split_min_n, tile_log2, wave_mb, stage_log2,
-                      stage_k, int(bool(stage_layers)))
+                      stage_k, int(bool(stage_layers)), ctas_per_sm)
     _check(lib.sv_batch_set_opts(b, ctypes.byref(o)))
 
 

@@ -44,11 +44,11 @@ constexpr int kBatchMaxN = 24;   // states up to 2^25 floats: 32-bit offsets
 // one or two qubits (CZ, Z, ...) that come right before the gate and are applied to its inputs:
 // amplitude i is negated when gsign + popc(i & zmask) + sum_d popc(i & (i >> dist[d]) & dmask[d])
 // is odd (any +-1 diagonal on at most two qubits is such a quadratic form over GF(2)).  k = 0 is a
-// sign-only sweep (a run with no gate after it in its stage, or before a 4-qubit gate); k < 0 is a
-// layer: one-qubit gates on the qubits of lmask, one 2x2 matrix each.
+// sign-only sweep (a run with no gate after it in its stage, or before a 4-qubit gate); k = -2 is
+// a register phase and k = -3, -4 are its records (see run_phase).
 constexpr int kSignDist = 4;   // distinct qubit distances of the pair terms of one run
 
-struct BGate {
+struct alignas(16) BGate {
     int k;
     int targets[SV_MAX_K];   // ascending
     int mat_off;             // in float2 units into the matrix table
@@ -57,8 +57,10 @@ struct BGate {
     unsigned zmask;          // single-qubit terms
     unsigned dmask[kSignDist];   // pair terms (a, a + dist[d]): bit a
     int dist[kSignDist];
-    unsigned lmask;          // k < 0 (a layer): its qubits; their 2x2 matrices follow at mat_off, ascending
+    unsigned lmask;          // k = -4 (a phase's sign run): the run's form on the window bits alone
 };
+
+static_assert(sizeof(BGate) % 16 == 0, "stage gate descriptors are copied 16 bytes at a time");
 
 struct BCirc {
     long long state_off;     // in floats into the arena
@@ -97,12 +99,23 @@ constexpr int kStageGateCap = 64;    // gate descriptors per chunk
 //   kStage  - tile `tile` of stage `step` of circuit c, through shared memory.
 enum : int { kWhole = 0, kSingle = 1, kTile = 2, kStage = 3 };
 
-struct BItem {
+struct alignas(16) BItem {   // 64 bytes
     int kind;
     int c;
     int step;
     int tile;
+    // kStage: what the item needs, copied here so that one 64-byte read starts it (instead of a
+    // chain of dependent reads through the circuit, stage and chunk tables)
+    int n;
+    int done_off;            // the circuit's first completion counter
+    int need_prev;           // tiles of the previous stage (the wait's target)
+    unsigned lmask;          // the stage's local qubits
+    long long state_off;
+    int chunk_begin;
+    int chunk_count;
+    BChunk ch0;              // the stage's first chunk (empty when it has none)
 };
+static_assert(sizeof(BItem) == 64, "work items are read 16 bytes at a time");
 
 template <int V, bool L2ONLY>
 __device__ __forceinline__ void ld_v(const float *p, float (&v)[V])
@@ -125,6 +138,14 @@ __device__ __forceinline__ void st_v(float *p, const float (&v)[V])
     else if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
     else *p = v[0];
 }
+
+// 16-byte asynchronous copy global -> shared (cached in L2 only), and the wait for all of them
+__device__ __forceinline__ void cp_async16(float *dst_smem, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // x's bits deposited, lowest first, into the set bits of mask
 __device__ __host__ __forceinline__ unsigned deposit_bits(unsigned x, unsigned mask)
@@ -167,122 +188,187 @@ __device__ void sign_sweep(float *S, int n, const BGate &g)
     }
 }
 
-// One phase of a layer (k < 0) on a 2^n-amplitude state in shared memory.  Every qubit of the layer
-// gets its own 2x2 matrix and they all commute, so the layer runs in phases: lane p of a warp holds
-// in-block position p of the 2^R amplitudes that differ only in the phase's R high qubits (qpos,
-// ascending; their matrices at uhi) and agree with the warp's set s on the other bits -- scalar
-// shared-memory accesses, consecutive lanes on consecutive floats, no bank conflicts.  The high
-// qubits' gates run on register pairs; with `low` set the in-block qubits of the layer (lomask, their
-// matrices at ulo) run too, each pair exchanged between lanes by a warp shuffle; with `sign` the
-// gate's sign run applies as the amplitudes are loaded.
-template <int R>
-__device__ void layer_phase(float *S, int n, const BGate &g, const int (&qpos)[5], const float2 *__restrict__ uhi,
-                            unsigned lomask, const float2 *__restrict__ ulo, bool sign)
+// Register phases.  A phase record (k = -2; targets[0] = Q0, targets[1] = the number of records
+// that follow it) applies its records, in order, to a 2^L-amplitude tile in shared memory, every
+// thread holding in registers the 32 amplitudes that differ only in the window of local qubits
+// Q0..Q0+4 (slot m: window bits m):
+//   k = -3: a 2x2 matrix on window qubit targets[0] (U at mat_off, row-major, then X U X);
+//   k = -5: a real 2x2 matrix on window qubit targets[0] (R, then X R X: four floats each);
+//   k = -6: a diagonal over the tile's qubits that factors over them: amplitude i times
+//           C * prod_{q : i_q = 1} w_q, from tables at mat_off: 32 entries over the window bits,
+//           32 over the thread's first five non-window bits (times C), 16 over its next four;
+//   k = -4: a sign run (the fields of a sign run; lmask = the run's form on the window bits alone,
+//           targets[r] = the pair partners of window qubit r) -- the amplitudes it negates.
+// One shared-memory round trip then serves every gate and sign run of the phase, in registers whose
+// indices are compile-time constants.  Q0 >= 5: the lanes of a warp take consecutive in-block
+// positions, scalar accesses without bank conflicts.  Q0 = 0: a thread holds one block and reads it
+// as eight 16-byte chunks in the order j ^ k (k = its block index mod 8, so the eight threads of a
+// shared-memory access phase meet eight different chunks); slot m then holds window position
+// m ^ 4k, i.e. local index bp ^ m with bp = base | 4k, and a gate on a window qubit whose bit is
+// set in 4k runs with its two rows and columns exchanged (X U X).
+//
+// Sign runs in registers: the run's quadratic form q over GF(2) splits as
+// q(bp ^ y) = q(bp) ^ q0(y) ^ sum_r y_r * parity(bp & N_r) for y in the window (q0: q without the
+// constant), so a thread forms the 32 slot signs as one mask: the host's table of q0 on the window,
+// flipped as a whole by q(bp) and on the slots with bit r set by the parity of bp's partners of r.
+__host__ __device__ constexpr unsigned slot_bit(int r)   // slots m with bit r set
 {
-    constexpr int M = 1 << R;
-    const int lane = threadIdx.x & 31;
-    const unsigned nsets = 1u << (n - 5 - R);
-    unsigned hmask = 0u;   // the phase's high qubits
+    return r == 0 ? 0xAAAAAAAAu : r == 1 ? 0xCCCCCCCCu : r == 2 ? 0xF0F0F0F0u : r == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+constexpr int kPhaseMaxRecords = 48;   // records of one phase (a chunk holds it whole)
+
+template <int R>
+__device__ __forceinline__ void slot_gate(float (&xr)[32], float (&xi)[32], const float4 p, const float4 q)
+{
+    // p = (u00, u01), q = (u10, u11) as (re, im) pairs
 #pragma unroll
-    for (int r = 0; r < R; ++r) hmask |= 1u << qpos[r];
-    const unsigned cmask = ((1u << n) - 1u) & ~31u & ~hmask;   // the set's bits
-    const unsigned warps = blockDim.x >> 5;
-    for (unsigned s = threadIdx.x >> 5; s < nsets; s += warps) {
-        const unsigned base = deposit_bits(s, cmask) | (unsigned)lane;
-        float xr[M], xi[M];
+    for (int m = 0; m < 32; ++m) {
+        if ((m >> R) & 1) continue;
+        const int m1 = m | (1 << R);
+        const float ar = xr[m], ai = xi[m], br = xr[m1], bi = xi[m1];
+        xr[m] = fmaf(p.x, ar, fmaf(-p.y, ai, fmaf(p.z, br, -p.w * bi)));
+        xi[m] = fmaf(p.x, ai, fmaf(p.y, ar, fmaf(p.z, bi, p.w * br)));
+        xr[m1] = fmaf(q.x, ar, fmaf(-q.y, ai, fmaf(q.z, br, -q.w * bi)));
+        xi[m1] = fmaf(q.x, ai, fmaf(q.y, ar, fmaf(q.z, bi, q.w * br)));
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void slot_rot(float (&xr)[32], float (&xi)[32], const float4 u)
+{
+    // u = (a00, a01, a10, a11), real
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            unsigned i = base;
+    for (int m = 0; m < 32; ++m) {
+        if ((m >> R) & 1) continue;
+        const int m1 = m | (1 << R);
+        const float ar = xr[m], ai = xi[m], br = xr[m1], bi = xi[m1];
+        xr[m] = fmaf(u.x, ar, u.y * br);
+        xi[m] = fmaf(u.x, ai, u.y * bi);
+        xr[m1] = fmaf(u.z, ar, u.w * br);
+        xi[m1] = fmaf(u.z, ai, u.w * bi);
+    }
+}
+
+template <int Q0>
+__device__ void run_phase(float *S, int L, const BGate *ops, int nops, const float2 *U, int mb)
+{
+    static_assert(Q0 == 0 || Q0 >= 5, "windows start at qubit 0 or above the block");
+    const unsigned nb = 1u << (L - 5);
+    for (unsigned it = threadIdx.x; it < nb; it += blockDim.x) {
+        unsigned base, f = 0u;
+        if constexpr (Q0 == 0) {
+            base = it << 5;
+            f = (it & 7u) << 2;
+        } else {
+            base = (it & ((1u << Q0) - 1u)) | ((it >> Q0) << (Q0 + 5));
+        }
+        const unsigned bp = base | f;
+        const unsigned ob = ((base >> 5) << 6) | (base & 31u);
+        float xr[32], xi[32];
+        if constexpr (Q0 == 0) {
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                if ((m >> r) & 1) i |= 1u << qpos[r];
-            const unsigned o = ((i >> 5) << 6) | (i & 31u);
-            xr[m] = S[o];
-            xi[m] = S[o + 32];
-            if (sign && sign_odd(g, i)) {
-                xr[m] = -xr[m];
-                xi[m] = -xi[m];
+            for (int j = 0; j < 8; ++j) {
+                const unsigned o = ob + ((unsigned)(4 * j) ^ f);
+                const float4 re = *reinterpret_cast<const float4 *>(S + o), im = *reinterpret_cast<const float4 *>(S + o + 32);
+                xr[4 * j] = re.x; xr[4 * j + 1] = re.y; xr[4 * j + 2] = re.z; xr[4 * j + 3] = re.w;
+                xi[4 * j] = im.x; xi[4 * j + 1] = im.y; xi[4 * j + 2] = im.z; xi[4 * j + 3] = im.w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                xr[m] = S[ob + ((unsigned)m << (Q0 + 1))];
+                xi[m] = S[ob + 32 + ((unsigned)m << (Q0 + 1))];
             }
         }
-        // high qubits: pairs of registers
+        for (int t = 0; t < nops; ++t) {
+            const BGate &g = ops[t];
+            if (g.k == -5) {
+                const int r = g.targets[0];
+                const unsigned flip = Q0 == 0 ? (f >> r) & 1u : 0u;
+                const float4 u = *reinterpret_cast<const float4 *>(U + (g.mat_off - mb) + 2 * (int)flip);
+                switch (r) {
+                case 0: slot_rot<0>(xr, xi, u); break;
+                case 1: slot_rot<1>(xr, xi, u); break;
+                case 2: slot_rot<2>(xr, xi, u); break;
+                case 3: slot_rot<3>(xr, xi, u); break;
+                default: slot_rot<4>(xr, xi, u); break;
+                }
+            } else if (g.k == -6) {
+                // diagonal: the thread's factor (its non-window bits are it) times the slot's
+                const float2 *T = U + (g.mat_off - mb);
+                const float2 ta = T[32 + (it & 31u)], tb = T[64 + (it >> 5)];
+                const float tr = ta.x * tb.x - ta.y * tb.y, ti = ta.x * tb.y + ta.y * tb.x;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float2 u00 = uhi[4 * r], u01 = uhi[4 * r + 1], u10 = uhi[4 * r + 2], u11 = uhi[4 * r + 3];
+                for (int m = 0; m < 32; m += 2) {
+                    // entries m ^ f and (m + 1) ^ f are adjacent (f is a multiple of 4): one 16-byte read
+                    const float4 sl = *reinterpret_cast<const float4 *>(T + ((unsigned)m ^ f));
+                    asm volatile("" ::: "memory");   // one table read at a time: no hoisting into registers
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                if ((m >> r) & 1) continue;
-                const int m1 = m | (1 << r);
-                const float ar = xr[m], ai = xi[m], br = xr[m1], bi = xi[m1];
-                xr[m] = u00.x * ar - u00.y * ai + u01.x * br - u01.y * bi;
-                xi[m] = u00.x * ai + u00.y * ar + u01.x * bi + u01.y * br;
-                xr[m1] = u10.x * ar - u10.y * ai + u11.x * br - u11.y * bi;
-                xi[m1] = u10.x * ai + u10.y * ar + u11.x * bi + u11.y * br;
+                    for (int h = 0; h < 2; ++h) {
+                        const float sx = h ? sl.z : sl.x, sy = h ? sl.w : sl.y;
+                        const float fr = tr * sx - ti * sy, fi = tr * sy + ti * sx;
+                        const float ar = xr[m + h], ai = xi[m + h];
+                        xr[m + h] = ar * fr - ai * fi;
+                        xi[m + h] = ar * fi + ai * fr;
+                    }
+                }
+            } else if (g.k == -3) {
+                const int r = g.targets[0];
+                const unsigned flip = Q0 == 0 ? (f >> r) & 1u : 0u;
+                const float4 *u = reinterpret_cast<const float4 *>(U + (g.mat_off - mb) + 4 * (int)flip);
+                const float4 p = u[0], q = u[1];
+                switch (r) {
+                case 0: slot_gate<0>(xr, xi, p, q); break;
+                case 1: slot_gate<1>(xr, xi, p, q); break;
+                case 2: slot_gate<2>(xr, xi, p, q); break;
+                case 3: slot_gate<3>(xr, xi, p, q); break;
+                default: slot_gate<4>(xr, xi, p, q); break;
+                }
+            } else {
+                unsigned par = g.gsign + (unsigned)__popc(bp & g.zmask);
+                for (int d = 0; d < g.nd; ++d) par += (unsigned)__popc(bp & (bp >> g.dist[d]) & g.dmask[d]);
+                unsigned sm = g.lmask ^ (0u - (par & 1u));
+#pragma unroll
+                for (int r = 0; r < 5; ++r) sm ^= (0u - ((unsigned)__popc(bp & (unsigned)g.targets[r]) & 1u)) & slot_bit(r);
+#pragma unroll
+                for (int m = 0; m < 32; ++m) {
+                    const unsigned sb = (sm << (31 - m)) & 0x80000000u;
+                    xr[m] = __uint_as_float(__float_as_uint(xr[m]) ^ sb);
+                    xi[m] = __uint_as_float(__float_as_uint(xi[m]) ^ sb);
+                }
             }
         }
-        // in-block qubits: the partner amplitude lives in lane p ^ 2^q
-        int t = 0;
-        for (unsigned lm = lomask; lm; lm &= lm - 1u, ++t) {
-            const int q = __ffs((int)lm) - 1;
-            const bool hi_half = (lane >> q) & 1;
-            // own coefficient and partner coefficient of this lane's output row
-            const float2 a = hi_half ? ulo[4 * t + 3] : ulo[4 * t], b = hi_half ? ulo[4 * t + 2] : ulo[4 * t + 1];
+        if constexpr (Q0 == 0) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const float pr = __shfl_xor_sync(0xffffffffu, xr[m], 1 << q);
-                const float pi = __shfl_xor_sync(0xffffffffu, xi[m], 1 << q);
-                const float yr = a.x * xr[m] - a.y * xi[m] + b.x * pr - b.y * pi;
-                const float yi = a.x * xi[m] + a.y * xr[m] + b.x * pi + b.y * pr;
-                xr[m] = yr;
-                xi[m] = yi;
+            for (int j = 0; j < 8; ++j) {
+                const unsigned o = ob + ((unsigned)(4 * j) ^ f);
+                *reinterpret_cast<float4 *>(S + o) = make_float4(xr[4 * j], xr[4 * j + 1], xr[4 * j + 2], xr[4 * j + 3]);
+                *reinterpret_cast<float4 *>(S + o + 32) = make_float4(xi[4 * j], xi[4 * j + 1], xi[4 * j + 2], xi[4 * j + 3]);
             }
-        }
+        } else {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            unsigned i = base;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if ((m >> r) & 1) i |= 1u << qpos[r];
-            const unsigned o = ((i >> 5) << 6) | (i & 31u);
-            S[o] = xr[m];
-            S[o + 32] = xi[m];
+            for (int m = 0; m < 32; ++m) {
+                S[ob + ((unsigned)m << (Q0 + 1))] = xr[m];
+                S[ob + 32 + ((unsigned)m << (Q0 + 1))] = xi[m];
+            }
         }
     }
 }
 
-// A layer: its high qubits (local bit >= 5) in phases of up to MAXR (five; four in the 512-thread
-// form, whose 128-register budget holds 2 x 16 amplitudes), the first phase also taking the
-// in-block qubits (shuffles) and the sign run; a barrier between phases.
-template <int MAXR>
-__device__ void apply_layer(float *S, int n, const BGate &g, const float2 *__restrict__ U)
+// The records ops[0, nops) of a phase whose window starts at local qubit q0 (0, 5 or L - 5 for
+// tiles of L = 10..14 qubits: the start picks the compiled form); U holds the chunk's matrices,
+// the first at offset mb of the stage matrix table.  Not inlined: the phase's 64 amplitude
+// registers get the register file to themselves, the caller's state is saved once per call.
+__device__ __noinline__ void apply_phase(float *S, int L, int q0, const BGate *ops, int nops, const float2 *U, int mb)
 {
-    const unsigned lo = g.lmask & 31u;
-    unsigned hi = g.lmask & ~31u;
-    const int nlo = __popc(lo);
-    const float2 *uhi = U + 4 * nlo;   // matrices ascending by qubit: the in-block ones first
-    bool first = true;
-    do {
-        int qpos[5] = {0, 0, 0, 0, 0};
-        int r = 0;
-        while (hi && r < MAXR && r < n - 5) {
-            qpos[r++] = __ffs((int)hi) - 1;
-            hi &= hi - 1u;
-        }
-        const unsigned lom = first ? lo : 0u;
-        const bool sg = first && (g.nd | g.zmask | g.gsign);
-        switch (r) {
-        case 0: layer_phase<0>(S, n, g, qpos, uhi, lom, U, sg); break;
-        case 1: layer_phase<1>(S, n, g, qpos, uhi, lom, U, sg); break;
-        case 2: layer_phase<2>(S, n, g, qpos, uhi, lom, U, sg); break;
-        case 3: layer_phase<3>(S, n, g, qpos, uhi, lom, U, sg); break;
-        case 4: layer_phase<4>(S, n, g, qpos, uhi, lom, U, sg); break;
-        default:
-            if constexpr (MAXR >= 5) layer_phase<5>(S, n, g, qpos, uhi, lom, U, sg);
-            break;
-        }
-        uhi += 4 * r;
-        first = false;
-        if (hi) __syncthreads();   // this phase's writes before the next phase's reads
-    } while (hi);
+    switch (q0) {
+    case 0: run_phase<0>(S, L, ops, nops, U, mb); break;
+    case 5: run_phase<5>(S, L, ops, nops, U, mb); break;
+    case 6: run_phase<6>(S, L, ops, nops, U, mb); break;
+    case 7: run_phase<7>(S, L, ops, nops, U, mb); break;
+    case 8: run_phase<8>(S, L, ops, nops, U, mb); break;
+    default: run_phase<9>(S, L, ops, nops, U, mb); break;
+    }
 }
 
 // Apply one fused gate of K qubits to groups [g_begin, g_end) of the state S (shared or global)
@@ -491,8 +577,12 @@ __device__ __forceinline__ void zero_floats(float *S, long long f0, long long f1
         reinterpret_cast<float4 *>(S)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
+// Three compiled forms: <256, 1> CTAs of at most 256 threads with up to 255 registers a thread
+// (WIDE: 4-qubit gates may move several groups per access), <512, 1> and <256, 2> (two CTAs on an
+// SM: 128 registers a thread, so that one CTA's loads, waits and barriers overlap the other's
+// arithmetic).
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
 {
     extern __shared__ __align__(16) float smem[];
     float2 *sU = reinterpret_cast<float2 *>(smem);                  // matrix area: A.mat_cap complex
@@ -500,44 +590,47 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
     float *sS = smem + 2 * A.mat_cap + A.gate_cap * (int)(sizeof(BGate) / 4);   // circuit state or tile
     __shared__ int cur;
     __shared__ int ok;
+    __shared__ BItem sW;          // the current item: fields are read where used (no long-lived registers)
     __shared__ unsigned sT[96];   // staged tiles: deposits of local index bits 3-8 ([0, 64)) and 9-13
     for (;;) {
         if (threadIdx.x == 0) cur = (int)atomicAdd(reinterpret_cast<unsigned *>(A.sync), 1u);
         __syncthreads();
         const int it = cur;
+        if (it < A.n_items && threadIdx.x < (int)(sizeof(BItem) / 16))
+            reinterpret_cast<int4 *>(&sW)[threadIdx.x] = reinterpret_cast<const int4 *>(A.items + it)[threadIdx.x];
         __syncthreads();
         if (it >= A.n_items) break;
-        const BItem W = A.items[it];
-        const BCirc C = A.circ[W.c];
-        float *G = A.arena + C.state_off;
-        const long long nf = state_floats(C.n);
+        const BItem &W = sW;
         if (W.kind == kStage) {
-            int *done = A.sync + 2 + C.done_off;
-            const BStage St = A.stages[C.stage_begin + W.step];
-            const int L = C.n < A.stage_log2 ? C.n : A.stage_log2;   // tile qubits (>= 8)
-            const unsigned hmask = ((1u << C.n) - 1u) & ~St.lmask;
+            int *done = A.sync + 2 + W.done_off;
+            float *G = A.arena + W.state_off;
+            const int L = W.n < A.stage_log2 ? W.n : A.stage_log2;   // tile qubits (>= 8)
+            const unsigned hmask = ((1u << W.n) - 1u) & ~W.lmask;
             const unsigned tb = deposit_bits((unsigned)W.tile, hmask);   // the tile's fixed bits
-            // a chunk's gate descriptors and matrices into shared memory (the first chunk's copy
-            // overlaps the wait and the tile load)
-            auto load_chunk = [&](int ci) -> BChunk {
-                const BChunk ch = A.chunks[St.chunk_begin + ci];
-                const int *src = reinterpret_cast<const int *>(A.sgates + ch.gate_begin);
-                int *dst = reinterpret_cast<int *>(sG);
-                for (int i = threadIdx.x; i < ch.gate_count * (int)(sizeof(BGate) / 4); i += blockDim.x) dst[i] = src[i];
-                for (int i = threadIdx.x; i < ch.mat_count; i += blockDim.x) sU[i] = A.smats[ch.mat_begin + i];
-                return ch;
+            // a chunk's gate descriptors and matrices into shared memory, 16 bytes at a time (the
+            // first chunk's copy overlaps the wait and the tile load)
+            auto load_chunk = [&](const BChunk &c) {
+                const int4 *src = reinterpret_cast<const int4 *>(A.sgates + c.gate_begin);
+                int4 *dst = reinterpret_cast<int4 *>(sG);
+                const int nv = c.gate_count * (int)(sizeof(BGate) / 16);
+                for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
+                const float4 *ms = reinterpret_cast<const float4 *>(A.smats + c.mat_begin);
+                float4 *md = reinterpret_cast<float4 *>(sU);
+                for (int i = threadIdx.x; i < (c.mat_count + 1) / 2; i += blockDim.x) md[i] = ms[i];
             };
-            BChunk ch{};
-            if (St.chunk_count > 0) ch = load_chunk(0);
-            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, A.need[C.done_off + W.step - 1]);
+            BChunk ch = W.ch0;
+            if (W.chunk_count > 0) load_chunk(ch);
+            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, W.need_prev);
             for (unsigned i = threadIdx.x; i < 96u; i += blockDim.x)
-                sT[i] = i < 64u ? deposit_bits(i << 3, St.lmask) : deposit_bits((i - 64u) << 9, St.lmask);
+                sT[i] = i < 64u ? deposit_bits(i << 3, W.lmask) : deposit_bits((i - 64u) << 9, W.lmask);
             __syncthreads();
             if (!ok) break;
             // local index l -> global index: bits 0-2 stay (S holds qubits 0-2), the rest deposit
             // into S's higher qubits, the tile's bits fill the others.  A thread moves four
             // amplitudes (16 bytes of real and of imaginary parts) at a time; eight consecutive
-            // local indices are one 32-byte run in global memory.
+            // local indices are one 32-byte run in global memory.  The tile loads by asynchronous
+            // copies straight into shared memory (through L2: other CTAs wrote it in the previous
+            // stage), all of a thread's copies in flight at once.
             const int nq = 1 << (L - 2);
             auto gofs = [&](unsigned l) -> unsigned {
                 const unsigned gi = (l & 7u) | sT[(l >> 3) & 63u] | sT[64 + (l >> 9)] | tb;
@@ -549,32 +642,41 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                 if (W.tile == 0 && threadIdx.x == 0) sS[0] = 1.f;
             } else {
                 for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                    const unsigned l = (unsigned)q << 2;
-                    const unsigned go = gofs(l), lo = ((l >> 5) << 6) | (l & 31u);
-                    // read through L2: other CTAs wrote these in the previous stage
-                    const float4 re = __ldcg(reinterpret_cast<const float4 *>(G + go));
-                    const float4 im = __ldcg(reinterpret_cast<const float4 *>(G + go + 32));
-                    *reinterpret_cast<float4 *>(sS + lo) = re;
-                    *reinterpret_cast<float4 *>(sS + lo + 32) = im;
+                    const unsigned l = (unsigned)q << 2, lo = ((l >> 5) << 6) | (l & 31u);
+                    const unsigned go = gofs(l);
+                    cp_async16(sS + lo, G + go);
+                    cp_async16(sS + lo + 32, G + go + 32);
                 }
+                cp_async_wait_all();
             }
             __syncthreads();
-            for (int ci = 0; ci < St.chunk_count; ++ci) {
+            for (int ci = 0; ci < W.chunk_count; ++ci) {
                 if (ci > 0) {   // the previous chunk's last gate ended with a barrier
-                    ch = load_chunk(ci);
+                    ch = A.chunks[W.chunk_begin + ci];
+                    load_chunk(ch);
                     __syncthreads();
                 }
                 for (int gi = 0; gi < ch.gate_count; ++gi) {
                     const BGate &g = sG[gi];   // read in place: the sign fields stay in shared memory
-                    if (g.k < 0) apply_layer<(MAXT <= 256 ? 5 : 4)>(sS, L, g, sU + (g.mat_off - ch.mat_begin));
-                    else if (g.k == 0) sign_sweep(sS, L, g);
-                    else apply_gate_cta<false, (MAXT <= 256), true, true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
+                    if (g.k < 0) {   // a phase and its records
+                        const int q0 = g.targets[0];
+                        apply_phase(sS, L, q0, sG + gi + 1, g.targets[1], sU, ch.mat_begin);
+                        gi += g.targets[1];
+                        // windows at 0 and 5: a warp holds the same 1024 amplitudes (local bits 0-9)
+                        // in both, so when the next record of this chunk is such a phase too, the
+                        // warp reads only what it wrote itself
+                        if (q0 <= 5 && gi + 1 < ch.gate_count && sG[gi + 1].k == -2 && sG[gi + 1].targets[0] <= 5) {
+                            __syncwarp();
+                            continue;
+                        }
+                    } else if (g.k == 0) sign_sweep(sS, L, g);
+                    else apply_gate_cta<false, (MAXT <= 256 && MINB == 1), true, true>(sS, L, g, sU + (g.mat_off - ch.mat_begin), 0u, 1u << (L - g.k));
                     __syncthreads();   // this gate's writes before the next gate's reads
                 }
             }
             for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                const unsigned l = (unsigned)q << 2;
-                const unsigned go = gofs(l), lo = ((l >> 5) << 6) | (l & 31u);
+                const unsigned l = (unsigned)q << 2, lo = ((l >> 5) << 6) | (l & 31u);
+                const unsigned go = gofs(l);
                 *reinterpret_cast<float4 *>(G + go) = *reinterpret_cast<const float4 *>(sS + lo);
                 *reinterpret_cast<float4 *>(G + go + 32) = *reinterpret_cast<const float4 *>(sS + lo + 32);
             }
@@ -585,6 +687,9 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
             }
             continue;
         }
+        const BCirc C = A.circ[W.c];
+        float *G = A.arena + C.state_off;
+        const long long nf = state_floats(C.n);
         if (W.kind != kTile) {
             // whole circuit in one CTA: shared memory or the global buffer
             float *S = W.kind == kWhole ? sS : G;
@@ -595,8 +700,8 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
                 const BGate g = A.gates[C.gate_begin + gi];
                 stage_matrix(sU, A.mats, g);
                 __syncthreads();   // matrix staged; previous gate's writes visible
-                if (W.kind == kWhole) apply_gate_cta<false, (MAXT <= 256), true, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
-                else apply_gate_cta<false, (MAXT <= 256), false, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                if (W.kind == kWhole) apply_gate_cta<false, (MAXT <= 256 && MINB == 1), true, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
+                else apply_gate_cta<false, (MAXT <= 256 && MINB == 1), false, false>(S, C.n, g, sU, 0u, 1u << (C.n - g.k));
                 __syncthreads();
             }
             if (W.kind == kWhole) {
@@ -624,7 +729,7 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(BatchArgs A)
             const unsigned groups = 1u << (C.n - g.k);
             const unsigned g0 = (unsigned)W.tile << A.tile_log2;
             const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
-            apply_gate_cta<true, (MAXT <= 256), false, false>(G, C.n, g, sU, g0, g1);
+            apply_gate_cta<true, (MAXT <= 256 && MINB == 1), false, false>(G, C.n, g, sU, g0, g1);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -670,7 +775,7 @@ struct sv_batch {
     bool list_stall = false;
     sv_batch_opts opts{};
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int graph_cfg[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -764,6 +869,42 @@ struct SignRun {
             }
     }
 };
+// A 2x2 unitary as U = P R Q: P = diag(p0, p1), R = (c, -s; s, c) real with c = |u00| and s = |u10|,
+// Q = diag(1, q1).  With U = e^(i phi) (x, -conj(y); y, conj(x)): p0 = u00 / |u00|, p1 = u10 / |u10|,
+// q1 = -u01 / (|u01| p0) (a zero column entry takes the other entry of its row's phase).  False when
+// the factors do not give back U to 1e-9 (a matrix that is not unitary).
+bool factor_prq(const std::array<cplx, 4> &U, cplx &p0, cplx &p1, double &c, double &s, cplx &q1)
+{
+    const double a = std::abs(U[0]), b = std::abs(U[1]), cc = std::abs(U[2]), d = std::abs(U[3]);
+    constexpr double kTiny = 1e-12;
+    auto unit = [](const cplx &z) { return z / std::abs(z); };
+    c = a;
+    s = cc;
+    if (cc <= kTiny && b <= kTiny) {   // diagonal
+        if (a <= kTiny || d <= kTiny) return false;
+        p0 = unit(U[0]);
+        p1 = unit(U[3]);
+        q1 = 1.0;
+        s = 0.0;
+        c = 1.0;
+    } else if (a <= kTiny && d <= kTiny) {   // anti-diagonal
+        p0 = -unit(U[1]);
+        p1 = unit(U[2]);
+        q1 = 1.0;
+        c = 0.0;
+        s = 1.0;
+    } else {
+        if (a <= kTiny || cc <= kTiny || b <= kTiny) return false;
+        p0 = unit(U[0]);
+        p1 = unit(U[2]);
+        q1 = -unit(U[1]) / p0;
+    }
+    const cplx r[4] = {p0 * c, -p0 * s * q1, p1 * s, p1 * c * q1};
+    for (int e = 0; e < 4; ++e)
+        if (std::abs(r[e] - U[(size_t)e]) > 1e-9) return false;
+    return true;
+}
+
 constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
 
 // Cut circuit gates gs (global targets, n qubits) into stages of at most L local qubits and append
@@ -773,7 +914,7 @@ constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
 // past every gate it overtakes) and the stage's qubits with its own still number at most L;
 // otherwise its qubits are closed for the rest of the scan.  The local set is then filled up to
 // L qubits with the lowest unused ones (longer contiguous runs per tile).
-void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, bool layers, std::vector<BStage> &st,
+void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, bool phase_opt, std::vector<BStage> &st,
                   std::vector<BChunk> &chunks, std::vector<BGate> &sg, std::vector<float2> &sm)
 {
     std::vector<const FusedGate *> rest = gs;
@@ -797,6 +938,12 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         bs.lmask = S;
         bs.chunk_begin = (int)chunks.size();
         auto local = [&](int q) { return __builtin_popcount(S & ((1u << q) - 1u)); };
+        // a chunk's matrices start at an even offset of the table (16-byte copies)
+        auto new_chunk = [&]() {
+            if (sm.size() & 1) sm.push_back(make_float2(0.f, 0.f));
+            chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
+        };
+        const bool phases = phase_opt && L >= 10;
         // per gate: U then its pair-swapped copy U' (U'[r][j] = U[r][j ^ 1]), starting at an even
         // offset of the chunk (16-byte aligned in shared memory); a sign run rides on the gate
         // (k = 0: a sign-only sweep)
@@ -804,7 +951,7 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
             const int dd = g ? (int)g->ur.size() : 0;
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
                 chunks.back().mat_count + 1 + 2 * dd > kStageMatCap)
-                chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
+                new_chunk();
             if (chunks.back().mat_count & 1) {
                 sm.push_back(make_float2(0.f, 0.f));
                 chunks.back().mat_count += 1;
@@ -830,47 +977,8 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         SignRun run;
         std::vector<const FusedGate *> dense_run;
         uint64_t dense_q = 0;
-        // a run of one-qubit gates as one layer: per qubit the product of its gates, in order
-        auto emit_layer = [&](const SignRun &r) {
-            std::vector<std::array<cplx, 4>> U(32);
-            unsigned lm = 0u;
-            for (const FusedGate *g : dense_run) {
-                const int q = local(g->targets[0]);
-                const cplx *G = g->mat.data();
-                std::array<cplx, 4> &P = U[(size_t)q];
-                if (!((lm >> q) & 1u)) {
-                    P = {G[0], G[1], G[2], G[3]};
-                    lm |= 1u << q;
-                } else {
-                    P = {G[0] * P[0] + G[1] * P[2], G[0] * P[1] + G[1] * P[3], G[2] * P[0] + G[3] * P[2], G[2] * P[1] + G[3] * P[3]};
-                }
-            }
-            const int dd = 4 * __builtin_popcount(lm);
-            if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
-                chunks.back().mat_count + 1 + dd > kStageMatCap)
-                chunks.push_back(BChunk{(int)sg.size(), 0, (int)sm.size(), 0});
-            if (chunks.back().mat_count & 1) {
-                sm.push_back(make_float2(0.f, 0.f));
-                chunks.back().mat_count += 1;
-            }
-            BGate b{};
-            r.fill(b);
-            b.k = -1;
-            b.lmask = lm;
-            b.mat_off = (int)sm.size();
-            for (int q = 0; q < 32; ++q)
-                if ((lm >> q) & 1u)
-                    for (int e = 0; e < 4; ++e) sm.push_back(make_float2((float)U[(size_t)q][e].real(), (float)U[(size_t)q][e].imag()));
-            sg.push_back(b);
-            chunks.back().gate_count += 1;
-            chunks.back().mat_count += dd;
-        };
         auto flush = [&]() {
-            bool one_qubit = layers && !dense_run.empty();
-            for (const FusedGate *g : dense_run) one_qubit = one_qubit && g->k == 1;
-            if (one_qubit) {
-                emit_layer(run);
-            } else if (!dense_run.empty()) {
+            if (!dense_run.empty()) {
                 std::vector<FusedGate> fused;
                 if (stage_k > 0) fused = refuse_gates(dense_run, n, stage_k);
                 for (size_t i = 0; i < (stage_k > 0 ? fused.size() : dense_run.size()); ++i) {
@@ -887,17 +995,264 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
             dense_run.clear();
             dense_q = 0;
         };
+        // Register phases (tiles of at least 10 qubits).  A run of one-qubit gates is a layer: per
+        // qubit the product of its gates, in order; the layers and the sign runs between them go
+        // into phases over windows of five local qubits starting at 0, 5 and L - 5.  A layer's
+        // gates all commute, so its windows may run in any order: it starts with the open phase's
+        // window when it has gates there (the sign run before it and its first window's gates join
+        // that phase) and ends on the far side, where the next layer starts.  A sign run joins the
+        // open phase (or waits for the next one).
+        //
+        // Each qubit's 2x2 unitary is factored U = P R Q (P, Q diagonal, R a real rotation; see
+        // factor_prq): the layer runs as real rotations, 4 multiply-adds per amplitude instead of
+        // 8, and one layer's P's with the next layer's Q's -- all diagonal, all commuting with the
+        // sign run between the layers -- become one diagonal over the tile's qubits, applied
+        // right before the next layer's first rotation (a complex factor per amplitude).
+        const int nwin = L > 10 ? 3 : 2;
+        const int q0s[3] = {0, 5, L - 5};
+        enum : int { kSubGate = 0, kSubSign = 1, kSubRot = 2, kSubDiag = 3 };
+        using Diag = std::array<std::array<cplx, 2>, 32>;   // per local qubit: its diagonal (d0, d1)
+        struct Sub {
+            int kind;
+            int r;
+            std::array<cplx, 4> U;      // kSubGate: the matrix; kSubRot: (c, -s, s, c) in the real parts
+            SignRun s;
+            Diag D;
+        };
+        auto unit_diag = []() {
+            Diag d;
+            for (auto &e : d) e = {cplx(1.0), cplx(1.0)};
+            return d;
+        };
+        int open_w = -1;
+        std::vector<Sub> open_subs;
+        std::vector<SignRun> pending;
+        Diag pend_p = unit_diag();   // the last layer's P's, not yet applied
+        bool pend_p_set = false;
+        auto emit_phase = [&]() {
+            if (open_w < 0) return;
+            int nm = 0;   // float2 of matrices
+            for (const Sub &u : open_subs) nm += u.kind == kSubGate ? 8 : u.kind == kSubRot ? 4 : u.kind == kSubDiag ? 80 : 0;
+            const int recs = 1 + (int)open_subs.size();
+            if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count + recs > kStageGateCap ||
+                chunks.back().mat_count + 1 + nm > kStageMatCap)
+                new_chunk();
+            if (chunks.back().mat_count & 1) {
+                sm.push_back(make_float2(0.f, 0.f));
+                chunks.back().mat_count += 1;
+            }
+            const int q0 = q0s[open_w];
+            BGate h{};
+            h.k = -2;
+            h.targets[0] = q0;
+            h.targets[1] = recs - 1;
+            sg.push_back(h);
+            auto f2 = [](const cplx &c) { return make_float2((float)c.real(), (float)c.imag()); };
+            for (const Sub &u : open_subs) {
+                BGate b{};
+                if (u.kind == kSubGate) {
+                    b.k = -3;
+                    b.targets[0] = u.r;
+                    b.mat_off = (int)sm.size();
+                    for (int e = 0; e < 4; ++e) sm.push_back(f2(u.U[(size_t)e]));
+                    for (int e = 0; e < 4; ++e) sm.push_back(f2(u.U[(size_t)(3 - e)]));   // X U X
+                } else if (u.kind == kSubRot) {
+                    b.k = -5;
+                    b.targets[0] = u.r;
+                    b.mat_off = (int)sm.size();
+                    const float a00 = (float)u.U[0].real(), a01 = (float)u.U[1].real(), a10 = (float)u.U[2].real(),
+                                a11 = (float)u.U[3].real();
+                    sm.push_back(make_float2(a00, a01));
+                    sm.push_back(make_float2(a10, a11));
+                    sm.push_back(make_float2(a11, a10));   // X R X
+                    sm.push_back(make_float2(a01, a00));
+                } else if (u.kind == kSubDiag) {
+                    // amplitude i gets C * prod over set bits q of i of w_q (w_q = d1 / d0, C = prod
+                    // of the d0): tables over the window's 5 bits (slot), the thread's first 5
+                    // non-window bits (with C) and its next 4 -- a thread's non-window bits are its
+                    // phase index it, bit j of it being the j-th non-window qubit, ascending
+                    b.k = -6;
+                    b.mat_off = (int)sm.size();
+                    cplx C(1.0);
+                    std::array<cplx, 32> w;
+                    for (int q = 0; q < 32; ++q) {
+                        C *= u.D[(size_t)q][0];
+                        w[(size_t)q] = u.D[(size_t)q][1] / u.D[(size_t)q][0];
+                    }
+                    int nw[9], nn = 0;
+                    for (int q = 0; q < L && nn < 9; ++q)
+                        if (q < q0 || q >= q0 + 5) nw[nn++] = q;
+                    for (int x = 0; x < 32; ++x) {
+                        cplx t(1.0);
+                        for (int r = 0; r < 5; ++r)
+                            if ((x >> r) & 1) t *= w[(size_t)(q0 + r)];
+                        sm.push_back(f2(t));
+                    }
+                    for (int x = 0; x < 32; ++x) {
+                        cplx t = C;
+                        for (int j = 0; j < 5 && j < nn; ++j)
+                            if ((x >> j) & 1) t *= w[(size_t)nw[j]];
+                        sm.push_back(f2(t));
+                    }
+                    for (int x = 0; x < 16; ++x) {
+                        cplx t(1.0);
+                        for (int j = 0; j < 4 && 5 + j < nn; ++j)
+                            if ((x >> j) & 1) t *= w[(size_t)nw[5 + j]];
+                        sm.push_back(f2(t));
+                    }
+                } else {
+                    u.s.fill(b);
+                    b.k = -4;
+                    unsigned qw = 0u;   // the form on the window bits alone, per slot
+                    for (unsigned m = 0; m < 32u; ++m) {
+                        const unsigned y = m << q0;
+                        unsigned par = (unsigned)__builtin_popcount(y & u.s.zmask);
+                        for (const auto &pr : u.s.pairs) par += (unsigned)__builtin_popcount(y & (y >> pr.first) & pr.second);
+                        qw |= (par & 1u) << m;
+                    }
+                    b.lmask = qw;
+                    for (int r = 0; r < 5; ++r) {   // pair partners of window qubit r
+                        const int c = q0 + r;
+                        unsigned nb = 0u;
+                        for (const auto &pr : u.s.pairs) {
+                            if (c >= pr.first && ((pr.second >> (c - pr.first)) & 1u)) nb |= 1u << (c - pr.first);
+                            if ((pr.second >> c) & 1u) nb |= 1u << (c + pr.first);
+                        }
+                        b.targets[r] = (int)nb;
+                    }
+                }
+                sg.push_back(b);
+            }
+            chunks.back().gate_count += recs;
+            chunks.back().mat_count += nm;
+            open_w = -1;
+            open_subs.clear();
+        };
+        auto open_phase = [&](int w) {
+            emit_phase();
+            open_w = w;
+            for (const SignRun &r : pending) open_subs.push_back(Sub{kSubSign, 0, {}, r, {}});
+            pending.clear();
+        };
+        auto add_sub = [&](Sub u) {
+            if ((int)open_subs.size() + 2 > kPhaseMaxRecords) open_phase(open_w);
+            open_subs.push_back(std::move(u));
+        };
+        auto add_signs = [&](const SignRun &r) {
+            if (r.empty()) return;
+            if (open_w >= 0) add_sub(Sub{kSubSign, 0, {}, r, {}});
+            else pending.push_back(r);
+        };
+        auto add_layer = [&]() {
+            std::array<std::array<cplx, 4>, 32> U{};
+            unsigned lm = 0u;
+            for (const FusedGate *g : dense_run) {
+                const int q = local(g->targets[0]);
+                const cplx *G = g->mat.data();
+                std::array<cplx, 4> &P = U[(size_t)q];
+                if (!((lm >> q) & 1u)) {
+                    P = {G[0], G[1], G[2], G[3]};
+                    lm |= 1u << q;
+                } else {
+                    P = {G[0] * P[0] + G[1] * P[2], G[0] * P[1] + G[1] * P[3], G[2] * P[0] + G[3] * P[2], G[2] * P[1] + G[3] * P[3]};
+                }
+            }
+            // factors: the diagonal before the rotations (pending P's times this layer's Q's) and
+            // the P's left pending; a matrix that does not factor stays a complex gate
+            Diag E = pend_p;
+            bool e_set = pend_p_set;
+            pend_p = unit_diag();
+            pend_p_set = false;
+            std::array<bool, 32> rot{};
+            for (int q = 0; q < L; ++q) {
+                if (!((lm >> q) & 1u)) continue;
+                cplx p0, p1, q1;
+                double c, sn;
+                if (factor_prq(U[(size_t)q], p0, p1, c, sn, q1)) {
+                    rot[(size_t)q] = true;
+                    U[(size_t)q] = {cplx(c), cplx(-sn), cplx(sn), cplx(c)};
+                    E[(size_t)q][1] *= q1;
+                    pend_p[(size_t)q] = {p0, p1};
+                    e_set = true;
+                    pend_p_set = true;
+                }
+            }
+            // windows: qubits 0-4 in the first, 10 and up in the last; L - 5..9 in either
+            unsigned need[3] = {0u, 0u, 0u}, flex = 0u;
+            for (int q = 0; q < L; ++q) {
+                if (!((lm >> q) & 1u)) continue;
+                if (q < 5) need[0] |= 1u << q;
+                else if (nwin == 3 && q >= 10) need[2] |= 1u << q;
+                else if (nwin == 3 && q >= L - 5) flex |= 1u << q;
+                else need[1] |= 1u << q;
+            }
+            if (flex) {
+                const int w = need[2] ? 2 : need[1] ? 1 : open_w == 2 ? 2 : 1;
+                need[w] |= flex;
+            }
+            int order[3], no = 0;
+            const bool open_in = open_w >= 0 && need[open_w] != 0u;
+            if (open_in) {
+                order[no++] = open_w;
+                if (open_w == nwin - 1) {
+                    for (int w = nwin - 2; w >= 0; --w)
+                        if (need[w]) order[no++] = w;
+                } else {
+                    for (int w = 0; w < nwin; ++w)
+                        if (w != open_w && need[w]) order[no++] = w;
+                }
+            } else {
+                for (int w = 0; w < nwin; ++w)
+                    if (need[w]) order[no++] = w;
+            }
+            for (int i = 0; i < no; ++i) {
+                const int w = order[i];
+                if (!(i == 0 && open_in)) open_phase(w);
+                if (i == 0 && e_set) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, E});
+                for (unsigned m = need[w]; m; m &= m - 1u) {
+                    const int q = __builtin_ctz(m);
+                    add_sub(Sub{rot[(size_t)q] ? kSubRot : kSubGate, q - q0s[w], U[(size_t)q], SignRun{}, {}});
+                }
+            }
+        };
+        auto flush_phases = [&]() {   // before a gate outside the phases, and at the stage's end
+            if (pend_p_set && open_w >= 0) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, pend_p});
+            pend_p = unit_diag();
+            pend_p_set = false;
+            emit_phase();
+            for (const SignRun &r : pending) emit(nullptr, r);
+            pending.clear();
+        };
+        // with phases: a run of one-qubit gates is a layer; other dense runs end the phases
+        auto flush_all = [&]() {
+            bool one_qubit = phases && !dense_run.empty();
+            for (const FusedGate *g : dense_run) one_qubit = one_qubit && g->k == 1;
+            if (one_qubit) {
+                add_signs(run);
+                add_layer();
+                run = SignRun{};
+                dense_run.clear();
+                dense_q = 0;
+            } else if (phases && dense_run.empty()) {
+                add_signs(run);
+                run = SignRun{};
+            } else {
+                if (phases) flush_phases();
+                flush();
+            }
+        };
         for (const FusedGate *g : taken) {
             int sg_bits[4];
             if (sign_pattern(*g, sg_bits)) {
-                if ((g->mask & dense_q) || !run.fits(*g, local)) flush();
+                if ((g->mask & dense_q) || !run.fits(*g, local)) flush_all();
                 run.add(*g, sg_bits, local);
             } else {
                 dense_run.push_back(g);
                 dense_q |= g->mask;
             }
         }
-        flush();
+        flush_all();
+        if (phases) flush_phases();
         bs.chunk_count = (int)chunks.size() - bs.chunk_begin;
         st.push_back(bs);
         rest.swap(left);
@@ -953,9 +1308,10 @@ int build_work_list(sv_batch *b)
             }
             split.push_back(c);
         } else {
-            items.push_back(BItem{kSingle, c, 0, 0});
+            items.push_back(BItem{kSingle, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}});
         }
     }
+    if (hsm.size() & 1) hsm.push_back(make_float2(0.f, 0.f));   // the last chunk's 16-byte copy stays inside
     // split circuits in waves of at most wave_mb MB of state (0: one wave), so a wave's states can
     // stay in L2 while its steps run; inside a wave the circuits' steps interleave level by level
     std::vector<std::vector<int>> waves;
@@ -980,13 +1336,33 @@ int build_work_list(sv_batch *b)
                 if (s >= (staged ? hc[(size_t)c].n_stages : hc[(size_t)c].gate_count + 1)) continue;
                 any = true;
                 const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
-                for (int i = 0; i < t; ++i) items.push_back(BItem{staged ? kStage : kTile, c, s, i});
+                BItem it{staged ? kStage : kTile, c, s, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}};
+                if (staged) {
+                    const BCirc &C = hc[(size_t)c];
+                    const BStage &St = hst[(size_t)(C.stage_begin + s)];
+                    it.n = C.n;
+                    it.done_off = C.done_off;
+                    it.need_prev = s > 0 ? need[(size_t)(C.done_off + s - 1)] : 0;
+                    it.lmask = St.lmask;
+                    it.state_off = C.state_off;
+                    it.chunk_begin = St.chunk_begin;
+                    it.chunk_count = St.chunk_count;
+                    if (St.chunk_count > 0) it.ch0 = hch[(size_t)St.chunk_begin];
+                }
+                for (int i = 0; i < t; ++i) {
+                    it.tile = i;
+                    items.push_back(it);
+                }
             }
             if (!any) break;
         }
     for (int c = 0; c < (int)hc.size(); ++c)
-        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0});
-    if (b->stall && !need.empty()) need[0] += 1;   // nothing completes the extra tile: its waiters give up
+        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}});
+    if (b->stall && !need.empty()) {   // nothing completes the extra tile: its waiters give up
+        need[0] += 1;
+        for (BItem &w : items)
+            if (w.kind == kStage && w.done_off == 0 && w.step == 1) w.need_prev += 1;
+    }
     cudaFree(b->d_items);
     cudaFree(b->d_need);
     cudaFree(b->d_sync);
@@ -1068,10 +1444,13 @@ int launch_batch(sv_batch *b)
     a.tile_log2 = b->opts.tile_log2;
     a.stage_log2 = b->opts.stage_log2;
     SV_CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, sizeof(int) * (2 + (size_t)b->n_counters), b->stream));
-    if (b->opts.threads <= 256)
-        batch_kernel<256><<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
+    const dim3 grid((unsigned)b->opts.ctas), block((unsigned)b->opts.threads);
+    if (b->opts.ctas_per_sm == 2)
+        batch_kernel<256, 2><<<grid, block, smem_bytes(b->opts), b->stream>>>(a);
+    else if (b->opts.threads <= 256)
+        batch_kernel<256, 1><<<grid, block, smem_bytes(b->opts), b->stream>>>(a);
     else
-        batch_kernel<512><<<(unsigned)b->opts.ctas, (unsigned)b->opts.threads, smem_bytes(b->opts), b->stream>>>(a);
+        batch_kernel<512, 1><<<grid, block, smem_bytes(b->opts), b->stream>>>(a);
     SV_CUDA_TRY(cudaGetLastError());
     return SV_OK;
 }
@@ -1087,6 +1466,29 @@ int check_opts(const sv_batch_opts &o)
     if (o.stage_log2 != 0 && (o.stage_log2 < kStageMinN || o.stage_log2 > 14)) { set_error("sv_batch: stage_log2 must be 0 or in [%d, 14]", kStageMinN); return SV_EINVAL; }
     if (o.stage_k < 0 || o.stage_k > kBatchMaxK) { set_error("sv_batch: stage_k must be in [0, %d]", kBatchMaxK); return SV_EINVAL; }
     if (o.stage_layers != 0 && o.stage_layers != 1) { set_error("sv_batch: stage_layers must be 0 or 1"); return SV_EINVAL; }
+    if (o.ctas_per_sm < 0 || o.ctas_per_sm > 2) { set_error("sv_batch: ctas_per_sm must be 0, 1 or 2"); return SV_EINVAL; }
+    if (o.ctas_per_sm == 2) {
+        if (o.threads > 256) { set_error("sv_batch: ctas_per_sm = 2 takes CTAs of at most 256 threads"); return SV_EINVAL; }
+        int dev = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+            set_error("sv_batch: device query failed");
+            return SV_ECUDA;
+        }
+        // each CTA also holds its static shared memory and the 1 KB the system reserves
+        if (2 * (smem_bytes(o) + 2048) > (size_t)per_sm) {
+            set_error("sv_batch: ctas_per_sm = 2 needs two CTAs' shared memory (%zu bytes each) on one SM", smem_bytes(o));
+            return SV_EINVAL;
+        }
+    }
+    return SV_OK;
+}
+
+int set_smem_attrs(const sv_batch_opts &o)
+{
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(o)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(o)));
+    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(o)));
     return SV_OK;
 }
 
@@ -1190,6 +1592,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
     b->opts.stage_log2 = 0;
     b->opts.stage_k = 0;
     b->opts.stage_layers = 0;
+    b->opts.ctas_per_sm = 1;
     *out = b;
     return SV_OK;
 }
@@ -1217,8 +1620,7 @@ extern "C" int sv_batch_set_opts(sv_batch *b, const sv_batch_opts *o)
     clear_error();
     if (!b || !o) { set_error("sv_batch_set_opts: NULL argument"); return SV_EINVAL; }
     SV_TRY(check_opts(*o));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(*o)));
+    SV_TRY(set_smem_attrs(*o));
     b->opts = *o;
     return SV_OK;
 }
@@ -1236,8 +1638,7 @@ extern "C" int sv_batch_run(sv_batch *b)
     clear_error();
     if (!b) { set_error("sv_batch_run: NULL batch"); return SV_EINVAL; }
     SV_TRY(check_opts(b->opts));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
-    SV_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(b->opts)));
+    SV_TRY(set_smem_attrs(b->opts));
     const int lcfg[7] = {b->opts.smem_max_n, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb, b->opts.stage_log2,
                          b->opts.stage_k, b->opts.stage_layers};
     const bool relist = !b->d_items || std::memcmp(lcfg, b->list_cfg, sizeof(lcfg)) != 0 || b->list_stall != b->stall;
@@ -1251,8 +1652,8 @@ extern "C" int sv_batch_run(sv_batch *b)
         SV_TRY(build_work_list(b));
     }
     if (!b->opts.use_graph) return launch_batch(b);
-    const int cfg[9] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb,
-                        b->opts.stage_log2, b->opts.stage_k, b->opts.stage_layers};
+    const int cfg[10] = {b->opts.threads, b->opts.smem_max_n, b->opts.ctas, b->opts.split_min_n, b->opts.tile_log2, b->opts.wave_mb,
+                         b->opts.stage_log2, b->opts.stage_k, b->opts.stage_layers, b->opts.ctas_per_sm};
     if (b->graph && std::memcmp(cfg, b->graph_cfg, sizeof(cfg)) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;

@@ -69,8 +69,9 @@ def run_batch(a):
     from .batch import Batch
     circuits = wl.hea_batch(count=a.count, seed=a.seed)
     b = Batch(circuits, a.max_k)
-    b.set(a.threads, a.smem_max_n, 2 * torch.cuda.get_device_properties(0).multi_processor_count, True,
-          a.split_min_n, a.tile_log2, a.wave_mb, a.stage_log2, a.stage_k, a.stage_layers)
+    ctas = a.ctas or 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    b.set(a.threads, a.smem_max_n, ctas, True, a.split_min_n, a.tile_log2, a.wave_mb, a.stage_log2, a.stage_k,
+          a.stage_layers, a.ctas_per_sm)
     us = _time(b.run, b.stream, a.warm, a.repeats)
     B.sv_device_status()
     info = B.sv_batch_get_info(b.h)
@@ -97,6 +98,8 @@ def main(argv=None):
     ap.add_argument("--stage-log2", type=int, default=0)
     ap.add_argument("--stage-k", type=int, default=0)
     ap.add_argument("--stage-layers", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=1)
+    ap.add_argument("--ctas", type=int, default=0, help="persistent CTAs (0: twice the SM count)")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--warm", type=int, default=1)
     ap.add_argument("--repeats", type=int, default=3)

@@ -114,25 +114,49 @@ def _sign_circuit(n, count, rng):
     return gates
 
 
+def _layer_circuit(n, layers, rng):
+    """Layers of one-qubit gates and sign gates between them: a third of the layers only on qubits
+    0-4 (phases of one window that outgrow one phase's record limit), the others on random subsets
+    (every window, the qubits two windows share); sign gates at distances 1-5 and single-qubit
+    signs."""
+    gates = []
+    for _ in range(layers):
+        qs = range(5) if rng.random() < 0.34 else [q for q in range(n) if rng.random() < 0.7]
+        for q in qs:
+            gates.append(wl.Gate((int(q),), wl.random_unitary(2, rng)))
+            if rng.random() < 0.3:
+                gates.append(wl.Gate((int(q),), wl.random_unitary(2, rng)))
+        for _ in range(int(rng.integers(1, n))):
+            d = int(rng.integers(1, 6))
+            a = int(rng.integers(0, n - d))
+            if rng.random() < 0.8:
+                gates.append(wl.Gate((a, a + d), np.diag([1, 1, 1, -1]).astype(np.complex128)))
+            else:
+                gates.append(wl.Gate((a,), np.diag([1, -1]).astype(np.complex128)))
+    return gates
+
+
 @pytest.mark.parametrize("layers", [0, 1])
 def test_sign_runs_match_oracle(env, layers):
     """Circuits kept unfused (fusion size 0), so each stage re-fuses its dense gates and applies
     its +-1 diagonals as sign runs on the inputs of the next gate (or as a sweep of their own):
-    HEA circuits (CZ ladders) and circuits dense in sign gates, at every stage tile size,
-    re-fusion size and CTA size, against the oracle.  With layers, runs of one-qubit gates go
-    through register phases (in-block qubits by warp shuffles, up to four or five higher qubits in
-    registers)."""
+    HEA circuits (CZ ladders), circuits dense in sign gates and layered circuits, at every stage
+    tile size, re-fusion size and CTA size, against the oracle.  With layers, runs of one-qubit
+    gates and the sign runs between them go through register phases (tiles of 10 or more qubits:
+    windows of five qubits in registers, sign runs formed per thread)."""
     B, batch = env
     rng = np.random.default_rng(31)
     circuits = [(int(n), wl.hea_circuit(int(n), 3, rng)) for n in [16, 9, 14, 12, 11]]
     circuits += [(int(n), _sign_circuit(int(n), c, rng)) for n, c in [(13, 150), (16, 80), (10, 200), (8, 60)]]
+    circuits += [(int(n), _layer_circuit(int(n), c, rng)) for n, c in [(14, 40), (11, 30), (15, 12)]]
+    circuits += [(17, wl.hea_circuit(17, 8, rng))]
     refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
-    # (threads, smem_max_n, ctas, split_min_n, stage_log2, stage_k)
-    configs = [(256, 0, 7, 1, 8, 0), (512, 0, 152, 8, 14, 4), (256, 0, 19, 8, 11, 2), (128, 0, 40, 8, 10, 3),
-               (512, 0, 304, 1, 13, 3), (256, 0, 1, 8, 12, 1)]
+    # (threads, smem_max_n, ctas, split_min_n, stage_log2, stage_k, CTAs per SM)
+    configs = [(256, 0, 7, 1, 8, 0, 1), (512, 0, 152, 8, 14, 4, 1), (256, 0, 19, 8, 11, 2, 1), (128, 0, 40, 8, 10, 3, 1),
+               (512, 0, 304, 1, 13, 3, 1), (256, 0, 1, 8, 12, 1, 1), (256, 0, 304, 8, 13, 2, 2), (128, 0, 60, 1, 12, 3, 2)]
     b = batch.Batch(circuits, 0)
-    for threads, smem_n, ctas, split_n, sl, sk in configs:
-        b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk, layers)
+    for threads, smem_n, ctas, split_n, sl, sk, per_sm in configs:
+        b.set(threads, smem_n, ctas, True, split_n, 12, 0, sl, sk, layers, per_sm)
         info = B.sv_batch_get_info(b.h)
         assert info["staged"] == len(circuits), info
         b.arena.fill_(float("nan"))
@@ -140,7 +164,7 @@ def test_sign_runs_match_oracle(env, layers):
         B.sv_device_status()
         for i, ref in enumerate(refs):
             got = b.state(i)
-            cfg = (threads, ctas, sl, sk, layers, i)
+            cfg = (threads, ctas, sl, sk, layers, per_sm, i)
             assert oracle.fidelity(ref, got) >= 1 - 1e-6, cfg
             assert oracle.l2_error(ref, got) <= 1e-4, cfg
     b.free()
@@ -262,7 +286,9 @@ def test_batch_rejects_bad_input(env):
     assert e.value.code == B.SV_ENOMEM
     h = B.sv_batch_create([f2], buf.data_ptr(), buf.numel() * 4)
     for bad in (dict(threads=1024), dict(split_min_n=25), dict(tile_log2=4), dict(tile_log2=17), dict(smem_max_n=15),
-                dict(wave_mb=-1), dict(stage_log2=7), dict(stage_log2=15), dict(stage_k=5), dict(stage_k=-1)):
+                dict(wave_mb=-1), dict(stage_log2=7), dict(stage_log2=15), dict(stage_k=5), dict(stage_k=-1),
+                dict(ctas_per_sm=3), dict(ctas_per_sm=-1), dict(ctas_per_sm=2, threads=512),
+                dict(ctas_per_sm=2, stage_log2=14)):
         kw = dict(threads=256, smem_max_n=12, ctas=8, use_graph=True, split_min_n=15, tile_log2=12, wave_mb=0)
         kw.update(bad)
         with pytest.raises(B.SvError) as e:
