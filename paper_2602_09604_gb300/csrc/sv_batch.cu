@@ -79,6 +79,7 @@ struct BStage {
     unsigned lmask;
     int chunk_begin;
     int chunk_count;
+    unsigned frame;          // local qubits whose bits the tile holds flipped when its gates end
 };
 
 struct BChunk {
@@ -99,12 +100,12 @@ constexpr int kStageGateCap = 64;    // gate descriptors per chunk
 //   kStage  - tile `tile` of stage `step` of circuit c, through shared memory.
 enum : int { kWhole = 0, kSingle = 1, kTile = 2, kStage = 3 };
 
-struct alignas(16) BItem {   // 64 bytes
+struct alignas(16) BItem {   // 80 bytes
     int kind;
     int c;
     int step;
     int tile;
-    // kStage: what the item needs, copied here so that one 64-byte read starts it (instead of a
+    // kStage: what the item needs, copied here so that one 80-byte read starts it (instead of a
     // chain of dependent reads through the circuit, stage and chunk tables)
     int n;
     int done_off;            // the circuit's first completion counter
@@ -114,8 +115,10 @@ struct alignas(16) BItem {   // 64 bytes
     int chunk_begin;
     int chunk_count;
     BChunk ch0;              // the stage's first chunk (empty when it has none)
+    unsigned frame;          // the stage's frame (see BStage): the tile stores local index l ^ frame
+    int pad[3];
 };
-static_assert(sizeof(BItem) == 64, "work items are read 16 bytes at a time");
+static_assert(sizeof(BItem) == 80, "work items are read 16 bytes at a time");
 
 template <int V, bool L2ONLY>
 __device__ __forceinline__ void ld_v(const float *p, float (&v)[V])
@@ -194,6 +197,8 @@ __device__ void sign_sweep(float *S, int n, const BGate &g)
 // Q0..Q0+4 (slot m: window bits m):
 //   k = -3: a 2x2 matrix on window qubit targets[0] (U at mat_off, row-major, then X U X);
 //   k = -5: a real 2x2 matrix on window qubit targets[0] (R, then X R X: four floats each);
+//   k = -8: T(t_r) = (1, -t_r; t_r, 1) on all five window qubits (pairs t_r, -t_r), one
+//           straight-line pass with no branch per gate: two multiply-adds per pair and component;
 //   k = -6: a diagonal over the tile's qubits that factors over them: amplitude i times
 //           C * prod_{q : i_q = 1} w_q, from tables at mat_off: 32 entries over the window bits,
 //           32 over the thread's first five non-window bits (times C), 16 over its next four;
@@ -230,6 +235,22 @@ __device__ __forceinline__ void slot_gate(float (&xr)[32], float (&xi)[32], cons
         xi[m] = fmaf(p.x, ai, fmaf(p.y, ar, fmaf(p.z, bi, p.w * br)));
         xr[m1] = fmaf(q.x, ar, fmaf(-q.y, ai, fmaf(q.z, br, -q.w * bi)));
         xi[m1] = fmaf(q.x, ai, fmaf(q.y, ar, fmaf(q.z, bi, q.w * br)));
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void slot_tan(float (&xr)[32], float (&xi)[32], const float t)
+{
+    // (a, b) -> (a - t b, t a + b): two multiply-adds per component
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        if ((m >> R) & 1) continue;
+        const int m1 = m | (1 << R);
+        const float ar = xr[m], ai = xi[m], br = xr[m1], bi = xi[m1];
+        xr[m] = fmaf(-t, br, ar);
+        xi[m] = fmaf(-t, bi, ai);
+        xr[m1] = fmaf(t, ar, br);
+        xi[m1] = fmaf(t, ai, bi);
     }
 }
 
@@ -282,7 +303,16 @@ __device__ void run_phase(float *S, int L, const BGate *ops, int nops, const flo
         }
         for (int t = 0; t < nops; ++t) {
             const BGate &g = ops[t];
-            if (g.k == -5) {
+            if (g.k == -8) {
+                // T(t_r) = (1, -t_r; t_r, 1) on all five window bits, straight-line (t = 0 where the
+                // layer has none): the pairs (t_r, -t_r) at mat_off, the second for a flipped bit
+                const float *tp = reinterpret_cast<const float *>(U + (g.mat_off - mb));
+                slot_tan<0>(xr, xi, tp[0]);
+                slot_tan<1>(xr, xi, tp[2]);
+                slot_tan<2>(xr, xi, tp[4 + (int)((f >> 2) & 1u)]);
+                slot_tan<3>(xr, xi, tp[6 + (int)((f >> 3) & 1u)]);
+                slot_tan<4>(xr, xi, tp[8 + (int)((f >> 4) & 1u)]);
+            } else if (g.k == -5) {
                 const int r = g.targets[0];
                 const unsigned flip = Q0 == 0 ? (f >> r) & 1u : 0u;
                 const float4 u = *reinterpret_cast<const float4 *>(U + (g.mat_off - mb) + 2 * (int)flip);
@@ -588,41 +618,53 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
     float2 *sU = reinterpret_cast<float2 *>(smem);                  // matrix area: A.mat_cap complex
     BGate *sG = reinterpret_cast<BGate *>(smem + 2 * A.mat_cap);     // staged: a chunk's descriptors
     float *sS = smem + 2 * A.mat_cap + A.gate_cap * (int)(sizeof(BGate) / 4);   // circuit state or tile
-    __shared__ int cur;
     __shared__ int ok;
-    __shared__ BItem sW;          // the current item: fields are read where used (no long-lived registers)
+    __shared__ int sIt[2];        // item index of each slot
+    __shared__ BItem sWb[2];      // the current item and the next one (fetched ahead); fields are
+                                  // read where used (no long-lived registers)
     __shared__ unsigned sT[96];   // staged tiles: deposits of local index bits 3-8 ([0, 64)) and 9-13
+    // a stage chunk's gate descriptors and matrices into shared memory by asynchronous 16-byte copies
+    auto load_chunk = [&](const BChunk &c) {
+        const float *src = reinterpret_cast<const float *>(A.sgates + c.gate_begin);
+        float *dst = reinterpret_cast<float *>(sG);
+        const int nv = c.gate_count * (int)(sizeof(BGate) / 16);
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+        const float *ms = reinterpret_cast<const float *>(A.smats + c.mat_begin);
+        float *md = reinterpret_cast<float *>(sU);
+        for (int i = threadIdx.x; i < (c.mat_count + 1) / 2; i += blockDim.x) cp_async16(md + 4 * i, ms + 4 * i);
+    };
+    // (thread 0) the next item from the queue into slot s: its index, and its record by asynchronous
+    // copies.  Taking an item ahead keeps the list order's guarantee: the earliest unfinished item
+    // is never one held ahead (the item its CTA works on is earlier and unfinished), so it runs and
+    // waits only on finished items.
+    auto fetch = [&](int s) {
+        const int nx = (int)atomicAdd(reinterpret_cast<unsigned *>(A.sync), 1u);
+        sIt[s] = nx;
+        if (nx < A.n_items)
+            for (int v = 0; v < (int)(sizeof(BItem) / 16); ++v)
+                cp_async16(reinterpret_cast<float *>(&sWb[s]) + 4 * v, reinterpret_cast<const float *>(A.items + nx) + 4 * v);
+    };
+    int slot = 0;
+    if (threadIdx.x == 0) {
+        fetch(0);
+        cp_async_wait_all();
+    }
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) cur = (int)atomicAdd(reinterpret_cast<unsigned *>(A.sync), 1u);
-        __syncthreads();
-        const int it = cur;
-        if (it < A.n_items && threadIdx.x < (int)(sizeof(BItem) / 16))
-            reinterpret_cast<int4 *>(&sW)[threadIdx.x] = reinterpret_cast<const int4 *>(A.items + it)[threadIdx.x];
-        __syncthreads();
-        if (it >= A.n_items) break;
-        const BItem &W = sW;
+        if (sIt[slot] >= A.n_items) break;
+        const BItem &W = sWb[slot];
         if (W.kind == kStage) {
-            int *done = A.sync + 2 + W.done_off;
-            float *G = A.arena + W.state_off;
+            // (the tile's pointers and bits are formed again from the item where they are used, so
+            // that nothing of them stays live in registers across the phases)
             const int L = W.n < A.stage_log2 ? W.n : A.stage_log2;   // tile qubits (>= 8)
-            const unsigned hmask = ((1u << W.n) - 1u) & ~W.lmask;
-            const unsigned tb = deposit_bits((unsigned)W.tile, hmask);   // the tile's fixed bits
-            // a chunk's gate descriptors and matrices into shared memory, 16 bytes at a time (the
-            // first chunk's copy overlaps the wait and the tile load)
-            auto load_chunk = [&](const BChunk &c) {
-                const int4 *src = reinterpret_cast<const int4 *>(A.sgates + c.gate_begin);
-                int4 *dst = reinterpret_cast<int4 *>(sG);
-                const int nv = c.gate_count * (int)(sizeof(BGate) / 16);
-                for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
-                const float4 *ms = reinterpret_cast<const float4 *>(A.smats + c.mat_begin);
-                float4 *md = reinterpret_cast<float4 *>(sU);
-                for (int i = threadIdx.x; i < (c.mat_count + 1) / 2; i += blockDim.x) md[i] = ms[i];
-            };
+            auto tile_bits = [&]() { return deposit_bits((unsigned)W.tile, ((1u << W.n) - 1u) & ~W.lmask); };
+            // the first chunk's copy overlaps the wait
             BChunk ch = W.ch0;
             if (W.chunk_count > 0) load_chunk(ch);
-            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, W.need_prev);
+            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, A.sync + 2 + W.done_off + W.step - 1, W.need_prev);
             for (unsigned i = threadIdx.x; i < 96u; i += blockDim.x)
                 sT[i] = i < 64u ? deposit_bits(i << 3, W.lmask) : deposit_bits((i - 64u) << 9, W.lmask);
+            cp_async_wait_all();
             __syncthreads();
             if (!ok) break;
             // local index l -> global index: bits 0-2 stay (S holds qubits 0-2), the rest deposit
@@ -630,9 +672,10 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
             // amplitudes (16 bytes of real and of imaginary parts) at a time; eight consecutive
             // local indices are one 32-byte run in global memory.  The tile loads by asynchronous
             // copies straight into shared memory (through L2: other CTAs wrote it in the previous
-            // stage), all of a thread's copies in flight at once.
+            // stage), all of a thread's copies in flight at once, and the next item is taken
+            // from the queue meanwhile.
             const int nq = 1 << (L - 2);
-            auto gofs = [&](unsigned l) -> unsigned {
+            auto gofs = [&](unsigned l, unsigned tb) -> unsigned {
                 const unsigned gi = (l & 7u) | sT[(l >> 3) & 63u] | sT[64 + (l >> 9)] | tb;
                 return ((gi >> 5) << 6) | (gi & 31u);
             };
@@ -641,19 +684,23 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
                 __syncthreads();
                 if (W.tile == 0 && threadIdx.x == 0) sS[0] = 1.f;
             } else {
+                const float *G = A.arena + W.state_off;
+                const unsigned tb = tile_bits();
                 for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                     const unsigned l = (unsigned)q << 2, lo = ((l >> 5) << 6) | (l & 31u);
-                    const unsigned go = gofs(l);
+                    const unsigned go = gofs(l, tb);
                     cp_async16(sS + lo, G + go);
                     cp_async16(sS + lo + 32, G + go + 32);
                 }
-                cp_async_wait_all();
             }
+            if (threadIdx.x == 0) fetch(slot ^ 1);
+            cp_async_wait_all();
             __syncthreads();
             for (int ci = 0; ci < W.chunk_count; ++ci) {
                 if (ci > 0) {   // the previous chunk's last gate ended with a barrier
                     ch = A.chunks[W.chunk_begin + ci];
                     load_chunk(ch);
+                    cp_async_wait_all();
                     __syncthreads();
                 }
                 for (int gi = 0; gi < ch.gate_count; ++gi) {
@@ -674,17 +721,32 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
                     __syncthreads();   // this gate's writes before the next gate's reads
                 }
             }
-            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                const unsigned l = (unsigned)q << 2, lo = ((l >> 5) << 6) | (l & 31u);
-                const unsigned go = gofs(l);
-                *reinterpret_cast<float4 *>(G + go) = *reinterpret_cast<const float4 *>(sS + lo);
-                *reinterpret_cast<float4 *>(G + go + 32) = *reinterpret_cast<const float4 *>(sS + lo + 32);
+            {
+                // the tile holds amplitude l at l ^ frame: its four amplitudes l..l+3 are the float4
+                // at (l ^ frame) & ~3, permuted by the frame's two low bits
+                float *G = A.arena + W.state_off;
+                const unsigned tb = tile_bits(), fr = W.frame;
+                auto perm = [fr](const float4 v) {
+                    switch (fr & 3u) {
+                    case 0: return v;
+                    case 1: return make_float4(v.y, v.x, v.w, v.z);
+                    case 2: return make_float4(v.z, v.w, v.x, v.y);
+                    default: return make_float4(v.w, v.z, v.y, v.x);
+                    }
+                };
+                for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                    const unsigned l = (unsigned)q << 2, ls = l ^ (fr & ~3u), lo = ((ls >> 5) << 6) | (ls & 31u);
+                    const unsigned go = gofs(l, tb);
+                    *reinterpret_cast<float4 *>(G + go) = perm(*reinterpret_cast<const float4 *>(sS + lo));
+                    *reinterpret_cast<float4 *>(G + go + 32) = perm(*reinterpret_cast<const float4 *>(sS + lo + 32));
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();   // release: this tile's writes before the count
-                atomicAdd(done + W.step, 1);
+                atomicAdd(A.sync + 2 + W.done_off + W.step, 1);
             }
+            slot ^= 1;
             continue;
         }
         const BCirc C = A.circ[W.c];
@@ -709,33 +771,40 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
                 for (long long i = threadIdx.x; i < nf / 4; i += blockDim.x) dst[i] = reinterpret_cast<const float4 *>(S)[i];
                 __syncthreads();
             }
-            continue;
-        }
-        // one tile of one step of a large circuit
-        int *done = A.sync + 2 + C.done_off;
-        if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, A.need[C.done_off + W.step - 1]);
-        __syncthreads();
-        if (!ok) break;
-        if (W.step == 0) {
-            const long long span = 2ll << (A.tile_log2 + 3);   // floats zeroed per tile
-            const long long f0 = (long long)W.tile * span;
-            zero_floats(G, f0, f0 + span < nf ? f0 + span : nf);
-            __syncthreads();
-            if (W.tile == 0 && threadIdx.x == 0) G[0] = 1.f;
         } else {
-            const BGate g = A.gates[C.gate_begin + W.step - 1];
-            stage_matrix(sU, A.mats, g);
+            // one tile of one step of a large circuit
+            int *done = A.sync + 2 + C.done_off;
+            if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, done + W.step - 1, A.need[C.done_off + W.step - 1]);
             __syncthreads();
-            const unsigned groups = 1u << (C.n - g.k);
-            const unsigned g0 = (unsigned)W.tile << A.tile_log2;
-            const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
-            apply_gate_cta<true, (MAXT <= 256 && MINB == 1), false, false>(G, C.n, g, sU, g0, g1);
+            if (!ok) break;
+            if (W.step == 0) {
+                const long long span = 2ll << (A.tile_log2 + 3);   // floats zeroed per tile
+                const long long f0 = (long long)W.tile * span;
+                zero_floats(G, f0, f0 + span < nf ? f0 + span : nf);
+                __syncthreads();
+                if (W.tile == 0 && threadIdx.x == 0) G[0] = 1.f;
+            } else {
+                const BGate g = A.gates[C.gate_begin + W.step - 1];
+                stage_matrix(sU, A.mats, g);
+                __syncthreads();
+                const unsigned groups = 1u << (C.n - g.k);
+                const unsigned g0 = (unsigned)W.tile << A.tile_log2;
+                const unsigned g1 = g0 + (1u << A.tile_log2) < groups ? g0 + (1u << A.tile_log2) : groups;
+                apply_gate_cta<true, (MAXT <= 256 && MINB == 1), false, false>(G, C.n, g, sU, g0, g1);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();   // release: this tile's writes before the count
+                atomicAdd(done + W.step, 1);
+            }
+        }
+        // the next item (the other kinds take it here, after their work)
+        if (threadIdx.x == 0) {
+            fetch(slot ^ 1);
+            cp_async_wait_all();
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();   // release: this tile's writes before the count
-            atomicAdd(done + W.step, 1);
-        }
+        slot ^= 1;
     }
 }
 
@@ -856,6 +925,22 @@ struct SignRun {
             pairs.push_back({b - a, 1u << a});
         }
     }
+    // the same signs over the index with the bits of F flipped: x_a -> x_a ^ f_a turns a linear term
+    // into itself plus a constant and a pair term into itself plus linear terms and a constant
+    SignRun flipped(unsigned F) const
+    {
+        SignRun r = *this;
+        r.gsign ^= (unsigned)__builtin_popcount(zmask & F) & 1u;
+        for (const auto &p : pairs)
+            for (unsigned m = p.second; m; m &= m - 1u) {
+                const int a = __builtin_ctz(m), b = a + p.first;
+                const unsigned fa = (F >> a) & 1u, fb = (F >> b) & 1u;
+                if (fb) r.zmask ^= 1u << a;
+                if (fa) r.zmask ^= 1u << b;
+                r.gsign ^= fa & fb;
+            }
+        return r;
+    }
     void fill(BGate &b) const
     {
         b.gsign = gsign;
@@ -947,8 +1032,18 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         // per gate: U then its pair-swapped copy U' (U'[r][j] = U[r][j ^ 1]), starting at an even
         // offset of the chunk (16-byte aligned in shared memory); a sign run rides on the gate
         // (k = 0: a sign-only sweep)
-        auto emit = [&](const FusedGate *g, const SignRun &run) {
+        // the tile's frame: local qubits whose bits it holds flipped (X applied, so that a rotation by
+        // more than 45 degrees costs what a small one does; see add_layer).  Everything emitted acts
+        // on the flipped tile: matrices conjugated by the flips, sign runs over the flipped index;
+        // the store puts amplitude l back at l ^ frame.
+        unsigned frame = 0u;
+        auto emit = [&](const FusedGate *g, const SignRun &run_true) {
             const int dd = g ? (int)g->ur.size() : 0;
+            const SignRun run = run_true.flipped(frame);
+            unsigned fm = 0u;   // the flips on g's targets, as bits of its matrix index
+            if (g)
+                for (int j = 0; j < g->k; ++j)
+                    if ((frame >> local(g->targets[j])) & 1u) fm |= 1u << j;
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
                 chunks.back().mat_count + 1 + 2 * dd > kStageMatCap)
                 new_chunk();
@@ -962,8 +1057,11 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
             if (g) {
                 b.k = g->k;
                 for (int j = 0; j < g->k; ++j) b.targets[j] = local(g->targets[j]);
-                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)e], g->ui[(size_t)e]));
-                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)(e ^ 1)], g->ui[(size_t)(e ^ 1)]));
+                // X^f U X^f: entry (r, c) from (r ^ f, c ^ f)
+                const int D = 1 << g->k;
+                auto src = [&](int e) { return (((e / D) ^ (int)fm) * D) + ((e % D) ^ (int)fm); };
+                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)src(e)], g->ui[(size_t)src(e)]));
+                for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)src(e ^ 1)], g->ui[(size_t)src(e ^ 1)]));
             }
             sg.push_back(b);
             chunks.back().gate_count += 1;
@@ -1010,7 +1108,7 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         // right before the next layer's first rotation (a complex factor per amplitude).
         const int nwin = L > 10 ? 3 : 2;
         const int q0s[3] = {0, 5, L - 5};
-        enum : int { kSubGate = 0, kSubSign = 1, kSubRot = 2, kSubDiag = 3 };
+        enum : int { kSubGate = 0, kSubSign = 1, kSubRot = 2, kSubDiag = 3, kSubTan5 = 4 };
         using Diag = std::array<std::array<cplx, 2>, 32>;   // per local qubit: its diagonal (d0, d1)
         struct Sub {
             int kind;
@@ -1018,6 +1116,7 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
             std::array<cplx, 4> U;      // kSubGate: the matrix; kSubRot: (c, -s, s, c) in the real parts
             SignRun s;
             Diag D;
+            std::array<std::array<double, 4>, 5> R5;   // kSubTan5: window bit r's t in R5[r][0]
         };
         auto unit_diag = []() {
             Diag d;
@@ -1032,7 +1131,8 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         auto emit_phase = [&]() {
             if (open_w < 0) return;
             int nm = 0;   // float2 of matrices
-            for (const Sub &u : open_subs) nm += u.kind == kSubGate ? 8 : u.kind == kSubRot ? 4 : u.kind == kSubDiag ? 80 : 0;
+            for (const Sub &u : open_subs)
+                nm += u.kind == kSubGate ? 8 : u.kind == kSubRot ? 4 : u.kind == kSubDiag ? 80 : u.kind == kSubTan5 ? 6 : 0;
             const int recs = 1 + (int)open_subs.size();
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count + recs > kStageGateCap ||
                 chunks.back().mat_count + 1 + nm > kStageMatCap)
@@ -1066,6 +1166,11 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
                     sm.push_back(make_float2(a10, a11));
                     sm.push_back(make_float2(a11, a10));   // X R X
                     sm.push_back(make_float2(a01, a00));
+                } else if (u.kind == kSubTan5) {
+                    b.k = -8;
+                    b.mat_off = (int)sm.size();
+                    for (int r = 0; r < 5; ++r) sm.push_back(make_float2((float)u.R5[(size_t)r][0], -(float)u.R5[(size_t)r][0]));
+                    sm.push_back(make_float2(0.f, 0.f));
                 } else if (u.kind == kSubDiag) {
                     // amplitude i gets C * prod over set bits q of i of w_q (w_q = d1 / d0, C = prod
                     // of the d0): tables over the window's 5 bits (slot), the thread's first 5
@@ -1131,18 +1236,33 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         auto open_phase = [&](int w) {
             emit_phase();
             open_w = w;
-            for (const SignRun &r : pending) open_subs.push_back(Sub{kSubSign, 0, {}, r, {}});
+            for (const SignRun &r : pending) open_subs.push_back(Sub{kSubSign, 0, {}, r.flipped(frame), {}, {}});
             pending.clear();
         };
         auto add_sub = [&](Sub u) {
             if ((int)open_subs.size() + 2 > kPhaseMaxRecords) open_phase(open_w);
             open_subs.push_back(std::move(u));
         };
-        auto add_signs = [&](const SignRun &r) {
+        auto add_signs = [&](const SignRun &r) {   // r over the true index (pending runs stay so)
             if (r.empty()) return;
-            if (open_w >= 0) add_sub(Sub{kSubSign, 0, {}, r, {}});
+            if (open_w >= 0) add_sub(Sub{kSubSign, 0, {}, r.flipped(frame), {}, {}});
             else pending.push_back(r);
         };
+        // the diagonal as it acts on the flipped tile: entries exchanged on the frame's qubits
+        auto diag_phys = [&](Diag d) {
+            for (int q = 0; q < 32; ++q)
+                if ((frame >> q) & 1u) std::swap(d[(size_t)q][0], d[(size_t)q][1]);
+            return d;
+        };
+        auto conj_phys = [&](std::array<cplx, 4> u, int q) {   // X U X on a flipped qubit
+            if ((frame >> q) & 1u) u = {u[3], u[2], u[1], u[0]};
+            return u;
+        };
+        // A rotation R = (c, -s; s, c) with 0 <= s, c runs as a multiple of T(t) = (1, -t; t, 1), two
+        // multiply-adds per pair of amplitudes: R = c T(s/c) when s <= c; otherwise R = s X T(c/s) Z
+        // (Z = diag(1, -1) before it, X after), and the X goes into the frame instead of being
+        // applied.  So |t| <= 1, and every scale (at least 1/sqrt 2) and Z joins the layer's
+        // leading diagonal.
         auto add_layer = [&]() {
             std::array<std::array<cplx, 4>, 32> U{};
             unsigned lm = 0u;
@@ -1155,26 +1275,6 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
                     lm |= 1u << q;
                 } else {
                     P = {G[0] * P[0] + G[1] * P[2], G[0] * P[1] + G[1] * P[3], G[2] * P[0] + G[3] * P[2], G[2] * P[1] + G[3] * P[3]};
-                }
-            }
-            // factors: the diagonal before the rotations (pending P's times this layer's Q's) and
-            // the P's left pending; a matrix that does not factor stays a complex gate
-            Diag E = pend_p;
-            bool e_set = pend_p_set;
-            pend_p = unit_diag();
-            pend_p_set = false;
-            std::array<bool, 32> rot{};
-            for (int q = 0; q < L; ++q) {
-                if (!((lm >> q) & 1u)) continue;
-                cplx p0, p1, q1;
-                double c, sn;
-                if (factor_prq(U[(size_t)q], p0, p1, c, sn, q1)) {
-                    rot[(size_t)q] = true;
-                    U[(size_t)q] = {cplx(c), cplx(-sn), cplx(sn), cplx(c)};
-                    E[(size_t)q][1] *= q1;
-                    pend_p[(size_t)q] = {p0, p1};
-                    e_set = true;
-                    pend_p_set = true;
                 }
             }
             // windows: qubits 0-4 in the first, 10 and up in the last; L - 5..9 in either
@@ -1205,18 +1305,76 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
                 for (int w = 0; w < nwin; ++w)
                     if (need[w]) order[no++] = w;
             }
+            // factors: the diagonal before the rotations (pending P's times this layer's Q's) and
+            // the P's left pending; a matrix that does not factor stays a complex gate.  Windows
+            // with three or more rotations run them as one straight-line record in T form.
+            Diag E = pend_p;
+            bool e_set = pend_p_set;
+            pend_p = unit_diag();
+            pend_p_set = false;
+            std::array<bool, 32> rot{};
+            std::array<double, 32> tq{};
+            unsigned tan_q = 0u, z_q = 0u;
+            double scale = 1.0;
+            for (int q = 0; q < L; ++q) {
+                if (!((lm >> q) & 1u)) continue;
+                cplx p0, p1, q1;
+                double c, sn;
+                if (factor_prq(U[(size_t)q], p0, p1, c, sn, q1)) {
+                    rot[(size_t)q] = true;
+                    U[(size_t)q] = {cplx(c), cplx(-sn), cplx(sn), cplx(c)};
+                    E[(size_t)q][1] *= q1;
+                    pend_p[(size_t)q] = {p0, p1};
+                    e_set = true;
+                    pend_p_set = true;
+                    tq[(size_t)q] = sn <= c ? sn / c : c / sn;
+                }
+            }
+            for (int w = 0; w < nwin; ++w) {
+                unsigned rm = 0u;
+                for (unsigned m = need[w]; m; m &= m - 1u)
+                    if (rot[(size_t)__builtin_ctz(m)]) rm |= m & (0u - m);
+                if (__builtin_popcount(rm) >= 3) tan_q |= rm;
+            }
+            for (unsigned m = tan_q; m; m &= m - 1u) {
+                const int q = __builtin_ctz(m);
+                const double c = U[(size_t)q][0].real(), sn = U[(size_t)q][2].real();
+                if (sn <= c) {
+                    scale *= c;
+                } else {
+                    scale *= sn;
+                    z_q |= 1u << q;
+                    E[(size_t)q][1] = -E[(size_t)q][1];
+                }
+            }
+            if (tan_q) {
+                E[0][0] *= scale;
+                E[0][1] *= scale;
+                e_set = true;
+            }
             for (int i = 0; i < no; ++i) {
                 const int w = order[i];
                 if (!(i == 0 && open_in)) open_phase(w);
-                if (i == 0 && e_set) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, E});
-                for (unsigned m = need[w]; m; m &= m - 1u) {
+                if (i == 0 && e_set) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, diag_phys(E), {}});
+                const unsigned tw = tan_q & need[w];
+                if (tw) {
+                    Sub f5{kSubTan5, 0, {}, SignRun{}, {}, {}};
+                    for (int r = 0; r < 5; ++r) {
+                        const int q = q0s[w] + r;
+                        const double t = ((tw >> q) & 1u) ? tq[(size_t)q] : 0.0;
+                        f5.R5[(size_t)r][0] = ((frame >> q) & 1u) ? -t : t;   // X T(t) X = T(-t)
+                    }
+                    add_sub(f5);
+                    frame ^= z_q & tw;   // the X after each rotation that went the long way
+                }
+                for (unsigned m = need[w] & ~tw; m; m &= m - 1u) {
                     const int q = __builtin_ctz(m);
-                    add_sub(Sub{rot[(size_t)q] ? kSubRot : kSubGate, q - q0s[w], U[(size_t)q], SignRun{}, {}});
+                    add_sub(Sub{rot[(size_t)q] ? kSubRot : kSubGate, q - q0s[w], conj_phys(U[(size_t)q], q), SignRun{}, {}, {}});
                 }
             }
         };
         auto flush_phases = [&]() {   // before a gate outside the phases, and at the stage's end
-            if (pend_p_set && open_w >= 0) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, pend_p});
+            if (pend_p_set && open_w >= 0) add_sub(Sub{kSubDiag, 0, {}, SignRun{}, diag_phys(pend_p), {}});
             pend_p = unit_diag();
             pend_p_set = false;
             emit_phase();
@@ -1254,6 +1412,7 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         flush_all();
         if (phases) flush_phases();
         bs.chunk_count = (int)chunks.size() - bs.chunk_begin;
+        bs.frame = frame;
         st.push_back(bs);
         rest.swap(left);
     }
@@ -1308,7 +1467,7 @@ int build_work_list(sv_batch *b)
             }
             split.push_back(c);
         } else {
-            items.push_back(BItem{kSingle, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}});
+            items.push_back(BItem{kSingle, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}});
         }
     }
     if (hsm.size() & 1) hsm.push_back(make_float2(0.f, 0.f));   // the last chunk's 16-byte copy stays inside
@@ -1336,7 +1495,7 @@ int build_work_list(sv_batch *b)
                 if (s >= (staged ? hc[(size_t)c].n_stages : hc[(size_t)c].gate_count + 1)) continue;
                 any = true;
                 const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
-                BItem it{staged ? kStage : kTile, c, s, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}};
+                BItem it{staged ? kStage : kTile, c, s, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}};
                 if (staged) {
                     const BCirc &C = hc[(size_t)c];
                     const BStage &St = hst[(size_t)(C.stage_begin + s)];
@@ -1348,6 +1507,7 @@ int build_work_list(sv_batch *b)
                     it.chunk_begin = St.chunk_begin;
                     it.chunk_count = St.chunk_count;
                     if (St.chunk_count > 0) it.ch0 = hch[(size_t)St.chunk_begin];
+                    it.frame = St.frame;
                 }
                 for (int i = 0; i < t; ++i) {
                     it.tile = i;
@@ -1357,7 +1517,7 @@ int build_work_list(sv_batch *b)
             if (!any) break;
         }
     for (int c = 0; c < (int)hc.size(); ++c)
-        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}});
+        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}});
     if (b->stall && !need.empty()) {   // nothing completes the extra tile: its waiters give up
         need[0] += 1;
         for (BItem &w : items)
