@@ -25,6 +25,8 @@
 // States use the library's blocked layout (32 reals then 32 imaginaries per 256-byte block).
 // The launch can be captured once in a CUDA graph and replayed.
 #include <algorithm>
+#include <cstdlib>
+#include <stdexcept>
 #include <array>
 #include <cstring>
 #include <mutex>
@@ -76,11 +78,24 @@ struct BCirc {
 // set bit); its gates (in the stage gate table, naming local qubits) come in chunks whose
 // descriptors and matrices fit the shared-memory areas reserved for them.
 struct BStage {
-    unsigned lmask;
+    unsigned lmask;          // physical qubits of the tile as it is loaded (as stored, for a first stage)
     int chunk_begin;
     int chunk_count;
     unsigned frame;          // local qubits whose bits the tile holds flipped when its gates end
+    int map;                 // store map (the next stage's qubit layout), -1: stored as loaded
 };
+
+// A stage tile stored in another qubit layout than it was loaded in (the next stage's): store-local
+// index bit j (the order of the store layout, its physical qubits 0-2 first) is load-local bit
+// src[j]; the store layout's physical local qubits are lmask; bit j of the tile index lands on
+// physical qubit tbit[j].
+struct alignas(16) BStoreMap {
+    unsigned lmask;
+    unsigned char src[16];
+    unsigned char tbit[16];
+    unsigned pad[3];
+};
+static_assert(sizeof(BStoreMap) == 48, "store maps are read 16 bytes at a time");
 
 struct BChunk {
     int gate_begin;          // in the stage gate table
@@ -116,7 +131,8 @@ struct alignas(16) BItem {   // 80 bytes
     int chunk_count;
     BChunk ch0;              // the stage's first chunk (empty when it has none)
     unsigned frame;          // the stage's frame (see BStage): the tile stores local index l ^ frame
-    int pad[3];
+    int map;                 // the stage's store map, -1: stored as loaded
+    int pad[2];
 };
 static_assert(sizeof(BItem) == 80, "work items are read 16 bytes at a time");
 
@@ -562,6 +578,7 @@ struct BatchArgs {
     const BChunk *chunks;    // their gate chunks
     const BGate *sgates;     // stage gates (local targets)
     const float2 *smats;     // their matrices
+    const BStoreMap *smaps;  // stage tiles stored in another layout
     int mat_cap;             // float2 of the shared-memory matrix area (>= 4^kBatchMaxK)
     int gate_cap;            // gate descriptors of the shared-memory descriptor area
     int *sync;         // [0] queue head, [1] abort flag, [2 + i] completion counter i
@@ -623,6 +640,8 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
     __shared__ BItem sWb[2];      // the current item and the next one (fetched ahead); fields are
                                   // read where used (no long-lived registers)
     __shared__ unsigned sT[96];   // staged tiles: deposits of local index bits 3-8 ([0, 64)) and 9-13
+    __shared__ BStoreMap sMap;    // a stage tile stored in another layout: its map
+    __shared__ unsigned short sP[256];   // and store-local -> load-local index, bits 0-6 ([0, 128)) and 7-13
     // a stage chunk's gate descriptors and matrices into shared memory by asynchronous 16-byte copies
     auto load_chunk = [&](const BChunk &c) {
         const float *src = reinterpret_cast<const float *>(A.sgates + c.gate_begin);
@@ -661,6 +680,9 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
             // the first chunk's copy overlaps the wait
             BChunk ch = W.ch0;
             if (W.chunk_count > 0) load_chunk(ch);
+            if (W.map >= 0 && threadIdx.x < (int)(sizeof(BStoreMap) / 16))
+                cp_async16(reinterpret_cast<float *>(&sMap) + 4 * threadIdx.x,
+                           reinterpret_cast<const float *>(A.smaps + W.map) + 4 * threadIdx.x);
             if (threadIdx.x == 0) ok = W.step == 0 || wait_count(A, A.sync + 2 + W.done_off + W.step - 1, W.need_prev);
             for (unsigned i = threadIdx.x; i < 96u; i += blockDim.x)
                 sT[i] = i < 64u ? deposit_bits(i << 3, W.lmask) : deposit_bits((i - 64u) << 9, W.lmask);
@@ -721,7 +743,41 @@ __global__ void __launch_bounds__(MAXT, MINB) batch_kernel(BatchArgs A)
                     __syncthreads();   // this gate's writes before the next gate's reads
                 }
             }
-            {
+            if (W.map >= 0) {
+                // stored in the next stage's layout: store-local index s (that layout's physical
+                // qubits 0-2 first) is load-local index P(s), held at P(s) ^ frame; four amplitudes
+                // consecutive in the store layout are gathered one by one and written as a float4
+                for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+                    unsigned v = 0u;
+                    for (int j = 0; j < 7; ++j) {
+                        const int sj = (i >> 7) * 7 + j;
+                        if (sj < L && ((i >> j) & 1)) v |= 1u << sMap.src[sj];
+                    }
+                    sP[i] = (unsigned short)v;
+                }
+                for (unsigned i = threadIdx.x; i < 96u; i += blockDim.x)
+                    sT[i] = i < 64u ? deposit_bits(i << 3, sMap.lmask) : deposit_bits((i - 64u) << 9, sMap.lmask);
+                __syncthreads();
+                float *G = A.arena + W.state_off;
+                unsigned tb = 0u;
+                for (int j = 0; j < W.n - L; ++j) tb |= (((unsigned)W.tile >> j) & 1u) << sMap.tbit[j];
+                const unsigned fr = W.frame, c1 = 1u << sMap.src[0], c2 = 1u << sMap.src[1];
+                for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                    const unsigned s0 = (unsigned)q << 2;
+                    const unsigned lb = ((unsigned)sP[s0 & 127u] | (unsigned)sP[128 + (s0 >> 7)]) ^ fr;
+                    float re[4], im[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const unsigned l = lb ^ ((j & 1) ? c1 : 0u) ^ ((j & 2) ? c2 : 0u);
+                        const unsigned o = ((l >> 5) << 6) | (l & 31u);
+                        re[j] = sS[o];
+                        im[j] = sS[o + 32];
+                    }
+                    const unsigned go = gofs(s0, tb);
+                    *reinterpret_cast<float4 *>(G + go) = make_float4(re[0], re[1], re[2], re[3]);
+                    *reinterpret_cast<float4 *>(G + go + 32) = make_float4(im[0], im[1], im[2], im[3]);
+                }
+            } else {
                 // the tile holds amplitude l at l ^ frame: its four amplitudes l..l+3 are the float4
                 // at (l ^ frame) & ~3, permuted by the frame's two low bits
                 float *G = A.arena + W.state_off;
@@ -835,6 +891,7 @@ struct sv_batch {
     BChunk *d_chunks = nullptr;
     BGate *d_sgates = nullptr;
     float2 *d_smats = nullptr;
+    BStoreMap *d_smaps = nullptr;
     int *d_err = nullptr;            // library's device error word (not owned)
     int n_items = 0;
     int n_counters = 0;
@@ -901,20 +958,26 @@ struct SignRun {
     bool fits(const FusedGate &g, Local local) const
     {
         if (g.k < 2) return true;
-        const int d = local(g.targets[1]) - local(g.targets[0]);
+        const int d = std::abs(local(g.targets[1]) - local(g.targets[0]));
         for (const auto &p : pairs)
             if (p.first == d) return true;
         return pairs.size() < (size_t)kSignDist;
     }
     // s(x) = s00 + (s00 ^ s10) x_a + (s00 ^ s01) x_b + (s00 ^ s10 ^ s01 ^ s11) x_a x_b over GF(2)
     template <typename Local>
-    void add(const FusedGate &g, const int (&s)[4], Local local)
+    void add(const FusedGate &g, const int (&s_in)[4], Local local)
     {
-        const int a = local(g.targets[0]);
+        // the gate's two qubits in local order (a below b); s over (bit of a) + 2 (bit of b)
+        int a = local(g.targets[0]);
+        int s[4] = {s_in[0], s_in[1], s_in[2], s_in[3]};
+        if (g.k >= 2 && local(g.targets[1]) < a) {
+            a = local(g.targets[1]);
+            std::swap(s[1], s[2]);
+        }
         gsign ^= (unsigned)s[0];
         if (s[0] ^ s[1]) zmask ^= 1u << a;
         if (g.k < 2) return;
-        const int b = local(g.targets[1]);
+        const int b = std::max(local(g.targets[0]), local(g.targets[1]));
         if (s[0] ^ s[2]) zmask ^= 1u << b;
         if (s[0] ^ s[1] ^ s[2] ^ s[3]) {
             for (auto &p : pairs)
@@ -992,37 +1055,216 @@ bool factor_prq(const std::array<cplx, 4> &U, cplx &p0, cplx &p1, double &c, dou
 
 constexpr unsigned kStageBase = 7u;   // qubits 0-2: in every stage's local set
 
-// Cut circuit gates gs (global targets, n qubits) into stages of at most L local qubits and append
-// them to the stage tables: stage gates are re-fused to at most stage_k qubits (0: kept as they
-// are) and renumbered to local qubits.  Greedy: scan the gates not yet placed in circuit order;
-// a gate joins the stage when no earlier unplaced gate shares a qubit with it (so it commutes
-// past every gate it overtakes) and the stage's qubits with its own still number at most L;
-// otherwise its qubits are closed for the rest of the scan.  The local set is then filled up to
-// L qubits with the lowest unused ones (longer contiguous runs per tile).
-void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, bool phase_opt, std::vector<BStage> &st,
-                  std::vector<BChunk> &chunks, std::vector<BGate> &sg, std::vector<float2> &sm)
+// A stage of a staged circuit: its gates, its local qubits and their order in the tile, and how the
+// tile moves between global memory and shared memory.
+struct StagePlan {
+    std::vector<const FusedGate *> gates;   // in circuit order
+    unsigned lam = 0u;                      // its local (logical) qubits
+    int local_of[32];                       // logical qubit -> local bit, -1 outside the tile
+    unsigned lmask = 0u;                    // physical local qubits of the load (of the store, first stage)
+    bool mapped = false;                    // stored in another layout than loaded
+    BStoreMap map{};
+    int load_pos[32];                       // logical qubit -> physical position, as loaded (as stored, first stage)
+    int store_pos[32];                      // and as stored
+};
+
+// Cut circuit gates gs (n qubits) into stages of at most L local qubits.
+//
+// Greedy: scanning the gates not yet placed in circuit order, a gate joins the stage when no
+// earlier unplaced gate shares a qubit with it (it commutes past every gate it overtakes) and the
+// stage's qubits with its own still number at most L; otherwise its qubits are closed for the
+// rest of the scan.
+//
+// A tile moves in 32-byte runs, so physical qubits 0-2 must be local at its load and at its store.
+// Between stages the state is relabelled: the layout a stage loads in puts three qubits that are
+// local in it and in the stage before at physical 0-2 (swapped there from the next layout), and
+// the stage before stores its tile in that layout.  The last stage stores in the circuit's own
+// order, so qubits 0-2 are local in it; the first builds its tile and stores it in the second's
+// layout.  Where the last stage has no room for qubits 0-2, or two neighbouring stages cannot
+// share three local qubits, a stage without gates goes in between (one pass that only relabels).
+// Any room left is filled with the qubits at the lowest physical positions (longer contiguous
+// runs per tile).
+std::vector<StagePlan> plan_stages(const std::vector<const FusedGate *> &gs, int n, int L)
 {
-    std::vector<const FusedGate *> rest = gs;
-    bool first = true;
-    while (first || !rest.empty()) {
-        first = false;
-        unsigned S = kStageBase, blocked = 0u;
-        std::vector<const FusedGate *> taken, left;
-        for (const FusedGate *g : rest) {
-            const unsigned q = (unsigned)g->mask;
-            if (!(q & blocked) && __builtin_popcount(S | q) <= L) {
-                S |= q;
-                taken.push_back(g);
-            } else {
-                blocked |= q;
-                left.push_back(g);
+    struct Stg {
+        std::vector<const FusedGate *> gates;
+        unsigned lam = 0u;    // local qubits so far
+        int B[3] = {0, 1, 2}; // the qubits its load layout puts at physical 0-2
+    };
+    const unsigned all = n >= 32 ? ~0u : (1u << n) - 1u;
+    std::vector<Stg> sv;
+    {
+        std::vector<const FusedGate *> rest = gs, left;
+        while (sv.empty() || !rest.empty()) {
+            Stg t;
+            unsigned blocked = 0u;
+            left.clear();
+            for (const FusedGate *g : rest) {
+                const unsigned q = (unsigned)g->mask;
+                if (!(q & blocked) && __builtin_popcount(t.lam | q) <= L) {
+                    t.lam |= q;
+                    t.gates.push_back(g);
+                } else {
+                    blocked |= q;
+                    left.push_back(g);
+                }
             }
+            sv.push_back(std::move(t));
+            rest.swap(left);
         }
-        for (int b = 0; b < n && __builtin_popcount(S) < L; ++b) S |= 1u << b;
+    }
+    // qubits 0-2 local in the last stage (it stores in the circuit's order)
+    if (__builtin_popcount(sv.back().lam | 7u) <= L) {
+        sv.back().lam |= 7u;
+    } else {
+        Stg t;
+        t.lam = 7u;
+        sv.push_back(t);
+    }
+    // boundaries from the last: three qubits local in both neighbours, preferring the qubits at
+    // physical 0-2 of the layout after the later one (the later one then stores as it loads),
+    // then shared qubits, then qubits that fit in one side's spare room
+    for (int k = (int)sv.size() - 2; k >= 0; --k) {
+        Stg &nx = sv[(size_t)k + 1];
+        int pref[3] = {0, 1, 2};
+        if (k + 2 < (int)sv.size()) std::copy(sv[(size_t)k + 2].B, sv[(size_t)k + 2].B + 3, pref);
+        auto pick = [&](Stg &cur) {
+            int B[3], nb = 0;
+            unsigned lam_r = cur.lam, lam_n = nx.lam;
+            auto try_add = [&](int x) {
+                if (nb == 3) return;
+                for (int j = 0; j < nb; ++j)
+                    if (B[j] == x) return;
+                const unsigned bit = 1u << x;
+                const bool in_r = lam_r & bit, in_n = lam_n & bit;
+                if ((!in_r && __builtin_popcount(lam_r) >= L) || (!in_n && __builtin_popcount(lam_n) >= L)) return;
+                lam_r |= bit;
+                lam_n |= bit;
+                B[nb++] = x;
+            };
+            for (int j = 0; j < 3; ++j) try_add(pref[j]);
+            if (nb < 3) {   // not all three: start over with shared qubits, then spare room
+                nb = 0;
+                lam_r = cur.lam;
+                lam_n = nx.lam;
+                for (int x = 0; x < n; ++x)
+                    if ((cur.lam & nx.lam) >> x & 1u) try_add(x);
+                for (int x = 0; x < n; ++x)
+                    if ((cur.lam | nx.lam) >> x & 1u) try_add(x);
+                for (int x = 0; x < n; ++x) try_add(x);
+            }
+            if (nb < 3) return false;
+            std::copy(B, B + 3, nx.B);
+            nx.lam = lam_n;
+            cur.lam = lam_r;
+            return true;
+        };
+        if (pick(sv[(size_t)k])) continue;
+        // a relabelling stage between them: three local qubits of each side
+        Stg t;
+        for (int x = 0, c = 0; x < n && c < 3; ++x)
+            if ((nx.lam >> x) & 1u) {
+                t.lam |= 1u << x;
+                ++c;
+            }
+        for (int x = 0, c = 0; x < n && c < 3; ++x)
+            if ((sv[(size_t)k].lam >> x) & 1u) {
+                t.lam |= 1u << x;
+                ++c;
+            }
+        sv.insert(sv.begin() + k + 1, t);
+        k += 2;   // next: the boundary (new stage, next), then (k, new stage); both share three qubits
+    }
+    // layouts, last stage first: the last stores in the circuit's order; stage k loads in layout
+    // pi[k] (= pi[k + 1] with B[k] swapped to physical 0-2), which stage k - 1 stores in
+    const int K = (int)sv.size();
+    std::vector<std::array<int, 32>> pi((size_t)K + 1);
+    for (int x = 0; x < 32; ++x) pi[(size_t)K][(size_t)x] = x;
+    for (int k = K - 1; k >= 1; --k) {
+        std::array<int, 32> p = pi[(size_t)k + 1];
+        const Stg &r = sv[(size_t)k];
+        for (int i = 0; i < 3; ++i) {
+            const int b = r.B[i];
+            int y = 0;
+            for (int x = 0; x < n; ++x)
+                if (p[(size_t)x] == i) y = x;
+            std::swap(p[(size_t)b], p[(size_t)y]);
+        }
+        pi[(size_t)k] = p;
+    }
+    pi[0] = pi[1];   // (the first stage loads nothing)
+    std::vector<StagePlan> out((size_t)K);
+    for (int k = 0; k < K; ++k) {
+        const Stg &r = sv[(size_t)k];
+        StagePlan &P = out[(size_t)k];
+        P.gates = r.gates;
+        const std::array<int, 32> &lay = k == 0 ? pi[1] : pi[(size_t)k];   // the first stage's order is its store's
+        const std::array<int, 32> &sto = pi[(size_t)k + 1];
+        unsigned lam = r.lam;
+        // the load layout's physical 0-2 are local (the last stage's are qubits 0-2)
+        for (int x = 0; x < n; ++x)
+            if (lay[(size_t)x] < 3) lam |= 1u << x;
+        // fill: lowest physical positions first
+        for (int pos = 0; pos < n && __builtin_popcount(lam) < L; ++pos)
+            for (int x = 0; x < n; ++x)
+                if (lay[(size_t)x] == pos) lam |= 1u << x;
+        P.lam = lam & all;
+        // local order: by physical position in the load layout (physical 0-2 first)
+        int order[32], no = 0;
+        for (int pos = 0; pos < n; ++pos)
+            for (int x = 0; x < n; ++x)
+                if (lay[(size_t)x] == pos && ((lam >> x) & 1u)) order[no++] = x;
+        for (int x = 0; x < 32; ++x) P.local_of[x] = -1;
+        P.lmask = 0u;
+        for (int i = 0; i < no; ++i) {
+            P.local_of[order[i]] = i;
+            P.lmask |= 1u << lay[(size_t)order[i]];
+        }
+        for (int x = 0; x < 32; ++x) {
+            P.load_pos[x] = lay[(size_t)x];
+            P.store_pos[x] = sto[(size_t)x];
+        }
+        P.mapped = k > 0 && lay != sto;
+        if (P.mapped) {
+            int so[32], ns = 0;
+            for (int pos = 0; pos < n; ++pos)
+                for (int x = 0; x < n; ++x)
+                    if (sto[(size_t)x] == pos && ((lam >> x) & 1u)) so[ns++] = x;
+            P.map.lmask = 0u;
+            for (int j = 0; j < ns; ++j) {
+                P.map.src[j] = (unsigned char)P.local_of[so[j]];
+                P.map.lmask |= 1u << sto[(size_t)so[j]];
+            }
+            int t = 0;   // tile index bit t: the t-th non-local physical position of the load layout
+            for (int pos = 0; pos < n; ++pos)
+                if (!((P.lmask >> pos) & 1u)) {
+                    int x = 0;
+                    for (int y = 0; y < n; ++y)
+                        if (lay[(size_t)y] == pos) x = y;
+                    P.map.tbit[t++] = (unsigned char)sto[(size_t)x];
+                }
+        }
+    }
+    return out;
+}
+
+// Append the stages of circuit gates gs (global targets, n qubits; see plan_stages) to the stage
+// tables: stage gates are re-fused to at most stage_k qubits (0: kept as they are) and renumbered to
+// local qubits.
+void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int stage_k, bool phase_opt, std::vector<BStage> &st,
+                  std::vector<BChunk> &chunks, std::vector<BGate> &sg, std::vector<float2> &sm, std::vector<BStoreMap> &maps)
+{
+    for (const StagePlan &plan : plan_stages(gs, n, L)) {
+        const std::vector<const FusedGate *> &taken = plan.gates;
         BStage bs{};
-        bs.lmask = S;
+        bs.lmask = plan.lmask;
         bs.chunk_begin = (int)chunks.size();
-        auto local = [&](int q) { return __builtin_popcount(S & ((1u << q) - 1u)); };
+        bs.map = -1;
+        if (plan.mapped) {
+            bs.map = (int)maps.size();
+            maps.push_back(plan.map);
+        }
+        auto local = [&](int q) { return plan.local_of[q]; };
         // a chunk's matrices start at an even offset of the table (16-byte copies)
         auto new_chunk = [&]() {
             if (sm.size() & 1) sm.push_back(make_float2(0.f, 0.f));
@@ -1040,10 +1282,16 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         auto emit = [&](const FusedGate *g, const SignRun &run_true) {
             const int dd = g ? (int)g->ur.size() : 0;
             const SignRun run = run_true.flipped(frame);
-            unsigned fm = 0u;   // the flips on g's targets, as bits of its matrix index
-            if (g)
+            // the kernel takes a gate's local targets ascending: perm[j] = the position in g's
+            // targets of its j-th lowest local target (the matrix index bits follow); fm = the
+            // flips on g's targets, as bits of its matrix index
+            int perm[SV_MAX_K] = {0, 1, 2, 3, 4, 5};
+            unsigned fm = 0u;
+            if (g) {
+                std::sort(perm, perm + g->k, [&](int x, int y) { return local(g->targets[x]) < local(g->targets[y]); });
                 for (int j = 0; j < g->k; ++j)
                     if ((frame >> local(g->targets[j])) & 1u) fm |= 1u << j;
+            }
             if (chunks.size() == (size_t)bs.chunk_begin || chunks.back().gate_count == kStageGateCap ||
                 chunks.back().mat_count + 1 + 2 * dd > kStageMatCap)
                 new_chunk();
@@ -1056,10 +1304,16 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
             b.mat_off = (int)sm.size();
             if (g) {
                 b.k = g->k;
-                for (int j = 0; j < g->k; ++j) b.targets[j] = local(g->targets[j]);
-                // X^f U X^f: entry (r, c) from (r ^ f, c ^ f)
+                for (int j = 0; j < g->k; ++j) b.targets[j] = local(g->targets[perm[j]]);
+                // X^f U X^f with the index bits reordered: entry (r, c) from (old(r) ^ f, old(c) ^ f)
                 const int D = 1 << g->k;
-                auto src = [&](int e) { return (((e / D) ^ (int)fm) * D) + ((e % D) ^ (int)fm); };
+                auto old_index = [&](int x) {
+                    int y = 0;
+                    for (int j = 0; j < g->k; ++j)
+                        if ((x >> j) & 1) y |= 1 << perm[j];
+                    return y;
+                };
+                auto src = [&](int e) { return ((old_index(e / D) ^ (int)fm) * D) + (old_index(e % D) ^ (int)fm); };
                 for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)src(e)], g->ui[(size_t)src(e)]));
                 for (int e = 0; e < dd; ++e) sm.push_back(make_float2(g->ur[(size_t)src(e ^ 1)], g->ui[(size_t)src(e ^ 1)]));
             }
@@ -1414,7 +1668,6 @@ void build_stages(const std::vector<const FusedGate *> &gs, int n, int L, int st
         bs.chunk_count = (int)chunks.size() - bs.chunk_begin;
         bs.frame = frame;
         st.push_back(bs);
-        rest.swap(left);
     }
 }
 
@@ -1434,6 +1687,7 @@ int build_work_list(sv_batch *b)
     std::vector<BChunk> hch;
     std::vector<BGate> hsg;
     std::vector<float2> hsm;
+    std::vector<BStoreMap> hmap;
     for (int c = 0; c < (int)hc.size(); ++c) {
         const int n = hc[(size_t)c].n;
         hc[(size_t)c].done_off = 0;
@@ -1447,7 +1701,7 @@ int build_work_list(sv_batch *b)
             for (int gi = 0; gi < hc[(size_t)c].gate_count; ++gi) gs.push_back(b->src[(size_t)(hc[(size_t)c].gate_begin + gi)]);
             hc[(size_t)c].stage_begin = (int)hst.size();
             try {
-                build_stages(gs, n, L, b->opts.stage_k, b->opts.stage_layers != 0, hst, hch, hsg, hsm);
+                build_stages(gs, n, L, b->opts.stage_k, b->opts.stage_layers != 0, hst, hch, hsg, hsm, hmap);
             } catch (const std::bad_alloc &) {
                 set_error("sv_batch: out of host memory building stages");
                 return SV_ENOMEM;
@@ -1467,7 +1721,7 @@ int build_work_list(sv_batch *b)
             }
             split.push_back(c);
         } else {
-            items.push_back(BItem{kSingle, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}});
+            items.push_back(BItem{kSingle, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, -1, {0, 0}});
         }
     }
     if (hsm.size() & 1) hsm.push_back(make_float2(0.f, 0.f));   // the last chunk's 16-byte copy stays inside
@@ -1495,7 +1749,7 @@ int build_work_list(sv_batch *b)
                 if (s >= (staged ? hc[(size_t)c].n_stages : hc[(size_t)c].gate_count + 1)) continue;
                 any = true;
                 const int t = need[(size_t)(hc[(size_t)c].done_off + s)];
-                BItem it{staged ? kStage : kTile, c, s, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}};
+                BItem it{staged ? kStage : kTile, c, s, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, -1, {0, 0}};
                 if (staged) {
                     const BCirc &C = hc[(size_t)c];
                     const BStage &St = hst[(size_t)(C.stage_begin + s)];
@@ -1508,6 +1762,7 @@ int build_work_list(sv_batch *b)
                     it.chunk_count = St.chunk_count;
                     if (St.chunk_count > 0) it.ch0 = hch[(size_t)St.chunk_begin];
                     it.frame = St.frame;
+                    it.map = St.map;
                 }
                 for (int i = 0; i < t; ++i) {
                     it.tile = i;
@@ -1517,7 +1772,7 @@ int build_work_list(sv_batch *b)
             if (!any) break;
         }
     for (int c = 0; c < (int)hc.size(); ++c)
-        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, {0, 0, 0}});
+        if (hc[(size_t)c].n <= b->opts.smem_max_n) items.push_back(BItem{kWhole, c, 0, 0, 0, 0, 0, 0u, 0, 0, 0, BChunk{}, 0u, -1, {0, 0}});
     if (b->stall && !need.empty()) {   // nothing completes the extra tile: its waiters give up
         need[0] += 1;
         for (BItem &w : items)
@@ -1530,6 +1785,8 @@ int build_work_list(sv_batch *b)
     cudaFree(b->d_chunks);
     cudaFree(b->d_sgates);
     cudaFree(b->d_smats);
+    cudaFree(b->d_smaps);
+    b->d_smaps = nullptr;
     b->d_items = nullptr;
     b->d_need = nullptr;
     b->d_sync = nullptr;
@@ -1566,6 +1823,9 @@ int build_work_list(sv_batch *b)
     if (e == cudaSuccess) e = cudaMalloc(&b->d_chunks, sizeof(BChunk) * std::max<size_t>(hch.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sgates, sizeof(BGate) * std::max<size_t>(hsg.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_smats, sizeof(float2) * std::max<size_t>(hsm.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_smaps, sizeof(BStoreMap) * std::max<size_t>(hmap.size(), 1));
+    if (e == cudaSuccess && !hmap.empty())
+        e = cudaMemcpy(b->d_smaps, hmap.data(), sizeof(BStoreMap) * hmap.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !items.empty()) e = cudaMemcpy(b->d_items, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !need.empty()) e = cudaMemcpy(b->d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !hst.empty()) e = cudaMemcpy(b->d_stages, hst.data(), sizeof(BStage) * hst.size(), cudaMemcpyHostToDevice);
@@ -1598,6 +1858,7 @@ int launch_batch(sv_batch *b)
     a.gate_cap = gate_cap(b->opts);
     a.sgates = b->d_sgates;
     a.smats = b->d_smats;
+    a.smaps = b->d_smaps;
     a.sync = b->d_sync;
     a.need = b->d_need;
     a.err = b->d_err;
@@ -1635,8 +1896,8 @@ int check_opts(const sv_batch_opts &o)
             set_error("sv_batch: device query failed");
             return SV_ECUDA;
         }
-        // each CTA also holds its static shared memory and the 1 KB the system reserves
-        if (2 * (smem_bytes(o) + 2048) > (size_t)per_sm) {
+        // each CTA also holds its static shared memory (under 3 KB) and the 1 KB the system reserves
+        if (2 * (smem_bytes(o) + 4096) > (size_t)per_sm) {
             set_error("sv_batch: ctas_per_sm = 2 needs two CTAs' shared memory (%zu bytes each) on one SM", smem_bytes(o));
             return SV_EINVAL;
         }
@@ -1772,6 +2033,7 @@ extern "C" void sv_batch_free(sv_batch *b)
     cudaFree(b->d_chunks);
     cudaFree(b->d_sgates);
     cudaFree(b->d_smats);
+    cudaFree(b->d_smaps);
     delete b;
 }
 

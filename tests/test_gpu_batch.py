@@ -170,6 +170,36 @@ def test_sign_runs_match_oracle(env, layers):
     b.free()
 
 
+@pytest.mark.parametrize("layers", [0, 1])
+def test_stages_relabel_qubits(env, layers):
+    """The state is relabelled between stages (a tile is stored in the next stage's qubit
+    layout), so no stage has to hold qubits 0-2: an 8-layer CZ-ladder circuit on 20 qubits takes
+    two stages of gates on 14 local qubits and one pass that only relabels (with qubits 0-2 in
+    every stage it took six); the states still equal the oracle's."""
+    B, batch = env
+    rng = np.random.default_rng(41)
+    circuits = [(20, wl.hea_circuit(20, 8, rng)), (17, wl.hea_circuit(17, 5, rng)), (19, _layer_circuit(19, 10, rng))]
+    refs = [oracle.run_circuit(n, g, 0) for n, g in circuits]
+    b = batch.Batch(circuits, 0)
+    b.set(512, 0, 152, True, 8, 12, 0, 14, 2, layers)
+    info = B.sv_batch_get_info(b.h)
+    assert info["staged"] == 3
+    one = batch.Batch(circuits[:1], 0)
+    one.set(512, 0, 152, True, 8, 12, 0, 14, 2, layers)
+    assert B.sv_batch_get_info(one.h)["stages"] == 3
+    one.free()
+    for sl in (14, 12, 10):
+        b.set(512, 0, 152, True, 8, 12, 0, sl, 2, layers)
+        b.arena.fill_(float("nan"))
+        b.run()
+        B.sv_device_status()
+        for i, ref in enumerate(refs):
+            got = b.state(i)
+            assert oracle.fidelity(ref, got) >= 1 - 1e-6, (sl, i)
+            assert oracle.l2_error(ref, got) <= 1e-4, (sl, i)
+    b.free()
+
+
 def test_staging_cuts_traffic_and_waves_keep_results(env):
     """Stages move fewer bytes than one pass per fused gate; waves and a direct launch give the
     same states as the graph replay."""
