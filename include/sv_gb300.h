@@ -399,6 +399,20 @@ typedef struct sv_batch_info {
 SV_API int sv_batch_get_info(sv_batch *b, sv_batch_info *out);
 /* Byte offset of circuit i's state inside the arena. */
 SV_API int sv_batch_state_offset(const sv_batch *b, int i, size_t *offset_bytes);
+/* The stages a batch cuts fused circuit f into at tiles of stage_log2 qubits (8..14; a circuit of
+ * fewer qubits uses all of them) -- host only, no GPU.  The circuit's n must be 8..24 and its gates
+ * uncontrolled.  Returns the number of stages S (or a negative SV_E* code) and writes, for the
+ * first min(S, max_stages) stages s:
+ *   gates[s]              the number of fused gates the stage applies;
+ *   lam[s]                its local qubits (bit q: circuit qubit q), 2^popcount amplitudes a tile;
+ *   load_pos[32 s + q]    the bit of a global index where qubit q sits when the stage loads its
+ *                         tiles (the layout the previous stage stored in; for the first stage, the
+ *                         layout it stores in);
+ *   store_pos[32 s + q]   and where it sits when the stage stores them (the last stage: q itself),
+ * and order[0 .. count(f)) = the fused gates' indices in the order the stages apply them (a
+ * reordering that moves gates only past gates on other qubits).  Any output may be NULL. */
+SV_API int sv_batch_plan_stages(const sv_fused *f, int stage_log2, int max_stages, int *gates, unsigned *lam, int *load_pos,
+                                int *store_pos, int *order);
 /* Test hook for the bounded waits.  on != 0: from the next sv_batch_run the first split circuit's
  * initialisation step (its first stage, when staged) counts one tile more than exists, so the
  * tiles of the next step wait on a counter that never fills; each gives up after about a second,

@@ -123,6 +123,7 @@ def _load():
         "sv_batch_run": (I, [P]),
         "sv_batch_run_loop": (I, [P]),
         "sv_batch_state_offset": (I, [P, I, ctypes.POINTER(ctypes.c_size_t)]),
+        "sv_batch_plan_stages": (I, [P, I, I, P, P, P, P, P]),
         "sv_batch_inject_stall": (I, [P, I]),
         "sv_batch_get_info": (I, [P, ctypes.POINTER(sv_batch_info)]),
         "sv_mlp_num_params": (I, []),
@@ -514,6 +515,29 @@ def sv_batch_run_loop(b) -> None:
 
 def sv_batch_inject_stall(b, on: bool) -> None:
     _check(lib.sv_batch_inject_stall(b, int(bool(on))))
+
+
+def sv_batch_plan_stages(f, stage_log2: int) -> list:
+    """The stages a batch cuts fused circuit f into (host only): per stage its gate count, local
+    qubits, load and store layouts (qubit -> physical bit), and the fused gates it applies."""
+    count = sv_fused_count(f)
+    k = lib.sv_batch_plan_stages(f, stage_log2, 0, None, None, None, None, None)
+    if k < 0:
+        _check(k)
+    gates = (ctypes.c_int * max(k, 1))()
+    lam = (ctypes.c_uint * max(k, 1))()
+    lpos = (ctypes.c_int * (32 * max(k, 1)))()
+    spos = (ctypes.c_int * (32 * max(k, 1)))()
+    order = (ctypes.c_int * max(count, 1))()
+    rc = lib.sv_batch_plan_stages(f, stage_log2, k, gates, lam, lpos, spos, order)
+    if rc < 0:
+        _check(rc)
+    out, at = [], 0
+    for s in range(k):
+        out.append({"gates": list(order[at:at + gates[s]]), "lam": int(lam[s]),
+                    "load_pos": list(lpos[32 * s:32 * s + 32]), "store_pos": list(spos[32 * s:32 * s + 32])})
+        at += gates[s]
+    return out
 
 
 def sv_batch_state_offset(b, i: int) -> int:

@@ -1915,6 +1915,41 @@ int set_smem_attrs(const sv_batch_opts &o)
 
 }  // namespace
 
+extern "C" int sv_batch_plan_stages(const sv_fused *f, int stage_log2, int max_stages, int *gates, unsigned *lam, int *load_pos,
+                                    int *store_pos, int *order)
+{
+    clear_error();
+    if (!f || max_stages < 0) { set_error("sv_batch_plan_stages: bad argument"); return SV_EINVAL; }
+    if (f->n < kStageMinN || f->n > kBatchMaxN) { set_error("sv_batch_plan_stages: n must be in [%d, %d]", kStageMinN, kBatchMaxN); return SV_EINVAL; }
+    if (stage_log2 < kStageMinN || stage_log2 > 14) { set_error("sv_batch_plan_stages: stage_log2 must be in [%d, 14]", kStageMinN); return SV_EINVAL; }
+    std::vector<const FusedGate *> gs;
+    for (const FusedGate &g : f->gates) {
+        if (g.cmask) { set_error("sv_batch_plan_stages: a gate keeps controls"); return SV_EINVAL; }
+        gs.push_back(&g);
+    }
+    std::vector<StagePlan> plan;
+    try {
+        plan = plan_stages(gs, f->n, std::min(f->n, stage_log2));
+    } catch (const std::bad_alloc &) {
+        set_error("sv_batch_plan_stages: out of host memory");
+        return SV_ENOMEM;
+    }
+    int at = 0;
+    for (int s = 0; s < (int)plan.size(); ++s) {
+        const StagePlan &P = plan[(size_t)s];
+        if (order)
+            for (const FusedGate *g : P.gates) order[at++] = (int)(g - f->gates.data());
+        if (s >= max_stages) continue;
+        if (gates) gates[s] = (int)P.gates.size();
+        if (lam) lam[s] = P.lam;
+        for (int q = 0; q < 32; ++q) {
+            if (load_pos) load_pos[32 * s + q] = q < f->n ? P.load_pos[q] : q;
+            if (store_pos) store_pos[32 * s + q] = q < f->n ? P.store_pos[q] : q;
+        }
+    }
+    return (int)plan.size();
+}
+
 extern "C" size_t sv_batch_arena_bytes(const int *n_qubits, int count)
 {
     if (!n_qubits || count < 0) return 0;
