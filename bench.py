@@ -203,7 +203,9 @@ def large_configs(B, wl, model, stream):
     rep = bt.report()
     out["hea256_batch"] = {k: rep[k] for k in ("workload", "batched_ms", "loop_ms", "speedup", "batched_per_gate_tiles_k4_ms",
                                                "traffic_gb", "fused_gates", "state_mb")}
-    out["hea256_batch"]["autotuned"] = {k: rep["autotuned"][k] for k in ("max_k", "stage_log2", "stage_k", "threads", "ctas")}
+    out["hea256_batch"]["autotuned"] = {k: rep["autotuned"][k] for k in ("max_k", "stage_log2", "stage_k", "stage_layers", "threads",
+                                                                        "ctas_per_sm", "ctas", "wave_mb", "split_min_n")}
+    out["hea256_batch"]["list"] = {k: rep["list"][k] for k in ("stages", "stage_gates", "staged", "items")}
     return out
 
 
