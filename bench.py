@@ -179,6 +179,7 @@ def large_configs(B, wl, model, stream):
         variants = [("learned_bf16x3", dict(max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4, model=model)),
                     ("plain_fp32_k4", dict(max_k=4))]
         variants += [(f"greedy_k{k}_bf16x3", dict(max_k=k, precision=B.PREC_BF16X3, tc_min_k=4)) for k in range(2, 7)]
+        variants += [("phases_bf16x3", dict(max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3, tc_min_k=4))]
         for label, kw in variants:
             if kw.get("model", 1) is None:
                 continue

@@ -82,7 +82,17 @@ enum sv_fuse_mode {
                              qubits, one commutes past the blocks between them, and the merged gate
                              is predicted 2% faster than the two); the candidate with the least
                              predicted time wins, each fused gate on its cheapest predicted path */
-    SV_FUSE_NONE = 2      /* no fusion: every input gate becomes its own dense gate (timing, baselines) */
+    SV_FUSE_NONE = 2,     /* no fusion: every input gate becomes its own dense gate (timing, baselines) */
+    SV_FUSE_PHASES = 3    /* greedy fusion into gates of up to max_k = 6 qubits (one open gate at a
+                             time) for the tensor cores (precision TF32 or BF16X3), where a diagonal
+                             gate with one qubit in a full fused gate and one outside it does not
+                             end the gate: its phase on the two qubits' common 1s is applied to the
+                             fused gate's outputs in the same pass (a post-phase; the linear parts
+                             go into the matrix or wait for the outside qubit's next gate).  A
+                             controlled-phase ladder (a QFT) then costs one pass per six qubits.
+                             Gates that cannot carry post-phases (fewer than six qubits, or three or
+                             more targets below qubit 5) get them as diagonal fused gates after
+                             them.  Not with start_qubits. */
 };
 
 typedef struct sv_state sv_state;   /* opaque; owns no state memory, only small workspaces */
@@ -132,6 +142,12 @@ typedef struct sv_fuse_opts {
     double (*cost_us)(int k, const int *targets, int path, int n_qubits, void *cost_ctx);
     void *cost_ctx;
 } sv_fuse_opts;
+
+/* Post-phases of fused gate i (SV_FUSE_PHASES): after the gate's matrix, an amplitude whose bits
+ * targets[target[t]] and qubit[t] are both 1 is multiplied by exp(i angle[t]), for every term t.
+ * Writes up to max_terms terms (any output may be NULL) and returns the number of terms, or a
+ * negative SV_E* code. */
+SV_API int sv_fused_get_post_phases(const sv_fused *f, int i, int max_terms, int *target, int *qubit, double *angle);
 
 /* Facts about one fused gate (introspection). */
 typedef struct sv_fused_info {

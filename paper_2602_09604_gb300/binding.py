@@ -21,7 +21,7 @@ PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3, PATH_C
 PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
               PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3", PATH_CONTROLLED: "controlled"}
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
-FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE = 0, 1, 2
+FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE, FUSE_PHASES = 0, 1, 2, 3
 MAX_K = 6
 MAX_CONTROLS = 33
 
@@ -105,6 +105,7 @@ def _load():
         "sv_fused_count": (I, [P]),
         "sv_fused_get_info": (I, [P, I, ctypes.POINTER(sv_fused_info)]),
         "sv_fused_get_matrix": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
+        "sv_fused_get_post_phases": (I, [P, I, I, P, P, P]),
         "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
         "sv_init_apply": (I, [P, ctypes.c_uint64, P, ctypes.POINTER(sv_timing)]),
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
@@ -277,6 +278,21 @@ def sv_fused_get_info(f, i: int) -> dict:
     return {"k": info.k, "targets": tuple(info.targets[: info.k]), "path": info.path,
             "n_source_gates": info.n_source_gates,
             "controls": tuple(q for q in range(64) if (cm >> q) & 1)}
+
+
+def sv_fused_get_post_phases(f, i: int) -> list:
+    """[(target index, qubit, angle)]: after fused gate i, amplitudes with both bits set get
+    exp(i angle)."""
+    k = lib.sv_fused_get_post_phases(f, i, 0, None, None, None)
+    if k < 0:
+        _check(k)
+    tg = (ctypes.c_int * max(k, 1))()
+    qb = (ctypes.c_int * max(k, 1))()
+    an = (ctypes.c_double * max(k, 1))()
+    rc = lib.sv_fused_get_post_phases(f, i, k, tg, qb, an)
+    if rc < 0:
+        _check(rc)
+    return [(int(tg[t]), int(qb[t]), float(an[t])) for t in range(k)]
 
 
 def sv_fused_get_matrix(f, i: int) -> np.ndarray:

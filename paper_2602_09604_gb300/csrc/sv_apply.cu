@@ -849,6 +849,9 @@ FusedGate remap_gate(const FusedGate &g, uint64_t A, int a)
 // earlier unflagged ones is exact: they share no qubit, so they commute.
 int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<char> *lazy, uint64_t A, uint64_t x, const char *who)
 {
+    if (st->c128)
+        for (const FusedGate &g : f->gates)
+            if (!g.post.empty()) { set_error("%s: post-phases (SV_FUSE_PHASES) are for complex64 states", who); return SV_EINVAL; }
     if (st->c128) SV_TRY(upload_fused_c128(f, st->device));
     else SV_TRY(upload_fused(f, st->device));
     const size_t ng = f->gates.size();
@@ -915,7 +918,7 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
         const size_t i0 = order[m];
         const FusedGate &g0 = f->gates[i0];
         first_reads_small = tc_gate_is_direct(g0) && f->d_tc && i0 < f->tc_offset.size() && f->tc_offset[i0] != SIZE_MAX &&
-                            st->n >= g0.k + 5;
+                            st->n >= g0.k + 5 && g0.post.empty();
     }
     int rc = SV_OK;
     for (size_t oi = 0; oi < ng && rc == SV_OK; ++oi) {
@@ -998,8 +1001,11 @@ extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused 
     if (!st->c128)
         for (size_t i = 0; i < f->gates.size(); ++i) {
             const FusedGate &g = f->gates[i];
-            const uint64_t q = g.mask | g.cmask;
-            if (!(q & blocked) && __builtin_popcountll(A | q) <= limit) {
+            // a gate with post-phases runs on the full state, and its phases name qubits outside
+            // it: a later gate on those cannot move ahead of it either
+            uint64_t q = g.mask | g.cmask;
+            for (const FusedGate::PostTerm &t : g.post) q |= uint64_t(1) << t.q;
+            if (!(q & blocked) && __builtin_popcountll(A | q) <= limit && g.post.empty()) {
                 A |= q;
                 lazy[i] = 1;
                 ++m;

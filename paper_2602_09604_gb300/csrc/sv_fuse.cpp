@@ -774,6 +774,253 @@ int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, in
     return SV_OK;
 }
 
+// ------------------------------------------------------------------ post-phase fusion
+//
+// One fused gate open at a time, its gates kept in order and multiplied out when it closes.  A
+// diagonal gate on qubits a (in the open gate, which has no room for b) and b (outside) splits
+// into its constant and linear parts (into the open gate for a; a diagonal gate of its own on b,
+// held until b's next gate) and its pair part theta x_a x_b: a post-phase term of the open gate
+// (it comes after the gate's gates on a and before anything on b).  Rules that keep the order:
+// a dense gate on a qubit with a post term (either side) ends the open gate, unless its qubits
+// fit and take the term's outside qubit in (then the term becomes an ordinary gate of the open
+// gate, appended: it commutes with everything since it was made); held diagonal gates on other
+// qubits are emitted before the next gate that touches their qubits.  A closed gate that cannot
+// carry post terms on the tensor cores (it must be a 6-qubit gate with at most two targets below
+// qubit 5, not both 0 and 1 among them) is first widened with the terms' outside qubits (the
+// terms become ordinary gates), then with idle qubits of at least 5; failing that, its terms
+// follow it as diagonal fused gates.
+FusedGate block_to_gate(Block &b);
+
+struct PhaseBlock {
+    std::vector<int> qubits;                                      // ascending
+    std::vector<std::pair<std::vector<int>, std::vector<cplx>>> ops;   // in order: (qubits, matrix)
+    std::vector<FusedGate::PostTerm> post;                        // j = the block qubit (not an index yet)
+    int n_src = 0;
+    uint64_t mask() const
+    {
+        uint64_t m = 0;
+        for (int q : qubits) m |= uint64_t(1) << q;
+        return m;
+    }
+};
+
+bool is_diag(const std::vector<cplx> &m, size_t d)
+{
+    for (size_t r = 0; r < d; ++r)
+        for (size_t c = 0; c < d; ++c)
+            if (r != c && std::abs(m[r * d + c]) > 1e-12) return false;
+    return true;
+}
+
+bool post_capable(const std::vector<int> &q)
+{
+    if (q.size() != 6) return false;
+    int nlow = 0;
+    for (int x : q) nlow += x < 5;
+    const bool v4 = q[0] == 0 && q[1] == 1;
+    return nlow <= 2 && !v4;
+}
+
+std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qubits, int max_k, int precision, int tc_min_k)
+{
+    std::vector<FusedGate> out;
+    PhaseBlock cur;
+    std::vector<std::pair<std::vector<int>, std::vector<cplx>>> held;   // diagonal gates off the open block
+    auto emit_block = [&](PhaseBlock &b) {
+        if (b.qubits.empty()) return;
+        // widen a block that holds post terms until it can carry them
+        if (!b.post.empty() && !post_capable(b.qubits)) {
+            std::vector<int> q = b.qubits;
+            for (const auto &t : b.post)
+                if ((int)q.size() < 6 && std::find(q.begin(), q.end(), t.q) == q.end()) q.push_back(t.q);
+            for (int x = n_qubits - 1; x >= 5 && (int)q.size() < 6; --x)
+                if (std::find(q.begin(), q.end(), x) == q.end()) q.push_back(x);
+            std::sort(q.begin(), q.end());
+            if ((int)q.size() <= max_k && post_capable(q)) {
+                b.qubits = q;
+                std::vector<FusedGate::PostTerm> keep;
+                for (const auto &t : b.post) {
+                    if (std::find(q.begin(), q.end(), t.q) != q.end()) {
+                        // both qubits inside now: an ordinary diagonal gate, after the others
+                        const std::vector<cplx> d = {1.0, 1.0, 1.0, std::polar(1.0, t.theta)};
+                        b.ops.push_back({{t.j, t.q}, d});
+                    } else {
+                        keep.push_back(t);
+                    }
+                }
+                b.post = keep;
+            }
+        }
+        PhaseBlock &B = b;
+        std::vector<cplx> M = identity(size_t(1) << B.qubits.size());
+        for (const auto &op : B.ops) left_multiply(M, B.qubits, op.second, op.first);
+        Block blk;
+        blk.qubits = B.qubits;
+        blk.mat = std::move(M);
+        blk.n_src = B.n_src;
+        FusedGate fg = block_to_gate(blk);
+        fg.path = classify_path(fg, n_qubits, precision, tc_min_k, SV_PATH_AUTO);
+        const bool carry = !B.post.empty() && post_capable(B.qubits) && fg.path != SV_PATH_LOW &&
+                           fg.path != SV_PATH_HIGH && fg.path != SV_PATH_MIXED;
+        std::vector<FusedGate::PostTerm> rest;
+        for (const auto &t : B.post) {
+            if (carry) {
+                const int j = int(std::find(B.qubits.begin(), B.qubits.end(), t.j) - B.qubits.begin());
+                fg.post.push_back(FusedGate::PostTerm{j, t.q, t.theta});
+            } else {
+                rest.push_back(t);
+            }
+        }
+        out.push_back(std::move(fg));
+        // terms the gate cannot carry: diagonal fused gates after it, greedily packed
+        if (!rest.empty()) {
+            std::vector<Dense> dd;
+            for (const auto &t : rest) {
+                Dense d;
+                d.q = {t.j, t.q};
+                d.m = {1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, std::polar(1.0, t.theta)};
+                dd.push_back(std::move(d));
+            }
+            std::vector<Block> bl = greedy_partition(dd, n_qubits, max_k);
+            materialize(bl, false);
+            for (Block &x : bl) {
+                FusedGate g = block_to_gate(x);
+                g.path = classify_path(g, n_qubits, precision, tc_min_k, SV_PATH_AUTO);
+                out.push_back(std::move(g));
+            }
+        }
+        b = PhaseBlock{};
+    };
+    auto emit_held = [&](uint64_t touching) {   // held diagonal gates on these qubits, packed
+        std::vector<std::pair<std::vector<int>, std::vector<cplx>>> keep;
+        std::vector<Dense> dd;
+        for (auto &h : held) {
+            uint64_t m = 0;
+            for (int q : h.first) m |= uint64_t(1) << q;
+            if (m & touching) {
+                Dense d;
+                d.q = h.first;
+                d.m = h.second;
+                dd.push_back(std::move(d));
+            } else {
+                keep.push_back(std::move(h));
+            }
+        }
+        held.swap(keep);
+        if (dd.empty()) return;
+        std::vector<Block> bl = greedy_partition(dd, n_qubits, max_k);
+        materialize(bl, false);
+        for (Block &x : bl) {
+            FusedGate g = block_to_gate(x);
+            g.path = classify_path(g, n_qubits, precision, tc_min_k, SV_PATH_AUTO);
+            out.push_back(std::move(g));
+        }
+    };
+    auto post_in = [&]() {
+        uint64_t m = 0;
+        for (const auto &t : cur.post) m |= uint64_t(1) << t.j;
+        return m;
+    };
+    auto post_out = [&]() {
+        uint64_t m = 0;
+        for (const auto &t : cur.post) m |= uint64_t(1) << t.q;
+        return m;
+    };
+    // qubits newly in the open block take its post terms on them in as ordinary gates
+    auto absorb_terms = [&](uint64_t newq) {
+        std::vector<FusedGate::PostTerm> keep;
+        for (const auto &t : cur.post) {
+            if ((newq >> t.q) & 1) {
+                const std::vector<cplx> d = {1.0, 1.0, 1.0, std::polar(1.0, t.theta)};
+                cur.ops.push_back({{t.j, t.q}, d});
+            } else {
+                keep.push_back(t);
+            }
+        }
+        cur.post = keep;
+    };
+    auto add_to_cur = [&](const std::vector<int> &q, const std::vector<cplx> &m) {
+        uint64_t newq = 0;
+        for (int x : q)
+            if (std::find(cur.qubits.begin(), cur.qubits.end(), x) == cur.qubits.end()) {
+                cur.qubits.push_back(x);
+                newq |= uint64_t(1) << x;
+            }
+        std::sort(cur.qubits.begin(), cur.qubits.end());
+        absorb_terms(newq);
+        cur.ops.push_back({q, m});
+        cur.n_src += 1;
+    };
+    for (const Dense &d : dense) {
+        uint64_t gm = 0;
+        for (int x : d.q) gm |= uint64_t(1) << x;
+        if (d.cmask) {   // a controlled gate kept whole: on its own, after what touches its qubits
+            const uint64_t all = gm | d.cmask;
+            if ((cur.mask() | post_out()) & all) emit_block(cur);
+            emit_held(all);
+            Block cb = controlled_block(d, true);
+            cb.mat = evaluate(*cb.node);
+            FusedGate g = block_to_gate(cb);
+            g.path = SV_PATH_CONTROLLED;
+            out.push_back(std::move(g));
+            continue;
+        }
+        const size_t dim = d.m.size() == 0 ? 0 : (size_t)std::llround(std::sqrt((double)d.m.size()));
+        const bool diag = is_diag(d.m, dim);
+        const uint64_t cm = cur.mask();
+        const int unionk = __builtin_popcountll(cm | gm);
+        if (diag && d.q.size() == 2 && (cm & gm) && unionk > max_k && !(post_out() & (cm & gm))) {
+            // one qubit in the open block, one outside: constant and linear parts, and a post term
+            const int a = (cm >> d.q[0]) & 1 ? d.q[0] : d.q[1];
+            const int b = a == d.q[0] ? d.q[1] : d.q[0];
+            const int ba = a == d.q[0] ? 0 : 1;   // local bit of a in d's index
+            const cplx d00 = d.m[0], da = d.m[(size_t)(5 * (1 << ba))], db = d.m[(size_t)(5 * (1 << (1 - ba)))], d11 = d.m[15];
+            // d = d00 * diag_a(1, da/d00) * diag_b(1, db/d00) * exp(i theta x_a x_b)
+            const double theta = std::arg(d11 * d00 / (da * db));
+            add_to_cur({a}, {d00, 0.0, 0.0, da});   // constant and the linear part on a
+            cur.n_src -= 1;
+            if (std::abs(db / d00 - 1.0) > 1e-15) held.push_back({{b}, {1.0, 0.0, 0.0, db / d00}});
+            cur.post.push_back(FusedGate::PostTerm{a, b, theta});
+            cur.n_src += 1;
+            continue;
+        }
+        if (diag && !(cm & gm) && unionk > max_k) {   // a diagonal gate off the open block: held
+            held.push_back({d.q, d.m});
+            continue;
+        }
+        // dense gates (and diagonal ones that fit): held diagonal gates on their qubits go first
+        const bool conflict = (gm & post_in()) != 0;
+        const bool fits = unionk <= max_k;
+        if (conflict || !fits) emit_block(cur);
+        // held gates touching g: into the open block when they fit with g, else before it
+        uint64_t hm = 0;
+        for (auto &h : held)
+            for (int x : h.first)
+                if ((gm >> x) & 1) {
+                    for (int y : h.first) hm |= uint64_t(1) << y;
+                }
+        if (hm) {
+            if (__builtin_popcountll(cur.mask() | gm | hm) <= max_k && !(hm & post_in())) {
+                std::vector<std::pair<std::vector<int>, std::vector<cplx>>> keep;
+                for (auto &h : held) {
+                    uint64_t m = 0;
+                    for (int y : h.first) m |= uint64_t(1) << y;
+                    if (m & gm) add_to_cur(h.first, h.second);
+                    else keep.push_back(std::move(h));
+                }
+                held.swap(keep);
+            } else {
+                emit_block(cur);
+                emit_held(gm);
+            }
+        }
+        add_to_cur(d.q, d.m);
+    }
+    emit_block(cur);
+    emit_held(~uint64_t(0));
+    return out;
+}
+
 bool is_unitary(const std::vector<cplx> &U, size_t d, double tol)
 {
     for (size_t i = 0; i < d; ++i)
@@ -866,7 +1113,14 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     if (opts.precision < SV_PREC_FP32 || opts.precision > SV_PREC_BF16X3) { set_error("sv_fuse_circuit: bad precision %d", opts.precision); return SV_EINVAL; }
     if (opts.tc_min_k < 1 || opts.tc_min_k > SV_MAX_K) { set_error("sv_fuse_circuit: tc_min_k=%d outside [1, 6]", opts.tc_min_k); return SV_EINVAL; }
     if (opts.force_path < SV_PATH_AUTO || opts.force_path > SV_PATH_TC_BF16X3) { set_error("sv_fuse_circuit: bad force_path"); return SV_EINVAL; }
-    if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE) { set_error("sv_fuse_circuit: bad mode"); return SV_EINVAL; }
+    if (opts.mode != SV_FUSE_GREEDY && opts.mode != SV_FUSE_LEARNED && opts.mode != SV_FUSE_NONE && opts.mode != SV_FUSE_PHASES) {
+        set_error("sv_fuse_circuit: bad mode");
+        return SV_EINVAL;
+    }
+    if (opts.mode == SV_FUSE_PHASES && (opts.precision == SV_PREC_FP32 || opts.start_qubits != 0 || opts.force_path != SV_PATH_AUTO)) {
+        set_error("sv_fuse_circuit: SV_FUSE_PHASES needs tensor-core precision, no start_qubits and no forced path");
+        return SV_EINVAL;
+    }
     if (opts.start_qubits < 0 || opts.start_qubits > kMaxStartQubits) { set_error("sv_fuse_circuit: start_qubits=%d outside [0, %d]", opts.start_qubits, kMaxStartQubits); return SV_EINVAL; }
 
     // ---- validate and densify every input gate (controls folded into the matrix where they fit
@@ -953,7 +1207,9 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     };
 
     try {
-        if (opts.mode == SV_FUSE_NONE) {
+        if (opts.mode == SV_FUSE_PHASES) {
+            f->gates = phase_partition(dense, n_qubits, opts.max_k, opts.precision, opts.tc_min_k);
+        } else if (opts.mode == SV_FUSE_NONE) {
             // one block per input gate, matrix re-expressed over its ascending qubit list
             for (int gi = 0; gi < n_gates; ++gi) {
                 if (dense[gi].cmask) {
@@ -1108,6 +1364,19 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
     }
     *out = f;
     return SV_OK;
+}
+
+extern "C" int sv_fused_get_post_phases(const sv_fused *f, int i, int max_terms, int *target, int *qubit, double *angle)
+{
+    clear_error();
+    if (!f || i < 0 || i >= (int)f->gates.size() || max_terms < 0) { set_error("sv_fused_get_post_phases: bad argument"); return SV_EINVAL; }
+    const std::vector<FusedGate::PostTerm> &post = f->gates[(size_t)i].post;
+    for (int t = 0; t < (int)post.size() && t < max_terms; ++t) {
+        if (target) target[t] = post[(size_t)t].j;
+        if (qubit) qubit[t] = post[(size_t)t].q;
+        if (angle) angle[t] = post[(size_t)t].theta;
+    }
+    return (int)post.size();
 }
 
 extern "C" int sv_fused_count(const sv_fused *f)

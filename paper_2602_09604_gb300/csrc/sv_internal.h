@@ -55,6 +55,14 @@ struct FusedGate {
     uint64_t cmask = 0;     // SV_PATH_CONTROLLED: control qubits (all must be 1); else 0
     std::vector<cplx> mat;  // 2^k x 2^k row-major, fp64
     std::vector<float> ur, ui;  // fp32 rounded once from mat
+    // post-phases (SV_FUSE_PHASES): after the matrix, amplitude i is multiplied by
+    // exp(i * sum of theta over the terms with bit targets[j] and bit q of i both set)
+    struct PostTerm {
+        int j;        // target index
+        int q;        // a qubit that is not a target
+        double theta;
+    };
+    std::vector<PostTerm> post;
 };
 
 // Shared-memory tile geometry of a fused gate (used by the CUDA-core tile kernel and the

@@ -54,6 +54,8 @@ struct TcArgs {
     const void *bimg;          // device B image(s)
     unsigned bbytes;           // bytes of the B image(s)
     int *err;                  // device error word (bounded-wait time-outs)
+    const float *ph;           // post-phases: angle tables [target][index byte][256]
+    int ph_nb;                 // index bytes the tables cover
 };
 
 // Virtual source (direct kernels with VS): input amplitude i is src[offset(i) - off] when
@@ -661,7 +663,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int MODE, bool VS, int LW, int EW, int WIN, bool V4>
+template <int MODE, bool VS, int LW, int EW, int WIN, bool V4, bool PH = false>
 __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs &a, const VsArgs &v)
 {
     using S = TcShape<6, MODE>;
@@ -840,12 +842,59 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
         const uint32_t t_lane = ((uint32_t)(quarter * 32)) << 16;
         for (long long i = 0; i < cnt; ++i) {
             const int c = (int)(i % kWsAcc);
-            if (!wait(bar_accfull + 8 * c, (uint32_t)((i / kWsAcc) & 1), 0x20)) break;
-            tc_fence_after();
             unsigned long long b;
             long long fb;
             const bool valid = group_base(tile_of(i), m, b, fb);
+            // post-phases: output member r of group b times exp(i sum_{t: r_t = 1} phi_t(b)), with
+            // phi_t(b) = the sum of target t's table entries over b's index bytes (b has zeros at the
+            // targets): every table read in flight at once, before the wait for the accumulator
+            float er[PH ? K : 1], ei[PH ? K : 1];
+            if constexpr (PH) {
+                constexpr int kMaxBytes = 5;   // indices of up to 40 bits
+                float part[K][kMaxBytes];
+#pragma unroll
+                for (int t = 0; t < K; ++t)
+#pragma unroll
+                    for (int cbyte = 0; cbyte < kMaxBytes; ++cbyte)
+                        part[t][cbyte] = (valid && cbyte < a.ph_nb)
+                                             ? __ldg(a.ph + (t * a.ph_nb + cbyte) * 256 + (int)((b >> (8 * cbyte)) & 255ull))
+                                             : 0.f;
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    const float phi = ((part[t][0] + part[t][1]) + (part[t][2] + part[t][3])) + part[t][4];
+                    sincosf(phi, &ei[t], &er[t]);
+                }
+            }
+            if (!wait(bar_accfull + 8 * c, (uint32_t)((i / kWsAcc) & 1), 0x20)) break;
+            tc_fence_after();
             const uint32_t td = tmem + (uint32_t)(c * S::KD) + t_lane;
+            if constexpr (PH) {
+                // members in Gray-code order, one complex product each
+                static_assert(EW == 4, "post-phases: one epilogue warp per lane quarter");
+#pragma unroll
+                for (int hb = 0; hb < 2; ++hb) {   // members 32 hb .. 32 hb + 31
+                    float ore[32], oim[32];
+                    tmem_ld32(td + (uint32_t)(32 * hb), ore);
+                    tmem_ld32(td + (uint32_t)(32 * (2 + hb)), oim);
+                    if (valid) {
+                        float fr = hb ? er[5] : 1.f, fi = hb ? ei[5] : 0.f;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int x = i ^ (i >> 1);
+                            if (i > 0) {   // bit t of the member changed: times e_t or its conjugate
+                                const int t = __ffs(i) - 1;
+                                const float si = ((x >> t) & 1) ? ei[t] : -ei[t];
+                                const float nr = fr * er[t] - fi * si, ni = fr * si + fi * er[t];
+                                fr = nr;
+                                fi = ni;
+                            }
+                            const float yr = ore[x] * fr - oim[x] * fi, yi = ore[x] * fi + oim[x] * fr;
+                            sv[fb + a.foff[32 * hb + x]] = yr;
+                            sv[fb + a.foff[32 * hb + x] + 32] = yi;
+                        }
+                    }
+                }
+            } else {
             constexpr int NB = EW == 4 ? 4 : 2;   // 32-column blocks this warp reads
 #pragma unroll
             for (int cb = 0; cb < NB; ++cb) {
@@ -860,6 +909,7 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                         sv[fb + a.foff[col % D] + (col >= D ? 32 : 0)] = o[x];
                     }
                 }
+            }
             }
             tc_fence_before();
             mbar_arrive(bar_accempty + 8 * c);
@@ -939,6 +989,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps, kWsWindow, false>(sv, a, v);
 }
 
+// k = 6, at most two targets below qubit 5 (not both 0 and 1), with post-phases in the epilogue
+template <int MODE>
+__global__ void __launch_bounds__(kWsThreads, 1) apply_tc_ws_kernel_ph(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+{
+    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps, kWsWindow, false, true>(sv, a, VsArgs{});
+}
+
 // ---------------------------------------------------------------------------------------- host
 uint16_t bf16_rn(double v)
 {
@@ -981,6 +1038,27 @@ size_t b_image_bytes(int k, int mode)
     const size_t KD = size_t(2) << k;
     return mode == kModeTF32 ? KD * KD * 4 : 2 * KD * KD * 2;
 }
+
+// Post-phase tables after a gate's B image (16-byte aligned): for target t and index byte c,
+// entry v = the sum of the angles of the terms on target t whose qubit is bit (q - 8c) of v,
+// reduced to (-pi, pi] in fp64 before rounding.
+size_t ph_table_offset(int k, int mode) { return (b_image_bytes(k, mode) + 15) & ~size_t(15); }
+size_t ph_table_bytes(int k, int n) { return sizeof(float) * (size_t)k * (size_t)((n + 7) / 8) * 256; }
+
+void write_ph_tables(const FusedGate &g, int n, float *out)
+{
+    const int nb = (n + 7) / 8;
+    for (int t = 0; t < g.k; ++t)
+        for (int c = 0; c < nb; ++c)
+            for (int v = 0; v < 256; ++v) {
+                double s = 0.0;
+                for (const FusedGate::PostTerm &pt : g.post)
+                    if (pt.j == t && pt.q >= 8 * c && pt.q < 8 * c + 8 && ((v >> (pt.q - 8 * c)) & 1)) s += pt.theta;
+                s = std::remainder(s, 2.0 * M_PI);
+                out[(t * nb + c) * 256 + v] = (float)s;
+            }
+}
+
 
 // B image(s) of one gate in the tcgen05 K-major no-swizzle layout (rows = output columns (c', r),
 // K = input columns (c, j)), written to img (b_image_bytes(g.k, mode) bytes, every byte set).
@@ -1077,6 +1155,15 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     a.bbytes = (unsigned)S::B_BYTES;
     SV_TRY(device_err_word(&a.err));
     if (vs && staged) { set_error("tensor-core gate: a virtual source needs a direct variant"); return SV_EINVAL; }
+    const bool ph = !g.post.empty();
+    if (ph) {
+        if (K != 6 || variant != 2 || vs || (g.targets[0] == 0 && g.targets[1] == 1)) {
+            set_error("tensor-core gate: post-phases need a k = 6 gate on the warp-specialised kernel");
+            return SV_EINVAL;
+        }
+        a.ph = reinterpret_cast<const float *>(static_cast<const unsigned char *>(dtc) + ph_table_offset(K, MODE));
+        a.ph_nb = (n + 7) / 8;
+    }
     VsArgs v{};
     if (vs) v = VsArgs{vs->src, vs->mask, vs->rest, vs->off};
     void (*kern)(float *, const TcArgs) = staged ? apply_tc_kernel<K, MODE, true> : apply_tc_kernel<K, MODE, false>;
@@ -1088,7 +1175,7 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
     if constexpr (K == 6) {   // the warp-specialised kernel exists for k = 6 only
         if (variant == 2) {
             const bool v4 = g.targets[0] == 0 && g.targets[1] == 1;
-            kern = v4 ? apply_tc_ws_kernel<MODE, true> : apply_tc_ws_kernel<MODE, false>;
+            kern = ph ? apply_tc_ws_kernel_ph<MODE> : v4 ? apply_tc_ws_kernel<MODE, true> : apply_tc_ws_kernel<MODE, false>;
             kern_vs = apply_tc_ws_kernel_vs<MODE>;
             smem = WsShape<MODE>::SMEM;
             tmem_cols = WsShape<MODE>::TMEM_COLS;
@@ -1096,9 +1183,9 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
             per_sm_regs = 1;
         }
     }
-    // function-attribute slot: variant, virtual source, 16-byte loaders
-    const int akey = variant + (vs ? 3 : 0) + (variant == 2 && !vs && g.targets[0] == 0 && g.targets[1] == 1 ? 6 : 0);
-    static uint64_t attr_set[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
+    // function-attribute slot: variant, virtual source, 16-byte loaders, post-phases
+    const int akey = ph ? 9 : variant + (vs ? 3 : 0) + (variant == 2 && !vs && g.targets[0] == 0 && g.targets[1] == 1 ? 6 : 0);
+    static uint64_t attr_set[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // per kernel form, a bit per device (attributes are per device)
     {
         int dev = 0;
         SV_CUDA_TRY(cudaGetDevice(&dev));
@@ -1137,7 +1224,9 @@ int plan_tc_operands(sv_fused *f, size_t *bytes)
             return SV_EINVAL;
         }
         f->tc_offset[i] = (total + 127) & ~size_t(127);
-        total = f->tc_offset[i] + b_image_bytes(g.k, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3);
+        const int mode = g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3;
+        total = f->tc_offset[i] + b_image_bytes(g.k, mode);
+        if (!g.post.empty()) total = f->tc_offset[i] + ph_table_offset(g.k, mode) + ph_table_bytes(g.k, f->n);
     }
     *bytes = total;
     return SV_OK;
@@ -1152,7 +1241,9 @@ int write_tc_operands(const sv_fused *f, unsigned char *dst)
         // the gates' images are independent: built on host threads (a k = 6 image is 32 K elements)
         host_parallel_for(tc.size(), (tc.size() + 3) / 4, [&](size_t t) {
             const FusedGate &g = f->gates[tc[t]];
-            write_b_image(g, g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3, dst + f->tc_offset[tc[t]]);
+            const int mode = g.path == SV_PATH_TC_TF32 ? kModeTF32 : kModeBF16X3;
+            write_b_image(g, mode, dst + f->tc_offset[tc[t]]);
+            if (!g.post.empty()) write_ph_tables(g, f->n, reinterpret_cast<float *>(dst + f->tc_offset[tc[t]] + ph_table_offset(g.k, mode)));
         });
     } catch (const std::exception &e) {
         set_error("tensor-core operand images: %s", e.what());

@@ -123,12 +123,32 @@ def test_34q_qft_learned_vs_fixed(env):
     B.sv_fused_free(f)
     nrm = st.norm()
     checks["learned_bf16x3"] = dict(zip(("max_rel_amp_error", "l2_estimate"), _qft_samples(st, n, x, 35)))
+    # post-phase fusion: the controlled-phase ladders ride on the six-qubit gates as per-amplitude
+    # phases in the same pass (one pass per six qubits, then the swap network)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3, tc_min_k=4)
+    phases_gates = B.sv_fused_count(f)
+    st.init(x)
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    st.apply(f)
+    e1.record(st.stream)
+    torch.cuda.synchronize()
+    res["phases_bf16x3"] = {"device_s": e0.elapsed_time(e1) / 1e3, "fused_gates": phases_gates}
+    B.sv_fused_free(f)
+    nrm_ph = st.norm()
+    checks["phases_bf16x3"] = dict(zip(("max_rel_amp_error", "l2_estimate"), _qft_samples(st, n, x, 36)))
     st.free()
     REPORT["qft34"] = {"gates": len(gates), "variants": res, "norm": nrm, "checks": checks}
     assert abs(nrm - 1) < 1e-4
     assert checks["plain_fp32_k4"]["max_rel_amp_error"] < 1e-4, checks
     assert checks["learned_bf16x3"]["l2_estimate"] <= 1e-4, checks
     assert checks["learned_bf16x3"]["max_rel_amp_error"] < 2e-4, checks
+    assert abs(nrm_ph - 1) < 1e-4
+    assert checks["phases_bf16x3"]["l2_estimate"] <= 1e-4, checks
+    assert checks["phases_bf16x3"]["max_rel_amp_error"] < 2e-4, checks
+    assert phases_gates <= 12 and res["phases_bf16x3"]["device_s"] < 0.25 * res["learned_bf16x3"]["device_s"], res
     # the learned search gains here: its candidates include the order with the controlled phases
     # (diagonal) deferred, which fuses into fewer passes than any fixed greedy size (105 vs 118)
     best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
