@@ -647,6 +647,28 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // 32 consecutive fp32 columns of this thread's TMEM lane.
+// two loads of 16 columns each (a, b), one wait for both
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        va[i] = __uint_as_float(r[i]);
+        vb[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -851,17 +873,17 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
             float er[PH ? K : 1], ei[PH ? K : 1];
             if constexpr (PH) {
                 constexpr int kMaxBytes = 5;   // indices of up to 40 bits
-                float part[K][kMaxBytes];
+                float tab[K][kMaxBytes];
 #pragma unroll
                 for (int t = 0; t < K; ++t)
 #pragma unroll
                     for (int cbyte = 0; cbyte < kMaxBytes; ++cbyte)
-                        part[t][cbyte] = (valid && cbyte < a.ph_nb)
+                        tab[t][cbyte] = (valid && cbyte < a.ph_nb)
                                              ? __ldg(a.ph + (t * a.ph_nb + cbyte) * 256 + (int)((b >> (8 * cbyte)) & 255ull))
                                              : 0.f;
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
-                    const float phi = ((part[t][0] + part[t][1]) + (part[t][2] + part[t][3])) + part[t][4];
+                    const float phi = ((tab[t][0] + tab[t][1]) + (tab[t][2] + tab[t][3])) + tab[t][4];
                     sincosf(phi, &ei[t], &er[t]);
                 }
             }
@@ -870,16 +892,23 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
             const uint32_t td = tmem + (uint32_t)(c * S::KD) + t_lane;
             if constexpr (PH) {
                 // members in Gray-code order, one complex product each
-                static_assert(EW == 4, "post-phases: one epilogue warp per lane quarter");
+                // EW = 8: two warps per lane quarter, each with half of the members
 #pragma unroll
-                for (int hb = 0; hb < 2; ++hb) {   // members 32 hb .. 32 hb + 31
-                    float ore[32], oim[32];
-                    tmem_ld32(td + (uint32_t)(32 * hb), ore);
-                    tmem_ld32(td + (uint32_t)(32 * (2 + hb)), oim);
+                for (int qq = 0; qq < 16 / EW; ++qq) {   // members 16 qc .. 16 qc + 15 (columns: real, then + 64 imaginary)
+                    const int qc = (EW == 8 ? 2 * part : 0) + qq;
+                    float ore[16], oim[16];
+                    tmem_ld16x2(td + (uint32_t)(16 * qc), td + (uint32_t)(64 + 16 * qc), ore, oim);
                     if (valid) {
-                        float fr = hb ? er[5] : 1.f, fi = hb ? ei[5] : 0.f;
+                        // the chunk's members share bits 4 and 5 (= qc)
+                        float fr = 1.f, fi = 0.f;
+                        if (qc & 1) { fr = er[4]; fi = ei[4]; }
+                        if (qc & 2) {
+                            const float nr = fr * er[5] - fi * ei[5], ni = fr * ei[5] + fi * er[5];
+                            fr = nr;
+                            fi = ni;
+                        }
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
+                        for (int i = 0; i < 16; ++i) {
                             const int x = i ^ (i >> 1);
                             if (i > 0) {   // bit t of the member changed: times e_t or its conjugate
                                 const int t = __ffs(i) - 1;
@@ -889,8 +918,8 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                                 fi = ni;
                             }
                             const float yr = ore[x] * fr - oim[x] * fi, yi = ore[x] * fi + oim[x] * fr;
-                            sv[fb + a.foff[32 * hb + x]] = yr;
-                            sv[fb + a.foff[32 * hb + x] + 32] = yi;
+                            sv[fb + a.foff[16 * qc + x]] = yr;
+                            sv[fb + a.foff[16 * qc + x] + 32] = yi;
                         }
                     }
                 }
@@ -989,11 +1018,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     tc_ws_body<MODE, true, kWsLoadWarps, kWsEpiWarps, kWsWindow, false>(sv, a, v);
 }
 
-// k = 6, at most two targets below qubit 5 (not both 0 and 1), with post-phases in the epilogue
+// k = 6, at most two targets below qubit 5 (not both 0 and 1), with post-phases in the epilogue:
+// two epilogue warps per tensor-memory lane quarter (the phases are the epilogue's work)
+constexpr int kWsPhEpiWarps = 8;
+constexpr int kWsPhThreads = (kWsLoadWarps + kWsPhEpiWarps + 1) * 32;
 template <int MODE>
-__global__ void __launch_bounds__(kWsThreads, 1) apply_tc_ws_kernel_ph(float *__restrict__ sv, const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(kWsPhThreads, 1) apply_tc_ws_kernel_ph(float *__restrict__ sv, const __grid_constant__ TcArgs a)
 {
-    tc_ws_body<MODE, false, kWsLoadWarps, kWsEpiWarps, kWsWindow, false, true>(sv, a, VsArgs{});
+    tc_ws_body<MODE, false, kWsLoadWarps, kWsPhEpiWarps, kWsWindow, false, true>(sv, a, VsArgs{});
 }
 
 // ---------------------------------------------------------------------------------------- host
@@ -1179,7 +1211,7 @@ int launch_tc_t(float *sv, int n, const FusedGate &g, const void *dtc, cudaStrea
             kern_vs = apply_tc_ws_kernel_vs<MODE>;
             smem = WsShape<MODE>::SMEM;
             tmem_cols = WsShape<MODE>::TMEM_COLS;
-            threads = kWsThreads;
+            threads = ph ? kWsPhThreads : kWsThreads;
             per_sm_regs = 1;
         }
     }
