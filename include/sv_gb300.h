@@ -63,8 +63,11 @@ enum sv_path {
     SV_PATH_MIXED = 3,
     SV_PATH_TC_TF32 = 4,
     SV_PATH_TC_BF16X3 = 5,
-    SV_PATH_CONTROLLED = 6   /* a gate kept with its controls: only amplitudes whose control bits
+    SV_PATH_CONTROLLED = 6,  /* a gate kept with its controls: only amplitudes whose control bits
                                 are all 1 are read and written (Section IV, ApplyControlledGate) */
+    SV_PATH_POST_PHASES = 256 /* not a path: a flag or-ed into the tensor-core path passed to a
+                                 caller's cost function (sv_fuse_opts.cost_us) for a gate that
+                                 carries post-phases (SV_FUSE_PHASES) */
 };
 
 enum sv_precision {
@@ -80,8 +83,11 @@ enum sv_fuse_mode {
                              under three rules for which blocks a gate closes, each improved by
                              cost-guided merging (two blocks merge when their union has <= max_k
                              qubits, one commutes past the blocks between them, and the merged gate
-                             is predicted 2% faster than the two); the candidate with the least
-                             predicted time wins, each fused gate on its cheapest predicted path */
+                             is predicted 2% faster than the two); with tensor-core precision,
+                             max_k 6, no start_qubits and a circuit holding diagonal two-qubit
+                             gates, the SV_FUSE_PHASES partition is a candidate too (its gates with
+                             post-phases scored as such); the candidate with the least predicted
+                             time wins, each fused gate on its cheapest predicted path */
     SV_FUSE_NONE = 2,     /* no fusion: every input gate becomes its own dense gate (timing, baselines) */
     SV_FUSE_PHASES = 3    /* greedy fusion into gates of up to max_k = 6 qubits (one open gate at a
                              time) for the tensor cores (precision TF32 or BF16X3), where a diagonal
@@ -137,7 +143,8 @@ typedef struct sv_fuse_opts {
     /* Learned mode with a caller's cost model instead of `model` (used when non-NULL): predicted
      * microseconds of one fused gate of k qubits (targets ascending) run on kernel path `path` in an
      * n-qubit state.  Called on the calling thread during sv_fuse_circuit, once per candidate fused
-     * gate and path; it must not call back into the library.  A negative or non-finite result makes
+     * gate and path (a gate that carries post-phases: path = its tensor-core path |
+     * SV_PATH_POST_PHASES); it must not call back into the library.  A negative or non-finite result makes
      * sv_fuse_circuit fail with SV_EINVAL.  cost_ctx is passed through. */
     double (*cost_us)(int k, const int *targets, int path, int n_qubits, void *cost_ctx);
     void *cost_ctx;
@@ -267,9 +274,10 @@ SV_API void sv_mlp_free(sv_mlp *m);
 SV_API int sv_mlp_get_params(const sv_mlp *m, float *out);     /* host buffer of sv_mlp_num_params() */
 SV_API int sv_mlp_set_params(sv_mlp *m, const float *in);
 /* Feature vector (16 floats) of a fused gate with k targets (any order), kernel path (enum sv_path)
- * and n qubits: [k/6, sorted targets / n (6, padded with -1), one-hot path LOW..TC_BF16X3 (5),
- * n/34, (#targets < 5)/5, max target / n, (smallest target < 5)]. */
-SV_API int sv_mlp_features(int k, const int *targets, int path, int n_qubits, float *out);
+ * and n qubits, carrying post-phases (SV_FUSE_PHASES) or not (post_phases 1 or 0):
+ * [k/6, sorted targets / n (6, padded with -1), one-hot path LOW..TC_BF16X3 (5), n/34,
+ * (#targets < 5)/5, max target / n, post_phases]. */
+SV_API int sv_mlp_features(int k, const int *targets, int path, int n_qubits, int post_phases, float *out);
 /* Loss and gradient of the mean squared error for B rows (X: B x 16, t: B standardised targets,
  * both host), at the current parameters; grads: host buffer of sv_mlp_num_params().  B <= 1024. */
 SV_API int sv_mlp_gradients(sv_mlp *m, const float *X, const float *t, int B, float *loss, float *grads);

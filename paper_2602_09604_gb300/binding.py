@@ -20,6 +20,7 @@ SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNITARY, SV_ESTATE = 0, 
 PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3, PATH_CONTROLLED = range(7)
 PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
               PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3", PATH_CONTROLLED: "controlled"}
+PATH_POST_PHASES = 256   # flag or-ed into the path a cost function sees for a gate with post-phases
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
 FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE, FUSE_PHASES = 0, 1, 2, 3
 MAX_K = 6
@@ -132,7 +133,7 @@ def _load():
         "sv_mlp_free": (None, [P]),
         "sv_mlp_get_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
         "sv_mlp_set_params": (I, [P, ctypes.POINTER(ctypes.c_float)]),
-        "sv_mlp_features": (I, [I, ctypes.POINTER(ctypes.c_int), I, I, ctypes.POINTER(ctypes.c_float)]),
+        "sv_mlp_features": (I, [I, ctypes.POINTER(ctypes.c_int), I, I, I, ctypes.POINTER(ctypes.c_float)]),
         "sv_mlp_gradients": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), I,
                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
         "sv_mlp_adam_step": (I, [P, ctypes.c_float]),
@@ -427,10 +428,10 @@ def sv_mlp_set_params(m, params) -> None:
     _check(lib.sv_mlp_set_params(m, _fptr(p)))
 
 
-def sv_mlp_features(k: int, targets, path: int, n: int) -> np.ndarray:
+def sv_mlp_features(k: int, targets, path: int, n: int, post_phases: bool = False) -> np.ndarray:
     t = (ctypes.c_int * MAX_K)(*[int(x) for x in targets])
     out = np.zeros(16, dtype=np.float32)
-    _check(lib.sv_mlp_features(k, t, path, n, _fptr(out)))
+    _check(lib.sv_mlp_features(k, t, path, n, int(bool(post_phases)), _fptr(out)))
     return out
 
 

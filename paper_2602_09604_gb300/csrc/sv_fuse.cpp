@@ -250,6 +250,7 @@ struct Dense {
     std::vector<int> q;        // qubits: targets then folded controls (local bit order of m)
     std::vector<cplx> m;       // dense matrix with those controls folded in
     uint64_t cmask = 0;        // controls kept as controls (the gate is not fused); else 0
+    int src = 1;               // input gates it stands for (0: a factor split off another gate)
 };
 
 // A controlled gate as its own block over its ascending targets (the matrix expression only with
@@ -263,7 +264,7 @@ Block controlled_block(const Dense &d, bool nodes = true)
         b.node = new_node(b.qubits, nullptr);
         b.node->ops.push_back(MatOp{d.m, d.q, nullptr});
     }
-    b.n_src = 1;
+    b.n_src = d.src;
     b.cmask = d.cmask;
     return b;
 }
@@ -366,7 +367,7 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
                     }
                 kb.pend.push_back({Q[0], P});
             }
-            kb.n_src += 1;
+            kb.n_src += dense[gi].src;
             kb.created = stamp++;
             continue;
         }
@@ -378,7 +379,7 @@ std::vector<Block> greedy_partition(const std::vector<Dense> &dense, int n_qubit
         Block nb;
         for (int q = 0; q < n_qubits; ++q)
             if ((um >> q) & 1) nb.qubits.push_back(q);
-        nb.n_src = 1;
+        nb.n_src = dense[gi].src;
         for (int b : kept)   // pending single-qubit gates carry over (their qubits stay disjoint)
             for (auto &pq : open[b].pend) nb.pend.push_back(pq);
         if (!nodes) {
@@ -547,6 +548,7 @@ uint64_t block_mask(const Block &b)
 // kept, so a (qubit set, state size) is scored once.  Keys: the mask with the state size in the top
 // bits (masks have at most 34 bits).
 uint64_t cost_key(uint64_t mask, int n) { return mask | ((uint64_t)n << 56); }
+constexpr uint64_t kPostKey = uint64_t(1) << 55;   // key flag: the gate carries post-phases
 
 class GateCost {
 public:
@@ -567,18 +569,24 @@ public:
         std::vector<std::array<int, SV_MAX_K>> tg(todo.size());
         for (size_t t = 0; t < todo.size(); ++t) {
             const int n = (int)(todo[t] >> 56);
+            const bool post = (todo[t] & kPostKey) != 0;
             FusedGate g;
-            for (int q = 0; q < 56; ++q)
+            for (int q = 0; q < 55; ++q)
                 if ((todo[t] >> q) & 1) g.targets[g.k++] = q;
             std::copy(g.targets, g.targets + SV_MAX_K, tg[t].begin());
-            std::vector<int> paths = {classify_path(g, n, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO)};
-            if (o_.precision != SV_PREC_FP32 && g.k >= 4 && n >= g.k + 5)
-                paths.push_back(o_.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3);
+            const int tc = o_.precision == SV_PREC_TF32 ? SV_PATH_TC_TF32 : SV_PATH_TC_BF16X3;
+            std::vector<int> paths;
+            if (post) {   // only the tensor-core kernel applies post-phases
+                paths.push_back(tc);
+            } else {
+                paths.push_back(classify_path(g, n, SV_PREC_FP32, SV_MAX_K + 1, SV_PATH_AUTO));
+                if (o_.precision != SV_PREC_FP32 && g.k >= 4 && n >= g.k + 5) paths.push_back(tc);
+            }
             for (int p : paths) {
                 rows.push_back({t, p});
                 if (!o_.cost_us) {
                     float feat[16];
-                    mlp_features(g.k, g.targets, p, n, feat);
+                    mlp_features(g.k, g.targets, p, n, post ? 1 : 0, feat);
                     X.insert(X.end(), feat, feat + 16);
                 }
             }
@@ -587,8 +595,9 @@ public:
         if (o_.cost_us) {
             for (size_t r = 0; r < rows.size(); ++r) {
                 const size_t t = rows[r].first;
-                const uint64_t mask = todo[t] & ((uint64_t(1) << 56) - 1);
-                us[r] = o_.cost_us(__builtin_popcountll(mask), tg[t].data(), rows[r].second, (int)(todo[t] >> 56), o_.cost_ctx);
+                const uint64_t mask = todo[t] & (kPostKey - 1);
+                const int path = rows[r].second | ((todo[t] & kPostKey) ? SV_PATH_POST_PHASES : 0);
+                us[r] = o_.cost_us(__builtin_popcountll(mask), tg[t].data(), path, (int)(todo[t] >> 56), o_.cost_ctx);
                 if (!(us[r] >= 0.0) || !std::isfinite(us[r])) {
                     set_error("sv_fuse_circuit: the cost function returned %g", us[r]);
                     return SV_EINVAL;
@@ -825,7 +834,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
 {
     std::vector<FusedGate> out;
     PhaseBlock cur;
-    std::vector<std::pair<std::vector<int>, std::vector<cplx>>> held;   // diagonal gates off the open block
+    std::vector<Dense> held;   // diagonal gates off the open block (src 0: a factor split off a gate)
     auto emit_block = [&](PhaseBlock &b) {
         if (b.qubits.empty()) return;
         // widen a block that holds post terms until it can carry them
@@ -879,6 +888,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
                 Dense d;
                 d.q = {t.j, t.q};
                 d.m = {1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, std::polar(1.0, t.theta)};
+                d.src = 0;   // its input gate is counted in the gate it followed
                 dd.push_back(std::move(d));
             }
             std::vector<Block> bl = greedy_partition(dd, n_qubits, max_k);
@@ -892,19 +902,11 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         b = PhaseBlock{};
     };
     auto emit_held = [&](uint64_t touching) {   // held diagonal gates on these qubits, packed
-        std::vector<std::pair<std::vector<int>, std::vector<cplx>>> keep;
-        std::vector<Dense> dd;
-        for (auto &h : held) {
+        std::vector<Dense> keep, dd;
+        for (Dense &h : held) {
             uint64_t m = 0;
-            for (int q : h.first) m |= uint64_t(1) << q;
-            if (m & touching) {
-                Dense d;
-                d.q = h.first;
-                d.m = h.second;
-                dd.push_back(std::move(d));
-            } else {
-                keep.push_back(std::move(h));
-            }
+            for (int q : h.q) m |= uint64_t(1) << q;
+            (m & touching ? dd : keep).push_back(std::move(h));
         }
         held.swap(keep);
         if (dd.empty()) return;
@@ -939,7 +941,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         }
         cur.post = keep;
     };
-    auto add_to_cur = [&](const std::vector<int> &q, const std::vector<cplx> &m) {
+    auto add_to_cur = [&](const std::vector<int> &q, const std::vector<cplx> &m, int src) {
         uint64_t newq = 0;
         for (int x : q)
             if (std::find(cur.qubits.begin(), cur.qubits.end(), x) == cur.qubits.end()) {
@@ -949,7 +951,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         std::sort(cur.qubits.begin(), cur.qubits.end());
         absorb_terms(newq);
         cur.ops.push_back({q, m});
-        cur.n_src += 1;
+        cur.n_src += src;
     };
     for (const Dense &d : dense) {
         uint64_t gm = 0;
@@ -977,15 +979,19 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
             const cplx d00 = d.m[0], da = d.m[(size_t)(5 * (1 << ba))], db = d.m[(size_t)(5 * (1 << (1 - ba)))], d11 = d.m[15];
             // d = d00 * diag_a(1, da/d00) * diag_b(1, db/d00) * exp(i theta x_a x_b)
             const double theta = std::arg(d11 * d00 / (da * db));
-            add_to_cur({a}, {d00, 0.0, 0.0, da});   // constant and the linear part on a
-            cur.n_src -= 1;
-            if (std::abs(db / d00 - 1.0) > 1e-15) held.push_back({{b}, {1.0, 0.0, 0.0, db / d00}});
+            add_to_cur({a}, {d00, 0.0, 0.0, da}, 1);   // constant and the linear part on a
+            if (std::abs(db / d00 - 1.0) > 1e-15) {
+                Dense hb;
+                hb.q = {b};
+                hb.m = {1.0, 0.0, 0.0, db / d00};
+                hb.src = 0;
+                held.push_back(std::move(hb));
+            }
             cur.post.push_back(FusedGate::PostTerm{a, b, theta});
-            cur.n_src += 1;
             continue;
         }
         if (diag && !(cm & gm) && unionk > max_k) {   // a diagonal gate off the open block: held
-            held.push_back({d.q, d.m});
+            held.push_back(d);
             continue;
         }
         // dense gates (and diagonal ones that fit): held diagonal gates on their qubits go first
@@ -994,18 +1000,18 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         if (conflict || !fits) emit_block(cur);
         // held gates touching g: into the open block when they fit with g, else before it
         uint64_t hm = 0;
-        for (auto &h : held)
-            for (int x : h.first)
+        for (const Dense &h : held)
+            for (int x : h.q)
                 if ((gm >> x) & 1) {
-                    for (int y : h.first) hm |= uint64_t(1) << y;
+                    for (int y : h.q) hm |= uint64_t(1) << y;
                 }
         if (hm) {
             if (__builtin_popcountll(cur.mask() | gm | hm) <= max_k && !(hm & post_in())) {
-                std::vector<std::pair<std::vector<int>, std::vector<cplx>>> keep;
-                for (auto &h : held) {
+                std::vector<Dense> keep;
+                for (Dense &h : held) {
                     uint64_t m = 0;
-                    for (int y : h.first) m |= uint64_t(1) << y;
-                    if (m & gm) add_to_cur(h.first, h.second);
+                    for (int y : h.q) m |= uint64_t(1) << y;
+                    if (m & gm) add_to_cur(h.q, h.m, h.src);
                     else keep.push_back(std::move(h));
                 }
                 held.swap(keep);
@@ -1014,7 +1020,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
                 emit_held(gm);
             }
         }
-        add_to_cur(d.q, d.m);
+        add_to_cur(d.q, d.m, 1);
     }
     emit_block(cur);
     emit_held(~uint64_t(0));
@@ -1337,6 +1343,39 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             for (size_t c = 0; c < cand.size(); ++c) {
                 const double tot = total(cand[c]);
                 if (c == 0 || tot < best_t) { best = c; best_t = tot; }
+            }
+            // the post-phase partition (SV_FUSE_PHASES) as one more candidate, where it can differ
+            // from the others: tensor-core precision, six-qubit gates, no light-cone split, and a
+            // diagonal two-qubit gate somewhere.  It is made with its matrices (the post terms
+            // come from the gates' entries); a gate that carries post-phases is scored as one.
+            bool phases = opts.precision != SV_PREC_FP32 && opts.max_k == 6 && !split && opts.force_path == SV_PATH_AUTO;
+            if (phases) {
+                bool any = false;
+                for (const Dense &d : dense)
+                    if (d.q.size() == 2 && is_diagonal(d)) any = true;
+                phases = any;
+            }
+            if (phases) {
+                std::vector<FusedGate> ph = phase_partition(dense, n_qubits, opts.max_k, opts.precision, opts.tc_min_k);
+                auto key_of = [&](const FusedGate &g) {
+                    uint64_t m = 0;
+                    for (int j = 0; j < g.k; ++j) m |= uint64_t(1) << g.targets[j];
+                    return cost_key(m, n_qubits) | (g.post.empty() ? 0 : kPostKey);
+                };
+                std::vector<uint64_t> keys;
+                for (const FusedGate &g : ph)
+                    if (!g.cmask) keys.push_back(key_of(g));
+                if ((rc = cost.ensure(keys)) != SV_OK) { delete f; return rc; }
+                double tot = 0.0;
+                for (uint64_t key : keys) tot += cost.us(key);
+                if (tot < best_t) {
+                    for (FusedGate &g : ph)   // gates without post-phases on their cheapest path
+                        if (!g.cmask && g.post.empty()) g.path = cost.path(key_of(g));
+                    f->gates = std::move(ph);
+                    f->lazy_limit = 0;
+                    *out = f;
+                    return SV_OK;
+                }
             }
             f->lazy_limit = __builtin_popcountll(cand[best].a_mask);
             // the winner again, with matrix expressions, and its merges replayed: the same blocks

@@ -145,7 +145,7 @@ int launch_tc_gate(float *sv, int n, const FusedGate &g, const void *dtc, cudaSt
 // that take a TcSource.
 bool tc_gate_is_direct(const FusedGate &g);
 // Cost model (sv_mlp.cu): feature vector, batched prediction in microseconds, trust test.
-void mlp_features(int k, const int *targets_sorted, int path, int n, float *f);
+void mlp_features(int k, const int *targets_sorted, int path, int n, int post, float *f);
 int mlp_predict_us(sv_mlp *m, const float *X, int rows, double *out_us);
 bool mlp_usable(const sv_mlp *m, double max_mape);
 int mlp_fallback_k(const sv_mlp *m);

@@ -214,7 +214,7 @@ int mlp_adam(sv_mlp *m, float lr)
 namespace svg {
 
 // Feature vector of one fused gate (see include/sv_gb300.h, sv_mlp_features).
-void mlp_features(int k, const int *targets_sorted, int path, int n, float *f)
+void mlp_features(int k, const int *targets_sorted, int path, int n, int post, float *f)
 {
     for (int i = 0; i < kIn; ++i) f[i] = 0.f;
     f[0] = (float)k / 6.f;
@@ -228,7 +228,7 @@ void mlp_features(int k, const int *targets_sorted, int path, int n, float *f)
     }
     f[13] = (float)low / 5.f;
     f[14] = (float)mx / (float)n;
-    f[15] = (k > 0 && targets_sorted[0] < 5) ? 1.f : 0.f;
+    f[15] = post ? 1.f : 0.f;
 }
 
 // Predicted microseconds of each feature row (rows on the host); model must be trained.
@@ -325,17 +325,18 @@ extern "C" int sv_mlp_set_params(sv_mlp *m, const float *in)
     return SV_OK;
 }
 
-extern "C" int sv_mlp_features(int k, const int *targets, int path, int n_qubits, float *out)
+extern "C" int sv_mlp_features(int k, const int *targets, int path, int n_qubits, int post_phases, float *out)
 {
     clear_error();
-    if (!targets || !out || k < 1 || k > SV_MAX_K || n_qubits < 1 || n_qubits > SV_MAX_QUBITS) {
+    if (!targets || !out || k < 1 || k > SV_MAX_K || n_qubits < 1 || n_qubits > SV_MAX_QUBITS || post_phases < 0 ||
+        post_phases > 1) {
         set_error("sv_mlp_features: bad argument");
         return SV_EINVAL;
     }
     int t[SV_MAX_K];
     for (int i = 0; i < k; ++i) t[i] = targets[i];
     std::sort(t, t + k);
-    mlp_features(k, t, path, n_qubits, out);
+    mlp_features(k, t, path, n_qubits, post_phases, out);
     return SV_OK;
 }
 

@@ -59,10 +59,14 @@ class _G:
 
 
 def fused_as_gates(B, f):
+    """The fused circuit as plain gates: each fused gate, then its post-phases (a learned partition
+    may be the post-phase one) as controlled phases on (target, outside qubit)."""
     out = []
     for i in range(B.sv_fused_count(f)):
         info = B.sv_fused_get_info(f, i)
         out.append(_G(info["targets"], B.sv_fused_get_matrix(f, i), info["controls"]))
+        for j, q, th in B.sv_fused_get_post_phases(f, i):
+            out.append(_G((info["targets"][j], q), np.diag([1, 1, 1, np.exp(1j * th)])))
     return out
 
 

@@ -1,7 +1,9 @@
 """CPU-only checks of post-phase fusion (SV_FUSE_PHASES, host code): the fused gates followed by
 their post-phases (applied here with numpy: amplitude i times exp(i theta) for each term whose two
 bits are set in i) give the oracle's state for the QFT and for circuits dense in diagonal gates;
-the QFT's controlled-phase ladders collapse into six-qubit gates; bad options are refused."""
+the QFT's controlled-phase ladders collapse into six-qubit gates; each input gate is counted once;
+bad options are refused; the learned search scores the post-phase partition (with the post-phase
+feature and cost flag) and takes it only when it is predicted cheaper."""
 import math
 
 import numpy as np
@@ -66,6 +68,8 @@ def test_qft_phase_fusion_is_exact_and_short(B, n):
     count = B.sv_fused_count(f)
     assert count <= math.ceil(n / 6) + math.ceil(n / 2 / 3) + 1, count
     assert sum(len(B.sv_fused_get_post_phases(f, i)) for i in range(count)) > 0
+    # every input gate is counted once (split-off factors and leftover phases count nowhere)
+    assert sum(B.sv_fused_get_info(f, i)["n_source_gates"] for i in range(count)) == len(gates)
     B.sv_fused_free(f)
 
 
@@ -81,6 +85,7 @@ def test_diagonal_heavy_phase_fusion_is_exact(B, n, seed):
         got = apply_fused_with_phases(B, f, n, psi)
         ref = oracle.run_circuit(n, gates, init)
         assert np.max(np.abs(got - ref)) <= 1e-11
+        assert sum(B.sv_fused_get_info(f, i)["n_source_gates"] for i in range(B.sv_fused_count(f))) == len(gates)
         for i in range(B.sv_fused_count(f)):   # only tensor-core six-qubit gates carry phases
             if B.sv_fused_get_post_phases(f, i):
                 info = B.sv_fused_get_info(f, i)
@@ -94,3 +99,74 @@ def test_phase_mode_refuses_bad_options(B):
     for kw in (dict(precision=B.PREC_FP32), dict(precision=B.PREC_BF16X3, start_qubits=6)):
         with pytest.raises(B.SvError):
             B.sv_fuse_circuit(gates, 10, max_k=6, mode=B.FUSE_PHASES, **kw)
+
+
+def test_post_phases_feature_and_flag(B):
+    t = (3, 7, 9, 12, 15, 20)
+    plain = B.sv_mlp_features(6, t, B.PATH_TC_BF16X3, 24)
+    post = B.sv_mlp_features(6, t, B.PATH_TC_BF16X3, 24, post_phases=True)
+    assert plain[15] == 0.0 and post[15] == 1.0
+    assert np.array_equal(plain[:15], post[:15])
+    assert B.sv_mlp_features(6, (0, 1, 2, 3, 4, 9), B.PATH_TC_BF16X3, 24)[13] == 1.0   # five low targets
+
+
+def test_post_gate_timing_circuit_fuses_one_to_one(B):
+    from paper_2602_09604_gb300.timing_sweep import fuse_post_gates, random_post_targets
+    rng = np.random.default_rng(4)
+    for n in (24, 28, 32):
+        sets = [random_post_targets(n, rng) for _ in range(5)]
+        for t in sets:
+            assert len(t) == 6 and sum(q < 5 for q in t) <= 2 and not {0, 1} <= set(t)
+        f = fuse_post_gates(n, sets, 3, rng)
+        assert B.sv_fused_count(f) == 15
+        assert [B.sv_fused_get_info(f, i)["targets"] for i in range(15)] == [t for t in sets for _ in range(3)]
+        B.sv_fused_free(f)
+
+
+def _learned(B, gates, n, post_factor, seen=None):
+    def cost(k, targets, path, nq):
+        if seen is not None:
+            seen.append(path)
+        c = 2.0 ** nq * (1.0 if (path & ~B.PATH_POST_PHASES) in (B.PATH_TC_TF32, B.PATH_TC_BF16X3) else 3.0)
+        return c * (post_factor if path & B.PATH_POST_PHASES else 1.0)
+    return B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4,
+                             cost_fn=cost)
+
+
+@pytest.mark.parametrize("n", [12, 15])
+def test_learned_search_scores_the_phase_partition(B, n):
+    """The learned search takes the post-phase partition when the cost says it is cheaper (the
+    QFT: a few six-qubit passes against many), and not when gates with post-phases cost too much;
+    either way the fused circuit is the circuit."""
+    gates = wl.qft_circuit(n)
+    fp = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3, tc_min_k=4)
+    n_phase = B.sv_fused_count(fp)
+    B.sv_fused_free(fp)
+    init = (0x3c3c3 * n) % (1 << n)
+    ref = oracle.run_circuit(n, gates, init)
+    seen = []
+    for factor, expect_post in ((1.2, True), (1e4, False)):
+        f = _learned(B, gates, n, factor, seen)
+        count = B.sv_fused_count(f)
+        n_post = sum(len(B.sv_fused_get_post_phases(f, i)) for i in range(count))
+        assert (n_post > 0) == expect_post, (factor, n_post)
+        if expect_post:
+            assert count == n_phase
+        psi = np.zeros(1 << n, complex)
+        psi[init] = 1.0
+        got = apply_fused_with_phases(B, f, n, psi)
+        assert np.max(np.abs(got - ref)) <= 1e-12
+        B.sv_fused_free(f)
+    # gates with post-phases reach the cost function with the flag, on a tensor-core path
+    flagged = [p for p in seen if p & B.PATH_POST_PHASES]
+    assert flagged and all(p & ~B.PATH_POST_PHASES == B.PATH_TC_BF16X3 for p in flagged)
+
+
+def test_learned_search_without_diagonal_pairs_has_no_post_phases(B):
+    rng = np.random.default_rng(9)
+    n = 12
+    gates = [wl.Gate(tuple(int(q) for q in rng.choice(n, size=2, replace=False)), wl.random_unitary(4, rng))
+             for _ in range(60)]
+    f = _learned(B, gates, n, 0.5)   # post-phases made cheap: still none to make
+    assert all(not B.sv_fused_get_post_phases(f, i) for i in range(B.sv_fused_count(f)))
+    B.sv_fused_free(f)
