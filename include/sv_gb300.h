@@ -65,6 +65,8 @@ enum sv_path {
     SV_PATH_TC_BF16X3 = 5,
     SV_PATH_CONTROLLED = 6,  /* a gate kept with its controls: only amplitudes whose control bits
                                 are all 1 are read and written (Section IV, ApplyControlledGate) */
+    SV_PATH_SWAPS = 7,       /* a swap network (SV_FUSE_PHASES): disjoint qubit swaps applied in one
+                                in-place pass; k = 0 and no matrix (sv_fused_get_swaps) */
     SV_PATH_POST_PHASES = 256 /* not a path: a flag or-ed into the tensor-core path passed to a
                                  caller's cost function (sv_fuse_opts.cost_us) for a gate that
                                  carries post-phases (SV_FUSE_PHASES) */
@@ -155,6 +157,11 @@ typedef struct sv_fuse_opts {
  * Writes up to max_terms terms (any output may be NULL) and returns the number of terms, or a
  * negative SV_E* code. */
 SV_API int sv_fused_get_post_phases(const sv_fused *f, int i, int max_terms, int *target, int *qubit, double *angle);
+
+/* Swap network of fused gate i (path SV_PATH_SWAPS): the qubit pairs (qubit_a[t], qubit_b[t]) whose
+ * amplitudes it exchanges, all disjoint.  Writes up to max_pairs pairs (outputs may be NULL) and
+ * returns the number of pairs (0 for any other gate), or a negative SV_E* code. */
+SV_API int sv_fused_get_swaps(const sv_fused *f, int i, int max_pairs, int *qubit_a, int *qubit_b);
 
 /* Facts about one fused gate (introspection). */
 typedef struct sv_fused_info {

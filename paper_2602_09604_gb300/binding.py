@@ -17,9 +17,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsvgb300.so")
 
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNITARY, SV_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3, PATH_CONTROLLED = range(7)
+PATH_AUTO, PATH_LOW, PATH_HIGH, PATH_MIXED, PATH_TC_TF32, PATH_TC_BF16X3, PATH_CONTROLLED, PATH_SWAPS = range(8)
 PATH_NAMES = {PATH_AUTO: "auto", PATH_LOW: "low", PATH_HIGH: "high", PATH_MIXED: "mixed",
-              PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3", PATH_CONTROLLED: "controlled"}
+              PATH_TC_TF32: "tc_tf32", PATH_TC_BF16X3: "tc_bf16x3", PATH_CONTROLLED: "controlled",
+              PATH_SWAPS: "swaps"}
 PATH_POST_PHASES = 256   # flag or-ed into the path a cost function sees for a gate with post-phases
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
 FUSE_GREEDY, FUSE_LEARNED, FUSE_NONE, FUSE_PHASES = 0, 1, 2, 3
@@ -107,6 +108,7 @@ def _load():
         "sv_fused_get_info": (I, [P, I, ctypes.POINTER(sv_fused_info)]),
         "sv_fused_get_matrix": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "sv_fused_get_post_phases": (I, [P, I, I, P, P, P]),
+        "sv_fused_get_swaps": (I, [P, I, I, P, P]),
         "sv_apply_fused_gates": (I, [P, P, ctypes.POINTER(sv_timing)]),
         "sv_init_apply": (I, [P, ctypes.c_uint64, P, ctypes.POINTER(sv_timing)]),
         "sv_norm": (I, [P, ctypes.POINTER(ctypes.c_double)]),
@@ -294,6 +296,19 @@ def sv_fused_get_post_phases(f, i: int) -> list:
     if rc < 0:
         _check(rc)
     return [(int(tg[t]), int(qb[t]), float(an[t])) for t in range(k)]
+
+
+def sv_fused_get_swaps(f, i: int) -> list:
+    """[(qubit a, qubit b)]: the disjoint swaps of fused gate i (a swap network), else []."""
+    k = lib.sv_fused_get_swaps(f, i, 0, None, None)
+    if k < 0:
+        _check(k)
+    qa = (ctypes.c_int * max(k, 1))()
+    qb = (ctypes.c_int * max(k, 1))()
+    rc = lib.sv_fused_get_swaps(f, i, k, qa, qb)
+    if rc < 0:
+        _check(rc)
+    return [(int(qa[t]), int(qb[t])) for t in range(k)]
 
 
 def sv_fused_get_matrix(f, i: int) -> np.ndarray:

@@ -611,6 +611,7 @@ int make_tile_map(const FusedGate &g, int n, int f, TileMap *m)
 
 int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, const void *dtc, cudaStream_t stream, int num_sms)
 {
+    if (g.path == SV_PATH_SWAPS) return launch_swaps(sv, n, g, stream, num_sms);
     if (g.k < 1 || g.k > SV_MAX_K) { set_error("launch: bad k=%d", g.k); return SV_EINVAL; }
     const float2 *umem = reinterpret_cast<const float2 *>(dmat);
     if (g.k == 6 && !umem && g.path != SV_PATH_TC_TF32 && g.path != SV_PATH_TC_BF16X3) {
@@ -851,7 +852,10 @@ int apply_core(sv_state *st, sv_fused *f, sv_timing *timings, const std::vector<
 {
     if (st->c128)
         for (const FusedGate &g : f->gates)
-            if (!g.post.empty()) { set_error("%s: post-phases (SV_FUSE_PHASES) are for complex64 states", who); return SV_EINVAL; }
+            if (!g.post.empty() || !g.swaps.empty()) {
+                set_error("%s: post-phases and swap networks (SV_FUSE_PHASES) are for complex64 states", who);
+                return SV_EINVAL;
+            }
     if (st->c128) SV_TRY(upload_fused_c128(f, st->device));
     else SV_TRY(upload_fused(f, st->device));
     const size_t ng = f->gates.size();
@@ -1002,10 +1006,10 @@ extern "C" int sv_init_apply(sv_state *st, uint64_t basis_index, const sv_fused 
         for (size_t i = 0; i < f->gates.size(); ++i) {
             const FusedGate &g = f->gates[i];
             // a gate with post-phases runs on the full state, and its phases name qubits outside
-            // it: a later gate on those cannot move ahead of it either
+            // it: a later gate on those cannot move ahead of it either; so does a swap network
             uint64_t q = g.mask | g.cmask;
             for (const FusedGate::PostTerm &t : g.post) q |= uint64_t(1) << t.q;
-            if (!(q & blocked) && __builtin_popcountll(A | q) <= limit && g.post.empty()) {
+            if (!(q & blocked) && __builtin_popcountll(A | q) <= limit && g.post.empty() && g.swaps.empty()) {
                 A |= q;
                 lazy[i] = 1;
                 ++m;

@@ -1925,6 +1925,7 @@ extern "C" int sv_batch_plan_stages(const sv_fused *f, int stage_log2, int max_s
     std::vector<const FusedGate *> gs;
     for (const FusedGate &g : f->gates) {
         if (g.cmask) { set_error("sv_batch_plan_stages: a gate keeps controls"); return SV_EINVAL; }
+        if (!g.post.empty() || !g.swaps.empty() || g.k < 1) { set_error("sv_batch_plan_stages: post-phases and swap networks are not staged"); return SV_EINVAL; }
         gs.push_back(&g);
     }
     std::vector<StagePlan> plan;
@@ -1974,6 +1975,7 @@ extern "C" int sv_batch_create(const sv_fused *const *circuits, int count, void 
         for (const FusedGate &g : circuits[i]->gates) {
             if (g.k > kBatchMaxK) { set_error("sv_batch_create: circuit %d has a %d-qubit fused gate (batch kernel takes k <= %d)", i, g.k, kBatchMaxK); return SV_EINVAL; }
             if (g.cmask) { set_error("sv_batch_create: circuit %d keeps a controlled gate (fuse with max_k >= its qubit count)", i); return SV_EINVAL; }
+            if (!g.post.empty() || !g.swaps.empty()) { set_error("sv_batch_create: circuit %d has post-phases or a swap network (SV_FUSE_PHASES is for single states)", i); return SV_EINVAL; }
         }
     }
     const size_t need = sv_batch_arena_bytes(ns.data(), count);

@@ -821,6 +821,20 @@ bool is_diag(const std::vector<cplx> &m, size_t d)
     return true;
 }
 
+// A SWAP gate: two qubits, no controls, the matrix exchanging |01> and |10>.
+bool is_swap(const Dense &d)
+{
+    if (d.cmask || d.q.size() != 2 || d.m.size() != 16) return false;
+    for (size_t r = 0; r < 4; ++r)
+        for (size_t c = 0; c < 4; ++c) {
+            const bool one = (r == 0 && c == 0) || (r == 3 && c == 3) || (r == 1 && c == 2) || (r == 2 && c == 1);
+            if (std::abs(d.m[r * 4 + c] - cplx(one ? 1.0 : 0.0)) > 1e-12) return false;
+        }
+    return true;
+}
+
+constexpr int kMinSwapRun = 3;   // consecutive disjoint SWAP gates that become one swap network
+
 bool post_capable(const std::vector<int> &q)
 {
     if (q.size() != 6) return false;
@@ -941,6 +955,42 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         }
         cur.post = keep;
     };
+    // swap networks: runs of at least kMinSwapRun consecutive SWAP gates on disjoint qubits (a
+    // state of at least 10 qubits) are applied as one in-place pass; a run stays open until a gate
+    // on one of its qubits arrives (gates on other qubits commute with it)
+    std::vector<int> run_id(dense.size(), -1);
+    if (n_qubits >= 10) {
+        size_t i = 0;
+        int id = 0;
+        while (i < dense.size()) {
+            size_t j = i;
+            uint64_t m = 0;
+            while (j < dense.size() && is_swap(dense[j])) {
+                const uint64_t q = (uint64_t(1) << dense[j].q[0]) | (uint64_t(1) << dense[j].q[1]);
+                if (m & q) break;
+                m |= q;
+                ++j;
+            }
+            if (j - i >= (size_t)kMinSwapRun) {
+                for (size_t t = i; t < j; ++t) run_id[t] = id;
+                ++id;
+                i = j;
+            } else {
+                i = std::max(j, i + 1);
+            }
+        }
+    }
+    FusedGate run;
+    int run_open = -1;
+    auto emit_run = [&]() {
+        if (run_open < 0) return;
+        run.path = SV_PATH_SWAPS;
+        run.k = 0;
+        run.mask_lo = (uint32_t)(run.mask & 0xffffffffull);
+        out.push_back(std::move(run));
+        run = FusedGate{};
+        run_open = -1;
+    };
     auto add_to_cur = [&](const std::vector<int> &q, const std::vector<cplx> &m, int src) {
         uint64_t newq = 0;
         for (int x : q)
@@ -953,9 +1003,20 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
         cur.ops.push_back({q, m});
         cur.n_src += src;
     };
-    for (const Dense &d : dense) {
+    for (size_t di = 0; di < dense.size(); ++di) {
+        const Dense &d = dense[di];
         uint64_t gm = 0;
         for (int x : d.q) gm |= uint64_t(1) << x;
+        if (run_open >= 0 && ((run_id[di] >= 0 && run_id[di] != run_open) || ((gm | d.cmask) & run.mask))) emit_run();
+        if (run_id[di] >= 0) {   // a SWAP of a run: after everything before it on its qubits
+            if ((cur.mask() | post_out()) & gm) emit_block(cur);
+            emit_held(gm);
+            run_open = run_id[di];
+            run.swaps.push_back({std::min(d.q[0], d.q[1]), std::max(d.q[0], d.q[1])});
+            run.mask |= gm;
+            run.n_src += d.src;
+            continue;
+        }
         if (d.cmask) {   // a controlled gate kept whole: on its own, after what touches its qubits
             const uint64_t all = gm | d.cmask;
             if ((cur.mask() | post_out()) & all) emit_block(cur);
@@ -1024,6 +1085,7 @@ std::vector<FusedGate> phase_partition(const std::vector<Dense> &dense, int n_qu
     }
     emit_block(cur);
     emit_held(~uint64_t(0));
+    emit_run();
     return out;
 }
 
@@ -1357,7 +1419,10 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
             }
             if (phases) {
                 std::vector<FusedGate> ph = phase_partition(dense, n_qubits, opts.max_k, opts.precision, opts.tc_min_k);
+                // a swap network is one read and one write of the state: scored as a one-qubit
+                // gate on the top qubit (the cheapest full pass there is)
                 auto key_of = [&](const FusedGate &g) {
+                    if (g.path == SV_PATH_SWAPS) return cost_key(uint64_t(1) << (n_qubits - 1), n_qubits);
                     uint64_t m = 0;
                     for (int j = 0; j < g.k; ++j) m |= uint64_t(1) << g.targets[j];
                     return cost_key(m, n_qubits) | (g.post.empty() ? 0 : kPostKey);
@@ -1370,7 +1435,7 @@ extern "C" int sv_fuse_circuit(const sv_gate *gates, int n_gates, int n_qubits,
                 for (uint64_t key : keys) tot += cost.us(key);
                 if (tot < best_t) {
                     for (FusedGate &g : ph)   // gates without post-phases on their cheapest path
-                        if (!g.cmask && g.post.empty()) g.path = cost.path(key_of(g));
+                        if (!g.cmask && g.post.empty() && g.path != SV_PATH_SWAPS) g.path = cost.path(key_of(g));
                     f->gates = std::move(ph);
                     f->lazy_limit = 0;
                     *out = f;
@@ -1418,6 +1483,18 @@ extern "C" int sv_fused_get_post_phases(const sv_fused *f, int i, int max_terms,
     return (int)post.size();
 }
 
+extern "C" int sv_fused_get_swaps(const sv_fused *f, int i, int max_pairs, int *qubit_a, int *qubit_b)
+{
+    clear_error();
+    if (!f || i < 0 || i >= (int)f->gates.size() || max_pairs < 0) { set_error("sv_fused_get_swaps: bad argument"); return SV_EINVAL; }
+    const std::vector<std::pair<int, int>> &sw = f->gates[(size_t)i].swaps;
+    for (int t = 0; t < (int)sw.size() && t < max_pairs; ++t) {
+        if (qubit_a) qubit_a[t] = sw[(size_t)t].first;
+        if (qubit_b) qubit_b[t] = sw[(size_t)t].second;
+    }
+    return (int)sw.size();
+}
+
 extern "C" int sv_fused_count(const sv_fused *f)
 {
     return f ? (int)f->gates.size() : SV_EINVAL;
@@ -1442,6 +1519,7 @@ extern "C" int sv_fused_get_matrix(const sv_fused *f, int i, double *out)
     clear_error();
     if (!f || !out || i < 0 || i >= (int)f->gates.size()) { set_error("sv_fused_get_matrix: bad argument"); return SV_EINVAL; }
     const FusedGate &g = f->gates[size_t(i)];
+    if (g.path == SV_PATH_SWAPS) { set_error("sv_fused_get_matrix: gate %d is a swap network (sv_fused_get_swaps)", i); return SV_EINVAL; }
     for (size_t e = 0; e < g.mat.size(); ++e) {
         out[2 * e] = g.mat[e].real();
         out[2 * e + 1] = g.mat[e].imag();

@@ -63,6 +63,8 @@ struct FusedGate {
         double theta;
     };
     std::vector<PostTerm> post;
+    // SV_PATH_SWAPS: the gate is these disjoint qubit swaps (k = 0, no matrix; mask = their qubits)
+    std::vector<std::pair<int, int>> swaps;
 };
 
 // Shared-memory tile geometry of a fused gate (used by the CUDA-core tile kernel and the
@@ -114,6 +116,9 @@ int launch_fused_gate(float *sv, int n, const FusedGate &g, const float *dmat, c
                       cudaStream_t stream, int num_sms);
 
 int device_sm_count(int device);
+
+// Swap networks (sv_swap.cu): one in-place pass applying g.swaps (10 <= n qubits).
+int launch_swaps(float *sv, int n, const FusedGate &g, cudaStream_t stream, int num_sms);
 
 // Tensor-core path (sv_tc.cu): host-side operand images and the launcher.
 // Tensor-core operand images of f's tensor-core gates: plan_tc_operands sets f->tc_offset (byte

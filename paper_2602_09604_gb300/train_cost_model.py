@@ -6,8 +6,8 @@ Timings: random fused gates (k = 1..6; targets all below qubit 5, all at or abov
 anywhere) on n = 24..32-qubit states, on every kernel path that can run them (CUDA-core class
 path, tensor cores in 3xBF16 and TF32 for k >= 4), median of repeats after a warm-up launch
 (timing_sweep.time_specs); and six-qubit tensor-core gates that carry post-phases
-(timing_sweep.time_post_specs, feature post_phases = 1).  Training: sv_mlp_train (the library's forward / backward / Adam
-kernels), 10% held out to measure the prediction error.
+(timing_sweep.time_post_specs, feature post_phases = 1).  Training: sv_mlp_train (the library's
+forward / backward / Adam kernels), 10% held out to measure the prediction error.
 """
 from __future__ import annotations
 

@@ -148,9 +148,9 @@ def test_34q_qft_learned_vs_fixed(env):
     assert abs(nrm_ph - 1) < 1e-4
     assert checks["phases_bf16x3"]["l2_estimate"] <= 1e-4, checks
     assert checks["phases_bf16x3"]["max_rel_amp_error"] < 2e-4, checks
-    assert phases_gates <= 12 and res["phases_bf16x3"]["device_s"] < 0.25 * res["learned_bf16x3"]["device_s"], res
-    # the learned search gains here: its candidates include the order with the controlled phases
-    # (diagonal) deferred, which fuses into fewer passes than any fixed greedy size (105 vs 118)
     best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
-    assert res["learned_bf16x3"]["fused_gates"] < res["greedy_k6_bf16x3"]["fused_gates"], res
-    assert res["learned_bf16x3"]["device_s"] <= 0.97 * best_fixed, res
+    assert phases_gates <= 12 and res["phases_bf16x3"]["device_s"] < 0.25 * best_fixed, res
+    # the learned search gains here: its candidates include the post-phase partition, which the
+    # model (trained on timings of gates with post-phases too) scores cheapest
+    assert res["learned_bf16x3"]["fused_gates"] == phases_gates, res
+    assert res["learned_bf16x3"]["device_s"] <= 0.25 * best_fixed, res

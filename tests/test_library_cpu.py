@@ -62,8 +62,12 @@ def fused_as_gates(B, f):
     """The fused circuit as plain gates: each fused gate, then its post-phases (a learned partition
     may be the post-phase one) as controlled phases on (target, outside qubit)."""
     out = []
+    swap = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
     for i in range(B.sv_fused_count(f)):
         info = B.sv_fused_get_info(f, i)
+        if info["path"] == B.PATH_SWAPS:   # a swap network (the post-phase partition makes them)
+            out += [_G((a, b), swap) for a, b in B.sv_fused_get_swaps(f, i)]
+            continue
         out.append(_G(info["targets"], B.sv_fused_get_matrix(f, i), info["controls"]))
         for j, q, th in B.sv_fused_get_post_phases(f, i):
             out.append(_G((info["targets"][j], q), np.diag([1, 1, 1, np.exp(1j * th)])))
@@ -75,7 +79,7 @@ def check_fusion(B, n, gates, max_k, init=0, **kw):
     try:
         infos = [B.sv_fused_get_info(f, i) for i in range(B.sv_fused_count(f))]
         biggest = max(len(g.targets) + len(g.controls) for g in gates)
-        assert all(1 <= x["k"] <= max(max_k, biggest) for x in infos)
+        assert all(1 <= x["k"] <= max(max_k, biggest) or (x["k"] == 0 and x["path"] == B.PATH_SWAPS) for x in infos)
         assert sum(x["n_source_gates"] for x in infos) == len(gates)
         assert all(list(x["targets"]) == sorted(x["targets"]) for x in infos)
         ref = oracle.run_circuit(n, gates, init)

@@ -21,10 +21,19 @@ def B():
     return binding
 
 
+SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
 def apply_fused_with_phases(B, f, n, psi):
     idx = np.arange(1 << n)
     for i in range(B.sv_fused_count(f)):
         info = B.sv_fused_get_info(f, i)
+        if info["path"] == B.PATH_SWAPS:   # a swap network: its swaps, one by one
+            assert info["k"] == 0 and not B.sv_fused_get_post_phases(f, i)
+            for a, b in B.sv_fused_get_swaps(f, i):
+                oracle.apply_gate(psi, n, wl.Gate((a, b), SWAP))
+            continue
+        assert not B.sv_fused_get_swaps(f, i)
         oracle.apply_gate(psi, n, wl.Gate(info["targets"], B.sv_fused_get_matrix(f, i)))
         post = B.sv_fused_get_post_phases(f, i)
         if post:
@@ -169,4 +178,52 @@ def test_learned_search_without_diagonal_pairs_has_no_post_phases(B):
              for _ in range(60)]
     f = _learned(B, gates, n, 0.5)   # post-phases made cheap: still none to make
     assert all(not B.sv_fused_get_post_phases(f, i) for i in range(B.sv_fused_count(f)))
+    B.sv_fused_free(f)
+
+
+def test_qft_swap_network_is_one_gate(B):
+    for n in (12, 15):
+        f = B.sv_fuse_circuit(wl.qft_circuit(n), n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+        nets = [i for i in range(B.sv_fused_count(f)) if B.sv_fused_get_info(f, i)["path"] == B.PATH_SWAPS]
+        assert nets == [B.sv_fused_count(f) - 1]
+        assert sorted(B.sv_fused_get_swaps(f, nets[0])) == [(q, n - 1 - q) for q in range(n // 2)]
+        assert B.sv_fused_get_info(f, nets[0])["n_source_gates"] == n // 2
+        with pytest.raises(B.SvError):
+            B.sv_fused_get_matrix(f, nets[0])
+        B.sv_fused_free(f)
+
+
+def test_short_or_overlapping_swap_runs_stay_ordinary_gates(B):
+    n = 12
+    for pairs in ([(0, 7), (3, 9)], [(0, 1), (1, 2), (2, 3)], [(4, 5), (6, 7), (5, 8)]):
+        gates = [wl.Gate(p, SWAP) for p in pairs]
+        f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+        assert all(B.sv_fused_get_info(f, i)["path"] != B.PATH_SWAPS for i in range(B.sv_fused_count(f)))
+        B.sv_fused_free(f)
+    # fewer than 10 qubits: no swap networks at all
+    f = B.sv_fuse_circuit([wl.Gate((q, 8 - q), SWAP) for q in range(4)], 9, max_k=6, mode=B.FUSE_PHASES,
+                          precision=B.PREC_BF16X3)
+    assert all(B.sv_fused_get_info(f, i)["path"] != B.PATH_SWAPS for i in range(B.sv_fused_count(f)))
+    B.sv_fused_free(f)
+
+
+@pytest.mark.parametrize("n,seed", [(10, 4), (12, 5), (14, 6)])
+def test_swap_runs_among_other_gates_are_exact(B, n, seed):
+    """Runs of disjoint swaps between dense, diagonal and controlled-phase gates: the swap network
+    is placed after everything before it on its qubits and before everything after it there."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(8):
+        gates += _diag_circuit(n, 25, rng)
+        qs = [int(q) for q in rng.permutation(n)]
+        gates += [wl.Gate((qs[2 * i], qs[2 * i + 1]), SWAP) for i in range(int(rng.integers(3, n // 2 + 1)))]
+    f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+    count = B.sv_fused_count(f)
+    assert sum(B.sv_fused_get_info(f, i)["path"] == B.PATH_SWAPS for i in range(count)) >= 4
+    assert sum(B.sv_fused_get_info(f, i)["n_source_gates"] for i in range(count)) == len(gates)
+    init = int(rng.integers(0, 1 << n))
+    psi = np.zeros(1 << n, complex)
+    psi[init] = 1.0
+    got = apply_fused_with_phases(B, f, n, psi)
+    assert np.max(np.abs(got - oracle.run_circuit(n, gates, init))) <= 1e-11
     B.sv_fused_free(f)
