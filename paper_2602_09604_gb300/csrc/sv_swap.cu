@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kSwapThreads, kSwapCtasPerSm) swap_kernel(floa
     float *stage = smem;        // kSwapStages x kSwapStageBlocks x 64 floats
     long long *toff = reinterpret_cast<long long *>(smem + kSwapStages * kSwapStageBlocks * 64);   // nb
     long long *meta = toff + nb;   // (kSwapStages + 1) x (base, partner): the tiles of the coming stages
-    unsigned short *tab = reinterpret_cast<unsigned short *>(meta + 2 * (kSwapStages + 1));   // nb * 32
+    unsigned short *tab = reinterpret_cast<unsigned short *>(meta + 2 * (kSwapStages + 1) + 2 * a.n_o);   // nb * 32
     unsigned char *fsw = reinterpret_cast<unsigned char *>(tab + nb * 32);                     // nb
     // float offset of tile block t from the tile's base block, and its bank swizzle: the 16-byte
     // chunk j of block t's real (imaginary) half is stored at chunk j ^ fsw[t], fsw[t] = t's bits
@@ -84,26 +84,53 @@ __global__ void __launch_bounds__(kSwapThreads, kSwapCtasPerSm) swap_kernel(floa
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nw = kSwapThreads / 32;
+    // thread 0 walks this CTA's contiguous range of tile ids and fills the stage table one stage
+    // ahead of its copies.  base(u) deposits u's bits at opos; the partner is base ^ L(base), L
+    // linear over GF(2) (each outside pair (x, y) adds x ^ y at both bits), so stepping u -> u + 1
+    // (bits opos[0..k] toggle, k = the trailing ones of u) updates base and L(base) by two table
+    // entries.
+    long long *flip = meta + 2 * (kSwapStages + 1);   // n_o entries: toggled block bits
+    long long *flipl = flip + a.n_o;                    // n_o entries: L of those
     const long long n_tiles = 1ll << a.n_o;
-    // thread 0 walks this CTA's tile ids and fills the stage table one stage ahead of its copies
-    long long u = blockIdx.x;
-    auto plan = [&](int j) {   // tile of stage j (a pair is moved from its smaller base)
-        long long base = -1, part = -1;
-        for (; u < n_tiles; u += gridDim.x) {
-            long long b = 0;
-            for (int i = 0; i < a.n_o; ++i) b |= ((u >> i) & 1ll) << a.opos[i];
-            long long p = b;
-            for (int i = 0; i < a.n_out; ++i)
-                if (((p >> a.out_a[i]) ^ (p >> a.out_b[i])) & 1ll) p ^= (1ll << a.out_a[i]) | (1ll << a.out_b[i]);
-            if (p >= b) {
-                base = b;
-                part = p;
-                u += gridDim.x;
-                break;
+    const long long per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    long long u = (long long)blockIdx.x * per, u_end = u + per < n_tiles ? u + per : n_tiles;
+    long long wb = 0, wl = 0;   // base(u) and L(base(u)), thread 0 only
+    if (threadIdx.x == 0) {
+        long long m = 0, l = 0;
+        for (int i = 0; i < a.n_o; ++i) {
+            const long long bit = 1ll << a.opos[i];
+            long long lbit = 0;
+            for (int j = 0; j < a.n_out; ++j)
+                if (a.opos[i] == a.out_a[j] || a.opos[i] == a.out_b[j]) lbit = (1ll << a.out_a[j]) | (1ll << a.out_b[j]);
+            m |= bit;
+            l ^= lbit;
+            flip[i] = m;
+            flipl[i] = l;
+            if ((u >> i) & 1) {
+                wb |= bit;
+                wl ^= lbit;
             }
         }
-        meta[2 * (j % (kSwapStages + 1))] = base;
-        meta[2 * (j % (kSwapStages + 1)) + 1] = part;
+    }
+    auto plan = [&](int j) {   // tile of stage j (a pair is moved from its smaller base)
+        long long b = -1, p = -1;
+        while (u < u_end) {
+            const long long pp = wb ^ wl;
+            const bool ok = pp >= wb;
+            if (ok) {
+                b = wb;
+                p = pp;
+            }
+            const int k = __ffsll(~u) - 1;   // u -> u + 1 toggles opos[0..k]
+            ++u;
+            if (k < a.n_o) {
+                wb ^= flip[k];
+                wl ^= flipl[k];
+            }
+            if (ok) break;
+        }
+        meta[2 * (j % (kSwapStages + 1))] = b;
+        meta[2 * (j % (kSwapStages + 1)) + 1] = p;
     };
     // 16-byte copies of stage j's tile (and partner) into its slot: chunk q = (tile s, block t,
     // chunk j of 16: real 0..7, imaginary 8..15)
@@ -119,9 +146,10 @@ __global__ void __launch_bounds__(kSwapThreads, kSwapCtasPerSm) swap_kernel(floa
         }
         cp_async_commit();   // one group per stage, empty or not
     };
+    __syncthreads();   // tables ready
     if (threadIdx.x == 0)
         for (int j = 0; j < kSwapStages; ++j) plan(j);
-    __syncthreads();   // tables and the first stages' tiles ready
+    __syncthreads();   // the first stages' tiles ready
 #pragma unroll 1
     for (int j = 0; j < kSwapStages - 1; ++j) issue(j);
 #pragma unroll 1
@@ -222,7 +250,8 @@ int launch_swaps(float *sv, int n, const FusedGate &g, cudaStream_t stream, int 
         return SV_EINVAL;
     }
     const size_t smem = (size_t)kSwapStages * kSwapStageBlocks * 64 * sizeof(float) + (size_t)nb * sizeof(long long) +
-                        (size_t)2 * (kSwapStages + 1) * sizeof(long long) + (size_t)nb * 32 * sizeof(unsigned short) + (size_t)nb;
+                        (size_t)(2 * (kSwapStages + 1) + 2 * a.n_o) * sizeof(long long) + (size_t)nb * 32 * sizeof(unsigned short) +
+                        (size_t)nb;
     static bool attr_set[64] = {};
     int dev = 0;
     SV_CUDA_TRY(cudaGetDevice(&dev));
