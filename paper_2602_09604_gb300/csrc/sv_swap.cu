@@ -23,11 +23,13 @@
 namespace svg {
 namespace {
 
-constexpr int kSwapThreads = 256;
-constexpr int kSwapStages = 4;
+constexpr int kSwapThreads = 512;
+constexpr int kSwapStages = 6;
 constexpr int kSwapStageBlocks = 64;   // 16 KB per stage: a tile pair of 2 x 32 blocks or one tile of 64
-constexpr int kSwapCtasPerSm = 3;
+constexpr int kSwapCtasPerSm = 2;      // 2 x 5 stages of 16 KB in flight per SM
 constexpr int kSwapMaxPairs = (SV_MAX_QUBITS + 1) / 2;
+constexpr int kSwapChunksPerThread = kSwapStageBlocks * 16 / kSwapThreads;   // 16-byte chunks of a stage
+constexpr int kSwapRowsPerWarp = kSwapStageBlocks * 2 / (kSwapThreads / 32);  // 128-byte rows of a stage
 
 struct SwapArgs {
     int tb;                              // tile-local block bits
@@ -132,21 +134,47 @@ __global__ void __launch_bounds__(kSwapThreads, kSwapCtasPerSm) swap_kernel(floa
         meta[2 * (j % (kSwapStages + 1))] = b;
         meta[2 * (j % (kSwapStages + 1)) + 1] = p;
     };
-    // 16-byte copies of stage j's tile (and partner) into its slot: chunk q = (tile s, block t,
-    // chunk j of 16: real 0..7, imaginary 8..15)
+    __syncthreads();   // tables ready
+    // this thread's share of every stage is the same up to the tile bases: its copies (chunk q =
+    // (tile s, block t, 16-byte chunk c16 of 16: real 0..7, imaginary 8..15)) and its output rows
+    // (row r = (tile s, block t, half c); the warp's rows all have c = warp & 1), with offsets
+    // taken once from the tables
+    // (block offsets are kept as 32-bit block counts: a state has at most 2^30 blocks)
+    const int c16 = threadIdx.x & 15;      // the same in every chunk of this thread
+    uint32_t cdst[kSwapChunksPerThread];   // byte offset in the stage
+    uint32_t cblk[kSwapChunksPerThread];   // block offset from the tile's base
+#pragma unroll
+    for (int j = 0; j < kSwapChunksPerThread; ++j) {
+        const int q = threadIdx.x + kSwapThreads * j;
+        const int sq = q >> (a.tb + 4), t = (q >> 4) & (nb - 1);
+        cdst[j] = 16u * (uint32_t)((sq * nb + t) * 16 + (c16 ^ fsw[t]));
+        cblk[j] = (uint32_t)(toff[t] >> 6);
+    }
+    const int cl = (warp & 1) * 32 + lane;   // the rows' half and lane: the same in every row
+    uint32_t rsrc[kSwapRowsPerWarp];         // source float offset in the stage's tile
+    uint32_t rblk[kSwapRowsPerWarp];         // block offset from the output tile's base
+#pragma unroll
+    for (int k = 0; k < kSwapRowsPerWarp; ++k) {
+        const int r = warp + nw * k;
+        const int t = (r >> 1) & (nb - 1);
+        rsrc[k] = (uint32_t)(tab[t * 32 + lane] + (r & 1) * 32);
+        rblk[k] = (uint32_t)(toff[t] >> 6);
+    }
+    // 16-byte copies of stage j's tile (and partner) into its slot
     auto issue = [&](int j) {
         const long long base = meta[2 * (j % (kSwapStages + 1))], part = meta[2 * (j % (kSwapStages + 1)) + 1];
         if (base >= 0) {
             const int chunks = (part == base ? 16 : 32) * nb;
             const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stage + (j % kSwapStages) * kSwapStageBlocks * 64);
-            for (int q = threadIdx.x; q < chunks; q += kSwapThreads) {
-                const int s = q >> (a.tb + 4), t = (q >> 4) & (nb - 1), c16 = q & 15;
-                cp_async16(s0 + 16u * (uint32_t)((s * nb + t) * 16 + (c16 ^ fsw[t])), sv + (s ? part : base) * 64 + toff[t] + 4 * c16);
+            const float *gb = sv + base * 64 + 4 * c16, *gp = sv + part * 64 + 4 * c16;
+#pragma unroll
+            for (int i = 0; i < kSwapChunksPerThread; ++i) {
+                const int q = threadIdx.x + kSwapThreads * i;
+                if (q < chunks) cp_async16(s0 + cdst[i], ((q >> (a.tb + 4)) ? gp : gb) + (size_t)cblk[i] * 64);
             }
         }
         cp_async_commit();   // one group per stage, empty or not
     };
-    __syncthreads();   // tables ready
     if (threadIdx.x == 0)
         for (int j = 0; j < kSwapStages; ++j) plan(j);
     __syncthreads();   // the first stages' tiles ready
@@ -164,10 +192,15 @@ __global__ void __launch_bounds__(kSwapThreads, kSwapCtasPerSm) swap_kernel(floa
         // partner)
         const float *buf = stage + (i % kSwapStages) * kSwapStageBlocks * 64;
         const int rows = (part == base ? 2 : 4) * nb;
-        for (int r = warp; r < rows; r += nw) {
-            const int s = r >> (a.tb + 1), t = (r >> 1) & (nb - 1), c = r & 1;
-            const float *src = (part == base || s) ? buf : buf + nb * 64;
-            sv[(s ? part : base) * 64 + toff[t] + c * 32 + lane] = src[tab[t * 32 + lane] + c * 32];
+        float *ob = sv + base * 64 + cl, *op = sv + part * 64 + cl;
+        const float *other = part == base ? buf : buf + nb * 64;   // the source of the base tile's rows
+#pragma unroll
+        for (int k = 0; k < kSwapRowsPerWarp; ++k) {
+            const int r = warp + nw * k;
+            if (r < rows) {
+                const bool s = (r >> (a.tb + 1)) != 0;
+                (s ? op : ob)[(size_t)rblk[k] * 64] = (s ? buf : other)[rsrc[k]];
+            }
         }
     }
     cp_async_wait<0>();
