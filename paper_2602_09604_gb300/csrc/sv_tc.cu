@@ -884,7 +884,17 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
                     const float phi = ((tab[t][0] + tab[t][1]) + (tab[t][2] + tab[t][3])) + tab[t][4];
-                    sincosf(phi, &ei[t], &er[t]);
+                    // |phi| <= 5 pi: less the nearest multiple of 2 pi (2 pi split into a float
+                    // and its remainder, so r keeps the rounding of phi), then the hardware
+                    // sine and cosine, whose absolute error on [-pi, pi] is below 1e-6, scaled
+                    // back to unit modulus (the phases keep the state's norm)
+                    const float k = rintf(phi * 0.15915494309189535f);
+                    const float r = fmaf(-k, -1.7484555e-07f, fmaf(-k, 6.28318548f, phi));
+                    float sn, cs;
+                    __sincosf(r, &sn, &cs);
+                    const float inv = rsqrtf(fmaf(cs, cs, sn * sn));
+                    er[t] = cs * inv;
+                    ei[t] = sn * inv;
                 }
             }
             if (!wait(bar_accfull + 8 * c, (uint32_t)((i / kWsAcc) & 1), 0x20)) break;
