@@ -164,15 +164,17 @@ def device_state_metrics(ref_buf, buf, chunk_blocks=1 << 21):
 
 
 def large_configs(B, wl, model, stream):
-    """The 33-qubit grid circuit (6x6 minus 3 sites, 24 cycles, seed 4; 64 GiB state) and the
-    34-qubit QFT of a seeded basis state (128 GiB): learned partition vs fixed greedy fusion at
-    every max size (3xBF16 tensor cores for 4+ qubit gates) and the plain fp32 CUDA-core K = 4,
-    device time of one circuit each (apply only; the state is set before each timing).  Then the
-    256-circuit HEA batch: one persistent graph launch (autotuned) vs the per-circuit launch loop."""
+    """The 30-qubit QFT of a seeded basis state (8 GiB state), the 33-qubit grid circuit (6x6 minus
+    3 sites, 24 cycles, seed 4; 64 GiB) and the 34-qubit QFT (128 GiB): learned partition vs fixed
+    greedy fusion at every max size (3xBF16 tensor cores for 4+ qubit gates), the plain fp32
+    CUDA-core K = 4 and post-phase fusion, device time of one circuit each (apply only; the state is
+    set before each timing).  Then the 256-circuit HEA batch: one persistent graph launch
+    (autotuned) vs the per-circuit launch loop."""
     import torch
     from paper_2602_09604_gb300.state import DeviceState
     out = {}
-    for name, n, gates, x in (("grid33_24c", wl.GRID_33.n, wl.random_grid_circuit(wl.GRID_33, 24, seed=4), 0),
+    for name, n, gates, x in (("qft30", 30, wl.qft_circuit(30), wl.qft_basis_index(30, seed=30)),
+                              ("grid33_24c", wl.GRID_33.n, wl.random_grid_circuit(wl.GRID_33, 24, seed=4), 0),
                               ("qft34", 34, wl.qft_circuit(34), wl.qft_basis_index(34, seed=34))):
         st = DeviceState(n, stream=stream)
         res = {}

@@ -100,6 +100,30 @@ def _qft_samples(st, n, x, seed):
     return float(d.max() * 2.0 ** (n / 2)), float(np.sqrt(np.mean(d * d) * 2.0 ** n))
 
 
+def test_30q_qft_learned_vs_fixed(env):
+    """The 30-qubit QFT (the second workload of the 30-qubit configuration): every fixed fusion
+    size, the plain fp32 K = 4 and the learned partition timed on one basis input; the learned
+    circuit (the post-phase partition with its swap network) checked against the closed form."""
+    B, DS, m = env
+    n = 30
+    gates = wl.qft_circuit(n)
+    x = wl.qft_basis_index(n, seed=30)
+    st = DS(n)
+    res = time_variants(B, st, n, gates, m, init=x)
+    f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, model=m)
+    st.init(x)
+    st.apply(f)
+    B.sv_fused_free(f)
+    nrm = st.norm()
+    max_rel, l2 = _qft_samples(st, n, x, 31)
+    st.free()
+    REPORT["qft30"] = {"gates": len(gates), "variants": res, "norm": nrm, "max_rel_amp_error": max_rel, "l2_estimate": l2}
+    assert abs(nrm - 1) < 1e-4 and l2 <= 1e-4 and max_rel < 2e-4, (nrm, l2, max_rel)
+    best_fixed = min(v["device_s"] for k, v in res.items() if k.startswith("greedy"))
+    assert res["learned_bf16x3"]["fused_gates"] <= 8, res
+    assert res["learned_bf16x3"]["device_s"] <= 0.25 * best_fixed, res
+
+
 def test_34q_qft_learned_vs_fixed(env):
     B, DS, m = env
     n = 34
