@@ -5,6 +5,7 @@ For timing and profiling single kernels outside the full circuit step:
     python -m paper_2602_09604_gb300.opbench expval --n 26 --strings 8
     python -m paper_2602_09604_gb300.opbench controlled --n 26 --k 1 --controls 7,12
     python -m paper_2602_09604_gb300.opbench batch --count 64
+    python -m paper_2602_09604_gb300.opbench qft --n 27 --mode phases
 
 Every run does --warm untimed repetitions, then --repeats timed ones, and prints one JSON line.
 """
@@ -80,9 +81,42 @@ def run_batch(a):
             "traffic_gbs": info["traffic_bytes"] / (us * 1e-6) / 1e9}
 
 
+def run_qft(a):
+    """The n-qubit QFT of a seeded basis state, fused in the given mode (3xBF16 tensor cores for
+    4+ qubit gates), applied whole: the circuit's device time and each fused gate's."""
+    gates = wl.qft_circuit(a.n)
+    x = wl.qft_basis_index(a.n, seed=a.n)
+    kw = dict(max_k=6, precision=B.PREC_BF16X3, tc_min_k=4)
+    model = None
+    if a.mode == "phases":
+        kw["mode"] = B.FUSE_PHASES
+    elif a.mode == "learned":
+        import os
+        model = B.sv_mlp_load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "cost_model_gb300.bin"))
+        kw.update(mode=B.FUSE_LEARNED, model=model)
+    f = B.sv_fuse_circuit(gates, a.n, **kw)
+    st = DeviceState(a.n)
+    ts = []
+    for r in range(a.warm + a.repeats):   # the state is set before each run, outside the timing
+        st.init(x)
+        ts.append(_time(lambda: st.apply(f), st.stream, 0, 1))
+    us = statistics.median(ts[a.warm:])
+    st.init(x)
+    rec = st.apply(f, timings=True)
+    B.sv_device_status()
+    out = {"op": "qft", "n": a.n, "mode": a.mode, "fused": B.sv_fused_count(f), "us": us,
+           "gates": [(r["k"], B.PATH_NAMES[r["path"]], round(r["us"], 1)) for r in rec], "norm": st.norm()}
+    st.free()
+    B.sv_fused_free(f)
+    if model is not None:
+        B.sv_mlp_free(model)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["expval", "controlled", "batch"])
+    ap.add_argument("op", choices=["expval", "controlled", "batch", "qft"])
+    ap.add_argument("--mode", default="phases", choices=["phases", "learned", "greedy"], help="qft: fusion mode")
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--strings", type=int, default=1)
     ap.add_argument("--x", default="0x20108", help="x mask of the Pauli strings")
@@ -104,7 +138,7 @@ def main(argv=None):
     ap.add_argument("--warm", type=int, default=1)
     ap.add_argument("--repeats", type=int, default=3)
     a = ap.parse_args(argv)
-    out = {"expval": run_expval, "controlled": run_controlled, "batch": run_batch}[a.op](a)
+    out = {"expval": run_expval, "controlled": run_controlled, "batch": run_batch, "qft": run_qft}[a.op](a)
     print(json.dumps(out))
 
 
