@@ -120,3 +120,15 @@ def test_plan_rejects_bad_input(B):
             B.sv_batch_plan_stages(f, bad)
     assert len(B.sv_batch_plan_stages(f, 10)) == 1   # no gates: one stage that builds |0...0>
     B.sv_fused_free(f)
+
+
+def test_plan_refuses_post_phases_and_swap_networks(B):
+    """Gates with post-phases and swap networks (SV_FUSE_PHASES) are for single states: the stage
+    planner (like the batch) refuses a circuit holding them."""
+    n = 12
+    f = B.sv_fuse_circuit(wl.qft_circuit(n), n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+    kinds = {B.sv_fused_get_info(f, i)["path"] for i in range(B.sv_fused_count(f))}
+    assert B.PATH_SWAPS in kinds
+    with pytest.raises(B.SvError):
+        B.sv_batch_plan_stages(f, 10)
+    B.sv_fused_free(f)
