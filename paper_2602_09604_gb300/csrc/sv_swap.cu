@@ -285,13 +285,19 @@ int launch_swaps(float *sv, int n, const FusedGate &g, cudaStream_t stream, int 
     const size_t smem = (size_t)kSwapStages * kSwapStageBlocks * 64 * sizeof(float) + (size_t)nb * sizeof(long long) +
                         (size_t)(2 * (kSwapStages + 1) + 2 * a.n_o) * sizeof(long long) + (size_t)nb * 32 * sizeof(unsigned short) +
                         (size_t)nb;
-    static bool attr_set[64] = {};
+    // the shared-memory limit is a per-device function attribute: set once per device
+    static std::mutex mu;
+    static uint64_t attr_set = 0;
     int dev = 0;
     SV_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 64 && !attr_set[dev]) {
-        SV_CUDA_TRY(cudaFuncSetAttribute(swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)kSwapStages * kSwapStageBlocks * 64 * sizeof(float) + 8192)));
-        attr_set[dev] = true;
+    {
+        const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!(attr_set & bit) || !bit) {
+            SV_CUDA_TRY(cudaFuncSetAttribute(swap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((size_t)kSwapStages * kSwapStageBlocks * 64 * sizeof(float) + 8192)));
+            attr_set |= bit;
+        }
     }
     const long long n_tiles = 1ll << a.n_o;
     const long long grid = std::min<long long>(n_tiles, (long long)num_sms * kSwapCtasPerSm);
