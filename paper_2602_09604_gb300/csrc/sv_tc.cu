@@ -33,6 +33,7 @@
 #include <cstring>
 #include <exception>
 #include <mutex>
+#include <type_traits>
 
 #include "sv_internal.h"
 
@@ -901,18 +902,21 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
             tc_fence_after();
             const uint32_t td = tmem + (uint32_t)(c * S::KD) + t_lane;
             if constexpr (PH) {
-                // members in Gray-code order, one complex product each
-                // EW = 8: two warps per lane quarter, each with half of the members
-#pragma unroll
-                for (int qq = 0; qq < 16 / EW; ++qq) {   // members 16 qc .. 16 qc + 15 (columns: real, then + 64 imaginary)
-                    const int qc = (EW == 8 ? 2 * part : 0) + qq;
+                // members in Gray-code order, one complex product each; chunk qc = members
+                // 16 qc .. 16 qc + 15 (columns: real, then + 64 imaginary), a compile-time index
+                // so that the member offsets are immediate operands and e_t stays in registers
+                auto chunk = [&](auto qc_c) {
+                    constexpr int qc = decltype(qc_c)::value;
                     float ore[16], oim[16];
                     tmem_ld16x2(td + (uint32_t)(16 * qc), td + (uint32_t)(64 + 16 * qc), ore, oim);
                     if (valid) {
                         // the chunk's members share bits 4 and 5 (= qc)
                         float fr = 1.f, fi = 0.f;
-                        if (qc & 1) { fr = er[4]; fi = ei[4]; }
-                        if (qc & 2) {
+                        if constexpr ((qc & 1) != 0) {
+                            fr = er[4];
+                            fi = ei[4];
+                        }
+                        if constexpr ((qc & 2) != 0) {
                             const float nr = fr * er[5] - fi * ei[5], ni = fr * ei[5] + fi * er[5];
                             fr = nr;
                             fi = ni;
@@ -921,7 +925,7 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                         for (int i = 0; i < 16; ++i) {
                             const int x = i ^ (i >> 1);
                             if (i > 0) {   // bit t of the member changed: times e_t or its conjugate
-                                const int t = __ffs(i) - 1;
+                                const int t = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : 3;
                                 const float si = ((x >> t) & 1) ? ei[t] : -ei[t];
                                 const float nr = fr * er[t] - fi * si, ni = fr * si + fi * er[t];
                                 fr = nr;
@@ -932,6 +936,20 @@ __device__ __forceinline__ void tc_ws_body(float *__restrict__ sv, const TcArgs 
                             sv[fb + a.foff[16 * qc + x] + 32] = yi;
                         }
                     }
+                };
+                if constexpr (EW == 8) {   // two warps per lane quarter, each with half of the members
+                    if (part == 0) {
+                        chunk(std::integral_constant<int, 0>{});
+                        chunk(std::integral_constant<int, 1>{});
+                    } else {
+                        chunk(std::integral_constant<int, 2>{});
+                        chunk(std::integral_constant<int, 3>{});
+                    }
+                } else {
+                    chunk(std::integral_constant<int, 0>{});
+                    chunk(std::integral_constant<int, 1>{});
+                    chunk(std::integral_constant<int, 2>{});
+                    chunk(std::integral_constant<int, 3>{});
                 }
             } else {
             constexpr int NB = EW == 4 ? 4 : 2;   // 32-column blocks this warp reads
