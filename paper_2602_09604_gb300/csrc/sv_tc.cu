@@ -1047,8 +1047,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 }
 
 // k = 6, at most two targets below qubit 5 (not both 0 and 1), with post-phases in the epilogue:
-// two epilogue warps per tensor-memory lane quarter (the phases are the epilogue's work)
-constexpr int kWsPhEpiWarps = 8;
+// one epilogue warp per tensor-memory lane quarter, as without them (two per quarter, 800 threads
+// at 72 registers, gave the loaders fewer registers and ran 2% slower)
+constexpr int kWsPhEpiWarps = 4;
 constexpr int kWsPhThreads = (kWsLoadWarps + kWsPhEpiWarps + 1) * 32;
 template <int MODE>
 __global__ void __launch_bounds__(kWsPhThreads, 1) apply_tc_ws_kernel_ph(float *__restrict__ sv, const __grid_constant__ TcArgs a)
