@@ -100,7 +100,9 @@ enum sv_fuse_mode {
                              controlled-phase ladder (a QFT) then costs one pass per six qubits.
                              Gates that cannot carry post-phases (fewer than six qubits, or three or
                              more targets below qubit 5) get them as diagonal fused gates after
-                             them.  Not with start_qubits. */
+                             them.  On states of 10 or more qubits, three or more consecutive SWAP
+                             gates on disjoint qubits become one swap network (SV_PATH_SWAPS: one
+                             in-place permutation pass).  Not with start_qubits. */
 };
 
 typedef struct sv_state sv_state;   /* opaque; owns no state memory, only small workspaces */
