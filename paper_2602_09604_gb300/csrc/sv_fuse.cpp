@@ -797,7 +797,10 @@ int merge_search(std::vector<Candidate> &cands, GateCost &cost, int n_qubits, in
 // carry post terms on the tensor cores (it must be a 6-qubit gate with at most two targets below
 // qubit 5, not both 0 and 1 among them) is first widened with the terms' outside qubits (the
 // terms become ordinary gates), then with idle qubits of at least 5; failing that, its terms
-// follow it as diagonal fused gates.
+// follow it as diagonal fused gates.  A run of at least kMinSwapRun consecutive SWAP gates on
+// disjoint qubits becomes one swap network (SV_PATH_SWAPS): the open gate is emitted first if it
+// or its terms touch the run's qubits, held gates on them likewise, and the run stays open until a
+// gate on one of its qubits arrives (gates on other qubits commute with it).
 FusedGate block_to_gate(Block &b);
 
 struct PhaseBlock {
