@@ -227,3 +227,46 @@ def test_swap_runs_among_other_gates_are_exact(B, n, seed):
     got = apply_fused_with_phases(B, f, n, psi)
     assert np.max(np.abs(got - oracle.run_circuit(n, gates, init))) <= 1e-11
     B.sv_fused_free(f)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_phase_partition_with_kept_controls_and_swaps_is_exact(B, seed):
+    """Kept controlled gates (more controls than the fusion size allows folding), diagonal pairs,
+    dense gates and swap runs in one circuit: the post-phase partition, and the learned search
+    with it among its candidates, give the oracle's state."""
+    rng = np.random.default_rng(seed)
+    n = 10
+    gates = []
+    for _ in range(4):
+        gates += _diag_circuit(n, 20, rng)
+        qs = [int(q) for q in rng.permutation(n)]
+        gates.append(wl.Gate((qs[0],), wl.random_unitary(2, rng), tuple(qs[1:8])))   # 7 controls: kept
+        qs = [int(q) for q in rng.permutation(n)]
+        gates += [wl.Gate((qs[2 * i], qs[2 * i + 1]), SWAP) for i in range(4)]
+    init = int(rng.integers(0, 1 << n))
+    ref = oracle.run_circuit(n, gates, init)
+    for f in (B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3),
+              _learned(B, gates, n, 1.1)):
+        count = B.sv_fused_count(f)
+        infos = [B.sv_fused_get_info(f, i) for i in range(count)]
+        assert sum(i["path"] == B.PATH_CONTROLLED for i in infos) == 4
+        assert sum(i["n_source_gates"] for i in infos) == len(gates)
+        psi = np.zeros(1 << n, complex)
+        psi[init] = 1.0
+        # apply gate by gate: controlled gates through the oracle with their controls
+        idx = np.arange(1 << n)
+        for i, info in enumerate(infos):
+            if info["path"] == B.PATH_SWAPS:
+                for a, b in B.sv_fused_get_swaps(f, i):
+                    oracle.apply_gate(psi, n, wl.Gate((a, b), SWAP))
+                continue
+            oracle.apply_gate(psi, n, wl.Gate(info["targets"], B.sv_fused_get_matrix(f, i), info["controls"]))
+            post = B.sv_fused_get_post_phases(f, i)
+            if post:
+                ph = np.zeros(1 << n)
+                for j, q, th in post:
+                    ph += th * (((idx >> info["targets"][j]) & 1) & ((idx >> q) & 1))
+                psi *= np.exp(1j * ph)
+        got = psi
+        assert np.max(np.abs(got - ref)) <= 1e-11
+        B.sv_fused_free(f)
