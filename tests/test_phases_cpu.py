@@ -270,3 +270,19 @@ def test_phase_partition_with_kept_controls_and_swaps_is_exact(B, seed):
         got = psi
         assert np.max(np.abs(got - ref)) <= 1e-11
         B.sv_fused_free(f)
+
+
+def test_phase_mode_below_six_qubits_has_swaps_but_no_post_terms(B):
+    """With max_k below 6 no fused gate can carry post terms (their kernel is the six-qubit one),
+    but swap runs still become swap networks; the circuit stays exact."""
+    n = 11
+    gates = wl.qft_circuit(n)
+    f = B.sv_fuse_circuit(gates, n, max_k=4, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+    count = B.sv_fused_count(f)
+    assert all(not B.sv_fused_get_post_phases(f, i) for i in range(count))
+    assert sum(B.sv_fused_get_info(f, i)["path"] == B.PATH_SWAPS for i in range(count)) == 1
+    psi = np.zeros(1 << n, complex)
+    psi[77] = 1.0
+    got = apply_fused_with_phases(B, f, n, psi)
+    assert np.max(np.abs(got - oracle.run_circuit(n, gates, 77))) <= 1e-12
+    B.sv_fused_free(f)
