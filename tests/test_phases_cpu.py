@@ -286,3 +286,35 @@ def test_phase_mode_below_six_qubits_has_swaps_but_no_post_terms(B):
     got = apply_fused_with_phases(B, f, n, psi)
     assert np.max(np.abs(got - oracle.run_circuit(n, gates, 77))) <= 1e-12
     B.sv_fused_free(f)
+
+
+def test_phase_partition_exact_on_random_circuits_property(B):
+    """Property check over many random circuits (hypothesis draws the seed, the size and the gate
+    mix): the post-phase partition with post terms and swap networks is the circuit."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2**31 - 1), n=st.integers(10, 11), count=st.integers(1, 90),
+               swap_every=st.integers(0, 4))
+    def check(seed, n, count, swap_every):
+        rng = np.random.default_rng(seed)
+        gates = []
+        for r in range(count):
+            gates += _diag_circuit(n, 1, rng)
+            if swap_every and r % (swap_every * 7) == 0:
+                qs = [int(q) for q in rng.permutation(n)]
+                gates += [wl.Gate((qs[2 * i], qs[2 * i + 1]), SWAP) for i in range(int(rng.integers(1, n // 2 + 1)))]
+        f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_PHASES, precision=B.PREC_BF16X3)
+        try:
+            infos = [B.sv_fused_get_info(f, i) for i in range(B.sv_fused_count(f))]
+            assert sum(i["n_source_gates"] for i in infos) == len(gates)
+            init = int(rng.integers(0, 1 << n))
+            psi = np.zeros(1 << n, complex)
+            psi[init] = 1.0
+            got = apply_fused_with_phases(B, f, n, psi)
+            assert np.max(np.abs(got - oracle.run_circuit(n, gates, init))) <= 1e-11
+        finally:
+            B.sv_fused_free(f)
+
+    check()
