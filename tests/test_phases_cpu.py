@@ -318,3 +318,35 @@ def test_phase_partition_exact_on_random_circuits_property(B):
             B.sv_fused_free(f)
 
     check()
+
+
+def test_learned_search_exact_under_random_costs_property(B):
+    """Whatever the cost function says (hypothesis draws the circuit and a random cost table), the
+    partition the learned search returns, post-phase candidate included, is the circuit."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=25, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2**31 - 1), post_factor=st.floats(0.2, 3.0))
+    def check(seed, post_factor):
+        rng = np.random.default_rng(seed)
+        n = 10
+        gates = wl.qft_circuit(n) if rng.random() < 0.3 else _diag_circuit(n, 60, rng)
+        salt = int(rng.integers(1, 1 << 30))
+
+        def cost(k, targets, path, nq):
+            h = (hash((k, tuple(targets), path & ~B.PATH_POST_PHASES, nq, salt)) % 1000) / 1000.0
+            c = 2.0 ** nq * (0.5 + h)
+            return c * (post_factor if path & B.PATH_POST_PHASES else 1.0)
+        f = B.sv_fuse_circuit(gates, n, max_k=6, mode=B.FUSE_LEARNED, precision=B.PREC_BF16X3, tc_min_k=4,
+                              cost_fn=cost)
+        try:
+            init = int(rng.integers(0, 1 << n))
+            psi = np.zeros(1 << n, complex)
+            psi[init] = 1.0
+            got = apply_fused_with_phases(B, f, n, psi)
+            assert np.max(np.abs(got - oracle.run_circuit(n, gates, init))) <= 1e-11
+        finally:
+            B.sv_fused_free(f)
+
+    check()
